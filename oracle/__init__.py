@@ -1,0 +1,250 @@
+"""FP64 CPU oracle for the stochastic Chebyshev moments of KITE (arXiv:1910.05194).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The CUDA library and its Python binding never import it, and it never
+imports them: the two sides meet only through the definitions in the paper.
+
+The arithmetic lives in ``kite_oracle.c`` (plain C, FP64, compiled with
+``-ffp-contract=off``); this module builds it with gcc on first use and wraps it
+with numpy-friendly functions.  Section/equation citations are in the C source.
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kite_oracle.c")
+_HDR = os.path.join(_HERE, "kite_oracle.h")
+_BUILD = os.path.join(_HERE, "_build")
+_LOCK = threading.Lock()
+_LIB = None
+
+HONEYCOMB = 0
+SQUARE = 1
+
+
+def _source_hash() -> str:
+    h = hashlib.sha1()
+    for p in (_SRC, _HDR):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle-<hash>.so`` (gcc, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    out = os.path.join(_BUILD, f"liboracle-{_source_hash()}.so")
+    if os.path.exists(out) and not force:
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+class System(ctypes.Structure):
+    """Mirror of ``orc_system``: a periodic honeycomb or square lattice with disorder."""
+    _fields_ = [("lattice", ctypes.c_int32), ("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("t", ctypes.c_double), ("W", ctypes.c_double),
+                ("delta", ctypes.c_double), ("p_vac", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+def make_system(lattice=HONEYCOMB, Lx=8, Ly=8, t=-2.7, W=0.0, delta=0.0, p_vac=0.0, seed=1):
+    return System(int(lattice), int(Lx), int(Ly), 0, float(t), float(W), float(delta),
+                  float(p_vac), int(seed))
+
+
+def lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            L = ctypes.CDLL(build())
+            P = ctypes.POINTER
+            d, i32, i64 = ctypes.c_double, ctypes.c_int, ctypes.c_int64
+            vp = ctypes.c_void_p
+            L.orc_philox4x32_10.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]
+            L.orc_norb.argtypes = [P(System)]
+            L.orc_norb.restype = i64
+            L.orc_neighbours.argtypes = [P(System), i64, P(i64)]
+            L.orc_neighbours.restype = i32
+            L.orc_bounds_auto.argtypes = [P(System), P(d), P(d)]
+            L.orc_disorder.argtypes = [P(System), i32, vp, vp]
+            L.orc_random_phase.argtypes = [P(System), i32, i32, vp, vp]
+            L.orc_moments_1d.argtypes = [P(System), i32, i32, i32, d, d, vp, vp, i32]
+            L.orc_moments_1d.restype = i32
+            L.orc_replica_1d.argtypes = [P(System), i32, i32, i32, d, d, i32, vp, vp, vp, i32]
+            L.orc_replica_1d.restype = i32
+            L.orc_velocity_x.argtypes = [P(System), vp, d, vp, vp]
+            L.orc_moments_2d.argtypes = [P(System), i32, i32, i32, d, d, vp, vp, vp, vp, i32]
+            L.orc_moments_2d.restype = i32
+            L.orc_kernel_jackson.argtypes = [i32, vp]
+            L.orc_kernel_lorentz.argtypes = [i32, d, vp]
+            L.orc_dos.argtypes = [vp, i32, vp, d, d, vp, i32, vp]
+            L.orc_cpgf_coeff.argtypes = [i32, d, d, i32, P(d), P(d)]
+            _LIB = L
+    return _LIB
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def norb(sys: System) -> int:
+    return int(lib().orc_norb(ctypes.byref(sys)))
+
+
+def neighbours(sys: System, o: int):
+    nb = (ctypes.c_int64 * 4)()
+    z = lib().orc_neighbours(ctypes.byref(sys), int(o), nb)
+    return [int(nb[k]) for k in range(z)]
+
+
+def bounds_auto(sys: System):
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    lib().orc_bounds_auto(ctypes.byref(sys), ctypes.byref(lo), ctypes.byref(hi))
+    return lo.value, hi.value
+
+
+def disorder(sys: System, realisation: int = 0):
+    """Raw on-site energies V (eV) and the vacancy mask of one realisation."""
+    n = norb(sys)
+    V = np.empty(n, np.float64)
+    vac = np.empty(n, np.uint8)
+    lib().orc_disorder(ctypes.byref(sys), int(realisation), _ptr(V), _ptr(vac))
+    return V, vac
+
+
+def random_phase(sys: System, R: int, realisation: int = 0):
+    """Random-phase start vectors [R][N] complex128 (zero on vacancies)."""
+    _, vac = disorder(sys, realisation)
+    n = norb(sys)
+    out = np.empty((R, n, 2), np.float64)
+    lib().orc_random_phase(ctypes.byref(sys), int(realisation), int(R), _ptr(vac), _ptr(out))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def _as_r0(r0, R, n):
+    if r0 is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(r0, np.complex128).reshape(R, n))
+    return np.ascontiguousarray(np.stack([a.real, a.imag], axis=-1))
+
+
+def _bounds(sys, e_min, e_max):
+    if e_min is None or e_max is None:
+        return bounds_auto(sys)
+    return float(e_min), float(e_max)
+
+
+def moments_1d(sys: System, M: int, R: int, realisation: int = 0, e_min=None, e_max=None,
+               r0=None, threads: int = 0):
+    """Per-vector complex moments mu[r][n] = <r0|T_n(H~)|r0>/N_eff, plain FP64."""
+    n = norb(sys)
+    lo, hi = _bounds(sys, e_min, e_max)
+    r0a = _as_r0(r0, R, n)
+    mu = np.empty((R, M, 2), np.float64)
+    rc = lib().orc_moments_1d(ctypes.byref(sys), int(realisation), int(M), int(R), lo, hi,
+                              _ptr(r0a), _ptr(mu), int(threads))
+    if rc != 0:
+        raise ValueError(f"orc_moments_1d failed ({rc})")
+    return mu[..., 0] + 1j * mu[..., 1]
+
+
+def replica_1d(sys: System, M: int, R: int, precision: int, realisation: int = 0, e_min=None,
+               e_max=None, r0=None, want_last: bool = False, threads: int = 0):
+    """Fixed-rounding replica of the recursion (precision 0 = FP32, 1 = FP64).
+
+    Returns (mu[r][n] complex, last) where ``last`` is None or [R][2][N] complex of the
+    working precision holding (r_{M-2}, r_{M-1})."""
+    n = norb(sys)
+    lo, hi = _bounds(sys, e_min, e_max)
+    r0a = _as_r0(r0, R, n)
+    mu = np.empty((R, M, 2), np.float64)
+    dt = np.float32 if precision == 0 else np.float64
+    last = np.empty((R, 2, n, 2), dt) if want_last else None
+    rc = lib().orc_replica_1d(ctypes.byref(sys), int(realisation), int(M), int(R), lo, hi,
+                              int(precision), _ptr(r0a), _ptr(mu), _ptr(last), int(threads))
+    if rc != 0:
+        raise ValueError(f"orc_replica_1d failed ({rc})")
+    muc = mu[..., 0] + 1j * mu[..., 1]
+    if last is not None:
+        cdt = np.complex64 if precision == 0 else np.complex128
+        last = last.view(cdt).reshape(R, 2, n)
+    return muc, last
+
+
+def velocity_x(sys: System, vac, t_scaled: float, vec):
+    n = norb(sys)
+    v = np.ascontiguousarray(np.stack([np.real(vec), np.imag(vec)], -1).astype(np.float64))
+    out = np.empty((n, 2), np.float64)
+    lib().orc_velocity_x(ctypes.byref(sys), _ptr(np.ascontiguousarray(vac, np.uint8)),
+                         float(t_scaled), _ptr(v), _ptr(out))
+    return out[:, 0] + 1j * out[:, 1]
+
+
+def moments_2d(sys: System, M: int, R: int, realisation: int = 0, e_min=None, e_max=None,
+               r0=None, want_families: bool = False, threads: int = 0):
+    """mu_nm = <a_n|b_m>/N_eff averaged over R vectors (a_n = T_n h~ r, b_m = h~ T_m r)."""
+    n = norb(sys)
+    lo, hi = _bounds(sys, e_min, e_max)
+    r0a = _as_r0(r0, R, n)
+    mu = np.empty((M, M, 2), np.float64)
+    A = np.empty((M, n, 2), np.float64) if want_families else None
+    B = np.empty((M, n, 2), np.float64) if want_families else None
+    rc = lib().orc_moments_2d(ctypes.byref(sys), int(realisation), int(M), int(R), lo, hi,
+                              _ptr(r0a), _ptr(mu), _ptr(A), _ptr(B), int(threads))
+    if rc != 0:
+        raise ValueError(f"orc_moments_2d failed ({rc})")
+    out = mu[..., 0] + 1j * mu[..., 1]
+    if want_families:
+        return out, A[..., 0] + 1j * A[..., 1], B[..., 0] + 1j * B[..., 1]
+    return out
+
+
+def kernel_jackson(M: int):
+    g = np.empty(M, np.float64)
+    lib().orc_kernel_jackson(int(M), _ptr(g))
+    return g
+
+
+def kernel_lorentz(M: int, lam: float):
+    g = np.empty(M, np.float64)
+    lib().orc_kernel_lorentz(int(M), float(lam), _ptr(g))
+    return g
+
+
+def dos(mu, E, e_min: float, e_max: float, g=None):
+    """rho(E) per orbital per eV from raw moments mu[0..M-1] (Eqs. e7/e8a + kernel g)."""
+    mu = np.ascontiguousarray(np.real(np.asarray(mu)), np.float64)
+    E = np.ascontiguousarray(E, np.float64)
+    ga = None if g is None else np.ascontiguousarray(g, np.float64)
+    rho = np.empty(E.shape[0], np.float64)
+    lib().orc_dos(_ptr(mu), int(mu.shape[0]), _ptr(ga), float(e_min), float(e_max), _ptr(E),
+                  int(E.shape[0]), _ptr(rho))
+    return rho
+
+
+def cpgf_coeff(n: int, eps: float, eta: float, sigma: int) -> complex:
+    re, im = ctypes.c_double(), ctypes.c_double()
+    lib().orc_cpgf_coeff(int(n), float(eps), float(eta), int(sigma), ctypes.byref(re),
+                         ctypes.byref(im))
+    return complex(re.value, im.value)

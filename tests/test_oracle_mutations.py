@@ -1,0 +1,60 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a temporary copy of ``oracle/kite_oracle.c`` (on the
+CPU, never in the tree), rebuilds it, and re-runs the pin suite against the mutant:
+at least one pin has to fail.  This is what makes the pins evidence rather than
+restatements of the oracle.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = [
+    ("velocity bond sign", "dx[1] = -0.5;", "dx[1] = 0.5;"),
+    ("wrong neighbour cell",
+     "nb[1] = 2 * (orc_wrap(y - 1, Ly) * Lx + orc_wrap(x + 1, Lx)) + 1;",
+     "nb[1] = 2 * (orc_wrap(y - 1, Ly) * Lx + orc_wrap(x - 1, Lx)) + 1;"),
+    ("inverted DOS weight (printed Eq. e8 prefactor)",
+     "sum += 2.0 * (g ? g[n] : 1.0) * mu[n] * t;", "sum += 0.5 * (g ? g[n] : 1.0) * mu[n] * t;"),
+    ("recursion sign", "nxt[k] = 2.0 * nxt[k] - prev[k];", "nxt[k] = 2.0 * nxt[k] + prev[k];"),
+    ("conjugation dropped in <a|b>",
+     "si += a[2 * o] * b[2 * o + 1] - a[2 * o + 1] * b[2 * o];",
+     "si += a[2 * o] * b[2 * o + 1] + a[2 * o + 1] * b[2 * o];"),
+    ("disorder not centred", "double v = sys->W * (u - 0.5);", "double v = sys->W * u;"),
+    ("velocity loses its sign", "double w = h->dx[4 * o + k] * h->tt;",
+     "double w = fabs(h->dx[4 * o + k]) * h->tt;"),
+    ("Jackson kernel off by one",
+     "g[n] = ((double)(M - n + 1) * cos(q * n) + sin(q * n) * cot) / (double)(M + 1);",
+     "g[n] = ((double)(M - n) * cos(q * n) + sin(q * n) * cot) / (double)(M + 1);"),
+    ("CPGF branch flipped", "double complex num = cexp(-s * I * (double)n * theta);",
+     "double complex num = cexp(s * I * (double)n * theta);"),
+    ("on-site term dropped", "double re = h->Vt[o] * x[2 * o], im = h->Vt[o] * x[2 * o + 1];",
+     "double re = 0.0 * x[2 * o], im = 0.0 * x[2 * o + 1];"),
+    ("normalised by N instead of N_eff", "if (!h->vac[o]) h->n_eff++;", "h->n_eff++;"),
+    ("vacancy draw ignored", "vac[o] = ((uint64_t)x[2] < thr) ? 1 : 0;", "vac[o] = 0;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, name, old, new):
+    src_dir = os.path.join(ROOT, "oracle")
+    dst = tmp_path / "oracle"
+    dst.mkdir()
+    for f in ("__init__.py", "kite_oracle.h"):
+        shutil.copy(os.path.join(src_dir, f), dst / f)
+    with open(os.path.join(src_dir, "kite_oracle.c")) as f:
+        src = f.read()
+    assert old in src, f"mutation anchor missing: {name}"
+    (dst / "kite_oracle.c").write_text(src.replace(old, new, 1))
+    shutil.copy(os.path.join(ROOT, "tests", "test_oracle_pins.py"), tmp_path / "test_oracle_pins.py")
+    env = dict(os.environ, PYTHONPATH=str(tmp_path))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
+                        "-p", "no:randomly", str(tmp_path / "test_oracle_pins.py")],
+                       cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught mutation '{name}':\n{r.stdout[-2000:]}"
+    assert "failed" in r.stdout, r.stdout[-2000:]

@@ -1,0 +1,389 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a closed form
+(Bloch dispersion of the clean lattice), a library routine (dense
+``numpy.linalg.eigh``), an exact low-order trace identity, the white-noise
+statistics the paper asks of the random vectors (Sec. 2c), or an exact quadrature
+rule.  A dropped term, a wrong sign, a transposed index or an inverted prefactor in
+the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+T_EV = -2.7
+
+
+def cheb_T(n_max, x):
+    """T_0..T_{n_max-1} at x via cos(n arccos x) (closed form, not the recursion)."""
+    x = np.clip(np.asarray(x, np.float64), -1.0, 1.0)
+    th = np.arccos(x)
+    n = np.arange(n_max)[:, None]
+    return np.cos(n * th[None, :])
+
+
+def dense_h(sys, realisation=0, e_min=None, e_max=None):
+    """Dense rescaled Hamiltonian on the non-vacant orbitals (uses oracle geometry and
+    draws, which the Bloch test pins independently)."""
+    n = oracle.norb(sys)
+    lo, hi = (oracle.bounds_auto(sys) if e_min is None else (e_min, e_max))
+    dp, dm = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    V, vac = oracle.disorder(sys, realisation)
+    H = np.zeros((n, n))
+    for o in range(n):
+        if vac[o]:
+            continue
+        H[o, o] = (V[o] - dp) / dm
+        for j in oracle.neighbours(sys, o):
+            if not vac[j]:
+                H[o, j] += sys.t / dm
+    keep = np.where(vac == 0)[0]
+    return H[np.ix_(keep, keep)], keep, vac
+
+
+def exact_trace_moments(sys, M, realisation=0, e_min=None, e_max=None):
+    """Oracle run with every basis vector as a start vector: sum over vectors of
+    <e_o|T_n|e_o>/N_eff = Tr T_n(H~)/N_eff."""
+    n = oracle.norb(sys)
+    r0 = np.eye(n, dtype=np.complex128)
+    mu = oracle.moments_1d(sys, M, n, realisation=realisation, e_min=e_min, e_max=e_max, r0=r0)
+    return mu.sum(axis=0)
+
+
+# --------------------------------------------------------------------------- RNG
+
+
+def test_philox_white_noise_statistics():
+    """Uniform draws: chi-square flat over 64 bins, independent words, distinct
+    counters give distinct blocks (Sec. 2c asks for white-noise variables only)."""
+    words = np.array([oracle.philox([i, 0, 7, 1], [123, 0]) for i in range(20000)], np.uint64)
+    u = ((words[:, 0] << np.uint64(21)) | (words[:, 1] >> np.uint64(11))).astype(np.float64) * 2.0**-53
+    counts, _ = np.histogram(u, bins=64, range=(0.0, 1.0))
+    exp = len(u) / 64
+    chi2 = ((counts - exp) ** 2 / exp).sum()
+    assert chi2 < 120.0  # 63 dof: mean 63, sd 11
+    assert abs(u.mean() - 0.5) < 5 * math.sqrt(1 / 12 / len(u))
+    # each output bit is balanced
+    bits = ((words[:, 2][:, None] >> np.arange(32, dtype=np.uint64)) & np.uint64(1)).astype(np.float64)
+    assert np.all(np.abs(bits.mean(0) - 0.5) < 5 * 0.5 / math.sqrt(len(u)))
+    # words of one block are uncorrelated
+    f = words.astype(np.float64) / 2**32
+    c = np.corrcoef(f.T)
+    assert np.all(np.abs(c - np.eye(4)) < 5 / math.sqrt(len(u)))
+    assert len({tuple(w) for w in words.tolist()}) == len(words)
+    # the key changes the stream
+    assert oracle.philox([0, 0, 7, 1], [123, 0]) != oracle.philox([0, 0, 7, 1], [124, 0])
+
+
+def test_disorder_distribution_and_vacancies():
+    """V uniform in [-W/2, W/2] +/- delta/2 (Sec. 4b); vacancies Bernoulli(p)."""
+    W, delta, p = 2.0, 0.6, 0.05
+    sys = oracle.make_system(Lx=128, Ly=96, W=W, delta=delta, p_vac=p, seed=11)
+    V, vac = oracle.disorder(sys)
+    n = V.size
+    VA, VB = V[0::2] - delta / 2, V[1::2] + delta / 2
+    for v in (VA, VB):
+        assert v.min() >= -W / 2 and v.max() < W / 2
+        assert abs(v.mean()) < 5 * W / math.sqrt(12 * v.size)
+        assert abs(v.var() - W * W / 12) < 0.02 * W * W / 12 + 5 * W * W / 12 / math.sqrt(v.size)
+    frac = vac.mean()
+    assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / n)
+    sys0 = oracle.make_system(Lx=16, Ly=16, W=0.0, p_vac=0.0)
+    V0, vac0 = oracle.disorder(sys0)
+    assert np.all(V0 == 0.0) and np.all(vac0 == 0)
+    sys1 = oracle.make_system(Lx=8, Ly=8, p_vac=1.0)
+    assert np.all(oracle.disorder(sys1)[1] == 1)
+
+
+def test_random_phase_is_white_noise():
+    """|xi| = 1 off vacancies, 0 on them; <xi> = 0, <xi xi> = 0, <|xi|^2> = 1 (Sec. 2c)."""
+    sys = oracle.make_system(Lx=64, Ly=64, p_vac=0.02, seed=3)
+    xi = oracle.random_phase(sys, R=4)
+    _, vac = oracle.disorder(sys)
+    on = vac == 0
+    assert np.all(xi[:, ~on] == 0)
+    assert np.allclose(np.abs(xi[:, on]), 1.0, atol=1e-15)
+    z = xi[:, on].ravel()
+    tol = 5 / math.sqrt(z.size)
+    assert abs(z.mean()) < tol
+    assert abs((z * z).mean()) < tol
+    # different vectors are independent
+    assert abs(np.vdot(xi[0, on], xi[1, on]) / on.sum()) < tol * 2
+
+
+# --------------------------------------------------------------- 1D moments
+
+
+def bloch_moments(lattice, Lx, Ly, t, M, e_min, e_max):
+    """Exact-trace moments of the clean periodic lattice from its Bloch dispersion."""
+    dm = 0.5 * (e_max - e_min)
+    dp = 0.5 * (e_max + e_min)
+    k1 = 2 * np.pi * np.arange(Lx) / Lx
+    k2 = 2 * np.pi * np.arange(Ly) / Ly
+    K1, K2 = np.meshgrid(k1, k2, indexing="ij")
+    if lattice == oracle.HONEYCOMB:
+        # A(x,y) couples to B(x,y), B(x+1,y-1), B(x,y-1)  (Listing 1 hoppings)
+        f = t * (1 + np.exp(1j * (K1 - K2)) + np.exp(-1j * K2))
+        E = np.concatenate([np.abs(f).ravel(), -np.abs(f).ravel()])
+    else:
+        E = (2 * t * (np.cos(K1) + np.cos(K2))).ravel()
+    x = (E - dp) / dm
+    return cheb_T(M, x).mean(axis=1)
+
+
+@pytest.mark.parametrize("lattice,Lx,Ly", [(oracle.HONEYCOMB, 4, 3), (oracle.HONEYCOMB, 5, 7),
+                                            (oracle.SQUARE, 6, 5), (oracle.SQUARE, 3, 8)])
+def test_exact_trace_matches_bloch_dispersion(lattice, Lx, Ly):
+    t = T_EV if lattice == oracle.HONEYCOMB else -1.0
+    sys = oracle.make_system(lattice=lattice, Lx=Lx, Ly=Ly, t=t)
+    lo, hi = oracle.bounds_auto(sys)
+    M = 40
+    mu = exact_trace_moments(sys, M)
+    ref = bloch_moments(lattice, Lx, Ly, t, M, lo, hi)
+    assert np.max(np.abs(mu.real - ref)) < 1e-12
+    assert np.max(np.abs(mu.imag)) < 1e-12
+    if lattice == oracle.HONEYCOMB:  # bipartite: odd moments vanish
+        assert np.max(np.abs(mu.real[1::2])) < 1e-12
+
+
+def test_exact_trace_matches_dense_diagonalisation_with_disorder():
+    sys = oracle.make_system(Lx=5, Ly=4, W=2.0, delta=0.4, p_vac=0.1, seed=21)
+    M = 32
+    H, keep, _ = dense_h(sys)
+    lam = np.linalg.eigvalsh(H)
+    assert np.all(np.abs(lam) <= 1.0)  # Gershgorin bounds hold (Sec. 2a, ||X|| <= 1)
+    ref = cheb_T(M, lam).mean(axis=1)
+    mu = exact_trace_moments(sys, M)
+    assert np.max(np.abs(mu.real - ref)) < 1e-12
+
+
+def test_low_order_exact_trace_identities():
+    """mu_0 = 1, mu_1 = mean V~, mu_2 = 2 mean(Z_i t~^2 + V~_i^2) - 1 on non-vacant
+    orbitals, Z_i counting non-vacant neighbours."""
+    sys = oracle.make_system(lattice=oracle.SQUARE, Lx=6, Ly=5, t=-1.0, W=3.0, p_vac=0.15, seed=4)
+    lo, hi = -7.0, 6.0  # asymmetric bounds: exercises de_plus
+    mu = exact_trace_moments(sys, 3, e_min=lo, e_max=hi).real
+    V, vac = oracle.disorder(sys)
+    dp, dm = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    on = np.where(vac == 0)[0]
+    Vt = (V[on] - dp) / dm
+    Z = np.array([sum(1 for j in oracle.neighbours(sys, o) if not vac[j]) for o in on])
+    tt = sys.t / dm
+    assert abs(mu[0] - 1.0) < 1e-14
+    assert abs(mu[1] - Vt.mean()) < 1e-14
+    assert abs(mu[2] - (2 * np.mean(Z * tt * tt + Vt * Vt) - 1)) < 1e-13
+
+
+def test_stochastic_estimate_within_trace_variance():
+    """Random-phase estimate vs exact trace: the STE variance for unit-modulus phases
+    is sum_{i!=j}|A_ij|^2 / N_eff^2 per vector (Sec. 2c)."""
+    sys = oracle.make_system(Lx=6, Ly=6, W=1.0, p_vac=0.05, seed=8)
+    M, R = 24, 6
+    H, keep, _ = dense_h(sys)
+    lam, U = np.linalg.eigh(H)
+    Tn = cheb_T(M, lam)
+    mu = oracle.moments_1d(sys, M, R).real.mean(axis=0)
+    ne = H.shape[0]
+    for n in range(M):
+        A = (U * Tn[n]) @ U.T
+        exact = np.trace(A) / ne
+        var = (np.sum(A * A) - np.sum(np.diag(A) ** 2)) / ne**2 / R
+        assert abs(mu[n] - exact) <= 5 * math.sqrt(var) + 1e-13, n
+
+
+def test_replica_agrees_with_definition():
+    sys = oracle.make_system(Lx=8, Ly=6, W=1.0, p_vac=0.03, seed=9)
+    M, R = 64, 2
+    mu = oracle.moments_1d(sys, M, R)
+    mu64, last64 = oracle.replica_1d(sys, M, R, precision=1, want_last=True)
+    mu32, last32 = oracle.replica_1d(sys, M, R, precision=0, want_last=True)
+    assert np.max(np.abs(mu64 - mu)) < 1e-12
+    assert np.max(np.abs(mu32 - mu)) < 5e-6
+    assert np.max(np.abs(last32 - last64)) < 1e-4
+    _, vac = oracle.disorder(sys)
+    assert np.all(last32[:, :, vac == 1] == 0)
+
+
+def test_replica_is_exact_on_dyadic_inputs():
+    """With t~ = 1/8, no disorder and +-1 start vectors every iterate is a dyadic
+    rational that fits in FP32 for the first steps: FP32, FP64 and the plain
+    definition must then agree exactly."""
+    sys = oracle.make_system(lattice=oracle.SQUARE, Lx=5, Ly=4, t=-1.0)
+    n = oracle.norb(sys)
+    rng = np.random.default_rng(0)
+    r0 = rng.choice([-1.0, 1.0], size=(1, n)).astype(np.complex128)
+    r0 = r0 + 1j * rng.choice([-1.0, 1.0], size=(1, n))
+    kw = dict(e_min=-8.0, e_max=8.0, r0=r0)
+    mu = oracle.moments_1d(sys, 6, 1, **kw)
+    m32, l32 = oracle.replica_1d(sys, 6, 1, 0, want_last=True, **kw)
+    m64, l64 = oracle.replica_1d(sys, 6, 1, 1, want_last=True, **kw)
+    assert np.array_equal(l32.astype(np.complex128), l64)
+    assert np.array_equal(m32, mu) and np.array_equal(m64, mu)
+
+
+# ------------------------------------------------------------ reconstruction
+
+
+def test_jackson_kernel_properties():
+    for M in (8, 64, 1000):
+        g = oracle.kernel_jackson(M)
+        assert abs(g[0] - 1.0) < 1e-15
+        assert np.all(np.diff(g) < 0) and g[-1] > 0
+    # the Jackson-damped expansion of a delta function has variance ~ (pi/M)^2
+    # at the band centre (Weisse et al. 2006): check with the exact moments of x0=0
+    M = 256
+    g = oracle.kernel_jackson(M)
+    mu = cheb_T(M, np.array([0.0]))[:, 0]
+    xs = np.cos(np.pi * (np.arange(4096) + 0.5) / 4096)
+    rho = oracle.dos(mu, xs, -1.0, 1.0, g)
+    w = np.pi / 4096 * np.sqrt(1 - xs**2) * rho
+    var = np.sum(w * xs**2)
+    assert abs(var / (np.pi / M) ** 2 - 1.0) < 0.05
+
+
+def test_dos_quadrature_sum_rules():
+    """On K Gauss-Chebyshev nodes (exact for these polynomial degrees),
+    (pi/K) sum sqrt(1-e^2) rho(e) T_j(e) = int rho T_j = g_j mu_j for every j, by the
+    orthogonality of Eq. e4.  This fixes the (2 - delta_n0) weight of the delta-function
+    expansion (the printed (1+delta_n0)/2 of Eq. e8 would give g_j mu_j / 4 for j >= 1)."""
+    sys = oracle.make_system(Lx=6, Ly=5, W=1.5, seed=2)
+    lo, hi = oracle.bounds_auto(sys)
+    M = 48
+    mu = exact_trace_moments(sys, M).real
+    g = oracle.kernel_jackson(M)
+    K = 512
+    eps = np.cos(np.pi * (np.arange(K) + 0.5) / K)
+    E = eps * 0.5 * (hi - lo) + 0.5 * (hi + lo)
+    rho = oracle.dos(mu, E, lo, hi, g) * 0.5 * (hi - lo)  # per unit eps
+    w = np.pi / K * np.sqrt(1 - eps**2) * rho
+    Tj = cheb_T(6, eps)
+    assert abs(w.sum() - g[0] * mu[0]) < 1e-12
+    for j in range(1, 6):
+        assert abs(np.sum(w * Tj[j]) - g[j] * mu[j]) < 1e-12
+    assert np.all(rho > -1e-12)  # Jackson kernel keeps the exact-trace DOS positive
+
+
+def test_dos_matches_broadened_spectrum():
+    """Jackson DOS of exact-trace moments vs the dense spectrum smeared by the same
+    kernel evaluated in closed form."""
+    sys = oracle.make_system(Lx=6, Ly=6, W=2.0, seed=5)
+    lo, hi = oracle.bounds_auto(sys)
+    M = 64
+    H, _, _ = dense_h(sys)
+    lam = np.linalg.eigvalsh(H)
+    g = oracle.kernel_jackson(M)
+    eps = np.linspace(-0.95, 0.95, 77)
+    Te = cheb_T(M, eps)
+    Tl = cheb_T(M, lam)
+    coef = g * (2.0 - (np.arange(M) == 0))
+    ref = (coef[:, None] * Te * Tl.mean(axis=1)[:, None]).sum(0) / (np.pi * np.sqrt(1 - eps**2))
+    mu = exact_trace_moments(sys, M).real
+    dm = 0.5 * (hi - lo)
+    rho = oracle.dos(mu, eps * dm, lo, hi, g) * dm
+    assert np.max(np.abs(rho - ref)) < 1e-11
+
+
+def test_cpgf_coefficients_resum_the_resolvent():
+    """sum_n g_n(eps) T_n(x)/(1+delta_n0) -> 1/(eps - x + i sigma eta) (Eqs.
+    green_function_cheb_expansion/b), uniformly in x for fixed eta."""
+    eta = 0.05
+    M = 1500
+    for sigma in (+1, -1):
+        for eps in (-0.7, 0.0, 0.33):
+            gn = np.array([oracle.cpgf_coeff(n, eps, eta, sigma) for n in range(M)])
+            gn[0] *= 0.5
+            for x in (-0.9, -0.2, 0.1, 0.8):
+                s = np.sum(gn * cheb_T(M, np.array([x]))[:, 0])
+                ref = 1.0 / (eps - x + 1j * sigma * eta)
+                assert abs(s - ref) < 1e-6 * abs(ref), (sigma, eps, x)
+
+
+def test_lorentz_kernel_definition():
+    g = oracle.kernel_lorentz(100, 4.0)
+    assert abs(g[0] - 1.0) < 1e-15
+    assert abs(g[50] - math.sinh(2.0) / math.sinh(4.0)) < 1e-15
+
+
+# ---------------------------------------------------------------- 2D moments
+
+
+def dense_vx(sys, vac, tt):
+    n = oracle.norb(sys)
+    cols = [oracle.velocity_x(sys, vac, tt, np.eye(n)[j]) for j in range(n)]
+    return np.array(cols).T.real
+
+
+def test_velocity_operator_is_antisymmetric_with_bond_weights():
+    """h~x = [x, H]: real antisymmetric; sum_j (x_i-x_j)^2 = 1/2 per honeycomb site
+    (bond x-offsets 0, +-a/2 from Listing 1) and 2 per square site."""
+    for lat, expect in ((oracle.HONEYCOMB, 0.5), (oracle.SQUARE, 2.0)):
+        sys = oracle.make_system(lattice=lat, Lx=5, Ly=4, t=1.0)
+        n = oracle.norb(sys)
+        hx = dense_vx(sys, np.zeros(n, np.uint8), 1.0)
+        assert np.array_equal(hx, -hx.T)
+        assert np.allclose((hx * hx).sum(axis=1), expect)
+
+
+def test_exact_trace_2d_moments_match_bloch_velocity():
+    """Clean honeycomb: mu_nm = (1/N) sum_k Tr[v(k) T_n(H(k)) v(k) T_m(H(k))] with the
+    Bloch velocity v(k) = dH(k)/dk_x (v = -i h~ = i[H,x]); the offsets of the bonds to
+    B(x+1,y-1) and B(x,y-1) are a1-a2 and -a2, whose x-components are +a/2 and -a/2."""
+    Lx, Ly, M = 4, 3, 10
+    sys = oracle.make_system(Lx=Lx, Ly=Ly, t=T_EV)
+    lo, hi = oracle.bounds_auto(sys)
+    dm = 0.5 * (hi - lo)
+    tt = T_EV / dm
+    n = oracle.norb(sys)
+    mu = oracle.moments_2d(sys, M, n, r0=np.eye(n, dtype=np.complex128)) * n
+    ref = np.zeros((M, M), np.complex128)
+    for m1 in range(Lx):
+        for m2 in range(Ly):
+            k1, k2 = 2 * np.pi * m1 / Lx, 2 * np.pi * m2 / Ly
+            p1, p2 = np.exp(1j * (k1 - k2)), np.exp(-1j * k2)
+            f = tt * (1 + p1 + p2)
+            df = tt * (0.5j * p1 - 0.5j * p2)  # d/dk_x with x in units of a
+            Hk = np.array([[0, f], [np.conj(f), 0]])
+            vk = np.array([[0, df], [np.conj(df), 0]])
+            lam, U = np.linalg.eigh(Hk)
+            Tn = cheb_T(M, lam)
+            vv = U.conj().T @ vk @ U
+            for a in range(2):
+                for b in range(2):
+                    ref += abs(vv[a, b]) ** 2 * np.outer(Tn[:, b], Tn[:, a])
+    ref /= n
+    assert np.max(np.abs(mu - ref)) < 1e-12
+    assert np.max(np.abs(mu.imag)) < 1e-12
+    assert np.max(np.abs(mu - mu.T)) < 1e-12
+    assert abs(mu[0, 0].real - 0.5 * tt * tt) < 1e-14
+
+
+def test_2d_moments_with_disorder_match_dense_diagonalisation():
+    sys = oracle.make_system(Lx=4, Ly=4, W=2.0, p_vac=0.1, seed=31)
+    M = 12
+    lo, hi = oracle.bounds_auto(sys)
+    dm = 0.5 * (hi - lo)
+    n = oracle.norb(sys)
+    H, keep, vac = dense_h(sys)
+    hx = dense_vx(sys, vac, sys.t / dm)[np.ix_(keep, keep)]
+    v = -1j * hx
+    lam, U = np.linalg.eigh(H)
+    Tn = cheb_T(M, lam)
+    vv = U.conj().T @ v @ U
+    P = np.abs(vv) ** 2
+    ref = np.einsum("ab,nb,ma->nm", P, Tn, Tn) / len(keep)
+    mu = oracle.moments_2d(sys, M, n, r0=np.eye(n, dtype=np.complex128)) * n
+    assert np.max(np.abs(mu - ref)) < 1e-12
+
+
+def test_2d_stochastic_estimate_is_close():
+    sys = oracle.make_system(Lx=16, Ly=16, W=1.0, seed=12)
+    M = 8
+    mu_st = oracle.moments_2d(sys, M, 4)
+    n = oracle.norb(sys)
+    # basis vectors: the vector average times n is the exact trace Tr[v T_n v T_m]/N
+    mu_ex = oracle.moments_2d(sys, M, n, r0=np.eye(n, dtype=np.complex128)) * n
+    scale = np.max(np.abs(mu_ex))
+    assert np.max(np.abs(mu_st - mu_ex)) < 0.1 * scale
