@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Benchmark of the stochastic Chebyshev (KPM) density-of-states hot path.
+
+Workload (one "step" = the whole DOS path on one batch of synthetic input):
+  honeycomb lattice 4096 x 4096 cells (33.5M orbitals), t = -2.7 eV, Anderson disorder
+  W = 2 eV, 0.5 % seeded vacancies, Gershgorin bounds, M = 2048 moments, R = 8
+  random-phase vectors, complex FP32 recursion with FP64 moment accumulation, then the
+  FP64 Jackson reconstruction of the DOS on a 1024-point energy grid.
+Metric: orbital * moment * vector updates per second (N_eff * M * R / step time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kite|reference]
+
+N > 1 runs under torchrun, one rank per GPU; each rank runs its own disorder
+realisation (independent samples, no data-path collective) and `value` is the total
+over ranks divided by the slowest rank's time ("weak" scaling).  `--impl reference`
+times the FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site·moment·vector updates/s, FP32 vs FP64 at stated error; % of HBM peak"
+UNIT = "updates/s"
+WORKLOAD = dict(lattice="honeycomb", Lx=4096, Ly=4096, t=-2.7, W=2.0, p_vac=0.005, M=2048, R=8,
+                precision="fp32 recursion, fp64 moment accumulation", K_energies=1024,
+                kernel="jackson")
+WORKLOAD_NAME = ("large_dos_honeycomb_4096x4096_W2_vac0.005_M2048_R8_fp32 + "
+                 "jackson_dos_1024pts")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="kite", choices=["kite", "reference"])
+    p.add_argument("--Lx", type=int, default=WORKLOAD["Lx"])
+    p.add_argument("--Ly", type=int, default=WORKLOAD["Ly"])
+    p.add_argument("--M", type=int, default=WORKLOAD["M"])
+    p.add_argument("--R", type=int, default=WORKLOAD["R"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    for fn in ("kite_kpm1d.cu", "kite_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1910_05194_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(updates_per_launch: float):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, scaled
+    per update, if the kernel source still matches the one profiled (else None)."""
+    path = os.path.join(ROOT, "profiles", "kpm_step_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_update"]) * updates_per_launch
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    cores = os.cpu_count() or 1
+    sysd = dict(lattice=0, Lx=args.Lx, Ly=args.Ly, t=WORKLOAD["t"], W=WORKLOAD["W"],
+                p_vac=WORKLOAD["p_vac"], seed=2)
+    sample_M, sample_R = 8, 1
+    s = oracle.make_system(**sysd)
+    n = oracle.norb(s)
+    _, vac = oracle.disorder(s)
+    n_eff = int((vac == 0).sum())
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.moments_1d(s, sample_M, sample_R, threads=cores)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    upd = n_eff * sample_M * sample_R
+    value = upd / float(np.mean(times))
+    sample = (f"oracle FP64 (C, OpenMP) on the full {args.Lx}x{args.Ly} lattice with "
+              f"M={sample_M}, R={sample_R} per step (bounded sample; metric per update)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, **WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_leg(args, kite, ctx, n_eff_gpu):
+    """Oracle timed on the host cores on a bounded sample of the workload, plus the
+    moment error of the GPU path on that same sample."""
+    import oracle
+    cores = os.cpu_count() or 1
+    sysd = dict(lattice=0, Lx=args.Lx, Ly=args.Ly, t=WORKLOAD["t"], W=WORKLOAD["W"],
+                p_vac=WORKLOAD["p_vac"], seed=2)
+    M, R = 16, 2
+    s = oracle.make_system(**sysd)
+    t0 = time.perf_counter()
+    mu_ref = oracle.moments_1d(s, M, R, threads=cores)
+    dt = time.perf_counter() - t0
+    _, vac = oracle.disorder(s)
+    n_eff = int((vac == 0).sum())
+    mu = np.zeros(M)
+    kite.moments_1d(ctx, kite.make_system(lattice=0, Lx=args.Lx, Ly=args.Ly, t=WORKLOAD["t"],
+                                          W=WORKLOAD["W"], p_vac=WORKLOAD["p_vac"], seed=2),
+                    kite.make_kpm(M, R, 1, kite.FP32), mu)
+    return {"value": n_eff * M * R / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"full {args.Lx}x{args.Ly} lattice, M={M}, R={R}, FP64 oracle (C, OpenMP), "
+                      f"{dt:.1f} s wall",
+            "max_abs_dmu_gpu_fp32_vs_oracle_on_sample": float(np.max(np.abs(mu - mu_ref.real.mean(0)))),
+            "n_eff_match": bool(n_eff == n_eff_gpu)}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import paper_1910_05194_gb300 as kite
+    from paper_1910_05194_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.Stream()
+    ctx = kite.Context(local, stream)
+    M, R = args.M, args.R
+    system = kite.make_system(kite.HONEYCOMB, args.Lx, args.Ly, WORKLOAD["t"], WORKLOAD["W"], 0.0,
+                              WORKLOAD["p_vac"], seed=2 + 1000003 * rank)
+    # realisation of this rank: different seed per rank (independent samples)
+    kpm = kite.make_kpm(M, R, 1, kite.FP32)
+    e_min, e_max = kite.bounds(system)
+    K = WORKLOAD["K_energies"]
+    E = torch.linspace(e_min, e_max, K + 2, dtype=torch.float64, device="cuda")[1:-1].contiguous()
+    mu = torch.zeros(M, dtype=torch.float64, device="cuda")
+    rho = torch.zeros(K, dtype=torch.float64, device="cuda")
+
+    def step():
+        st = kite.moments_1d(ctx, system, kpm, mu)
+        kite.reconstruct_dos(ctx, mu, M, M, kite.KERNEL_JACKSON, 0.0, e_min, e_max, E, K, rho)
+        return st
+
+    for _ in range(args.warmup):
+        st = step()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    step_s, step_n, step_bytes = 0.0, 0, 0.0
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        st = step()
+        step_s += st.step_seconds
+        step_n += st.step_launches
+        step_bytes += st.step_bytes
+    ev1.record(stream)
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t_step = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_step, op=dist.ReduceOp.MAX)
+    ms = float(t_step.item())
+    updates_per_step = float(st.n_eff) * M * R
+    value = updates_per_step * world / (ms * 1e-3)
+    launches_per_step = 1 + 1 + (M - 1) + 1 + 1 + 2  # onsite, init, steps, reduce, average, dos x2
+    roofline = None
+    if step_n > 0:
+        peak, peak_kind = measured_peaks()
+        achieved = step_bytes / step_s / 1e9
+        upd_per_launch = float(st.n_eff) * R
+        traffic = profiled_traffic(upd_per_launch)
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic,
+                    "kernel": "k_step<float, honeycomb, 4 chunks>",
+                    "algorithmic_bytes_per_launch": step_bytes / step_n,
+                    "avg_launch_us": 1e6 * step_s / step_n, "peak_kind": peak_kind + " (copy test)"}
+
+    # ---- end to end through the C ABI with host buffers -------------------------------
+    e2e = None
+    if not args.no_e2e:
+        import synth
+        n = int(args.Lx) * int(args.Ly) * 2
+        r0_host = torch.empty((R, n, 2), dtype=torch.float64, pin_memory=True)
+        for r in range(R):  # seeded unit-phase start vectors, one vector at a time
+            z = synth.unit_phase_vectors(n, 1, seed=12345 + 1000 * rank + r)[0]
+            r0_host[r, :, 0] = torch.from_numpy(z.real)
+            r0_host[r, :, 1] = torch.from_numpy(z.imag)
+            del z
+        mu_h = torch.zeros(M, dtype=torch.float64).pin_memory()
+        E_h = E.cpu().pin_memory()
+        rho_h = torch.zeros(K, dtype=torch.float64).pin_memory()
+        kpm_h = kite.make_kpm(M, R, 1, kite.FP32, r0=r0_host)
+
+        def e2e_step():
+            kite.moments_1d(ctx, system, kpm_h, mu_h)
+            kite.reconstruct_dos(ctx, mu_h, M, M, kite.KERNEL_JACKSON, 0.0, e_min, e_max, E_h, K, rho_h)
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(e2e_steps):
+            e2e_step()
+        barrier()
+        t_e2e = (time.perf_counter() - t0) / e2e_steps
+        t_e2e_t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(t_e2e_t, op=dist.ReduceOp.MAX)
+        h2d = r0_host.numel() * 8 + mu_h.numel() * 8 + E_h.numel() * 8
+        d2h = mu_h.numel() * 8 + rho_h.numel() * 8
+        e2e = {"value": updates_per_step * world / float(t_e2e_t.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "path": "kite_moments_1d(host start vectors, host mu) + kite_reconstruct_dos(host E, host rho)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_leg(args, kite, ctx, st.n_eff)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD_NAME, **WORKLOAD, "Lx": args.Lx, "Ly": args.Ly,
+                           "M": M, "R": R, "n_eff": int(st.n_eff),
+                           "l2": "inputs larger than L2 (three 2.1 GB vector buffers per step)",
+                           "parallelism": f"{world} independent realisations" if world > 1 else "single GPU",
+                           "grid": st.grid, "block": st.block},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": launches_per_step * args.steps,
+                "wall_s_timed": wall}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

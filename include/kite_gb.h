@@ -1,0 +1,184 @@
+/*
+ * kite_gb.h -- C ABI of the GB300-native stochastic Chebyshev (kernel polynomial)
+ * expansion of lattice Green's functions described in KITE (arXiv:1910.05194).
+ *
+ * Every call takes plain pointers and sizes.  A pointer argument documented as
+ * "host or device" may point to host memory (pageable or pinned) or to device memory
+ * of the context's GPU; the library tells them apart with cudaPointerGetAttributes.
+ * The caller owns every input and output buffer.  The library owns its work buffers
+ * (grown on demand inside the context, released by kite_destroy).
+ *
+ * Calls are ordered on the context's stream and return after their results are
+ * complete and visible in the caller's buffers.  Every call returns KITE_OK (0) or a
+ * negative status; on failure no output buffer holds a trusted result, and
+ * kite_last_error() gives a one-line reason.  Nothing in the library aborts or exits.
+ *
+ * Notation (Sec. 2 of the paper): H~ = (H - de_plus)/de_minus with
+ * de_pm = (E_max +- E_min)/2 (Eqs. rescalingH/rescalingE); T_n are Chebyshev
+ * polynomials (Eq. e3, operator form Eq. e6); mu_n = <r|T_n(H~)|r>/N_eff are the
+ * moments of the average density of states (Eqs. e7, e8) estimated with random
+ * vectors (stochastic trace evaluation, Sec. 2c).
+ */
+#ifndef KITE_GB_H
+#define KITE_GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------- */
+#define KITE_OK 0
+#define KITE_ERR_ARG (-1)         /* invalid argument (sizes, enums, null pointers)     */
+#define KITE_ERR_OOM (-2)         /* device allocation failed                           */
+#define KITE_ERR_CUDA (-3)        /* a CUDA runtime call or kernel launch failed        */
+#define KITE_ERR_BOUNDS (-4)      /* |mu_n| > 1 + 1e-3 or non-finite: spectrum left
+                                     [-1,1] (Eq. e6 requires ||H~|| <= 1)               */
+#define KITE_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up                 */
+#define KITE_ERR_UNSUPPORTED (-6) /* valid request this build does not implement        */
+
+/* ---- enums -------------------------------------------------------------------- */
+#define KITE_HONEYCOMB 0 /* Listing 1: a1=[a,0], a2=[a/2, a sqrt3/2], two orbitals A, B   */
+#define KITE_SQUARE 1    /* one orbital per cell, four nearest neighbours               */
+
+#define KITE_FP32 0 /* complex FP32 recursion, FP64 moment accumulation above 32 terms */
+#define KITE_FP64 1 /* complex FP64 recursion                                           */
+
+#define KITE_KERNEL_NONE 0
+#define KITE_KERNEL_JACKSON 1 /* g_n of Weisse et al. 2006 (the paper's KPM reference)   */
+#define KITE_KERNEL_LORENTZ 2 /* g_n = sinh(lambda(1-n/M))/sinh(lambda), Sec. 2a        */
+
+/* ---- problem description -------------------------------------------------------- */
+
+/* A periodic tight-binding lattice with disorder (Sec. 3d, Listings 1-3; Sec. 4b).
+ * Orbitals are numbered o = 2*(y*Lx + x) + s for the honeycomb lattice (s = 0 for A,
+ * 1 for B) and o = y*Lx + x for the square lattice; N = number of orbitals.
+ *   lattice  KITE_HONEYCOMB or KITE_SQUARE
+ *   Lx, Ly   unit cells along a1, a2 (>= 1); boundaries are periodic in both
+ *   t        nearest-neighbour hopping (eV)
+ *   W        Anderson on-site disorder, V_o uniform in [-W/2, W/2] (eV), >= 0
+ *   delta    staggered potential: +delta/2 on A, -delta/2 on B (honeycomb only, eV)
+ *   p_vac    probability that an orbital is a vacancy (removed with its bonds), [0,1]
+ *   seed     key of the Philox4x32-10 counter-based generator that draws V_o, the
+ *            vacancies and the random-phase vectors.  Realisation s, orbital o:
+ *            counter (o_lo, o_hi, s, 1); vector v of realisation s: (o_lo, o_hi,
+ *            s*R + v, 2).  u = (w0 * 2^21 + (w1 >> 11)) * 2^-53,
+ *            V_o = W*(u - 1/2) [+- delta/2], vacant iff w2 < floor(p_vac * 2^32),
+ *            phase vector entry exp(2 pi i u) (0 on vacancies). */
+typedef struct {
+  int32_t lattice;
+  int32_t Lx, Ly;
+  int32_t reserved;
+  double t;
+  double W;
+  double delta;
+  double p_vac;
+  uint64_t seed;
+} kite_system;
+
+/* Chebyshev expansion parameters (the calculation settings of Sec. 3d: num_moments,
+ * num_random, num_disorder, precision, spectrum range).
+ *   M          number of moments mu_0..mu_{M-1} (>= 1)
+ *   R          random vectors per disorder realisation (>= 1)
+ *   S          disorder realisations (>= 1)
+ *   precision  KITE_FP32 or KITE_FP64
+ *   e_min, e_max  spectrum endpoints in eV; both 0 selects the Gershgorin enclosure
+ *              +-(Z|t| + W/2 + |delta|/2) * 1.01 (kite_bounds)
+ *   r0         optional start vectors instead of random phases: [S*R][N] complex FP64,
+ *              interleaved (re, im), host or device; entries on vacancies are ignored
+ *              (the vacancy is removed from the Hilbert space).  NULL = random phases.
+ *   r_last     optional output: per vector the last two iterates (T_{M-2} r, T_{M-1} r)
+ *              as [S*R][2][N] interleaved complex of the working precision (complex64
+ *              for KITE_FP32, complex128 for KITE_FP64), host or device; for M = 1 both
+ *              slots hold r.  NULL = not wanted.  Lets a caller check the recursion bit
+ *              for bit or checkpoint a run. */
+typedef struct {
+  int32_t M;
+  int32_t R;
+  int32_t S;
+  int32_t precision;
+  double e_min;
+  double e_max;
+  const double* r0;
+  void* r_last;
+} kite_kpm;
+
+/* Per-call statistics (all optional outputs). */
+typedef struct {
+  double seconds;       /* device time of the moment sweep (CUDA events)            */
+  double updates;       /* orbital * moment * vector updates done (N_eff*(M-1)*R*S)  */
+  double bytes_moved;   /* algorithmic HBM bytes of the sweep (see DESIGN)           */
+  double gbps;          /* bytes_moved / seconds / 1e9                               */
+  double max_abs_imag;  /* max_n |Im mu_n| of the vector average (0 for exact H~)    */
+  double e_min, e_max;  /* bounds used (eV)                                          */
+  int64_t n_eff;        /* non-vacant orbitals of the last realisation               */
+  int32_t grid, block;  /* launch shape of the sweep kernel                           */
+  double step_seconds;  /* device time of the recursion-step launches alone          */
+  int64_t step_launches;/* number of recursion-step launches timed in step_seconds   */
+  double step_bytes;    /* algorithmic bytes of those launches                       */
+} kite_stats;
+
+typedef struct kite_ctx kite_ctx;
+
+/* ---- context -------------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`, bound to `cuda_stream` (a cudaStream_t;
+ * NULL creates a private non-blocking stream).  *out receives the handle.
+ * Errors: KITE_ERR_ARG (out NULL, bad device), KITE_ERR_CUDA. */
+int kite_create(kite_ctx** out, int device, void* cuda_stream);
+
+/* Releases the context, its private stream and work buffers.  NULL is a no-op. */
+void kite_destroy(kite_ctx* ctx);
+
+/* Rebinds the context to another stream of the same device (NULL = private stream). */
+int kite_set_stream(kite_ctx* ctx, void* cuda_stream);
+
+/* Static, thread-safe description of a status code. */
+const char* kite_status_string(int status);
+
+/* Detail of the last failed call on this context ("" if none).  Valid until the next
+ * call on the same context. */
+const char* kite_last_error(const kite_ctx* ctx);
+
+/* Gershgorin spectrum enclosure used when e_min = e_max = 0 (Eqs. rescalingH/E and the
+ * bound warning of Sec. 4b): e_max = -e_min = (Z|t| + W/2 + |delta|/2) * 1.01 with
+ * Z = 3 (honeycomb) or 4 (square).  Host-only arithmetic in FP64.
+ * Errors: KITE_ERR_ARG. */
+int kite_bounds(const kite_system* sys, double* e_min, double* e_max);
+
+/* ---- 1D moments ----------------------------------------------------------------- */
+
+/* Moments of the average DOS, mu_n = (1/(S R)) sum_{s,r} <r|T_n(H~)|r> / N_eff for
+ * n = 0..M-1 (Eqs. e6-e8, stochastic trace of Sec. 2c; cost Z*N*M*R*S, Eq.
+ * PcomplexityFactor).  T_1 r = H~ r, T_{n+1} r = 2 H~ T_n r - T_{n-1} r, with H~
+ * applied matrix-free (Sec. 3a pattern rules): on-site term and nearest-neighbour
+ * hopping, vacancies removed.  Moments are raw (mu_0 = 1); the reconstruction applies
+ * the (2 - delta_n0) weight of the delta-function expansion.
+ *   mu          [M] FP64, real part of the average, host or device (required)
+ *   mu_per_vec  [S*R][M] complex FP64 interleaved (re, im) per vector, or NULL
+ *   st          statistics, or NULL
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA, KITE_ERR_BOUNDS. */
+int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, double* mu,
+                    double* mu_per_vec, kite_stats* st);
+
+/* ---- reconstruction ------------------------------------------------------------- */
+
+/* Density of states per orbital and per eV on caller energies (Eqs. e7, e8a with the
+ * kernel damping mu_n -> g_n mu_n of Sec. 2a):
+ *   eps = (E - de_plus)/de_minus;  rho(E) = [g_0 mu_0 + 2 sum_{n=1}^{M_use-1} g_n mu_n
+ *   T_n(eps)] / (pi sqrt(1 - eps^2) de_minus), 0 outside |eps| < 1.
+ * Computed in FP64 on the GPU.  M_use <= M_avail moments are used (Sec. 3c: a subset
+ * of the computed moments), the kernel built for M = M_use.
+ *   mu      [M_avail] FP64 raw moments, host or device
+ *   kernel  KITE_KERNEL_NONE / _JACKSON / _LORENTZ (param = lambda for Lorentz)
+ *   E       [K] energies (eV), host or device;  rho  [K] FP64 output, host or device
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
+int kite_reconstruct_dos(kite_ctx* ctx, const double* mu, int M_avail, int M_use, int kernel,
+                         double param, double e_min, double e_max, const double* E, int K,
+                         double* rho);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KITE_GB_H */

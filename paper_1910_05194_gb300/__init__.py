@@ -1,0 +1,193 @@
+"""GB300-native stochastic Chebyshev (kernel polynomial) moments of lattice Green's
+functions, after KITE (arXiv:1910.05194).
+
+This module is a thin ctypes binding of ``libkite_gb.so``: it marshals structs and
+pointers (numpy arrays, torch tensors or raw addresses) and calls the C ABI declared
+in ``include/kite_gb.h``.  Every step of the computation runs in the library's CUDA
+kernels; there is no Python or CPU fallback.  If the library has not been built, the
+first call raises :class:`KiteError` telling how to build it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkite_gb.so")
+
+OK = 0
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_BOUNDS, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+HONEYCOMB, SQUARE = 0, 1
+FP32, FP64 = 0, 1
+KERNEL_NONE, KERNEL_JACKSON, KERNEL_LORENTZ = 0, 1, 2
+
+EXPORTED = ("kite_create", "kite_destroy", "kite_set_stream", "kite_status_string",
+            "kite_last_error", "kite_bounds", "kite_moments_1d", "kite_reconstruct_dos")
+
+
+class KiteError(RuntimeError):
+    def __init__(self, status: int, detail: str = ""):
+        self.status = status
+        super().__init__(f"kite status {status}: {detail}")
+
+
+class System(ctypes.Structure):
+    """``kite_system``: periodic honeycomb/square lattice with disorder."""
+    _fields_ = [("lattice", ctypes.c_int32), ("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("t", ctypes.c_double), ("W", ctypes.c_double),
+                ("delta", ctypes.c_double), ("p_vac", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class KPM(ctypes.Structure):
+    """``kite_kpm``: expansion parameters."""
+    _fields_ = [("M", ctypes.c_int32), ("R", ctypes.c_int32), ("S", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("e_min", ctypes.c_double),
+                ("e_max", ctypes.c_double), ("r0", ctypes.c_void_p), ("r_last", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    """``kite_stats``: per-call statistics."""
+    _fields_ = [("seconds", ctypes.c_double), ("updates", ctypes.c_double),
+                ("bytes_moved", ctypes.c_double), ("gbps", ctypes.c_double),
+                ("max_abs_imag", ctypes.c_double), ("e_min", ctypes.c_double),
+                ("e_max", ctypes.c_double), ("n_eff", ctypes.c_int64), ("grid", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("step_seconds", ctypes.c_double),
+                ("step_launches", ctypes.c_int64), ("step_bytes", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def make_system(lattice=HONEYCOMB, Lx=64, Ly=64, t=-2.7, W=0.0, delta=0.0, p_vac=0.0, seed=1):
+    return System(int(lattice), int(Lx), int(Ly), 0, float(t), float(W), float(delta),
+                  float(p_vac), int(seed))
+
+
+def make_kpm(M, R=1, S=1, precision=FP32, e_min=0.0, e_max=0.0, r0=None, r_last=None):
+    return KPM(int(M), int(R), int(S), int(precision), float(e_min), float(e_max),
+               _addr(r0), _addr(r_last))
+
+
+_LOCK = threading.Lock()
+_LIB = None
+
+
+def lib():
+    """The loaded ``libkite_gb.so`` (raises KiteError if it was never built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            if not os.path.exists(LIB_PATH):
+                raise KiteError(ERR_UNSUPPORTED,
+                                f"{LIB_PATH} is missing; build it with "
+                                "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            P, vp, i32, d = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            L.kite_create.argtypes = [P(vp), i32, vp]
+            L.kite_create.restype = i32
+            L.kite_destroy.argtypes = [vp]
+            L.kite_destroy.restype = None
+            L.kite_set_stream.argtypes = [vp, vp]
+            L.kite_set_stream.restype = i32
+            L.kite_status_string.argtypes = [i32]
+            L.kite_status_string.restype = ctypes.c_char_p
+            L.kite_last_error.argtypes = [vp]
+            L.kite_last_error.restype = ctypes.c_char_p
+            L.kite_bounds.argtypes = [P(System), P(d), P(d)]
+            L.kite_bounds.restype = i32
+            L.kite_moments_1d.argtypes = [vp, P(System), P(KPM), vp, vp, P(Stats)]
+            L.kite_moments_1d.restype = i32
+            L.kite_reconstruct_dos.argtypes = [vp, vp, i32, i32, i32, d, d, d, vp, i32, vp]
+            L.kite_reconstruct_dos.restype = i32
+            _LIB = L
+    return _LIB
+
+
+def _addr(x):
+    """Device/host address of a torch tensor, numpy array or raw int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):  # torch.Tensor
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):  # numpy.ndarray
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Context:
+    """A ``kite_ctx``: one device, one stream, reusable work buffers."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._h = ctypes.c_void_p()
+        rc = lib().kite_create(ctypes.byref(self._h), int(device), _stream_handle(stream))
+        if rc != OK:
+            raise KiteError(rc, lib().kite_status_string(rc).decode())
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, rc: int):
+        if rc != OK:
+            detail = lib().kite_last_error(self._h).decode() or lib().kite_status_string(rc).decode()
+            raise KiteError(rc, detail)
+
+    def set_stream(self, stream):
+        self.check(lib().kite_set_stream(self._h, _stream_handle(stream)))
+
+    def close(self):
+        if self._h:
+            lib().kite_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def bounds(system: System):
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    rc = lib().kite_bounds(ctypes.byref(system), ctypes.byref(lo), ctypes.byref(hi))
+    if rc != OK:
+        raise KiteError(rc, "kite_bounds")
+    return lo.value, hi.value
+
+
+def moments_1d(ctx: Context, system: System, kpm: KPM, mu, mu_per_vec=None) -> Stats:
+    """kite_moments_1d: mu[M] (FP64, host or device), optional mu_per_vec[S*R][M][2]."""
+    st = Stats()
+    ctx.check(lib().kite_moments_1d(ctx.handle, ctypes.byref(system), ctypes.byref(kpm),
+                                    _addr(mu), _addr(mu_per_vec), ctypes.byref(st)))
+    return st
+
+
+def reconstruct_dos(ctx: Context, mu, M_avail: int, M_use: int, kernel: int, param: float,
+                    e_min: float, e_max: float, E, K: int, rho):
+    """kite_reconstruct_dos: rho[K] per orbital per eV from raw moments (FP64, GPU)."""
+    ctx.check(lib().kite_reconstruct_dos(ctx.handle, _addr(mu), int(M_avail), int(M_use),
+                                         int(kernel), float(param), float(e_min), float(e_max),
+                                         _addr(E), int(K), _addr(rho)))

@@ -1,0 +1,338 @@
+// kite_capi.cu -- context, argument validation and the extern "C" entry points of
+// libkite_gb.so.  All compute runs in the kernels of the other translation units.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "kite_internal.h"
+
+namespace kite {
+
+int moments_1d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
+                    double* mu_dev, double* imag_dev, double* mu_vec_dev, kite_stats* st,
+                    const double* r0_dev_all);
+int reconstruct_dos_impl(kite_ctx* ctx, const double* mu_dev, int M_use, int kernel,
+                         double param, const Scale& sc, const double* E_dev, int K,
+                         double* rho_dev, double* coef_dev);
+
+int fail(kite_ctx* ctx, int status, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return status;
+}
+
+int cuda_fail(kite_ctx* ctx, cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky launch error where possible
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(ctx, e == cudaErrorMemoryAllocation ? KITE_ERR_OOM : KITE_ERR_CUDA, m);
+}
+
+int ensure_ws(kite_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return KITE_OK;
+  if (ctx->ws) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&ctx->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&ctx->ws, bytes);
+    want = bytes;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ws = nullptr;
+    return fail(ctx, KITE_ERR_OOM,
+                "work space of " + std::to_string(bytes >> 20) + " MiB could not be allocated");
+  }
+  ctx->ws_bytes = want;
+  return KITE_OK;
+}
+
+int ensure_pinned(kite_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->pinned_bytes) return KITE_OK;
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  ctx->pinned = nullptr;
+  ctx->pinned_bytes = 0;
+  if (cudaMallocHost(&ctx->pinned, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, KITE_ERR_OOM, "pinned staging buffer");
+  }
+  ctx->pinned_bytes = bytes;
+  return KITE_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaError_t copy_in(kite_ctx* ctx, void* dst_dev, const void* src, size_t bytes) {
+  return cudaMemcpyAsync(dst_dev, src, bytes, cudaMemcpyDefault, ctx->stream);
+}
+
+cudaError_t copy_out(kite_ctx* ctx, void* dst, const void* src_dev, size_t bytes) {
+  return cudaMemcpyAsync(dst, src_dev, bytes, cudaMemcpyDefault, ctx->stream);
+}
+
+static int validate_system(kite_ctx* ctx, const kite_system* s) {
+  if (!s) return fail(ctx, KITE_ERR_ARG, "system is NULL");
+  if (s->lattice != KITE_HONEYCOMB && s->lattice != KITE_SQUARE)
+    return fail(ctx, KITE_ERR_ARG, "unknown lattice");
+  if (s->Lx < 1 || s->Ly < 1) return fail(ctx, KITE_ERR_ARG, "Lx and Ly must be >= 1");
+  const double cells = (double)s->Lx * (double)s->Ly;
+  if (cells * (s->lattice == KITE_HONEYCOMB ? 2 : 1) > 4.0e9)
+    return fail(ctx, KITE_ERR_ARG, "more than 4e9 orbitals");
+  if (!isfinite(s->t) || !isfinite(s->W) || !isfinite(s->delta) || s->W < 0.0)
+    return fail(ctx, KITE_ERR_ARG, "t, W, delta must be finite and W >= 0");
+  if (!(s->p_vac >= 0.0 && s->p_vac <= 1.0)) return fail(ctx, KITE_ERR_ARG, "p_vac outside [0,1]");
+  return KITE_OK;
+}
+
+static void gershgorin(const kite_system* s, double* lo, double* hi) {
+  const double Z = s->lattice == KITE_HONEYCOMB ? 3.0 : 4.0;
+  const double vmax = 0.5 * fabs(s->W) + (s->lattice == KITE_HONEYCOMB ? 0.5 * fabs(s->delta) : 0.0);
+  const double b = (Z * fabs(s->t) + vmax) * 1.01;
+  *lo = -b;
+  *hi = b;
+}
+
+int resolve_bounds(kite_ctx* ctx, const kite_system* sys, double e_min, double e_max, Scale* sc) {
+  if (e_min == 0.0 && e_max == 0.0) {
+    gershgorin(sys, &e_min, &e_max);
+  }
+  if (!(e_max > e_min) || !isfinite(e_min) || !isfinite(e_max))
+    return fail(ctx, KITE_ERR_ARG, "e_max must exceed e_min");
+  sc->e_min = e_min;
+  sc->e_max = e_max;
+  sc->de_plus = 0.5 * (e_max + e_min);
+  sc->de_minus = 0.5 * (e_max - e_min);
+  return KITE_OK;
+}
+
+}  // namespace kite
+
+using namespace kite;
+
+extern "C" {
+
+const char* kite_status_string(int status) {
+  switch (status) {
+    case KITE_OK: return "ok";
+    case KITE_ERR_ARG: return "invalid argument";
+    case KITE_ERR_OOM: return "out of device memory";
+    case KITE_ERR_CUDA: return "CUDA error";
+    case KITE_ERR_BOUNDS: return "moments out of bounds (spectrum outside [-1,1] after rescaling)";
+    case KITE_ERR_TIMEOUT: return "device-side wait timed out";
+    case KITE_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+  }
+}
+
+const char* kite_last_error(const kite_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int kite_create(kite_ctx** out, int device, void* cuda_stream) {
+  if (!out) return KITE_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return KITE_ERR_ARG;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return KITE_ERR_CUDA;
+  kite_ctx* c = new kite_ctx();
+  c->device = device;
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete c;
+    return KITE_ERR_CUDA;
+  }
+  if (cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return KITE_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+      cudaEventCreate(&c->ev2) != cudaSuccess || cudaEventCreate(&c->ev3) != cudaSuccess) {
+    delete c;
+    return KITE_ERR_CUDA;
+  }
+  // Keep memory freed with cudaFreeAsync cached in the device pool between calls
+  // (a per-process setting of this process's pool; nothing outlives the process).
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  *out = c;
+  return KITE_OK;
+}
+
+void kite_destroy(kite_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  if (ctx->ev2) cudaEventDestroy(ctx->ev2);
+  if (ctx->ev3) cudaEventDestroy(ctx->ev3);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+int kite_set_stream(kite_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return KITE_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  ctx->own_stream = false;
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(ctx, KITE_ERR_CUDA, "stream creation failed");
+    ctx->own_stream = true;
+  }
+  return KITE_OK;
+}
+
+int kite_bounds(const kite_system* sys, double* e_min, double* e_max) {
+  if (!e_min || !e_max) return KITE_ERR_ARG;
+  int rc = validate_system(nullptr, sys);
+  if (rc != KITE_OK) return rc;
+  gershgorin(sys, e_min, e_max);
+  return KITE_OK;
+}
+
+int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, double* mu,
+                    double* mu_per_vec, kite_stats* st) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  int rc = validate_system(ctx, sys);
+  if (rc != KITE_OK) return rc;
+  if (!kpm || !mu) return fail(ctx, KITE_ERR_ARG, "kpm and mu are required");
+  if (kpm->M < 1 || kpm->R < 1 || kpm->S < 1)
+    return fail(ctx, KITE_ERR_ARG, "M, R and S must be >= 1");
+  if (kpm->precision != KITE_FP32 && kpm->precision != KITE_FP64)
+    return fail(ctx, KITE_ERR_ARG, "precision must be KITE_FP32 or KITE_FP64");
+  if ((double)kpm->R * kpm->S > 65536.0) return fail(ctx, KITE_ERR_ARG, "R*S > 65536");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  Scale sc;
+  rc = resolve_bounds(ctx, sys, kpm->e_min, kpm->e_max, &sc);
+  if (rc != KITE_OK) return rc;
+
+  const int M = kpm->M;
+  const size_t nvec = (size_t)kpm->R * kpm->S;
+  const int64_t N = (int64_t)sys->Lx * sys->Ly * (sys->lattice == KITE_HONEYCOMB ? 2 : 1);
+  // Caller start vectors live in a separate allocation so the sweep's work space stays put.
+  const double* r0_dev = nullptr;
+  void* r0_stage = nullptr;
+  if (kpm->r0) {
+    if (is_device_ptr(kpm->r0)) {
+      r0_dev = kpm->r0;
+    } else {
+      const size_t bytes = nvec * (size_t)N * 2 * sizeof(double);
+      KITE_CUDA_TRY(ctx, cudaMallocAsync(&r0_stage, bytes, ctx->stream));
+      KITE_CUDA_TRY(ctx, copy_in(ctx, r0_stage, kpm->r0, bytes));
+      r0_dev = static_cast<const double*>(r0_stage);
+    }
+  }
+  // outputs: device staging for mu, imag and per-vector moments
+  double* out_dev = nullptr;
+  const size_t out_doubles = 2 * (size_t)M + nvec * (size_t)M * 2;
+  KITE_CUDA_TRY(ctx, cudaMallocAsync((void**)&out_dev, out_doubles * sizeof(double), ctx->stream));
+  double* mu_dev = out_dev;
+  double* imag_dev = out_dev + M;
+  double* mu_vec_dev = out_dev + 2 * (size_t)M;
+  kite_stats local{};
+  rc = moments_1d_impl(ctx, sys, kpm, sc, mu_dev, imag_dev, mu_vec_dev, &local, r0_dev);
+  if (rc == KITE_OK) {
+    std::vector<double> host(2 * (size_t)M);
+    cudaError_t e = cudaMemcpyAsync(host.data(), out_dev, 2 * (size_t)M * sizeof(double),
+                                    cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = copy_out(ctx, mu, mu_dev, (size_t)M * sizeof(double));
+    if (e == cudaSuccess && mu_per_vec)
+      e = copy_out(ctx, mu_per_vec, mu_vec_dev, nvec * (size_t)M * 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(ctx, e, "copying moments out");
+    } else {
+      double max_im = 0.0;
+      bool ok = true;
+      for (int n = 0; n < M; ++n) {
+        const double re = host[n], im = host[M + n];
+        if (!isfinite(re) || !isfinite(im) || fabs(re) > 1.0 + 1e-3) ok = false;
+        max_im = fmax(max_im, fabs(im));
+      }
+      local.max_abs_imag = max_im;
+      local.e_min = sc.e_min;
+      local.e_max = sc.e_max;
+      if (!ok)
+        rc = fail(ctx, KITE_ERR_BOUNDS,
+                  "a moment is non-finite or exceeds 1 in magnitude: the spectrum of the "
+                  "rescaled Hamiltonian is not inside [-1,1]");
+    }
+  }
+  cudaFreeAsync(out_dev, ctx->stream);
+  if (r0_stage) cudaFreeAsync(r0_stage, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  if (st) *st = local;
+  return rc;
+}
+
+int kite_reconstruct_dos(kite_ctx* ctx, const double* mu, int M_avail, int M_use, int kernel,
+                         double param, double e_min, double e_max, const double* E, int K,
+                         double* rho) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  if (!mu || !E || !rho || K < 0 || M_avail < 1 || M_use < 1 || M_use > M_avail)
+    return fail(ctx, KITE_ERR_ARG, "need mu, E, rho and 1 <= M_use <= M_avail, K >= 0");
+  if (kernel != KITE_KERNEL_NONE && kernel != KITE_KERNEL_JACKSON && kernel != KITE_KERNEL_LORENTZ)
+    return fail(ctx, KITE_ERR_ARG, "unknown kernel");
+  if (kernel == KITE_KERNEL_LORENTZ && !(param > 0.0))
+    return fail(ctx, KITE_ERR_ARG, "Lorentz kernel needs lambda > 0");
+  if (!(e_max > e_min)) return fail(ctx, KITE_ERR_ARG, "e_max must exceed e_min");
+  if (K == 0) return KITE_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  Scale sc{e_min, e_max, 0.5 * (e_max + e_min), 0.5 * (e_max - e_min)};
+  const bool mu_d = is_device_ptr(mu), E_d = is_device_ptr(E), rho_d = is_device_ptr(rho);
+  double* buf = nullptr;
+  const size_t nbuf = (size_t)M_use * 2 + (size_t)K * 2;
+  KITE_CUDA_TRY(ctx, cudaMallocAsync((void**)&buf, nbuf * sizeof(double), ctx->stream));
+  double* mu_dev = mu_d ? const_cast<double*>(mu) : buf;
+  double* coef = buf + M_use;
+  double* E_dev = E_d ? const_cast<double*>(E) : buf + 2 * (size_t)M_use;
+  double* rho_dev = rho_d ? rho : buf + 2 * (size_t)M_use + K;
+  int rc = KITE_OK;
+  cudaError_t e = cudaSuccess;
+  if (!mu_d) e = copy_in(ctx, mu_dev, mu, (size_t)M_use * sizeof(double));
+  if (e == cudaSuccess && !E_d) e = copy_in(ctx, E_dev, E, (size_t)K * sizeof(double));
+  if (e != cudaSuccess) rc = cuda_fail(ctx, e, "copying inputs");
+  if (rc == KITE_OK) rc = reconstruct_dos_impl(ctx, mu_dev, M_use, kernel, param, sc, E_dev, K, rho_dev, coef);
+  if (rc == KITE_OK && !rho_d) {
+    e = copy_out(ctx, rho, rho_dev, (size_t)K * sizeof(double));
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "copying rho");
+  }
+  cudaFreeAsync(buf, ctx->stream);
+  cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "reconstruct_dos");
+  return rc;
+}
+
+}  // extern "C"

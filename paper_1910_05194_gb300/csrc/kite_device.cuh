@@ -1,0 +1,124 @@
+// kite_device.cuh -- device helpers: counter-based random numbers and the 16-byte
+// vector chunks the stencil kernels move.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kite {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as
+// 1, 2, 3", SC'11).  Ten rounds; each multiplies counter words 0 and 2 by the
+// round constants, crosses the high halves with words 1/3 and the key, and the key
+// advances by the Weyl increments between rounds.
+struct Philox4 {
+  uint32_t w[4];
+};
+
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                 uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  Philox4 r;
+  r.w[0] = c0;
+  r.w[1] = c1;
+  r.w[2] = c2;
+  r.w[3] = c3;
+  return r;
+}
+
+enum : uint32_t { kTagDisorder = 1u, kTagPhase = 2u };
+
+// 53-bit uniform in [0,1): exact in FP64.
+__device__ __forceinline__ double u53(const Philox4& x) {
+  const uint64_t k = (uint64_t(x.w[0]) << 21) | uint64_t(x.w[1] >> 11);
+  return __dmul_rn(__ull2double_rn(k), 0x1p-53);
+}
+
+// A 16-byte chunk of interleaved complex values: two complex FP32 or one complex FP64.
+template <typename Real>
+struct Chunk;
+
+template <>
+struct Chunk<float> {
+  static constexpr int kReals = 4;
+  static constexpr int kVecs = 2;
+  float v[4];
+  __device__ __forceinline__ static Chunk ldg(const void* base, size_t idx) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(base) + idx);
+    Chunk c;
+    c.v[0] = t.x;
+    c.v[1] = t.y;
+    c.v[2] = t.z;
+    c.v[3] = t.w;
+    return c;
+  }
+  __device__ __forceinline__ static Chunk ld(const void* base, size_t idx) {
+    const float4 t = reinterpret_cast<const float4*>(base)[idx];
+    Chunk c;
+    c.v[0] = t.x;
+    c.v[1] = t.y;
+    c.v[2] = t.z;
+    c.v[3] = t.w;
+    return c;
+  }
+  __device__ __forceinline__ void st(void* base, size_t idx) const {
+    reinterpret_cast<float4*>(base)[idx] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+
+template <>
+struct Chunk<double> {
+  static constexpr int kReals = 2;
+  static constexpr int kVecs = 1;
+  double v[2];
+  __device__ __forceinline__ static Chunk ldg(const void* base, size_t idx) {
+    const double2 t = __ldg(reinterpret_cast<const double2*>(base) + idx);
+    Chunk c;
+    c.v[0] = t.x;
+    c.v[1] = t.y;
+    return c;
+  }
+  __device__ __forceinline__ static Chunk ld(const void* base, size_t idx) {
+    const double2 t = reinterpret_cast<const double2*>(base)[idx];
+    Chunk c;
+    c.v[0] = t.x;
+    c.v[1] = t.y;
+    return c;
+  }
+  __device__ __forceinline__ void st(void* base, size_t idx) const {
+    reinterpret_cast<double2*>(base)[idx] = make_double2(v[0], v[1]);
+  }
+};
+
+// Rounded arithmetic with no contraction or reassociation, for both precisions.
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename Real>
+__device__ __forceinline__ Real quiet_nan();
+template <>
+__device__ __forceinline__ float quiet_nan<float>() { return __int_as_float(0x7fc00000); }
+template <>
+__device__ __forceinline__ double quiet_nan<double>() {
+  return __longlong_as_double(0x7ff8000000000000ll);
+}
+
+}  // namespace kite

@@ -1,0 +1,72 @@
+// kite_internal.h -- internal declarations shared by the translation units of
+// libkite_gb.so (never installed, never seen by callers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "kite_gb.h"
+
+struct kite_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  std::string last_error;
+  // Work buffer: one growing device allocation carved per call.
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  // Small pinned host staging area (moments, status words).
+  void* pinned = nullptr;
+  size_t pinned_bytes = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+};
+
+namespace kite {
+
+// Records a message on the context and returns `status`.
+int fail(kite_ctx* ctx, int status, const std::string& msg);
+int cuda_fail(kite_ctx* ctx, cudaError_t e, const char* what);
+
+// Ensures at least `bytes` of device work space; returns KITE_OK / KITE_ERR_OOM.
+int ensure_ws(kite_ctx* ctx, size_t bytes);
+int ensure_pinned(kite_ctx* ctx, size_t bytes);
+
+// True if p is device (or managed) memory of the current device.
+bool is_device_ptr(const void* p);
+
+// Copies `bytes` between caller memory (host or device) and device memory on the
+// context stream.
+cudaError_t copy_in(kite_ctx* ctx, void* dst_dev, const void* src, size_t bytes);
+cudaError_t copy_out(kite_ctx* ctx, void* dst, const void* src_dev, size_t bytes);
+
+// Carves aligned sub-buffers out of the work space.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+  size_t used() const { return (off + 255) & ~size_t(255); }
+};
+
+// Rescaling of Eqs. rescalingH/rescalingE.
+struct Scale {
+  double e_min, e_max, de_plus, de_minus;
+};
+int resolve_bounds(kite_ctx* ctx, const kite_system* sys, double e_min, double e_max, Scale* sc);
+
+}  // namespace kite
+
+#define KITE_CUDA_TRY(ctx, expr)                              \
+  do {                                                        \
+    cudaError_t kite_e_ = (expr);                             \
+    if (kite_e_ != cudaSuccess) return kite::cuda_fail(ctx, kite_e_, #expr); \
+  } while (0)
