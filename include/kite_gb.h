@@ -162,6 +162,15 @@ int kite_bounds(const kite_system* sys, double* e_min, double* e_max);
 int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, double* mu,
                     double* mu_per_vec, kite_stats* st);
 
+/* Test hook for failure detection (no counterpart in the paper).  When `enable` is
+ * non-zero, the first recursion step of the next kite_moments_1d call on this context
+ * arms one shared-memory barrier of one CTA for 16 bytes more than it copies, so that
+ * CTA's bounded wait gives up (after about a second), it drains its own copies and
+ * returns, and the call reports KITE_ERR_TIMEOUT.  Nothing is accessed out of bounds,
+ * no wait is unbounded, and the context stays usable.  The hook disarms itself.
+ * Errors: KITE_ERR_ARG. */
+int kite_debug_stall_once(kite_ctx* ctx, int enable);
+
 /* ---- reconstruction ------------------------------------------------------------- */
 
 /* Density of states per orbital and per eV on caller energies (Eqs. e7, e8a with the

@@ -85,6 +85,8 @@ def lib():
             L.orc_moments_1d.restype = i32
             L.orc_replica_1d.argtypes = [P(System), i32, i32, i32, d, d, i32, vp, vp, vp, i32]
             L.orc_replica_1d.restype = i32
+            L.orc_replica_window.argtypes = [P(System), i32, i32, i32, d, d, i32, i32, i32, i32, vp]
+            L.orc_replica_window.restype = i32
             L.orc_velocity_x.argtypes = [P(System), vp, d, vp, vp]
             L.orc_moments_2d.argtypes = [P(System), i32, i32, i32, d, d, vp, vp, vp, vp, i32]
             L.orc_moments_2d.restype = i32
@@ -248,3 +250,20 @@ def cpgf_coeff(n: int, eps: float, eta: float, sigma: int) -> complex:
     lib().orc_cpgf_coeff(int(n), float(eps), float(eta), int(sigma), ctypes.byref(re),
                          ctypes.byref(im))
     return complex(re.value, im.value)
+
+
+def replica_window(sys: System, M: int, R: int, precision: int, x0: int, y0: int,
+                   realisation: int = 0, e_min=None, e_max=None, half=None):
+    """(r_{M-2}, r_{M-1}) of the fixed-rounding replica at cell (x0, y0) of a large
+    lattice, computed on a light-cone window: [R][2][orbitals per cell] complex."""
+    lo, hi = _bounds(sys, e_min, e_max)
+    sorb = 2 if sys.lattice == HONEYCOMB else 1
+    dt = np.float32 if precision == 0 else np.float64
+    out = np.empty((R, 2, sorb, 2), dt)
+    h = M if half is None else int(half)
+    rc = lib().orc_replica_window(ctypes.byref(sys), int(realisation), int(M), int(R), lo, hi,
+                                  int(precision), int(x0), int(y0), h, _ptr(out))
+    if rc != 0:
+        raise ValueError(f"orc_replica_window failed ({rc})")
+    cdt = np.complex64 if precision == 0 else np.complex128
+    return out.view(cdt).reshape(R, 2, sorb)

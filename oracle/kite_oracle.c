@@ -643,3 +643,143 @@ void orc_cpgf_coeff(int n, double eps, double eta, int sigma, double* re, double
   *re = creal(gval);
   *im = cimag(gval);
 }
+
+/* ------------------------------------------------------------------------------ */
+/* Replica iterates at one site of a large periodic lattice, computed on a window.   */
+/* The stencil couples nearest neighbours only, so T_n(H~) r at an orbital depends   */
+/* only on orbitals within n hops (finite propagation of the recursion, Eq. e6).     */
+/* Each hop moves the cell by at most one step in x and in y, so a window of          */
+/* half-width h >= M cells around (x0, y0), with neighbours outside the window read   */
+/* as zero, reproduces the global recursion exactly at its centre.  Draws use the    */
+/* global orbital indices, so the window sees the global disorder, vacancies and     */
+/* random phases.  out: [R][2][orbitals per cell] complex of the working precision,  */
+/* the last two iterates (r_{M-2}, r_{M-1}) at the cell (x0, y0).                    */
+/* ------------------------------------------------------------------------------ */
+int orc_replica_window(const orc_system* sys, int realisation, int M, int R, double e_min,
+                       double e_max, int precision, int x0, int y0, int half, void* out) {
+  if (M < 1 || R < 1 || half < M || !(e_max > e_min)) return -1;
+  if (precision != 0 && precision != 1) return -1;
+  const int sorb = sys->lattice == 0 ? 2 : 1;
+  const int w = 2 * half + 1;
+  const int64_t nw = (int64_t)w * w * sorb;
+  double de_plus = 0.5 * (e_max + e_min), de_minus = 0.5 * (e_max - e_min);
+  double tt = sys->t / de_minus;
+  int64_t* gidx = (int64_t*)malloc(sizeof(int64_t) * nw);
+  int64_t* nb = (int64_t*)malloc(sizeof(int64_t) * 4 * nw); /* -1 = outside the window */
+  double* vt = (double*)malloc(sizeof(double) * nw);
+  uint8_t* vac = (uint8_t*)malloc(nw);
+  double* r0 = (double*)malloc(sizeof(double) * 2 * nw * R);
+  if (!gidx || !nb || !vt || !vac || !r0) return -2;
+  double thr_d = floor(sys->p_vac * 4294967296.0);
+  uint64_t thr = sys->p_vac <= 0.0 ? 0 : (thr_d >= 4294967296.0 ? 4294967296ull : (uint64_t)thr_d);
+  const double two_pi = 6.283185307179586;
+  for (int wy = 0; wy < w; ++wy)
+    for (int wx = 0; wx < w; ++wx)
+      for (int s = 0; s < sorb; ++s) {
+        int64_t l = ((int64_t)wy * w + wx) * sorb + s;
+        int64_t gx = orc_wrap((int64_t)x0 - half + wx, sys->Lx);
+        int64_t gy = orc_wrap((int64_t)y0 - half + wy, sys->Ly);
+        int64_t o = (gy * sys->Lx + gx) * sorb + s;
+        gidx[l] = o;
+        uint32_t x[4];
+        orc_draw(sys, (uint64_t)o, (uint32_t)realisation, ORC_TAG_DISORDER, x);
+        double v = sys->W * (orc_u53(x) - 0.5);
+        if (sys->lattice == 0 && sys->delta != 0.0) {
+          double hd = 0.5 * sys->delta;
+          v = v + (s == 0 ? hd : -hd);
+        }
+        vac[l] = ((uint64_t)x[2] < thr) ? 1 : 0;
+        vt[l] = (v - de_plus) / de_minus;
+        for (int r = 0; r < R; ++r) {
+          double* z = r0 + 2 * ((int64_t)r * nw + l);
+          if (vac[l]) {
+            z[0] = z[1] = 0.0;
+            continue;
+          }
+          uint32_t y[4];
+          orc_draw(sys, (uint64_t)o, (uint32_t)realisation * (uint32_t)R + (uint32_t)r,
+                   ORC_TAG_PHASE, y);
+          double phi = two_pi * orc_u53(y);
+          z[0] = cos(phi);
+          z[1] = sin(phi);
+        }
+        /* neighbours in the order of orc_neighbours_dx, in window coordinates */
+        int64_t* q = nb + 4 * l;
+        q[0] = q[1] = q[2] = q[3] = -1;
+#define ORC_WIN(X, Y, S) (((X) < 0 || (X) >= w || (Y) < 0 || (Y) >= w) ? -1 : (((int64_t)(Y) * w + (X)) * sorb + (S)))
+        if (sys->lattice == 0) {
+          if (s == 0) {
+            q[0] = ORC_WIN(wx, wy, 1);
+            q[1] = ORC_WIN(wx + 1, wy - 1, 1);
+            q[2] = ORC_WIN(wx, wy - 1, 1);
+          } else {
+            q[0] = ORC_WIN(wx, wy, 0);
+            q[1] = ORC_WIN(wx - 1, wy + 1, 0);
+            q[2] = ORC_WIN(wx, wy + 1, 0);
+          }
+        } else {
+          q[0] = ORC_WIN(wx - 1, wy, 0);
+          q[1] = ORC_WIN(wx + 1, wy, 0);
+          q[2] = ORC_WIN(wx, wy - 1, 0);
+          q[3] = ORC_WIN(wx, wy + 1, 0);
+        }
+#undef ORC_WIN
+      }
+  const int Z = sys->lattice == 0 ? 3 : 4;
+  const int64_t centre = ((int64_t)half * w + half) * sorb;
+#define ORC_WINDOW_RUN(REAL, FMA)                                                           \
+  {                                                                                         \
+    REAL* a = (REAL*)malloc(sizeof(REAL) * 2 * nw);                                         \
+    REAL* b = (REAL*)malloc(sizeof(REAL) * 2 * nw);                                         \
+    REAL* c = (REAL*)malloc(sizeof(REAL) * 2 * nw);                                         \
+    REAL tr = (REAL)tt;                                                                     \
+    for (int r = 0; r < R; ++r) {                                                           \
+      REAL *prev = a, *cur = b, *nxt = c;                                                   \
+      for (int64_t k = 0; k < 2 * nw; ++k) cur[k] = (REAL)r0[2 * (int64_t)r * nw + k];      \
+      memcpy(prev, cur, sizeof(REAL) * 2 * nw);                                             \
+      for (int n = 0; n + 1 < M; ++n) {                                                     \
+        for (int64_t l = 0; l < nw; ++l)                                                    \
+          for (int cc = 0; cc < 2; ++cc) {                                                  \
+            REAL v;                                                                         \
+            if (vac[l]) {                                                                   \
+              v = (REAL)0;                                                                  \
+            } else {                                                                        \
+              const int64_t* q = nb + 4 * l;                                                \
+              REAL n1 = q[0] < 0 ? (REAL)0 : cur[2 * q[0] + cc];                            \
+              REAL n2 = q[1] < 0 ? (REAL)0 : cur[2 * q[1] + cc];                            \
+              REAL n3 = q[2] < 0 ? (REAL)0 : cur[2 * q[2] + cc];                            \
+              REAL s = n1 + n2;                                                             \
+              s = s + n3;                                                                   \
+              if (Z == 4) s = s + (q[3] < 0 ? (REAL)0 : cur[2 * q[3] + cc]);                \
+              REAL p = (REAL)vt[l] * cur[2 * l + cc];                                       \
+              REAL hv = FMA(tr, s, p);                                                      \
+              v = n == 0 ? hv : FMA((REAL)2, hv, -prev[2 * l + cc]);                        \
+            }                                                                               \
+            nxt[2 * l + cc] = v;                                                            \
+          }                                                                                 \
+        REAL* tmp = prev;                                                                   \
+        prev = cur;                                                                         \
+        cur = nxt;                                                                          \
+        nxt = tmp;                                                                          \
+      }                                                                                     \
+      REAL* dst = (REAL*)out + (int64_t)r * 2 * sorb * 2;                                   \
+      for (int s = 0; s < sorb; ++s) {                                                      \
+        dst[2 * s] = prev[2 * (centre + s)];                                                \
+        dst[2 * s + 1] = prev[2 * (centre + s) + 1];                                        \
+        dst[2 * sorb + 2 * s] = cur[2 * (centre + s)];                                      \
+        dst[2 * sorb + 2 * s + 1] = cur[2 * (centre + s) + 1];                              \
+      }                                                                                     \
+    }                                                                                       \
+    free(a);                                                                                \
+    free(b);                                                                                \
+    free(c);                                                                                \
+  }
+  if (precision == 0) ORC_WINDOW_RUN(float, fmaf) else ORC_WINDOW_RUN(double, fma)
+#undef ORC_WINDOW_RUN
+  free(gidx);
+  free(nb);
+  free(vt);
+  free(vac);
+  free(r0);
+  return 0;
+}

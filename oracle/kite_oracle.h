@@ -51,6 +51,9 @@ int orc_replica_1d(const orc_system* sys, int realisation, int M, int R, double 
                    double e_max, int precision, const double* r0_in, double* mu_per_vec,
                    void* r_last, int threads);
 
+int orc_replica_window(const orc_system* sys, int realisation, int M, int R, double e_min,
+                       double e_max, int precision, int x0, int y0, int half, void* out);
+
 void orc_velocity_x(const orc_system* sys, const uint8_t* vac, double t_scaled,
                     const double* in, double* out);
 int orc_moments_2d(const orc_system* sys, int realisation, int M, int R, double e_min,

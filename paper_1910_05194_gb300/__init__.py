@@ -23,7 +23,8 @@ FP32, FP64 = 0, 1
 KERNEL_NONE, KERNEL_JACKSON, KERNEL_LORENTZ = 0, 1, 2
 
 EXPORTED = ("kite_create", "kite_destroy", "kite_set_stream", "kite_status_string",
-            "kite_last_error", "kite_bounds", "kite_moments_1d", "kite_reconstruct_dos")
+            "kite_last_error", "kite_bounds", "kite_moments_1d", "kite_reconstruct_dos",
+            "kite_debug_stall_once")
 
 
 class KiteError(RuntimeError):
@@ -100,6 +101,8 @@ def lib():
             L.kite_moments_1d.restype = i32
             L.kite_reconstruct_dos.argtypes = [vp, vp, i32, i32, i32, d, d, d, vp, i32, vp]
             L.kite_reconstruct_dos.restype = i32
+            L.kite_debug_stall_once.argtypes = [vp, i32]
+            L.kite_debug_stall_once.restype = i32
             _LIB = L
     return _LIB
 
@@ -191,3 +194,8 @@ def reconstruct_dos(ctx: Context, mu, M_avail: int, M_use: int, kernel: int, par
     ctx.check(lib().kite_reconstruct_dos(ctx.handle, _addr(mu), int(M_avail), int(M_use),
                                          int(kernel), float(param), float(e_min), float(e_max),
                                          _addr(E), int(K), _addr(rho)))
+
+
+def debug_stall_once(ctx: Context, enable: bool = True):
+    """Test hook: the next kite_moments_1d call's first step times out (KITE_ERR_TIMEOUT)."""
+    ctx.check(lib().kite_debug_stall_once(ctx.handle, int(bool(enable))))

@@ -170,6 +170,11 @@ int kite_create(kite_ctx** out, int device, void* cuda_stream) {
     delete c;
     return KITE_ERR_CUDA;
   }
+  if (cudaMalloc(&c->d_status, 256) != cudaSuccess || cudaMemset(c->d_status, 0, 256) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return KITE_ERR_CUDA;
+  }
   // Keep memory freed with cudaFreeAsync cached in the device pool between calls
   // (a per-process setting of this process's pool; nothing outlives the process).
   cudaMemPool_t pool;
@@ -192,6 +197,7 @@ void kite_destroy(kite_ctx* ctx) {
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->ev2) cudaEventDestroy(ctx->ev2);
   if (ctx->ev3) cudaEventDestroy(ctx->ev3);
+  if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -209,6 +215,12 @@ int kite_set_stream(kite_ctx* ctx, void* cuda_stream) {
       return fail(ctx, KITE_ERR_CUDA, "stream creation failed");
     ctx->own_stream = true;
   }
+  return KITE_OK;
+}
+
+int kite_debug_stall_once(kite_ctx* ctx, int enable) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->debug_stall = enable ? 1 : 0;
   return KITE_OK;
 }
 

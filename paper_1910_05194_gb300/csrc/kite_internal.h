@@ -22,6 +22,9 @@ struct kite_ctx {
   void* pinned = nullptr;
   size_t pinned_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+  // Device status word: kernels set it (never trap) when a bounded wait gives up.
+  int* d_status = nullptr;
+  int debug_stall = 0;  // test hook, see kite_debug_stall_once
 };
 
 namespace kite {

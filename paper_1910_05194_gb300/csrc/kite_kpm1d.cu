@@ -99,9 +99,9 @@ __global__ void k_init_r0(int64_t ncell, const Real* __restrict__ vt, int vec_ba
 //
 // Work unit = one row segment of TX cells (TX*threads-per-cell = 256 threads, one
 // 16-byte chunk each).  Each CTA of the persistent grid owns a contiguous range of
-// units ordered strip-major, so it marches down the rows of an x-strip and the rows
-// above/below (the neighbours of the honeycomb/square stencil) are re-read from L1/L2
-// instead of HBM.  Per-site rounding sequence (shared with the oracle's replica):
+// units ordered strip-major, so it marches down the rows of an x-strip; each row of r_n
+// is fetched from HBM once per strip (plus one halo row per segment end and one halo
+// cell per side) and reused from shared memory by the rows above and below.  Per-site rounding sequence (shared with the oracle's replica):
 //   s = (nb1 + nb2) + nb3 [+ nb4];  h = fma(t~, s, V~ * r);
 //   first step: out = h;  otherwise out = fma(2, h, -r_prev);  vacancy: out = 0.
 // Honeycomb neighbours: A(x,y) <- B(x,y), B(x+1,y-1), B(x,y-1);
@@ -117,97 +117,195 @@ struct AccT<double> {
   using T = double;
 };
 
+// Shared-memory ring: kStages slots, each one row segment of the strip.  A slot holds
+// r_n of the row with one halo cell on either side (the periodic neighbours x0-1 and
+// x0+TX), and for interior rows also r_{n-1} and r_0 of the row.  Computing row y needs
+// the slots of rows y-1, y, y+1; the copy of row y+kStages-1 is issued as soon as row
+// y-1's slot is free, so ~6 rows (~75 KB per CTA) are always in flight.
+constexpr int kStages = 8;
+constexpr int kBarBytes = 128;
+
+template <int LAT, int C>
+struct StepShape {
+  static constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
+  static constexpr int TPC = SORB * C;              // threads per cell
+  static constexpr int TX = kBlock / TPC;           // cells per row segment
+  static constexpr int CELLB = SORB * C * 16;       // bytes of one cell of the batch
+  static constexpr int ROWB = TX * CELLB;           // bytes of one row segment (4096)
+  static constexpr int CURB = (TX + 2) * CELLB;     // r_n row segment with halo cells
+  static constexpr int STAGEB = CURB + 2 * ROWB;    // + r_{n-1} and r_0
+  static constexpr int SMEM = kBarBytes + kStages * STAGEB;
+};
+
 template <typename Real, int LAT, int C, bool FIRST>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 2)
     k_step(const void* r_prev, const void* __restrict__ r_cur, void* r_out,
            const void* __restrict__ r0, const Real* __restrict__ vt, Real tt, int Lx, int Ly,
-           long long units, double* __restrict__ partial, double* __restrict__ partial0) {
+           long long units, double* __restrict__ partial, double* __restrict__ partial0,
+           int* __restrict__ err, int stall) {
   using Ch = Chunk<Real>;
   using Acc = typename AccT<Real>::T;
+  using Sh = StepShape<LAT, C>;
   constexpr int VPC = Ch::kVecs, NR = Ch::kReals;
-  constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
-  constexpr int TPC = SORB * C;
-  constexpr int TX = kBlock / TPC;
+  constexpr int SORB = Sh::SORB, TPC = Sh::TPC, TX = Sh::TX, CELLB = Sh::CELLB;
   constexpr int QT = 2 * VPC;  // (re, im) per vector held by one thread
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  unsigned char* stages = smem + kBarBytes;
+  __shared__ int s_abort;
+
   const int tid = threadIdx.x;
   const int xl = tid / TPC;
   const int j = tid - xl * TPC;
   const int s = j / C;
   const int c = j - s * C;
+  const int choff = (s * C + c) * 16;             // this thread's chunk inside a cell
+  const int nboff = ((1 - s) * C + c) * 16;       // same chunk, other sublattice
+
+  if (tid == 0) {
+    for (int k = 0; k < kStages; ++k) mbar_init(&bars[k], 1);
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  __syncthreads();
 
   const long long u0 = units * (long long)blockIdx.x / gridDim.x;
   const long long u1 = units * (long long)(blockIdx.x + 1) / gridDim.x;
-  int sx = (int)(u0 / Ly);
-  int y = (int)(u0 - (long long)sx * Ly);
 
   double dacc[QT], dacc0[QT];
   Acc facc[QT], facc0[QT];
 #pragma unroll
   for (int k = 0; k < QT; ++k) dacc[k] = dacc0[k] = 0.0, facc[k] = facc0[k] = Acc(0);
   int rows = 0;
+  long long gslot = 0;  // slots consumed so far (phase bookkeeping of the ring)
+  bool aborted = false;
 
-  for (long long u = u0; u < u1; ++u) {
-    const int x = sx * TX + xl;
-    if (x < Lx) {
-      const size_t cell = (size_t)y * Lx + x;
-      const size_t self = (cell * SORB + s) * C + c;
-      const int ym = (y == 0) ? Ly - 1 : y - 1;
-      const int yp = (y + 1 == Ly) ? 0 : y + 1;
-      const int xm = (x == 0) ? Lx - 1 : x - 1;
-      const int xp = (x + 1 == Lx) ? 0 : x + 1;
-      Ch n1, n2, n3, n4;
-      if (LAT == KITE_HONEYCOMB) {
-        const int so = 1 - s;  // the other sublattice
-        const int ny = s == 0 ? ym : yp;
-        const int nx = s == 0 ? xp : xm;
-        n1 = Ch::ldg(r_cur, (cell * 2 + so) * C + c);
-        n2 = Ch::ldg(r_cur, (((size_t)ny * Lx + nx) * 2 + so) * C + c);
-        n3 = Ch::ldg(r_cur, (((size_t)ny * Lx + x) * 2 + so) * C + c);
-      } else {
-        n1 = Ch::ldg(r_cur, ((size_t)y * Lx + xm) * C + c);
-        n2 = Ch::ldg(r_cur, ((size_t)y * Lx + xp) * C + c);
-        n3 = Ch::ldg(r_cur, ((size_t)ym * Lx + x) * C + c);
-        n4 = Ch::ldg(r_cur, ((size_t)yp * Lx + x) * C + c);
+  for (long long u = u0; u < u1 && !aborted;) {
+    // one segment = consecutive rows of one x-strip
+    const int sx = (int)(u / Ly);
+    const int yb = (int)(u - (long long)sx * Ly);
+    const int nr = (int)min(u1 - u, (long long)(Ly - yb));
+    const int x0 = sx * TX;
+    const int txv = min(TX, Lx - x0);
+    const int xlh = (x0 == 0) ? Lx - 1 : x0 - 1;
+    const int xrh = (x0 + txv == Lx) ? 0 : x0 + txv;
+    const int nslots = nr + 2;
+
+    auto issue = [&](int jj) {  // producer: thread 0 only
+      const long long g = gslot + jj;
+      const int st = (int)(g % kStages);
+      unsigned char* base = stages + st * Sh::STAGEB;
+      int row = yb - 1 + jj;
+      row = row < 0 ? row + Ly : (row >= Ly ? row - Ly : row);
+      const bool interior = !FIRST && jj >= 1 && jj <= nr;
+      const uint32_t main_b = (uint32_t)txv * CELLB;
+      uint32_t bytes = main_b + 2 * CELLB + (interior ? 2 * main_b : 0);
+      if (stall && blockIdx.x == 0 && g == 0) bytes += 16;  // test hook: never completes
+      mbar_arrive_expect_tx(&bars[st], bytes);
+      const unsigned char* rowp = static_cast<const unsigned char*>(r_cur) + (size_t)row * Lx * CELLB;
+      bulk_g2s(base + CELLB, rowp + (size_t)x0 * CELLB, main_b, &bars[st]);
+      bulk_g2s(base, rowp + (size_t)xlh * CELLB, CELLB, &bars[st]);
+      bulk_g2s(base + (size_t)(txv + 1) * CELLB, rowp + (size_t)xrh * CELLB, CELLB, &bars[st]);
+      if (interior) {
+        const size_t off = ((size_t)row * Lx + x0) * CELLB;
+        bulk_g2s(base + Sh::CURB, static_cast<const unsigned char*>(r_prev) + off, main_b, &bars[st]);
+        bulk_g2s(base + Sh::CURB + Sh::ROWB, static_cast<const unsigned char*>(r0) + off, main_b,
+                 &bars[st]);
       }
-      const Ch me = Ch::ldg(r_cur, self);
-      const Ch z0 = FIRST ? me : Ch::ldg(r0, self);
-      Ch pv;
-      if (!FIRST) pv = Ch::ld(r_prev, self);
-      const Real v = vt[cell * SORB + s];
-      const bool vacant = v != v;
-      Ch out;
-#pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        Real sum = radd(n1.v[k], n2.v[k]);
-        sum = radd(sum, n3.v[k]);
-        if (LAT == KITE_SQUARE) sum = radd(sum, n4.v[k]);
-        const Real h = rfma(tt, sum, rmul(v, me.v[k]));
-        Real o = FIRST ? h : rfma(Real(2), h, -pv.v[k]);
-        out.v[k] = vacant ? Real(0) : o;
+    };
+    if (tid == 0)
+      for (int jj = 0; jj < min(kStages, nslots); ++jj) issue(jj);
+
+    const bool active = xl < txv;
+    Real vnext = active ? vt[((size_t)yb * Lx + x0 + xl) * SORB + s] : Real(0);
+    int i = 0;
+    for (; i < nr; ++i) {
+      bool ok = true;
+      for (int jj = (i == 0 ? 0 : i + 2); jj <= i + 2; ++jj) {
+        const long long g = gslot + jj;
+        ok = mbar_wait_bounded(&bars[g % kStages], (uint32_t)((g / kStages) & 1)) && ok;
       }
-      out.st(r_out, self);
+      if (!ok) s_abort = 1;
+      const int y = yb + i;
+      const Real v = vnext;
+      if (active && i + 1 < nr) vnext = vt[((size_t)(y + 1) * Lx + x0 + xl) * SORB + s];
+      if (ok && active) {
+        const unsigned char* up = stages + (int)((gslot + i) % kStages) * Sh::STAGEB;
+        const unsigned char* mid = stages + (int)((gslot + i + 1) % kStages) * Sh::STAGEB;
+        const unsigned char* dn = stages + (int)((gslot + i + 2) % kStages) * Sh::STAGEB;
+        const Ch me = *reinterpret_cast<const Ch*>(mid + (xl + 1) * CELLB + choff);
+        Ch n1, n2, n3, n4;
+        if (LAT == KITE_HONEYCOMB) {
+          // A(x,y) <- B(x,y), B(x+1,y-1), B(x,y-1);  B(x,y) <- A(x,y), A(x-1,y+1), A(x,y+1)
+          const unsigned char* other = s == 0 ? up : dn;
+          const int dxi = s == 0 ? xl + 2 : xl;
+          n1 = *reinterpret_cast<const Ch*>(mid + (xl + 1) * CELLB + nboff);
+          n2 = *reinterpret_cast<const Ch*>(other + dxi * CELLB + nboff);
+          n3 = *reinterpret_cast<const Ch*>(other + (xl + 1) * CELLB + nboff);
+        } else {
+          n1 = *reinterpret_cast<const Ch*>(mid + xl * CELLB + choff);
+          n2 = *reinterpret_cast<const Ch*>(mid + (xl + 2) * CELLB + choff);
+          n3 = *reinterpret_cast<const Ch*>(up + (xl + 1) * CELLB + choff);
+          n4 = *reinterpret_cast<const Ch*>(dn + (xl + 1) * CELLB + choff);
+        }
+        Ch pv, z0;
+        if (FIRST) {
+          z0 = me;
+        } else {
+          pv = *reinterpret_cast<const Ch*>(mid + Sh::CURB + xl * CELLB + choff);
+          z0 = *reinterpret_cast<const Ch*>(mid + Sh::CURB + Sh::ROWB + xl * CELLB + choff);
+        }
+        const bool vacant = v != v;
+        Ch out;
 #pragma unroll
-      for (int q = 0; q < VPC; ++q) {
-        const Acc ar = z0.v[2 * q], ai = z0.v[2 * q + 1];
-        const Acc br = out.v[2 * q], bi = out.v[2 * q + 1];
-        facc[2 * q] += ar * br + ai * bi;
-        facc[2 * q + 1] += ar * bi - ai * br;
-        if (FIRST) facc0[2 * q] += ar * ar + ai * ai;
-      }
-      if (++rows == kFlushRows) {
-        rows = 0;
+        for (int k = 0; k < NR; ++k) {
+          Real sum = radd(n1.v[k], n2.v[k]);
+          sum = radd(sum, n3.v[k]);
+          if (LAT == KITE_SQUARE) sum = radd(sum, n4.v[k]);
+          const Real h = rfma(tt, sum, rmul(v, me.v[k]));
+          const Real o = FIRST ? h : rfma(Real(2), h, -pv.v[k]);
+          out.v[k] = vacant ? Real(0) : o;
+        }
+        out.st(r_out, (((size_t)y * Lx + x0 + xl) * SORB + s) * C + c);
 #pragma unroll
-        for (int k = 0; k < QT; ++k) {
-          dacc[k] += (double)facc[k];
-          facc[k] = Acc(0);
-          if (FIRST) dacc0[k] += (double)facc0[k], facc0[k] = Acc(0);
+        for (int q = 0; q < VPC; ++q) {
+          const Acc ar = z0.v[2 * q], ai = z0.v[2 * q + 1];
+          const Acc br = out.v[2 * q], bi = out.v[2 * q + 1];
+          facc[2 * q] += ar * br + ai * bi;
+          facc[2 * q + 1] += ar * bi - ai * br;
+          if (FIRST) facc0[2 * q] += ar * ar + ai * ai;
+        }
+        if (++rows == kFlushRows) {
+          rows = 0;
+#pragma unroll
+          for (int k = 0; k < QT; ++k) {
+            dacc[k] += (double)facc[k];
+            facc[k] = Acc(0);
+            if (FIRST) dacc0[k] += (double)facc0[k], facc0[k] = Acc(0);
+          }
         }
       }
+      __syncthreads();  // every thread is done with slot i
+      if (s_abort) {
+        aborted = true;
+        break;
+      }
+      if (tid == 0 && i + kStages < nslots) issue(i + kStages);
     }
-    if (++y == Ly) {
-      y = 0;
-      ++sx;
+    if (aborted) {
+      // drain: wait (bounded) for this CTA's copies still in flight, then give up
+      if (tid == 0) {
+        const int last = min(nslots, i + kStages) - 1;
+        for (int jj = i; jj <= last; ++jj) {  // completed phases return at once
+          const long long g = gslot + jj;
+          mbar_wait_bounded(&bars[g % kStages], (uint32_t)((g / kStages) & 1));
+        }
+        atomicExch(err, 1);
+      }
+      return;
     }
+    gslot += nslots;
+    u += nr;
   }
 #pragma unroll
   for (int k = 0; k < QT; ++k) {
@@ -215,9 +313,9 @@ __global__ void __launch_bounds__(kBlock)
     if (FIRST) dacc0[k] += (double)facc0[k];
   }
 
-  // CTA reduction in fixed order: lane (vector v = c*VPC + q, component) sums the
-  // threads holding chunk c, in thread order.
-  __shared__ double red[kBlock][QT];
+  // CTA reduction in fixed order (the ring is drained, so its memory is reused):
+  // lane (vector v = c*VPC + q, component) sums the threads holding chunk c.
+  double(*red)[QT] = reinterpret_cast<double(*)[QT]>(stages);
   constexpr int Q = 2 * C * VPC;
 #pragma unroll
   for (int k = 0; k < QT; ++k) red[tid][k] = dacc[k];
@@ -302,7 +400,10 @@ int grid_for(kite_ctx* ctx, long long units) {
   static int occ = -1;  // per template instance; device-independent enough for one GPU type
   if (occ < 0) {
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_step<Real, LAT, C, FIRST>, kBlock, 0) !=
+    const int smem = StepShape<LAT, C>::SMEM;
+    cudaFuncSetAttribute(k_step<Real, LAT, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_step<Real, LAT, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_step<Real, LAT, C, FIRST>, kBlock, smem) !=
             cudaSuccess ||
         o < 1)
       o = 1;
@@ -333,20 +434,25 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
   // r_{n+1} overwrites r_{n-1} in place except at n = 1 (r_0 is kept for the moments).
   auto where = [&](int n) -> void* { return n == 0 ? r0 : ((n & 1) ? bA : bB); };
   KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
+  constexpr int SM = StepShape<LAT, C>::SMEM;
   if (M >= 2)
-    k_step<Real, LAT, C, true><<<G, kBlock, 0, st>>>(nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly,
-                                                     units, partial + (size_t)G * Q, partial);
+    k_step<Real, LAT, C, true><<<G, kBlock, SM, st>>>(nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly,
+                                                      units, partial + (size_t)G * Q, partial,
+                                                      ctx->d_status, ctx->debug_stall);
+  ctx->debug_stall = 0;
   for (int n = 1; n + 1 < M; ++n)
-    k_step<Real, LAT, C, false><<<G, kBlock, 0, st>>>(where(n - 1), where(n), where(n + 1), r0,
-                                                      vt, tt, p.Lx, p.Ly, units,
-                                                      partial + (size_t)(n + 1) * G * Q, nullptr);
+    k_step<Real, LAT, C, false><<<G, kBlock, SM, st>>>(where(n - 1), where(n), where(n + 1), r0,
+                                                       vt, tt, p.Lx, p.Ly, units,
+                                                       partial + (size_t)(n + 1) * G * Q, nullptr,
+                                                       ctx->d_status, 0);
   KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
   KITE_CUDA_TRY(ctx, cudaGetLastError());
   if (M == 1) {
     // mu_0 alone: one FIRST pass would also write r_1; a plain dot is enough, but the
     // FIRST kernel is cheap and keeps one code path.
-    k_step<Real, LAT, C, true><<<G, kBlock, 0, st>>>(nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly,
-                                                     units, partial + (size_t)G * Q, partial);
+    k_step<Real, LAT, C, true><<<G, kBlock, SM, st>>>(nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly,
+                                                      units, partial + (size_t)G * Q, partial,
+                                                      ctx->d_status, 0);
     KITE_CUDA_TRY(ctx, cudaGetLastError());
   }
   const int total = M * Q;
@@ -437,6 +543,7 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
   int grid_used = 0;
   double step_s = 0.0, step_bytes = 0.0;
   int64_t step_n = 0;
+  KITE_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
   for (int s = 0; s < p.S; ++s) {
     KITE_CUDA_TRY(ctx, cudaMemsetAsync(ne, 0, sizeof(unsigned long long), st));
     {
@@ -521,8 +628,12 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
       }
     }
     unsigned long long ne_host = 0;
+    int status_host = 0;
     KITE_CUDA_TRY(ctx, cudaMemcpyAsync(&ne_host, ne, sizeof(ne_host), cudaMemcpyDeviceToHost, st));
+    KITE_CUDA_TRY(ctx, cudaMemcpyAsync(&status_host, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (status_host != 0)
+      return fail(ctx, KITE_ERR_TIMEOUT, "a bounded wait on a bulk copy gave up in the step kernel");
     n_eff_last = (int64_t)ne_host;
   }
   {

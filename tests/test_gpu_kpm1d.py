@@ -181,3 +181,49 @@ def test_dos_reconstruction_matches_oracle(ctx):
         kite.reconstruct_dos(ctx, mu, M, 200, kern, par, lo, hi, E, E.size, rho)
         ref = oracle.dos(mu[:200], E, lo, hi, g)
         assert np.max(np.abs(rho - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_bounded_wait_timeout_is_reported_and_context_survives(ctx):
+    """A barrier armed for bytes that never arrive: the bounded wait gives up, the call
+    returns KITE_ERR_TIMEOUT, and the next call on the same context is correct."""
+    d = dict(lattice=oracle.HONEYCOMB, Lx=64, Ly=48, t=-2.7, W=1.0, seed=6)
+    kite.debug_stall_once(ctx)
+    with pytest.raises(kite.KiteError) as e:
+        run_gpu(ctx, d, 32, 4)
+    assert e.value.status == kite.ERR_TIMEOUT
+    mu, _, _, _ = run_gpu(ctx, d, 32, 4)
+    ref = oracle.moments_1d(osys(**d), 32, 4).real.mean(0)
+    assert np.max(np.abs(mu - ref)) <= 1e-5
+
+
+def test_full_size_launch_sampled_sites_match_window_oracle(ctx):
+    """The bench's lattice (4096 x 4096 honeycomb, R = 8, FP32) and launch configuration,
+    with few moments: iterates at sampled sites against the light-cone window replica,
+    N_eff exact, mu_0 = 1."""
+    torch = pytest.importorskip("torch")
+    d = dict(lattice=oracle.HONEYCOMB, Lx=4096, Ly=4096, t=-2.7, W=2.0, p_vac=0.005, seed=2)
+    M, R = 12, 8
+    n = 2 * 4096 * 4096
+    last = torch.zeros((R, 2, n), dtype=torch.complex64, device="cuda")
+    mu = torch.zeros(M, dtype=torch.float64, device="cuda")
+    st = kite.moments_1d(ctx, ksys(**d), kite.make_kpm(M, R, 1, kite.FP32, r_last=last), mu)
+    s = osys(**d)
+    rng = np.random.default_rng(0)
+    sites = [(0, 0), (4095, 4095), (4095, 0), (0, 4095), (31, 32), (32, 31), (2047, 2048)]
+    sites += [tuple(int(v) for v in rng.integers(0, 4096, 2)) for _ in range(9)]
+    exact, total = 0, 0
+    for (x0, y0) in sites:
+        ref = oracle.replica_window(s, M, R, 0, x0, y0)  # [R][2][2]
+        o = 2 * (y0 * 4096 + x0)
+        got = last[:, :, o:o + 2].cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= 1e-5, (x0, y0)
+        exact += int(np.sum(got == ref))
+        total += got.size
+    # device random phases use CUDA's FP64 sincos, the oracle libm's: they round to the
+    # same FP32 value except at rare ties, so nearly every iterate is bit-identical
+    assert exact >= 0.98 * total
+    _, vac = oracle.disorder(s)
+    assert st.n_eff == int((vac == 0).sum())
+    mu_h = mu.cpu().numpy()
+    assert abs(mu_h[0] - 1.0) <= 1e-6
+    assert np.all(np.abs(mu_h) <= 1.0)

@@ -387,3 +387,21 @@ def test_2d_stochastic_estimate_is_close():
     mu_ex = oracle.moments_2d(sys, M, n, r0=np.eye(n, dtype=np.complex128)) * n
     scale = np.max(np.abs(mu_ex))
     assert np.max(np.abs(mu_st - mu_ex)) < 0.1 * scale
+
+
+@pytest.mark.parametrize("lattice", [oracle.HONEYCOMB, oracle.SQUARE])
+def test_light_cone_window_reproduces_full_replica(lattice):
+    """T_n r at a site depends only on orbitals within n hops: the window replica equals
+    the full-lattice replica bit for bit at sampled sites, corners included."""
+    Lx, Ly = (40, 36) if lattice == oracle.HONEYCOMB else (45, 33)
+    t = T_EV if lattice == oracle.HONEYCOMB else -1.0
+    s = oracle.make_system(lattice=lattice, Lx=Lx, Ly=Ly, t=t, W=2.0, p_vac=0.03, seed=5,
+                           delta=0.3 if lattice == oracle.HONEYCOMB else 0.0)
+    M, R = 12, 2
+    sorb = 2 if lattice == oracle.HONEYCOMB else 1
+    for prec in (0, 1):
+        _, full = oracle.replica_1d(s, M, R, prec, want_last=True)
+        for (x0, y0) in ((0, 0), (Lx - 1, Ly - 1), (17, 5), (3, Ly - 2)):
+            w = oracle.replica_window(s, M, R, prec, x0, y0)
+            o = (y0 * Lx + x0) * sorb
+            assert np.array_equal(w, full[:, :, o:o + sorb])
