@@ -129,7 +129,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha1()
-    for fn in ("kite_kpm1d.cu", "kite_device.cuh"):
+    for fn in ("kite_kpm1d.cu", "kite_step.cuh", "kite_device.cuh"):
         with open(os.path.join(ROOT, "paper_1910_05194_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -117,6 +117,8 @@ typedef struct {
   double step_seconds;  /* device time of the recursion-step launches alone          */
   int64_t step_launches;/* number of recursion-step launches timed in step_seconds   */
   double step_bytes;    /* algorithmic bytes of those launches                       */
+  double gemm_seconds;  /* 2D moments: device time of the tensor-core contraction    */
+  double gemm_flops;    /* 2D moments: tensor flops of the contraction (3 BF16 GEMMs) */
 } kite_stats;
 
 typedef struct kite_ctx kite_ctx;
@@ -170,6 +172,40 @@ int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
  * no wait is unbounded, and the context stays usable.  The hook disarms itself.
  * Errors: KITE_ERR_ARG. */
 int kite_debug_stall_once(kite_ctx* ctx, int enable);
+
+/* ---- 2D moments ----------------------------------------------------------------- */
+
+/* 2D moments of the first-order Kubo-Bastin conductivity sigma_xx (Sec. 2b,
+ * Eqs. cond 1st order, Gammanm, conductivity_1st_order):
+ *   mu_nm = (1/(S R)) sum_{s,r} <r| v T_n(H~) v T_m(H~) |r> / N_eff,   v = -i h~x,
+ * with h~x = [x, H~] applied matrix-free (x in units of the lattice constant a; bond
+ * x-offsets 0, +-a/2 on the honeycomb lattice, +-a on the square lattice).  Computed as
+ * mu_nm = <a_n|b_m> with the stored families a_n = T_n h~x r and b_m = h~x T_m r, and
+ * contracted on the tensor cores (see kite_inner_products).  The paper's tensor is
+ * Gamma^{x,x}_nm = -mu_nm / ((1 + delta_n0)(1 + delta_m0)).
+ *   kpm->precision must be KITE_FP32 (complex FP32 recursion, split-BF16 contraction,
+ *   FP64 sums); kpm->r0 may give start vectors; kpm->r_last is ignored.
+ *   mu_nm  [M][M] complex FP64 interleaved (re, im), row n, column m; host or device.
+ * Work memory: about 24 * M * N bytes per pair of random vectors.
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA, KITE_ERR_TIMEOUT,
+ *         KITE_ERR_UNSUPPORTED (precision other than FP32). */
+int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, double* mu_nm,
+                    kite_stats* st);
+
+/* ---- 2D moments: the contraction primitive ---------------------------------------- */
+
+/* Complex inner products of two vector families, the contraction behind the 2D
+ * Kubo-Bastin moments Gamma_nm = Tr[h T_n h T_m]/N (Sec. 2b, Eq. Gammanm):
+ *   C[n][m] = scale * sum_{i<N} conj(A[n][i]) * B[m][i],   n < M, m < M2.
+ * Runs on the tensor cores (tcgen05.mma): every FP32 input x is split into
+ * bf16 hi = bf16(x) and lo = bf16(x - hi); products keep hi*hi + hi*lo + lo*hi; sums are
+ * FP32 inside a K sub-chunk of `sub_k` products and FP64 above (sub_k = 0: default 2048).
+ *   A  [M][N]  complex FP32 interleaved (re, im), host or device
+ *   B  [M2][N] complex FP32 interleaved, host or device
+ *   C  [M][M2] complex FP64 interleaved, host or device (overwritten)
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA, KITE_ERR_TIMEOUT. */
+int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
+                        double scale, double* C, int sub_k);
 
 /* ---- reconstruction ------------------------------------------------------------- */
 

@@ -24,7 +24,7 @@ KERNEL_NONE, KERNEL_JACKSON, KERNEL_LORENTZ = 0, 1, 2
 
 EXPORTED = ("kite_create", "kite_destroy", "kite_set_stream", "kite_status_string",
             "kite_last_error", "kite_bounds", "kite_moments_1d", "kite_reconstruct_dos",
-            "kite_debug_stall_once")
+            "kite_debug_stall_once", "kite_inner_products", "kite_moments_2d")
 
 
 class KiteError(RuntimeError):
@@ -54,7 +54,8 @@ class Stats(ctypes.Structure):
                 ("max_abs_imag", ctypes.c_double), ("e_min", ctypes.c_double),
                 ("e_max", ctypes.c_double), ("n_eff", ctypes.c_int64), ("grid", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("step_seconds", ctypes.c_double),
-                ("step_launches", ctypes.c_int64), ("step_bytes", ctypes.c_double)]
+                ("step_launches", ctypes.c_int64), ("step_bytes", ctypes.c_double),
+                ("gemm_seconds", ctypes.c_double), ("gemm_flops", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -101,6 +102,10 @@ def lib():
             L.kite_moments_1d.restype = i32
             L.kite_reconstruct_dos.argtypes = [vp, vp, i32, i32, i32, d, d, d, vp, i32, vp]
             L.kite_reconstruct_dos.restype = i32
+            L.kite_moments_2d.argtypes = [vp, P(System), P(KPM), vp, P(Stats)]
+            L.kite_moments_2d.restype = i32
+            L.kite_inner_products.argtypes = [vp, vp, vp, i32, i32, ctypes.c_int64, d, vp, i32]
+            L.kite_inner_products.restype = i32
             L.kite_debug_stall_once.argtypes = [vp, i32]
             L.kite_debug_stall_once.restype = i32
             _LIB = L
@@ -199,3 +204,18 @@ def reconstruct_dos(ctx: Context, mu, M_avail: int, M_use: int, kernel: int, par
 def debug_stall_once(ctx: Context, enable: bool = True):
     """Test hook: the next kite_moments_1d call's first step times out (KITE_ERR_TIMEOUT)."""
     ctx.check(lib().kite_debug_stall_once(ctx.handle, int(bool(enable))))
+
+
+def inner_products(ctx: Context, A, B, M: int, M2: int, N: int, scale: float, C, sub_k: int = 0):
+    """kite_inner_products: C[n][m] = scale * sum_i conj(A[n][i]) B[m][i] (split-BF16
+    tensor cores, FP64 output).  A [M][N], B [M2][N] complex64; C [M][M2] complex128."""
+    ctx.check(lib().kite_inner_products(ctx.handle, _addr(A), _addr(B), int(M), int(M2), int(N),
+                                        float(scale), _addr(C), int(sub_k)))
+
+
+def moments_2d(ctx: Context, system: System, kpm: KPM, mu_nm) -> Stats:
+    """kite_moments_2d: mu_nm[M][M] complex FP64 (host or device)."""
+    st = Stats()
+    ctx.check(lib().kite_moments_2d(ctx.handle, ctypes.byref(system), ctypes.byref(kpm),
+                                    _addr(mu_nm), ctypes.byref(st)))
+    return st

@@ -14,6 +14,10 @@ namespace kite {
 int moments_1d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
                     double* mu_dev, double* imag_dev, double* mu_vec_dev, kite_stats* st,
                     const double* r0_dev_all);
+int moments_2d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
+                    double* mu_nm_dev, kite_stats* st, const double* r0_dev_all);
+int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
+                        double scale, double* C, int sub_kb);
 int reconstruct_dos_impl(kite_ctx* ctx, const double* mu_dev, int M_use, int kernel,
                          double param, const Scale& sc, const double* E_dev, int K,
                          double* rho_dev, double* coef_dev);
@@ -305,6 +309,99 @@ int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   if (r0_stage) cudaFreeAsync(r0_stage, ctx->stream);
   cudaStreamSynchronize(ctx->stream);
   if (st) *st = local;
+  return rc;
+}
+
+int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, double* mu_nm,
+                    kite_stats* st) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  int rc = validate_system(ctx, sys);
+  if (rc != KITE_OK) return rc;
+  if (!kpm || !mu_nm) return fail(ctx, KITE_ERR_ARG, "kpm and mu_nm are required");
+  if (kpm->M < 1 || kpm->R < 1 || kpm->S < 1 || kpm->M > 65536)
+    return fail(ctx, KITE_ERR_ARG, "need 1 <= M <= 65536, R >= 1, S >= 1");
+  if (kpm->precision != KITE_FP32)
+    return fail(ctx, KITE_ERR_UNSUPPORTED, "2D moments run the FP32 recursion only");
+  if ((double)kpm->R * kpm->S > 65536.0) return fail(ctx, KITE_ERR_ARG, "R*S > 65536");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  Scale sc;
+  rc = resolve_bounds(ctx, sys, kpm->e_min, kpm->e_max, &sc);
+  if (rc != KITE_OK) return rc;
+  const int M = kpm->M;
+  const size_t nvec = (size_t)kpm->R * kpm->S;
+  const int64_t N = (int64_t)sys->Lx * sys->Ly * (sys->lattice == KITE_HONEYCOMB ? 2 : 1);
+  const double* r0_dev = nullptr;
+  void* r0_stage = nullptr;
+  if (kpm->r0) {
+    if (is_device_ptr(kpm->r0)) {
+      r0_dev = kpm->r0;
+    } else {
+      const size_t bytes = nvec * (size_t)N * 2 * sizeof(double);
+      KITE_CUDA_TRY(ctx, cudaMallocAsync(&r0_stage, bytes, ctx->stream));
+      KITE_CUDA_TRY(ctx, copy_in(ctx, r0_stage, kpm->r0, bytes));
+      r0_dev = static_cast<const double*>(r0_stage);
+    }
+  }
+  const bool out_d = is_device_ptr(mu_nm);
+  double* out_dev = mu_nm;
+  const size_t out_bytes = sizeof(double) * 2 * (size_t)M * M;
+  if (!out_d) KITE_CUDA_TRY(ctx, cudaMallocAsync((void**)&out_dev, out_bytes, ctx->stream));
+  kite_stats local{};
+  rc = moments_2d_impl(ctx, sys, kpm, sc, out_dev, &local, r0_dev);
+  if (rc == KITE_OK && !out_d) {
+    cudaError_t e = copy_out(ctx, mu_nm, out_dev, out_bytes);
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "copying mu_nm");
+  }
+  if (!out_d) cudaFreeAsync(out_dev, ctx->stream);
+  if (r0_stage) cudaFreeAsync(r0_stage, ctx->stream);
+  cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "moments_2d");
+  local.e_min = sc.e_min;
+  local.e_max = sc.e_max;
+  if (st) *st = local;
+  return rc;
+}
+
+int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
+                        double scale, double* C, int sub_k) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  if (!A || !B || !C || M < 1 || M2 < 1 || N < 1 || sub_k < 0 || !isfinite(scale))
+    return fail(ctx, KITE_ERR_ARG, "need A, B, C, M >= 1, M2 >= 1, N >= 1, sub_k >= 0");
+  if ((double)M * N > 4.0e10 || (double)M2 * N > 4.0e10)
+    return fail(ctx, KITE_ERR_ARG, "families larger than 4e10 complex entries");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  const int sub_kb = sub_k == 0 ? 32 : (sub_k + 63) / 64;
+  const size_t a_bytes = (size_t)M * N * 8, b_bytes = (size_t)M2 * N * 8, c_bytes = (size_t)M * M2 * 16;
+  const bool a_d = is_device_ptr(A), b_d = is_device_ptr(B), c_d = is_device_ptr(C);
+  char* stage = nullptr;
+  const size_t st_bytes = (a_d ? 0 : a_bytes) + (b_d ? 0 : b_bytes) + (c_d ? 0 : c_bytes) + 512;
+  KITE_CUDA_TRY(ctx, cudaMallocAsync((void**)&stage, st_bytes, ctx->stream));
+  size_t off = 0;
+  const float* Ad = A;
+  const float* Bd = B;
+  double* Cd = C;
+  cudaError_t e = cudaSuccess;
+  if (!a_d) { Ad = reinterpret_cast<float*>(stage + off); e = copy_in(ctx, stage + off, A, a_bytes); off += (a_bytes + 255) & ~size_t(255); }
+  if (e == cudaSuccess && !b_d) { Bd = reinterpret_cast<float*>(stage + off); e = copy_in(ctx, stage + off, B, b_bytes); off += (b_bytes + 255) & ~size_t(255); }
+  if (!c_d) Cd = reinterpret_cast<double*>(stage + off);
+  int rc = e == cudaSuccess ? KITE_OK : cuda_fail(ctx, e, "copying A/B");
+  if (rc == KITE_OK) rc = inner_products_impl(ctx, Ad, Bd, M, M2, N, scale, Cd, sub_kb);
+  if (rc == KITE_OK && !c_d) {
+    e = copy_out(ctx, C, Cd, c_bytes);
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "copying C");
+  }
+  int status_host = 0;
+  if (rc == KITE_OK) {
+    e = cudaMemcpyAsync(&status_host, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "status");
+  }
+  cudaFreeAsync(stage, ctx->stream);
+  cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "inner_products");
+  if (rc == KITE_OK && status_host != 0)
+    rc = fail(ctx, KITE_ERR_TIMEOUT, "a bounded wait gave up in the tensor-core contraction");
   return rc;
 }
 

@@ -1,0 +1,511 @@
+// kite_gemm.cu -- complex inner products C[n][m] = sum_k A[n][k] * B[m][k] of
+// split-BF16 operands on the 5th-generation tensor cores (tcgen05.mma with TMEM
+// accumulators, TMA tile loads), FP32 accumulation within a K sub-chunk and FP64 above.
+//
+// The 2D Kubo-Bastin moments (Sec. 2b, Eq. Gammanm) are mu_nm = <a_n|b_m>/N: a complex
+// contraction over all orbitals of two stored Chebyshev vector families.  Written as
+// real GEMMs over K = 2N interleaved (re, im) values:
+//   Re <a|b> = sum (ar br + ai bi)   = A' . B'
+//   Im <a|b> = sum (ar bi - ai br)   = A' . (-i b)'
+// so the B operand holds, for every m, the rows b_m and -i b_m (the "extended" B with
+// 2M rows) and one real GEMM A' B_ext^T gives both parts.  Each FP32 value x is split
+// into hi = bf16(x), lo = bf16(x - hi); the product keeps hi*hi + hi*lo + lo*hi.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "kite_device.cuh"
+#include "kite_internal.h"
+
+namespace kite {
+namespace {
+
+constexpr int kBM = 128;                       // rows of A per tile (UMMA M)
+constexpr int kBN = 256;                       // rows of B per tile (UMMA N)
+constexpr int kBK = 64;                        // K per stage = one 128-byte swizzle row
+constexpr int kUK = 16;                        // K per tcgen05.mma of kind::f16
+constexpr int kGStages = 2;
+constexpr int kATile = kBM * kBK * 2;          // 16 KB
+constexpr int kBTile = kBN * kBK * 2;          // 32 KB
+constexpr int kStageBytes = 2 * kATile + 2 * kBTile;   // A hi, A lo, B hi, B lo
+constexpr int kGemmThreads = 192;              // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kAccCols = kBN;                  // FP32 accumulator columns per buffer
+constexpr int kTmemCols = 2 * kAccCols;        // double-buffered accumulator
+constexpr int kEpiPitch = 33;                  // floats per transposed row (bank-conflict free)
+constexpr int kEpiBytes = 4 * 32 * kEpiPitch * 4;
+constexpr int kGemmSmem = 1024 + kGStages * kStageBytes + kEpiBytes + 256;
+
+// Instruction descriptor of tcgen05.mma kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                            ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+
+// Shared-memory matrix descriptor for a K-major tile written by TMA with 128-byte
+// swizzle: start address >> 4 (bits 0-13), leading byte offset (unused with swizzle,
+// 16 B), stride byte offset = 1024 B between 8-row groups (bits 32-45), descriptor
+// version 1 (bit 46), swizzle mode 2 = 128 B (bits 61-63).
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+// Arrives on `bar` once every tcgen05 operation issued so far by this thread completes.
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 32 lanes x 32 columns of 32-bit accumulator: thread t of the warp gets lane
+// (warp quarter)*32 + t, columns col..col+31.
+__device__ __forceinline__ void tmem_ld_32x32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Bounded wait that also gives up as soon as another role of the CTA has aborted.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
+                                              volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
+struct GemmArgs {
+  int T;            // output tiles = TM * TN
+  int TN;           // tiles along the B rows
+  int S;            // K splits
+  int items;        // S * T
+  int kb_total;     // K blocks of 64
+  int kb_per_item;  // K blocks per split
+  int sub_kb;       // K blocks per FP32 accumulation sub-chunk
+  int Mrows;        // rows of A (valid)
+  int Nrows;        // rows of B (valid) = columns of C
+  double* part;     // [S][Mrows][Nrows] FP64 partial sums
+  int* err;
+};
+
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    k_gemm_split_bf16(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                      const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                      const GemmArgs a) {
+  extern __shared__ unsigned char gsmem_raw[];
+  // 1024-byte aligned operand stages (128-byte swizzle atoms repeat every 1024 bytes)
+  const uint32_t raw = smem_u32(gsmem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gsmem = gsmem_raw + (base - raw);
+  float* epi = reinterpret_cast<float*>(gsmem + kGStages * kStageBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gsmem + kGStages * kStageBytes + kEpiBytes);
+  uint64_t* full = bars;                  // [kGStages] TMA -> MMA
+  uint64_t* empty = bars + kGStages;      // [kGStages] MMA -> TMA
+  uint64_t* tfull = bars + 2 * kGStages;  // [2] MMA -> epilogue
+  uint64_t* tempty = bars + 2 * kGStages + 2;  // [2] epilogue -> MMA
+  uint64_t* drain = bars + 2 * kGStages + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kGStages + 5);
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kGStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 128);
+    }
+    mbar_init(drain, 1);
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  if (warp == 1) {  // the whole warp allocates the accumulator columns
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---- TMA producer
+      int st = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      int pend[kGStages];  // parity of the last phase issued on each stage (-1: none)
+      for (int i = 0; i < kGStages; ++i) pend[i] = -1;
+      for (int item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
+        const int s = item / a.T, t = item - (item / a.T) * a.T;
+        const int tm = t / a.TN, tn = t - (t / a.TN) * a.TN;
+        const int kb0 = s * a.kb_per_item, kb1 = min(a.kb_total, kb0 + a.kb_per_item);
+        for (int kb = kb0; kb < kb1; ++kb) {
+          if (!wait_or_abort(&empty[st], ph ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[st], kStageBytes);
+          const uint32_t sb = base + st * kStageBytes;
+          tma_load_2d(sb, &tmAh, &full[st], kb * kBK, tm * kBM);
+          tma_load_2d(sb + kATile, &tmAl, &full[st], kb * kBK, tm * kBM);
+          tma_load_2d(sb + 2 * kATile, &tmBh, &full[st], kb * kBK, tn * kBN);
+          tma_load_2d(sb + 2 * kATile + kBTile, &tmBl, &full[st], kb * kBK, tn * kBN);
+          pend[st] = (int)ph;
+          if (++st == kGStages) st = 0, ph ^= 1u;
+        }
+      }
+      if (!ok) {
+        // drain: wait (bounded) until the last copies issued on every stage have landed
+        for (int i = 0; i < kGStages; ++i)
+          if (pend[i] >= 0) mbar_wait_bounded(&full[i], (uint32_t)pend[i]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer
+      int st = 0, acc = 0;
+      uint32_t ph = 0, aph = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
+        const int s = item / a.T;
+        const int kb0 = s * a.kb_per_item, kb1 = min(a.kb_total, kb0 + a.kb_per_item);
+        for (int kc = kb0; kc < kb1 && ok; kc += a.sub_kb) {
+          if (!wait_or_abort(&tempty[acc], aph ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(acc * kAccCols);
+          const int kce = min(kb1, kc + a.sub_kb);
+          for (int kb = kc; kb < kce; ++kb) {
+            if (!wait_or_abort(&full[st], ph, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sb = base + st * kStageBytes;
+#pragma unroll
+            for (int kk = 0; kk < kBK / kUK; ++kk) {
+              const uint32_t koff = kk * kUK * 2;  // bytes along the swizzled row
+              const uint64_t ah = desc_sw128(sb + koff);
+              const uint64_t al = desc_sw128(sb + kATile + koff);
+              const uint64_t bh = desc_sw128(sb + 2 * kATile + koff);
+              const uint64_t bl = desc_sw128(sb + 2 * kATile + kBTile + koff);
+              umma_bf16(d, ah, bh, (kb > kc || kk > 0) ? 1u : 0u);
+              umma_bf16(d, ah, bl, 1u);
+              umma_bf16(d, al, bh, 1u);
+            }
+            umma_commit(&empty[st]);  // stage reusable once these MMAs have read it
+            if (++st == kGStages) st = 0, ph ^= 1u;
+          }
+          if (!ok) break;
+          umma_commit(&tfull[acc]);  // accumulator ready for the epilogue
+          if (++acc == 2) acc = 0, aph ^= 1u;
+        }
+      }
+      // make sure no MMA is still writing TMEM before the columns are released
+      umma_commit(drain);
+      const long long t0 = clock64();
+      while (!mbar_try_wait(drain, 0) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+  } else {  // ---- epilogue: warps 2..5 drain the idle accumulator into FP64 partials
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    float* tile = epi + (warp - 2) * 32 * kEpiPitch;
+    int acc = 0;
+    uint32_t aph = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
+      const int s = item / a.T, t = item - (item / a.T) * a.T;
+      const int tm = t / a.TN, tn = t - (t / a.TN) * a.TN;
+      const int kb0 = s * a.kb_per_item, kb1 = min(a.kb_total, kb0 + a.kb_per_item);
+      bool first = true;
+      for (int kc = kb0; kc < kb1; kc += a.sub_kb) {
+        if (!wait_or_abort(&tfull[acc], aph, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int c0 = 0; c0 < kAccCols; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld_32x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols + c0), r);
+          // transpose 32 rows x 32 columns through shared memory for coalesced FP64 RMW
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) tile[lane * kEpiPitch + jj] = __uint_as_float(r[jj]);
+          __syncwarp();
+          const int col = tn * kBN + c0 + lane;
+          for (int rr = 0; rr < 32; ++rr) {
+            const int row = tm * kBM + q * 32 + rr;
+            if (row < a.Mrows && col < a.Nrows) {
+              double* p = a.part + ((size_t)s * a.Mrows + row) * a.Nrows + col;
+              const double v = (double)tile[rr * kEpiPitch + lane];
+              *p = first ? v : *p + v;
+            }
+          }
+          __syncwarp();
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[acc]);
+        first = false;
+        if (++acc == 2) acc = 0, aph ^= 1u;
+      }
+    }
+  }
+
+  __syncthreads();
+  if (s_abort && threadIdx.x == 0) atomicExch(a.err, 1);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Operand preparation and reduction (used by the generic inner-product entry point)
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));  // x - hi is exact in FP32
+}
+
+// rows [rows][N] complex FP32 -> hi/lo [out_rows][Kp] bf16 with K = 2N interleaved
+// (re, im).  rot = 1 writes -i*z = (im, -re) instead of z.  Columns [2N, Kp) are zero.
+__global__ void k_split_rows(const float2* __restrict__ z, int rows, int64_t N, int64_t Kp,
+                             int row_off, int rot, __nv_bfloat16* __restrict__ hi,
+                             __nv_bfloat16* __restrict__ lo) {
+  const int64_t total = (int64_t)rows * (Kp / 2);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / (Kp / 2));
+    const int64_t o = e - (int64_t)r * (Kp / 2);
+    float re = 0.f, im = 0.f;
+    if (o < N) {
+      const float2 v = z[(int64_t)r * N + o];
+      re = rot ? v.y : v.x;
+      im = rot ? -v.x : v.y;
+    }
+    __nv_bfloat16 h0, l0, h1, l1;
+    split_bf16(re, h0, l0);
+    split_bf16(im, h1, l1);
+    const int64_t dst = (int64_t)(row_off + r) * Kp + 2 * o;
+    hi[dst] = h0;
+    hi[dst + 1] = h1;
+    lo[dst] = l0;
+    lo[dst + 1] = l1;
+  }
+}
+
+// C[n][m] (complex FP64) = sum_s part[s][n][m] + i sum_s part[s][n][M2 + m], scaled.
+__global__ void k_reduce_cplx(const double* __restrict__ part, int S, int M, int M2,
+                              double scale, double* __restrict__ out, int accumulate) {
+  const int64_t total = (int64_t)M * M2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(e / M2), m = (int)(e - (e / M2) * M2);
+    const int ldc = 2 * M2;
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < S; ++s) {
+      const double* p = part + ((size_t)s * M + n) * ldc;
+      re += p[m];
+      im += p[M2 + m];
+    }
+    if (accumulate) {
+      out[2 * e] += re * scale;
+      out[2 * e + 1] += im * scale;
+    } else {
+      out[2 * e] = re * scale;
+      out[2 * e + 1] = im * scale;
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode(kite_ctx* ctx) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  (void)ctx;
+  return fn;
+}
+
+int make_map(kite_ctx* ctx, CUtensorMap* m, const void* ptr, int64_t Kp, int rows, int box_rows) {
+  auto enc = get_encode(ctx);
+  if (!enc) return fail(ctx, KITE_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(ctx, KITE_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return KITE_OK;
+}
+
+}  // namespace
+
+// Split-BF16 GEMM over operands already in hi/lo form:
+//   part[s][n][m] for n < Mrows (A rows), m < Nrows (B rows), K = Kp (multiple of 64).
+// Returns the number of splits used in *S_out.  `part` must hold S*Mrows*Nrows doubles;
+// plan_gemm_splits() gives S.
+int plan_gemm_splits(kite_ctx* ctx, int Mrows, int Nrows, int64_t Kp) {
+  const int TM = (Mrows + kBM - 1) / kBM, TN = (Nrows + kBN - 1) / kBN;
+  const int T = TM * TN;
+  const int kb_total = (int)(Kp / kBK);
+  // splits so that items fill whole waves of the persistent grid, at least 2 K blocks each
+  int best = 1;
+  for (int s = 1; s <= std::max(1, kb_total / 2); ++s) {
+    if ((int64_t)s * T > 16LL * ctx->num_sms) break;
+    best = s;
+    if (((int64_t)s * T) % ctx->num_sms == 0 && (int64_t)s * T >= 4LL * ctx->num_sms) break;
+  }
+  return best;
+}
+
+int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void* Bhi,
+                    const void* Blo, int Mrows, int Nrows, int64_t Kp, int S, int sub_kb,
+                    double* part) {
+  if (Kp % kBK != 0) return fail(ctx, KITE_ERR_ARG, "K must be padded to a multiple of 64");
+  CUtensorMap mAh, mAl, mBh, mBl;
+  int rc;
+  if ((rc = make_map(ctx, &mAh, Ahi, Kp, Mrows, kBM)) != KITE_OK) return rc;
+  if ((rc = make_map(ctx, &mAl, Alo, Kp, Mrows, kBM)) != KITE_OK) return rc;
+  if ((rc = make_map(ctx, &mBh, Bhi, Kp, Nrows, kBN)) != KITE_OK) return rc;
+  if ((rc = make_map(ctx, &mBl, Blo, Kp, Nrows, kBN)) != KITE_OK) return rc;
+  GemmArgs a;
+  a.TN = (Nrows + kBN - 1) / kBN;
+  a.T = ((Mrows + kBM - 1) / kBM) * a.TN;
+  a.kb_total = (int)(Kp / kBK);
+  a.S = std::max(1, std::min(S, a.kb_total));
+  a.kb_per_item = (a.kb_total + a.S - 1) / a.S;
+  a.S = (a.kb_total + a.kb_per_item - 1) / a.kb_per_item;
+  a.items = a.S * a.T;
+  a.sub_kb = std::max(1, sub_kb);
+  a.Mrows = Mrows;
+  a.Nrows = Nrows;
+  a.part = part;
+  a.err = ctx->d_status;
+  static bool attr = false;
+  if (!attr) {
+    KITE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_gemm_split_bf16,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
+    attr = true;
+  }
+  const int grid = std::min(a.items, ctx->num_sms);
+  k_gemm_split_bf16<<<grid, kGemmThreads, kGemmSmem, ctx->stream>>>(mAh, mAl, mBh, mBl, a);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  return KITE_OK;
+}
+
+int reduce_cplx(kite_ctx* ctx, const double* part, int S, int M, int M2, double scale,
+                double* out, bool accumulate) {
+  const int64_t total = (int64_t)M * M2;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->num_sms * 8);
+  k_reduce_cplx<<<std::max(1, blocks), 256, 0, ctx->stream>>>(part, S, M, M2, scale, out,
+                                                               accumulate ? 1 : 0);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  return KITE_OK;
+}
+
+// Generic entry: C[n][m] = scale * sum_i conj(A[n][i]) B[m][i], A [M][N], B [M2][N] complex
+// FP32 (device), C [M][M2] complex FP64 (device).
+int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
+                        double scale, double* C, int sub_kb) {
+  const int64_t Kp = ((2 * N + kBK - 1) / kBK) * kBK;
+  const int Nrows = 2 * M2;
+  const int S = plan_gemm_splits(ctx, M, Nrows, Kp);
+  const size_t a_bytes = (size_t)M * Kp * 2, b_bytes = (size_t)Nrows * Kp * 2;
+  const size_t part_n = (size_t)S * M * Nrows;
+  Carver cv(nullptr);
+  cv.take<char>(a_bytes);
+  cv.take<char>(a_bytes);
+  cv.take<char>(b_bytes);
+  cv.take<char>(b_bytes);
+  cv.take<double>(part_n);
+  int rc = ensure_ws(ctx, cv.used());
+  if (rc != KITE_OK) return rc;
+  Carver w(ctx->ws);
+  auto* Ahi = w.take<__nv_bfloat16>((size_t)M * Kp);
+  auto* Alo = w.take<__nv_bfloat16>((size_t)M * Kp);
+  auto* Bhi = w.take<__nv_bfloat16>((size_t)Nrows * Kp);
+  auto* Blo = w.take<__nv_bfloat16>((size_t)Nrows * Kp);
+  double* part = w.take<double>(part_n);
+  const int blocks = ctx->num_sms * 8;
+  // A' = conj-free interleave of a (the conjugation lives in the choice of B rows)
+  k_split_rows<<<blocks, 256, 0, ctx->stream>>>(reinterpret_cast<const float2*>(A), M, N, Kp, 0, 0, Ahi, Alo);
+  k_split_rows<<<blocks, 256, 0, ctx->stream>>>(reinterpret_cast<const float2*>(B), M2, N, Kp, 0, 0, Bhi, Blo);
+  k_split_rows<<<blocks, 256, 0, ctx->stream>>>(reinterpret_cast<const float2*>(B), M2, N, Kp, M2, 1, Bhi, Blo);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  KITE_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+  rc = gemm_split_bf16(ctx, Ahi, Alo, Bhi, Blo, M, Nrows, Kp, S, sub_kb, part);
+  if (rc != KITE_OK) return rc;
+  return reduce_cplx(ctx, part, S, M, M2, scale, C, false);
+}
+
+}  // namespace kite

@@ -1,0 +1,251 @@
+// kite_kpm2d.cu -- 2D Kubo-Bastin moments (Sec. 2b, Eq. Gammanm).
+//
+//   mu_nm = (1/(S R N_eff)) sum_{s,r} <a_n|b_m>,  a_n = T_n(H~) h~x r,  b_m = h~x T_m(H~) r,
+// with h~x = [x, H~] (x in units of the lattice constant).  Because h~x is anti-Hermitian,
+// <r| h~ T_n h~ T_m |r> = -<a_n|b_m>; the paper's Gamma^{x,x}_nm is
+// -mu_nm / ((1 + d_n0)(1 + d_m0)) and mu_nm = <r|v T_n v T_m|r>/N for v = -i h~x.
+//
+// Per batch of (up to) two random vectors: the A family is the recursion started from
+// a_0 = h~x r_0, each step writing its output row in split-BF16 form; the B family is the
+// recursion from r_0, each step writing h~x r_n (from the neighbours it already staged)
+// as the rows b_n and -i b_n.  The tensor-core contraction (kite_gemm.cu) then gives
+// Re and Im of <a_n|b_m> in one real GEMM per vector.
+#include "kite_step.cuh"
+
+namespace kite {
+
+int plan_gemm_splits(kite_ctx* ctx, int Mrows, int Nrows, int64_t Kp);
+int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void* Bhi,
+                    const void* Blo, int Mrows, int Nrows, int64_t Kp, int S, int sub_kb,
+                    double* part);
+int reduce_cplx(kite_ctx* ctx, const double* part, int S, int M, int M2, double scale,
+                double* out, bool accumulate);
+
+namespace {
+
+constexpr int kGemmSubKb = 32;  // 2048 products per FP32 accumulation sub-chunk
+
+// h~x applied to a whole FP32 batch (one chunk = two vectors).  mode 1: writes the
+// result as row `col` of the A family (and to out_vec if given); mode 2: rows `col` and
+// `col + M` of the extended B family.
+template <int LAT>
+__global__ void k_velocity(const float4* __restrict__ in, float4* __restrict__ out_vec,
+                           const float* __restrict__ vt, int Lx, int Ly, int mode, const FamOut fam) {
+  constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
+  const int64_t norb = (int64_t)Lx * Ly * SORB;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < norb;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(o % SORB);
+    const int64_t cell = o / SORB;
+    const int x = (int)(cell % Lx), y = (int)(cell / Lx);
+    const int xm = x == 0 ? Lx - 1 : x - 1, xp = x + 1 == Lx ? 0 : x + 1;
+    const int ym = y == 0 ? Ly - 1 : y - 1, yp = y + 1 == Ly ? 0 : y + 1;
+    float4 v;
+    if (LAT == KITE_HONEYCOMB) {
+      // A: n2 = B(x+1,y-1) (offset -a/2), n3 = B(x,y-1) (+a/2)
+      // B: n2 = A(x-1,y+1) (+a/2), n3 = A(x,y+1) (-a/2)
+      const int so = 1 - s;
+      const int ny = s == 0 ? ym : yp, nx = s == 0 ? xp : xm;
+      const float4 n2 = __ldg(in + ((int64_t)ny * Lx + nx) * 2 + so);
+      const float4 n3 = __ldg(in + ((int64_t)ny * Lx + x) * 2 + so);
+      const float sg = s == 0 ? fam.tvel : -fam.tvel;
+      v = make_float4(sg * (n3.x - n2.x), sg * (n3.y - n2.y), sg * (n3.z - n2.z), sg * (n3.w - n2.w));
+    } else {
+      const float4 n1 = __ldg(in + (int64_t)y * Lx + xm);
+      const float4 n2 = __ldg(in + (int64_t)y * Lx + xp);
+      const float t = fam.tvel;
+      v = make_float4(t * (n1.x - n2.x), t * (n1.y - n2.y), t * (n1.z - n2.z), t * (n1.w - n2.w));
+    }
+    if (vt[o] != vt[o]) v = make_float4(0.f, 0.f, 0.f, 0.f);  // vacancy
+    if (out_vec) out_vec[o] = v;
+    if (mode == 1) {
+      fam_store(fam, 0, fam.col, o, v.x, v.y);
+      fam_store(fam, 1, fam.col, o, v.z, v.w);
+    } else {
+      fam_store(fam, 0, fam.col, o, v.x, v.y);
+      fam_store(fam, 0, fam.col + fam.M, o, v.y, -v.x);
+      fam_store(fam, 1, fam.col, o, v.z, v.w);
+      fam_store(fam, 1, fam.col + fam.M, o, v.w, -v.z);
+    }
+  }
+}
+
+template <int LAT>
+int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
+           double* mu_nm_dev, kite_stats* stats, const double* r0_dev_all) {
+  constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
+  constexpr int C = 1;  // two FP32 vectors per 16-byte chunk
+  using Sh = StepShape<LAT, C>;
+  const int M = kpm->M, R = kpm->R, Sreal = kpm->S;
+  const int64_t ncell = (int64_t)sys->Lx * sys->Ly, N = ncell * SORB;
+  const int64_t Kp = ((2 * N + 63) / 64) * 64;
+  const int VB = 2;
+  const int G = grid_for<float, LAT, C, false>(ctx, (long long)((sys->Lx + Sh::TX - 1) / Sh::TX) * sys->Ly);
+  const long long units = (long long)((sys->Lx + Sh::TX - 1) / Sh::TX) * sys->Ly;
+  const int Sg = plan_gemm_splits(ctx, M, 2 * M, Kp);
+  const size_t vec_bytes = (size_t)ncell * SORB * C * 16;
+  const size_t famA = (size_t)M * Kp, famB = (size_t)2 * M * Kp;  // bf16 elements per array
+
+  auto layout = [&](Carver& k, float** vt, void** r0, void** bA, void** bB,
+                    __nv_bfloat16** Ah, __nv_bfloat16** Al, __nv_bfloat16** Bh,
+                    __nv_bfloat16** Bl, double** part, unsigned long long** ne) {
+    *vt = k.take<float>(N);
+    *r0 = k.take<char>(vec_bytes);
+    *bA = k.take<char>(vec_bytes);
+    *bB = k.take<char>(vec_bytes);
+    for (int v = 0; v < VB; ++v) {
+      Ah[v] = k.take<__nv_bfloat16>(famA);
+      Al[v] = k.take<__nv_bfloat16>(famA);
+      Bh[v] = k.take<__nv_bfloat16>(famB);
+      Bl[v] = k.take<__nv_bfloat16>(famB);
+    }
+    *part = k.take<double>((size_t)Sg * M * 2 * M);
+    *ne = k.take<unsigned long long>(1);
+  };
+  float* vt;
+  void *r0, *bA, *bB;
+  __nv_bfloat16 *Ah[VB], *Al[VB], *Bh[VB], *Bl[VB];
+  double* part;
+  unsigned long long* ne;
+  {
+    Carver probe(nullptr);
+    layout(probe, &vt, &r0, &bA, &bB, Ah, Al, Bh, Bl, &part, &ne);
+    int rc = ensure_ws(ctx, probe.used());
+    if (rc != KITE_OK) return rc;
+  }
+  Carver w(ctx->ws);
+  layout(w, &vt, &r0, &bA, &bB, Ah, Al, Bh, Bl, &part, &ne);
+  cudaStream_t st = ctx->stream;
+  if (Kp > 2 * N) {  // zero the K padding of every family row once
+    for (int v = 0; v < VB; ++v) {
+      const size_t pitch = (size_t)Kp * 2, width = (size_t)(Kp - 2 * N) * 2;
+      KITE_CUDA_TRY(ctx, cudaMemset2DAsync(Ah[v] + 2 * N, pitch, 0, width, M, st));
+      KITE_CUDA_TRY(ctx, cudaMemset2DAsync(Al[v] + 2 * N, pitch, 0, width, M, st));
+      KITE_CUDA_TRY(ctx, cudaMemset2DAsync(Bh[v] + 2 * N, pitch, 0, width, 2 * M, st));
+      KITE_CUDA_TRY(ctx, cudaMemset2DAsync(Bl[v] + 2 * N, pitch, 0, width, 2 * M, st));
+    }
+  }
+  KITE_CUDA_TRY(ctx, cudaMemsetAsync(mu_nm_dev, 0, sizeof(double) * 2 * (size_t)M * M, st));
+  KITE_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+
+  const float tt = (float)(sys->t / sc.de_minus);
+  const float tvel = LAT == KITE_HONEYCOMB ? 0.5f * tt : tt;
+  const double thr_d = floor(sys->p_vac * 4294967296.0);
+  const uint64_t vac_thr =
+      sys->p_vac <= 0.0 ? 0ull : (thr_d >= 4294967296.0 ? 4294967296ull : (uint64_t)thr_d);
+  const uint32_t k0 = (uint32_t)sys->seed, k1 = (uint32_t)(sys->seed >> 32);
+  const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->num_sms * 16);
+  constexpr int SM = Sh::SMEM;
+  cudaFuncSetAttribute(k_step<float, LAT, C, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
+  cudaFuncSetAttribute(k_step<float, LAT, C, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
+  cudaFuncSetAttribute(k_step<float, LAT, C, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
+  cudaFuncSetAttribute(k_step<float, LAT, C, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
+
+  FamOut fa{}, fb{};
+  for (int v = 0; v < VB; ++v) {
+    fa.hi[v] = Ah[v];
+    fa.lo[v] = Al[v];
+    fb.hi[v] = Bh[v];
+    fb.lo[v] = Bl[v];
+  }
+  fa.Kp = fb.Kp = Kp;
+  fa.M = fb.M = M;
+  fa.tvel = fb.tvel = tvel;
+
+  double gemm_s = 0.0, rec_s = 0.0;
+  int64_t n_eff = 0;
+  for (int s = 0; s < Sreal; ++s) {
+    KITE_CUDA_TRY(ctx, cudaMemsetAsync(ne, 0, sizeof(unsigned long long), st));
+    k_onsite<float><<<blocks, 256, 0, st>>>(N, sys->lattice, sys->W, 0.5 * sys->delta, sc.de_plus,
+                                            sc.de_minus, vac_thr, (uint32_t)s, k0, k1, vt, ne);
+    unsigned long long ne_host = 0;
+    KITE_CUDA_TRY(ctx, cudaMemcpyAsync(&ne_host, ne, sizeof(ne_host), cudaMemcpyDeviceToHost, st));
+    KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    n_eff = (int64_t)ne_host;
+    const double scale = n_eff > 0 ? 1.0 / ((double)n_eff * R * Sreal) : 0.0;
+    for (int base = 0; base < R; base += VB) {
+      const int nvec = std::min(VB, R - base);
+      const double* r0_in = r0_dev_all ? r0_dev_all + (size_t)s * R * N * 2 : nullptr;
+      k_init_r0<float, SORB, C><<<blocks, 256, 0, st>>>(ncell, vt, base, nvec, (uint32_t)s * R,
+                                                         k0, k1, r0_in, N, r0);
+      KITE_CUDA_TRY(ctx, cudaGetLastError());
+      KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, st));
+      // A family: a_0 = h~x r_0 (row 0, and the recursion's start vector in bB)
+      fa.col = 0;
+      k_velocity<LAT><<<blocks, 256, 0, st>>>(static_cast<const float4*>(r0),
+                                              static_cast<float4*>(bB), vt, sys->Lx, sys->Ly, 1, fa);
+      auto whereA = [&](int n) -> void* { return (n & 1) ? bA : bB; };
+      for (int n = 0; n + 1 < M; ++n) {
+        fa.col = n + 1;
+        if (n == 0)
+          k_step<float, LAT, C, true, 1><<<G, kBlock, SM, st>>>(
+              nullptr, whereA(0), whereA(1), nullptr, vt, tt, sys->Lx, sys->Ly, units, nullptr,
+              nullptr, ctx->d_status, 0, fa);
+        else
+          k_step<float, LAT, C, false, 1><<<G, kBlock, SM, st>>>(
+              whereA(n - 1), whereA(n), whereA(n + 1), nullptr, vt, tt, sys->Lx, sys->Ly, units,
+              nullptr, nullptr, ctx->d_status, 0, fa);
+      }
+      // B family: recursion from r_0; step n writes b_n = h~x r_n
+      auto whereB = [&](int n) -> void* { return n == 0 ? r0 : ((n & 1) ? bA : bB); };
+      for (int n = 0; n + 1 < M; ++n) {
+        fb.col = n;
+        if (n == 0)
+          k_step<float, LAT, C, true, 2><<<G, kBlock, SM, st>>>(
+              nullptr, whereB(0), whereB(1), nullptr, vt, tt, sys->Lx, sys->Ly, units, nullptr,
+              nullptr, ctx->d_status, 0, fb);
+        else
+          k_step<float, LAT, C, false, 2><<<G, kBlock, SM, st>>>(
+              whereB(n - 1), whereB(n), whereB(n + 1), nullptr, vt, tt, sys->Lx, sys->Ly, units,
+              nullptr, nullptr, ctx->d_status, 0, fb);
+      }
+      fb.col = M - 1;
+      k_velocity<LAT><<<blocks, 256, 0, st>>>(static_cast<const float4*>(whereB(M - 1)), nullptr, vt,
+                                              sys->Lx, sys->Ly, 2, fb);
+      KITE_CUDA_TRY(ctx, cudaGetLastError());
+      KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, st));
+      // contraction, one vector at a time, accumulated in FP64
+      KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
+      for (int v = 0; v < nvec; ++v) {
+        int rc = gemm_split_bf16(ctx, Ah[v], Al[v], Bh[v], Bl[v], M, 2 * M, Kp, Sg, kGemmSubKb, part);
+        if (rc != KITE_OK) return rc;
+        rc = reduce_cplx(ctx, part, Sg, M, M, scale, mu_nm_dev, true);
+        if (rc != KITE_OK) return rc;
+      }
+      KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
+      KITE_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev3));
+      float ms_rec = 0.f, ms_gemm = 0.f;
+      cudaEventElapsedTime(&ms_rec, ctx->ev0, ctx->ev1);
+      cudaEventElapsedTime(&ms_gemm, ctx->ev2, ctx->ev3);
+      rec_s += 1e-3 * ms_rec;
+      gemm_s += 1e-3 * ms_gemm;
+    }
+  }
+  int status_host = 0;
+  KITE_CUDA_TRY(ctx, cudaMemcpyAsync(&status_host, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (status_host != 0) return fail(ctx, KITE_ERR_TIMEOUT, "a bounded wait gave up in the 2D path");
+  if (stats) {
+    stats->seconds = rec_s + gemm_s;
+    stats->step_seconds = rec_s;
+    stats->step_launches = (int64_t)Sreal * ((R + VB - 1) / VB) * 2 * (M > 1 ? M - 1 : 0);
+    stats->gemm_seconds = gemm_s;
+    // three BF16 products of an M x 2M x Kp real GEMM per vector
+    stats->gemm_flops = 3.0 * 2.0 * (double)M * (2.0 * M) * (double)Kp * R * Sreal;
+    stats->updates = (double)n_eff * M * R * Sreal * 2.0;
+    stats->n_eff = n_eff;
+    stats->grid = G;
+    stats->block = kBlock;
+  }
+  return KITE_OK;
+}
+
+}  // namespace
+
+int moments_2d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
+                    double* mu_nm_dev, kite_stats* st, const double* r0_dev_all) {
+  if (sys->lattice == KITE_HONEYCOMB) return run_2d<KITE_HONEYCOMB>(ctx, sys, kpm, sc, mu_nm_dev, st, r0_dev_all);
+  return run_2d<KITE_SQUARE>(ctx, sys, kpm, sc, mu_nm_dev, st, r0_dev_all);
+}
+
+}  // namespace kite

@@ -1,0 +1,447 @@
+// kite_step.cuh -- device kernels of the Chebyshev recursion shared by the 1D (moment)
+// and 2D (vector family) drivers: on-site draws, start vectors, the pipelined stencil
+// step and batch/caller layout conversion.  Everything lives in an anonymous namespace,
+// so each translation unit instantiates its own copies.
+#pragma once
+
+#include <math.h>
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "kite_device.cuh"
+#include "kite_internal.h"
+
+namespace kite {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kFlushRows = 32;  // FP32 moment partials are promoted to FP64 every 32 rows
+
+// ------------------------------------------------------------------------------------
+// On-site energies V~_o = (V_o - de_plus)/de_minus of one realisation, a quiet NaN on
+// vacancies, and the count of non-vacant orbitals.  Same draws and the same sequence
+// of correctly rounded FP64 operations as the problem statement in kite_gb.h.
+// ------------------------------------------------------------------------------------
+template <typename Real>
+__global__ void k_onsite(int64_t N, int lattice, double W, double half_delta, double de_plus,
+                         double de_minus, uint64_t vac_thr, uint32_t realisation, uint32_t k0,
+                         uint32_t k1, Real* __restrict__ vt,
+                         unsigned long long* __restrict__ n_eff) {
+  unsigned int count = 0;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < N;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const Philox4 x = philox4x32_10((uint32_t)o, (uint32_t)((uint64_t)o >> 32), realisation,
+                                    kTagDisorder, k0, k1);
+    double v = __dmul_rn(W, __dsub_rn(u53(x), 0.5));
+    if (lattice == KITE_HONEYCOMB && half_delta != 0.0)
+      v = __dadd_rn(v, (o & 1) == 0 ? half_delta : -half_delta);
+    const bool vacant = (uint64_t)x.w[2] < vac_thr;
+    const double vtil = __ddiv_rn(__dsub_rn(v, de_plus), de_minus);
+    vt[o] = vacant ? quiet_nan<Real>() : (Real)vtil;
+    count += vacant ? 0u : 1u;
+  }
+  // integer sums are order independent: warp-aggregate, one atomic per warp
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) count += __shfl_xor_sync(0xffffffffu, count, d);
+  if ((threadIdx.x & 31) == 0 && count) atomicAdd(n_eff, (unsigned long long)count);
+}
+
+// ------------------------------------------------------------------------------------
+// Start vectors of one batch: random phases exp(2 pi i u) or caller vectors (FP64,
+// rounded once), zero on vacancies and on padding lanes.
+// ------------------------------------------------------------------------------------
+template <typename Real, int SORB, int C>
+__global__ void k_init_r0(int64_t ncell, const Real* __restrict__ vt, int vec_base, int nvec,
+                          uint32_t phase_base, uint32_t k0, uint32_t k1,
+                          const double* __restrict__ r0_in, int64_t N, void* __restrict__ r0) {
+  using Ch = Chunk<Real>;
+  const int64_t nchunk = ncell * SORB * C;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nchunk;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(q % C);
+    const int64_t o = q / C;  // orbital index = cell*SORB + s
+    const bool vacant = isnan((double)vt[o]);
+    Ch out;
+#pragma unroll
+    for (int k = 0; k < Ch::kVecs; ++k) {
+      const int v = c * Ch::kVecs + k;  // lane within the batch
+      double re = 0.0, im = 0.0;
+      if (v < nvec && !vacant) {
+        if (r0_in) {
+          const double* z = r0_in + 2 * ((int64_t)(vec_base + v) * N + o);
+          re = z[0];
+          im = z[1];
+        } else {
+          const Philox4 x = philox4x32_10((uint32_t)o, (uint32_t)((uint64_t)o >> 32),
+                                          phase_base + (uint32_t)(vec_base + v), kTagPhase,
+                                          k0, k1);
+          const double phi = __dmul_rn(6.283185307179586, u53(x));
+          sincos(phi, &im, &re);
+        }
+      }
+      out.v[2 * k] = (Real)re;
+      out.v[2 * k + 1] = (Real)im;
+    }
+    out.st(r0, q);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// One recursion step fused with the moment dot product.
+//
+// Work unit = one row segment of TX cells (TX*threads-per-cell = 256 threads, one
+// 16-byte chunk each).  Each CTA of the persistent grid owns a contiguous range of
+// units ordered strip-major, so it marches down the rows of an x-strip; each row of r_n
+// is fetched from HBM once per strip (plus one halo row per segment end and one halo
+// cell per side) and reused from shared memory by the rows above and below.  Per-site rounding sequence (shared with the oracle's replica):
+//   s = (nb1 + nb2) + nb3 [+ nb4];  h = fma(t~, s, V~ * r);
+//   first step: out = h;  otherwise out = fma(2, h, -r_prev);  vacancy: out = 0.
+// Honeycomb neighbours: A(x,y) <- B(x,y), B(x+1,y-1), B(x,y-1);
+//                       B(x,y) <- A(x,y), A(x-1,y+1), A(x,y+1)  (Listing 1 bonds).
+// Square neighbours: (x-1,y), (x+1,y), (x,y-1), (x,y+1).
+// ------------------------------------------------------------------------------------
+template <typename Real>
+struct AccT {
+  using T = float;
+};
+template <>
+struct AccT<double> {
+  using T = double;
+};
+
+// Shared-memory ring: kStages slots, each one row segment of the strip.  A slot holds
+// r_n of the row with one halo cell on either side (the periodic neighbours x0-1 and
+// x0+TX), and for interior rows also r_{n-1} and r_0 of the row.  Computing row y needs
+// the slots of rows y-1, y, y+1; the copy of row y+kStages-1 is issued as soon as row
+// y-1's slot is free, so ~6 rows (~75 KB per CTA) are always in flight.
+constexpr int kStages = 8;
+constexpr int kBarBytes = 128;
+
+template <int LAT, int C>
+struct StepShape {
+  static constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
+  static constexpr int TPC = SORB * C;              // threads per cell
+  static constexpr int TX = kBlock / TPC;           // cells per row segment
+  static constexpr int CELLB = SORB * C * 16;       // bytes of one cell of the batch
+  static constexpr int ROWB = TX * CELLB;           // bytes of one row segment (4096)
+  static constexpr int CURB = (TX + 2) * CELLB;     // r_n row segment with halo cells
+  static constexpr int STAGEB = CURB + 2 * ROWB;    // + r_{n-1} and r_0
+  static constexpr int SMEM = kBarBytes + kStages * STAGEB;
+};
+
+// Vector-family outputs of a step (2D moments, Sec. 2b): per vector of the batch, rows of
+// Kp bf16 values (hi = bf16(x), lo = bf16(x - hi)) holding interleaved (re, im) per
+// orbital.  MODE 1 writes the step's output r_{n+1} as row `col` of the A family;
+// MODE 2 writes h~x r_n, built from the neighbours already staged for the step, as
+// rows `col` (b) and `col + M` (-i b) of the extended B family.
+constexpr int kMaxFamVecs = 2;
+struct FamOut {
+  __nv_bfloat16* hi[kMaxFamVecs];
+  __nv_bfloat16* lo[kMaxFamVecs];
+  int64_t Kp;
+  int col;
+  int M;
+  float tvel;  // t~ times the bond x-offset unit: t~/2 (honeycomb), t~ (square)
+};
+
+__device__ __forceinline__ void fam_store(const FamOut& f, int v, int row, int64_t o, float re,
+                                          float im) {
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(re), h1 = __float2bfloat16_rn(im);
+  const __nv_bfloat16 l0 = __float2bfloat16_rn(re - __bfloat162float(h0));
+  const __nv_bfloat16 l1 = __float2bfloat16_rn(im - __bfloat162float(h1));
+  const int64_t idx = (int64_t)row * f.Kp + 2 * o;
+  *reinterpret_cast<__nv_bfloat162*>(f.hi[v] + idx) = __halves2bfloat162(h0, h1);
+  *reinterpret_cast<__nv_bfloat162*>(f.lo[v] + idx) = __halves2bfloat162(l0, l1);
+}
+
+// CTA reduction of the per-thread moment partials in fixed order (the ring is drained, so
+// its memory is reused): lane (vector v = c*VPC + q, component) sums the threads holding
+// chunk c, in thread order.
+template <int QT, int C, typename Acc>
+__device__ __forceinline__ void moment_partials(double (&dacc)[QT], Acc (&facc)[QT],
+                                                double (&dacc0)[QT], Acc (&facc0)[QT], bool first,
+                                                unsigned char* stages, double* partial,
+                                                double* partial0) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < QT; ++k) {
+    dacc[k] += (double)facc[k];
+    if (first) dacc0[k] += (double)facc0[k];
+  }
+
+  double(*red)[QT] = reinterpret_cast<double(*)[QT]>(stages);
+  constexpr int Q = C * QT;
+#pragma unroll
+  for (int k = 0; k < QT; ++k) red[tid][k] = dacc[k];
+  __syncthreads();
+  if (tid < Q) {
+    const int cc = tid / QT, k = tid - (tid / QT) * QT;
+    double sum = 0.0;
+    for (int t = cc; t < kBlock; t += C) sum += red[t][k];
+    partial[(size_t)blockIdx.x * Q + tid] = sum;
+  }
+  if (first) {
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < QT; ++k) red[tid][k] = dacc0[k];
+    __syncthreads();
+    if (tid < Q) {
+      const int cc = tid / QT, k = tid - (tid / QT) * QT;
+      double sum = 0.0;
+      for (int t = cc; t < kBlock; t += C) sum += red[t][k];
+      partial0[(size_t)blockIdx.x * Q + tid] = sum;
+    }
+  }
+}
+
+
+template <typename Real, int LAT, int C, bool FIRST, int MODE = 0>
+__global__ void __launch_bounds__(kBlock, 2)
+    k_step(const void* r_prev, const void* __restrict__ r_cur, void* r_out,
+           const void* __restrict__ r0, const Real* __restrict__ vt, Real tt, int Lx, int Ly,
+           long long units, double* __restrict__ partial, double* __restrict__ partial0,
+           int* __restrict__ err, int stall, const FamOut fam) {
+  static_assert(MODE == 0 || (sizeof(Real) == 4 && C * 2 <= kMaxFamVecs),
+                "family modes run on FP32 batches of at most two vectors");
+  using Ch = Chunk<Real>;
+  using Acc = typename AccT<Real>::T;
+  using Sh = StepShape<LAT, C>;
+  constexpr int VPC = Ch::kVecs, NR = Ch::kReals;
+  constexpr int SORB = Sh::SORB, TPC = Sh::TPC, TX = Sh::TX, CELLB = Sh::CELLB;
+  constexpr int QT = 2 * VPC;  // (re, im) per vector held by one thread
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  unsigned char* stages = smem + kBarBytes;
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x;
+  const int xl = tid / TPC;
+  const int j = tid - xl * TPC;
+  const int s = j / C;
+  const int c = j - s * C;
+  const int choff = (s * C + c) * 16;             // this thread's chunk inside a cell
+  const int nboff = ((1 - s) * C + c) * 16;       // same chunk, other sublattice
+
+  if (tid == 0) {
+    for (int k = 0; k < kStages; ++k) mbar_init(&bars[k], 1);
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+
+  const long long u0 = units * (long long)blockIdx.x / gridDim.x;
+  const long long u1 = units * (long long)(blockIdx.x + 1) / gridDim.x;
+
+  double dacc[QT], dacc0[QT];
+  Acc facc[QT], facc0[QT];
+#pragma unroll
+  for (int k = 0; k < QT; ++k) dacc[k] = dacc0[k] = 0.0, facc[k] = facc0[k] = Acc(0);
+  int rows = 0;
+  long long gslot = 0;  // slots consumed so far (phase bookkeeping of the ring)
+  bool aborted = false;
+
+  for (long long u = u0; u < u1 && !aborted;) {
+    // one segment = consecutive rows of one x-strip
+    const int sx = (int)(u / Ly);
+    const int yb = (int)(u - (long long)sx * Ly);
+    const int nr = (int)min(u1 - u, (long long)(Ly - yb));
+    const int x0 = sx * TX;
+    const int txv = min(TX, Lx - x0);
+    const int xlh = (x0 == 0) ? Lx - 1 : x0 - 1;
+    const int xrh = (x0 + txv == Lx) ? 0 : x0 + txv;
+    const int nslots = nr + 2;
+
+    auto issue = [&](int jj) {  // producer: thread 0 only
+      const long long g = gslot + jj;
+      const int st = (int)(g % kStages);
+      unsigned char* base = stages + st * Sh::STAGEB;
+      int row = yb - 1 + jj;
+      row = row < 0 ? row + Ly : (row >= Ly ? row - Ly : row);
+      const bool interior = !FIRST && jj >= 1 && jj <= nr;
+      const uint32_t main_b = (uint32_t)txv * CELLB;
+      // r_0 is only staged when moments are accumulated (MODE 0)
+      uint32_t bytes = main_b + 2 * CELLB + (interior ? (MODE == 0 ? 2 : 1) * main_b : 0);
+      if (stall && blockIdx.x == 0 && g == 0) bytes += 16;  // test hook: never completes
+      mbar_arrive_expect_tx(&bars[st], bytes);
+      const unsigned char* rowp = static_cast<const unsigned char*>(r_cur) + (size_t)row * Lx * CELLB;
+      bulk_g2s(base + CELLB, rowp + (size_t)x0 * CELLB, main_b, &bars[st]);
+      bulk_g2s(base, rowp + (size_t)xlh * CELLB, CELLB, &bars[st]);
+      bulk_g2s(base + (size_t)(txv + 1) * CELLB, rowp + (size_t)xrh * CELLB, CELLB, &bars[st]);
+      if (interior) {
+        const size_t off = ((size_t)row * Lx + x0) * CELLB;
+        bulk_g2s(base + Sh::CURB, static_cast<const unsigned char*>(r_prev) + off, main_b, &bars[st]);
+        if (MODE == 0)
+          bulk_g2s(base + Sh::CURB + Sh::ROWB, static_cast<const unsigned char*>(r0) + off, main_b,
+                   &bars[st]);
+      }
+    };
+    if (tid == 0)
+      for (int jj = 0; jj < min(kStages, nslots); ++jj) issue(jj);
+
+    const bool active = xl < txv;
+    Real vnext = active ? vt[((size_t)yb * Lx + x0 + xl) * SORB + s] : Real(0);
+    int i = 0;
+    for (; i < nr; ++i) {
+      bool ok = true;
+      for (int jj = (i == 0 ? 0 : i + 2); jj <= i + 2; ++jj) {
+        const long long g = gslot + jj;
+        ok = mbar_wait_bounded(&bars[g % kStages], (uint32_t)((g / kStages) & 1)) && ok;
+      }
+      if (!ok) s_abort = 1;
+      const int y = yb + i;
+      const Real v = vnext;
+      if (active && i + 1 < nr) vnext = vt[((size_t)(y + 1) * Lx + x0 + xl) * SORB + s];
+      if (ok && active) {
+        const unsigned char* up = stages + (int)((gslot + i) % kStages) * Sh::STAGEB;
+        const unsigned char* mid = stages + (int)((gslot + i + 1) % kStages) * Sh::STAGEB;
+        const unsigned char* dn = stages + (int)((gslot + i + 2) % kStages) * Sh::STAGEB;
+        const Ch me = *reinterpret_cast<const Ch*>(mid + (xl + 1) * CELLB + choff);
+        Ch n1, n2, n3, n4;
+        if (LAT == KITE_HONEYCOMB) {
+          // A(x,y) <- B(x,y), B(x+1,y-1), B(x,y-1);  B(x,y) <- A(x,y), A(x-1,y+1), A(x,y+1)
+          const unsigned char* other = s == 0 ? up : dn;
+          const int dxi = s == 0 ? xl + 2 : xl;
+          n1 = *reinterpret_cast<const Ch*>(mid + (xl + 1) * CELLB + nboff);
+          n2 = *reinterpret_cast<const Ch*>(other + dxi * CELLB + nboff);
+          n3 = *reinterpret_cast<const Ch*>(other + (xl + 1) * CELLB + nboff);
+        } else {
+          n1 = *reinterpret_cast<const Ch*>(mid + xl * CELLB + choff);
+          n2 = *reinterpret_cast<const Ch*>(mid + (xl + 2) * CELLB + choff);
+          n3 = *reinterpret_cast<const Ch*>(up + (xl + 1) * CELLB + choff);
+          n4 = *reinterpret_cast<const Ch*>(dn + (xl + 1) * CELLB + choff);
+        }
+        Ch pv, z0;
+        if (FIRST) {
+          z0 = me;
+        } else {
+          pv = *reinterpret_cast<const Ch*>(mid + Sh::CURB + xl * CELLB + choff);
+          if (MODE == 0)
+            z0 = *reinterpret_cast<const Ch*>(mid + Sh::CURB + Sh::ROWB + xl * CELLB + choff);
+        }
+        const bool vacant = v != v;
+        Ch out;
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+          Real sum = radd(n1.v[k], n2.v[k]);
+          sum = radd(sum, n3.v[k]);
+          if (LAT == KITE_SQUARE) sum = radd(sum, n4.v[k]);
+          const Real h = rfma(tt, sum, rmul(v, me.v[k]));
+          const Real o = FIRST ? h : rfma(Real(2), h, -pv.v[k]);
+          out.v[k] = vacant ? Real(0) : o;
+        }
+        out.st(r_out, (((size_t)y * Lx + x0 + xl) * SORB + s) * C + c);
+        if constexpr (MODE != 0) {
+          const int64_t o = ((int64_t)y * Lx + x0 + xl) * SORB + s;
+#pragma unroll
+          for (int q = 0; q < VPC; ++q) {
+            const int vv = c * VPC + q;
+            if constexpr (MODE == 1) {
+              fam_store(fam, vv, fam.col, o, out.v[2 * q], out.v[2 * q + 1]);
+            } else {
+              // h~x r at this orbital: bond x-offsets 0, -a/2, +a/2 (A) and 0, +a/2, -a/2 (B)
+              // for the neighbours n1, n2, n3; -a and +a for (x-1), (x+1) on the square lattice
+              float vr, vi;
+              if (LAT == KITE_HONEYCOMB) {
+                const float sg = s == 0 ? fam.tvel : -fam.tvel;
+                vr = sg * (n3.v[2 * q] - n2.v[2 * q]);
+                vi = sg * (n3.v[2 * q + 1] - n2.v[2 * q + 1]);
+              } else {
+                vr = fam.tvel * (n1.v[2 * q] - n2.v[2 * q]);
+                vi = fam.tvel * (n1.v[2 * q + 1] - n2.v[2 * q + 1]);
+              }
+              if (vacant) vr = vi = 0.f;
+              fam_store(fam, vv, fam.col, o, vr, vi);
+              fam_store(fam, vv, fam.col + fam.M, o, vi, -vr);
+            }
+          }
+        } else {  // MODE 0: fused moment <r_0|r_{n+1}> (and <r_0|r_0> on the first step)
+#pragma unroll
+          for (int q = 0; q < VPC; ++q) {
+            const Acc ar = z0.v[2 * q], ai = z0.v[2 * q + 1];
+            const Acc br = out.v[2 * q], bi = out.v[2 * q + 1];
+            facc[2 * q] += ar * br + ai * bi;
+            facc[2 * q + 1] += ar * bi - ai * br;
+            if (FIRST) facc0[2 * q] += ar * ar + ai * ai;
+          }
+          if (++rows == kFlushRows) {
+            rows = 0;
+#pragma unroll
+            for (int k = 0; k < QT; ++k) {
+              dacc[k] += (double)facc[k];
+              facc[k] = Acc(0);
+              if (FIRST) dacc0[k] += (double)facc0[k], facc0[k] = Acc(0);
+            }
+          }
+        }
+      }
+      __syncthreads();  // every thread is done with slot i
+      if (s_abort) {
+        aborted = true;
+        break;
+      }
+      if (tid == 0 && i + kStages < nslots) issue(i + kStages);
+    }
+    if (aborted) {
+      // drain: wait (bounded) for this CTA's copies still in flight, then give up
+      if (tid == 0) {
+        const int last = min(nslots, i + kStages) - 1;
+        for (int jj = i; jj <= last; ++jj) {  // completed phases return at once
+          const long long g = gslot + jj;
+          mbar_wait_bounded(&bars[g % kStages], (uint32_t)((g / kStages) & 1));
+        }
+        atomicExch(err, 1);
+      }
+      return;
+    }
+    gslot += nslots;
+    u += nr;
+  }
+  if constexpr (MODE == 0) moment_partials<QT, C>(dacc, facc, dacc0, facc0, FIRST, stages, partial, partial0);
+}
+
+// Copies one iterate buffer (batch layout) into the caller layout [vec][slot][N].
+template <typename Real, int SORB, int C>
+__global__ void k_extract(int64_t ncell, const void* __restrict__ buf, int nvec, int vec_base,
+                          int slot, int64_t N, Real* __restrict__ dst) {
+  using Ch = Chunk<Real>;
+  const int64_t nchunk = ncell * SORB * C;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nchunk;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(q % C);
+    const int64_t o = q / C;
+    const Ch z = Ch::ldg(buf, q);
+#pragma unroll
+    for (int k = 0; k < Ch::kVecs; ++k) {
+      const int v = c * Ch::kVecs + k;
+      if (v >= nvec) continue;
+      Real* d = dst + 2 * (((int64_t)(vec_base + v) * 2 + slot) * N + o);
+      d[0] = z.v[2 * k];
+      d[1] = z.v[2 * k + 1];
+    }
+  }
+}
+
+
+template <typename Real, int LAT, int C, bool FIRST>
+int grid_for(kite_ctx* ctx, long long units) {
+  static int occ = -1;  // per template instance; device-independent enough for one GPU type
+  if (occ < 0) {
+    int o = 0;
+    const int smem = StepShape<LAT, C>::SMEM;
+    cudaFuncSetAttribute(k_step<Real, LAT, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_step<Real, LAT, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_step<Real, LAT, C, FIRST>, kBlock, smem) !=
+            cudaSuccess ||
+        o < 1)
+      o = 1;
+    occ = o;
+  }
+  long long g = (long long)ctx->num_sms * occ;
+  return (int)std::max(1LL, std::min(g, units));
+}
+
+
+}  // namespace
+}  // namespace kite
