@@ -243,6 +243,7 @@ def main():
     E = torch.linspace(e_min, e_max, K + 2, dtype=torch.float64, device="cuda")[1:-1].contiguous()
     mu = torch.zeros(M, dtype=torch.float64, device="cuda")
     rho = torch.zeros(K, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()  # the context's stream does not wait on torch's stream
 
     def step():
         st = kite.moments_1d(ctx, system, kpm, mu)
@@ -302,6 +303,7 @@ def main():
         E_h = E.cpu().pin_memory()
         rho_h = torch.zeros(K, dtype=torch.float64).pin_memory()
         kpm_h = kite.make_kpm(M, R, 1, kite.FP32, r0=r0_host)
+        torch.cuda.synchronize()
 
         def e2e_step():
             kite.moments_1d(ctx, system, kpm_h, mu_h)

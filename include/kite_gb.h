@@ -9,7 +9,9 @@
  * (grown on demand inside the context, released by kite_destroy).
  *
  * Calls are ordered on the context's stream and return after their results are
- * complete and visible in the caller's buffers.  Every call returns KITE_OK (0) or a
+ * complete and visible in the caller's buffers.  Device inputs produced on another
+ * stream must be complete before the call (bind the context to that stream, or
+ * synchronise): the library does not wait on streams it does not own.  Every call returns KITE_OK (0) or a
  * negative status; on failure no output buffer holds a trusted result, and
  * kite_last_error() gives a one-line reason.  Nothing in the library aborts or exits.
  *
@@ -126,7 +128,8 @@ typedef struct kite_ctx kite_ctx;
 /* ---- context -------------------------------------------------------------------- */
 
 /* Creates a context on CUDA device `device`, bound to `cuda_stream` (a cudaStream_t;
- * NULL creates a private non-blocking stream).  *out receives the handle.
+ * NULL creates a private stream that is ordered with the legacy default stream, so work
+ * the caller queued there completes first).  *out receives the handle.
  * Errors: KITE_ERR_ARG (out NULL, bad device), KITE_ERR_CUDA. */
 int kite_create(kite_ctx** out, int device, void* cuda_stream);
 
@@ -198,14 +201,17 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
  * Kubo-Bastin moments Gamma_nm = Tr[h T_n h T_m]/N (Sec. 2b, Eq. Gammanm):
  *   C[n][m] = scale * sum_{i<N} conj(A[n][i]) * B[m][i],   n < M, m < M2.
  * Runs on the tensor cores (tcgen05.mma): every FP32 input x is split into
- * bf16 hi = bf16(x) and lo = bf16(x - hi); products keep hi*hi + hi*lo + lo*hi; sums are
- * FP32 inside a K sub-chunk of `sub_k` products and FP64 above (sub_k = 0: default 2048).
+ * bf16 hi = bf16(x) and lo = bf16(x - hi); products keep hi*hi + hi*lo + lo*hi
+ * (`products` = 3) or also lo*lo (`products` = 4 or 0, the default); sums are FP32 inside
+ * a K sub-chunk of `sub_k` products and FP64 above (sub_k = 0: default 1024).
  *   A  [M][N]  complex FP32 interleaved (re, im), host or device
  *   B  [M2][N] complex FP32 interleaved, host or device
  *   C  [M][M2] complex FP64 interleaved, host or device (overwritten)
+ * Device buffers are read and written on the context's stream: order any producer on
+ * another stream before the call (e.g. bind the context to that stream).
  * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA, KITE_ERR_TIMEOUT. */
 int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
-                        double scale, double* C, int sub_k);
+                        double scale, double* C, int sub_k, int products);
 
 /* ---- reconstruction ------------------------------------------------------------- */
 
@@ -222,6 +228,30 @@ int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, in
 int kite_reconstruct_dos(kite_ctx* ctx, const double* mu, int M_avail, int M_use, int kernel,
                          double param, double e_min, double e_max, const double* E, int K,
                          double* rho);
+
+/* First-order optical conductivity sigma_xx(omega) in units of e^2/hbar from the 2D
+ * moments of kite_moments_2d (Sec. 2b, Eqs. Gammanm and conductivity_1st_order, in
+ * rescaled units w = hbar omega / de_minus, eta in eV):
+ *   Gamma_nm = -g_n g_m mu_nm / ((1 + d_n0)(1 + d_m0)),
+ *   Lambda_nm(w) = int de f(e) [g^R_n(e + w) Delta_m(e) + Delta_n(e) g^A_m(e - w)],
+ *   sigma(w) = -i (n_orb a^2 / Omega_c) / w * sum_nm Lambda_nm(w) Gamma_nm,
+ * with the CPGF coefficients g^{R/A}_n of Eq. green_function_cheb_expansionb and the
+ * Fermi-sea integral done by Gauss-Legendre quadrature in theta (e = cos theta) with
+ * n_quad nodes (0: 2 M_use + 64).  kT = 0 integrates [E_min, E_F]; kT > 0 (eV) weights the
+ * whole band by the Fermi function.  n_orb a^2/Omega_c = 4/sqrt(3) (honeycomb), 1 (square).
+ * The diamagnetic term sum_n Lambda_n Gamma^xx_n (purely imaginary for omega > 0) is not
+ * included: Re sigma is complete, Im sigma lacks it.  kernel = KITE_KERNEL_JACKSON damps
+ * both indices (use with eta -> 0, the KPM Kubo-Bastin form); KITE_KERNEL_NONE with
+ * eta > 0 is the CPGF form.  All arithmetic FP64 on the GPU.
+ *   mu_nm  [M_avail][M_avail] complex FP64, host or device; the leading M_use x M_use
+ *          block is used
+ *   omega  [K] photon energies hbar*omega (eV, > 0), host or device
+ *   sigma  [K] complex FP64 output, host or device
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
+int kite_reconstruct_sigma(kite_ctx* ctx, const double* mu_nm, int M_avail, int M_use,
+                           int lattice, int kernel, double e_min, double e_max, double E_F,
+                           double kT, double eta, const double* omega, int K, int n_quad,
+                           double* sigma);
 
 #ifdef __cplusplus
 }

@@ -293,7 +293,7 @@ def unit_cell_factor(lattice: int):
 
 
 def sigma_xx(mu_nm, omega, e_min: float, e_max: float, E_F: float, eta: float, lattice: int,
-             kernel: str = "jackson", n_quad: int = 0, gamma_n=None):
+             kernel: str = "jackson", n_quad: int = 0, gamma_n=None, kT: float = 0.0):
     """First-order optical conductivity sigma_xx(omega) in units of e^2/hbar (T = 0),
     from the 2D moments mu_nm = <r|v T_n v T_m|r>/N, v = -i h~x (Sec. 2b):
 
@@ -303,7 +303,8 @@ def sigma_xx(mu_nm, omega, e_min: float, e_max: float, E_F: float, eta: float, l
                                                   (Eq. conductivity_1st_order, rescaled)
     with w = hbar omega / de_minus, eta in eV, Delta_m(e) de = (2/pi) cos(m theta) d theta
     for e = cos theta, and the Fermi-sea integral by Gauss-Legendre quadrature in theta
-    (numpy.polynomial.legendre.leggauss).  kernel: "jackson" damps Gamma by g_n g_m;
+    (numpy.polynomial.legendre.leggauss); kT > 0 (eV) integrates the whole band weighted
+    by the Fermi function.  kernel: "jackson" damps Gamma by g_n g_m;
     None leaves it undamped.  gamma_n (optional) = Gamma^xx_n for the diamagnetic term."""
     mu = np.asarray(mu_nm, np.complex128)
     M = mu.shape[0]
@@ -314,12 +315,16 @@ def sigma_xx(mu_nm, omega, e_min: float, e_max: float, E_F: float, eta: float, l
         g = kernel_jackson(M)
         G = G * g[:, None] * g[None, :]
     eF = (E_F - dp) / dm
-    thF = np.arccos(np.clip(eF, -1.0, 1.0))
+    # T = 0: Fermi sea [-1, eps_F] (theta in [theta_F, pi]); T > 0: the whole band with the
+    # Fermi function f(E) = 1/(1 + exp((E - E_F)/kT)) as a weight
+    thF = np.arccos(np.clip(eF, -1.0, 1.0)) if kT <= 0.0 else 0.0
     K = n_quad if n_quad > 0 else 2 * M + 64
     x, wq = np.polynomial.legendre.leggauss(K)
     theta = thF + (np.pi - thF) * 0.5 * (x + 1.0)
     wq = wq * 0.5 * (np.pi - thF)
     eps = np.cos(theta)
+    if kT > 0.0:
+        wq = wq / (1.0 + np.exp((eps * dm + dp - E_F) / kT))
     D = (2.0 / np.pi) * np.cos(np.arange(M)[:, None] * theta[None, :]) * wq[None, :]  # Delta_m de
     eta_t = eta / dm
     U = G @ D        # sum_m Gamma_nm Delta_m(e_k) de_k

@@ -24,7 +24,8 @@ KERNEL_NONE, KERNEL_JACKSON, KERNEL_LORENTZ = 0, 1, 2
 
 EXPORTED = ("kite_create", "kite_destroy", "kite_set_stream", "kite_status_string",
             "kite_last_error", "kite_bounds", "kite_moments_1d", "kite_reconstruct_dos",
-            "kite_debug_stall_once", "kite_inner_products", "kite_moments_2d")
+            "kite_debug_stall_once", "kite_inner_products", "kite_moments_2d",
+            "kite_reconstruct_sigma")
 
 
 class KiteError(RuntimeError):
@@ -102,9 +103,12 @@ def lib():
             L.kite_moments_1d.restype = i32
             L.kite_reconstruct_dos.argtypes = [vp, vp, i32, i32, i32, d, d, d, vp, i32, vp]
             L.kite_reconstruct_dos.restype = i32
+            L.kite_reconstruct_sigma.argtypes = [vp, vp, i32, i32, i32, i32, d, d, d, d, d, vp,
+                                                 i32, i32, vp]
+            L.kite_reconstruct_sigma.restype = i32
             L.kite_moments_2d.argtypes = [vp, P(System), P(KPM), vp, P(Stats)]
             L.kite_moments_2d.restype = i32
-            L.kite_inner_products.argtypes = [vp, vp, vp, i32, i32, ctypes.c_int64, d, vp, i32]
+            L.kite_inner_products.argtypes = [vp, vp, vp, i32, i32, ctypes.c_int64, d, vp, i32, i32]
             L.kite_inner_products.restype = i32
             L.kite_debug_stall_once.argtypes = [vp, i32]
             L.kite_debug_stall_once.restype = i32
@@ -206,11 +210,12 @@ def debug_stall_once(ctx: Context, enable: bool = True):
     ctx.check(lib().kite_debug_stall_once(ctx.handle, int(bool(enable))))
 
 
-def inner_products(ctx: Context, A, B, M: int, M2: int, N: int, scale: float, C, sub_k: int = 0):
+def inner_products(ctx: Context, A, B, M: int, M2: int, N: int, scale: float, C, sub_k: int = 0,
+                   products: int = 0):
     """kite_inner_products: C[n][m] = scale * sum_i conj(A[n][i]) B[m][i] (split-BF16
     tensor cores, FP64 output).  A [M][N], B [M2][N] complex64; C [M][M2] complex128."""
     ctx.check(lib().kite_inner_products(ctx.handle, _addr(A), _addr(B), int(M), int(M2), int(N),
-                                        float(scale), _addr(C), int(sub_k)))
+                                        float(scale), _addr(C), int(sub_k), int(products)))
 
 
 def moments_2d(ctx: Context, system: System, kpm: KPM, mu_nm) -> Stats:
@@ -219,3 +224,13 @@ def moments_2d(ctx: Context, system: System, kpm: KPM, mu_nm) -> Stats:
     ctx.check(lib().kite_moments_2d(ctx.handle, ctypes.byref(system), ctypes.byref(kpm),
                                     _addr(mu_nm), ctypes.byref(st)))
     return st
+
+
+def reconstruct_sigma(ctx: Context, mu_nm, M_avail: int, M_use: int, lattice: int, kernel: int,
+                      e_min: float, e_max: float, E_F: float, kT: float, eta: float, omega,
+                      K: int, sigma, n_quad: int = 0):
+    """kite_reconstruct_sigma: sigma_xx[K] (complex FP64, units e^2/hbar) from mu_nm."""
+    ctx.check(lib().kite_reconstruct_sigma(ctx.handle, _addr(mu_nm), int(M_avail), int(M_use),
+                                           int(lattice), int(kernel), float(e_min), float(e_max),
+                                           float(E_F), float(kT), float(eta), _addr(omega), int(K),
+                                           int(n_quad), _addr(sigma)))

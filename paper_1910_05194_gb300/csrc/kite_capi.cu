@@ -17,7 +17,10 @@ int moments_1d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
 int moments_2d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
                     double* mu_nm_dev, kite_stats* st, const double* r0_dev_all);
 int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
-                        double scale, double* C, int sub_kb);
+                        double scale, double* C, int sub_kb, int nprod);
+int reconstruct_sigma_impl(kite_ctx* ctx, const double* mu_dev, int M_avail, int M, int lattice,
+                           int kernel, const Scale& sc, double E_F, double kT, double eta,
+                           const double* omega_host, int K_w, int n_quad, double* sigma_dev);
 int reconstruct_dos_impl(kite_ctx* ctx, const double* mu_dev, int M_use, int kernel,
                          double param, const Scale& sc, const double* E_dev, int K,
                          double* rho_dev, double* coef_dev);
@@ -163,7 +166,8 @@ int kite_create(kite_ctx** out, int device, void* cuda_stream) {
   if (cuda_stream) {
     c->stream = static_cast<cudaStream_t>(cuda_stream);
   } else {
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    // a blocking stream: ordered with work the caller left on the legacy default stream
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamDefault) != cudaSuccess) {
       delete c;
       return KITE_ERR_CUDA;
     }
@@ -215,7 +219,7 @@ int kite_set_stream(kite_ctx* ctx, void* cuda_stream) {
   if (cuda_stream) {
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   } else {
-    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess)
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamDefault) != cudaSuccess)
       return fail(ctx, KITE_ERR_CUDA, "stream creation failed");
     ctx->own_stream = true;
   }
@@ -364,15 +368,17 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
 }
 
 int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
-                        double scale, double* C, int sub_k) {
+                        double scale, double* C, int sub_k, int products) {
   if (!ctx) return KITE_ERR_ARG;
   ctx->last_error.clear();
   if (!A || !B || !C || M < 1 || M2 < 1 || N < 1 || sub_k < 0 || !isfinite(scale))
     return fail(ctx, KITE_ERR_ARG, "need A, B, C, M >= 1, M2 >= 1, N >= 1, sub_k >= 0");
+  if (products != 0 && products != 3 && products != 4)
+    return fail(ctx, KITE_ERR_ARG, "products must be 0 (default 4), 3 or 4");
   if ((double)M * N > 4.0e10 || (double)M2 * N > 4.0e10)
     return fail(ctx, KITE_ERR_ARG, "families larger than 4e10 complex entries");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
-  const int sub_kb = sub_k == 0 ? 32 : (sub_k + 63) / 64;
+  const int sub_kb = sub_k == 0 ? 16 : (sub_k + 63) / 64;
   const size_t a_bytes = (size_t)M * N * 8, b_bytes = (size_t)M2 * N * 8, c_bytes = (size_t)M * M2 * 16;
   const bool a_d = is_device_ptr(A), b_d = is_device_ptr(B), c_d = is_device_ptr(C);
   char* stage = nullptr;
@@ -387,7 +393,7 @@ int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, in
   if (e == cudaSuccess && !b_d) { Bd = reinterpret_cast<float*>(stage + off); e = copy_in(ctx, stage + off, B, b_bytes); off += (b_bytes + 255) & ~size_t(255); }
   if (!c_d) Cd = reinterpret_cast<double*>(stage + off);
   int rc = e == cudaSuccess ? KITE_OK : cuda_fail(ctx, e, "copying A/B");
-  if (rc == KITE_OK) rc = inner_products_impl(ctx, Ad, Bd, M, M2, N, scale, Cd, sub_kb);
+  if (rc == KITE_OK) rc = inner_products_impl(ctx, Ad, Bd, M, M2, N, scale, Cd, sub_kb, products == 3 ? 3 : 4);
   if (rc == KITE_OK && !c_d) {
     e = copy_out(ctx, C, Cd, c_bytes);
     if (e != cudaSuccess) rc = cuda_fail(ctx, e, "copying C");
@@ -441,6 +447,54 @@ int kite_reconstruct_dos(kite_ctx* ctx, const double* mu, int M_avail, int M_use
   cudaFreeAsync(buf, ctx->stream);
   cudaError_t es = cudaStreamSynchronize(ctx->stream);
   if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "reconstruct_dos");
+  return rc;
+}
+
+int kite_reconstruct_sigma(kite_ctx* ctx, const double* mu_nm, int M_avail, int M_use,
+                           int lattice, int kernel, double e_min, double e_max, double E_F,
+                           double kT, double eta, const double* omega, int K, int n_quad,
+                           double* sigma) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  if (!mu_nm || !omega || !sigma || K < 0 || M_avail < 1 || M_use < 1 || M_use > M_avail ||
+      n_quad < 0 || n_quad > (1 << 20))
+    return fail(ctx, KITE_ERR_ARG, "need mu_nm, omega, sigma and 1 <= M_use <= M_avail");
+  if (lattice != KITE_HONEYCOMB && lattice != KITE_SQUARE) return fail(ctx, KITE_ERR_ARG, "unknown lattice");
+  if (kernel != KITE_KERNEL_NONE && kernel != KITE_KERNEL_JACKSON)
+    return fail(ctx, KITE_ERR_ARG, "sigma supports KITE_KERNEL_NONE and KITE_KERNEL_JACKSON");
+  if (!(e_max > e_min) || !(eta > 0.0) || !(kT >= 0.0) || !isfinite(E_F))
+    return fail(ctx, KITE_ERR_ARG, "need e_max > e_min, eta > 0, kT >= 0");
+  if (K == 0) return KITE_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  std::vector<double> om(K);
+  cudaError_t e = cudaMemcpy(om.data(), omega, K * sizeof(double), cudaMemcpyDefault);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reading omega");
+  for (int i = 0; i < K; ++i)
+    if (!(om[i] > 0.0) || !isfinite(om[i])) return fail(ctx, KITE_ERR_ARG, "omega must be > 0");
+  Scale sc{e_min, e_max, 0.5 * (e_max + e_min), 0.5 * (e_max - e_min)};
+  const bool mu_d = is_device_ptr(mu_nm), s_d = is_device_ptr(sigma);
+  const size_t mu_bytes = 2 * sizeof(double) * (size_t)M_avail * M_avail;
+  double* stage = nullptr;
+  const size_t st_bytes = (mu_d ? 0 : mu_bytes) + (s_d ? 0 : 2 * sizeof(double) * K) + 512;
+  KITE_CUDA_TRY(ctx, cudaMallocAsync((void**)&stage, st_bytes, ctx->stream));
+  const double* mu_dev = mu_nm;
+  double* sig_dev = sigma;
+  if (!mu_d) {
+    mu_dev = stage;
+    e = copy_in(ctx, stage, mu_nm, mu_bytes);
+  }
+  if (!s_d) sig_dev = stage + (mu_d ? 0 : 2 * (size_t)M_avail * M_avail);
+  int rc = e == cudaSuccess ? KITE_OK : cuda_fail(ctx, e, "copying mu_nm");
+  if (rc == KITE_OK)
+    rc = reconstruct_sigma_impl(ctx, mu_dev, M_avail, M_use, lattice, kernel, sc, E_F, kT, eta,
+                                om.data(), K, n_quad, sig_dev);
+  if (rc == KITE_OK && !s_d) {
+    e = copy_out(ctx, sigma, sig_dev, 2 * sizeof(double) * K);
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "copying sigma");
+  }
+  cudaFreeAsync(stage, ctx->stream);
+  cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "reconstruct_sigma");
   return rc;
 }
 

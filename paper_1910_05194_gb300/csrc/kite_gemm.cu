@@ -9,7 +9,9 @@
 //   Im <a|b> = sum (ar bi - ai br)   = A' . (-i b)'
 // so the B operand holds, for every m, the rows b_m and -i b_m (the "extended" B with
 // 2M rows) and one real GEMM A' B_ext^T gives both parts.  Each FP32 value x is split
-// into hi = bf16(x), lo = bf16(x - hi); the product keeps hi*hi + hi*lo + lo*hi.
+// into hi = bf16(x), lo = bf16(x - hi); the product keeps hi*hi + hi*lo + lo*hi and, by
+// default, lo*lo: the dropped lo*lo term is always positive for aligned products (e.g. the
+// diagonal <h r|h r>) and would bias them by up to ~5e-6 relative.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -133,6 +135,7 @@ struct GemmArgs {
   int kb_total;     // K blocks of 64
   int kb_per_item;  // K blocks per split
   int sub_kb;       // K blocks per FP32 accumulation sub-chunk
+  int nprod;        // 3: hi*hi + hi*lo + lo*hi;  4: + lo*lo
   int Mrows;        // rows of A (valid)
   int Nrows;        // rows of B (valid) = columns of C
   double* part;     // [S][Mrows][Nrows] FP64 partial sums
@@ -250,6 +253,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
               umma_bf16(d, ah, bh, (kb > kc || kk > 0) ? 1u : 0u);
               umma_bf16(d, ah, bl, 1u);
               umma_bf16(d, al, bh, 1u);
+              if (a.nprod == 4) umma_bf16(d, al, bl, 1u);
             }
             umma_commit(&empty[st]);  // stage reusable once these MMAs have read it
             if (++st == kGStages) st = 0, ph ^= 1u;
@@ -430,7 +434,7 @@ int plan_gemm_splits(kite_ctx* ctx, int Mrows, int Nrows, int64_t Kp) {
 
 int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void* Bhi,
                     const void* Blo, int Mrows, int Nrows, int64_t Kp, int S, int sub_kb,
-                    double* part) {
+                    int nprod, double* part) {
   if (Kp % kBK != 0) return fail(ctx, KITE_ERR_ARG, "K must be padded to a multiple of 64");
   CUtensorMap mAh, mAl, mBh, mBl;
   int rc;
@@ -447,6 +451,7 @@ int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void*
   a.S = (a.kb_total + a.kb_per_item - 1) / a.kb_per_item;
   a.items = a.S * a.T;
   a.sub_kb = std::max(1, sub_kb);
+  a.nprod = nprod == 3 ? 3 : 4;
   a.Mrows = Mrows;
   a.Nrows = Nrows;
   a.part = part;
@@ -476,7 +481,7 @@ int reduce_cplx(kite_ctx* ctx, const double* part, int S, int M, int M2, double 
 // Generic entry: C[n][m] = scale * sum_i conj(A[n][i]) B[m][i], A [M][N], B [M2][N] complex
 // FP32 (device), C [M][M2] complex FP64 (device).
 int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
-                        double scale, double* C, int sub_kb) {
+                        double scale, double* C, int sub_kb, int nprod) {
   const int64_t Kp = ((2 * N + kBK - 1) / kBK) * kBK;
   const int Nrows = 2 * M2;
   const int S = plan_gemm_splits(ctx, M, Nrows, Kp);
@@ -503,7 +508,7 @@ int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, in
   k_split_rows<<<blocks, 256, 0, ctx->stream>>>(reinterpret_cast<const float2*>(B), M2, N, Kp, M2, 1, Bhi, Blo);
   KITE_CUDA_TRY(ctx, cudaGetLastError());
   KITE_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
-  rc = gemm_split_bf16(ctx, Ahi, Alo, Bhi, Blo, M, Nrows, Kp, S, sub_kb, part);
+  rc = gemm_split_bf16(ctx, Ahi, Alo, Bhi, Blo, M, Nrows, Kp, S, sub_kb, nprod, part);
   if (rc != KITE_OK) return rc;
   return reduce_cplx(ctx, part, S, M, M2, scale, C, false);
 }

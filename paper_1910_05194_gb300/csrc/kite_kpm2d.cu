@@ -17,13 +17,14 @@ namespace kite {
 int plan_gemm_splits(kite_ctx* ctx, int Mrows, int Nrows, int64_t Kp);
 int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void* Bhi,
                     const void* Blo, int Mrows, int Nrows, int64_t Kp, int S, int sub_kb,
-                    double* part);
+                    int nprod, double* part);
 int reduce_cplx(kite_ctx* ctx, const double* part, int S, int M, int M2, double scale,
                 double* out, bool accumulate);
 
 namespace {
 
-constexpr int kGemmSubKb = 32;  // 2048 products per FP32 accumulation sub-chunk
+constexpr int kGemmSubKb = 16;  // 1024 products per FP32 accumulation sub-chunk
+constexpr int kGemmProducts = 4; // hi*hi + hi*lo + lo*hi + lo*lo
 
 // h~x applied to a whole FP32 batch (one chunk = two vectors).  mode 1: writes the
 // result as row `col` of the A family (and to out_vec if given); mode 2: rows `col` and
@@ -207,7 +208,8 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
       // contraction, one vector at a time, accumulated in FP64
       KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
       for (int v = 0; v < nvec; ++v) {
-        int rc = gemm_split_bf16(ctx, Ah[v], Al[v], Bh[v], Bl[v], M, 2 * M, Kp, Sg, kGemmSubKb, part);
+        int rc = gemm_split_bf16(ctx, Ah[v], Al[v], Bh[v], Bl[v], M, 2 * M, Kp, Sg, kGemmSubKb,
+                                 kGemmProducts, part);
         if (rc != KITE_OK) return rc;
         rc = reduce_cplx(ctx, part, Sg, M, M, scale, mu_nm_dev, true);
         if (rc != KITE_OK) return rc;
@@ -230,8 +232,8 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
     stats->step_seconds = rec_s;
     stats->step_launches = (int64_t)Sreal * ((R + VB - 1) / VB) * 2 * (M > 1 ? M - 1 : 0);
     stats->gemm_seconds = gemm_s;
-    // three BF16 products of an M x 2M x Kp real GEMM per vector
-    stats->gemm_flops = 3.0 * 2.0 * (double)M * (2.0 * M) * (double)Kp * R * Sreal;
+    // kGemmProducts BF16 products of an M x 2M x Kp real GEMM per vector
+    stats->gemm_flops = (double)kGemmProducts * 2.0 * (double)M * (2.0 * M) * (double)Kp * R * Sreal;
     stats->updates = (double)n_eff * M * R * Sreal * 2.0;
     stats->n_eff = n_eff;
     stats->grid = G;

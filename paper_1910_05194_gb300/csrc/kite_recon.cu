@@ -6,6 +6,8 @@
 // truncated at M terms (Eq. e8a) and damped by a kernel g_n (Sec. 2a).
 #include <math.h>
 
+#include <vector>
+
 #include "kite_internal.h"
 
 namespace kite {
@@ -74,6 +76,239 @@ int reconstruct_dos_impl(kite_ctx* ctx, const double* mu_dev, int M_use, int ker
                                                        E_dev, K, rho_dev);
   KITE_CUDA_TRY(ctx, cudaGetLastError());
   return KITE_OK;
+}
+
+}  // namespace kite
+
+// ====================================================================================
+// First-order optical conductivity sigma_xx(omega) from the 2D moments (Sec. 2b):
+//   Gamma_nm = -g_n g_m mu_nm / ((1 + d_n0)(1 + d_m0))            (Eq. Gammanm, damped)
+//   S(w) = int de f(e) sum_nm Gamma_nm [g^R_n(e + w) Delta_m(e) + Delta_n(e) g^A_m(e - w)]
+//   sigma(w) = -i (n_orb a^2/Omega_c) / w * S(w)   [units e^2/hbar, w = hbar omega/de_minus]
+// (Eq. conductivity_1st_order in rescaled units).  With e = cos(theta), Delta_m(e) de =
+// (2/pi) cos(m theta) d theta, integrated by Gauss-Legendre quadrature in theta.  Then
+// U[n][k] = sum_m Gamma_nm D[m][k] and W[m][k] = sum_n Gamma_nm D[n][k] (two FP64 GEMMs),
+// and per frequency S = sum_k sum_n (g^R_n(e_k + w) U[n][k] + g^A_n(e_k - w) W[n][k]).
+// The CPGF coefficients (Eq. green_function_cheb_expansionb) are geometric in n:
+// g^{s}_n(z) = -2 s i q^n / sqrt(1 - z^2) with q = exp(-s i arccos z) = z - s i sqrt(1 - z^2)
+// for the principal branches, so only a complex square root is needed per (w, node).
+// ====================================================================================
+namespace kite {
+namespace {
+
+struct cplx {
+  double re, im;
+};
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+  const double d = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+// principal square root (Re >= 0), cancellation-free in both half planes
+__device__ __forceinline__ cplx csqrt_p(cplx z) {
+  const double r = hypot(z.re, z.im);
+  if (r == 0.0) return {0.0, 0.0};
+  if (z.re >= 0.0) {
+    const double t = sqrt(0.5 * (r + z.re));
+    return {t, z.im / (2.0 * t)};
+  }
+  const double t = sqrt(0.5 * (r - z.re));
+  return {fabs(z.im) / (2.0 * t), z.im >= 0.0 ? t : -t};
+}
+
+__global__ void k_sig_gamma(const double* __restrict__ mu, int M_avail, int M, int kernel,
+                            double* __restrict__ gam) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)M * M) return;
+  const int n = (int)(e / M), m = (int)(e - (e / M) * M);
+  auto jackson = [&](int k) {
+    const double q = 3.141592653589793 / (double)(M + 1);
+    return ((double)(M - k + 1) * cos(q * k) + sin(q * k) * (cos(q) / sin(q))) / (double)(M + 1);
+  };
+  double w = (n == 0 ? 0.5 : 1.0) * (m == 0 ? 0.5 : 1.0);
+  if (kernel == KITE_KERNEL_JACKSON) w *= jackson(n) * jackson(m);
+  const double* p = mu + 2 * ((int64_t)n * M_avail + m);
+  gam[2 * e] = -w * p[0];
+  gam[2 * e + 1] = -w * p[1];
+}
+
+// D[m][k] = (2/pi) cos(m theta_k) w_k
+__global__ void k_sig_dmat(const double* __restrict__ theta, const double* __restrict__ wq, int M,
+                           int K, double* __restrict__ D) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)M * K) return;
+  const int m = (int)(e / K), k = (int)(e - (e / K) * K);
+  D[e] = 0.6366197723675814 * cos((double)m * theta[k]) * wq[k];
+}
+
+// C[i][k] = sum_j A(i,j) B[j][k], A complex [M][M] (A(i,j) = G[i][j] or, if trans, G[j][i]),
+// B real [M][K], C complex [M][K].  16x16 tiles through shared memory.
+__global__ void k_zgemm_real(const double* __restrict__ G, int trans, const double* __restrict__ B,
+                             int M, int K, double* __restrict__ Cm) {
+  __shared__ double As_re[16][17], As_im[16][17], Bs[16][17];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.y * 16 + ty, k = blockIdx.x * 16 + tx;
+  double re = 0.0, im = 0.0;
+  for (int j0 = 0; j0 < M; j0 += 16) {
+    const int ia = blockIdx.y * 16 + ty, ja = j0 + tx;
+    double ar = 0.0, ai = 0.0;
+    if (ia < M && ja < M) {
+      const int64_t idx = trans ? (int64_t)ja * M + ia : (int64_t)ia * M + ja;
+      ar = G[2 * idx];
+      ai = G[2 * idx + 1];
+    }
+    As_re[ty][tx] = ar;
+    As_im[ty][tx] = ai;
+    const int jb = j0 + ty;
+    Bs[ty][tx] = (jb < M && k < K) ? B[(int64_t)jb * K + k] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      re += As_re[ty][jj] * Bs[jj][tx];
+      im += As_im[ty][jj] * Bs[jj][tx];
+    }
+    __syncthreads();
+  }
+  if (i < M && k < K) {
+    Cm[2 * ((int64_t)i * K + k)] = re;
+    Cm[2 * ((int64_t)i * K + k) + 1] = im;
+  }
+}
+
+// One block per frequency: S(w) = sum_k [sum_n gR_n(e_k + w) U[n][k] + gA_n(e_k - w) W[n][k]]
+__global__ void k_sig_omega(const double* __restrict__ U, const double* __restrict__ W,
+                            const double* __restrict__ theta, int M, int K,
+                            const double* __restrict__ wt, double eta_t, double factor,
+                            double* __restrict__ sigma) {
+  const int iw = blockIdx.x;
+  const double w = wt[iw];
+  double sre = 0.0, sim = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const double e = cos(theta[k]);
+    // retarded: z = e + w + i eta, g_n = -2i q^n / sqrt(1 - z^2), q = z - i sqrt(1 - z^2)
+    // advanced: z = e - w - i eta, g_n = +2i q^n / sqrt(1 - z^2), q = z + i sqrt(1 - z^2)
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      const double s = sgn == 0 ? 1.0 : -1.0;
+      const cplx z = {e + s * w, s * eta_t};
+      const cplx one_m_z2 = {1.0 - (z.re * z.re - z.im * z.im), -2.0 * z.re * z.im};
+      const cplx r = csqrt_p(one_m_z2);
+      const cplx q = {z.re + s * r.im, z.im - s * r.re};  // z - s i r
+      cplx g = cdiv({0.0, -2.0 * s}, r);
+      const double* X = sgn == 0 ? U : W;
+      double ar = 0.0, ai = 0.0;
+      for (int n = 0; n < M; ++n) {
+        const double xr = X[2 * ((int64_t)n * K + k)], xi = X[2 * ((int64_t)n * K + k) + 1];
+        ar += g.re * xr - g.im * xi;
+        ai += g.re * xi + g.im * xr;
+        g = cmul(g, q);
+      }
+      sre += ar;
+      sim += ai;
+    }
+  }
+  __shared__ double red_re[256], red_im[256];
+  red_re[threadIdx.x] = sre;
+  red_im[threadIdx.x] = sim;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      red_re[threadIdx.x] += red_re[threadIdx.x + st];
+      red_im[threadIdx.x] += red_im[threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    // sigma = -i * factor / w * S
+    const double Sr = red_re[0], Si = red_im[0];
+    sigma[2 * iw] = factor / w * Si;
+    sigma[2 * iw + 1] = -factor / w * Sr;
+  }
+}
+
+}  // namespace
+
+// Gauss-Legendre nodes/weights on [-1, 1] (Newton iteration on P_K from the three-term
+// recurrence), host FP64.
+void gauss_legendre(int K, double* x, double* w) {
+  const double pi = 3.141592653589793;
+  for (int i = 0; i < (K + 1) / 2; ++i) {
+    double z = cos(pi * (i + 0.75) / (K + 0.5)), dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = 0.0;
+      for (int j = 1; j <= K; ++j) {
+        const double p2 = p1;
+        p1 = p0;
+        p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+      }
+      dp = K * (z * p0 - p1) / (z * z - 1.0);
+      const double dz = p0 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = 0.0;
+      for (int j = 1; j <= K; ++j) {
+        const double p2 = p1;
+        p1 = p0;
+        p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+      }
+      dp = K * (z * p0 - p1) / (z * z - 1.0);
+    }
+    x[i] = -z;
+    x[K - 1 - i] = z;
+    w[i] = w[K - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+int reconstruct_sigma_impl(kite_ctx* ctx, const double* mu_dev, int M_avail, int M, int lattice,
+                           int kernel, const Scale& sc, double E_F, double kT, double eta,
+                           const double* omega_host, int K_w, int n_quad, double* sigma_dev) {
+  const int K = n_quad > 0 ? n_quad : 2 * M + 64;
+  const double eF = (E_F - sc.de_plus) / sc.de_minus;
+  const double thF = kT > 0.0 ? 0.0 : acos(fmin(1.0, fmax(-1.0, eF)));
+  std::vector<double> x(K), wq(K), th(K), wts(2 * (size_t)K_w);
+  gauss_legendre(K, x.data(), wq.data());
+  const double pi = 3.141592653589793;
+  for (int k = 0; k < K; ++k) {
+    th[k] = thF + (pi - thF) * 0.5 * (x[k] + 1.0);
+    wq[k] *= 0.5 * (pi - thF);
+    if (kT > 0.0) {
+      const double E = cos(th[k]) * sc.de_minus + sc.de_plus;
+      wq[k] /= (1.0 + exp((E - E_F) / kT));
+    }
+  }
+  for (int i = 0; i < K_w; ++i) wts[i] = omega_host[i] / sc.de_minus;
+  const size_t nG = 2 * (size_t)M * M, nD = (size_t)M * K, nU = 2 * (size_t)M * K;
+  double* buf = nullptr;
+  const size_t total = nG + nD + 2 * nU + 2 * (size_t)K + K_w;
+  KITE_CUDA_TRY(ctx, cudaMallocAsync((void**)&buf, total * sizeof(double), ctx->stream));
+  double* G = buf;
+  double* D = G + nG;
+  double* U = D + nD;
+  double* W = U + nU;
+  double* th_d = W + nU;
+  double* wq_d = th_d + K;
+  double* wt_d = wq_d + K;
+  cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaMemcpyAsync(th_d, th.data(), K * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(wq_d, wq.data(), K * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(wt_d, wts.data(), K_w * sizeof(double), cudaMemcpyHostToDevice, st);
+  int rc = e == cudaSuccess ? KITE_OK : cuda_fail(ctx, e, "sigma set-up");
+  if (rc == KITE_OK) {
+    k_sig_gamma<<<(int)(((int64_t)M * M + 255) / 256), 256, 0, st>>>(mu_dev, M_avail, M, kernel, G);
+    k_sig_dmat<<<(int)(((int64_t)M * K + 255) / 256), 256, 0, st>>>(th_d, wq_d, M, K, D);
+    dim3 blk(16, 16), grd((K + 15) / 16, (M + 15) / 16);
+    k_zgemm_real<<<grd, blk, 0, st>>>(G, 0, D, M, K, U);
+    k_zgemm_real<<<grd, blk, 0, st>>>(G, 1, D, M, K, W);
+    const double factor = lattice == KITE_HONEYCOMB ? 4.0 / sqrt(3.0) : 1.0;
+    k_sig_omega<<<K_w, 256, 0, st>>>(U, W, th_d, M, K, wt_d, eta / sc.de_minus, factor, sigma_dev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "sigma kernels");
+  }
+  cudaFreeAsync(buf, st);
+  return rc;
 }
 
 }  // namespace kite
