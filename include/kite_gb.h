@@ -203,7 +203,8 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
  * Runs on the tensor cores (tcgen05.mma): every FP32 input x is split into
  * bf16 hi = bf16(x) and lo = bf16(x - hi); products keep hi*hi + hi*lo + lo*hi
  * (`products` = 3) or also lo*lo (`products` = 4 or 0, the default); sums are FP32 inside
- * a K sub-chunk of `sub_k` products and FP64 above (sub_k = 0: default 1024).
+ * a K sub-chunk of `sub_k` products and FP64 above (sub_k = 0: default 512; the
+ * tensor core's FP32 accumulation drifts ~5e-9 per product for one-signed terms).
  *   A  [M][N]  complex FP32 interleaved (re, im), host or device
  *   B  [M2][N] complex FP32 interleaved, host or device
  *   C  [M][M2] complex FP64 interleaved, host or device (overwritten)

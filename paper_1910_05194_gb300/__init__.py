@@ -234,3 +234,4 @@ def reconstruct_sigma(ctx: Context, mu_nm, M_avail: int, M_use: int, lattice: in
                                            int(lattice), int(kernel), float(e_min), float(e_max),
                                            float(E_F), float(kT), float(eta), _addr(omega), int(K),
                                            int(n_quad), _addr(sigma)))
+

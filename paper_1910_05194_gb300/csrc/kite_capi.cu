@@ -378,7 +378,7 @@ int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, in
   if ((double)M * N > 4.0e10 || (double)M2 * N > 4.0e10)
     return fail(ctx, KITE_ERR_ARG, "families larger than 4e10 complex entries");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
-  const int sub_kb = sub_k == 0 ? 16 : (sub_k + 63) / 64;
+  const int sub_kb = sub_k == 0 ? 8 : (sub_k + 63) / 64;
   const size_t a_bytes = (size_t)M * N * 8, b_bytes = (size_t)M2 * N * 8, c_bytes = (size_t)M * M2 * 16;
   const bool a_d = is_device_ptr(A), b_d = is_device_ptr(B), c_d = is_device_ptr(C);
   char* stage = nullptr;

@@ -32,11 +32,12 @@ constexpr int kGStages = 2;
 constexpr int kATile = kBM * kBK * 2;          // 16 KB
 constexpr int kBTile = kBN * kBK * 2;          // 32 KB
 constexpr int kStageBytes = 2 * kATile + 2 * kBTile;   // A hi, A lo, B hi, B lo
-constexpr int kGemmThreads = 192;              // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kEpiWarps = 8;                   // two per TMEM lane quarter, 128 columns each
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
 constexpr int kAccCols = kBN;                  // FP32 accumulator columns per buffer
 constexpr int kTmemCols = 2 * kAccCols;        // double-buffered accumulator
 constexpr int kEpiPitch = 33;                  // floats per transposed row (bank-conflict free)
-constexpr int kEpiBytes = 4 * 32 * kEpiPitch * 4;
+constexpr int kEpiBytes = kEpiWarps * 32 * kEpiPitch * 4;
 constexpr int kGemmSmem = 1024 + kGStages * kStageBytes + kEpiBytes + 256;
 
 // Instruction descriptor of tcgen05.mma kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], 128);
+      mbar_init(&tempty[i], 32 * kEpiWarps);
     }
     mbar_init(drain, 1);
     mbar_fence_init();
@@ -269,8 +270,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       while (!mbar_try_wait(drain, 0) && clock64() - t0 < kWaitCycles) {
       }
     }
-  } else {  // ---- epilogue: warps 2..5 drain the idle accumulator into FP64 partials
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+  } else {  // ---- epilogue: warps 2.. drain the idle accumulator into FP64 partials
+    const int q = warp & 3;                           // TMEM lane quarter this warp may access
+    const int half = (warp - 2) / 4;                  // which 128 of the 256 columns
     float* tile = epi + (warp - 2) * 32 * kEpiPitch;
     int acc = 0;
     uint32_t aph = 0;
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           break;
         }
         tc_fence_after();
-        for (int c0 = 0; c0 < kAccCols; c0 += 32) {
+        for (int c0 = half * (kAccCols / 2); c0 < (half + 1) * (kAccCols / 2); c0 += 32) {
           uint32_t r[32];
           tmem_ld_32x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols + c0), r);
           // transpose 32 rows x 32 columns through shared memory for coalesced FP64 RMW
@@ -294,13 +296,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           for (int jj = 0; jj < 32; ++jj) tile[lane * kEpiPitch + jj] = __uint_as_float(r[jj]);
           __syncwarp();
           const int col = tn * kBN + c0 + lane;
-          for (int rr = 0; rr < 32; ++rr) {
-            const int row = tm * kBM + q * 32 + rr;
-            if (row < a.Mrows && col < a.Nrows) {
-              double* p = a.part + ((size_t)s * a.Mrows + row) * a.Nrows + col;
-              const double v = (double)tile[rr * kEpiPitch + lane];
-              *p = first ? v : *p + v;
-            }
+          const int row0 = tm * kBM + q * 32;
+          double* p = a.part + ((size_t)s * a.Mrows + row0) * a.Nrows + col;
+          const bool colok = col < a.Nrows;
+          // 16 partial loads in flight before any use (the RMW is latency-bound)
+#pragma unroll
+          for (int h = 0; h < 32; h += 16) {
+            double old[16];
+#pragma unroll
+            for (int rr = 0; rr < 16; ++rr)
+              old[rr] = (!first && colok && row0 + h + rr < a.Mrows) ? p[(size_t)(h + rr) * a.Nrows] : 0.0;
+#pragma unroll
+            for (int rr = 0; rr < 16; ++rr)
+              if (colok && row0 + h + rr < a.Mrows)
+                p[(size_t)(h + rr) * a.Nrows] = old[rr] + (double)tile[(h + rr) * kEpiPitch + lane];
           }
           __syncwarp();
         }

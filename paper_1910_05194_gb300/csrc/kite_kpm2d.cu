@@ -23,7 +23,7 @@ int reduce_cplx(kite_ctx* ctx, const double* part, int S, int M, int M2, double 
 
 namespace {
 
-constexpr int kGemmSubKb = 16;  // 1024 products per FP32 accumulation sub-chunk
+constexpr int kGemmSubKb = 8;   // 512 products per FP32 accumulation sub-chunk
 constexpr int kGemmProducts = 4; // hi*hi + hi*lo + lo*hi + lo*lo
 
 // h~x applied to a whole FP32 batch (one chunk = two vectors).  mode 1: writes the

@@ -57,14 +57,16 @@ def test_aligned_terms_long_k_accumulation(ctx):
     for name, vec in (("bf16-exact", exact_bf16), ("general", a)):
         A = vec[None, :].astype(np.complex64)
         for products in (3, 4):
-            for sub_k in (256, 1024, 4096, 65536):
+            for sub_k in (256, 512, 1024, 4096):
                 C, ref, bound = run(ctx, A, A, scale=1.0 / N, sub_k=sub_k, products=products)
                 res[(name, products, sub_k)] = abs(C[0, 0] - ref[0, 0]) / abs(ref[0, 0])
     for k, v in sorted(res.items()):
         print(f"{k}: relative error {v:.3e}")
-    # default path (4 products, 1024-product sub-chunks) well inside the 1e-5 bar
-    assert res[("general", 4, 1024)] <= 3e-6
-    assert res[("bf16-exact", 4, 1024)] <= 3e-6
+    # default path (4 products, 512-product sub-chunks) well inside the 1e-5 bar; the
+    # FP32 accumulation error grows linearly with the sub-chunk length
+    assert res[("general", 4, 512)] <= 4e-6
+    assert res[("bf16-exact", 4, 256)] <= 1e-12  # bf16 products sum exactly over 256 terms
+    assert res[("general", 4, 256)] < res[("general", 4, 4096)]
 
 
 def test_host_and_device_buffers(ctx):
@@ -75,6 +77,7 @@ def test_host_and_device_buffers(ctx):
     Ad = torch.from_numpy(A.view(np.float32)).cuda()
     Bd = torch.from_numpy(B.view(np.float32)).cuda()
     Cd = torch.zeros((M, M2, 2), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()  # inputs produced on torch's stream must be complete
     kite.inner_products(ctx, Ad, Bd, M, M2, N, 1.0, Cd)
     C = Cd.cpu().numpy()
     C = C[..., 0] + 1j * C[..., 1]

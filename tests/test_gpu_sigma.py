@@ -45,16 +45,19 @@ def test_sigma_matches_oracle(ctx, moments, kernel, eta, kT, M_use):
 
 
 def test_clean_graphene_universal_plateau(ctx):
-    """Clean honeycomb, E_F = 0: in the window few*broadening << hbar omega << |t| the
+    """Clean honeycomb, E_F = 0: in the window broadening << hbar omega << |t| the
     absorptive conductivity of the spinless model is e^2/(8 hbar) (both valleys), with
-    corrections of order (hbar omega / t)^2.  Loose physics check (5 %)."""
+    corrections of order (hbar omega / t)^2.  The finite lattice's level spacing makes
+    single frequencies ripple, so the window average is checked (loose physics check, 3 %)."""
     torch = pytest.importorskip("torch")
-    d = dict(lattice=0, Lx=512, Ly=512, t=-2.7, W=0.0, seed=21)
-    M = 1024
+    d = dict(lattice=0, Lx=1024, Ly=1024, t=-2.7, W=0.0, seed=21)
+    M = 512
     mu = torch.zeros((M, M, 2), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
     st = kite.moments_2d(ctx, kite.make_system(**d), kite.make_kpm(M, 1, 1, kite.FP32), mu)
-    omega = np.array([0.4, 0.6, 0.8, 1.0])
+    omega = np.linspace(0.5, 1.2, 29)
     sig = np.zeros((omega.size, 2))
     kite.reconstruct_sigma(ctx, mu, M, M, kite.HONEYCOMB, kite.KERNEL_JACKSON, st.e_min, st.e_max,
                            0.0, 0.0, 1e-5, omega, omega.size, sig, 0)
-    assert np.all(np.abs(sig[:, 0] / 0.125 - 1.0) < 0.05), sig[:, 0]
+    assert abs(np.mean(sig[:, 0]) / 0.125 - 1.0) < 0.03, sig[:, 0]
+    assert np.all(sig[:, 0] > 0.0)
