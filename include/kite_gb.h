@@ -214,6 +214,30 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
 int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
                         double scale, double* C, int sub_k, int products);
 
+/* ---- 1D moments without allocation (no counterpart in the paper) ------------------ */
+
+/* kite_moments_1d for callers that cannot allocate device memory at the moment they need
+ * moments: for example code running inside a host framework whose caching allocator has
+ * already reserved the GPU's memory, or a latency-critical loop that must never wait on
+ * the allocator.  It runs the same kernels as kite_moments_1d but keeps every intermediate
+ * in one fixed 32 MiB array per GPU -- a file-scope __device__ variable of this library,
+ * held by every GPU that loads the library until the process exits -- and calls no
+ * cudaMalloc, cudaFree or other allocating routine, and needs no kite_ctx.
+ *   sys, kpm   as for kite_moments_1d; e_min = e_max = 0 selects the Gershgorin bounds;
+ *              R <= 8 (FP32) or 4 (FP64); kpm->r0 and kpm->r_last must be NULL
+ *   mu         [M] FP64 moments (vector average), host or device, complete on return
+ *   cuda_stream  stream the work is queued on (NULL = legacy default stream)
+ *   err, err_len optional buffer for a one-line reason when the call fails
+ * A system whose intermediates do not fit in 32 MiB is rejected with KITE_ERR_ARG and a
+ * message giving the size it needs.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array, which keeps the previous call's contents: each call clears
+ * what must start at zero, but calls that overlap on the GPU (other streams or host
+ * threads) race on it and must be serialised by the caller.
+ * Errors: KITE_ERR_ARG, KITE_ERR_CUDA, KITE_ERR_BOUNDS, KITE_ERR_TIMEOUT. */
+int kite_moments_1d_static(const kite_system* sys, const kite_kpm* kpm, double* mu,
+                           void* cuda_stream, char* err, int err_len);
+
 /* ---- reconstruction ------------------------------------------------------------- */
 
 /* Density of states per orbital and per eV on caller energies (Eqs. e7, e8a with the

@@ -25,7 +25,7 @@ KERNEL_NONE, KERNEL_JACKSON, KERNEL_LORENTZ = 0, 1, 2
 EXPORTED = ("kite_create", "kite_destroy", "kite_set_stream", "kite_status_string",
             "kite_last_error", "kite_bounds", "kite_moments_1d", "kite_reconstruct_dos",
             "kite_debug_stall_once", "kite_inner_products", "kite_moments_2d",
-            "kite_reconstruct_sigma")
+            "kite_reconstruct_sigma", "kite_moments_1d_static")
 
 
 class KiteError(RuntimeError):
@@ -106,6 +106,8 @@ def lib():
             L.kite_reconstruct_sigma.argtypes = [vp, vp, i32, i32, i32, i32, d, d, d, d, d, vp,
                                                  i32, i32, vp]
             L.kite_reconstruct_sigma.restype = i32
+            L.kite_moments_1d_static.argtypes = [P(System), P(KPM), vp, vp, ctypes.c_char_p, i32]
+            L.kite_moments_1d_static.restype = i32
             L.kite_moments_2d.argtypes = [vp, P(System), P(KPM), vp, P(Stats)]
             L.kite_moments_2d.restype = i32
             L.kite_inner_products.argtypes = [vp, vp, vp, i32, i32, ctypes.c_int64, d, vp, i32, i32]
@@ -235,3 +237,12 @@ def reconstruct_sigma(ctx: Context, mu_nm, M_avail: int, M_use: int, lattice: in
                                            float(E_F), float(kT), float(eta), _addr(omega), int(K),
                                            int(n_quad), _addr(sigma)))
 
+
+def moments_1d_static(system: System, kpm: KPM, mu, stream=None):
+    """kite_moments_1d_static: the 1D moments without any device allocation (fixed 32 MiB
+    array per GPU, no context).  For callers that cannot allocate at call time."""
+    err = ctypes.create_string_buffer(256)
+    rc = lib().kite_moments_1d_static(ctypes.byref(system), ctypes.byref(kpm), _addr(mu),
+                                      _stream_handle(stream), err, 256)
+    if rc != OK:
+        raise KiteError(rc, err.value.decode() or lib().kite_status_string(rc).decode())
