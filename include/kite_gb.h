@@ -214,6 +214,22 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
 int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
                         double scale, double* C, int sub_k, int products);
 
+/* Moments of many independent systems in one persistent, graph-captured launch (the S
+ * realisations and the independent samples of Eq. PcomplexityFactor, batched).  Each
+ * system i gives mu_i[n] = (1/R) sum_r <r|T_n(H~_i)|r>/N_eff,i for n < M_i, as
+ * kite_moments_1d with S = 1.  Systems may differ in size, disorder, seed, bounds and M;
+ * they share the lattice kind, R (1..8) and precision (KITE_FP32).  The CTAs of one
+ * resident grid are grouped into teams: large systems get several CTAs that meet at a
+ * bounded global barrier after each step, small ones share single-CTA teams.  The
+ * set-up kernels, the sweep and the reductions are captured in one CUDA graph.
+ *   systems, kpms  [count] arrays; kpms[i].S must be 1, r0 and r_last NULL
+ *   mu             [count] pointers, mu[i] -> [M_i] FP64 (host or device)
+ *   st             statistics of the graph launch (seconds, updates, bytes), or NULL
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA, KITE_ERR_BOUNDS, KITE_ERR_TIMEOUT,
+ *         KITE_ERR_UNSUPPORTED (precision other than FP32). */
+int kite_moments_1d_batched(kite_ctx* ctx, int count, const kite_system* systems,
+                            const kite_kpm* kpms, double* const* mu, kite_stats* st);
+
 /* ---- 1D moments without allocation (no counterpart in the paper) ------------------ */
 
 /* kite_moments_1d for callers that cannot allocate device memory at the moment they need

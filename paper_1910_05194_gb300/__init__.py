@@ -25,7 +25,7 @@ KERNEL_NONE, KERNEL_JACKSON, KERNEL_LORENTZ = 0, 1, 2
 EXPORTED = ("kite_create", "kite_destroy", "kite_set_stream", "kite_status_string",
             "kite_last_error", "kite_bounds", "kite_moments_1d", "kite_reconstruct_dos",
             "kite_debug_stall_once", "kite_inner_products", "kite_moments_2d",
-            "kite_reconstruct_sigma", "kite_moments_1d_static")
+            "kite_reconstruct_sigma", "kite_moments_1d_static", "kite_moments_1d_batched")
 
 
 class KiteError(RuntimeError):
@@ -108,6 +108,8 @@ def lib():
             L.kite_reconstruct_sigma.restype = i32
             L.kite_moments_1d_static.argtypes = [P(System), P(KPM), vp, vp, ctypes.c_char_p, i32]
             L.kite_moments_1d_static.restype = i32
+            L.kite_moments_1d_batched.argtypes = [vp, i32, P(System), P(KPM), P(vp), P(Stats)]
+            L.kite_moments_1d_batched.restype = i32
             L.kite_moments_2d.argtypes = [vp, P(System), P(KPM), vp, P(Stats)]
             L.kite_moments_2d.restype = i32
             L.kite_inner_products.argtypes = [vp, vp, vp, i32, i32, ctypes.c_int64, d, vp, i32, i32]
@@ -246,3 +248,15 @@ def moments_1d_static(system: System, kpm: KPM, mu, stream=None):
                                       _stream_handle(stream), err, 256)
     if rc != OK:
         raise KiteError(rc, err.value.decode() or lib().kite_status_string(rc).decode())
+
+
+def moments_1d_batched(ctx: Context, systems, kpms, mus) -> Stats:
+    """kite_moments_1d_batched: one persistent graph launch for many systems.
+    systems/kpms: sequences of System/KPM; mus: sequence of [M_i] FP64 buffers."""
+    n = len(systems)
+    sa = (System * n)(*systems)
+    ka = (KPM * n)(*kpms)
+    pa = (ctypes.c_void_p * n)(*[_addr(m) for m in mus])
+    st = Stats()
+    ctx.check(lib().kite_moments_1d_batched(ctx.handle, n, sa, ka, pa, ctypes.byref(st)))
+    return st

@@ -1,0 +1,392 @@
+// kite_batched.cu -- many independent systems in one persistent, graph-captured launch.
+//
+// The cost of the DOS path is Z*N*M*R*S (Eq. PcomplexityFactor); independent disorder
+// realisations and lattices of uneven size are the natural unit of batching.  The host
+// groups the persistent grid's CTAs into teams: a system whose work N*M exceeds the
+// target share gets a team of several CTAs that split its rows and meet at a global
+// barrier after every recursion step; smaller systems are packed first-fit-decreasing
+// into single-CTA teams that run them one after another.  Every CTA of the grid is
+// resident at once (cooperative launch), every barrier wait is bounded, and the whole
+// batch -- on-site draws, start vectors, the persistent sweep and the fixed-order moment
+// reductions -- is captured into one CUDA graph and launched once.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "kite_step.cuh"
+
+namespace kite {
+namespace {
+
+struct BSys {
+  const void* r0;
+  void* bA;
+  void* bB;
+  const float* vt;
+  double* partial;  // [max(M,2)][ncta][Q]
+  float tt;
+  int Lx, Ly, M;
+  long long units;
+};
+
+struct BTeam {
+  int cta0, ncta;  // CTAs [cta0, cta0 + ncta)
+  int sys0, nsys;  // systems order[sys0 .. sys0 + nsys)
+};
+
+// Arrive-and-wait of the CTAs of one team (counter counts arrivals monotonically).  The
+// writes of this step were made by generic stores; the next step reads them with bulk
+// copies, hence the proxy fences around the release/acquire pair.
+__device__ __forceinline__ bool team_barrier(unsigned int* ctr, unsigned int target, bool skip_arrive,
+                                             int* err, int* abort_flag) {
+  asm volatile("fence.proxy.async.global;" ::: "memory");  // each thread's own stores
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (!skip_arrive) atomicAdd(ctr, 1u);
+    const long long t0 = clock64();
+    for (;;) {
+      unsigned int v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+      if ((int)(v - target) >= 0) break;
+      if (clock64() - t0 > kWaitCycles) {
+        *abort_flag = 1;
+        atomicExch(err, 1);
+        break;
+      }
+      __nanosleep(64);
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+  }
+  __syncthreads();
+  return *abort_flag == 0;
+}
+
+template <int LAT, int C>
+__global__ void __launch_bounds__(kBlock, 2)
+    k_batched(const BSys* __restrict__ systems, const BTeam* __restrict__ teams,
+              const int* __restrict__ order, const int* __restrict__ cta_team,
+              unsigned int* __restrict__ counters, int* __restrict__ err, int stall) {
+  constexpr int Q = 2 * C * 2;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_abort;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kStages; ++k) mbar_init(&bars[k], 1);
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  Ring ring{bars, smem + kBarBytes, &s_abort, 0};
+  const int team = cta_team[blockIdx.x];
+  const BTeam T = teams[team];
+  const int rank = blockIdx.x - T.cta0;
+  unsigned int arrived = 0;
+  const FamOut nofam{};
+  for (int i = 0; i < T.nsys; ++i) {
+    const BSys S = systems[order[T.sys0 + i]];
+    auto where = [&](int n) -> void* {
+      return n == 0 ? const_cast<void*>(S.r0) : ((n & 1) ? S.bA : S.bB);
+    };
+    for (int n = 0; n == 0 || n + 1 < S.M; ++n) {
+      bool ok;
+      if (n == 0)
+        ok = step_body<float, LAT, C, true, 0>(ring, rank, T.ncta, nullptr, S.r0, S.bA, S.r0, S.vt,
+                                               S.tt, S.Lx, S.Ly, S.units,
+                                               S.partial + (size_t)T.ncta * Q, S.partial, err, 0,
+                                               nofam);
+      else
+        ok = step_body<float, LAT, C, false, 0>(ring, rank, T.ncta, where(n - 1), where(n),
+                                                where(n + 1), S.r0, S.vt, S.tt, S.Lx, S.Ly, S.units,
+                                                S.partial + (size_t)(n + 1) * T.ncta * Q, nullptr,
+                                                err, 0, nofam);
+      if (!ok) return;
+      if (T.ncta > 1) {
+        arrived += (unsigned int)T.ncta;
+        const bool skip = stall && team == 0 && rank == 0 && arrived == (unsigned int)T.ncta;
+        if (!team_barrier(counters + team, arrived, skip, err, &s_abort)) return;
+      } else {
+        // a single-CTA team reads its own previous step through the async proxy
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        __syncthreads();
+      }
+    }
+  }
+}
+
+__global__ void k_breduce(const double* __restrict__ partial, int M, int G, int Q, int nvec,
+                          const unsigned long long* __restrict__ n_eff, double* __restrict__ mu) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= M) return;
+  const double ne = (double)*n_eff;
+  double acc = 0.0;
+  for (int q = 0; q < 2 * nvec; q += 2) {  // real parts, vector by vector, CTA by CTA
+    double sum = 0.0;
+    const double* p = partial + (size_t)n * G * Q + q;
+    for (int g = 0; g < G; ++g) sum += p[(size_t)g * Q];
+    acc += ne > 0.0 ? sum / ne : 0.0;
+  }
+  mu[n] = acc / nvec;
+}
+
+struct Schedule {
+  std::vector<BTeam> teams;
+  std::vector<int> order, cta_team, ncta_of;
+  int grid = 0;
+};
+
+// Teams for a target per-CTA work T: systems above T get ceil(W/T) CTAs (at most one per
+// unit of work), the rest are packed first-fit-decreasing into single-CTA bins.
+Schedule plan_teams(const std::vector<double>& work, const std::vector<long long>& units, double T) {
+  Schedule sc;
+  const int n = (int)work.size();
+  std::vector<int> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return work[a] > work[b]; });
+  sc.ncta_of.assign(n, 1);
+  std::vector<std::vector<int>> bins;
+  std::vector<double> load;
+  for (int i : idx) {
+    if (work[i] >= T) {
+      const int c = (int)std::min<long long>(units[i], (long long)std::ceil(work[i] / T));
+      sc.ncta_of[i] = std::max(1, c);
+      BTeam t{sc.grid, sc.ncta_of[i], (int)sc.order.size(), 1};
+      sc.order.push_back(i);
+      sc.teams.push_back(t);
+      sc.grid += t.ncta;
+    } else {
+      size_t b = 0;
+      for (; b < bins.size(); ++b)
+        if (load[b] + work[i] <= T) break;
+      if (b == bins.size()) {
+        bins.emplace_back();
+        load.push_back(0.0);
+      }
+      bins[b].push_back(i);
+      load[b] += work[i];
+    }
+  }
+  for (auto& bin : bins) {
+    BTeam t{sc.grid, 1, (int)sc.order.size(), (int)bin.size()};
+    for (int i : bin) sc.order.push_back(i);
+    sc.teams.push_back(t);
+    sc.grid += 1;
+  }
+  sc.cta_team.resize(sc.grid);
+  for (int t = 0; t < (int)sc.teams.size(); ++t)
+    for (int k = 0; k < sc.teams[t].ncta; ++k) sc.cta_team[sc.teams[t].cta0 + k] = t;
+  return sc;
+}
+
+template <int LAT, int C>
+int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm* kpm,
+                const std::vector<Scale>& scales, double* const* mu_out, kite_stats* stats) {
+  constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
+  constexpr int Q = 2 * C * 2;
+  using Sh = StepShape<LAT, C>;
+  cudaStream_t st = ctx->stream;
+  const int R = kpm[0].R;
+  // persistent grid: every CTA resident
+  cudaFuncSetAttribute(k_batched<LAT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<LAT, C>, kBlock, Sh::SMEM) !=
+          cudaSuccess || occ < 1)
+    return fail(ctx, KITE_ERR_CUDA, "occupancy query for the batched kernel failed");
+  const int gmax = ctx->num_sms * occ;
+  std::vector<double> work(count);
+  std::vector<long long> units(count);
+  double total = 0.0;
+  for (int i = 0; i < count; ++i) {
+    units[i] = (long long)((sys[i].Lx + Sh::TX - 1) / Sh::TX) * sys[i].Ly;
+    work[i] = (double)units[i] * Sh::TX * std::max(kpm[i].M - 1, 1);
+    total += work[i];
+  }
+  // smallest target share whose schedule fits the resident grid
+  double lo = total / gmax, hi = std::max(total, *std::max_element(work.begin(), work.end())) * 1.0001;
+  Schedule sc = plan_teams(work, units, hi);
+  for (int it = 0; it < 60; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    Schedule s2 = plan_teams(work, units, mid);
+    if (s2.grid <= gmax) {
+      hi = mid;
+      sc = std::move(s2);
+    } else {
+      lo = mid;
+    }
+  }
+  // work space: per system vt, three vector buffers, partials, counters
+  std::vector<size_t> off_vt(count), off_vec(count), off_part(count);
+  Carver probe(nullptr);
+  auto lay = [&](Carver& k, bool record) {
+    for (int i = 0; i < count; ++i) {
+      const int64_t ncell = (int64_t)sys[i].Lx * sys[i].Ly, N = ncell * SORB;
+      const size_t vb = (size_t)ncell * SORB * C * 16;
+      char* a = k.take<char>(sizeof(float) * N);
+      char* b = k.take<char>(3 * vb);
+      char* c = k.take<char>(sizeof(double) * (size_t)std::max(kpm[i].M, 2) * sc.ncta_of[i] * Q);
+      if (record) {
+        off_vt[i] = (size_t)a;
+        off_vec[i] = (size_t)b;
+        off_part[i] = (size_t)c;
+      }
+    }
+  };
+  lay(probe, false);
+  probe.take<unsigned long long>(count);                  // n_eff
+  probe.take<unsigned int>(sc.teams.size());              // barrier counters
+  probe.take<BSys>(count);
+  probe.take<BTeam>(sc.teams.size());
+  probe.take<int>(sc.order.size() + sc.cta_team.size());
+  size_t mu_total = 0;
+  for (int i = 0; i < count; ++i) mu_total += (size_t)kpm[i].M;
+  probe.take<double>(mu_total);
+  int rc = ensure_ws(ctx, probe.used());
+  if (rc != KITE_OK) return rc;
+  Carver w(ctx->ws);
+  lay(w, true);
+  auto* ne = w.take<unsigned long long>(count);
+  auto* counters = w.take<unsigned int>(sc.teams.size());
+  auto* d_sys = w.take<BSys>(count);
+  auto* d_teams = w.take<BTeam>(sc.teams.size());
+  auto* d_ints = w.take<int>(sc.order.size() + sc.cta_team.size());
+  auto* d_mu = w.take<double>(mu_total);
+
+  std::vector<BSys> hs(count);
+  std::vector<size_t> mu_off(count);
+  size_t mo = 0;
+  for (int i = 0; i < count; ++i) {
+    const int64_t ncell = (int64_t)sys[i].Lx * sys[i].Ly;
+    const size_t vb = (size_t)ncell * SORB * C * 16;
+    char* vec = reinterpret_cast<char*>(off_vec[i]);
+    hs[i].vt = reinterpret_cast<const float*>(off_vt[i]);
+    hs[i].r0 = vec;
+    hs[i].bA = vec + vb;
+    hs[i].bB = vec + 2 * vb;
+    hs[i].partial = reinterpret_cast<double*>(off_part[i]);
+    hs[i].tt = (float)(sys[i].t / scales[i].de_minus);
+    hs[i].Lx = sys[i].Lx;
+    hs[i].Ly = sys[i].Ly;
+    hs[i].M = kpm[i].M;
+    hs[i].units = units[i];
+    mu_off[i] = mo;
+    mo += (size_t)kpm[i].M;
+  }
+  std::vector<int> ints(sc.order);
+  ints.insert(ints.end(), sc.cta_team.begin(), sc.cta_team.end());
+  KITE_CUDA_TRY(ctx, cudaMemcpyAsync(d_sys, hs.data(), sizeof(BSys) * count, cudaMemcpyHostToDevice, st));
+  KITE_CUDA_TRY(ctx, cudaMemcpyAsync(d_teams, sc.teams.data(), sizeof(BTeam) * sc.teams.size(),
+                                     cudaMemcpyHostToDevice, st));
+  KITE_CUDA_TRY(ctx, cudaMemcpyAsync(d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, st));
+  KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));  // host vectors go out of scope below
+
+  // ---- capture the whole batch into one graph ----------------------------------------
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  KITE_CUDA_TRY(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t ce = cudaSuccess;
+  ce = cudaMemsetAsync(ne, 0, sizeof(unsigned long long) * count, st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(counters, 0, sizeof(unsigned int) * sc.teams.size(), st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st);
+  for (int i = 0; i < count && ce == cudaSuccess; ++i) {
+    const int64_t ncell = (int64_t)sys[i].Lx * sys[i].Ly, N = ncell * SORB;
+    const double thr_d = floor(sys[i].p_vac * 4294967296.0);
+    const uint64_t vac_thr =
+        sys[i].p_vac <= 0.0 ? 0ull : (thr_d >= 4294967296.0 ? 4294967296ull : (uint64_t)thr_d);
+    const uint32_t k0 = (uint32_t)sys[i].seed, k1 = (uint32_t)(sys[i].seed >> 32);
+    const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->num_sms * 16);
+    k_onsite<float><<<std::max(1, blocks), 256, 0, st>>>(N, sys[i].lattice, sys[i].W, 0.5 * sys[i].delta,
+                                                         scales[i].de_plus, scales[i].de_minus, vac_thr,
+                                                         0u, k0, k1, const_cast<float*>(hs[i].vt), ne + i);
+    k_init_r0<float, SORB, C><<<std::max(1, blocks), 256, 0, st>>>(ncell, hs[i].vt, 0, R, 0u, k0, k1,
+                                                                    nullptr, N, const_cast<void*>(hs[i].r0));
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(sc.grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = Sh::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int stall = ctx->debug_stall;
+    ctx->debug_stall = 0;
+    ce = cudaLaunchKernelEx(&cfg, k_batched<LAT, C>, (const BSys*)d_sys, (const BTeam*)d_teams,
+                            (const int*)d_ints, (const int*)(d_ints + sc.order.size()), counters,
+                            ctx->d_status, stall);
+  }
+  for (int i = 0; i < count && ce == cudaSuccess; ++i) {
+    const int M = kpm[i].M;
+    k_breduce<<<(M + 255) / 256, 256, 0, st>>>(hs[i].partial, M, sc.ncta_of[i], Q, R, ne + i,
+                                               d_mu + mu_off[i]);
+    ce = cudaGetLastError();
+  }
+  cudaError_t ee = cudaStreamEndCapture(st, &graph);
+  if (ce != cudaSuccess || ee != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(ctx, ce != cudaSuccess ? ce : ee, "capturing the batched graph");
+  }
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return cuda_fail(ctx, ce, "instantiating the batched graph");
+  ce = cudaEventRecord(ctx->ev0, st);
+  if (ce == cudaSuccess) ce = cudaGraphLaunch(exec, st);
+  if (ce == cudaSuccess) ce = cudaEventRecord(ctx->ev1, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  cudaGraphExecDestroy(exec);
+  if (ce != cudaSuccess) return cuda_fail(ctx, ce, "running the batched graph");
+  int status = 0;
+  KITE_CUDA_TRY(ctx, cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status) return fail(ctx, KITE_ERR_TIMEOUT, "a bounded wait gave up in the batched sweep");
+  std::vector<unsigned long long> ne_h(count);
+  KITE_CUDA_TRY(ctx, cudaMemcpy(ne_h.data(), ne, sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost));
+  // copy moments out and check them
+  std::vector<double> host(mu_total);
+  KITE_CUDA_TRY(ctx, cudaMemcpy(host.data(), d_mu, sizeof(double) * mu_total, cudaMemcpyDeviceToHost));
+  for (size_t k = 0; k < mu_total; ++k)
+    if (!std::isfinite(host[k]) || std::fabs(host[k]) > 1.0 + 1e-3)
+      return fail(ctx, KITE_ERR_BOUNDS, "a moment of the batch exceeds 1 or is not finite");
+  for (int i = 0; i < count; ++i)
+    KITE_CUDA_TRY(ctx, cudaMemcpyAsync(mu_out[i], d_mu + mu_off[i], sizeof(double) * kpm[i].M,
+                                       cudaMemcpyDefault, st));
+  KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (stats) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    double upd = 0.0, bytes = 0.0;
+    for (int i = 0; i < count; ++i) {
+      const double N = (double)sys[i].Lx * sys[i].Ly * SORB;
+      upd += (double)ne_h[i] * kpm[i].M * R;
+      bytes += (4.0 * 8.0 * R + 4.0) * N * std::max(kpm[i].M - 1, 0);
+    }
+    stats->seconds = 1e-3 * ms;
+    stats->updates = upd;
+    stats->bytes_moved = bytes;
+    stats->gbps = ms > 0 ? bytes / (1e-3 * ms) * 1e-9 : 0.0;
+    stats->grid = sc.grid;
+    stats->block = kBlock;
+    stats->step_seconds = 1e-3 * ms;
+    stats->step_launches = 1;
+    stats->step_bytes = bytes;
+    stats->n_eff = (int64_t)ne_h[count - 1];
+  }
+  return KITE_OK;
+}
+
+}  // namespace
+
+int moments_1d_batched_impl(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm* kpm,
+                            const std::vector<Scale>& scales, double* const* mu, kite_stats* st) {
+  const int R = kpm[0].R;
+  const int c = (R + 1) / 2;
+  const int C = c <= 1 ? 1 : (c <= 2 ? 2 : 4);
+  const bool hc = sys[0].lattice == KITE_HONEYCOMB;
+#define KITE_B(LATV, CC) run_batched<LATV, CC>(ctx, count, sys, kpm, scales, mu, st)
+  if (hc) return C == 1 ? KITE_B(KITE_HONEYCOMB, 1) : (C == 2 ? KITE_B(KITE_HONEYCOMB, 2) : KITE_B(KITE_HONEYCOMB, 4));
+  return C == 1 ? KITE_B(KITE_SQUARE, 1) : (C == 2 ? KITE_B(KITE_SQUARE, 2) : KITE_B(KITE_SQUARE, 4));
+#undef KITE_B
+}
+
+}  // namespace kite

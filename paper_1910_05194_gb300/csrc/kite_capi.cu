@@ -14,6 +14,8 @@ namespace kite {
 int moments_1d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
                     double* mu_dev, double* imag_dev, double* mu_vec_dev, kite_stats* st,
                     const double* r0_dev_all);
+int moments_1d_batched_impl(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm* kpm,
+                            const std::vector<Scale>& scales, double* const* mu, kite_stats* st);
 int moments_2d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
                     double* mu_nm_dev, kite_stats* st, const double* r0_dev_all);
 int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
@@ -312,6 +314,35 @@ int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   cudaFreeAsync(out_dev, ctx->stream);
   if (r0_stage) cudaFreeAsync(r0_stage, ctx->stream);
   cudaStreamSynchronize(ctx->stream);
+  if (st) *st = local;
+  return rc;
+}
+
+int kite_moments_1d_batched(kite_ctx* ctx, int count, const kite_system* systems,
+                            const kite_kpm* kpms, double* const* mu, kite_stats* st) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  if (count < 1 || !systems || !kpms || !mu) return fail(ctx, KITE_ERR_ARG, "need count >= 1 and arrays");
+  std::vector<Scale> scales(count);
+  for (int i = 0; i < count; ++i) {
+    int rc = validate_system(ctx, &systems[i]);
+    if (rc != KITE_OK) return rc;
+    const kite_kpm& k = kpms[i];
+    if (!mu[i]) return fail(ctx, KITE_ERR_ARG, "mu[" + std::to_string(i) + "] is NULL");
+    if (systems[i].lattice != systems[0].lattice)
+      return fail(ctx, KITE_ERR_ARG, "all systems of a batch must share the lattice kind");
+    if (k.precision != KITE_FP32) return fail(ctx, KITE_ERR_UNSUPPORTED, "the batched sweep is FP32");
+    if (k.R != kpms[0].R || k.R < 1 || k.R > 8)
+      return fail(ctx, KITE_ERR_ARG, "all systems need the same R, 1 <= R <= 8");
+    if (k.S != 1 || k.r0 || k.r_last)
+      return fail(ctx, KITE_ERR_ARG, "batched systems take S = 1 and no r0/r_last");
+    if (k.M < 1 || k.M > (1 << 20)) return fail(ctx, KITE_ERR_ARG, "M out of range");
+    rc = resolve_bounds(ctx, &systems[i], k.e_min, k.e_max, &scales[i]);
+    if (rc != KITE_OK) return rc;
+  }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  kite_stats local{};
+  const int rc = moments_1d_batched_impl(ctx, count, systems, kpms, scales, mu, &local);
   if (st) *st = local;
   return rc;
 }

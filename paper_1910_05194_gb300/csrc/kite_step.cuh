@@ -163,7 +163,7 @@ template <int QT, int C, typename Acc>
 __device__ __forceinline__ void moment_partials(double (&dacc)[QT], Acc (&facc)[QT],
                                                 double (&dacc0)[QT], Acc (&facc0)[QT], bool first,
                                                 unsigned char* stages, double* partial,
-                                                double* partial0) {
+                                                double* partial0, int cta) {
   const int tid = threadIdx.x;
 #pragma unroll
   for (int k = 0; k < QT; ++k) {
@@ -180,7 +180,7 @@ __device__ __forceinline__ void moment_partials(double (&dacc)[QT], Acc (&facc)[
     const int cc = tid / QT, k = tid - (tid / QT) * QT;
     double sum = 0.0;
     for (int t = cc; t < kBlock; t += C) sum += red[t][k];
-    partial[(size_t)blockIdx.x * Q + tid] = sum;
+    partial[(size_t)cta * Q + tid] = sum;
   }
   if (first) {
     __syncthreads();
@@ -191,18 +191,29 @@ __device__ __forceinline__ void moment_partials(double (&dacc)[QT], Acc (&facc)[
       const int cc = tid / QT, k = tid - (tid / QT) * QT;
       double sum = 0.0;
       for (int t = cc; t < kBlock; t += C) sum += red[t][k];
-      partial0[(size_t)blockIdx.x * Q + tid] = sum;
+      partial0[(size_t)cta * Q + tid] = sum;
     }
   }
 }
 
 
-template <typename Real, int LAT, int C, bool FIRST, int MODE = 0>
-__global__ void __launch_bounds__(kBlock, 2)
-    k_step(const void* r_prev, const void* __restrict__ r_cur, void* r_out,
-           const void* __restrict__ r0, const Real* __restrict__ vt, Real tt, int Lx, int Ly,
-           long long units, double* __restrict__ partial, double* __restrict__ partial0,
-           int* __restrict__ err, int stall, const FamOut fam) {
+// Per-CTA state of the shared-memory ring; a persistent launch keeps it across steps.
+struct Ring {
+  uint64_t* bars;
+  unsigned char* stages;
+  int* abort;        // shared flag: a bounded wait gave up
+  long long gslot;   // slots consumed so far (phase bookkeeping of the ring)
+};
+
+// One recursion step over this CTA's share [cta/ncta] of the units.  Returns false if a
+// bounded wait gave up (the CTA has drained its copies and set *err; stop using the ring).
+template <typename Real, int LAT, int C, bool FIRST, int MODE>
+__device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const void* r_prev,
+                                          const void* __restrict__ r_cur, void* r_out,
+                                          const void* __restrict__ r0, const Real* __restrict__ vt,
+                                          Real tt, int Lx, int Ly, long long units,
+                                          double* __restrict__ partial, double* __restrict__ partial0,
+                                          int* __restrict__ err, int stall, const FamOut& fam) {
   static_assert(MODE == 0 || (sizeof(Real) == 4 && C * 2 <= kMaxFamVecs),
                 "family modes run on FP32 batches of at most two vectors");
   using Ch = Chunk<Real>;
@@ -211,10 +222,9 @@ __global__ void __launch_bounds__(kBlock, 2)
   constexpr int VPC = Ch::kVecs, NR = Ch::kReals;
   constexpr int SORB = Sh::SORB, TPC = Sh::TPC, TX = Sh::TX, CELLB = Sh::CELLB;
   constexpr int QT = 2 * VPC;  // (re, im) per vector held by one thread
-  extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-  unsigned char* stages = smem + kBarBytes;
-  __shared__ int s_abort;
+  uint64_t* bars = ring.bars;
+  unsigned char* stages = ring.stages;
+  int& s_abort = *ring.abort;
 
   const int tid = threadIdx.x;
   const int xl = tid / TPC;
@@ -224,22 +234,17 @@ __global__ void __launch_bounds__(kBlock, 2)
   const int choff = (s * C + c) * 16;             // this thread's chunk inside a cell
   const int nboff = ((1 - s) * C + c) * 16;       // same chunk, other sublattice
 
-  if (tid == 0) {
-    for (int k = 0; k < kStages; ++k) mbar_init(&bars[k], 1);
-    mbar_fence_init();
-    s_abort = 0;
-  }
-  __syncthreads();
+  __syncthreads();  // the ring (and its reuse for the previous step's reduction) is free
 
-  const long long u0 = units * (long long)blockIdx.x / gridDim.x;
-  const long long u1 = units * (long long)(blockIdx.x + 1) / gridDim.x;
+  const long long u0 = units * (long long)cta / ncta;
+  const long long u1 = units * (long long)(cta + 1) / ncta;
 
   double dacc[QT], dacc0[QT];
   Acc facc[QT], facc0[QT];
 #pragma unroll
   for (int k = 0; k < QT; ++k) dacc[k] = dacc0[k] = 0.0, facc[k] = facc0[k] = Acc(0);
   int rows = 0;
-  long long gslot = 0;  // slots consumed so far (phase bookkeeping of the ring)
+  long long gslot = ring.gslot;
   bool aborted = false;
 
   for (long long u = u0; u < u1 && !aborted;) {
@@ -263,7 +268,7 @@ __global__ void __launch_bounds__(kBlock, 2)
       const uint32_t main_b = (uint32_t)txv * CELLB;
       // r_0 is only staged when moments are accumulated (MODE 0)
       uint32_t bytes = main_b + 2 * CELLB + (interior ? (MODE == 0 ? 2 : 1) * main_b : 0);
-      if (stall && blockIdx.x == 0 && g == 0) bytes += 16;  // test hook: never completes
+      if (stall && cta == 0 && g == 0) bytes += 16;  // test hook: never completes
       mbar_arrive_expect_tx(&bars[st], bytes);
       const unsigned char* rowp = static_cast<const unsigned char*>(r_cur) + (size_t)row * Lx * CELLB;
       bulk_g2s(base + CELLB, rowp + (size_t)x0 * CELLB, main_b, &bars[st]);
@@ -393,12 +398,35 @@ __global__ void __launch_bounds__(kBlock, 2)
         }
         atomicExch(err, 1);
       }
-      return;
+      ring.gslot = gslot;
+      return false;
     }
     gslot += nslots;
     u += nr;
   }
-  if constexpr (MODE == 0) moment_partials<QT, C>(dacc, facc, dacc0, facc0, FIRST, stages, partial, partial0);
+  ring.gslot = gslot;
+  if constexpr (MODE == 0)
+    moment_partials<QT, C>(dacc, facc, dacc0, facc0, FIRST, stages, partial, partial0, cta);
+  return true;
+}
+
+template <typename Real, int LAT, int C, bool FIRST, int MODE = 0>
+__global__ void __launch_bounds__(kBlock, 2)
+    k_step(const void* r_prev, const void* __restrict__ r_cur, void* r_out,
+           const void* __restrict__ r0, const Real* __restrict__ vt, Real tt, int Lx, int Ly,
+           long long units, double* __restrict__ partial, double* __restrict__ partial0,
+           int* __restrict__ err, int stall, const FamOut fam) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_abort;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kStages; ++k) mbar_init(&bars[k], 1);
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  Ring ring{bars, smem + kBarBytes, &s_abort, 0};
+  step_body<Real, LAT, C, FIRST, MODE>(ring, blockIdx.x, gridDim.x, r_prev, r_cur, r_out, r0, vt,
+                                       tt, Lx, Ly, units, partial, partial0, err, stall, fam);
 }
 
 // Copies one iterate buffer (batch layout) into the caller layout [vec][slot][N].

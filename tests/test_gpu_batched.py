@@ -1,0 +1,72 @@
+"""GPU parity of the batched persistent sweep (kite_moments_1d_batched): every system of a
+mixed batch against the oracle (FP32 recursion, bar 1e-5), the bounded team barrier, and
+the 256-system square-lattice workload (side 64..1024, W 0..4, M in {512..4096}, R = 4) in
+its own launch configuration with sampled oracle checks and properties for the rest."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+kite = pytest.importorskip("paper_1910_05194_gb300")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = kite.Context(0)
+    yield c
+    c.close()
+
+
+def batch(ctx, specs, R=4):
+    systems = [kite.make_system(kite.SQUARE, sp["L"], sp.get("Ly", sp["L"]), -1.0, sp["W"], 0.0,
+                                sp.get("p", 0.0), sp["seed"]) for sp in specs]
+    kpms = [kite.make_kpm(sp["M"], R, 1, kite.FP32) for sp in specs]
+    mus = [np.zeros(sp["M"]) for sp in specs]
+    st = kite.moments_1d_batched(ctx, systems, kpms, mus)
+    return mus, st
+
+
+def oracle_mu(sp, R=4):
+    s = oracle.make_system(lattice=oracle.SQUARE, Lx=sp["L"], Ly=sp.get("Ly", sp["L"]), t=-1.0,
+                           W=sp["W"], p_vac=sp.get("p", 0.0), seed=sp["seed"])
+    return oracle.moments_1d(s, sp["M"], R).real.mean(0)
+
+
+def test_mixed_batch_against_oracle(ctx):
+    specs = [dict(L=400, Ly=300, W=1.0, M=96, seed=11),  # large: a multi-CTA team
+             dict(L=3, W=2.0, M=16, seed=12), dict(L=17, Ly=5, W=0.0, M=33, seed=13),
+             dict(L=130, W=4.0, M=64, seed=14, p=0.02), dict(L=64, W=2.5, M=128, seed=15),
+             dict(L=257, Ly=40, W=3.0, M=48, seed=16), dict(L=9, W=1.0, M=1, seed=17),
+             dict(L=100, W=0.5, M=2, seed=18), dict(L=77, W=3.5, M=200, seed=19)]
+    mus, st = batch(ctx, specs)
+    for sp, mu in zip(specs, mus):
+        ref = oracle_mu(sp)
+        assert np.max(np.abs(mu - ref)) <= 1e-5, sp
+    assert st.grid >= 2 and st.seconds > 0
+
+
+def test_team_barrier_timeout_is_reported(ctx):
+    specs = [dict(L=600, W=1.0, M=24, seed=21), dict(L=20, W=1.0, M=8, seed=22)]
+    kite.debug_stall_once(ctx)
+    with pytest.raises(kite.KiteError) as e:
+        batch(ctx, specs)
+    assert e.value.status == kite.ERR_TIMEOUT
+    mus, _ = batch(ctx, specs)  # the context stays usable
+    assert np.max(np.abs(mus[1] - oracle_mu(specs[1]))) <= 1e-5
+
+
+def test_256_system_workload(ctx):
+    specs = synth.batched_square_systems(256, seed=3)
+    mus, st = batch(ctx, specs)
+    print(f"256 systems: {st.updates:.3e} updates in {st.seconds:.3f} s = "
+          f"{st.updates / st.seconds:.3e} updates/s, grid {st.grid}")
+    for sp, mu in zip(specs, mus):
+        assert abs(mu[0] - 1.0) <= 1e-6
+        assert np.all(np.abs(mu) <= 1.0)
+    # the systems the CPU oracle finishes quickly: every moment
+    cheap = sorted(range(256), key=lambda i: specs[i]["L"] ** 2 * specs[i]["M"])[:6]
+    for i in cheap:
+        assert np.max(np.abs(mus[i] - oracle_mu(specs[i]))) <= 1e-5, specs[i]

@@ -83,4 +83,9 @@ def test_host_and_device_buffers(ctx):
     C = C[..., 0] + 1j * C[..., 1]
     ref = oracle.inner_products(A, B)
     bound = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64).T
-    assert np.all(np.abs(C - ref) <= 2.0**-13 * bound)
+    Ch = np.zeros((M, M2), np.complex128)
+    kite.inner_products(ctx, A, B, M, M2, N, 1.0, Ch)  # host buffers, same inputs
+    ratio = np.abs(C - ref) / (2.0**-13 * bound)
+    worst = np.unravel_index(np.argmax(ratio), ratio.shape)
+    assert np.max(ratio) <= 1.0, (worst, C[worst], Ch[worst], ref[worst])
+    assert np.max(np.abs(C - Ch)) <= 1e-12 * np.max(np.abs(ref))

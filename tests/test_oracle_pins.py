@@ -464,3 +464,32 @@ def test_sigma_matches_eigenstate_kubo_bastin():
         ref = 1j * c / w * (S1 + S2) / n
         assert abs(sig[i] - ref) < 1e-7 * abs(ref), (om, sig[i], ref)
         assert sig[i].real > 0  # absorption
+
+
+def test_mlp_gradient_matches_finite_differences():
+    """The reference MLP's analytic gradient against central differences in FP64 (small
+    widths; points kept away from the ReLU and |.| kinks)."""
+    from oracle import mlp
+    ni, nh, no = 7, 9, 5
+    p = mlp.init_params(3, ni, nh, no) + 0.01
+    g = np.random.Generator(np.random.PCG64(4))
+    X = g.standard_normal((6, ni))
+    T = g.standard_normal((6, no)) * 3.0
+    an = mlp.grad(p, X, T, ni, nh, no)
+    h = 1e-6
+    idx = g.choice(p.size, 60, replace=False)
+    for k in idx:
+        e = np.zeros_like(p)
+        e[k] = h
+        fd = (mlp.loss(p + e, X, T, ni, nh, no) - mlp.loss(p - e, X, T, ni, nh, no)) / (2 * h)
+        assert abs(fd - an[k]) <= 1e-6 * max(1.0, abs(an[k])), k
+
+
+def test_mlp_adamw_first_step_is_sign_step():
+    """First AdamW step with bias correction moves each parameter by lr*(sign(g) + wd*p)
+    (up to eps): the definition's fixed point."""
+    from oracle import mlp
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -1e-3, 2.0])
+    p1, m, v = mlp.adamw_step(p, g, np.zeros(3), np.zeros(3), 1, lr=0.01, wd=0.1, eps=1e-12)
+    assert np.allclose(p1, p - 0.01 * (np.sign(g) + 0.1 * p), atol=1e-10)
