@@ -230,6 +230,58 @@ int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, in
 int kite_moments_1d_batched(kite_ctx* ctx, int count, const kite_system* systems,
                             const kite_kpm* kpms, double* const* mu, kite_stats* st);
 
+/* ---- learned reconstruction (no counterpart in the paper) -------------------------- */
+
+/* A multilayer perceptron KITE_MLP_IN -> KITE_MLP_HIDDEN -> KITE_MLP_HIDDEN -> KITE_MLP_OUT
+ * (ReLU, BF16 weights and activations, FP32 accumulation on the tensor cores) that maps the
+ * first KITE_MLP_IN Chebyshev moments of a system to its density of states on
+ * KITE_MLP_OUT energies reconstructed from many more moments (the resolution of the
+ * reconstruction scales as the inverse number of moments, Sec. 2a).  Parameters are one
+ * flat FP32 vector W1[H][IN], b1[H], W2[H][H], b2[H], W3[OUT][H], b3[OUT] (row-major).
+ * Inputs are multiplied by the per-column `scale` [IN] (NULL = 1) on the device.  All
+ * pointers may be host or device memory. */
+#define KITE_MLP_IN 128
+#define KITE_MLP_HIDDEN 512
+#define KITE_MLP_OUT 1024
+
+typedef struct {
+  int32_t epochs;       /* passes over the training set                      */
+  int32_t batch;        /* rows per optimiser step                           */
+  double lr;            /* peak learning rate (cosine schedule to zero)      */
+  double weight_decay;  /* AdamW decoupled weight decay                      */
+  uint64_t seed;        /* shuffling                                         */
+} kite_mlp_train_cfg;
+
+/* Number of FP32 parameters of the network. */
+int64_t kite_mlp_param_count(void);
+
+/* Trains in place: mean-absolute-error loss over X [n][IN] -> T [n][OUT], AdamW
+ * (beta 0.9/0.999, eps 1e-8) on FP32 master weights, hand-written forward and backward
+ * kernels.  params [P] holds the initial weights on entry and the trained ones on exit;
+ * loss_curve [epochs] (or NULL) receives the mean training loss of each epoch.
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
+int kite_mlp_train(kite_ctx* ctx, const float* X, const float* T, int n, const float* scale,
+                   const kite_mlp_train_cfg* cfg, float* params, float* loss_curve);
+
+/* Y [n][OUT] = network(X [n][IN] * scale).  Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
+int kite_mlp_forward(kite_ctx* ctx, const float* params, const float* X, int n,
+                     const float* scale, float* Y);
+
+/* Gradient [P] of the mean absolute error over all n x OUT outputs (for checks), and the
+ * loss.  Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
+int kite_mlp_gradient(kite_ctx* ctx, const float* params, const float* X, const float* T, int n,
+                      const float* scale, float* grad, double* loss);
+
+/* Label-free consistency gate of predicted densities rho [n][OUT] (per eV, on the midpoint
+ * grid eps_j = -1 + (2j+1)/OUT of the rescaled energy): the Chebyshev moments
+ * m_k = int rho(eps) T_k(eps) d eps (midpoint rule) must match the known moments
+ * mu [n][mu_ld] for k < kcheck within tol; flags[b] = 1 marks a prediction to replace by
+ * the plain reconstruction.  deviation [n] (or NULL) receives max_k |m_k - mu_k|.
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
+int kite_learned_gate(kite_ctx* ctx, const float* rho, const double* mu, int mu_ld, int n,
+                      int kcheck, double e_min, double e_max, double tol, int* flags,
+                      double* deviation);
+
 /* ---- 1D moments without allocation (no counterpart in the paper) ------------------ */
 
 /* kite_moments_1d for callers that cannot allocate device memory at the moment they need

@@ -25,7 +25,10 @@ KERNEL_NONE, KERNEL_JACKSON, KERNEL_LORENTZ = 0, 1, 2
 EXPORTED = ("kite_create", "kite_destroy", "kite_set_stream", "kite_status_string",
             "kite_last_error", "kite_bounds", "kite_moments_1d", "kite_reconstruct_dos",
             "kite_debug_stall_once", "kite_inner_products", "kite_moments_2d",
-            "kite_reconstruct_sigma", "kite_moments_1d_static", "kite_moments_1d_batched")
+            "kite_reconstruct_sigma", "kite_moments_1d_static", "kite_moments_1d_batched",
+            "kite_mlp_param_count", "kite_mlp_train", "kite_mlp_forward", "kite_mlp_gradient",
+            "kite_learned_gate")
+MLP_IN, MLP_HIDDEN, MLP_OUT = 128, 512, 1024
 
 
 class KiteError(RuntimeError):
@@ -60,6 +63,12 @@ class Stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class MLPTrainCfg(ctypes.Structure):
+    """``kite_mlp_train_cfg``."""
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_double),
+                ("weight_decay", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
 def make_system(lattice=HONEYCOMB, Lx=64, Ly=64, t=-2.7, W=0.0, delta=0.0, p_vac=0.0, seed=1):
@@ -110,6 +119,16 @@ def lib():
             L.kite_moments_1d_static.restype = i32
             L.kite_moments_1d_batched.argtypes = [vp, i32, P(System), P(KPM), P(vp), P(Stats)]
             L.kite_moments_1d_batched.restype = i32
+            L.kite_mlp_param_count.argtypes = []
+            L.kite_mlp_param_count.restype = ctypes.c_int64
+            L.kite_mlp_train.argtypes = [vp, vp, vp, i32, vp, P(MLPTrainCfg), vp, vp]
+            L.kite_mlp_train.restype = i32
+            L.kite_mlp_forward.argtypes = [vp, vp, vp, i32, vp, vp]
+            L.kite_mlp_forward.restype = i32
+            L.kite_mlp_gradient.argtypes = [vp, vp, vp, vp, i32, vp, vp, P(d)]
+            L.kite_mlp_gradient.restype = i32
+            L.kite_learned_gate.argtypes = [vp, vp, vp, i32, i32, i32, d, d, d, vp, vp]
+            L.kite_learned_gate.restype = i32
             L.kite_moments_2d.argtypes = [vp, P(System), P(KPM), vp, P(Stats)]
             L.kite_moments_2d.restype = i32
             L.kite_inner_products.argtypes = [vp, vp, vp, i32, i32, ctypes.c_int64, d, vp, i32, i32]
@@ -260,3 +279,33 @@ def moments_1d_batched(ctx: Context, systems, kpms, mus) -> Stats:
     st = Stats()
     ctx.check(lib().kite_moments_1d_batched(ctx.handle, n, sa, ka, pa, ctypes.byref(st)))
     return st
+
+
+def mlp_param_count() -> int:
+    return int(lib().kite_mlp_param_count())
+
+
+def mlp_train(ctx: Context, X, T, n: int, params, epochs=50, batch=256, lr=1e-3, weight_decay=1e-4,
+              seed=0, scale=None, loss_curve=None):
+    """kite_mlp_train: trains `params` (FP32 [P]) in place on X [n][IN] -> T [n][OUT]."""
+    cfg = MLPTrainCfg(int(epochs), int(batch), float(lr), float(weight_decay), int(seed))
+    ctx.check(lib().kite_mlp_train(ctx.handle, _addr(X), _addr(T), int(n), _addr(scale),
+                                   ctypes.byref(cfg), _addr(params), _addr(loss_curve)))
+
+
+def mlp_forward(ctx: Context, params, X, n: int, Y, scale=None):
+    ctx.check(lib().kite_mlp_forward(ctx.handle, _addr(params), _addr(X), int(n), _addr(scale), _addr(Y)))
+
+
+def mlp_gradient(ctx: Context, params, X, T, n: int, grad, scale=None) -> float:
+    loss = ctypes.c_double()
+    ctx.check(lib().kite_mlp_gradient(ctx.handle, _addr(params), _addr(X), _addr(T), int(n),
+                                      _addr(scale), _addr(grad), ctypes.byref(loss)))
+    return loss.value
+
+
+def learned_gate(ctx: Context, rho, mu, mu_ld: int, n: int, kcheck: int, e_min: float, e_max: float,
+                 tol: float, flags, deviation=None):
+    ctx.check(lib().kite_learned_gate(ctx.handle, _addr(rho), _addr(mu), int(mu_ld), int(n), int(kcheck),
+                                      float(e_min), float(e_max), float(tol), _addr(flags),
+                                      _addr(deviation)))

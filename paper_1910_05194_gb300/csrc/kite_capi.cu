@@ -14,6 +14,14 @@ namespace kite {
 int moments_1d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
                     double* mu_dev, double* imag_dev, double* mu_vec_dev, kite_stats* st,
                     const double* r0_dev_all);
+int64_t mlp_param_count();
+int mlp_gradient_impl(kite_ctx* ctx, const float* params, const float* X, const float* T, int n,
+                      const float* scale, float* grad, double* loss);
+int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, const float* scale, float* Y);
+int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const float* scale,
+                   const kite_mlp_train_cfg* cfg, float* params, float* loss_curve);
+int mlp_gate_impl(kite_ctx* ctx, const float* rho, const double* mu, int mu_ld, int n, int kcheck,
+                  double de_minus, double tol, int* flags, double* dev);
 int moments_1d_batched_impl(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm* kpm,
                             const std::vector<Scale>& scales, double* const* mu, kite_stats* st);
 int moments_2d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
@@ -128,6 +136,47 @@ int resolve_bounds(kite_ctx* ctx, const kite_system* sys, double e_min, double e
   sc->de_minus = 0.5 * (e_max - e_min);
   return KITE_OK;
 }
+
+// Device views of caller buffers: device pointers pass through; host buffers are staged
+// in one stream-ordered allocation released at the end of the call.
+struct Staging {
+  kite_ctx* ctx;
+  std::vector<void*> owned;
+  ~Staging() {
+    for (void* p : owned) cudaFreeAsync(p, ctx->stream);
+  }
+  template <typename T>
+  int in(const T* src, size_t count, const T** out) {
+    if (!src || is_device_ptr(src)) {
+      *out = src;
+      return KITE_OK;
+    }
+    void* d = nullptr;
+    KITE_CUDA_TRY(ctx, cudaMallocAsync(&d, sizeof(T) * std::max<size_t>(count, 1), ctx->stream));
+    owned.push_back(d);
+    KITE_CUDA_TRY(ctx, copy_in(ctx, d, src, sizeof(T) * count));
+    *out = static_cast<const T*>(d);
+    return KITE_OK;
+  }
+  template <typename T>
+  int out(T* dst, size_t count, T** dev) {
+    if (!dst || is_device_ptr(dst)) {
+      *dev = dst;
+      return KITE_OK;
+    }
+    void* d = nullptr;
+    KITE_CUDA_TRY(ctx, cudaMallocAsync(&d, sizeof(T) * std::max<size_t>(count, 1), ctx->stream));
+    owned.push_back(d);
+    *dev = static_cast<T*>(d);
+    return KITE_OK;
+  }
+  template <typename T>
+  int back(T* dst, const T* dev, size_t count) {
+    if (!dst || dst == dev) return KITE_OK;
+    KITE_CUDA_TRY(ctx, copy_out(ctx, dst, dev, sizeof(T) * count));
+    return KITE_OK;
+  }
+};
 
 }  // namespace kite
 
@@ -315,6 +364,86 @@ int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   if (r0_stage) cudaFreeAsync(r0_stage, ctx->stream);
   cudaStreamSynchronize(ctx->stream);
   if (st) *st = local;
+  return rc;
+}
+
+int64_t kite_mlp_param_count(void) { return mlp_param_count(); }
+
+int kite_mlp_train(kite_ctx* ctx, const float* X, const float* T, int n, const float* scale,
+                   const kite_mlp_train_cfg* cfg, float* params, float* loss_curve) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  if (!X || !T || !cfg || !params || n < 1 || cfg->epochs < 1 || cfg->batch < 1 || !(cfg->lr > 0.0) ||
+      !(cfg->weight_decay >= 0.0))
+    return fail(ctx, KITE_ERR_ARG, "need X, T, params, n >= 1 and a valid configuration");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  Staging sg{ctx, {}};
+  const float *Xd, *Td, *Sd;
+  int rc = sg.in(X, (size_t)n * KITE_MLP_IN, &Xd);
+  if (rc == KITE_OK) rc = sg.in(T, (size_t)n * KITE_MLP_OUT, &Td);
+  if (rc == KITE_OK) rc = sg.in(scale, KITE_MLP_IN, &Sd);
+  std::vector<float> curve(cfg->epochs);
+  if (rc == KITE_OK) rc = mlp_train_impl(ctx, Xd, Td, n, Sd, cfg, params, curve.data());
+  if (rc == KITE_OK && loss_curve) std::copy(curve.begin(), curve.end(), loss_curve);
+  cudaStreamSynchronize(ctx->stream);
+  return rc;
+}
+
+int kite_mlp_forward(kite_ctx* ctx, const float* params, const float* X, int n, const float* scale,
+                     float* Y) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  if (!params || !X || !Y || n < 1) return fail(ctx, KITE_ERR_ARG, "need params, X, Y and n >= 1");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  Staging sg{ctx, {}};
+  const float *Xd, *Sd;
+  float* Yd;
+  int rc = sg.in(X, (size_t)n * KITE_MLP_IN, &Xd);
+  if (rc == KITE_OK) rc = sg.in(scale, KITE_MLP_IN, &Sd);
+  if (rc == KITE_OK) rc = sg.out(Y, (size_t)n * KITE_MLP_OUT, &Yd);
+  if (rc == KITE_OK) rc = mlp_forward_impl(ctx, params, Xd, n, Sd, Yd);
+  if (rc == KITE_OK) rc = sg.back(Y, Yd, (size_t)n * KITE_MLP_OUT);
+  cudaStreamSynchronize(ctx->stream);
+  return rc;
+}
+
+int kite_mlp_gradient(kite_ctx* ctx, const float* params, const float* X, const float* T, int n,
+                      const float* scale, float* grad, double* loss) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  if (!params || !X || !T || !grad || n < 1) return fail(ctx, KITE_ERR_ARG, "need params, X, T, grad, n >= 1");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  Staging sg{ctx, {}};
+  const float *Xd, *Td, *Sd;
+  int rc = sg.in(X, (size_t)n * KITE_MLP_IN, &Xd);
+  if (rc == KITE_OK) rc = sg.in(T, (size_t)n * KITE_MLP_OUT, &Td);
+  if (rc == KITE_OK) rc = sg.in(scale, KITE_MLP_IN, &Sd);
+  if (rc == KITE_OK) rc = mlp_gradient_impl(ctx, params, Xd, Td, n, Sd, grad, loss);
+  cudaStreamSynchronize(ctx->stream);
+  return rc;
+}
+
+int kite_learned_gate(kite_ctx* ctx, const float* rho, const double* mu, int mu_ld, int n,
+                      int kcheck, double e_min, double e_max, double tol, int* flags,
+                      double* deviation) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  if (!rho || !mu || !flags || n < 1 || kcheck < 1 || mu_ld < kcheck || !(e_max > e_min) || !(tol >= 0.0))
+    return fail(ctx, KITE_ERR_ARG, "need rho, mu, flags, n >= 1, 1 <= kcheck <= mu_ld");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  Staging sg{ctx, {}};
+  const float* rd;
+  const double* md;
+  int* fd;
+  double* dd;
+  int rc = sg.in(rho, (size_t)n * KITE_MLP_OUT, &rd);
+  if (rc == KITE_OK) rc = sg.in(mu, (size_t)n * mu_ld, &md);
+  if (rc == KITE_OK) rc = sg.out(flags, (size_t)n, &fd);
+  if (rc == KITE_OK) rc = sg.out(deviation, (size_t)n, &dd);
+  if (rc == KITE_OK) rc = mlp_gate_impl(ctx, rd, md, mu_ld, n, kcheck, 0.5 * (e_max - e_min), tol, fd, dd);
+  if (rc == KITE_OK) rc = sg.back(flags, fd, (size_t)n);
+  if (rc == KITE_OK && deviation) rc = sg.back(deviation, dd, (size_t)n);
+  cudaStreamSynchronize(ctx->stream);
   return rc;
 }
 

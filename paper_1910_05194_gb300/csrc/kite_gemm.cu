@@ -443,7 +443,7 @@ int plan_gemm_splits(kite_ctx* ctx, int Mrows, int Nrows, int64_t Kp) {
 
 int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void* Bhi,
                     const void* Blo, int Mrows, int Nrows, int64_t Kp, int S, int sub_kb,
-                    int nprod, double* part) {
+                    int nprod, double* part, int* S_used) {
   if (Kp % kBK != 0) return fail(ctx, KITE_ERR_ARG, "K must be padded to a multiple of 64");
   CUtensorMap mAh, mAl, mBh, mBl;
   int rc;
@@ -457,8 +457,9 @@ int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void*
   a.kb_total = (int)(Kp / kBK);
   a.S = std::max(1, std::min(S, a.kb_total));
   a.kb_per_item = (a.kb_total + a.S - 1) / a.S;
-  a.S = (a.kb_total + a.kb_per_item - 1) / a.kb_per_item;
+  a.S = (a.kb_total + a.kb_per_item - 1) / a.kb_per_item;  // every split has >= 1 K block
   a.items = a.S * a.T;
+  *S_used = a.S;  // the reduction must sum exactly the splits written here
   a.sub_kb = std::max(1, sub_kb);
   a.nprod = nprod == 3 ? 3 : 4;
   a.Mrows = Mrows;
@@ -517,9 +518,10 @@ int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, in
   k_split_rows<<<blocks, 256, 0, ctx->stream>>>(reinterpret_cast<const float2*>(B), M2, N, Kp, M2, 1, Bhi, Blo);
   KITE_CUDA_TRY(ctx, cudaGetLastError());
   KITE_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
-  rc = gemm_split_bf16(ctx, Ahi, Alo, Bhi, Blo, M, Nrows, Kp, S, sub_kb, nprod, part);
+  int S_used = 0;
+  rc = gemm_split_bf16(ctx, Ahi, Alo, Bhi, Blo, M, Nrows, Kp, S, sub_kb, nprod, part, &S_used);
   if (rc != KITE_OK) return rc;
-  return reduce_cplx(ctx, part, S, M, M2, scale, C, false);
+  return reduce_cplx(ctx, part, S_used, M, M2, scale, C, false);
 }
 
 }  // namespace kite

@@ -17,7 +17,7 @@ namespace kite {
 int plan_gemm_splits(kite_ctx* ctx, int Mrows, int Nrows, int64_t Kp);
 int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void* Bhi,
                     const void* Blo, int Mrows, int Nrows, int64_t Kp, int S, int sub_kb,
-                    int nprod, double* part);
+                    int nprod, double* part, int* S_used);
 int reduce_cplx(kite_ctx* ctx, const double* part, int S, int M, int M2, double scale,
                 double* out, bool accumulate);
 
@@ -208,10 +208,11 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
       // contraction, one vector at a time, accumulated in FP64
       KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
       for (int v = 0; v < nvec; ++v) {
+        int S_used = 0;
         int rc = gemm_split_bf16(ctx, Ah[v], Al[v], Bh[v], Bl[v], M, 2 * M, Kp, Sg, kGemmSubKb,
-                                 kGemmProducts, part);
+                                 kGemmProducts, part, &S_used);
         if (rc != KITE_OK) return rc;
-        rc = reduce_cplx(ctx, part, Sg, M, M, scale, mu_nm_dev, true);
+        rc = reduce_cplx(ctx, part, S_used, M, M, scale, mu_nm_dev, true);
         if (rc != KITE_OK) return rc;
       }
       KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));

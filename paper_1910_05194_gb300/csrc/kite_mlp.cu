@@ -1,0 +1,388 @@
+// kite_mlp.cu -- the learned DOS reconstructor: a multilayer perceptron IN -> H -> H -> OUT
+// (ReLU, BF16 weights/activations, FP32 accumulation) trained with a mean-absolute-error
+// loss and AdamW on FP32 master weights, all in this file's kernels.
+//
+// The paper has no learned component; its Sec. 2a notes that the energy resolution of the
+// Chebyshev reconstruction scales as the inverse number of moments.  The network maps the
+// first IN moments of a system to its density of states on OUT energies as reconstructed
+// from many more moments.  A label-free consistency gate recomputes the low Chebyshev
+// moments of the predicted density and flags predictions that disagree with the input.
+//
+// Parameter layout (one flat FP32 vector): W1[H][IN], b1[H], W2[H][H], b2[H], W3[OUT][H],
+// b3[OUT], row-major.
+#include <cuda_bf16.h>
+#include <mma.h>
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <random>
+#include <vector>
+
+#include "kite_internal.h"
+
+namespace kite {
+namespace {
+
+constexpr int IN = KITE_MLP_IN, HID = KITE_MLP_HIDDEN, OUT = KITE_MLP_OUT;
+constexpr int64_t kOffW1 = 0, kOffB1 = kOffW1 + (int64_t)HID * IN, kOffW2 = kOffB1 + HID,
+                  kOffB2 = kOffW2 + (int64_t)HID * HID, kOffW3 = kOffB2 + HID,
+                  kOffB3 = kOffW3 + (int64_t)OUT * HID, kParams = kOffB3 + OUT;
+
+// ------------------------------------------------------------------------------------
+// GEMM on the tensor cores (BF16 in, FP32 accumulate): C[m][n] = sum_k A(m,k) B(k,n)
+//   A(m,k) = transA ? A[k*lda + m] : A[m*lda + k];  B(k,n) = transB ? B[n*ldb + k] : B[k*ldb + n]
+// Epilogue: + bias[n]; relu; mask by mask[m][n] > 0; store FP32 (C32) and/or BF16 (C16).
+// 64x64 CTA tile, 4 warps of 32x32 (2x2 WMMA 16x16x16 fragments), K step 32 via smem.
+// ------------------------------------------------------------------------------------
+struct GemmEpi {
+  const float* bias;
+  const __nv_bfloat16* mask;
+  int relu;
+  float* C32;
+  __nv_bfloat16* C16;
+  int ldc;
+  float alpha;
+};
+
+__global__ void __launch_bounds__(128) k_mlp_gemm(const __nv_bfloat16* __restrict__ A, int lda, int transA,
+                                                  const __nv_bfloat16* __restrict__ B, int ldb, int transB,
+                                                  int M, int N, int K, const GemmEpi ep) {
+  using namespace nvcuda;
+  constexpr int BM = 64, BN = 64, BK = 32, PA = BK + 8, PB = BN + 8, PC = BN + 4;
+  __shared__ __align__(32) __nv_bfloat16 As[BM][PA];
+  __shared__ __align__(32) __nv_bfloat16 Bs[BK][PB];
+  __shared__ __align__(32) float Cs[BM][PC];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) wmma::fill_fragment(acc[i][j], 0.0f);
+  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += 128) {
+      const int r = transA ? e % BM : e / BK, c = transA ? e / BM : e % BK;
+      const int gm = m0 + r, gk = k0 + c;
+      As[r][c] = (gm < M && gk < K) ? (transA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk]) : zero;
+    }
+    for (int e = tid; e < BK * BN; e += 128) {
+      const int r = transB ? e % BK : e / BN, c = transB ? e / BK : e % BN;
+      const int gk = k0 + r, gn = n0 + c;
+      Bs[r][c] = (gk < K && gn < N) ? (transB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn]) : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 16) {
+      wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, wmma::row_major> fa[2];
+      wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, wmma::row_major> fb[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) wmma::load_matrix_sync(fa[i], &As[wm + 16 * i][kk], PA);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) wmma::load_matrix_sync(fb[j], &Bs[kk][wn + 16 * j], PB);
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+      wmma::store_matrix_sync(&Cs[wm + 16 * i][wn + 16 * j], acc[i][j], PC, wmma::mem_row_major);
+  __syncthreads();
+  for (int e = tid; e < BM * BN; e += 128) {
+    const int r = e / BN, c = e % BN, gm = m0 + r, gn = n0 + c;
+    if (gm >= M || gn >= N) continue;
+    float v = ep.alpha * Cs[r][c];
+    if (ep.bias) v += ep.bias[gn];
+    if (ep.relu) v = fmaxf(v, 0.0f);
+    if (ep.mask && !(__bfloat162float(ep.mask[(int64_t)gm * ep.ldc + gn]) > 0.0f)) v = 0.0f;
+    if (ep.C32) ep.C32[(int64_t)gm * ep.ldc + gn] = v;
+    if (ep.C16) ep.C16[(int64_t)gm * ep.ldc + gn] = __float2bfloat16(v);
+  }
+}
+
+// rows of X (FP32, optional per-column scale) gathered by idx -> BF16
+__global__ void k_mlp_gather(const float* __restrict__ X, const int* __restrict__ idx, int rows, int cols,
+                             const float* __restrict__ scale, __nv_bfloat16* __restrict__ out,
+                             const float* __restrict__ T, float* __restrict__ Tout, int tcols) {
+  const int64_t total = (int64_t)rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / cols), c = (int)(e % cols);
+    const int64_t src = idx ? idx[r] : r;
+    out[e] = __float2bfloat16(X[src * cols + c] * (scale ? scale[c] : 1.0f));
+  }
+  if (T) {
+    const int64_t tt = (int64_t)rows * tcols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tt; e += (int64_t)gridDim.x * blockDim.x) {
+      const int r = (int)(e / tcols), c = (int)(e % tcols);
+      const int64_t src = idx ? idx[r] : r;
+      Tout[e] = T[src * tcols + c];
+    }
+  }
+}
+
+// dY = sign(Y - T) / count (BF16) and the partial L1 sums per block
+__global__ void k_mlp_l1grad(const float* __restrict__ Y, const float* __restrict__ T, int64_t n,
+                             float inv_count, __nv_bfloat16* __restrict__ dY, double* __restrict__ lsum) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const float d = Y[e] - T[e];
+    dY[e] = __float2bfloat16(d > 0.f ? inv_count : (d < 0.f ? -inv_count : 0.f));
+    s += fabs((double)d);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) lsum[blockIdx.x] = red[0];
+}
+
+// db[n] = sum_m D[m][n] in fixed order (one thread per column)
+__global__ void k_mlp_colsum(const __nv_bfloat16* __restrict__ D, int M, int N, float* __restrict__ db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int m = 0; m < M; ++m) s += __bfloat162float(D[(int64_t)m * N + n]);
+  db[n] = s;
+}
+
+// AdamW (decoupled weight decay) on FP32 master weights; refreshes the BF16 copy
+__global__ void k_mlp_adamw(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, __nv_bfloat16* __restrict__ pb, int64_t n, float lr,
+                            float b1, float b2, float eps, float wd, float c1, float c2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float upd = (mi / c1) / (sqrtf(vi / c2) + eps) + wd * p[i];
+    p[i] -= lr * upd;
+    pb[i] = __float2bfloat16(p[i]);
+  }
+}
+
+__global__ void k_mlp_tobf16(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16(x[i]);
+}
+
+// Consistency gate: Chebyshev moments of the predicted density on the midpoint grid
+// eps_j = -1 + (2j+1)/OUT (rho in units per unit eps): m_k = (2/OUT) sum_j rho_j T_k(eps_j)
+// compared with the input moments mu_k for k < kcheck; flag if max |m_k - mu_k| > tol.
+__global__ void k_mlp_gate(const float* __restrict__ rho, const double* __restrict__ mu, int mu_ld, int kcheck,
+                           double de_minus, double tol, int* __restrict__ flag, double* __restrict__ dev) {
+  const int b = blockIdx.x;
+  __shared__ double red[128];
+  double worst = 0.0;
+  for (int k = 0; k < kcheck; ++k) {
+    double s = 0.0;
+    for (int j = threadIdx.x; j < OUT; j += blockDim.x) {
+      const double e = -1.0 + (2.0 * j + 1.0) / OUT;
+      s += (double)rho[(int64_t)b * OUT + j] * de_minus * cos(k * acos(e));
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = 64; st > 0; st >>= 1) {
+      if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) worst = fmax(worst, fabs(red[0] * 2.0 / OUT - mu[(int64_t)b * mu_ld + k]));
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    flag[b] = worst > tol ? 1 : 0;
+    if (dev) dev[b] = worst;
+  }
+}
+
+struct Net {
+  __nv_bfloat16* pb;  // bf16 parameters
+  __nv_bfloat16 *X, *H1, *H2, *dY, *dZ2, *dZ1;
+  float *Y, *T, *grad;
+};
+
+void gemm(cudaStream_t st, const __nv_bfloat16* A, int lda, int tA, const __nv_bfloat16* B, int ldb, int tB,
+          int M, int N, int K, GemmEpi ep) {
+  dim3 grid((N + 63) / 64, (M + 63) / 64);
+  k_mlp_gemm<<<grid, 128, 0, st>>>(A, lda, tA, B, ldb, tB, M, N, K, ep);
+}
+
+GemmEpi epi(float* C32, __nv_bfloat16* C16, int ldc, const float* bias = nullptr, int relu = 0,
+            const __nv_bfloat16* mask = nullptr) {
+  GemmEpi e;
+  e.bias = bias;
+  e.mask = mask;
+  e.relu = relu;
+  e.C32 = C32;
+  e.C16 = C16;
+  e.ldc = ldc;
+  e.alpha = 1.0f;
+  return e;
+}
+
+// forward on rows already in net.X (BF16, scaled); writes net.Y (FP32)
+void forward(cudaStream_t st, const Net& net, const float* p32, int rows) {
+  gemm(st, net.X, IN, 0, net.pb + kOffW1, IN, 1, rows, HID, IN, epi(nullptr, net.H1, HID, p32 + kOffB1, 1));
+  gemm(st, net.H1, HID, 0, net.pb + kOffW2, HID, 1, rows, HID, HID, epi(nullptr, net.H2, HID, p32 + kOffB2, 1));
+  gemm(st, net.H2, HID, 0, net.pb + kOffW3, HID, 1, rows, OUT, HID, epi(net.Y, nullptr, OUT, p32 + kOffB3));
+}
+
+// backward of the mean L1 loss over rows x OUT; gradient into net.grad
+void backward(cudaStream_t st, const Net& net, int rows, double* lsum, int lblocks) {
+  const int64_t n = (int64_t)rows * OUT;
+  k_mlp_l1grad<<<lblocks, 256, 0, st>>>(net.Y, net.T, n, 1.0f / (float)n, net.dY, lsum);
+  float* g = net.grad;
+  gemm(st, net.dY, OUT, 1, net.H2, HID, 0, OUT, HID, rows, epi(g + kOffW3, nullptr, HID));
+  k_mlp_colsum<<<(OUT + 255) / 256, 256, 0, st>>>(net.dY, rows, OUT, g + kOffB3);
+  gemm(st, net.dY, OUT, 0, net.pb + kOffW3, HID, 0, rows, HID, OUT, epi(nullptr, net.dZ2, HID, nullptr, 0, net.H2));
+  gemm(st, net.dZ2, HID, 1, net.H1, HID, 0, HID, HID, rows, epi(g + kOffW2, nullptr, HID));
+  k_mlp_colsum<<<(HID + 255) / 256, 256, 0, st>>>(net.dZ2, rows, HID, g + kOffB2);
+  gemm(st, net.dZ2, HID, 0, net.pb + kOffW2, HID, 0, rows, HID, HID, epi(nullptr, net.dZ1, HID, nullptr, 0, net.H1));
+  gemm(st, net.dZ1, HID, 1, net.X, IN, 0, HID, IN, rows, epi(g + kOffW1, nullptr, IN));
+  k_mlp_colsum<<<(HID + 255) / 256, 256, 0, st>>>(net.dZ1, rows, HID, g + kOffB1);
+}
+
+int carve_net(kite_ctx* ctx, int rows, Net* net, float** extra, size_t extra_floats) {
+  Carver probe(nullptr);
+  auto lay = [&](Carver& k, Net& n, float** ex) {
+    n.pb = k.take<__nv_bfloat16>(kParams);
+    n.X = k.take<__nv_bfloat16>((size_t)rows * IN);
+    n.H1 = k.take<__nv_bfloat16>((size_t)rows * HID);
+    n.H2 = k.take<__nv_bfloat16>((size_t)rows * HID);
+    n.dY = k.take<__nv_bfloat16>((size_t)rows * OUT);
+    n.dZ2 = k.take<__nv_bfloat16>((size_t)rows * HID);
+    n.dZ1 = k.take<__nv_bfloat16>((size_t)rows * HID);
+    n.Y = k.take<float>((size_t)rows * OUT);
+    n.T = k.take<float>((size_t)rows * OUT);
+    n.grad = k.take<float>(kParams);
+    *ex = k.take<float>(extra_floats);
+  };
+  Net dummy;
+  float* dex;
+  lay(probe, dummy, &dex);
+  int rc = ensure_ws(ctx, probe.used());
+  if (rc != KITE_OK) return rc;
+  Carver w(ctx->ws);
+  lay(w, *net, extra);
+  return KITE_OK;
+}
+
+}  // namespace
+
+int64_t mlp_param_count() { return kParams; }
+
+// Full-batch gradient of the mean L1 loss (for checks): params, X [n][IN], T [n][OUT] device.
+int mlp_gradient_impl(kite_ctx* ctx, const float* params, const float* X, const float* T, int n,
+                      const float* scale, float* grad, double* loss) {
+  Net net;
+  float* ex;
+  int rc = carve_net(ctx, n, &net, &ex, kParams + 4096);
+  if (rc != KITE_OK) return rc;
+  cudaStream_t st = ctx->stream;
+  float* p32 = ex;
+  double* lsum = reinterpret_cast<double*>(ex + kParams);
+  KITE_CUDA_TRY(ctx, cudaMemcpyAsync(p32, params, sizeof(float) * kParams, cudaMemcpyDefault, st));
+  k_mlp_tobf16<<<1024, 256, 0, st>>>(p32, net.pb, kParams);
+  k_mlp_gather<<<1024, 256, 0, st>>>(X, nullptr, n, IN, scale, net.X, T, net.T, OUT);
+  forward(st, net, p32, n);
+  const int lblocks = 256;
+  backward(st, net, n, lsum, lblocks);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  KITE_CUDA_TRY(ctx, cudaMemcpyAsync(grad, net.grad, sizeof(float) * kParams, cudaMemcpyDefault, st));
+  std::vector<double> ls(lblocks);
+  KITE_CUDA_TRY(ctx, cudaMemcpyAsync(ls.data(), lsum, sizeof(double) * lblocks, cudaMemcpyDeviceToHost, st));
+  KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (loss) *loss = std::accumulate(ls.begin(), ls.end(), 0.0) / ((double)n * OUT);
+  return KITE_OK;
+}
+
+int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, const float* scale, float* Y) {
+  const int chunk = 4096;
+  Net net;
+  float* ex;
+  int rc = carve_net(ctx, std::min(n, chunk), &net, &ex, kParams);
+  if (rc != KITE_OK) return rc;
+  cudaStream_t st = ctx->stream;
+  KITE_CUDA_TRY(ctx, cudaMemcpyAsync(ex, params, sizeof(float) * kParams, cudaMemcpyDefault, st));
+  k_mlp_tobf16<<<1024, 256, 0, st>>>(ex, net.pb, kParams);
+  for (int r0 = 0; r0 < n; r0 += chunk) {
+    const int rows = std::min(chunk, n - r0);
+    k_mlp_gather<<<1024, 256, 0, st>>>(X + (int64_t)r0 * IN, nullptr, rows, IN, scale, net.X, nullptr, nullptr, 0);
+    forward(st, net, ex, rows);
+    KITE_CUDA_TRY(ctx, cudaMemcpyAsync(Y + (int64_t)r0 * OUT, net.Y, sizeof(float) * rows * OUT, cudaMemcpyDefault, st));
+  }
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  return KITE_OK;
+}
+
+int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const float* scale,
+                   const kite_mlp_train_cfg* cfg, float* params, float* loss_curve) {
+  const int bs = std::max(1, std::min(cfg->batch, n));
+  Net net;
+  float* ex;
+  int rc = carve_net(ctx, bs, &net, &ex, 3 * kParams + 4096 + (size_t)bs);
+  if (rc != KITE_OK) return rc;
+  cudaStream_t st = ctx->stream;
+  float* p32 = ex;
+  float* m = ex + kParams;
+  float* v = ex + 2 * kParams;
+  double* lsum = reinterpret_cast<double*>(ex + 3 * kParams);
+  int* d_idx = reinterpret_cast<int*>(ex + 3 * kParams + 4096);
+  KITE_CUDA_TRY(ctx, cudaMemcpyAsync(p32, params, sizeof(float) * kParams, cudaMemcpyDefault, st));
+  KITE_CUDA_TRY(ctx, cudaMemsetAsync(m, 0, sizeof(float) * 2 * kParams, st));
+  k_mlp_tobf16<<<1024, 256, 0, st>>>(p32, net.pb, kParams);
+  std::mt19937_64 rng(cfg->seed);
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  const int steps_per_epoch = (n + bs - 1) / bs;
+  const int total = cfg->epochs * steps_per_epoch;
+  const int lblocks = 128;
+  std::vector<double> ls(lblocks);
+  int t = 0;
+  for (int ep = 0; ep < cfg->epochs; ++ep) {
+    std::shuffle(order.begin(), order.end(), rng);
+    double epoch_loss = 0.0;
+    for (int b = 0; b < steps_per_epoch; ++b) {
+      const int rows = std::min(bs, n - b * bs);
+      KITE_CUDA_TRY(ctx, cudaMemcpyAsync(d_idx, order.data() + (size_t)b * bs, sizeof(int) * rows,
+                                         cudaMemcpyHostToDevice, st));
+      k_mlp_gather<<<512, 256, 0, st>>>(X, d_idx, rows, IN, scale, net.X, T, net.T, OUT);
+      forward(st, net, p32, rows);
+      backward(st, net, rows, lsum, lblocks);
+      ++t;
+      // cosine learning-rate schedule
+      const double lr = cfg->lr * 0.5 * (1.0 + std::cos(3.141592653589793 * (t - 1) / std::max(1, total)));
+      const float c1 = (float)(1.0 - std::pow(0.9, t)), c2 = (float)(1.0 - std::pow(0.999, t));
+      k_mlp_adamw<<<1024, 256, 0, st>>>(p32, net.grad, m, v, net.pb, kParams, (float)lr, 0.9f, 0.999f, 1e-8f,
+                                        (float)cfg->weight_decay, c1, c2);
+      KITE_CUDA_TRY(ctx, cudaGetLastError());
+      KITE_CUDA_TRY(ctx, cudaMemcpyAsync(ls.data(), lsum, sizeof(double) * lblocks, cudaMemcpyDeviceToHost, st));
+      KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));  // d_idx / order reuse
+      epoch_loss += std::accumulate(ls.begin(), ls.end(), 0.0);
+    }
+    if (loss_curve) loss_curve[ep] = (float)(epoch_loss / ((double)n * OUT));
+  }
+  KITE_CUDA_TRY(ctx, cudaMemcpyAsync(params, p32, sizeof(float) * kParams, cudaMemcpyDefault, st));
+  KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  return KITE_OK;
+}
+
+int mlp_gate_impl(kite_ctx* ctx, const float* rho, const double* mu, int mu_ld, int n, int kcheck,
+                  double de_minus, double tol, int* flags, double* dev) {
+  k_mlp_gate<<<n, 128, 0, ctx->stream>>>(rho, mu, mu_ld, kcheck, de_minus, tol, flags, dev);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  return KITE_OK;
+}
+
+}  // namespace kite
