@@ -15,6 +15,43 @@ import numpy as np
 IN, HID, OUT = 128, 512, 1024
 
 
+def round_bf16(x):
+    """Round to the nearest bfloat16 (ties to even) via float32, returned as float64: the
+    precision in which the kernels store weights and activations.  Used so that decisions
+    taken on stored values (the ReLU masks) are taken on the same values on both sides."""
+    a = np.ascontiguousarray(np.asarray(x, np.float32))
+    u = a.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def kernel_params(p, n_in=IN, n_hid=HID, n_out=OUT):
+    """The parameters as the kernels use them: weights rounded to bfloat16, biases float32."""
+    out, off = [], 0
+    for s in shapes(n_in, n_hid, n_out):
+        k = int(np.prod(s))
+        part = np.asarray(p[off:off + k])
+        out.append(round_bf16(part) if len(s) == 2 else part.astype(np.float32).astype(np.float64))
+        off += k
+    return np.concatenate(out)
+
+
+def midpoint_eps(n_out=OUT):
+    """The output grid in the rescaled energy: eps_j = -1 + (2j+1)/n_out."""
+    return -1.0 + (2.0 * np.arange(n_out) + 1.0) / n_out
+
+
+def prior(mu_in, e_min, e_max, n_out=OUT):
+    """The residual prior: the Jackson reconstruction (Eq. e8a with the Jackson kernel of
+    order len(mu_in)) from the given moments on the midpoint grid, per eV; rows of mu_in."""
+    import oracle
+    mu_in = np.atleast_2d(np.asarray(mu_in, np.float64))
+    m = mu_in.shape[1]
+    g = oracle.kernel_jackson(m)
+    E = midpoint_eps(n_out) * 0.5 * (e_max - e_min) + 0.5 * (e_max + e_min)
+    return np.stack([oracle.dos(row, E, e_min, e_max, g) for row in mu_in])
+
+
 def shapes(n_in=IN, n_hid=HID, n_out=OUT):
     return [(n_hid, n_in), (n_hid,), (n_hid, n_hid), (n_hid,), (n_out, n_hid), (n_out,)]
 
@@ -32,37 +69,41 @@ def unpack(p, n_in=IN, n_hid=HID, n_out=OUT):
     return out
 
 
-def forward(p, X, n_in=IN, n_hid=HID, n_out=OUT):
-    """Returns (Y, cache): Y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 per row of X."""
+def forward(p, X, n_in=IN, n_hid=HID, n_out=OUT, act_round=None):
+    """Returns (Y, cache): Y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 per row of X.
+    act_round (or None) is applied to the hidden activations after the ReLU, modelling the
+    precision in which they are stored; the masks below are taken on the stored values."""
     W1, b1, W2, b2, W3, b3 = unpack(p, n_in, n_hid, n_out)
+    rnd = (lambda a: a) if act_round is None else act_round
     X = np.asarray(X, np.float64)
     Z1 = X @ W1.T + b1
-    H1 = np.maximum(Z1, 0.0)
+    H1 = rnd(np.maximum(Z1, 0.0))
     Z2 = H1 @ W2.T + b2
-    H2 = np.maximum(Z2, 0.0)
+    H2 = rnd(np.maximum(Z2, 0.0))
     Y = H2 @ W3.T + b3
     return Y, (X, Z1, H1, Z2, H2)
 
 
-def loss(p, X, T, n_in=IN, n_hid=HID, n_out=OUT):
+def loss(p, X, T, n_in=IN, n_hid=HID, n_out=OUT, act_round=None):
     """Mean absolute error over all outputs of all rows."""
-    Y, _ = forward(p, X, n_in, n_hid, n_out)
+    Y, _ = forward(p, X, n_in, n_hid, n_out, act_round)
     return float(np.mean(np.abs(Y - np.asarray(T, np.float64))))
 
 
-def grad(p, X, T, n_in=IN, n_hid=HID, n_out=OUT):
-    """Analytic gradient of `loss` by the chain rule (sign(0) taken as 0)."""
+def grad(p, X, T, n_in=IN, n_hid=HID, n_out=OUT, act_round=None):
+    """Analytic gradient of `loss` by the chain rule (sign(0) taken as 0; the activation
+    rounding, if any, is passed through as the identity)."""
     W1, b1, W2, b2, W3, b3 = unpack(p, n_in, n_hid, n_out)
-    Y, (X, Z1, H1, Z2, H2) = forward(p, X, n_in, n_hid, n_out)
+    Y, (X, Z1, H1, Z2, H2) = forward(p, X, n_in, n_hid, n_out, act_round)
     dY = np.sign(Y - np.asarray(T, np.float64)) / Y.size
     dW3 = dY.T @ H2
     db3 = dY.sum(0)
     dH2 = dY @ W3
-    dZ2 = dH2 * (Z2 > 0)
+    dZ2 = dH2 * (H2 > 0)
     dW2 = dZ2.T @ H1
     db2 = dZ2.sum(0)
     dH1 = dZ2 @ W2
-    dZ1 = dH1 * (Z1 > 0)
+    dZ1 = dH1 * (H1 > 0)
     dW1 = dZ1.T @ X
     db1 = dZ1.sum(0)
     return np.concatenate([g.ravel() for g in (dW1, db1, dW2, db2, dW3, db3)])

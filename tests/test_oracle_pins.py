@@ -493,3 +493,52 @@ def test_mlp_adamw_first_step_is_sign_step():
     g = np.array([0.3, -1e-3, 2.0])
     p1, m, v = mlp.adamw_step(p, g, np.zeros(3), np.zeros(3), 1, lr=0.01, wd=0.1, eps=1e-12)
     assert np.allclose(p1, p - 0.01 * (np.sign(g) + 0.1 * p), atol=1e-10)
+
+
+def test_bf16_rounding_ties_to_even_and_matches_torch():
+    """round_bf16: 8 significant bits, ties to even (1 + 2^-8 -> 1, 1 + 3*2^-8 -> 1 + 2^-6),
+    and the same values as torch's float32 -> bfloat16 conversion on random inputs."""
+    from oracle import mlp
+    assert mlp.round_bf16(1.0 + 2.0**-8) == 1.0
+    assert mlp.round_bf16(1.0 + 3 * 2.0**-8) == 1.0 + 2.0**-6
+    assert mlp.round_bf16(1.0 + 2.0**-8 + 2.0**-20) == 1.0 + 2.0**-7
+    assert mlp.round_bf16(-3.0) == -3.0
+    torch = pytest.importorskip("torch")
+    x = np.random.Generator(np.random.PCG64(12)).standard_normal(4096).astype(np.float32) * 10.0
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.round_bf16(x), ref)
+
+
+def test_mlp_activation_rounding_moves_only_the_stored_values():
+    """With act_round the forward pass equals the plain one evaluated layer by layer on the
+    rounded activations, and the masks follow the stored (rounded) activations."""
+    from oracle import mlp
+    ni, nh, no = 6, 10, 4
+    p = mlp.init_params(5, ni, nh, no) + 0.003
+    X = np.random.Generator(np.random.PCG64(6)).standard_normal((5, ni))
+    W1, b1, W2, b2, W3, b3 = mlp.unpack(p, ni, nh, no)
+    H1 = mlp.round_bf16(np.maximum(X @ W1.T + b1, 0))
+    H2 = mlp.round_bf16(np.maximum(H1 @ W2.T + b2, 0))
+    Y, _ = mlp.forward(p, X, ni, nh, no, act_round=mlp.round_bf16)
+    assert np.array_equal(Y, H2 @ W3.T + b3)
+    Yp, _ = mlp.forward(p, X, ni, nh, no)
+    assert 0 < np.max(np.abs(Y - Yp)) <= 1e-2 * np.max(np.abs(Yp))
+
+
+def test_mlp_prior_closed_forms():
+    """The residual prior (Jackson reconstruction on the midpoint grid): mu = (1, 0, ...)
+    gives 1/(pi a sqrt(1 - eps^2)) exactly (g_0 = 1); moments of a point spectrum
+    mu_k = T_k(x0) give a broadened peak at x0 whose midpoint-rule weight is 1."""
+    from oracle import mlp
+    e_min, e_max = -3.0, 5.0
+    a = 0.5 * (e_max - e_min)
+    eps = mlp.midpoint_eps(256)
+    mu = np.zeros(64)
+    mu[0] = 1.0
+    rho = mlp.prior(mu, e_min, e_max, n_out=256)[0]
+    assert np.allclose(rho, 1.0 / (np.pi * a * np.sqrt(1.0 - eps**2)), rtol=1e-13, atol=0)
+    x0 = 0.3
+    mu = np.cos(np.arange(64) * np.arccos(x0))
+    rho = mlp.prior(mu, e_min, e_max, n_out=1024)[0]
+    assert abs(np.sum(rho) * a * 2.0 / 1024 - 1.0) < 1e-3
+    assert abs(mlp.midpoint_eps(1024)[np.argmax(rho)] - x0) < 4.0 / 1024
