@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--R", type=int, default=WORKLOAD["R"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-doubling", action="store_true")
     return p.parse_args()
 
 
@@ -288,6 +289,38 @@ def main():
                     "algorithmic_bytes_per_launch": step_bytes / step_n,
                     "avg_launch_us": 1e6 * step_s / step_n, "peak_kind": peak_kind + " (copy test)"}
 
+    # ---- moment doubling on the same workload (two moments per recursion step) --------
+    doubling = None
+    if not args.no_doubling:
+        kpm_d = kite.make_kpm(M, R, 1, kite.FP32, doubling=True)
+        mu_d = torch.zeros(M, dtype=torch.float64, device="cuda")
+
+        def step_d():
+            st_d = kite.moments_1d(ctx, system, kpm_d, mu_d)
+            kite.reconstruct_dos(ctx, mu_d, M, M, kite.KERNEL_JACKSON, 0.0, e_min, e_max, E, K, rho)
+            return st_d
+
+        for _ in range(args.warmup):
+            step_d()
+        barrier()
+        ev0.record(stream)
+        ds, dn, db = 0.0, 0, 0.0
+        for _ in range(args.steps):
+            st_d = step_d()
+            ds += st_d.step_seconds
+            dn += st_d.step_launches
+            db += st_d.step_bytes
+        ev1.record(stream)
+        barrier()
+        ms_d = ev0.elapsed_time(ev1) / args.steps
+        peak, _ = measured_peaks()
+        doubling = {"value": updates_per_step * world / (ms_d * 1e-3), "unit": UNIT, "ms_per_step": ms_d,
+                    "step_launches_per_step": dn // args.steps,
+                    "step_gbs": db / ds / 1e9, "step_frac": db / ds / 1e9 / peak,
+                    "max_abs_diff_vs_plain": float((mu_d - mu).abs().max().item()),
+                    "note": "mu_2n = 2<r_n|r_n> - mu_0, mu_2n+1 = 2<r_n|r_n+1> - mu_1: ceil(M/2) "
+                            "steps, r_0 not re-read; same M moments, same unit"}
+
     # ---- end to end through the C ABI with host buffers -------------------------------
     e2e = None
     if not args.no_e2e:
@@ -341,6 +374,7 @@ def main():
                            "parallelism": f"{world} independent realisations" if world > 1 else "single GPU",
                            "grid": st.grid, "block": st.block},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "moment_doubling": doubling,
                 "gpu_launches": launches_per_step * args.steps,
                 "wall_s_timed": wall}
         print(json.dumps(line), flush=True)

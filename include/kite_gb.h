@@ -94,7 +94,13 @@ typedef struct {
  *              as [S*R][2][N] interleaved complex of the working precision (complex64
  *              for KITE_FP32, complex128 for KITE_FP64), host or device; for M = 1 both
  *              slots hold r.  NULL = not wanted.  Lets a caller check the recursion bit
- *              for bit or checkpoint a run. */
+ *              for bit or checkpoint a run.  Ignored when doubling is set.
+ *   doubling   0: mu_n = <r|T_n r> for every n (one recursion step per moment).
+ *              1: moment doubling -- T_n^2 = (T_2n + T_0)/2 and T_{n+1} T_n =
+ *              (T_{2n+1} + T_1)/2 for the Hermitian H~ give mu_2n = 2<r_n|r_n> - mu_0 and
+ *              mu_{2n+1} = 2<r_{n+1}|r_n> - mu_1, so ceil(M/2) steps yield M moments and
+ *              r_0 is never re-read (identical in exact arithmetic, not bit for bit).
+ *   reserved   must be 0 */
 typedef struct {
   int32_t M;
   int32_t R;
@@ -104,6 +110,8 @@ typedef struct {
   double e_max;
   const double* r0;
   void* r_last;
+  int32_t doubling;
+  int32_t reserved;
 } kite_kpm;
 
 /* Per-call statistics (all optional outputs). */
@@ -222,7 +230,8 @@ int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, in
  * resident grid are grouped into teams: large systems get several CTAs that meet at a
  * bounded global barrier after each step, small ones share single-CTA teams.  The
  * set-up kernels, the sweep and the reductions are captured in one CUDA graph.
- *   systems, kpms  [count] arrays; kpms[i].S must be 1, r0 and r_last NULL
+ *   systems, kpms  [count] arrays; kpms[i].S must be 1, r0 and r_last NULL; doubling
+ *                  (0 or 1, see kite_kpm) the same for every system of the batch
  *   mu             [count] pointers, mu[i] -> [M_i] FP64 (host or device)
  *   st             statistics of the graph launch (seconds, updates, bytes), or NULL
  * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA, KITE_ERR_BOUNDS, KITE_ERR_TIMEOUT,
@@ -244,6 +253,22 @@ int kite_moments_1d_batched(kite_ctx* ctx, int count, const kite_system* systems
 #define KITE_MLP_HIDDEN 512
 #define KITE_MLP_OUT 1024
 
+/* Optional residual prior of the network (NULL = none).  With KITE_PRIOR_JACKSON the
+ * network's output is added to the Jackson reconstruction (Eq. e8a, Jackson kernel of
+ * order KITE_MLP_IN) from the same first KITE_MLP_IN moments -- the raw X rows, before
+ * `scale` -- on the midpoint grid eps_j = -1 + (2j+1)/KITE_MLP_OUT of the window
+ * [e_min, e_max] (density per eV, as kite_reconstruct_dos), so the network learns only
+ * the correction that the many-moment reconstruction adds.  Training subtracts the same
+ * prior from the targets. */
+#define KITE_PRIOR_NONE 0
+#define KITE_PRIOR_JACKSON 1
+typedef struct {
+  int32_t kind;      /* KITE_PRIOR_NONE or KITE_PRIOR_JACKSON                   */
+  int32_t reserved;  /* must be 0                                               */
+  double e_min;      /* energy window of the moments and the output grid (eV)   */
+  double e_max;
+} kite_mlp_prior;
+
 typedef struct {
   int32_t epochs;       /* passes over the training set                      */
   int32_t batch;        /* rows per optimiser step                           */
@@ -258,14 +283,17 @@ int64_t kite_mlp_param_count(void);
 /* Trains in place: mean-absolute-error loss over X [n][IN] -> T [n][OUT], AdamW
  * (beta 0.9/0.999, eps 1e-8) on FP32 master weights, hand-written forward and backward
  * kernels.  params [P] holds the initial weights on entry and the trained ones on exit;
- * loss_curve [epochs] (or NULL) receives the mean training loss of each epoch.
+ * loss_curve [epochs] (or NULL) receives the mean training loss of each epoch.  prior
+ * (or NULL) as above: the loss is taken on prior + network.
  * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
 int kite_mlp_train(kite_ctx* ctx, const float* X, const float* T, int n, const float* scale,
-                   const kite_mlp_train_cfg* cfg, float* params, float* loss_curve);
+                   const kite_mlp_train_cfg* cfg, float* params, float* loss_curve,
+                   const kite_mlp_prior* prior);
 
-/* Y [n][OUT] = network(X [n][IN] * scale).  Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
+/* Y [n][OUT] = network(X [n][IN] * scale) (+ the prior of X, if prior is not NULL).
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
 int kite_mlp_forward(kite_ctx* ctx, const float* params, const float* X, int n,
-                     const float* scale, float* Y);
+                     const float* scale, float* Y, const kite_mlp_prior* prior);
 
 /* Gradient [P] of the mean absolute error over all n x OUT outputs (for checks), and the
  * loss.  Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
@@ -292,7 +320,8 @@ int kite_learned_gate(kite_ctx* ctx, const float* rho, const double* mu, int mu_
  * held by every GPU that loads the library until the process exits -- and calls no
  * cudaMalloc, cudaFree or other allocating routine, and needs no kite_ctx.
  *   sys, kpm   as for kite_moments_1d; e_min = e_max = 0 selects the Gershgorin bounds;
- *              R <= 8 (FP32) or 4 (FP64); kpm->r0 and kpm->r_last must be NULL
+ *              R <= 8 (FP32) or 4 (FP64); kpm->r0 and kpm->r_last must be NULL and
+ *              kpm->doubling 0
  *   mu         [M] FP64 moments (vector average), host or device, complete on return
  *   cuda_stream  stream the work is queued on (NULL = legacy default stream)
  *   err, err_len optional buffer for a one-line reason when the call fails

@@ -48,7 +48,8 @@ class KPM(ctypes.Structure):
     """``kite_kpm``: expansion parameters."""
     _fields_ = [("M", ctypes.c_int32), ("R", ctypes.c_int32), ("S", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("e_min", ctypes.c_double),
-                ("e_max", ctypes.c_double), ("r0", ctypes.c_void_p), ("r_last", ctypes.c_void_p)]
+                ("e_max", ctypes.c_double), ("r0", ctypes.c_void_p), ("r_last", ctypes.c_void_p),
+                ("doubling", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -65,6 +66,15 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+PRIOR_NONE, PRIOR_JACKSON = 0, 1
+
+
+class MLPPrior(ctypes.Structure):
+    """``kite_mlp_prior``."""
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("e_min", ctypes.c_double),
+                ("e_max", ctypes.c_double)]
+
+
 class MLPTrainCfg(ctypes.Structure):
     """``kite_mlp_train_cfg``."""
     _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_double),
@@ -76,9 +86,10 @@ def make_system(lattice=HONEYCOMB, Lx=64, Ly=64, t=-2.7, W=0.0, delta=0.0, p_vac
                   float(p_vac), int(seed))
 
 
-def make_kpm(M, R=1, S=1, precision=FP32, e_min=0.0, e_max=0.0, r0=None, r_last=None):
+def make_kpm(M, R=1, S=1, precision=FP32, e_min=0.0, e_max=0.0, r0=None, r_last=None,
+             doubling=False):
     return KPM(int(M), int(R), int(S), int(precision), float(e_min), float(e_max),
-               _addr(r0), _addr(r_last))
+               _addr(r0), _addr(r_last), int(bool(doubling)), 0)
 
 
 _LOCK = threading.Lock()
@@ -121,9 +132,9 @@ def lib():
             L.kite_moments_1d_batched.restype = i32
             L.kite_mlp_param_count.argtypes = []
             L.kite_mlp_param_count.restype = ctypes.c_int64
-            L.kite_mlp_train.argtypes = [vp, vp, vp, i32, vp, P(MLPTrainCfg), vp, vp]
+            L.kite_mlp_train.argtypes = [vp, vp, vp, i32, vp, P(MLPTrainCfg), vp, vp, P(MLPPrior)]
             L.kite_mlp_train.restype = i32
-            L.kite_mlp_forward.argtypes = [vp, vp, vp, i32, vp, vp]
+            L.kite_mlp_forward.argtypes = [vp, vp, vp, i32, vp, vp, P(MLPPrior)]
             L.kite_mlp_forward.restype = i32
             L.kite_mlp_gradient.argtypes = [vp, vp, vp, vp, i32, vp, vp, P(d)]
             L.kite_mlp_gradient.restype = i32
@@ -281,20 +292,31 @@ def moments_1d_batched(ctx: Context, systems, kpms, mus) -> Stats:
     return st
 
 
+def jackson_prior(e_min: float, e_max: float) -> MLPPrior:
+    """The residual prior of kite_mlp_train / kite_mlp_forward on the window [e_min, e_max]."""
+    return MLPPrior(PRIOR_JACKSON, 0, float(e_min), float(e_max))
+
+
+def _prior_ref(prior):
+    return ctypes.byref(prior) if prior is not None else None
+
+
 def mlp_param_count() -> int:
     return int(lib().kite_mlp_param_count())
 
 
 def mlp_train(ctx: Context, X, T, n: int, params, epochs=50, batch=256, lr=1e-3, weight_decay=1e-4,
-              seed=0, scale=None, loss_curve=None):
+              seed=0, scale=None, loss_curve=None, prior=None):
     """kite_mlp_train: trains `params` (FP32 [P]) in place on X [n][IN] -> T [n][OUT]."""
     cfg = MLPTrainCfg(int(epochs), int(batch), float(lr), float(weight_decay), int(seed))
     ctx.check(lib().kite_mlp_train(ctx.handle, _addr(X), _addr(T), int(n), _addr(scale),
-                                   ctypes.byref(cfg), _addr(params), _addr(loss_curve)))
+                                   ctypes.byref(cfg), _addr(params), _addr(loss_curve),
+                                   _prior_ref(prior)))
 
 
-def mlp_forward(ctx: Context, params, X, n: int, Y, scale=None):
-    ctx.check(lib().kite_mlp_forward(ctx.handle, _addr(params), _addr(X), int(n), _addr(scale), _addr(Y)))
+def mlp_forward(ctx: Context, params, X, n: int, Y, scale=None, prior=None):
+    ctx.check(lib().kite_mlp_forward(ctx.handle, _addr(params), _addr(X), int(n), _addr(scale), _addr(Y),
+                                     _prior_ref(prior)))
 
 
 def mlp_gradient(ctx: Context, params, X, T, n: int, grad, scale=None) -> float:

@@ -62,7 +62,10 @@ __device__ __forceinline__ bool team_barrier(unsigned int* ctr, unsigned int tar
   return *abort_flag == 0;
 }
 
-template <int LAT, int C>
+// DBL: moment doubling for the whole batch (two moments per step, r_0 not re-read):
+// step 0 writes <r_0|r_0>, <r_0|r_1> into slots 0, 1; step n >= 1 writes <r_n|r_n>,
+// <r_n|r_{n+1}> into slots 2n, 2n+1; k_breduce turns slots into moments.
+template <int LAT, int C, bool DBL>
 __global__ void __launch_bounds__(kBlock, 2)
     k_batched(const BSys* __restrict__ systems, const BTeam* __restrict__ teams,
               const int* __restrict__ order, const int* __restrict__ cta_team,
@@ -87,18 +90,26 @@ __global__ void __launch_bounds__(kBlock, 2)
     auto where = [&](int n) -> void* {
       return n == 0 ? const_cast<void*>(S.r0) : ((n & 1) ? S.bA : S.bB);
     };
-    for (int n = 0; n == 0 || n + 1 < S.M; ++n) {
+    constexpr int MODE = DBL ? 3 : 0;
+    const int steps = DBL ? (S.M + 1) / 2 : max(S.M - 1, 1);
+    for (int n = 0; n < steps; ++n) {
       bool ok;
       if (n == 0)
-        ok = step_body<float, LAT, C, true, 0>(ring, rank, T.ncta, nullptr, S.r0, S.bA, S.r0, S.vt,
-                                               S.tt, S.Lx, S.Ly, S.units,
-                                               S.partial + (size_t)T.ncta * Q, S.partial, err, 0,
-                                               nofam);
+        ok = step_body<float, LAT, C, true, MODE>(ring, rank, T.ncta, nullptr, S.r0, S.bA, S.r0, S.vt,
+                                                  S.tt, S.Lx, S.Ly, S.units,
+                                                  S.partial + (size_t)T.ncta * Q, S.partial, err, 0,
+                                                  nofam);
+      else if (DBL)
+        ok = step_body<float, LAT, C, false, MODE>(ring, rank, T.ncta, where(n - 1), where(n),
+                                                   where(n + 1), S.r0, S.vt, S.tt, S.Lx, S.Ly, S.units,
+                                                   S.partial + (size_t)(2 * n + 1) * T.ncta * Q,
+                                                   S.partial + (size_t)(2 * n) * T.ncta * Q, err, 0,
+                                                   nofam);
       else
-        ok = step_body<float, LAT, C, false, 0>(ring, rank, T.ncta, where(n - 1), where(n),
-                                                where(n + 1), S.r0, S.vt, S.tt, S.Lx, S.Ly, S.units,
-                                                S.partial + (size_t)(n + 1) * T.ncta * Q, nullptr,
-                                                err, 0, nofam);
+        ok = step_body<float, LAT, C, false, MODE>(ring, rank, T.ncta, where(n - 1), where(n),
+                                                   where(n + 1), S.r0, S.vt, S.tt, S.Lx, S.Ly, S.units,
+                                                   S.partial + (size_t)(n + 1) * T.ncta * Q, nullptr,
+                                                   err, 0, nofam);
       if (!ok) return;
       if (T.ncta > 1) {
         arrived += (unsigned int)T.ncta;
@@ -113,19 +124,26 @@ __global__ void __launch_bounds__(kBlock, 2)
   }
 }
 
-__global__ void k_breduce(const double* __restrict__ partial, int M, int G, int Q, int nvec,
+// mean over the vectors of slot k's real part, CTA partials summed in fixed order
+__device__ double slot_mean(const double* __restrict__ partial, int k, int G, int Q, int nvec, double ne) {
+  double acc = 0.0;
+  for (int q = 0; q < 2 * nvec; q += 2) {  // real parts, vector by vector, CTA by CTA
+    double sum = 0.0;
+    const double* p = partial + (size_t)k * G * Q + q;
+    for (int g = 0; g < G; ++g) sum += p[(size_t)g * Q];
+    acc += ne > 0.0 ? sum / ne : 0.0;
+  }
+  return acc / nvec;
+}
+
+// mu_n from the slots; with doubling mu_n = 2 slot_n - slot_(n mod 2) for n >= 2
+__global__ void k_breduce(const double* __restrict__ partial, int M, int G, int Q, int nvec, int dbl,
                           const unsigned long long* __restrict__ n_eff, double* __restrict__ mu) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= M) return;
   const double ne = (double)*n_eff;
-  double acc = 0.0;
-  for (int q = 0; q < 2 * nvec; q += 2) {  // real parts, vector by vector, CTA by CTA
-    double sum = 0.0;
-    const double* p = partial + (size_t)n * G * Q + q;
-    for (int g = 0; g < G; ++g) sum += p[(size_t)g * Q];
-    acc += ne > 0.0 ? sum / ne : 0.0;
-  }
-  mu[n] = acc / nvec;
+  const double v = slot_mean(partial, n, G, Q, nvec, ne);
+  mu[n] = (dbl && n >= 2) ? 2.0 * v - slot_mean(partial, n & 1, G, Q, nvec, ne) : v;
 }
 
 struct Schedule {
@@ -177,7 +195,7 @@ Schedule plan_teams(const std::vector<double>& work, const std::vector<long long
   return sc;
 }
 
-template <int LAT, int C>
+template <int LAT, int C, bool DBL>
 int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm* kpm,
                 const std::vector<Scale>& scales, double* const* mu_out, kite_stats* stats) {
   constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
@@ -185,10 +203,11 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
   using Sh = StepShape<LAT, C>;
   cudaStream_t st = ctx->stream;
   const int R = kpm[0].R;
+  auto steps_of = [](int M) { return DBL ? (M + 1) / 2 : std::max(M - 1, 1); };
   // persistent grid: every CTA resident
-  cudaFuncSetAttribute(k_batched<LAT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+  cudaFuncSetAttribute(k_batched<LAT, C, DBL>, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<LAT, C>, kBlock, Sh::SMEM) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<LAT, C, DBL>, kBlock, Sh::SMEM) !=
           cudaSuccess || occ < 1)
     return fail(ctx, KITE_ERR_CUDA, "occupancy query for the batched kernel failed");
   const int gmax = ctx->num_sms * occ;
@@ -197,7 +216,7 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
   double total = 0.0;
   for (int i = 0; i < count; ++i) {
     units[i] = (long long)((sys[i].Lx + Sh::TX - 1) / Sh::TX) * sys[i].Ly;
-    work[i] = (double)units[i] * Sh::TX * std::max(kpm[i].M - 1, 1);
+    work[i] = (double)units[i] * Sh::TX * steps_of(kpm[i].M);
     total += work[i];
   }
   // smallest target share whose schedule fits the resident grid
@@ -222,7 +241,7 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
       const size_t vb = (size_t)ncell * SORB * C * 16;
       char* a = k.take<char>(sizeof(float) * N);
       char* b = k.take<char>(3 * vb);
-      char* c = k.take<char>(sizeof(double) * (size_t)std::max(kpm[i].M, 2) * sc.ncta_of[i] * Q);
+      char* c = k.take<char>(sizeof(double) * (size_t)(std::max(kpm[i].M, 2) + 1) * sc.ncta_of[i] * Q);
       if (record) {
         off_vt[i] = (size_t)a;
         off_vec[i] = (size_t)b;
@@ -313,13 +332,13 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
     cfg.numAttrs = 1;
     const int stall = ctx->debug_stall;
     ctx->debug_stall = 0;
-    ce = cudaLaunchKernelEx(&cfg, k_batched<LAT, C>, (const BSys*)d_sys, (const BTeam*)d_teams,
+    ce = cudaLaunchKernelEx(&cfg, k_batched<LAT, C, DBL>, (const BSys*)d_sys, (const BTeam*)d_teams,
                             (const int*)d_ints, (const int*)(d_ints + sc.order.size()), counters,
                             ctx->d_status, stall);
   }
   for (int i = 0; i < count && ce == cudaSuccess; ++i) {
     const int M = kpm[i].M;
-    k_breduce<<<(M + 255) / 256, 256, 0, st>>>(hs[i].partial, M, sc.ncta_of[i], Q, R, ne + i,
+    k_breduce<<<(M + 255) / 256, 256, 0, st>>>(hs[i].partial, M, sc.ncta_of[i], Q, R, DBL ? 1 : 0, ne + i,
                                                d_mu + mu_off[i]);
     ce = cudaGetLastError();
   }
@@ -359,7 +378,8 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
     for (int i = 0; i < count; ++i) {
       const double N = (double)sys[i].Lx * sys[i].Ly * SORB;
       upd += (double)ne_h[i] * kpm[i].M * R;
-      bytes += (4.0 * 8.0 * R + 4.0) * N * std::max(kpm[i].M - 1, 0);
+      // per orbital and step: r_{n-1}, r_n (and r_0 without doubling) in, r_{n+1} out, on-site
+      bytes += ((DBL ? 3.0 : 4.0) * 8.0 * R + 4.0) * N * (DBL ? steps_of(kpm[i].M) : std::max(kpm[i].M - 1, 0));
     }
     stats->seconds = 1e-3 * ms;
     stats->updates = upd;
@@ -383,7 +403,9 @@ int moments_1d_batched_impl(kite_ctx* ctx, int count, const kite_system* sys, co
   const int c = (R + 1) / 2;
   const int C = c <= 1 ? 1 : (c <= 2 ? 2 : 4);
   const bool hc = sys[0].lattice == KITE_HONEYCOMB;
-#define KITE_B(LATV, CC) run_batched<LATV, CC>(ctx, count, sys, kpm, scales, mu, st)
+#define KITE_B(LATV, CC)                                                       \
+  (kpm[0].doubling ? run_batched<LATV, CC, true>(ctx, count, sys, kpm, scales, mu, st) \
+                   : run_batched<LATV, CC, false>(ctx, count, sys, kpm, scales, mu, st))
   if (hc) return C == 1 ? KITE_B(KITE_HONEYCOMB, 1) : (C == 2 ? KITE_B(KITE_HONEYCOMB, 2) : KITE_B(KITE_HONEYCOMB, 4));
   return C == 1 ? KITE_B(KITE_SQUARE, 1) : (C == 2 ? KITE_B(KITE_SQUARE, 2) : KITE_B(KITE_SQUARE, 4));
 #undef KITE_B

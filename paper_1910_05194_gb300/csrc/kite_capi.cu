@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -17,9 +18,11 @@ int moments_1d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
 int64_t mlp_param_count();
 int mlp_gradient_impl(kite_ctx* ctx, const float* params, const float* X, const float* T, int n,
                       const float* scale, float* grad, double* loss);
-int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, const float* scale, float* Y);
+int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, const float* scale, float* Y,
+                     const kite_mlp_prior* prior);
 int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const float* scale,
-                   const kite_mlp_train_cfg* cfg, float* params, float* loss_curve);
+                   const kite_mlp_train_cfg* cfg, float* params, float* loss_curve,
+                   const kite_mlp_prior* prior);
 int mlp_gate_impl(kite_ctx* ctx, const float* rho, const double* mu, int mu_ld, int n, int kcheck,
                   double de_minus, double tol, int* flags, double* dev);
 int moments_1d_batched_impl(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm* kpm,
@@ -178,6 +181,14 @@ struct Staging {
   }
 };
 
+int check_prior(kite_ctx* ctx, const kite_mlp_prior* prior) {
+  if (!prior) return KITE_OK;
+  if ((prior->kind != KITE_PRIOR_NONE && prior->kind != KITE_PRIOR_JACKSON) || prior->reserved != 0 ||
+      !(prior->e_max > prior->e_min) || !std::isfinite(prior->e_min) || !std::isfinite(prior->e_max))
+    return fail(ctx, KITE_ERR_ARG, "prior: kind must be KITE_PRIOR_NONE/JACKSON, reserved 0, e_max > e_min");
+  return KITE_OK;
+}
+
 }  // namespace kite
 
 using namespace kite;
@@ -303,6 +314,8 @@ int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   if (kpm->precision != KITE_FP32 && kpm->precision != KITE_FP64)
     return fail(ctx, KITE_ERR_ARG, "precision must be KITE_FP32 or KITE_FP64");
   if ((double)kpm->R * kpm->S > 65536.0) return fail(ctx, KITE_ERR_ARG, "R*S > 65536");
+  if ((kpm->doubling != 0 && kpm->doubling != 1) || kpm->reserved != 0)
+    return fail(ctx, KITE_ERR_ARG, "doubling must be 0 or 1 and reserved 0");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
   Scale sc;
   rc = resolve_bounds(ctx, sys, kpm->e_min, kpm->e_max, &sc);
@@ -369,13 +382,16 @@ int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
 
 int64_t kite_mlp_param_count(void) { return mlp_param_count(); }
 
+
 int kite_mlp_train(kite_ctx* ctx, const float* X, const float* T, int n, const float* scale,
-                   const kite_mlp_train_cfg* cfg, float* params, float* loss_curve) {
+                   const kite_mlp_train_cfg* cfg, float* params, float* loss_curve,
+                   const kite_mlp_prior* prior) {
   if (!ctx) return KITE_ERR_ARG;
   ctx->last_error.clear();
   if (!X || !T || !cfg || !params || n < 1 || cfg->epochs < 1 || cfg->batch < 1 || !(cfg->lr > 0.0) ||
       !(cfg->weight_decay >= 0.0))
     return fail(ctx, KITE_ERR_ARG, "need X, T, params, n >= 1 and a valid configuration");
+  if (check_prior(ctx, prior) != KITE_OK) return KITE_ERR_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
   Staging sg{ctx, {}};
   const float *Xd, *Td, *Sd;
@@ -383,17 +399,18 @@ int kite_mlp_train(kite_ctx* ctx, const float* X, const float* T, int n, const f
   if (rc == KITE_OK) rc = sg.in(T, (size_t)n * KITE_MLP_OUT, &Td);
   if (rc == KITE_OK) rc = sg.in(scale, KITE_MLP_IN, &Sd);
   std::vector<float> curve(cfg->epochs);
-  if (rc == KITE_OK) rc = mlp_train_impl(ctx, Xd, Td, n, Sd, cfg, params, curve.data());
+  if (rc == KITE_OK) rc = mlp_train_impl(ctx, Xd, Td, n, Sd, cfg, params, curve.data(), prior);
   if (rc == KITE_OK && loss_curve) std::copy(curve.begin(), curve.end(), loss_curve);
   cudaStreamSynchronize(ctx->stream);
   return rc;
 }
 
 int kite_mlp_forward(kite_ctx* ctx, const float* params, const float* X, int n, const float* scale,
-                     float* Y) {
+                     float* Y, const kite_mlp_prior* prior) {
   if (!ctx) return KITE_ERR_ARG;
   ctx->last_error.clear();
   if (!params || !X || !Y || n < 1) return fail(ctx, KITE_ERR_ARG, "need params, X, Y and n >= 1");
+  if (check_prior(ctx, prior) != KITE_OK) return KITE_ERR_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
   Staging sg{ctx, {}};
   const float *Xd, *Sd;
@@ -401,7 +418,7 @@ int kite_mlp_forward(kite_ctx* ctx, const float* params, const float* X, int n, 
   int rc = sg.in(X, (size_t)n * KITE_MLP_IN, &Xd);
   if (rc == KITE_OK) rc = sg.in(scale, KITE_MLP_IN, &Sd);
   if (rc == KITE_OK) rc = sg.out(Y, (size_t)n * KITE_MLP_OUT, &Yd);
-  if (rc == KITE_OK) rc = mlp_forward_impl(ctx, params, Xd, n, Sd, Yd);
+  if (rc == KITE_OK) rc = mlp_forward_impl(ctx, params, Xd, n, Sd, Yd, prior);
   if (rc == KITE_OK) rc = sg.back(Y, Yd, (size_t)n * KITE_MLP_OUT);
   cudaStreamSynchronize(ctx->stream);
   return rc;
@@ -463,8 +480,10 @@ int kite_moments_1d_batched(kite_ctx* ctx, int count, const kite_system* systems
     if (k.precision != KITE_FP32) return fail(ctx, KITE_ERR_UNSUPPORTED, "the batched sweep is FP32");
     if (k.R != kpms[0].R || k.R < 1 || k.R > 8)
       return fail(ctx, KITE_ERR_ARG, "all systems need the same R, 1 <= R <= 8");
-    if (k.S != 1 || k.r0 || k.r_last)
-      return fail(ctx, KITE_ERR_ARG, "batched systems take S = 1 and no r0/r_last");
+    if (k.S != 1 || k.r0 || k.r_last || k.reserved != 0)
+      return fail(ctx, KITE_ERR_ARG, "batched systems take S = 1, no r0/r_last, reserved = 0");
+    if ((k.doubling != 0 && k.doubling != 1) || k.doubling != kpms[0].doubling)
+      return fail(ctx, KITE_ERR_ARG, "all systems of a batch need the same doubling, 0 or 1");
     if (k.M < 1 || k.M > (1 << 20)) return fail(ctx, KITE_ERR_ARG, "M out of range");
     rc = resolve_bounds(ctx, &systems[i], k.e_min, k.e_max, &scales[i]);
     if (rc != KITE_OK) return rc;
@@ -488,6 +507,8 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   if (kpm->precision != KITE_FP32)
     return fail(ctx, KITE_ERR_UNSUPPORTED, "2D moments run the FP32 recursion only");
   if ((double)kpm->R * kpm->S > 65536.0) return fail(ctx, KITE_ERR_ARG, "R*S > 65536");
+  if (kpm->doubling != 0 || kpm->reserved != 0)
+    return fail(ctx, KITE_ERR_ARG, "the 2D moments take doubling = 0 and reserved = 0");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
   Scale sc;
   rc = resolve_bounds(ctx, sys, kpm->e_min, kpm->e_max, &sc);

@@ -41,6 +41,18 @@ __global__ void k_reduce(const double* __restrict__ partial, int M, int G, int Q
   mu_vec[((size_t)(vec_base + v) * M + n) * 2 + comp] = ne > 0.0 ? sum / ne : 0.0;
 }
 
+// Moment doubling (T_n^2 = (T_2n + T_0)/2, T_{n+1} T_n = (T_{2n+1} + T_1)/2): slot k >= 2
+// holds <r_n|r_n> (k = 2n) or <r_n|r_{n+1}> (k = 2n+1); mu_k = 2 slot_k - mu_(k mod 2).
+__global__ void k_undouble(double* __restrict__ mu_vec, int M, int nvec, int vec_base) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nvec * M) return;
+  const int v = idx / M, n = idx - (idx / M) * M;
+  if (n < 2) return;
+  double* m = mu_vec + (size_t)(vec_base + v) * M * 2;
+  m[2 * n] = 2.0 * m[2 * n] - m[2 * (n & 1)];
+  m[2 * n + 1] = 2.0 * m[2 * n + 1] - m[2 * (n & 1) + 1];
+}
+
 __global__ void k_average(const double* __restrict__ mu_vec, int nv, int M, double* __restrict__ mu,
                           double* __restrict__ imag) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -62,8 +74,13 @@ struct Plan {
   int Lx, Ly, sorb;
   int R, S, M;
   bool fp64;
+  bool doubling;  // two moments per step from <r_n|r_n> and <r_n|r_{n+1}>
   int max_batch;  // vectors per pass
 };
+
+// recursion steps that write r_{n+1}: M - 1 plainly; with doubling, the step from r_n
+// also yields mu_2n and mu_2n+1, so steps n = 0 .. ceil(M/2) - 1 suffice
+inline int steps_for(const Plan& p) { return p.doubling ? (p.M + 1) / 2 : p.M - 1; }
 
 template <typename Real, int LAT, int C>
 int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, void* bA,
@@ -79,6 +96,34 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
   auto where = [&](int n) -> void* { return n == 0 ? r0 : ((n & 1) ? bA : bB); };
   KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
   constexpr int SM = StepShape<LAT, C>::SMEM;
+  if (p.doubling) {
+    // step 0: r_1 = H~ r_0 with <r_0|r_0> -> slot 0 and <r_0|r_1> -> slot 1; step n >= 1
+    // (r_{n+1} from r_n, r_{n-1}): <r_n|r_n> -> slot 2n, <r_n|r_{n+1}> -> slot 2n+1
+    const int steps = steps_for(p);
+    k_step<Real, LAT, C, true, 3><<<G, kBlock, SM, st>>>(nullptr, r0, bA, nullptr, vt, tt, p.Lx,
+                                                         p.Ly, units, partial + (size_t)G * Q,
+                                                         partial, ctx->d_status,
+                                                         ctx->debug_stall, FamOut{});
+    ctx->debug_stall = 0;
+    for (int n = 1; n < steps; ++n)
+      k_step<Real, LAT, C, false, 3><<<G, kBlock, SM, st>>>(
+          where(n - 1), where(n), where(n + 1), nullptr, vt, tt, p.Lx, p.Ly, units,
+          partial + (size_t)(2 * n + 1) * G * Q, partial + (size_t)(2 * n) * G * Q, ctx->d_status,
+          0, FamOut{});
+    KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
+    KITE_CUDA_TRY(ctx, cudaGetLastError());
+    const int total = M * Q;
+    k_reduce<<<(total + 255) / 256, 256, 0, st>>>(partial, M, G, Q, nvec, vec_base, n_eff, mu_vec);
+    k_undouble<<<(nvec * M + 255) / 256, 256, 0, st>>>(mu_vec, M, nvec, vec_base);
+    KITE_CUDA_TRY(ctx, cudaGetLastError());
+    float ms = 0.f;
+    KITE_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev3));
+    KITE_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev3));
+    *step_seconds += 1e-3 * ms;
+    *step_launches += steps;
+    *last_cur = *last_prev = nullptr;
+    return KITE_OK;
+  }
   if (M >= 2)
     k_step<Real, LAT, C, true><<<G, kBlock, SM, st>>>(nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly,
                                                       units, partial + (size_t)G * Q, partial,
@@ -137,6 +182,7 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
   p.R = kpm->R;
   p.S = kpm->S;
   p.M = kpm->M;
+  p.doubling = kpm->doubling != 0;
   p.max_batch = kMaxC * VPC;
   auto chunks_for = [&](int nvec) {
     const int c = (nvec + VPC - 1) / VPC;
@@ -161,7 +207,7 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
     *r0 = k.take<char>(vec_bytes);
     *bA = k.take<char>(vec_bytes);
     *bB = k.take<char>(vec_bytes);
-    *partial = k.take<double>((size_t)std::max(p.M, 2) * Gmax * 2 * Cmax * VPC);
+    *partial = k.take<double>((size_t)(std::max(p.M, 2) + 1) * Gmax * 2 * Cmax * VPC);
     *ne = k.take<unsigned long long>(1);
     *mu_vec = k.take<double>(nvec_total * p.M * 2);
   };
@@ -232,12 +278,18 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
       // algorithmic bytes of this batch's step launches: per orbital and step, read
       // r_{n-1}, r_n, r_0 and write r_{n+1} for each of the batch's 16-byte chunks, and
       // read the shared on-site term (the first step has no r_{n-1} and reads r_0 once)
-      if (p.M >= 2) {
+      if (p.doubling) {
+        // doubling never re-reads r_0: r_{n-1}, r_n in, r_{n+1} out per later step
+        const double chunk_bytes = 16.0 * SORB * C * (double)p.ncell;
+        const int steps = steps_for(p);
+        step_bytes += (double)(steps - 1) * (3.0 * chunk_bytes + (double)p.N * sizeof(Real)) +
+                      (2.0 * chunk_bytes + (double)p.N * sizeof(Real));
+      } else if (p.M >= 2) {
         const double chunk_bytes = 16.0 * SORB * C * (double)p.ncell;
         step_bytes += (double)(p.M - 2) * (4.0 * chunk_bytes + (double)p.N * sizeof(Real)) +
                       (2.0 * chunk_bytes + (double)p.N * sizeof(Real));
       }
-      if (kpm->r_last) {
+      if (kpm->r_last && !p.doubling) {
         // extract into a device staging area or directly into a device destination
         const int64_t nchunk = p.ncell * SORB * C;
         const int64_t blocks = std::min<int64_t>((nchunk + 255) / 256, (int64_t)ctx->num_sms * 16);
@@ -294,8 +346,8 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
     stats->updates = (double)n_eff_last * p.M * p.R * p.S;
     // algorithmic bytes per orbital and step: read r_{n-1}, r_n, r_0, write r_{n+1}
     // for every vector, plus the shared on-site term
-    const double per_orb_step = 4.0 * 2.0 * sizeof(Real) * p.R + (double)sizeof(Real);
-    stats->bytes_moved = per_orb_step * (double)p.N * (double)(p.M > 1 ? p.M - 1 : 0) * p.S;
+    const double per_orb_step = (p.doubling ? 3.0 : 4.0) * 2.0 * sizeof(Real) * p.R + (double)sizeof(Real);
+    stats->bytes_moved = per_orb_step * (double)p.N * (double)steps_for(p) * p.S;
     stats->gbps = stats->seconds > 0 ? stats->bytes_moved / stats->seconds * 1e-9 : 0.0;
     stats->n_eff = n_eff_last;
     stats->grid = grid_used;

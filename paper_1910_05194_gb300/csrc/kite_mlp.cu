@@ -37,6 +37,7 @@ constexpr int64_t kOffW1 = 0, kOffB1 = kOffW1 + (int64_t)HID * IN, kOffW2 = kOff
 // ------------------------------------------------------------------------------------
 struct GemmEpi {
   const float* bias;
+  const float* add;  // optional addend [M][ldc] (the residual prior)
   const __nv_bfloat16* mask;
   int relu;
   float* C32;
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(128) k_mlp_gemm(const __nv_bfloat16* __restric
     if (gm >= M || gn >= N) continue;
     float v = ep.alpha * Cs[r][c];
     if (ep.bias) v += ep.bias[gn];
+    if (ep.add) v += ep.add[(int64_t)gm * ep.ldc + gn];
     if (ep.relu) v = fmaxf(v, 0.0f);
     if (ep.mask && !(__bfloat162float(ep.mask[(int64_t)gm * ep.ldc + gn]) > 0.0f)) v = 0.0f;
     if (ep.C32) ep.C32[(int64_t)gm * ep.ldc + gn] = v;
@@ -107,10 +109,52 @@ __global__ void __launch_bounds__(128) k_mlp_gemm(const __nv_bfloat16* __restric
   }
 }
 
-// rows of X (FP32, optional per-column scale) gathered by idx -> BF16
+// Jackson kernel of order IN (Sec. 2a, kernel polynomial method) times the Chebyshev
+// weight 2 - delta_k0 of Eq. e8a, computed on the host.
+struct PriorCoef {
+  double c[IN];
+};
+
+PriorCoef prior_coef() {
+  PriorCoef pc;
+  const double pi = 3.141592653589793, q = pi / (IN + 1);
+  for (int k = 0; k < IN; ++k) {
+    const double g = ((IN - k + 1) * std::cos(q * k) + std::sin(q * k) * std::cos(q) / std::sin(q)) / (IN + 1);
+    pc.c[k] = (k == 0 ? 1.0 : 2.0) * g;
+  }
+  return pc;
+}
+
+// Residual prior P[r][j] = sum_k c_k X[r][k] T_k(eps_j) / (pi a sqrt(1 - eps_j^2)) on the
+// midpoint grid eps_j = -1 + (2j+1)/OUT, a = (e_max - e_min)/2: the Jackson density per eV
+// from the raw moments X (FP64 sums, forward Chebyshev recurrence).  One block per row.
+__global__ void __launch_bounds__(256) k_mlp_prior(const float* __restrict__ X, int rows, const PriorCoef pc,
+                                                   double inv_pi_a, float* __restrict__ P) {
+  __shared__ double cx[IN];
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < IN; k += blockDim.x) cx[k] = pc.c[k] * (double)X[(int64_t)r * IN + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < OUT; j += blockDim.x) {
+      const double e = -1.0 + (2.0 * j + 1.0) / OUT;
+      double t0 = 1.0, t1 = e, sum = cx[0] + cx[1] * e;
+      for (int k = 2; k < IN; ++k) {
+        const double t2 = 2.0 * e * t1 - t0;
+        sum += cx[k] * t2;
+        t0 = t1;
+        t1 = t2;
+      }
+      P[(int64_t)r * OUT + j] = (float)(sum * inv_pi_a / sqrt(1.0 - e * e));
+    }
+  }
+}
+
+// rows of X (FP32, optional per-column scale) gathered by idx -> BF16; targets gathered
+// alongside, minus the prior rows Tsub when given
 __global__ void k_mlp_gather(const float* __restrict__ X, const int* __restrict__ idx, int rows, int cols,
                              const float* __restrict__ scale, __nv_bfloat16* __restrict__ out,
-                             const float* __restrict__ T, float* __restrict__ Tout, int tcols) {
+                             const float* __restrict__ T, float* __restrict__ Tout, int tcols,
+                             const float* __restrict__ Tsub = nullptr) {
   const int64_t total = (int64_t)rows * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / cols), c = (int)(e % cols);
@@ -122,7 +166,7 @@ __global__ void k_mlp_gather(const float* __restrict__ X, const int* __restrict_
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tt; e += (int64_t)gridDim.x * blockDim.x) {
       const int r = (int)(e / tcols), c = (int)(e % tcols);
       const int64_t src = idx ? idx[r] : r;
-      Tout[e] = T[src * tcols + c];
+      Tout[e] = T[src * tcols + c] - (Tsub ? Tsub[src * tcols + c] : 0.0f);
     }
   }
 }
@@ -221,6 +265,7 @@ GemmEpi epi(float* C32, __nv_bfloat16* C16, int ldc, const float* bias = nullptr
             const __nv_bfloat16* mask = nullptr) {
   GemmEpi e;
   e.bias = bias;
+  e.add = nullptr;
   e.mask = mask;
   e.relu = relu;
   e.C32 = C32;
@@ -230,11 +275,21 @@ GemmEpi epi(float* C32, __nv_bfloat16* C16, int ldc, const float* bias = nullptr
   return e;
 }
 
-// forward on rows already in net.X (BF16, scaled); writes net.Y (FP32)
-void forward(cudaStream_t st, const Net& net, const float* p32, int rows) {
+// forward on rows already in net.X (BF16, scaled); writes net.Y (FP32) = network (+ add)
+void forward(cudaStream_t st, const Net& net, const float* p32, int rows, const float* add = nullptr) {
   gemm(st, net.X, IN, 0, net.pb + kOffW1, IN, 1, rows, HID, IN, epi(nullptr, net.H1, HID, p32 + kOffB1, 1));
   gemm(st, net.H1, HID, 0, net.pb + kOffW2, HID, 1, rows, HID, HID, epi(nullptr, net.H2, HID, p32 + kOffB2, 1));
-  gemm(st, net.H2, HID, 0, net.pb + kOffW3, HID, 1, rows, OUT, HID, epi(net.Y, nullptr, OUT, p32 + kOffB3));
+  GemmEpi e3 = epi(net.Y, nullptr, OUT, p32 + kOffB3);
+  e3.add = add;
+  gemm(st, net.H2, HID, 0, net.pb + kOffW3, HID, 1, rows, OUT, HID, e3);
+}
+
+bool use_prior(const kite_mlp_prior* prior) { return prior && prior->kind == KITE_PRIOR_JACKSON; }
+
+void launch_prior(cudaStream_t st, int num_sms, const float* X, int rows, const kite_mlp_prior* prior, float* P) {
+  const double a = 0.5 * (prior->e_max - prior->e_min);
+  const int blocks = std::max(1, std::min(rows, num_sms * 8));
+  k_mlp_prior<<<blocks, 256, 0, st>>>(X, rows, prior_coef(), 1.0 / (3.141592653589793 * a), P);
 }
 
 // backward of the mean L1 loss over rows x OUT; gradient into net.grad
@@ -306,11 +361,13 @@ int mlp_gradient_impl(kite_ctx* ctx, const float* params, const float* X, const 
   return KITE_OK;
 }
 
-int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, const float* scale, float* Y) {
+int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, const float* scale, float* Y,
+                     const kite_mlp_prior* prior) {
   const int chunk = 4096;
   Net net;
   float* ex;
-  int rc = carve_net(ctx, std::min(n, chunk), &net, &ex, kParams);
+  const bool pri = use_prior(prior);
+  int rc = carve_net(ctx, std::min(n, chunk), &net, &ex, kParams + (pri ? (size_t)std::min(n, chunk) * OUT : 0));
   if (rc != KITE_OK) return rc;
   cudaStream_t st = ctx->stream;
   KITE_CUDA_TRY(ctx, cudaMemcpyAsync(ex, params, sizeof(float) * kParams, cudaMemcpyDefault, st));
@@ -318,7 +375,9 @@ int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, 
   for (int r0 = 0; r0 < n; r0 += chunk) {
     const int rows = std::min(chunk, n - r0);
     k_mlp_gather<<<1024, 256, 0, st>>>(X + (int64_t)r0 * IN, nullptr, rows, IN, scale, net.X, nullptr, nullptr, 0);
-    forward(st, net, ex, rows);
+    float* P = pri ? ex + kParams : nullptr;
+    if (pri) launch_prior(st, ctx->num_sms, X + (int64_t)r0 * IN, rows, prior, P);
+    forward(st, net, ex, rows, P);
     KITE_CUDA_TRY(ctx, cudaMemcpyAsync(Y + (int64_t)r0 * OUT, net.Y, sizeof(float) * rows * OUT, cudaMemcpyDefault, st));
   }
   KITE_CUDA_TRY(ctx, cudaGetLastError());
@@ -327,11 +386,13 @@ int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, 
 }
 
 int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const float* scale,
-                   const kite_mlp_train_cfg* cfg, float* params, float* loss_curve) {
+                   const kite_mlp_train_cfg* cfg, float* params, float* loss_curve,
+                   const kite_mlp_prior* prior) {
   const int bs = std::max(1, std::min(cfg->batch, n));
   Net net;
   float* ex;
-  int rc = carve_net(ctx, bs, &net, &ex, 3 * kParams + 4096 + (size_t)bs);
+  const bool pri = use_prior(prior);
+  int rc = carve_net(ctx, bs, &net, &ex, 3 * kParams + 4096 + (size_t)bs + (pri ? (size_t)n * OUT : 0));
   if (rc != KITE_OK) return rc;
   cudaStream_t st = ctx->stream;
   float* p32 = ex;
@@ -339,6 +400,9 @@ int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const f
   float* v = ex + 2 * kParams;
   double* lsum = reinterpret_cast<double*>(ex + 3 * kParams);
   int* d_idx = reinterpret_cast<int*>(ex + 3 * kParams + 4096);
+  // the prior of every training row, once; the batches gather T - prior as targets
+  float* P = pri ? ex + 3 * kParams + 4096 + bs : nullptr;
+  if (pri) launch_prior(st, ctx->num_sms, X, n, prior, P);
   KITE_CUDA_TRY(ctx, cudaMemcpyAsync(p32, params, sizeof(float) * kParams, cudaMemcpyDefault, st));
   KITE_CUDA_TRY(ctx, cudaMemsetAsync(m, 0, sizeof(float) * 2 * kParams, st));
   k_mlp_tobf16<<<1024, 256, 0, st>>>(p32, net.pb, kParams);
@@ -357,7 +421,7 @@ int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const f
       const int rows = std::min(bs, n - b * bs);
       KITE_CUDA_TRY(ctx, cudaMemcpyAsync(d_idx, order.data() + (size_t)b * bs, sizeof(int) * rows,
                                          cudaMemcpyHostToDevice, st));
-      k_mlp_gather<<<512, 256, 0, st>>>(X, d_idx, rows, IN, scale, net.X, T, net.T, OUT);
+      k_mlp_gather<<<512, 256, 0, st>>>(X, d_idx, rows, IN, scale, net.X, T, net.T, OUT, P);
       forward(st, net, p32, rows);
       backward(st, net, rows, lsum, lblocks);
       ++t;

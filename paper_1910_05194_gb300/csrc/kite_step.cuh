@@ -135,7 +135,8 @@ struct StepShape {
 // Kp bf16 values (hi = bf16(x), lo = bf16(x - hi)) holding interleaved (re, im) per
 // orbital.  MODE 1 writes the step's output r_{n+1} as row `col` of the A family;
 // MODE 2 writes h~x r_n, built from the neighbours already staged for the step, as
-// rows `col` (b) and `col + M` (-i b) of the extended B family.
+// rows `col` (b) and `col + M` (-i b) of the extended B family.  MODE 3 (moment doubling)
+// accumulates <r_n|r_{n+1}> and <r_n|r_n> instead of <r_0|r_{n+1}>; r_0 is not staged.
 constexpr int kMaxFamVecs = 2;
 struct FamOut {
   __nv_bfloat16* hi[kMaxFamVecs];
@@ -214,7 +215,7 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
                                           Real tt, int Lx, int Ly, long long units,
                                           double* __restrict__ partial, double* __restrict__ partial0,
                                           int* __restrict__ err, int stall, const FamOut& fam) {
-  static_assert(MODE == 0 || (sizeof(Real) == 4 && C * 2 <= kMaxFamVecs),
+  static_assert(MODE == 0 || MODE == 3 || (sizeof(Real) == 4 && C * 2 <= kMaxFamVecs),
                 "family modes run on FP32 batches of at most two vectors");
   using Ch = Chunk<Real>;
   using Acc = typename AccT<Real>::T;
@@ -337,7 +338,26 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
           out.v[k] = vacant ? Real(0) : o;
         }
         out.st(r_out, (((size_t)y * Lx + x0 + xl) * SORB + s) * C + c);
-        if constexpr (MODE != 0) {
+        if constexpr (MODE == 3) {
+          // moment doubling: <r_n|r_{n+1}> into facc, <r_n|r_n> into facc0
+#pragma unroll
+          for (int q = 0; q < VPC; ++q) {
+            const Acc ar = me.v[2 * q], ai = me.v[2 * q + 1];
+            const Acc br = out.v[2 * q], bi = out.v[2 * q + 1];
+            facc[2 * q] += ar * br + ai * bi;
+            facc[2 * q + 1] += ar * bi - ai * br;
+            facc0[2 * q] += ar * ar + ai * ai;
+          }
+          if (++rows == kFlushRows) {
+            rows = 0;
+#pragma unroll
+            for (int k = 0; k < QT; ++k) {
+              dacc[k] += (double)facc[k];
+              dacc0[k] += (double)facc0[k];
+              facc[k] = facc0[k] = Acc(0);
+            }
+          }
+        } else if constexpr (MODE != 0) {
           const int64_t o = ((int64_t)y * Lx + x0 + xl) * SORB + s;
 #pragma unroll
           for (int q = 0; q < VPC; ++q) {
@@ -407,6 +427,8 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
   ring.gslot = gslot;
   if constexpr (MODE == 0)
     moment_partials<QT, C>(dacc, facc, dacc0, facc0, FIRST, stages, partial, partial0, cta);
+  if constexpr (MODE == 3)
+    moment_partials<QT, C>(dacc, facc, dacc0, facc0, true, stages, partial, partial0, cta);
   return true;
 }
 
@@ -460,6 +482,8 @@ int grid_for(kite_ctx* ctx, long long units) {
     const int smem = StepShape<LAT, C>::SMEM;
     cudaFuncSetAttribute(k_step<Real, LAT, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_step<Real, LAT, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_step<Real, LAT, C, true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_step<Real, LAT, C, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_step<Real, LAT, C, FIRST>, kBlock, smem) !=
             cudaSuccess ||
         o < 1)

@@ -20,10 +20,10 @@ def ctx():
     c.close()
 
 
-def batch(ctx, specs, R=4):
+def batch(ctx, specs, R=4, doubling=False):
     systems = [kite.make_system(kite.SQUARE, sp["L"], sp.get("Ly", sp["L"]), -1.0, sp["W"], 0.0,
                                 sp.get("p", 0.0), sp["seed"]) for sp in specs]
-    kpms = [kite.make_kpm(sp["M"], R, 1, kite.FP32) for sp in specs]
+    kpms = [kite.make_kpm(sp["M"], R, 1, kite.FP32, doubling=doubling) for sp in specs]
     mus = [np.zeros(sp["M"]) for sp in specs]
     st = kite.moments_1d_batched(ctx, systems, kpms, mus)
     return mus, st
@@ -48,6 +48,23 @@ def test_mixed_batch_against_oracle(ctx):
     assert st.grid >= 2 and st.seconds > 0
 
 
+@pytest.mark.parametrize("R", [4, 1])
+def test_mixed_batch_with_moment_doubling(ctx, R):
+    """The same mixed batch with moment doubling (two moments per step, odd and tiny M,
+    multi-CTA and packed teams): same 1e-5 bar against the oracle's plain moments."""
+    specs = [dict(L=400, Ly=300, W=1.0, M=96, seed=11), dict(L=3, W=2.0, M=16, seed=12),
+             dict(L=17, Ly=5, W=0.0, M=33, seed=13), dict(L=130, W=4.0, M=64, seed=14, p=0.02),
+             dict(L=9, W=1.0, M=1, seed=17), dict(L=100, W=0.5, M=2, seed=18),
+             dict(L=77, W=3.5, M=201, seed=19)]
+    mus, st = batch(ctx, specs, R=R, doubling=True)
+    for sp, mu in zip(specs, mus):
+        assert np.max(np.abs(mu - oracle_mu(sp, R))) <= 1e-5, sp
+    with pytest.raises(kite.KiteError):  # doubling must be uniform over a batch
+        systems = [kite.make_system(kite.SQUARE, 8, 8, -1.0, 1.0, 0.0, 0.0, 1)] * 2
+        kite.moments_1d_batched(ctx, systems, [kite.make_kpm(8, 1, 1, kite.FP32, doubling=d)
+                                               for d in (True, False)], [np.zeros(8), np.zeros(8)])
+
+
 def test_team_barrier_timeout_is_reported(ctx):
     specs = [dict(L=600, W=1.0, M=24, seed=21), dict(L=20, W=1.0, M=8, seed=22)]
     kite.debug_stall_once(ctx)
@@ -70,3 +87,10 @@ def test_256_system_workload(ctx):
     cheap = sorted(range(256), key=lambda i: specs[i]["L"] ** 2 * specs[i]["M"])[:6]
     for i in cheap:
         assert np.max(np.abs(mus[i] - oracle_mu(specs[i]))) <= 1e-5, specs[i]
+    # the same workload with moment doubling: half the steps, same moments
+    mus_d, st_d = batch(ctx, specs, doubling=True)
+    print(f"256 systems, doubling: {st_d.updates / st_d.seconds:.3e} updates/s in {st_d.seconds:.3f} s")
+    for i in range(256):
+        assert np.max(np.abs(mus_d[i] - mus[i])) <= 2e-5, specs[i]
+    for i in cheap:
+        assert np.max(np.abs(mus_d[i] - oracle_mu(specs[i]))) <= 1e-5, specs[i]

@@ -35,7 +35,7 @@ def ksys(**kw):
 
 
 def run_gpu(ctx, sysd, M, R, S=1, precision=kite.FP32, r0=None, want_last=False, e_min=0.0,
-            e_max=0.0):
+            e_max=0.0, doubling=False):
     s = ksys(**sysd)
     n = oracle.norb(osys(**sysd))
     r0a = None
@@ -43,7 +43,7 @@ def run_gpu(ctx, sysd, M, R, S=1, precision=kite.FP32, r0=None, want_last=False,
         r0a = np.ascontiguousarray(np.stack([r0.real, r0.imag], -1).astype(np.float64))
     dt = np.complex64 if precision == kite.FP32 else np.complex128
     last = np.zeros((S * R, 2, n), dt) if want_last else None
-    kpm = kite.make_kpm(M, R, S, precision, e_min, e_max, r0a, last)
+    kpm = kite.make_kpm(M, R, S, precision, e_min, e_max, r0a, last, doubling=doubling)
     mu = np.zeros(M, np.float64)
     muv = np.zeros((S * R, M, 2), np.float64)
     st = kite.moments_1d(ctx, s, kpm, mu, muv)
@@ -123,6 +123,33 @@ def test_fp32_moments_within_north_star_tolerance(ctx):
     ref = oracle.moments_1d(osys(**d), M, R)
     assert np.max(np.abs(mu - ref.real.mean(0))) <= 1e-5
     assert np.max(np.abs(muv - ref)) <= 1e-5
+
+
+DOUBLING_CASES = [
+    # (system, M, R, S, precision, bar): bars as for the plain path
+    (dict(lattice=oracle.HONEYCOMB, Lx=64, Ly=64, t=-2.7, W=1.0, seed=1), 256, 4, 1, "fp64", 1e-12),
+    (dict(lattice=oracle.HONEYCOMB, Lx=96, Ly=80, t=-2.7, W=2.0, p_vac=0.005, seed=2), 512, 8, 1,
+     "fp32", 1e-5),
+    (dict(lattice=oracle.SQUARE, Lx=300, Ly=5, t=-1.0, W=3.0, p_vac=0.05, seed=5), 33, 6, 2, "fp32", 1e-5),
+    (dict(lattice=oracle.HONEYCOMB, Lx=37, Ly=29, t=-2.7, W=2.0, delta=0.5, p_vac=0.02, seed=8), 3, 3,
+     1, "fp64", 1e-12),
+    (dict(lattice=oracle.SQUARE, Lx=17, Ly=40, t=-1.0, W=1.0, seed=3), 2, 1, 1, "fp32", 1e-5),
+    (dict(lattice=oracle.SQUARE, Lx=17, Ly=40, t=-1.0, W=1.0, seed=3), 1, 1, 1, "fp64", 1e-12),
+]
+
+
+@pytest.mark.parametrize("case", DOUBLING_CASES)
+def test_moment_doubling_matches_oracle(ctx, case):
+    """Moment doubling (mu_2n = 2<r_n|r_n> - mu_0, mu_2n+1 = 2<r_n|r_n+1> - mu_1) against the
+    oracle's plain mu_n = <r_0|T_n r_0>: same bars as the plain path, ceil(M/2) steps, odd
+    and tiny M, realisations and padded vector batches included."""
+    d, M, R, S, prec, bar = case
+    precision = kite.FP64 if prec == "fp64" else kite.FP32
+    mu, muv, _, st = run_gpu(ctx, d, M, R, S=S, precision=precision, doubling=True)
+    ref = np.concatenate([oracle.moments_1d(osys(**d), M, R, realisation=s) for s in range(S)], 0)
+    assert np.max(np.abs(muv - ref)) <= bar
+    assert np.max(np.abs(mu - ref.real.mean(0))) <= bar
+    assert st.step_launches == S * ((R + (7 if prec == "fp32" else 3)) // (8 if prec == "fp32" else 4)) * ((M + 1) // 2)
 
 
 def test_exact_trace_with_basis_vectors_pins_device_draws(ctx):
