@@ -287,6 +287,22 @@ def cpgf_coeffs(n_max: int, z_real, eta: float, sigma: int):
     return -2.0 * sigma * 1j * np.exp(-sigma * 1j * n * th[None, :]) / np.sqrt(1.0 - z * z)[None, :]
 
 
+def green(mu, E, e_min: float, e_max: float, eta: float, g=None):
+    """Average Green's function per orbital G(E + i eta) in 1/eV from raw moments
+    (Eqs. green_function_cheb_expansion/b traced as in Eq. e7): with eps = (E - de_plus) /
+    de_minus and eta~ = eta / de_minus,
+      G(E + i eta) = (1/de_minus) sum_n [g_n mu_n / (1 + delta_n0)] g^{+,eta~}_n(eps),
+    optionally damped by a kernel g.  The eta-resolved density is -Im G / pi."""
+    mu = np.real(np.asarray(mu, np.float64))
+    M = mu.shape[0]
+    dm, dp = 0.5 * (e_max - e_min), 0.5 * (e_max + e_min)
+    eps = (np.asarray(E, np.float64) - dp) / dm
+    w = np.where(np.arange(M) == 0, 0.5, 1.0) * mu
+    if g is not None:
+        w = w * np.asarray(g, np.float64)
+    return (w @ cpgf_coeffs(M, eps, eta / dm, +1)) / dm
+
+
 def unit_cell_factor(lattice: int):
     """(orbitals per cell) * a^2 / Omega_c: honeycomb 2 * 2/sqrt(3), square 1."""
     return 2.0 * 2.0 / np.sqrt(3.0) if lattice == HONEYCOMB else 1.0

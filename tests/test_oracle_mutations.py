@@ -40,21 +40,33 @@ MUTATIONS = [
 ]
 
 
-@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pins_catch_planted_mistake(tmp_path, name, old, new):
+def run_pins_on_copy(tmp_path, old, new):
     src_dir = os.path.join(ROOT, "oracle")
     dst = tmp_path / "oracle"
     dst.mkdir()
-    for f in ("__init__.py", "kite_oracle.h"):
-        shutil.copy(os.path.join(src_dir, f), dst / f)
+    for f in os.listdir(src_dir):  # every module of the oracle package, not the build
+        if f.endswith((".py", ".h")):
+            shutil.copy(os.path.join(src_dir, f), dst / f)
     with open(os.path.join(src_dir, "kite_oracle.c")) as f:
         src = f.read()
-    assert old in src, f"mutation anchor missing: {name}"
+    assert old in src, f"mutation anchor missing: {old}"
     (dst / "kite_oracle.c").write_text(src.replace(old, new, 1))
     shutil.copy(os.path.join(ROOT, "tests", "test_oracle_pins.py"), tmp_path / "test_oracle_pins.py")
     env = dict(os.environ, PYTHONPATH=str(tmp_path))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
-                        "-p", "no:randomly", str(tmp_path / "test_oracle_pins.py")],
-                       cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
+                           "-p", "no:randomly", str(tmp_path / "test_oracle_pins.py")],
+                          cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
+
+
+def test_unmutated_copy_passes(tmp_path):
+    """The control: the copied oracle and pins pass as they are, so a failure below is
+    the planted mistake's doing."""
+    r = run_pins_on_copy(tmp_path, "", "")
+    assert r.returncode == 0, r.stdout[-3000:]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, name, old, new):
+    r = run_pins_on_copy(tmp_path, old, new)
     assert r.returncode != 0, f"no pin caught mutation '{name}':\n{r.stdout[-2000:]}"
     assert "failed" in r.stdout, r.stdout[-2000:]

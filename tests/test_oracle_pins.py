@@ -542,3 +542,23 @@ def test_mlp_prior_closed_forms():
     rho = mlp.prior(mu, e_min, e_max, n_out=1024)[0]
     assert abs(np.sum(rho) * a * 2.0 / 1024 - 1.0) < 1e-3
     assert abs(mlp.midpoint_eps(1024)[np.argmax(rho)] - x0) < 4.0 / 1024
+
+
+def test_green_function_matches_exact_resolvent_trace():
+    """G(E + i eta) from exact-trace moments of a small disordered lattice equals the
+    resolvent trace (1/N) sum_k 1/(E - E_k + i eta) of its eigenvalues once the CPGF
+    series has converged (M >> de_minus / eta); its -Im/pi integrates to ~1."""
+    sys_ = oracle.make_system(lattice=oracle.HONEYCOMB, Lx=4, Ly=3, t=-2.7, W=2.0, p_vac=0.1, seed=21)
+    lo, hi = oracle.bounds_auto(sys_)
+    M = 3000
+    mu = exact_trace_moments(sys_, M).real
+    H, keep, vac = dense_h(sys_)
+    Ek = np.linalg.eigvalsh(H) * 0.5 * (hi - lo) + 0.5 * (hi + lo)  # back to eV
+    eta = 0.15
+    E = np.linspace(lo * 0.95, hi * 0.95, 41)
+    G = oracle.green(mu, E, lo, hi, eta)
+    ref = np.array([np.mean(1.0 / (e - Ek + 1j * eta)) for e in E])
+    assert np.max(np.abs(G - ref)) < 1e-8 * np.max(np.abs(ref))
+    Ef = np.linspace(lo, hi, 20001)
+    rho = -oracle.green(mu, Ef, lo, hi, eta).imag / np.pi
+    assert abs(np.trapezoid(rho, Ef) - 1.0) < 0.05  # Lorentzian tails beyond the window
