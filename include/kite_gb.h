@@ -186,22 +186,29 @@ int kite_debug_stall_once(kite_ctx* ctx, int enable);
 
 /* ---- 2D moments ----------------------------------------------------------------- */
 
-/* 2D moments of the first-order Kubo-Bastin conductivity sigma_xx (Sec. 2b,
+/* Velocity directions of the 2D moments. */
+#define KITE_DIR_X 0
+#define KITE_DIR_Y 1
+
+/* 2D moments of the first-order Kubo-Bastin conductivity sigma_ab (Sec. 2b,
  * Eqs. cond 1st order, Gammanm, conductivity_1st_order):
- *   mu_nm = (1/(S R)) sum_{s,r} <r| v T_n(H~) v T_m(H~) |r> / N_eff,   v = -i h~x,
- * with h~x = [x, H~] applied matrix-free (x in units of the lattice constant a; bond
- * x-offsets 0, +-a/2 on the honeycomb lattice, +-a on the square lattice).  Computed as
- * mu_nm = <a_n|b_m> with the stored families a_n = T_n h~x r and b_m = h~x T_m r, and
+ *   mu_nm = (1/(S R)) sum_{s,r} <r| v_a T_n(H~) v_b T_m(H~) |r> / N_eff,   v_d = -i h~d,
+ * with h~d = [r_d, H~] applied matrix-free (positions in units of the lattice constant a;
+ * honeycomb orbital positions of the paper's lattice set-up: a1 = (1, 0),
+ * a2 = (1/2, sqrt(3)/2), A at (0, -a_cc/2), B at (0, a_cc/2), a_cc = 1/sqrt(3), so the
+ * bond x-offsets are 0, +-1/2 and the y-offsets a_cc, -a_cc/2; square: +-1).  Computed as
+ * mu_nm = <a_n|b_m> with the stored families a_n = T_n h~a r and b_m = h~b T_m r, and
  * contracted on the tensor cores (see kite_inner_products).  The paper's tensor is
- * Gamma^{x,x}_nm = -mu_nm / ((1 + delta_n0)(1 + delta_m0)).
+ * Gamma^{a,b}_nm = -mu_nm / ((1 + delta_n0)(1 + delta_m0)).
+ *   alpha, beta  KITE_DIR_X or KITE_DIR_Y (a and b above)
  *   kpm->precision must be KITE_FP32 (complex FP32 recursion, split-BF16 contraction,
  *   FP64 sums); kpm->r0 may give start vectors; kpm->r_last is ignored.
  *   mu_nm  [M][M] complex FP64 interleaved (re, im), row n, column m; host or device.
  * Work memory: about 24 * M * N bytes per pair of random vectors.
  * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA, KITE_ERR_TIMEOUT,
  *         KITE_ERR_UNSUPPORTED (precision other than FP32). */
-int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, double* mu_nm,
-                    kite_stats* st);
+int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, int alpha,
+                    int beta, double* mu_nm, kite_stats* st);
 
 /* ---- 2D moments: the contraction primitive ---------------------------------------- */
 
@@ -210,9 +217,11 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
  *   C[n][m] = scale * sum_{i<N} conj(A[n][i]) * B[m][i],   n < M, m < M2.
  * Runs on the tensor cores (tcgen05.mma): every FP32 input x is split into
  * bf16 hi = bf16(x) and lo = bf16(x - hi); products keep hi*hi + hi*lo + lo*hi
- * (`products` = 3) or also lo*lo (`products` = 4 or 0, the default); sums are FP32 inside
- * a K sub-chunk of `sub_k` products and FP64 above (sub_k = 0: default 512; the
- * tensor core's FP32 accumulation drifts ~5e-9 per product for one-signed terms).
+ * (`products` = 3) or also lo*lo (`products` = 4 or 0, the default).  Sums are FP32 inside
+ * a K sub-chunk of `sub_k` products (sub_k = 0: default 512; the tensor core's FP32
+ * accumulation drifts ~5e-9 per product for one-signed terms), then FP32 over `fold`
+ * sub-chunks (fold = 0: default 16; 1 sends every sub-chunk to FP64 directly), and FP64
+ * above that.
  *   A  [M][N]  complex FP32 interleaved (re, im), host or device
  *   B  [M2][N] complex FP32 interleaved, host or device
  *   C  [M][M2] complex FP64 interleaved, host or device (overwritten)
@@ -220,7 +229,7 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
  * another stream before the call (e.g. bind the context to that stream).
  * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA, KITE_ERR_TIMEOUT. */
 int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
-                        double scale, double* C, int sub_k, int products);
+                        double scale, double* C, int sub_k, int products, int fold);
 
 /* Moments of many independent systems in one persistent, graph-captured launch (the S
  * realisations and the independent samples of Eq. PcomplexityFactor, batched).  Each
@@ -247,8 +256,9 @@ int kite_moments_1d_batched(kite_ctx* ctx, int count, const kite_system* systems
  * KITE_MLP_OUT energies reconstructed from many more moments (the resolution of the
  * reconstruction scales as the inverse number of moments, Sec. 2a).  Parameters are one
  * flat FP32 vector W1[H][IN], b1[H], W2[H][H], b2[H], W3[OUT][H], b3[OUT] (row-major).
- * Inputs are multiplied by the per-column `scale` [IN] (NULL = 1) on the device.  All
- * pointers may be host or device memory. */
+ * Inputs are normalised on the device as (x - shift[c]) * scale[c] with per-column
+ * `shift` [IN] (NULL = 0) and `scale` [IN] (NULL = 1).  All pointers may be host or
+ * device memory. */
 #define KITE_MLP_IN 128
 #define KITE_MLP_HIDDEN 512
 #define KITE_MLP_OUT 1024
@@ -256,7 +266,7 @@ int kite_moments_1d_batched(kite_ctx* ctx, int count, const kite_system* systems
 /* Optional residual prior of the network (NULL = none).  With KITE_PRIOR_JACKSON the
  * network's output is added to the Jackson reconstruction (Eq. e8a, Jackson kernel of
  * order KITE_MLP_IN) from the same first KITE_MLP_IN moments -- the raw X rows, before
- * `scale` -- on the midpoint grid eps_j = -1 + (2j+1)/KITE_MLP_OUT of the window
+ * shift and scale -- on the midpoint grid eps_j = -1 + (2j+1)/KITE_MLP_OUT of the window
  * [e_min, e_max] (density per eV, as kite_reconstruct_dos), so the network learns only
  * the correction that the many-moment reconstruction adds.  Training subtracts the same
  * prior from the targets. */
@@ -286,19 +296,20 @@ int64_t kite_mlp_param_count(void);
  * loss_curve [epochs] (or NULL) receives the mean training loss of each epoch.  prior
  * (or NULL) as above: the loss is taken on prior + network.
  * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
-int kite_mlp_train(kite_ctx* ctx, const float* X, const float* T, int n, const float* scale,
-                   const kite_mlp_train_cfg* cfg, float* params, float* loss_curve,
-                   const kite_mlp_prior* prior);
+int kite_mlp_train(kite_ctx* ctx, const float* X, const float* T, int n, const float* shift,
+                   const float* scale, const kite_mlp_train_cfg* cfg, float* params,
+                   float* loss_curve, const kite_mlp_prior* prior);
 
-/* Y [n][OUT] = network(X [n][IN] * scale) (+ the prior of X, if prior is not NULL).
- * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
+/* Y [n][OUT] = network((X [n][IN] - shift) * scale) (+ the prior of X, if prior is not
+ * NULL).  Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
 int kite_mlp_forward(kite_ctx* ctx, const float* params, const float* X, int n,
-                     const float* scale, float* Y, const kite_mlp_prior* prior);
+                     const float* shift, const float* scale, float* Y,
+                     const kite_mlp_prior* prior);
 
 /* Gradient [P] of the mean absolute error over all n x OUT outputs (for checks), and the
  * loss.  Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
 int kite_mlp_gradient(kite_ctx* ctx, const float* params, const float* X, const float* T, int n,
-                      const float* scale, float* grad, double* loss);
+                      const float* shift, const float* scale, float* grad, double* loss);
 
 /* Label-free consistency gate of predicted densities rho [n][OUT] (per eV, on the midpoint
  * grid eps_j = -1 + (2j+1)/OUT of the rescaled energy): the Chebyshev moments
@@ -350,6 +361,23 @@ int kite_moments_1d_static(const kite_system* sys, const kite_kpm* kpm, double* 
 int kite_reconstruct_dos(kite_ctx* ctx, const double* mu, int M_avail, int M_use, int kernel,
                          double param, double e_min, double e_max, const double* E, int K,
                          double* rho);
+
+/* Average Green's function per orbital at complex energy E + i eta, the eta-resolved
+ * companion of the DOS (Eqs. green_function_cheb_expansion/b traced as in Eq. e7):
+ *   G(E + i eta) = (1/de_minus) sum_{n<M_use} g_n mu_n / (1 + delta_n0) g^{+,eta~}_n(eps),
+ * eps = (E - de_plus)/de_minus, eta~ = eta/de_minus, with the retarded Chebyshev
+ * polynomial Green's function coefficients g^{+,eta~}_n(eps) = -2i exp(-i n arccos z) /
+ * sqrt(1 - z^2), z = eps + i eta~, and an optional kernel g_n (as kite_reconstruct_dos).
+ * FP64 on the GPU.  The series converges for M_use >> de_minus/eta.
+ *   mu      [M_avail] raw moments (FP64), host or device
+ *   eta     broadening in eV (> 0)
+ *   E       [K] energies in eV, host or device
+ *   G       [K] complex FP64 interleaved (re, im) in 1/eV, host or device, or NULL
+ *   rho     [K] eta-broadened density -Im G / pi per eV, host or device, or NULL
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
+int kite_reconstruct_green(kite_ctx* ctx, const double* mu, int M_avail, int M_use, int kernel,
+                           double param, double e_min, double e_max, double eta,
+                           const double* E, int K, double* G, double* rho);
 
 /* First-order optical conductivity sigma_xx(omega) in units of e^2/hbar from the 2D
  * moments of kite_moments_2d (Sec. 2b, Eqs. Gammanm and conductivity_1st_order, in

@@ -88,7 +88,8 @@ def lib():
             L.orc_replica_window.argtypes = [P(System), i32, i32, i32, d, d, i32, i32, i32, i32, vp]
             L.orc_replica_window.restype = i32
             L.orc_velocity_x.argtypes = [P(System), vp, d, vp, vp]
-            L.orc_moments_2d.argtypes = [P(System), i32, i32, i32, d, d, vp, vp, vp, vp, i32]
+            L.orc_velocity.argtypes = [P(System), vp, d, i32, vp, vp]
+            L.orc_moments_2d.argtypes = [P(System), i32, i32, i32, d, d, vp, vp, vp, vp, i32, i32, i32]
             L.orc_moments_2d.restype = i32
             L.orc_kernel_jackson.argtypes = [i32, vp]
             L.orc_kernel_lorentz.argtypes = [i32, d, vp]
@@ -195,17 +196,24 @@ def replica_1d(sys: System, M: int, R: int, precision: int, realisation: int = 0
 
 
 def velocity_x(sys: System, vac, t_scaled: float, vec):
+    return velocity(sys, vac, t_scaled, vec, 0)
+
+
+def velocity(sys: System, vac, t_scaled: float, vec, direction: int = 0):
+    """h~ vec with h~ = [r_dir, H~] (direction 0: x, 1: y) on the lattice of `sys`."""
     n = norb(sys)
     v = np.ascontiguousarray(np.stack([np.real(vec), np.imag(vec)], -1).astype(np.float64))
     out = np.empty((n, 2), np.float64)
-    lib().orc_velocity_x(ctypes.byref(sys), _ptr(np.ascontiguousarray(vac, np.uint8)),
-                         float(t_scaled), _ptr(v), _ptr(out))
+    lib().orc_velocity(ctypes.byref(sys), _ptr(np.ascontiguousarray(vac, np.uint8)),
+                       float(t_scaled), int(direction), _ptr(v), _ptr(out))
     return out[:, 0] + 1j * out[:, 1]
 
 
 def moments_2d(sys: System, M: int, R: int, realisation: int = 0, e_min=None, e_max=None,
-               r0=None, want_families: bool = False, threads: int = 0):
-    """mu_nm = <a_n|b_m>/N_eff averaged over R vectors (a_n = T_n h~ r, b_m = h~ T_m r)."""
+               r0=None, want_families: bool = False, threads: int = 0, alpha: int = 0,
+               beta: int = 0):
+    """mu_nm = <a_n|b_m>/N_eff averaged over R vectors with a_n = T_n h~alpha r and
+    b_m = h~beta T_m r (directions 0: x, 1: y), i.e. <r|v_alpha T_n v_beta T_m|r>/N."""
     n = norb(sys)
     lo, hi = _bounds(sys, e_min, e_max)
     r0a = _as_r0(r0, R, n)
@@ -213,7 +221,8 @@ def moments_2d(sys: System, M: int, R: int, realisation: int = 0, e_min=None, e_
     A = np.empty((M, n, 2), np.float64) if want_families else None
     B = np.empty((M, n, 2), np.float64) if want_families else None
     rc = lib().orc_moments_2d(ctypes.byref(sys), int(realisation), int(M), int(R), lo, hi,
-                              _ptr(r0a), _ptr(mu), _ptr(A), _ptr(B), int(threads))
+                              _ptr(r0a), _ptr(mu), _ptr(A), _ptr(B), int(alpha), int(beta),
+                              int(threads))
     if rc != 0:
         raise ValueError(f"orc_moments_2d failed ({rc})")
     out = mu[..., 0] + 1j * mu[..., 1]

@@ -83,9 +83,16 @@ static int64_t orc_wrap(int64_t v, int64_t L) {
 /* Neighbours of orbital o in a fixed order, with the x-component (in units of a)
  * of the bond vector r_o - r_j used by the velocity operator h~x = [x, H]
  * (Sec. 2b, generalised velocity with n = 1).  Returns the coordination number. */
-static int orc_neighbours_dx(const orc_system* sys, int64_t o, int64_t nb[4], double dx[4]) {
+/* Neighbours of orbital o with the bond offsets (x_o - x_j, y_o - y_j) in units of the
+ * lattice constant a.  Honeycomb (the paper's lattice set-up listing): a1 = (1, 0),
+ * a2 = (1/2, sqrt(3)/2), A at (0, -a_cc/2) and B at (0, +a_cc/2) in each cell with
+ * a_cc = 1/sqrt(3); bonds A(x,y) - B(x+dx1, y+dx2) for cell offsets (0,0), (1,-1), (0,-1).
+ * Square: a1 = (1, 0), a2 = (0, 1). */
+static int orc_neighbours_geo(const orc_system* sys, int64_t o, int64_t nb[4], double dx[4],
+                              double dy[4]) {
   int64_t Lx = sys->Lx, Ly = sys->Ly;
   if (sys->lattice == 0) {
+    const double acc = 1.0 / sqrt(3.0);
     int64_t cell = o >> 1, s = o & 1;
     int64_t x = cell % Lx, y = cell / Lx;
     if (s == 0) { /* A(x,y) -> B(x,y), B(x+1,y-1), B(x,y-1) */
@@ -95,6 +102,9 @@ static int orc_neighbours_dx(const orc_system* sys, int64_t o, int64_t nb[4], do
       dx[0] = 0.0;
       dx[1] = -0.5;
       dx[2] = 0.5;
+      dy[0] = -acc;
+      dy[1] = 0.5 * acc;
+      dy[2] = 0.5 * acc;
     } else { /* B(x,y) -> A(x,y), A(x-1,y+1), A(x,y+1) */
       nb[0] = 2 * (y * Lx + x);
       nb[1] = 2 * (orc_wrap(y + 1, Ly) * Lx + orc_wrap(x - 1, Lx));
@@ -102,6 +112,9 @@ static int orc_neighbours_dx(const orc_system* sys, int64_t o, int64_t nb[4], do
       dx[0] = 0.0;
       dx[1] = 0.5;
       dx[2] = -0.5;
+      dy[0] = acc;
+      dy[1] = -0.5 * acc;
+      dy[2] = -0.5 * acc;
     }
     return 3;
   }
@@ -114,12 +127,16 @@ static int orc_neighbours_dx(const orc_system* sys, int64_t o, int64_t nb[4], do
   dx[1] = -1.0;
   dx[2] = 0.0;
   dx[3] = 0.0;
+  dy[0] = 0.0;
+  dy[1] = 0.0;
+  dy[2] = 1.0;
+  dy[3] = -1.0;
   return 4;
 }
 
 int orc_neighbours(const orc_system* sys, int64_t o, int64_t nb[4]) {
-  double dx[4];
-  return orc_neighbours_dx(sys, o, nb, dx);
+  double dx[4], dy[4];
+  return orc_neighbours_geo(sys, o, nb, dx, dy);
 }
 
 /* Spectral bounds.  The paper rescales H into [-1,1] with the endpoints of the
@@ -190,7 +207,8 @@ typedef struct {
   int64_t N;
   int Z;
   int64_t* nb;   /* [N][4] */
-  double* dx;    /* [N][4] */
+  double* dx;    /* [N][4] bond offsets x_o - x_j */
+  double* dy;    /* [N][4] bond offsets y_o - y_j */
   double* Vt;    /* rescaled on-site */
   uint8_t* vac;
   double tt;     /* rescaled hopping */
@@ -202,16 +220,17 @@ static int orc_ham_build(orc_ham* h, const orc_system* sys, int realisation, dou
   h->N = orc_norb(sys);
   h->nb = (int64_t*)malloc(sizeof(int64_t) * 4 * h->N);
   h->dx = (double*)malloc(sizeof(double) * 4 * h->N);
+  h->dy = (double*)malloc(sizeof(double) * 4 * h->N);
   h->Vt = (double*)malloc(sizeof(double) * h->N);
   h->vac = (uint8_t*)malloc(h->N);
-  if (!h->nb || !h->dx || !h->Vt || !h->vac) return -2;
+  if (!h->nb || !h->dx || !h->dy || !h->Vt || !h->vac) return -2;
   double de_plus = 0.5 * (e_max + e_min);
   double de_minus = 0.5 * (e_max - e_min);
   double* V = h->Vt;
   orc_disorder(sys, realisation, V, h->vac);
   h->n_eff = 0;
   for (int64_t o = 0; o < h->N; ++o) {
-    h->Z = orc_neighbours_dx(sys, o, h->nb + 4 * o, h->dx + 4 * o);
+    h->Z = orc_neighbours_geo(sys, o, h->nb + 4 * o, h->dx + 4 * o, h->dy + 4 * o);
     h->Vt[o] = (V[o] - de_plus) / de_minus;
     if (!h->vac[o]) h->n_eff++;
   }
@@ -222,6 +241,7 @@ static int orc_ham_build(orc_ham* h, const orc_system* sys, int realisation, dou
 static void orc_ham_free(orc_ham* h) {
   free(h->nb);
   free(h->dx);
+  free(h->dy);
   free(h->Vt);
   free(h->vac);
 }
@@ -468,7 +488,11 @@ int orc_replica_1d(const orc_system* sys, int realisation, int M, int R, double 
 /*   mu_nm = <a_n|b_m>/N_eff averaged over vectors, i.e. <r|v T_n v T_m|r>/N_eff for   */
 /*   v = -i h~ (= i[H,x]); Gamma_nm = -mu_nm/((1+d_n0)(1+d_m0)).                       */
 /* ------------------------------------------------------------------------------ */
-static void orc_apply_vx(const orc_ham* h, const double* x, double* y) {
+/* y = h~ x with h~ = [r_dir, H~] (dir 0: x, 1: y): (h~)_oj = (r_o - r_j) H~_oj over the
+ * bonds (Sec. 2b, the velocity operator v = i[H, r] = -i h~ in units of the lattice
+ * constant). */
+static void orc_apply_v(const orc_ham* h, int dir, const double* x, double* y) {
+  const double* off = dir ? h->dy : h->dx;
 #pragma omp parallel for schedule(static)
   for (int64_t o = 0; o < h->N; ++o) {
     double re = 0.0, im = 0.0;
@@ -476,7 +500,7 @@ static void orc_apply_vx(const orc_ham* h, const double* x, double* y) {
       for (int k = 0; k < h->Z; ++k) {
         int64_t j = h->nb[4 * o + k];
         if (h->vac[j]) continue;
-        double w = h->dx[4 * o + k] * h->tt;
+        double w = off[4 * o + k] * h->tt;
         re += w * x[2 * j];
         im += w * x[2 * j + 1];
       }
@@ -486,18 +510,26 @@ static void orc_apply_vx(const orc_ham* h, const double* x, double* y) {
   }
 }
 
-void orc_velocity_x(const orc_system* sys, const uint8_t* vac, double t_scaled,
-                    const double* in, double* out) {
+void orc_velocity(const orc_system* sys, const uint8_t* vac, double t_scaled, int dir,
+                  const double* in, double* out) {
   orc_ham h;
   h.N = orc_norb(sys);
   h.nb = (int64_t*)malloc(sizeof(int64_t) * 4 * h.N);
   h.dx = (double*)malloc(sizeof(double) * 4 * h.N);
+  h.dy = (double*)malloc(sizeof(double) * 4 * h.N);
   h.vac = (uint8_t*)vac;
   h.tt = t_scaled;
-  for (int64_t o = 0; o < h.N; ++o) h.Z = orc_neighbours_dx(sys, o, h.nb + 4 * o, h.dx + 4 * o);
-  orc_apply_vx(&h, in, out);
+  for (int64_t o = 0; o < h.N; ++o)
+    h.Z = orc_neighbours_geo(sys, o, h.nb + 4 * o, h.dx + 4 * o, h.dy + 4 * o);
+  orc_apply_v(&h, dir, in, out);
   free(h.nb);
   free(h.dx);
+  free(h.dy);
+}
+
+void orc_velocity_x(const orc_system* sys, const uint8_t* vac, double t_scaled,
+                    const double* in, double* out) {
+  orc_velocity(sys, vac, t_scaled, 0, in, out);
 }
 
 /* Runs the recursion from `start`, storing T_n(H~) start for n < M into fam[n]. */
@@ -527,7 +559,7 @@ static void orc_family(const orc_ham* h, int M, const double* start, double* fam
  * families [M][N] complex (for inspection in tests). */
 int orc_moments_2d(const orc_system* sys, int realisation, int M, int R, double e_min,
                    double e_max, const double* r0_in, double* mu_nm, double* a_fam,
-                   double* b_fam, int threads) {
+                   double* b_fam, int dir_a, int dir_b, int threads) {
 #ifdef _OPENMP
   if (threads > 0) omp_set_num_threads(threads);
 #else
@@ -549,10 +581,10 @@ int orc_moments_2d(const orc_system* sys, int realisation, int M, int R, double 
   double inv = h.n_eff > 0 ? 1.0 / ((double)h.n_eff * (double)R) : 0.0;
   for (int r = 0; r < R; ++r) {
     const double* v0 = r0 + 2 * (int64_t)r * N;
-    orc_apply_vx(&h, v0, start);
-    orc_family(&h, M, start, A, work); /* a_n = T_n h~ r */
-    orc_family(&h, M, v0, T, work);    /* T_m r          */
-    for (int m = 0; m < M; ++m) orc_apply_vx(&h, T + 2 * N * (int64_t)m, B + 2 * N * (int64_t)m);
+    orc_apply_v(&h, dir_a, v0, start);
+    orc_family(&h, M, start, A, work); /* a_n = T_n h~a r */
+    orc_family(&h, M, v0, T, work);    /* T_m r           */
+    for (int m = 0; m < M; ++m) orc_apply_v(&h, dir_b, T + 2 * N * (int64_t)m, B + 2 * N * (int64_t)m);
     /* plain triple loop: mu_nm += sum_o conj(a_n[o]) b_m[o] */
 #pragma omp parallel for schedule(static)
     for (int n = 0; n < M; ++n) {

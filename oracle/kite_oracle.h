@@ -56,9 +56,11 @@ int orc_replica_window(const orc_system* sys, int realisation, int M, int R, dou
 
 void orc_velocity_x(const orc_system* sys, const uint8_t* vac, double t_scaled,
                     const double* in, double* out);
+void orc_velocity(const orc_system* sys, const uint8_t* vac, double t_scaled, int dir,
+                  const double* in, double* out);
 int orc_moments_2d(const orc_system* sys, int realisation, int M, int R, double e_min,
                    double e_max, const double* r0_in, double* mu_nm, double* a_fam,
-                   double* b_fam, int threads);
+                   double* b_fam, int dir_a, int dir_b, int threads);
 
 void orc_kernel_jackson(int M, double* g);
 void orc_kernel_lorentz(int M, double lambda, double* g);

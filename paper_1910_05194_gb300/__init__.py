@@ -21,10 +21,11 @@ ERR_ARG, ERR_OOM, ERR_CUDA, ERR_BOUNDS, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -
 HONEYCOMB, SQUARE = 0, 1
 FP32, FP64 = 0, 1
 KERNEL_NONE, KERNEL_JACKSON, KERNEL_LORENTZ = 0, 1, 2
+DIR_X, DIR_Y = 0, 1
 
 EXPORTED = ("kite_create", "kite_destroy", "kite_set_stream", "kite_status_string",
             "kite_last_error", "kite_bounds", "kite_moments_1d", "kite_reconstruct_dos",
-            "kite_debug_stall_once", "kite_inner_products", "kite_moments_2d",
+            "kite_debug_stall_once", "kite_inner_products", "kite_moments_2d", "kite_reconstruct_green",
             "kite_reconstruct_sigma", "kite_moments_1d_static", "kite_moments_1d_batched",
             "kite_mlp_param_count", "kite_mlp_train", "kite_mlp_forward", "kite_mlp_gradient",
             "kite_learned_gate")
@@ -132,17 +133,19 @@ def lib():
             L.kite_moments_1d_batched.restype = i32
             L.kite_mlp_param_count.argtypes = []
             L.kite_mlp_param_count.restype = ctypes.c_int64
-            L.kite_mlp_train.argtypes = [vp, vp, vp, i32, vp, P(MLPTrainCfg), vp, vp, P(MLPPrior)]
+            L.kite_mlp_train.argtypes = [vp, vp, vp, i32, vp, vp, P(MLPTrainCfg), vp, vp, P(MLPPrior)]
             L.kite_mlp_train.restype = i32
-            L.kite_mlp_forward.argtypes = [vp, vp, vp, i32, vp, vp, P(MLPPrior)]
+            L.kite_mlp_forward.argtypes = [vp, vp, vp, i32, vp, vp, vp, P(MLPPrior)]
             L.kite_mlp_forward.restype = i32
-            L.kite_mlp_gradient.argtypes = [vp, vp, vp, vp, i32, vp, vp, P(d)]
+            L.kite_mlp_gradient.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, P(d)]
             L.kite_mlp_gradient.restype = i32
             L.kite_learned_gate.argtypes = [vp, vp, vp, i32, i32, i32, d, d, d, vp, vp]
             L.kite_learned_gate.restype = i32
-            L.kite_moments_2d.argtypes = [vp, P(System), P(KPM), vp, P(Stats)]
+            L.kite_moments_2d.argtypes = [vp, P(System), P(KPM), i32, i32, vp, P(Stats)]
             L.kite_moments_2d.restype = i32
-            L.kite_inner_products.argtypes = [vp, vp, vp, i32, i32, ctypes.c_int64, d, vp, i32, i32]
+            L.kite_reconstruct_green.argtypes = [vp, vp, i32, i32, i32, d, d, d, d, vp, i32, vp, vp]
+            L.kite_reconstruct_green.restype = i32
+            L.kite_inner_products.argtypes = [vp, vp, vp, i32, i32, ctypes.c_int64, d, vp, i32, i32, i32]
             L.kite_inner_products.restype = i32
             L.kite_debug_stall_once.argtypes = [vp, i32]
             L.kite_debug_stall_once.restype = i32
@@ -244,19 +247,28 @@ def debug_stall_once(ctx: Context, enable: bool = True):
     ctx.check(lib().kite_debug_stall_once(ctx.handle, int(bool(enable))))
 
 
+def reconstruct_green(ctx: Context, mu, M_avail: int, M_use: int, kernel: int, param: float,
+                      e_min: float, e_max: float, eta: float, E, K: int, G=None, rho=None):
+    """kite_reconstruct_green: G[K] complex (1/eV) and/or rho[K] = -Im G/pi at E + i eta."""
+    ctx.check(lib().kite_reconstruct_green(ctx.handle, _addr(mu), int(M_avail), int(M_use), int(kernel),
+                                           float(param), float(e_min), float(e_max), float(eta), _addr(E),
+                                           int(K), _addr(G), _addr(rho)))
+
+
 def inner_products(ctx: Context, A, B, M: int, M2: int, N: int, scale: float, C, sub_k: int = 0,
-                   products: int = 0):
+                   products: int = 0, fold: int = 0):
     """kite_inner_products: C[n][m] = scale * sum_i conj(A[n][i]) B[m][i] (split-BF16
     tensor cores, FP64 output).  A [M][N], B [M2][N] complex64; C [M][M2] complex128."""
     ctx.check(lib().kite_inner_products(ctx.handle, _addr(A), _addr(B), int(M), int(M2), int(N),
-                                        float(scale), _addr(C), int(sub_k), int(products)))
+                                        float(scale), _addr(C), int(sub_k), int(products), int(fold)))
 
 
-def moments_2d(ctx: Context, system: System, kpm: KPM, mu_nm) -> Stats:
-    """kite_moments_2d: mu_nm[M][M] complex FP64 (host or device)."""
+def moments_2d(ctx: Context, system: System, kpm: KPM, mu_nm, alpha: int = 0, beta: int = 0) -> Stats:
+    """kite_moments_2d: mu_nm[M][M] complex FP64 (host or device) for the velocity
+    directions alpha, beta (DIR_X = 0, DIR_Y = 1)."""
     st = Stats()
-    ctx.check(lib().kite_moments_2d(ctx.handle, ctypes.byref(system), ctypes.byref(kpm),
-                                    _addr(mu_nm), ctypes.byref(st)))
+    ctx.check(lib().kite_moments_2d(ctx.handle, ctypes.byref(system), ctypes.byref(kpm), int(alpha),
+                                    int(beta), _addr(mu_nm), ctypes.byref(st)))
     return st
 
 
@@ -306,23 +318,23 @@ def mlp_param_count() -> int:
 
 
 def mlp_train(ctx: Context, X, T, n: int, params, epochs=50, batch=256, lr=1e-3, weight_decay=1e-4,
-              seed=0, scale=None, loss_curve=None, prior=None):
+              seed=0, scale=None, loss_curve=None, prior=None, shift=None):
     """kite_mlp_train: trains `params` (FP32 [P]) in place on X [n][IN] -> T [n][OUT]."""
     cfg = MLPTrainCfg(int(epochs), int(batch), float(lr), float(weight_decay), int(seed))
-    ctx.check(lib().kite_mlp_train(ctx.handle, _addr(X), _addr(T), int(n), _addr(scale),
+    ctx.check(lib().kite_mlp_train(ctx.handle, _addr(X), _addr(T), int(n), _addr(shift), _addr(scale),
                                    ctypes.byref(cfg), _addr(params), _addr(loss_curve),
                                    _prior_ref(prior)))
 
 
-def mlp_forward(ctx: Context, params, X, n: int, Y, scale=None, prior=None):
-    ctx.check(lib().kite_mlp_forward(ctx.handle, _addr(params), _addr(X), int(n), _addr(scale), _addr(Y),
-                                     _prior_ref(prior)))
+def mlp_forward(ctx: Context, params, X, n: int, Y, scale=None, prior=None, shift=None):
+    ctx.check(lib().kite_mlp_forward(ctx.handle, _addr(params), _addr(X), int(n), _addr(shift), _addr(scale),
+                                     _addr(Y), _prior_ref(prior)))
 
 
-def mlp_gradient(ctx: Context, params, X, T, n: int, grad, scale=None) -> float:
+def mlp_gradient(ctx: Context, params, X, T, n: int, grad, scale=None, shift=None) -> float:
     loss = ctypes.c_double()
     ctx.check(lib().kite_mlp_gradient(ctx.handle, _addr(params), _addr(X), _addr(T), int(n),
-                                      _addr(scale), _addr(grad), ctypes.byref(loss)))
+                                      _addr(shift), _addr(scale), _addr(grad), ctypes.byref(loss)))
     return loss.value
 
 

@@ -111,6 +111,9 @@ __global__ void __launch_bounds__(kBlock, 2)
                                                    S.partial + (size_t)(n + 1) * T.ncta * Q, nullptr,
                                                    err, 0, nofam);
       if (!ok) return;
+      // step_body reused the ring's shared memory for its reduction (generic-proxy
+      // writes); order them before the next step's bulk copies into the same memory
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       if (T.ncta > 1) {
         arrived += (unsigned int)T.ncta;
         const bool skip = stall && team == 0 && rank == 0 && arrived == (unsigned int)T.ncta;

@@ -17,23 +17,26 @@ int moments_1d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
                     const double* r0_dev_all);
 int64_t mlp_param_count();
 int mlp_gradient_impl(kite_ctx* ctx, const float* params, const float* X, const float* T, int n,
-                      const float* scale, float* grad, double* loss);
-int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, const float* scale, float* Y,
-                     const kite_mlp_prior* prior);
-int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const float* scale,
+                      const float* shift, const float* scale, float* grad, double* loss);
+int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, const float* shift,
+                     const float* scale, float* Y, const kite_mlp_prior* prior);
+int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const float* shift, const float* scale,
                    const kite_mlp_train_cfg* cfg, float* params, float* loss_curve,
                    const kite_mlp_prior* prior);
 int mlp_gate_impl(kite_ctx* ctx, const float* rho, const double* mu, int mu_ld, int n, int kcheck,
                   double de_minus, double tol, int* flags, double* dev);
 int moments_1d_batched_impl(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm* kpm,
                             const std::vector<Scale>& scales, double* const* mu, kite_stats* st);
-int moments_2d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
-                    double* mu_nm_dev, kite_stats* st, const double* r0_dev_all);
+int moments_2d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc, int alpha,
+                    int beta, double* mu_nm_dev, kite_stats* st, const double* r0_dev_all);
 int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
-                        double scale, double* C, int sub_kb, int nprod);
+                        double scale, double* C, int sub_kb, int fold, int nprod);
 int reconstruct_sigma_impl(kite_ctx* ctx, const double* mu_dev, int M_avail, int M, int lattice,
                            int kernel, const Scale& sc, double E_F, double kT, double eta,
                            const double* omega_host, int K_w, int n_quad, double* sigma_dev);
+int reconstruct_green_impl(kite_ctx* ctx, const double* mu_dev, int M_use, int kernel, double param,
+                           const Scale& sc, double eta, const double* E_dev, int K, double* G_dev,
+                           double* rho_dev, double* coef_dev);
 int reconstruct_dos_impl(kite_ctx* ctx, const double* mu_dev, int M_use, int kernel,
                          double param, const Scale& sc, const double* E_dev, int K,
                          double* rho_dev, double* coef_dev);
@@ -383,8 +386,8 @@ int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
 int64_t kite_mlp_param_count(void) { return mlp_param_count(); }
 
 
-int kite_mlp_train(kite_ctx* ctx, const float* X, const float* T, int n, const float* scale,
-                   const kite_mlp_train_cfg* cfg, float* params, float* loss_curve,
+int kite_mlp_train(kite_ctx* ctx, const float* X, const float* T, int n, const float* shift,
+                   const float* scale, const kite_mlp_train_cfg* cfg, float* params, float* loss_curve,
                    const kite_mlp_prior* prior) {
   if (!ctx) return KITE_ERR_ARG;
   ctx->last_error.clear();
@@ -394,48 +397,51 @@ int kite_mlp_train(kite_ctx* ctx, const float* X, const float* T, int n, const f
   if (check_prior(ctx, prior) != KITE_OK) return KITE_ERR_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
   Staging sg{ctx, {}};
-  const float *Xd, *Td, *Sd;
+  const float *Xd, *Td, *Hd, *Sd;
   int rc = sg.in(X, (size_t)n * KITE_MLP_IN, &Xd);
   if (rc == KITE_OK) rc = sg.in(T, (size_t)n * KITE_MLP_OUT, &Td);
+  if (rc == KITE_OK) rc = sg.in(shift, KITE_MLP_IN, &Hd);
   if (rc == KITE_OK) rc = sg.in(scale, KITE_MLP_IN, &Sd);
   std::vector<float> curve(cfg->epochs);
-  if (rc == KITE_OK) rc = mlp_train_impl(ctx, Xd, Td, n, Sd, cfg, params, curve.data(), prior);
+  if (rc == KITE_OK) rc = mlp_train_impl(ctx, Xd, Td, n, Hd, Sd, cfg, params, curve.data(), prior);
   if (rc == KITE_OK && loss_curve) std::copy(curve.begin(), curve.end(), loss_curve);
   cudaStreamSynchronize(ctx->stream);
   return rc;
 }
 
-int kite_mlp_forward(kite_ctx* ctx, const float* params, const float* X, int n, const float* scale,
-                     float* Y, const kite_mlp_prior* prior) {
+int kite_mlp_forward(kite_ctx* ctx, const float* params, const float* X, int n, const float* shift,
+                     const float* scale, float* Y, const kite_mlp_prior* prior) {
   if (!ctx) return KITE_ERR_ARG;
   ctx->last_error.clear();
   if (!params || !X || !Y || n < 1) return fail(ctx, KITE_ERR_ARG, "need params, X, Y and n >= 1");
   if (check_prior(ctx, prior) != KITE_OK) return KITE_ERR_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
   Staging sg{ctx, {}};
-  const float *Xd, *Sd;
+  const float *Xd, *Hd, *Sd;
   float* Yd;
   int rc = sg.in(X, (size_t)n * KITE_MLP_IN, &Xd);
+  if (rc == KITE_OK) rc = sg.in(shift, KITE_MLP_IN, &Hd);
   if (rc == KITE_OK) rc = sg.in(scale, KITE_MLP_IN, &Sd);
   if (rc == KITE_OK) rc = sg.out(Y, (size_t)n * KITE_MLP_OUT, &Yd);
-  if (rc == KITE_OK) rc = mlp_forward_impl(ctx, params, Xd, n, Sd, Yd, prior);
+  if (rc == KITE_OK) rc = mlp_forward_impl(ctx, params, Xd, n, Hd, Sd, Yd, prior);
   if (rc == KITE_OK) rc = sg.back(Y, Yd, (size_t)n * KITE_MLP_OUT);
   cudaStreamSynchronize(ctx->stream);
   return rc;
 }
 
 int kite_mlp_gradient(kite_ctx* ctx, const float* params, const float* X, const float* T, int n,
-                      const float* scale, float* grad, double* loss) {
+                      const float* shift, const float* scale, float* grad, double* loss) {
   if (!ctx) return KITE_ERR_ARG;
   ctx->last_error.clear();
   if (!params || !X || !T || !grad || n < 1) return fail(ctx, KITE_ERR_ARG, "need params, X, T, grad, n >= 1");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
   Staging sg{ctx, {}};
-  const float *Xd, *Td, *Sd;
+  const float *Xd, *Td, *Hd, *Sd;
   int rc = sg.in(X, (size_t)n * KITE_MLP_IN, &Xd);
   if (rc == KITE_OK) rc = sg.in(T, (size_t)n * KITE_MLP_OUT, &Td);
+  if (rc == KITE_OK) rc = sg.in(shift, KITE_MLP_IN, &Hd);
   if (rc == KITE_OK) rc = sg.in(scale, KITE_MLP_IN, &Sd);
-  if (rc == KITE_OK) rc = mlp_gradient_impl(ctx, params, Xd, Td, n, Sd, grad, loss);
+  if (rc == KITE_OK) rc = mlp_gradient_impl(ctx, params, Xd, Td, n, Hd, Sd, grad, loss);
   cudaStreamSynchronize(ctx->stream);
   return rc;
 }
@@ -495,8 +501,8 @@ int kite_moments_1d_batched(kite_ctx* ctx, int count, const kite_system* systems
   return rc;
 }
 
-int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, double* mu_nm,
-                    kite_stats* st) {
+int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, int alpha, int beta,
+                    double* mu_nm, kite_stats* st) {
   if (!ctx) return KITE_ERR_ARG;
   ctx->last_error.clear();
   int rc = validate_system(ctx, sys);
@@ -509,6 +515,8 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   if ((double)kpm->R * kpm->S > 65536.0) return fail(ctx, KITE_ERR_ARG, "R*S > 65536");
   if (kpm->doubling != 0 || kpm->reserved != 0)
     return fail(ctx, KITE_ERR_ARG, "the 2D moments take doubling = 0 and reserved = 0");
+  if ((alpha != KITE_DIR_X && alpha != KITE_DIR_Y) || (beta != KITE_DIR_X && beta != KITE_DIR_Y))
+    return fail(ctx, KITE_ERR_ARG, "alpha and beta must be KITE_DIR_X or KITE_DIR_Y");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
   Scale sc;
   rc = resolve_bounds(ctx, sys, kpm->e_min, kpm->e_max, &sc);
@@ -533,7 +541,7 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   const size_t out_bytes = sizeof(double) * 2 * (size_t)M * M;
   if (!out_d) KITE_CUDA_TRY(ctx, cudaMallocAsync((void**)&out_dev, out_bytes, ctx->stream));
   kite_stats local{};
-  rc = moments_2d_impl(ctx, sys, kpm, sc, out_dev, &local, r0_dev);
+  rc = moments_2d_impl(ctx, sys, kpm, sc, alpha, beta, out_dev, &local, r0_dev);
   if (rc == KITE_OK && !out_d) {
     cudaError_t e = copy_out(ctx, mu_nm, out_dev, out_bytes);
     if (e != cudaSuccess) rc = cuda_fail(ctx, e, "copying mu_nm");
@@ -549,11 +557,11 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
 }
 
 int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
-                        double scale, double* C, int sub_k, int products) {
+                        double scale, double* C, int sub_k, int products, int fold) {
   if (!ctx) return KITE_ERR_ARG;
   ctx->last_error.clear();
-  if (!A || !B || !C || M < 1 || M2 < 1 || N < 1 || sub_k < 0 || !isfinite(scale))
-    return fail(ctx, KITE_ERR_ARG, "need A, B, C, M >= 1, M2 >= 1, N >= 1, sub_k >= 0");
+  if (!A || !B || !C || M < 1 || M2 < 1 || N < 1 || sub_k < 0 || fold < 0 || !isfinite(scale))
+    return fail(ctx, KITE_ERR_ARG, "need A, B, C, M >= 1, M2 >= 1, N >= 1, sub_k >= 0, fold >= 0");
   if (products != 0 && products != 3 && products != 4)
     return fail(ctx, KITE_ERR_ARG, "products must be 0 (default 4), 3 or 4");
   if ((double)M * N > 4.0e10 || (double)M2 * N > 4.0e10)
@@ -574,7 +582,8 @@ int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, in
   if (e == cudaSuccess && !b_d) { Bd = reinterpret_cast<float*>(stage + off); e = copy_in(ctx, stage + off, B, b_bytes); off += (b_bytes + 255) & ~size_t(255); }
   if (!c_d) Cd = reinterpret_cast<double*>(stage + off);
   int rc = e == cudaSuccess ? KITE_OK : cuda_fail(ctx, e, "copying A/B");
-  if (rc == KITE_OK) rc = inner_products_impl(ctx, Ad, Bd, M, M2, N, scale, Cd, sub_kb, products == 3 ? 3 : 4);
+  if (rc == KITE_OK) rc = inner_products_impl(ctx, Ad, Bd, M, M2, N, scale, Cd, sub_kb,
+                                                   fold == 0 ? 16 : fold, products == 3 ? 3 : 4);
   if (rc == KITE_OK && !c_d) {
     e = copy_out(ctx, C, Cd, c_bytes);
     if (e != cudaSuccess) rc = cuda_fail(ctx, e, "copying C");
@@ -628,6 +637,41 @@ int kite_reconstruct_dos(kite_ctx* ctx, const double* mu, int M_avail, int M_use
   cudaFreeAsync(buf, ctx->stream);
   cudaError_t es = cudaStreamSynchronize(ctx->stream);
   if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "reconstruct_dos");
+  return rc;
+}
+
+int kite_reconstruct_green(kite_ctx* ctx, const double* mu, int M_avail, int M_use, int kernel,
+                           double param, double e_min, double e_max, double eta, const double* E, int K,
+                           double* G, double* rho) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  if (!mu || !E || (!G && !rho) || K < 0 || M_avail < 1 || M_use < 1 || M_use > M_avail)
+    return fail(ctx, KITE_ERR_ARG, "need mu, E, G or rho, and 1 <= M_use <= M_avail, K >= 0");
+  if (kernel != KITE_KERNEL_NONE && kernel != KITE_KERNEL_JACKSON && kernel != KITE_KERNEL_LORENTZ)
+    return fail(ctx, KITE_ERR_ARG, "unknown kernel");
+  if (kernel == KITE_KERNEL_LORENTZ && !(param > 0.0))
+    return fail(ctx, KITE_ERR_ARG, "Lorentz kernel needs lambda > 0");
+  if (!(e_max > e_min)) return fail(ctx, KITE_ERR_ARG, "e_max must exceed e_min");
+  if (!(eta > 0.0) || !std::isfinite(eta)) return fail(ctx, KITE_ERR_ARG, "eta must be > 0");
+  if (K == 0) return KITE_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  Scale sc{e_min, e_max, 0.5 * (e_max + e_min), 0.5 * (e_max - e_min)};
+  Staging sg{ctx, {}};
+  const double *mu_dev, *E_dev;
+  double *G_dev = nullptr, *rho_dev = nullptr, *coef = nullptr;
+  int rc = sg.in(mu, (size_t)M_use, &mu_dev);
+  if (rc == KITE_OK) rc = sg.in(E, (size_t)K, &E_dev);
+  if (rc == KITE_OK && G) rc = sg.out(G, 2 * (size_t)K, &G_dev);
+  if (rc == KITE_OK && rho) rc = sg.out(rho, (size_t)K, &rho_dev);
+  if (rc == KITE_OK) {
+    KITE_CUDA_TRY(ctx, cudaMallocAsync((void**)&coef, sizeof(double) * (size_t)M_use, ctx->stream));
+    rc = reconstruct_green_impl(ctx, mu_dev, M_use, kernel, param, sc, eta, E_dev, K, G_dev, rho_dev, coef);
+    cudaFreeAsync(coef, ctx->stream);
+  }
+  if (rc == KITE_OK && G) rc = sg.back(G, G_dev, 2 * (size_t)K);
+  if (rc == KITE_OK && rho) rc = sg.back(rho, rho_dev, (size_t)K);
+  cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "reconstruct_green");
   return rc;
 }
 

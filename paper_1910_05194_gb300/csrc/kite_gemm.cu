@@ -113,6 +113,19 @@ __device__ __forceinline__ void tmem_ld_32x32(uint32_t taddr, uint32_t (&r)[32])
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 32 lanes x 16 columns (the fold of a finished sub-chunk reads half a block at a time to
+// keep the register footprint next to the FP32 second-level accumulator small)
+__device__ __forceinline__ void tmem_ld_32x16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // Bounded wait that also gives up as soon as another role of the CTA has aborted.
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
                                               volatile int* abort_flag) {
@@ -135,7 +148,8 @@ struct GemmArgs {
   int items;        // S * T
   int kb_total;     // K blocks of 64
   int kb_per_item;  // K blocks per split
-  int sub_kb;       // K blocks per FP32 accumulation sub-chunk
+  int sub_kb;       // K blocks per FP32 accumulation sub-chunk (in TMEM)
+  int fold;         // sub-chunks summed in FP32 registers before the FP64 partials
   int nprod;        // 3: hi*hi + hi*lo + lo*hi;  4: + lo*lo
   int Mrows;        // rows of A (valid)
   int Nrows;        // rows of B (valid) = columns of C
@@ -270,10 +284,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       while (!mbar_try_wait(drain, 0) && clock64() - t0 < kWaitCycles) {
       }
     }
-  } else {  // ---- epilogue: warps 2.. drain the idle accumulator into FP64 partials
+  } else {  // ---- epilogue: warps 2.. fold the idle accumulator into FP32 registers
+    // Two FP32 levels below FP64: the tensor core sums one sub-chunk (sub_kb K blocks) in
+    // TMEM; this warp adds each finished sub-chunk of its 32 rows x 128 columns into d2
+    // (registers) and frees the TMEM buffer at once, so the MMA never waits on memory;
+    // every `fold` sub-chunks (and at the end of an item) d2 goes into the FP64 partials.
     const int q = warp & 3;                           // TMEM lane quarter this warp may access
     const int half = (warp - 2) / 4;                  // which 128 of the 256 columns
     float* tile = epi + (warp - 2) * 32 * kEpiPitch;
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * (kAccCols / 2));
+    float d2[4][32];
     int acc = 0;
     uint32_t aph = 0;
     bool ok = true;
@@ -281,42 +301,58 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       const int s = item / a.T, t = item - (item / a.T) * a.T;
       const int tm = t / a.TN, tn = t - (t / a.TN) * a.TN;
       const int kb0 = s * a.kb_per_item, kb1 = min(a.kb_total, kb0 + a.kb_per_item);
+      const int row0 = tm * kBM + q * 32;
+      double* pbase = a.part + ((size_t)s * a.Mrows + row0) * a.Nrows;
       bool first = true;
+      int nsub = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) d2[j][jj] = 0.f;
       for (int kc = kb0; kc < kb1; kc += a.sub_kb) {
         if (!wait_or_abort(&tfull[acc], aph, abort_flag)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        for (int c0 = half * (kAccCols / 2); c0 < (half + 1) * (kAccCols / 2); c0 += 32) {
-          uint32_t r[32];
-          tmem_ld_32x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols + c0), r);
-          // transpose 32 rows x 32 columns through shared memory for coalesced FP64 RMW
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) tile[lane * kEpiPitch + jj] = __uint_as_float(r[jj]);
+        for (int j = 0; j < 8; ++j) {
+          uint32_t r[16];
+          tmem_ld_32x16(lane_base + (uint32_t)(acc * kAccCols + j * 16), r);
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) d2[j >> 1][(j & 1) * 16 + jj] += __uint_as_float(r[jj]);
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[acc]);  // the MMA may refill this buffer now
+        if (++acc == 2) acc = 0, aph ^= 1u;
+        if (++nsub < a.fold && kc + a.sub_kb < kb1) continue;
+        // flush d2 into the FP64 partials: transpose 32 rows x 32 columns through shared
+        // memory so that a warp's FP64 loads and stores run along a row
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) tile[lane * kEpiPitch + jj] = d2[j][jj];
           __syncwarp();
-          const int col = tn * kBN + c0 + lane;
-          const int row0 = tm * kBM + q * 32;
-          double* p = a.part + ((size_t)s * a.Mrows + row0) * a.Nrows + col;
+          const int col = tn * kBN + half * (kAccCols / 2) + j * 32 + lane;
           const bool colok = col < a.Nrows;
-          // 16 partial loads in flight before any use (the RMW is latency-bound)
+          double* p = pbase + col;
 #pragma unroll
-          for (int h = 0; h < 32; h += 16) {
-            double old[16];
+          for (int jj = 0; jj < 32; ++jj) d2[j][jj] = 0.f;
 #pragma unroll
-            for (int rr = 0; rr < 16; ++rr)
+          for (int h = 0; h < 32; h += 8) {
+            double old[8];  // 8 loads in flight before any use
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr)
               old[rr] = (!first && colok && row0 + h + rr < a.Mrows) ? p[(size_t)(h + rr) * a.Nrows] : 0.0;
 #pragma unroll
-            for (int rr = 0; rr < 16; ++rr)
+            for (int rr = 0; rr < 8; ++rr)
               if (colok && row0 + h + rr < a.Mrows)
                 p[(size_t)(h + rr) * a.Nrows] = old[rr] + (double)tile[(h + rr) * kEpiPitch + lane];
           }
           __syncwarp();
         }
-        tc_fence_before();
-        mbar_arrive(&tempty[acc]);
         first = false;
-        if (++acc == 2) acc = 0, aph ^= 1u;
+        nsub = 0;
       }
     }
   }
@@ -443,7 +479,7 @@ int plan_gemm_splits(kite_ctx* ctx, int Mrows, int Nrows, int64_t Kp) {
 
 int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void* Bhi,
                     const void* Blo, int Mrows, int Nrows, int64_t Kp, int S, int sub_kb,
-                    int nprod, double* part, int* S_used) {
+                    int fold, int nprod, double* part, int* S_used) {
   if (Kp % kBK != 0) return fail(ctx, KITE_ERR_ARG, "K must be padded to a multiple of 64");
   CUtensorMap mAh, mAl, mBh, mBl;
   int rc;
@@ -461,6 +497,7 @@ int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void*
   a.items = a.S * a.T;
   *S_used = a.S;  // the reduction must sum exactly the splits written here
   a.sub_kb = std::max(1, sub_kb);
+  a.fold = std::max(1, fold);
   a.nprod = nprod == 3 ? 3 : 4;
   a.Mrows = Mrows;
   a.Nrows = Nrows;
@@ -491,7 +528,7 @@ int reduce_cplx(kite_ctx* ctx, const double* part, int S, int M, int M2, double 
 // Generic entry: C[n][m] = scale * sum_i conj(A[n][i]) B[m][i], A [M][N], B [M2][N] complex
 // FP32 (device), C [M][M2] complex FP64 (device).
 int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
-                        double scale, double* C, int sub_kb, int nprod) {
+                        double scale, double* C, int sub_kb, int fold, int nprod) {
   const int64_t Kp = ((2 * N + kBK - 1) / kBK) * kBK;
   const int Nrows = 2 * M2;
   const int S = plan_gemm_splits(ctx, M, Nrows, Kp);
@@ -519,7 +556,7 @@ int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, in
   KITE_CUDA_TRY(ctx, cudaGetLastError());
   KITE_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
   int S_used = 0;
-  rc = gemm_split_bf16(ctx, Ahi, Alo, Bhi, Blo, M, Nrows, Kp, S, sub_kb, nprod, part, &S_used);
+  rc = gemm_split_bf16(ctx, Ahi, Alo, Bhi, Blo, M, Nrows, Kp, S, sub_kb, fold, nprod, part, &S_used);
   if (rc != KITE_OK) return rc;
   return reduce_cplx(ctx, part, S_used, M, M2, scale, C, false);
 }

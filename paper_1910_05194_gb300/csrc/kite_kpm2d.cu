@@ -1,13 +1,14 @@
 // kite_kpm2d.cu -- 2D Kubo-Bastin moments (Sec. 2b, Eq. Gammanm).
 //
-//   mu_nm = (1/(S R N_eff)) sum_{s,r} <a_n|b_m>,  a_n = T_n(H~) h~x r,  b_m = h~x T_m(H~) r,
-// with h~x = [x, H~] (x in units of the lattice constant).  Because h~x is anti-Hermitian,
-// <r| h~ T_n h~ T_m |r> = -<a_n|b_m>; the paper's Gamma^{x,x}_nm is
-// -mu_nm / ((1 + d_n0)(1 + d_m0)) and mu_nm = <r|v T_n v T_m|r>/N for v = -i h~x.
+//   mu_nm = (1/(S R N_eff)) sum_{s,r} <a_n|b_m>,  a_n = T_n(H~) h~a r,  b_m = h~b T_m(H~) r,
+// with h~d = [r_d, H~] for the directions a, b in {x, y} (positions in units of the
+// lattice constant).  Because h~ is anti-Hermitian, <r| h~a T_n h~b T_m |r> = -<a_n|b_m>;
+// the paper's Gamma^{a,b}_nm is -mu_nm / ((1 + d_n0)(1 + d_m0)) and
+// mu_nm = <r|v_a T_n v_b T_m|r>/N for v = -i h~.
 //
 // Per batch of (up to) two random vectors: the A family is the recursion started from
-// a_0 = h~x r_0, each step writing its output row in split-BF16 form; the B family is the
-// recursion from r_0, each step writing h~x r_n (from the neighbours it already staged)
+// a_0 = h~a r_0, each step writing its output row in split-BF16 form; the B family is the
+// recursion from r_0, each step writing h~b r_n (from the neighbours it already staged)
 // as the rows b_n and -i b_n.  The tensor-core contraction (kite_gemm.cu) then gives
 // Re and Im of <a_n|b_m> in one real GEMM per vector.
 #include "kite_step.cuh"
@@ -17,18 +18,19 @@ namespace kite {
 int plan_gemm_splits(kite_ctx* ctx, int Mrows, int Nrows, int64_t Kp);
 int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void* Bhi,
                     const void* Blo, int Mrows, int Nrows, int64_t Kp, int S, int sub_kb,
-                    int nprod, double* part, int* S_used);
+                    int fold, int nprod, double* part, int* S_used);
 int reduce_cplx(kite_ctx* ctx, const double* part, int S, int M, int M2, double scale,
                 double* out, bool accumulate);
 
 namespace {
 
-constexpr int kGemmSubKb = 8;   // 512 products per FP32 accumulation sub-chunk
+constexpr int kGemmSubKb = 8;   // 512 products per FP32 accumulation sub-chunk (TMEM)
+constexpr int kGemmFold = 16;   // sub-chunks summed in FP32 registers before FP64
 constexpr int kGemmProducts = 4; // hi*hi + hi*lo + lo*hi + lo*lo
 
-// h~x applied to a whole FP32 batch (one chunk = two vectors).  mode 1: writes the
-// result as row `col` of the A family (and to out_vec if given); mode 2: rows `col` and
-// `col + M` of the extended B family.
+// h~ = [r_dir, H~] applied to a whole FP32 batch (one chunk = two vectors).  mode 1: writes
+// the result as row `col` of the A family (and to out_vec if given); mode 2: rows `col`
+// and `col + M` of the extended B family.  Bond offsets as in the step kernel's MODE 2.
 template <int LAT>
 __global__ void k_velocity(const float4* __restrict__ in, float4* __restrict__ out_vec,
                            const float* __restrict__ vt, int Lx, int Ly, int mode, const FamOut fam) {
@@ -43,17 +45,21 @@ __global__ void k_velocity(const float4* __restrict__ in, float4* __restrict__ o
     const int ym = y == 0 ? Ly - 1 : y - 1, yp = y + 1 == Ly ? 0 : y + 1;
     float4 v;
     if (LAT == KITE_HONEYCOMB) {
-      // A: n2 = B(x+1,y-1) (offset -a/2), n3 = B(x,y-1) (+a/2)
-      // B: n2 = A(x-1,y+1) (+a/2), n3 = A(x,y+1) (-a/2)
+      // A: n1 = B(x,y), n2 = B(x+1,y-1), n3 = B(x,y-1);  B: n1 = A(x,y), n2 = A(x-1,y+1), n3 = A(x,y+1)
       const int so = 1 - s;
       const int ny = s == 0 ? ym : yp, nx = s == 0 ? xp : xm;
+      const float4 n1 = __ldg(in + cell * 2 + so);
       const float4 n2 = __ldg(in + ((int64_t)ny * Lx + nx) * 2 + so);
       const float4 n3 = __ldg(in + ((int64_t)ny * Lx + x) * 2 + so);
       const float sg = s == 0 ? fam.tvel : -fam.tvel;
-      v = make_float4(sg * (n3.x - n2.x), sg * (n3.y - n2.y), sg * (n3.z - n2.z), sg * (n3.w - n2.w));
+      if (fam.dir == 0)
+        v = make_float4(sg * (n3.x - n2.x), sg * (n3.y - n2.y), sg * (n3.z - n2.z), sg * (n3.w - n2.w));
+      else
+        v = make_float4(sg * ((n2.x + n3.x) - 2.f * n1.x), sg * ((n2.y + n3.y) - 2.f * n1.y),
+                        sg * ((n2.z + n3.z) - 2.f * n1.z), sg * ((n2.w + n3.w) - 2.f * n1.w));
     } else {
-      const float4 n1 = __ldg(in + (int64_t)y * Lx + xm);
-      const float4 n2 = __ldg(in + (int64_t)y * Lx + xp);
+      const float4 n1 = __ldg(in + (fam.dir == 0 ? (int64_t)y * Lx + xm : (int64_t)ym * Lx + x));
+      const float4 n2 = __ldg(in + (fam.dir == 0 ? (int64_t)y * Lx + xp : (int64_t)yp * Lx + x));
       const float t = fam.tvel;
       v = make_float4(t * (n1.x - n2.x), t * (n1.y - n2.y), t * (n1.z - n2.z), t * (n1.w - n2.w));
     }
@@ -72,8 +78,8 @@ __global__ void k_velocity(const float4* __restrict__ in, float4* __restrict__ o
 }
 
 template <int LAT>
-int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
-           double* mu_nm_dev, kite_stats* stats, const double* r0_dev_all) {
+int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc, int alpha,
+           int beta, double* mu_nm_dev, kite_stats* stats, const double* r0_dev_all) {
   constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
   constexpr int C = 1;  // two FP32 vectors per 16-byte chunk
   using Sh = StepShape<LAT, C>;
@@ -130,7 +136,11 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
   KITE_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
 
   const float tt = (float)(sys->t / sc.de_minus);
-  const float tvel = LAT == KITE_HONEYCOMB ? 0.5f * tt : tt;
+  // t~ times the bond-offset unit of each direction (x: a/2, y: a_cc/2 on the honeycomb)
+  auto tvel_of = [&](int dir) -> float {
+    if (LAT != KITE_HONEYCOMB) return tt;
+    return dir == 0 ? 0.5f * tt : (float)(0.5 * (sys->t / sc.de_minus) / sqrt(3.0));
+  };
   const double thr_d = floor(sys->p_vac * 4294967296.0);
   const uint64_t vac_thr =
       sys->p_vac <= 0.0 ? 0ull : (thr_d >= 4294967296.0 ? 4294967296ull : (uint64_t)thr_d);
@@ -151,7 +161,10 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
   }
   fa.Kp = fb.Kp = Kp;
   fa.M = fb.M = M;
-  fa.tvel = fb.tvel = tvel;
+  fa.dir = alpha;
+  fb.dir = beta;
+  fa.tvel = tvel_of(alpha);
+  fb.tvel = tvel_of(beta);
 
   double gemm_s = 0.0, rec_s = 0.0;
   int64_t n_eff = 0;
@@ -171,7 +184,7 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
                                                          k0, k1, r0_in, N, r0);
       KITE_CUDA_TRY(ctx, cudaGetLastError());
       KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, st));
-      // A family: a_0 = h~x r_0 (row 0, and the recursion's start vector in bB)
+      // A family: a_0 = h~alpha r_0 (row 0, and the recursion's start vector in bB)
       fa.col = 0;
       k_velocity<LAT><<<blocks, 256, 0, st>>>(static_cast<const float4*>(r0),
                                               static_cast<float4*>(bB), vt, sys->Lx, sys->Ly, 1, fa);
@@ -187,7 +200,7 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
               whereA(n - 1), whereA(n), whereA(n + 1), nullptr, vt, tt, sys->Lx, sys->Ly, units,
               nullptr, nullptr, ctx->d_status, 0, fa);
       }
-      // B family: recursion from r_0; step n writes b_n = h~x r_n
+      // B family: recursion from r_0; step n writes b_n = h~beta r_n
       auto whereB = [&](int n) -> void* { return n == 0 ? r0 : ((n & 1) ? bA : bB); };
       for (int n = 0; n + 1 < M; ++n) {
         fb.col = n;
@@ -209,7 +222,7 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
       KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
       for (int v = 0; v < nvec; ++v) {
         int S_used = 0;
-        int rc = gemm_split_bf16(ctx, Ah[v], Al[v], Bh[v], Bl[v], M, 2 * M, Kp, Sg, kGemmSubKb,
+        int rc = gemm_split_bf16(ctx, Ah[v], Al[v], Bh[v], Bl[v], M, 2 * M, Kp, Sg, kGemmSubKb, kGemmFold,
                                  kGemmProducts, part, &S_used);
         if (rc != KITE_OK) return rc;
         rc = reduce_cplx(ctx, part, S_used, M, M, scale, mu_nm_dev, true);
@@ -245,10 +258,11 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
 
 }  // namespace
 
-int moments_2d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
-                    double* mu_nm_dev, kite_stats* st, const double* r0_dev_all) {
-  if (sys->lattice == KITE_HONEYCOMB) return run_2d<KITE_HONEYCOMB>(ctx, sys, kpm, sc, mu_nm_dev, st, r0_dev_all);
-  return run_2d<KITE_SQUARE>(ctx, sys, kpm, sc, mu_nm_dev, st, r0_dev_all);
+int moments_2d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc, int alpha,
+                    int beta, double* mu_nm_dev, kite_stats* st, const double* r0_dev_all) {
+  if (sys->lattice == KITE_HONEYCOMB)
+    return run_2d<KITE_HONEYCOMB>(ctx, sys, kpm, sc, alpha, beta, mu_nm_dev, st, r0_dev_all);
+  return run_2d<KITE_SQUARE>(ctx, sys, kpm, sc, alpha, beta, mu_nm_dev, st, r0_dev_all);
 }
 
 }  // namespace kite

@@ -149,17 +149,18 @@ __global__ void __launch_bounds__(256) k_mlp_prior(const float* __restrict__ X, 
   }
 }
 
-// rows of X (FP32, optional per-column scale) gathered by idx -> BF16; targets gathered
-// alongside, minus the prior rows Tsub when given
+// rows of X (FP32, optional per-column shift and scale: (x - shift) * scale) gathered by
+// idx -> BF16; targets gathered alongside, minus the prior rows Tsub when given
 __global__ void k_mlp_gather(const float* __restrict__ X, const int* __restrict__ idx, int rows, int cols,
-                             const float* __restrict__ scale, __nv_bfloat16* __restrict__ out,
+                             const float* __restrict__ shift, const float* __restrict__ scale,
+                             __nv_bfloat16* __restrict__ out,
                              const float* __restrict__ T, float* __restrict__ Tout, int tcols,
                              const float* __restrict__ Tsub = nullptr) {
   const int64_t total = (int64_t)rows * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / cols), c = (int)(e % cols);
     const int64_t src = idx ? idx[r] : r;
-    out[e] = __float2bfloat16(X[src * cols + c] * (scale ? scale[c] : 1.0f));
+    out[e] = __float2bfloat16((X[src * cols + c] - (shift ? shift[c] : 0.0f)) * (scale ? scale[c] : 1.0f));
   }
   if (T) {
     const int64_t tt = (int64_t)rows * tcols;
@@ -338,7 +339,7 @@ int64_t mlp_param_count() { return kParams; }
 
 // Full-batch gradient of the mean L1 loss (for checks): params, X [n][IN], T [n][OUT] device.
 int mlp_gradient_impl(kite_ctx* ctx, const float* params, const float* X, const float* T, int n,
-                      const float* scale, float* grad, double* loss) {
+                      const float* shift, const float* scale, float* grad, double* loss) {
   Net net;
   float* ex;
   int rc = carve_net(ctx, n, &net, &ex, kParams + 4096);
@@ -348,7 +349,7 @@ int mlp_gradient_impl(kite_ctx* ctx, const float* params, const float* X, const 
   double* lsum = reinterpret_cast<double*>(ex + kParams);
   KITE_CUDA_TRY(ctx, cudaMemcpyAsync(p32, params, sizeof(float) * kParams, cudaMemcpyDefault, st));
   k_mlp_tobf16<<<1024, 256, 0, st>>>(p32, net.pb, kParams);
-  k_mlp_gather<<<1024, 256, 0, st>>>(X, nullptr, n, IN, scale, net.X, T, net.T, OUT);
+  k_mlp_gather<<<1024, 256, 0, st>>>(X, nullptr, n, IN, shift, scale, net.X, T, net.T, OUT);
   forward(st, net, p32, n);
   const int lblocks = 256;
   backward(st, net, n, lsum, lblocks);
@@ -361,7 +362,8 @@ int mlp_gradient_impl(kite_ctx* ctx, const float* params, const float* X, const 
   return KITE_OK;
 }
 
-int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, const float* scale, float* Y,
+int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, const float* shift,
+                     const float* scale, float* Y,
                      const kite_mlp_prior* prior) {
   const int chunk = 4096;
   Net net;
@@ -374,7 +376,8 @@ int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, 
   k_mlp_tobf16<<<1024, 256, 0, st>>>(ex, net.pb, kParams);
   for (int r0 = 0; r0 < n; r0 += chunk) {
     const int rows = std::min(chunk, n - r0);
-    k_mlp_gather<<<1024, 256, 0, st>>>(X + (int64_t)r0 * IN, nullptr, rows, IN, scale, net.X, nullptr, nullptr, 0);
+    k_mlp_gather<<<1024, 256, 0, st>>>(X + (int64_t)r0 * IN, nullptr, rows, IN, shift, scale, net.X, nullptr,
+                                       nullptr, 0);
     float* P = pri ? ex + kParams : nullptr;
     if (pri) launch_prior(st, ctx->num_sms, X + (int64_t)r0 * IN, rows, prior, P);
     forward(st, net, ex, rows, P);
@@ -385,7 +388,7 @@ int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, 
   return KITE_OK;
 }
 
-int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const float* scale,
+int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const float* shift, const float* scale,
                    const kite_mlp_train_cfg* cfg, float* params, float* loss_curve,
                    const kite_mlp_prior* prior) {
   const int bs = std::max(1, std::min(cfg->batch, n));
@@ -421,7 +424,7 @@ int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const f
       const int rows = std::min(bs, n - b * bs);
       KITE_CUDA_TRY(ctx, cudaMemcpyAsync(d_idx, order.data() + (size_t)b * bs, sizeof(int) * rows,
                                          cudaMemcpyHostToDevice, st));
-      k_mlp_gather<<<512, 256, 0, st>>>(X, d_idx, rows, IN, scale, net.X, T, net.T, OUT, P);
+      k_mlp_gather<<<512, 256, 0, st>>>(X, d_idx, rows, IN, shift, scale, net.X, T, net.T, OUT, P);
       forward(st, net, p32, rows);
       backward(st, net, rows, lsum, lblocks);
       ++t;

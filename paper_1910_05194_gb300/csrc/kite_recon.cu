@@ -65,7 +65,72 @@ __global__ void k_dos_eval(const double* __restrict__ coef, int M, double de_plu
   if (k < K) rho[k] = inside ? sum / (3.141592653589793 * sqrt(1.0 - eps * eps)) / de_minus : 0.0;
 }
 
+// Average Green's function G(E + i eta) per eV (Eqs. green_function_cheb_expansion/b traced
+// as in Eq. e7): sum_n (c_n / 2) g^{+,eta~}_n(eps) / de_minus with c_n = (2 - d_n0) g_n mu_n
+// from k_dos_coef, and the retarded CPGF coefficients g_n = -2i q^n / sqrt(1 - z^2),
+// q = z - i sqrt(1 - z^2), z = eps + i eta~ (geometric in n).  One thread per energy.
+struct gcplx {
+  double re, im;
+};
+__device__ __forceinline__ gcplx gmul(gcplx a, gcplx b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__device__ __forceinline__ gcplx gsqrt(gcplx z) {  // principal branch
+  const double r = hypot(z.re, z.im);
+  if (r == 0.0) return {0.0, 0.0};
+  if (z.re >= 0.0) {
+    const double t = sqrt(0.5 * (r + z.re));
+    return {t, z.im / (2.0 * t)};
+  }
+  const double t = sqrt(0.5 * (r - z.re));
+  return {fabs(z.im) / (2.0 * t), z.im >= 0.0 ? t : -t};
+}
+
+__global__ void k_green_eval(const double* __restrict__ coef, int M, double de_plus, double de_minus,
+                             double eta_t, const double* __restrict__ E, int K, double* __restrict__ G,
+                             double* __restrict__ rho) {
+  __shared__ double tile[1024];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const double eps = k < K ? (E[k] - de_plus) / de_minus : 0.0;
+  const gcplx z = {eps, eta_t};
+  const gcplx r = gsqrt({1.0 - (z.re * z.re - z.im * z.im), -2.0 * z.re * z.im});
+  const gcplx q = {z.re + r.im, z.im - r.re};  // z - i r
+  // g_0 = -2i / r
+  const double rr = r.re * r.re + r.im * r.im;
+  gcplx g = {-2.0 * r.im / rr, -2.0 * r.re / rr};
+  double are = 0.0, aim = 0.0;
+  for (int base = 0; base < M; base += 1024) {
+    const int len = min(1024, M - base);
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) tile[i] = 0.5 * coef[base + i];
+    __syncthreads();
+    for (int i = 0; i < len; ++i) {
+      are += tile[i] * g.re;
+      aim += tile[i] * g.im;
+      g = gmul(g, q);
+    }
+  }
+  if (k < K) {
+    if (G) {
+      G[2 * k] = are / de_minus;
+      G[2 * k + 1] = aim / de_minus;
+    }
+    if (rho) rho[k] = -aim / de_minus / 3.141592653589793;
+  }
+}
+
 }  // namespace
+
+int reconstruct_green_impl(kite_ctx* ctx, const double* mu_dev, int M_use, int kernel, double param,
+                           const Scale& sc, double eta, const double* E_dev, int K, double* G_dev,
+                           double* rho_dev, double* coef_dev) {
+  k_dos_coef<<<(M_use + 255) / 256, 256, 0, ctx->stream>>>(mu_dev, M_use, kernel, param, coef_dev);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  k_green_eval<<<(K + 127) / 128, 128, 0, ctx->stream>>>(coef_dev, M_use, sc.de_plus, sc.de_minus,
+                                                         eta / sc.de_minus, E_dev, K, G_dev, rho_dev);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  return KITE_OK;
+}
 
 int reconstruct_dos_impl(kite_ctx* ctx, const double* mu_dev, int M_use, int kernel,
                          double param, const Scale& sc, const double* E_dev, int K,

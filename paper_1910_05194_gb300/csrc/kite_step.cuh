@@ -144,7 +144,9 @@ struct FamOut {
   int64_t Kp;
   int col;
   int M;
-  float tvel;  // t~ times the bond x-offset unit: t~/2 (honeycomb), t~ (square)
+  int dir;     // velocity direction of MODE 2: 0 = x, 1 = y
+  float tvel;  // t~ times the bond-offset unit of `dir`: honeycomb x t~/2, y t~ a_cc/2
+               // (a_cc = 1/sqrt(3)); square t~
 };
 
 __device__ __forceinline__ void fam_store(const FamOut& f, int v, int row, int64_t o, float re,
@@ -365,16 +367,26 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
             if constexpr (MODE == 1) {
               fam_store(fam, vv, fam.col, o, out.v[2 * q], out.v[2 * q + 1]);
             } else {
-              // h~x r at this orbital: bond x-offsets 0, -a/2, +a/2 (A) and 0, +a/2, -a/2 (B)
-              // for the neighbours n1, n2, n3; -a and +a for (x-1), (x+1) on the square lattice
+              // h~ r at this orbital, h~ = [r_dir, H~]: honeycomb bond offsets (x, y) of the
+              // neighbours n1, n2, n3 are (0, -a_cc), (-a/2, a_cc/2), (a/2, a_cc/2) on A
+              // and the negatives on B; square (x-1), (x+1), (y-1), (y+1) have x offsets
+              // +1, -1 and y offsets +1, -1 for n1, n2 and n3, n4
               float vr, vi;
               if (LAT == KITE_HONEYCOMB) {
                 const float sg = s == 0 ? fam.tvel : -fam.tvel;
-                vr = sg * (n3.v[2 * q] - n2.v[2 * q]);
-                vi = sg * (n3.v[2 * q + 1] - n2.v[2 * q + 1]);
-              } else {
+                if (fam.dir == 0) {
+                  vr = sg * (n3.v[2 * q] - n2.v[2 * q]);
+                  vi = sg * (n3.v[2 * q + 1] - n2.v[2 * q + 1]);
+                } else {
+                  vr = sg * ((n2.v[2 * q] + n3.v[2 * q]) - 2.f * n1.v[2 * q]);
+                  vi = sg * ((n2.v[2 * q + 1] + n3.v[2 * q + 1]) - 2.f * n1.v[2 * q + 1]);
+                }
+              } else if (fam.dir == 0) {
                 vr = fam.tvel * (n1.v[2 * q] - n2.v[2 * q]);
                 vi = fam.tvel * (n1.v[2 * q + 1] - n2.v[2 * q + 1]);
+              } else {
+                vr = fam.tvel * (n3.v[2 * q] - n4.v[2 * q]);
+                vi = fam.tvel * (n3.v[2 * q + 1] - n4.v[2 * q + 1]);
               }
               if (vacant) vr = vi = 0.f;
               fam_store(fam, vv, fam.col, o, vr, vi);

@@ -86,33 +86,36 @@ def l1_error(rho, ref, e_min: float, e_max: float) -> np.ndarray:
     return np.sum(np.abs(np.asarray(rho, np.float64) - np.asarray(ref, np.float64)), axis=1) * dE
 
 
-def input_scale(X: np.ndarray) -> np.ndarray:
-    """Fixed per-index input normalisation: 1 / std of each moment over the training set
-    (mu_0 = 1 is left as is)."""
-    s = (1.0 / np.maximum(X.std(0), 1e-3)).astype(np.float32)
-    s[0] = 1.0
-    return s
+def input_norm(X: np.ndarray):
+    """Fixed per-index input normalisation from the training set: (x - mean) / std, with
+    std floored at 1e-4 (mu_0 = 1 for every sample maps to 0).  Returns (shift, scale).
+    Without centring, moments whose mean is far from zero relative to their spread give
+    pre-activations so large that the ReLU units die early in training."""
+    shift = X.mean(0).astype(np.float32)
+    scale = (1.0 / np.maximum(X.std(0), 1e-4)).astype(np.float32)
+    return shift, scale
 
 
-def train(ctx: Context, X, T, e_min: float, e_max: float, params, epochs=60, batch=256, lr=1e-3,
+def train(ctx: Context, X, T, e_min: float, e_max: float, params, epochs=200, batch=256, lr=1e-3,
           weight_decay=1e-4, seed=0):
-    """Trains `params` in place as a residual on the Jackson prior; returns (scale, curve)."""
-    scale = input_scale(X)
+    """Trains `params` in place as a residual on the Jackson prior; returns (norm, curve)
+    with norm = (shift, scale) of the inputs."""
+    norm = input_norm(X)
     curve = np.zeros(epochs, np.float32)
     mlp_train(ctx, np.ascontiguousarray(X, np.float32), np.ascontiguousarray(T, np.float32), X.shape[0],
-              params, epochs=epochs, batch=batch, lr=lr, weight_decay=weight_decay, seed=seed, scale=scale,
-              loss_curve=curve, prior=jackson_prior(e_min, e_max))
-    return scale, curve
+              params, epochs=epochs, batch=batch, lr=lr, weight_decay=weight_decay, seed=seed, shift=norm[0],
+              scale=norm[1], loss_curve=curve, prior=jackson_prior(e_min, e_max))
+    return norm, curve
 
 
-def infer(ctx: Context, params, scale, mu, e_min: float, e_max: float, kcheck: int = 16,
+def infer(ctx: Context, params, norm, mu, e_min: float, e_max: float, kcheck: int = 16,
           tol: float = 0.02):
     """Learned densities [n][OUT] (per eV, midpoint grid) from the first MLP_IN moments of
     each row of mu, with the consistency gate: returns (rho, flags, deviation)."""
     n = mu.shape[0]
     X = np.ascontiguousarray(mu[:, :MLP_IN], np.float32)
     rho = np.zeros((n, MLP_OUT), np.float32)
-    mlp_forward(ctx, params, X, n, rho, scale=scale, prior=jackson_prior(e_min, e_max))
+    mlp_forward(ctx, params, X, n, rho, shift=norm[0], scale=norm[1], prior=jackson_prior(e_min, e_max))
     flags = np.zeros(n, np.int32)
     dev = np.zeros(n)
     learned_gate(ctx, rho, np.ascontiguousarray(mu, np.float64), mu.shape[1], n, kcheck, e_min, e_max,
@@ -129,14 +132,14 @@ def plain_dos(ctx: Context, system, M: int, R: int, e_min: float, e_max: float,
     return jackson_dos(ctx, mu[None, :], M, e_min, e_max)[0]
 
 
-def reconstruct(ctx: Context, systems, params, scale, R: int, e_min: float, e_max: float,
+def reconstruct(ctx: Context, systems, params, norm, R: int, e_min: float, e_max: float,
                 M_fallback: int, kcheck: int = 16, tol: float = 0.02):
     """The learned path with fallback: 128 FP32 moments per system in one batched launch
     (moment doubling), the network, the gate, and the plain FP64 path at M_fallback for
     flagged systems.
     Returns (rho [n][OUT], flags)."""
     mu, _ = batched_moments(ctx, systems, MLP_IN, R, e_min, e_max)
-    rho, flags, _ = infer(ctx, params, scale, mu, e_min, e_max, kcheck, tol)
+    rho, flags, _ = infer(ctx, params, norm, mu, e_min, e_max, kcheck, tol)
     for i in np.nonzero(flags)[0]:
         rho[i] = plain_dos(ctx, systems[i], M_fallback, R, e_min, e_max)
     return rho, flags
@@ -173,13 +176,13 @@ def main(argv=None):
     params = synth.mlp_init(a.seed + 1, head_scale=0.01)
     assert params.size == mlp_param_count()
     t0 = time.perf_counter()
-    scale, curve = train(ctx, X[:ntr], T[:ntr], e_min, e_max, params, epochs=a.epochs, batch=a.batch,
-                         lr=a.lr, seed=a.seed)
+    norm, curve = train(ctx, X[:ntr], T[:ntr], e_min, e_max, params, epochs=a.epochs, batch=a.batch,
+                        lr=a.lr, seed=a.seed)
     t_train = time.perf_counter() - t0
 
     test_mu, test_T = mu[ntr:], T[ntr:]
     base = jackson_dos(ctx, test_mu, MLP_IN, e_min, e_max)
-    rho, flags, dev = infer(ctx, params, scale, test_mu, e_min, e_max)
+    rho, flags, dev = infer(ctx, params, norm, test_mu, e_min, e_max)
     l1_net = l1_error(rho, test_T, e_min, e_max)
     l1_base = l1_error(base, test_T, e_min, e_max)
     # the plain path's order that reaches the network's held-out L1 error
@@ -196,9 +199,9 @@ def main(argv=None):
     ts = systems[ntr:ntr + a.time_sample]
     res = {}
     if M_plain is not None:
-        reconstruct(ctx, ts[:4], params, scale, a.R, e_min, e_max, M_plain)  # warm-up
+        reconstruct(ctx, ts[:4], params, norm, a.R, e_min, e_max, M_plain)  # warm-up
         t0 = time.perf_counter()
-        _, fl = reconstruct(ctx, ts, params, scale, a.R, e_min, e_max, M_plain)
+        _, fl = reconstruct(ctx, ts, params, norm, a.R, e_min, e_max, M_plain)
         res["learned_s"] = time.perf_counter() - t0
         res["learned_flagged"] = int(np.sum(fl))
         plain_dos(ctx, ts[0], M_plain, a.R, e_min, e_max)  # warm-up

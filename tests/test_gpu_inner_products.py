@@ -3,7 +3,8 @@ the plain FP64 definition C = scale * conj(A) B^T (the contraction of Eq. Gamman
 
 Error model of the GPU path: each FP32 input is represented as hi + lo (bf16 each) to
 relative 2^-17, the dropped lo*lo term is 2^-16 relative per product, FP32 sums inside
-sub-chunks of `sub_k` products and FP64 above.  The bar, written per test, is a bound on
+sub-chunks of `sub_k` products, FP32 again over `fold` sub-chunks (registers) and FP64
+above.  The bar, written per test, is a bound on
 |C_gpu - C_ref| relative to sum_i |A_n(i)| |B_m(i)| (the scale of the terms)."""
 import numpy as np
 import pytest
@@ -23,13 +24,13 @@ def ctx():
     c.close()
 
 
-def run(ctx, A, B, scale=1.0, sub_k=0, products=0):
+def run(ctx, A, B, scale=1.0, sub_k=0, products=0, fold=0):
     M, N = A.shape
     M2 = B.shape[0]
     A32 = np.ascontiguousarray(A.astype(np.complex64))
     B32 = np.ascontiguousarray(B.astype(np.complex64))
     C = np.zeros((M, M2), np.complex128)
-    kite.inner_products(ctx, A32, B32, M, M2, N, scale, C, sub_k, products)
+    kite.inner_products(ctx, A32, B32, M, M2, N, scale, C, sub_k, products, fold)
     ref = oracle.inner_products(A32, B32, scale)
     bound = np.abs(scale) * (np.abs(A32).astype(np.float64) @ np.abs(B32).astype(np.float64).T)
     return C, ref, bound
@@ -58,13 +59,19 @@ def test_aligned_terms_long_k_accumulation(ctx):
         A = vec[None, :].astype(np.complex64)
         for products in (3, 4):
             for sub_k in (256, 512, 1024, 4096):
-                C, ref, bound = run(ctx, A, A, scale=1.0 / N, sub_k=sub_k, products=products)
+                # fold = 1: every sub-chunk straight to FP64, the sub-chunk alone measured
+                C, ref, bound = run(ctx, A, A, scale=1.0 / N, sub_k=sub_k, products=products, fold=1)
                 res[(name, products, sub_k)] = abs(C[0, 0] - ref[0, 0]) / abs(ref[0, 0])
-    for k, v in sorted(res.items()):
+        for fold in (4, 16, 64):
+            C, ref, bound = run(ctx, A, A, scale=1.0 / N, sub_k=512, products=4, fold=fold)
+            res[(name, 4, 512, "fold", fold)] = abs(C[0, 0] - ref[0, 0]) / abs(ref[0, 0])
+    for k, v in sorted(res.items(), key=str):
         print(f"{k}: relative error {v:.3e}")
-    # default path (4 products, 512-product sub-chunks) well inside the 1e-5 bar; the
-    # FP32 accumulation error grows linearly with the sub-chunk length
+    # default path (4 products, 512-product sub-chunks, 16 of them summed in FP32) well
+    # inside the 1e-5 bar; the FP32 accumulation error grows linearly with the sub-chunk
+    # length, while the second FP32 level adds ~fold/4 * 2^-24 at most
     assert res[("general", 4, 512)] <= 4e-6
+    assert res[("general", 4, 512, "fold", 16)] <= res[("general", 4, 512)] + 5e-7
     assert res[("bf16-exact", 4, 256)] <= 1e-12  # bf16 products sum exactly over 256 terms
     assert res[("general", 4, 256)] < res[("general", 4, 4096)]
 

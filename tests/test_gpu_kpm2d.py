@@ -2,7 +2,8 @@
 plain FP64 triple loop over the stored families.
 
 Bar: max |mu_gpu - mu_oracle| <= 1e-5 * max |mu_oracle| (FP32 recursion, split-BF16
-tensor-core contraction with FP32 sums inside 2048-product sub-chunks, FP64 above)."""
+tensor-core contraction with FP32 sums inside 512-product sub-chunks and over 16 of them,
+FP64 above), for every pair of velocity directions (x, y)."""
 import numpy as np
 import pytest
 
@@ -21,13 +22,14 @@ def ctx():
     c.close()
 
 
-def run2d(ctx, d, M, R, S=1, r0=None):
+def run2d(ctx, d, M, R, S=1, r0=None, alpha=0, beta=0):
     n = oracle.norb(oracle.make_system(**d))
     r0a = None
     if r0 is not None:
         r0a = np.ascontiguousarray(np.stack([r0.real, r0.imag], -1).astype(np.float64))
     mu = np.zeros((M, M, 2), np.float64)
-    st = kite.moments_2d(ctx, kite.make_system(**d), kite.make_kpm(M, R, S, kite.FP32, r0=r0a), mu)
+    st = kite.moments_2d(ctx, kite.make_system(**d), kite.make_kpm(M, R, S, kite.FP32, r0=r0a), mu,
+                         alpha, beta)
     return mu[..., 0] + 1j * mu[..., 1], st
 
 
@@ -43,6 +45,18 @@ def test_small_lattices_against_triple_loop(ctx, d, M, R):
     assert np.max(np.abs(mu - ref)) <= 1e-5 * scale
     _, vac = oracle.disorder(oracle.make_system(**d))
     assert st.n_eff == int((vac == 0).sum())
+
+
+@pytest.mark.parametrize("alpha,beta", [(1, 1), (0, 1), (1, 0)])
+@pytest.mark.parametrize("d,M,R", [
+    (dict(lattice=0, Lx=24, Ly=20, t=-2.7, W=1.0, p_vac=0.02, seed=4), 32, 3),
+    (dict(lattice=1, Lx=33, Ly=17, t=-1.0, W=3.0, p_vac=0.03, seed=6), 48, 1),
+])
+def test_y_and_mixed_directions_against_triple_loop(ctx, d, M, R, alpha, beta):
+    """mu^{yy}, mu^{xy}, mu^{yx} (sigma_yy and the Hall pair) against the oracle."""
+    mu, st = run2d(ctx, d, M, R, alpha=alpha, beta=beta)
+    ref = oracle.moments_2d(oracle.make_system(**d), M, R, alpha=alpha, beta=beta)
+    assert np.max(np.abs(mu - ref)) <= 1e-5 * np.max(np.abs(ref))
 
 
 def test_caller_start_vectors(ctx):

@@ -62,6 +62,21 @@ def test_forward_and_gradient_match_oracle(ctx):
         off += k
 
 
+def test_input_normalisation_matches_oracle(ctx):
+    """(x - shift) * scale in FP32 before the BF16 rounding, as the oracle computes it."""
+    n = 48
+    p = synth.mlp_init(13)
+    g = np.random.Generator(np.random.PCG64(14))
+    X = (0.3 + 0.05 * g.standard_normal((n, omlp.IN))).astype(np.float32)
+    shift = X.mean(0).astype(np.float32)
+    scale = (1.0 / X.std(0)).astype(np.float32)
+    Y = np.zeros((n, omlp.OUT), np.float32)
+    kite.mlp_forward(ctx, p, X, n, Y, shift=shift, scale=scale)
+    Xk = omlp.round_bf16((X - shift) * scale)
+    Yref, _ = omlp.forward(omlp.kernel_params(p), Xk, act_round=omlp.round_bf16)
+    assert rel(Y, Yref) <= 2e-2
+
+
 def test_jackson_prior_matches_oracle(ctx):
     """With all parameters zero the network adds nothing: the output is the prior alone."""
     n = 40
@@ -99,10 +114,10 @@ def test_training_beats_the_plain_low_order_reconstruction(ctx):
     mu, T, base, e_min, e_max = make_dataset(ctx, ntr + nte, seed=70_000)
     X = mu[:, :omlp.IN].astype(np.float32)
     p = synth.mlp_init(11, head_scale=0.01)
-    scale, curve = learned.train(ctx, X[:ntr], T[:ntr], e_min, e_max, p, epochs=40, batch=128, lr=1e-3,
-                                 seed=3)
+    norm, curve = learned.train(ctx, X[:ntr], T[:ntr], e_min, e_max, p, epochs=40, batch=128, lr=1e-3,
+                                seed=3)
     assert curve[-1] < curve[0]
-    rho, flags, dev = learned.infer(ctx, p, scale, mu[ntr:], e_min, e_max)
+    rho, flags, dev = learned.infer(ctx, p, norm, mu[ntr:], e_min, e_max)
     l1_net = np.mean(learned.l1_error(rho, T[ntr:], e_min, e_max))
     l1_base = np.mean(learned.l1_error(base[ntr:], T[ntr:], e_min, e_max))
     print(f"held-out L1: network {l1_net:.4f}, Jackson M=128 {l1_base:.4f}; loss {curve[0]:.4g} -> "

@@ -26,8 +26,10 @@ MUTATIONS = [
      "si += a[2 * o] * b[2 * o + 1] - a[2 * o + 1] * b[2 * o];",
      "si += a[2 * o] * b[2 * o + 1] + a[2 * o + 1] * b[2 * o];"),
     ("disorder not centred", "double v = sys->W * (u - 0.5);", "double v = sys->W * u;"),
-    ("velocity loses its sign", "double w = h->dx[4 * o + k] * h->tt;",
-     "double w = fabs(h->dx[4 * o + k]) * h->tt;"),
+    ("velocity loses its sign", "double w = off[4 * o + k] * h->tt;",
+     "double w = fabs(off[4 * o + k]) * h->tt;"),
+    ("y bond offset sign", "dy[1] = 0.5 * acc;", "dy[1] = -0.5 * acc;"),
+    ("velocity direction ignored", "const double* off = dir ? h->dy : h->dx;", "const double* off = h->dx;"),
     ("Jackson kernel off by one",
      "g[n] = ((double)(M - n + 1) * cos(q * n) + sin(q * n) * cot) / (double)(M + 1);",
      "g[n] = ((double)(M - n) * cos(q * n) + sin(q * n) * cot) / (double)(M + 1);"),

@@ -360,21 +360,90 @@ def test_exact_trace_2d_moments_match_bloch_velocity():
     assert abs(mu[0, 0].real - 0.5 * tt * tt) < 1e-14
 
 
-def test_2d_moments_with_disorder_match_dense_diagonalisation():
+def test_y_velocity_is_antisymmetric_with_bond_weights():
+    """h~y = [y, H]: real antisymmetric; sum_j (y_i-y_j)^2 = a_cc^2 + 2 (a_cc/2)^2 = 1/2 per
+    honeycomb site (a_cc = a/sqrt(3), orbital positions of the lattice set-up listing) and
+    2 per square site; and sum_j (x_i-x_j)(y_i-y_j) = 0 (no preferred diagonal)."""
+    for lat, expect in ((oracle.HONEYCOMB, 0.5), (oracle.SQUARE, 2.0)):
+        sys = oracle.make_system(lattice=lat, Lx=5, Ly=4, t=1.0)
+        n = oracle.norb(sys)
+        zero = np.zeros(n, np.uint8)
+        hy = np.array([oracle.velocity(sys, zero, 1.0, np.eye(n)[j], 1) for j in range(n)]).T.real
+        hx = dense_vx(sys, zero, 1.0)
+        assert np.array_equal(hy, -hy.T)
+        assert np.allclose((hy * hy).sum(axis=1), expect)
+        assert np.allclose((hx * hy).sum(axis=1), 0.0)
+
+
+def bloch_2d_moments(Lx, Ly, M, tt, alpha, beta):
+    """(1/N) sum_k Tr[v_alpha(k) T_n(H(k)) v_beta(k) T_m(H(k))] for the clean honeycomb
+    lattice in the atomic gauge: H_AB(k) = t~ sum_d exp(i k.d) over the three bond vectors
+    d = r_B - r_A = (0, a_cc), (a/2, -a_cc/2), (-a/2, -a_cc/2), v(k) = dH/dk (v = i[H, r])."""
+    acc = 1.0 / np.sqrt(3.0)
+    bonds = np.array([[0.0, acc], [0.5, -0.5 * acc], [-0.5, -0.5 * acc]])
+    ref = np.zeros((M, M), np.complex128)
+    for m1 in range(Lx):
+        for m2 in range(Ly):
+            k1, k2 = 2 * np.pi * m1 / Lx, 2 * np.pi * m2 / Ly  # k.a1, k.a2
+            k = np.array([k1, (2.0 * k2 - k1) / np.sqrt(3.0)])
+            ph = np.exp(1j * bonds @ k)
+            f = tt * ph.sum()
+            Hk = np.array([[0, f], [np.conj(f), 0]])
+            vs = []
+            for d in (alpha, beta):
+                df = tt * np.sum(1j * bonds[:, d] * ph)
+                vs.append(np.array([[0, df], [np.conj(df), 0]]))
+            lam, U = np.linalg.eigh(Hk)
+            Tn = cheb_T(M, lam)
+            va, vb = (U.conj().T @ v @ U for v in vs)
+            for a in range(2):
+                for b in range(2):
+                    ref += va[a, b] * vb[b, a] * np.outer(Tn[:, b], Tn[:, a])
+    return ref / (2 * Lx * Ly)
+
+
+@pytest.mark.parametrize("alpha,beta", [(0, 0), (1, 1), (0, 1), (1, 0)])
+def test_exact_trace_2d_moments_match_bloch_velocity_all_directions(alpha, beta):
+    """The four tensor components against the Bloch velocities dH/dk_x, dH/dk_y."""
+    Lx, Ly, M = 4, 3, 10
+    sys = oracle.make_system(Lx=Lx, Ly=Ly, t=T_EV)
+    lo, hi = oracle.bounds_auto(sys)
+    tt = T_EV / (0.5 * (hi - lo))
+    n = oracle.norb(sys)
+    mu = oracle.moments_2d(sys, M, n, r0=np.eye(n, dtype=np.complex128), alpha=alpha, beta=beta) * n
+    ref = bloch_2d_moments(Lx, Ly, M, tt, alpha, beta)
+    assert np.max(np.abs(mu - ref)) < 1e-12
+
+
+def test_clean_honeycomb_response_is_isotropic():
+    """On the clean L x L torus (a 120-degree rotation and the mirror x -> -x map it to
+    itself) Tr[h T_n h T_m] is isotropic: mu^yy = mu^xx and mu^xy = mu^yx = 0."""
+    sys = oracle.make_system(Lx=4, Ly=4, t=T_EV)
+    n = oracle.norb(sys)
+    eye = np.eye(n, dtype=np.complex128)
+    mu = {(a, b): oracle.moments_2d(sys, 9, n, r0=eye, alpha=a, beta=b) * n for a in (0, 1) for b in (0, 1)}
+    assert np.max(np.abs(mu[(1, 1)] - mu[(0, 0)])) < 1e-12
+    assert np.max(np.abs(mu[(0, 1)])) < 1e-12 and np.max(np.abs(mu[(1, 0)])) < 1e-12
+    assert np.max(np.abs(mu[(0, 0)])) > 1e-3
+
+
+@pytest.mark.parametrize("alpha,beta", [(0, 0), (1, 1), (0, 1)])
+def test_2d_moments_with_disorder_match_dense_diagonalisation(alpha, beta):
     sys = oracle.make_system(Lx=4, Ly=4, W=2.0, p_vac=0.1, seed=31)
     M = 12
     lo, hi = oracle.bounds_auto(sys)
     dm = 0.5 * (hi - lo)
     n = oracle.norb(sys)
     H, keep, vac = dense_h(sys)
-    hx = dense_vx(sys, vac, sys.t / dm)[np.ix_(keep, keep)]
-    v = -1j * hx
+    vel = []
+    for d in (alpha, beta):
+        h = np.array([oracle.velocity(sys, vac, sys.t / dm, np.eye(n)[j], d) for j in range(n)]).T.real
+        vel.append(-1j * h[np.ix_(keep, keep)])
     lam, U = np.linalg.eigh(H)
     Tn = cheb_T(M, lam)
-    vv = U.conj().T @ v @ U
-    P = np.abs(vv) ** 2
-    ref = np.einsum("ab,nb,ma->nm", P, Tn, Tn) / len(keep)
-    mu = oracle.moments_2d(sys, M, n, r0=np.eye(n, dtype=np.complex128)) * n
+    va, vb = (U.conj().T @ v @ U for v in vel)
+    ref = np.einsum("ab,ba,nb,ma->nm", va, vb, Tn, Tn) / len(keep)
+    mu = oracle.moments_2d(sys, M, n, r0=np.eye(n, dtype=np.complex128), alpha=alpha, beta=beta) * n
     assert np.max(np.abs(mu - ref)) < 1e-12
 
 
