@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-doubling", action="store_true")
+    p.add_argument("--no-secondary", action="store_true")
     return p.parse_args()
 
 
@@ -211,6 +212,58 @@ def cpu_baseline_leg(args, kite, ctx, n_eff_gpu):
             "n_eff_match": bool(n_eff == n_eff_gpu)}
 
 
+def secondary_legs(kite, ctx, peaks):
+    """The other hot-path configurations, each in its own launch configuration: the small
+    FP64 DOS call (latency-bound, microseconds per call), the 256-system batched
+    persistent launch, and the 2D Kubo-Bastin moments (families + tensor-core
+    contraction).  Parity of each lives in the tests; here only their timings."""
+    import synth
+    out = {}
+    # small FP64 DOS: honeycomb 64x64, W = 1, bounds +-(3|t| + 0.5) * 1.01, M = 256, R = 4
+    b = (3 * 2.7 + 0.5) * 1.01
+    s1 = kite.make_system(kite.HONEYCOMB, 64, 64, -2.7, 1.0, 0.0, 0.0, 1)
+    mu1 = np.zeros(256)
+    res = {}
+    for name, dbl in (("plain", False), ("doubling", True)):
+        kpm1 = kite.make_kpm(256, 4, 1, kite.FP64, -b, b, doubling=dbl)
+        for _ in range(3):
+            kite.moments_1d(ctx, s1, kpm1, mu1)
+        t0 = time.perf_counter()
+        for _ in range(20):
+            kite.moments_1d(ctx, s1, kpm1, mu1)
+        res[name + "_us_per_call"] = 1e6 * (time.perf_counter() - t0) / 20
+    out["small_dos_honeycomb_64x64_M256_R4_fp64"] = res
+    # batched: 256 square systems, L 64..1024, W 0..4, M in {512..4096}, R = 4, one launch
+    specs = synth.batched_square_systems(256, seed=3)
+    systems = [kite.make_system(kite.SQUARE, sp["L"], sp["L"], -1.0, sp["W"], 0.0, 0.0, sp["seed"])
+               for sp in specs]
+    mus = [np.zeros(sp["M"]) for sp in specs]
+    res = {}
+    for name, dbl in (("plain", False), ("doubling", True)):
+        kpms = [kite.make_kpm(sp["M"], 4, 1, kite.FP32, doubling=dbl) for sp in specs]
+        st = kite.moments_1d_batched(ctx, systems, kpms, mus)
+        res[name] = {"updates_per_s": st.updates / st.seconds, "seconds": st.seconds,
+                     "hbm_gbs": st.bytes_moved / st.seconds / 1e9, "grid": st.grid}
+    res["updates"] = st.updates
+    out["batched_256_square_systems_R4_fp32_one_graph_launch"] = res
+    # 2D Kubo-Bastin moments: honeycomb 1024x1024, W = 1, M = 1024, R = 4 (xx)
+    s4 = kite.make_system(kite.HONEYCOMB, 1024, 1024, -2.7, 1.0, 0.0, 0.0, 4)
+    import torch
+    mu_nm = torch.zeros((1024, 1024, 2), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = kite.moments_2d(ctx, s4, kite.make_kpm(1024, 4, 1, kite.FP32), mu_nm)
+    wall = time.perf_counter() - t0
+    tflops = st.gemm_flops / st.gemm_seconds / 1e12
+    out["kubo_bastin_honeycomb_1024x1024_M1024_R4"] = {
+        "wall_s": wall, "families_s": st.step_seconds, "contraction_s": st.gemm_seconds,
+        "contraction_tflops": tflops, "bf16_peak_tflops": peaks.get("bf16_tflops"),
+        "contraction_frac_of_burst": tflops / peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None,
+        "contraction_frac_of_sustained": (tflops / peaks["bf16_tflops_sustained"]
+                                          if peaks.get("bf16_tflops_sustained") else None)}
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -362,6 +415,14 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_leg(args, kite, ctx, st.n_eff)
+    secondary = None
+    if rank == 0 and world == 1 and not args.no_secondary:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                peaks = json.load(f)
+        except Exception:
+            peaks = {}
+        secondary = secondary_legs(kite, ctx, peaks)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -374,7 +435,7 @@ def main():
                            "parallelism": f"{world} independent realisations" if world > 1 else "single GPU",
                            "grid": st.grid, "block": st.block},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "moment_doubling": doubling,
+                "moment_doubling": doubling, "secondary": secondary,
                 "gpu_launches": launches_per_step * args.steps,
                 "wall_s_timed": wall}
         print(json.dumps(line), flush=True)

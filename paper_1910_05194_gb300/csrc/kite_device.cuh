@@ -170,6 +170,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
+// Element (row, k) of a split-BF16 vector family stored K-blocked: the 64 K columns of one
+// block for all `rows` rows are contiguous ([K/64][rows][64]), so a TMA box of 64 columns
+// by 128 or 256 rows is one contiguous run of memory instead of rows spread Kp apart.
+__host__ __device__ __forceinline__ int64_t fam_index(int64_t row, int64_t k, int64_t rows) {
+  return ((k >> 6) * rows + row) * 64 + (k & 63);
+}
+
 // 1D bulk copy global -> shared, completion counted in bytes on `bar`.  Both addresses
 // 16-byte aligned, size a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,

@@ -59,12 +59,13 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y) {
+// One box of a K-blocked family: 64 columns (x = 0) of rows [y, y + box) in K block z.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint64_t* bar,
+                                            int y, int z) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(0), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -221,10 +222,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           }
           mbar_arrive_expect_tx(&full[st], kStageBytes);
           const uint32_t sb = base + st * kStageBytes;
-          tma_load_2d(sb, &tmAh, &full[st], kb * kBK, tm * kBM);
-          tma_load_2d(sb + kATile, &tmAl, &full[st], kb * kBK, tm * kBM);
-          tma_load_2d(sb + 2 * kATile, &tmBh, &full[st], kb * kBK, tn * kBN);
-          tma_load_2d(sb + 2 * kATile + kBTile, &tmBl, &full[st], kb * kBK, tn * kBN);
+          tma_load_3d(sb, &tmAh, &full[st], tm * kBM, kb);
+          tma_load_3d(sb + kATile, &tmAl, &full[st], tm * kBM, kb);
+          tma_load_3d(sb + 2 * kATile, &tmBh, &full[st], tn * kBN, kb);
+          tma_load_3d(sb + 2 * kATile + kBTile, &tmBl, &full[st], tn * kBN, kb);
           pend[st] = (int)ph;
           if (++st == kGStages) st = 0, ph ^= 1u;
         }
@@ -375,10 +376,11 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));  // x - hi is exact in FP32
 }
 
-// rows [rows][N] complex FP32 -> hi/lo [out_rows][Kp] bf16 with K = 2N interleaved
-// (re, im).  rot = 1 writes -i*z = (im, -re) instead of z.  Columns [2N, Kp) are zero.
+// rows [rows][N] complex FP32 -> hi/lo families of `out_rows` rows and K = Kp columns
+// (K-blocked, fam_index) holding 2N interleaved (re, im) values.  rot = 1 writes
+// -i*z = (im, -re) instead of z.  Columns [2N, Kp) are zero.
 __global__ void k_split_rows(const float2* __restrict__ z, int rows, int64_t N, int64_t Kp,
-                             int row_off, int rot, __nv_bfloat16* __restrict__ hi,
+                             int row_off, int out_rows, int rot, __nv_bfloat16* __restrict__ hi,
                              __nv_bfloat16* __restrict__ lo) {
   const int64_t total = (int64_t)rows * (Kp / 2);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -394,7 +396,7 @@ __global__ void k_split_rows(const float2* __restrict__ z, int rows, int64_t N, 
     __nv_bfloat16 h0, l0, h1, l1;
     split_bf16(re, h0, l0);
     split_bf16(im, h1, l1);
-    const int64_t dst = (int64_t)(row_off + r) * Kp + 2 * o;
+    const int64_t dst = fam_index(row_off + r, 2 * o, out_rows);
     hi[dst] = h0;
     hi[dst + 1] = h1;
     lo[dst] = l0;
@@ -442,14 +444,15 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode(kite_ctx* ctx) {
   return fn;
 }
 
+// Tensor map of a K-blocked family [Kp/64][rows][64] (bf16): dims {64, rows, Kp/64}.
 int make_map(kite_ctx* ctx, CUtensorMap* m, const void* ptr, int64_t Kp, int rows, int box_rows) {
   auto enc = get_encode(ctx);
   if (!enc) return fail(ctx, KITE_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
-  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
+  cuuint64_t dims[3] = {(cuuint64_t)kBK, (cuuint64_t)rows, (cuuint64_t)(Kp / kBK)};
+  cuuint64_t strides[2] = {(cuuint64_t)kBK * 2, (cuuint64_t)rows * kBK * 2};
+  cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
@@ -550,9 +553,11 @@ int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, in
   double* part = w.take<double>(part_n);
   const int blocks = ctx->num_sms * 8;
   // A' = conj-free interleave of a (the conjugation lives in the choice of B rows)
-  k_split_rows<<<blocks, 256, 0, ctx->stream>>>(reinterpret_cast<const float2*>(A), M, N, Kp, 0, 0, Ahi, Alo);
-  k_split_rows<<<blocks, 256, 0, ctx->stream>>>(reinterpret_cast<const float2*>(B), M2, N, Kp, 0, 0, Bhi, Blo);
-  k_split_rows<<<blocks, 256, 0, ctx->stream>>>(reinterpret_cast<const float2*>(B), M2, N, Kp, M2, 1, Bhi, Blo);
+  k_split_rows<<<blocks, 256, 0, ctx->stream>>>(reinterpret_cast<const float2*>(A), M, N, Kp, 0, M, 0, Ahi, Alo);
+  k_split_rows<<<blocks, 256, 0, ctx->stream>>>(reinterpret_cast<const float2*>(B), M2, N, Kp, 0, Nrows, 0, Bhi,
+                                                Blo);
+  k_split_rows<<<blocks, 256, 0, ctx->stream>>>(reinterpret_cast<const float2*>(B), M2, N, Kp, M2, Nrows, 1, Bhi,
+                                                Blo);
   KITE_CUDA_TRY(ctx, cudaGetLastError());
   KITE_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
   int S_used = 0;

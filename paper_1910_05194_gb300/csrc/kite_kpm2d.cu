@@ -123,13 +123,14 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
   Carver w(ctx->ws);
   layout(w, &vt, &r0, &bA, &bB, Ah, Al, Bh, Bl, &part, &ne);
   cudaStream_t st = ctx->stream;
-  if (Kp > 2 * N) {  // zero the K padding of every family row once
+  if (Kp > 2 * N) {  // zero the K padding (the tail of the last K block of every row) once
+    const int64_t k0 = 2 * N;  // first padded column; Kp - k0 < 64, all in the last block
+    const size_t width = (size_t)(Kp - k0) * 2;
     for (int v = 0; v < VB; ++v) {
-      const size_t pitch = (size_t)Kp * 2, width = (size_t)(Kp - 2 * N) * 2;
-      KITE_CUDA_TRY(ctx, cudaMemset2DAsync(Ah[v] + 2 * N, pitch, 0, width, M, st));
-      KITE_CUDA_TRY(ctx, cudaMemset2DAsync(Al[v] + 2 * N, pitch, 0, width, M, st));
-      KITE_CUDA_TRY(ctx, cudaMemset2DAsync(Bh[v] + 2 * N, pitch, 0, width, 2 * M, st));
-      KITE_CUDA_TRY(ctx, cudaMemset2DAsync(Bl[v] + 2 * N, pitch, 0, width, 2 * M, st));
+      KITE_CUDA_TRY(ctx, cudaMemset2DAsync(Ah[v] + fam_index(0, k0, M), 128, 0, width, M, st));
+      KITE_CUDA_TRY(ctx, cudaMemset2DAsync(Al[v] + fam_index(0, k0, M), 128, 0, width, M, st));
+      KITE_CUDA_TRY(ctx, cudaMemset2DAsync(Bh[v] + fam_index(0, k0, 2 * M), 128, 0, width, 2 * M, st));
+      KITE_CUDA_TRY(ctx, cudaMemset2DAsync(Bl[v] + fam_index(0, k0, 2 * M), 128, 0, width, 2 * M, st));
     }
   }
   KITE_CUDA_TRY(ctx, cudaMemsetAsync(mu_nm_dev, 0, sizeof(double) * 2 * (size_t)M * M, st));
@@ -160,6 +161,8 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
     fb.lo[v] = Bl[v];
   }
   fa.Kp = fb.Kp = Kp;
+  fa.rows = M;
+  fb.rows = 2 * M;
   fa.M = fb.M = M;
   fa.dir = alpha;
   fb.dir = beta;

@@ -133,7 +133,7 @@ struct StepShape {
 
 // Vector-family outputs of a step (2D moments, Sec. 2b): per vector of the batch, rows of
 // Kp bf16 values (hi = bf16(x), lo = bf16(x - hi)) holding interleaved (re, im) per
-// orbital.  MODE 1 writes the step's output r_{n+1} as row `col` of the A family;
+// orbital, stored K-blocked (fam_index).  MODE 1 writes the step's output r_{n+1} as row `col` of the A family;
 // MODE 2 writes h~x r_n, built from the neighbours already staged for the step, as
 // rows `col` (b) and `col + M` (-i b) of the extended B family.  MODE 3 (moment doubling)
 // accumulates <r_n|r_{n+1}> and <r_n|r_n> instead of <r_0|r_{n+1}>; r_0 is not staged.
@@ -142,6 +142,7 @@ struct FamOut {
   __nv_bfloat16* hi[kMaxFamVecs];
   __nv_bfloat16* lo[kMaxFamVecs];
   int64_t Kp;
+  int rows;    // rows of the family array (M for A, 2M for the extended B)
   int col;
   int M;
   int dir;     // velocity direction of MODE 2: 0 = x, 1 = y
@@ -154,7 +155,7 @@ __device__ __forceinline__ void fam_store(const FamOut& f, int v, int row, int64
   const __nv_bfloat16 h0 = __float2bfloat16_rn(re), h1 = __float2bfloat16_rn(im);
   const __nv_bfloat16 l0 = __float2bfloat16_rn(re - __bfloat162float(h0));
   const __nv_bfloat16 l1 = __float2bfloat16_rn(im - __bfloat162float(h1));
-  const int64_t idx = (int64_t)row * f.Kp + 2 * o;
+  const int64_t idx = fam_index(row, 2 * o, f.rows);
   *reinterpret_cast<__nv_bfloat162*>(f.hi[v] + idx) = __halves2bfloat162(h0, h1);
   *reinterpret_cast<__nv_bfloat162*>(f.lo[v] + idx) = __halves2bfloat162(l0, l1);
 }
