@@ -208,9 +208,10 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
   const int R = kpm[0].R;
   auto steps_of = [](int M) { return DBL ? (M + 1) / 2 : std::max(M - 1, 1); };
   // persistent grid: every CTA resident
-  cudaFuncSetAttribute(k_batched<LAT, C, DBL>, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+  constexpr int SMEM = Sh::template smem_bytes<DBL ? 3 : 0>();  // doubling stages no r_0
+  cudaFuncSetAttribute(k_batched<LAT, C, DBL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<LAT, C, DBL>, kBlock, Sh::SMEM) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<LAT, C, DBL>, kBlock, SMEM) !=
           cudaSuccess || occ < 1)
     return fail(ctx, KITE_ERR_CUDA, "occupancy query for the batched kernel failed");
   const int gmax = ctx->num_sms * occ;
@@ -326,7 +327,7 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(sc.grid);
     cfg.blockDim = dim3(kBlock);
-    cfg.dynamicSmemBytes = Sh::SMEM;
+    cfg.dynamicSmemBytes = SMEM;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

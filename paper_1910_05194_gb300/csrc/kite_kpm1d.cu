@@ -97,16 +97,17 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
   KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
   constexpr int SM = StepShape<LAT, C>::SMEM;
   if (p.doubling) {
+    constexpr int SMD = StepShape<LAT, C>::SMEM_NR0;
     // step 0: r_1 = H~ r_0 with <r_0|r_0> -> slot 0 and <r_0|r_1> -> slot 1; step n >= 1
     // (r_{n+1} from r_n, r_{n-1}): <r_n|r_n> -> slot 2n, <r_n|r_{n+1}> -> slot 2n+1
     const int steps = steps_for(p);
-    k_step<Real, LAT, C, true, 3><<<G, kBlock, SM, st>>>(nullptr, r0, bA, nullptr, vt, tt, p.Lx,
+    k_step<Real, LAT, C, true, 3><<<G, kBlock, SMD, st>>>(nullptr, r0, bA, nullptr, vt, tt, p.Lx,
                                                          p.Ly, units, partial + (size_t)G * Q,
                                                          partial, ctx->d_status,
                                                          ctx->debug_stall, FamOut{});
     ctx->debug_stall = 0;
     for (int n = 1; n < steps; ++n)
-      k_step<Real, LAT, C, false, 3><<<G, kBlock, SM, st>>>(
+      k_step<Real, LAT, C, false, 3><<<G, kBlock, SMD, st>>>(
           where(n - 1), where(n), where(n + 1), nullptr, vt, tt, p.Lx, p.Ly, units,
           partial + (size_t)(2 * n + 1) * G * Q, partial + (size_t)(2 * n) * G * Q, ctx->d_status,
           0, FamOut{});
@@ -159,11 +160,11 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
   return KITE_OK;
 }
 
-template <typename Real, int LAT>
+template <typename Real, int LAT, int MODE>
 int grid_for_c(kite_ctx* ctx, int C, long long units) {
-  if (C == 1) return grid_for<Real, LAT, 1, false>(ctx, units);
-  if (C == 2) return grid_for<Real, LAT, 2, false>(ctx, units);
-  return grid_for<Real, LAT, 4, false>(ctx, units);
+  if (C == 1) return grid_for<Real, LAT, 1, false, MODE>(ctx, units);
+  if (C == 2) return grid_for<Real, LAT, 2, false, MODE>(ctx, units);
+  return grid_for<Real, LAT, 4, false, MODE>(ctx, units);
 }
 
 template <typename Real, int LAT>
@@ -194,8 +195,10 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
   };
   const int Cmax = chunks_for(std::min(p.R, p.max_batch));
   const int Ctail = chunks_for(p.R % p.max_batch == 0 ? std::min(p.R, p.max_batch) : p.R % p.max_batch);
-  const int Gmax = std::max(grid_for_c<Real, LAT>(ctx, Cmax, units_for(Cmax)),
-                            grid_for_c<Real, LAT>(ctx, Ctail, units_for(Ctail)));
+  auto grid_c = [&](int C) {
+    return p.doubling ? grid_for_c<Real, LAT, 3>(ctx, C, units_for(C)) : grid_for_c<Real, LAT, 0>(ctx, C, units_for(C));
+  };
+  const int Gmax = std::max(grid_c(Cmax), grid_c(Ctail));
 
   // work space
   const size_t vec_bytes = (size_t)p.ncell * SORB * Cmax * 16;
@@ -265,7 +268,8 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
       const int vec_base = s * p.R + base;
 #define KITE_SWEEP(CC)                                                                       \
   do {                                                                                       \
-    const int G = grid_for<Real, LAT, CC, false>(ctx, u);                                    \
+    const int G = p.doubling ? grid_for<Real, LAT, CC, false, 3>(ctx, u)                     \
+                             : grid_for<Real, LAT, CC, false>(ctx, u);                        \
     grid_used = G;                                                                           \
     rc = sweep_batch<Real, LAT, CC>(ctx, p, vt, tt, r0, bA, bB, partial, G, u, nvec,         \
                                     vec_base, ne, mu_vec, &lp, &lc, &step_s, &step_n);       \

@@ -87,7 +87,7 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
   const int64_t ncell = (int64_t)sys->Lx * sys->Ly, N = ncell * SORB;
   const int64_t Kp = ((2 * N + 63) / 64) * 64;
   const int VB = 2;
-  const int G = grid_for<float, LAT, C, false>(ctx, (long long)((sys->Lx + Sh::TX - 1) / Sh::TX) * sys->Ly);
+  const int G = grid_for<float, LAT, C, false, 1>(ctx, (long long)((sys->Lx + Sh::TX - 1) / Sh::TX) * sys->Ly);
   const long long units = (long long)((sys->Lx + Sh::TX - 1) / Sh::TX) * sys->Ly;
   const int Sg = plan_gemm_splits(ctx, M, 2 * M, Kp);
   const size_t vec_bytes = (size_t)ncell * SORB * C * 16;
@@ -147,7 +147,7 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
       sys->p_vac <= 0.0 ? 0ull : (thr_d >= 4294967296.0 ? 4294967296ull : (uint64_t)thr_d);
   const uint32_t k0 = (uint32_t)sys->seed, k1 = (uint32_t)(sys->seed >> 32);
   const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->num_sms * 16);
-  constexpr int SM = Sh::SMEM;
+  constexpr int SM = Sh::SMEM_NR0;  // the family modes never stage r_0
   cudaFuncSetAttribute(k_step<float, LAT, C, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
   cudaFuncSetAttribute(k_step<float, LAT, C, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
   cudaFuncSetAttribute(k_step<float, LAT, C, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);

@@ -129,6 +129,14 @@ struct StepShape {
   static constexpr int CURB = (TX + 2) * CELLB;     // r_n row segment with halo cells
   static constexpr int STAGEB = CURB + 2 * ROWB;    // + r_{n-1} and r_0
   static constexpr int SMEM = kBarBytes + kStages * STAGEB;
+  // modes that never stage r_0 (families, moment doubling) use shorter stages: a third
+  // CTA fits on each SM
+  static constexpr int STAGEB_NR0 = CURB + ROWB;
+  static constexpr int SMEM_NR0 = kBarBytes + kStages * STAGEB_NR0;
+  template <int MODE>
+  static constexpr int stage_bytes() { return MODE == 0 ? STAGEB : STAGEB_NR0; }
+  template <int MODE>
+  static constexpr int smem_bytes() { return MODE == 0 ? SMEM : SMEM_NR0; }
 };
 
 // Vector-family outputs of a step (2D moments, Sec. 2b): per vector of the batch, rows of
@@ -225,6 +233,7 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
   using Sh = StepShape<LAT, C>;
   constexpr int VPC = Ch::kVecs, NR = Ch::kReals;
   constexpr int SORB = Sh::SORB, TPC = Sh::TPC, TX = Sh::TX, CELLB = Sh::CELLB;
+  constexpr int STG = Sh::template stage_bytes<MODE>();
   constexpr int QT = 2 * VPC;  // (re, im) per vector held by one thread
   uint64_t* bars = ring.bars;
   unsigned char* stages = ring.stages;
@@ -265,7 +274,7 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
     auto issue = [&](int jj) {  // producer: thread 0 only
       const long long g = gslot + jj;
       const int st = (int)(g % kStages);
-      unsigned char* base = stages + st * Sh::STAGEB;
+      unsigned char* base = stages + st * STG;
       int row = yb - 1 + jj;
       row = row < 0 ? row + Ly : (row >= Ly ? row - Ly : row);
       const bool interior = !FIRST && jj >= 1 && jj <= nr;
@@ -303,9 +312,9 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
       const Real v = vnext;
       if (active && i + 1 < nr) vnext = vt[((size_t)(y + 1) * Lx + x0 + xl) * SORB + s];
       if (ok && active) {
-        const unsigned char* up = stages + (int)((gslot + i) % kStages) * Sh::STAGEB;
-        const unsigned char* mid = stages + (int)((gslot + i + 1) % kStages) * Sh::STAGEB;
-        const unsigned char* dn = stages + (int)((gslot + i + 2) % kStages) * Sh::STAGEB;
+        const unsigned char* up = stages + (int)((gslot + i) % kStages) * STG;
+        const unsigned char* mid = stages + (int)((gslot + i + 1) % kStages) * STG;
+        const unsigned char* dn = stages + (int)((gslot + i + 2) % kStages) * STG;
         const Ch me = *reinterpret_cast<const Ch*>(mid + (xl + 1) * CELLB + choff);
         Ch n1, n2, n3, n4;
         if (LAT == KITE_HONEYCOMB) {
@@ -487,17 +496,17 @@ __global__ void k_extract(int64_t ncell, const void* __restrict__ buf, int nvec,
 }
 
 
-template <typename Real, int LAT, int C, bool FIRST>
+// Persistent grid of the step kernel of a mode: resident CTAs per SM x SMs, at most one
+// CTA per unit.  Also sets the kernels' dynamic shared-memory limit.
+template <typename Real, int LAT, int C, bool FIRST, int MODE = 0>
 int grid_for(kite_ctx* ctx, long long units) {
   static int occ = -1;  // per template instance; device-independent enough for one GPU type
   if (occ < 0) {
     int o = 0;
-    const int smem = StepShape<LAT, C>::SMEM;
-    cudaFuncSetAttribute(k_step<Real, LAT, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_step<Real, LAT, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_step<Real, LAT, C, true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_step<Real, LAT, C, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_step<Real, LAT, C, FIRST>, kBlock, smem) !=
+    const int smem = StepShape<LAT, C>::template smem_bytes<MODE>();
+    cudaFuncSetAttribute(k_step<Real, LAT, C, true, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_step<Real, LAT, C, false, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_step<Real, LAT, C, FIRST, MODE>, kBlock, smem) !=
             cudaSuccess ||
         o < 1)
       o = 1;
