@@ -100,7 +100,15 @@ typedef struct {
  *              (T_{2n+1} + T_1)/2 for the Hermitian H~ give mu_2n = 2<r_n|r_n> - mu_0 and
  *              mu_{2n+1} = 2<r_{n+1}|r_n> - mu_1, so ceil(M/2) steps yield M moments and
  *              r_0 is never re-read (identical in exact arithmetic, not bit for bit).
- *   reserved   must be 0 */
+ *   real_vectors  0: complex unit-modulus random phases exp(2 pi i u) (default).
+ *              1: real random signs +-1 (the sign from the same draw, u < 1/2 -> +1) --
+ *              the paper allows real or complex white noise (Sec. 2c); for the real
+ *              Hamiltonians here both are unbiased.  A real vector takes half the bytes
+ *              of a complex one (a batch holds 16 FP32 or 8 FP64 of them) and its trace
+ *              estimate has twice the variance of a unit-phase vector (2 sum_{i!=j} A_ij^2
+ *              against sum_{i!=j} |A_ij|^2), so the cost per unit of accuracy is the same
+ *              at half the memory.  kite_moments_1d only; r_last must be NULL; caller
+ *              start vectors (r0) contribute their real parts. */
 typedef struct {
   int32_t M;
   int32_t R;
@@ -111,7 +119,7 @@ typedef struct {
   const double* r0;
   void* r_last;
   int32_t doubling;
-  int32_t reserved;
+  int32_t real_vectors;
 } kite_kpm;
 
 /* Per-call statistics (all optional outputs). */
@@ -174,6 +182,40 @@ int kite_bounds(const kite_system* sys, double* e_min, double* e_max);
  * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA, KITE_ERR_BOUNDS. */
 int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, double* mu,
                     double* mu_per_vec, kite_stats* st);
+
+/* Chebyshev moments of the k-resolved spectral function (the paper's spectral-function
+ * section, the quantity behind ARPES): the recursion starts from the plane wave
+ *   |k> = sum_alpha w_alpha sum_i exp(i k.R_i^alpha) |i, alpha>
+ * (zero on vacant orbitals) instead of a random vector, and
+ *   mu_n(k) = <k| T_n(H~) |k> / N_eff,
+ * averaged over kpm->S disorder realisations, so that rho_k(E) follows from
+ * kite_reconstruct_dos applied to the real parts.  Orbital positions R_i^alpha in units of
+ * the lattice constant: honeycomb cell (x, y) at x a1 + y a2, a1 = (1, 0),
+ * a2 = (1/2, sqrt(3)/2), A at (0, -a_cc/2), B at (0, +a_cc/2), a_cc = 1/sqrt(3) (the
+ * paper's lattice set-up); square (x, y).  With random orbital weights averaged
+ * (<w_a* w_b> = delta_ab) the clean-lattice result is the band structure with equal
+ * weights; fixed weights give the intensities of those weights.
+ *   kpm      M, precision, bounds (e_min = e_max = 0: Gershgorin), S realisations; R must
+ *            be 1 (one start vector per k-point); r0, r_last NULL; doubling allowed
+ *   k        [nk][2] (kx, ky) in 1/a, host or device
+ *   weights  [orbitals per cell][2] complex w_alpha, host or device; NULL = all 1
+ *   mu       [nk][M] complex FP64 interleaved, host or device
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA, KITE_ERR_BOUNDS, KITE_ERR_TIMEOUT. */
+int kite_spectral_k(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const double* k,
+                    int nk, const double* weights, double* mu, kite_stats* st);
+
+/* Chebyshev moments of the local density of states (the paper's LDOS section):
+ *   mu_n(i) = <i| T_n(H~) |i>  for the orbitals i = orbitals[j],
+ * one disorder realisation (kpm->S = 1), the recursion started from the orbital's basis
+ * vector on the whole lattice (a sweep batch holds 8 FP32 or 4 FP64 orbitals); rho_i(E)
+ * follows from kite_reconstruct_dos on the real parts.  mu_0 = 1 (0 for a vacant orbital).
+ * Orbital index = (y Lx + x) * orbitals per cell + sublattice.
+ *   kpm       M, precision, bounds, R = 1, S = 1, r0 and r_last NULL, doubling allowed
+ *   orbitals  [n] int64, host or device
+ *   mu        [n][M] complex FP64 interleaved, host or device
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA, KITE_ERR_BOUNDS, KITE_ERR_TIMEOUT. */
+int kite_ldos(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const int64_t* orbitals,
+              int n, double* mu, kite_stats* st);
 
 /* Test hook for failure detection (no counterpart in the paper).  When `enable` is
  * non-zero, the first recursion step of the next kite_moments_1d call on this context

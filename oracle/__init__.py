@@ -81,6 +81,7 @@ def lib():
             L.orc_bounds_auto.argtypes = [P(System), P(d), P(d)]
             L.orc_disorder.argtypes = [P(System), i32, vp, vp]
             L.orc_random_phase.argtypes = [P(System), i32, i32, vp, vp]
+            L.orc_random_real.argtypes = [P(System), i32, i32, vp, vp]
             L.orc_moments_1d.argtypes = [P(System), i32, i32, i32, d, d, vp, vp, i32]
             L.orc_moments_1d.restype = i32
             L.orc_replica_1d.argtypes = [P(System), i32, i32, i32, d, d, i32, vp, vp, vp, i32]
@@ -143,6 +144,42 @@ def random_phase(sys: System, R: int, realisation: int = 0):
     out = np.empty((R, n, 2), np.float64)
     lib().orc_random_phase(ctypes.byref(sys), int(realisation), int(R), _ptr(vac), _ptr(out))
     return out[..., 0] + 1j * out[..., 1]
+
+
+def random_real(sys: System, R: int, realisation: int = 0):
+    """Real random-sign start vectors [R][N] (+-1, zero on vacancies) as complex128."""
+    _, vac = disorder(sys, realisation)
+    n = norb(sys)
+    out = np.empty((R, n, 2), np.float64)
+    lib().orc_random_real(ctypes.byref(sys), int(realisation), int(R), _ptr(vac), _ptr(out))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def orbital_positions(sys: System):
+    """Positions (x, y) of every orbital in units of the lattice constant: honeycomb cell
+    (x, y) at x a1 + y a2 with a1 = (1, 0), a2 = (1/2, sqrt(3)/2), A at (0, -a_cc/2) and B
+    at (0, +a_cc/2), a_cc = 1/sqrt(3) (the paper's lattice set-up listing); square (x, y)."""
+    n = norb(sys)
+    o = np.arange(n)
+    if sys.lattice == HONEYCOMB:
+        cell, s = o // 2, o % 2
+        x, y = cell % sys.Lx, cell // sys.Lx
+        acc = 1.0 / np.sqrt(3.0)
+        return np.stack([x + 0.5 * y, np.sqrt(3.0) / 2.0 * y + np.where(s == 0, -0.5, 0.5) * acc], -1)
+    return np.stack([o % sys.Lx, o // sys.Lx], -1).astype(np.float64)
+
+
+def bloch_vector(sys: System, k, weights, realisation: int = 0):
+    """|k> = sum_alpha w_alpha sum_i exp(i k.R_i^alpha) |i, alpha> (Sec. "Spectral
+    functions"), zero on vacant orbitals; k = (kx, ky) in 1/a, weights[alpha] complex."""
+    R = orbital_positions(sys)
+    _, vac = disorder(sys, realisation)
+    n = norb(sys)
+    sorb = 2 if sys.lattice == HONEYCOMB else 1
+    w = np.asarray(weights, np.complex128)[np.arange(n) % sorb]
+    v = w * np.exp(1j * (R @ np.asarray(k, np.float64)))
+    v[vac != 0] = 0.0
+    return v
 
 
 def _as_r0(r0, R, n):

@@ -197,6 +197,28 @@ void orc_random_phase(const orc_system* sys, int realisation, int R, const uint8
   }
 }
 
+/* Real white-noise start vectors (Sec. 2c allows real or complex variables): the sign
+ * +-1 of the same draw as the phase, +1 when u < 1/2; 0 on vacant orbitals.  Written as
+ * complex values with zero imaginary part, [R][N]. */
+void orc_random_real(const orc_system* sys, int realisation, int R, const uint8_t* vac,
+                     double* r0) {
+  int64_t N = orc_norb(sys);
+  for (int r = 0; r < R; ++r) {
+    for (int64_t o = 0; o < N; ++o) {
+      double* z = r0 + 2 * ((int64_t)r * N + o);
+      z[1] = 0.0;
+      if (vac[o]) {
+        z[0] = 0.0;
+        continue;
+      }
+      uint32_t x[4];
+      uint32_t w2 = (uint32_t)realisation * (uint32_t)R + (uint32_t)r;
+      orc_draw(sys, (uint64_t)o, w2, ORC_TAG_PHASE, x);
+      z[0] = orc_u53(x) < 0.5 ? 1.0 : -1.0;
+    }
+  }
+}
+
 /* ------------------------------------------------------------------------------ */
 /* 1D moments: the plain FP64 definition.                                            */
 /*   H~ = (H - de_plus)/de_minus                         (Eq. rescalingH)            */

@@ -43,6 +43,8 @@ void orc_bounds_auto(const orc_system* sys, double* e_min, double* e_max);
 void orc_disorder(const orc_system* sys, int realisation, double* V, uint8_t* vac);
 void orc_random_phase(const orc_system* sys, int realisation, int R, const uint8_t* vac,
                       double* r0);
+void orc_random_real(const orc_system* sys, int realisation, int R, const uint8_t* vac,
+                     double* r0);
 
 int orc_moments_1d(const orc_system* sys, int realisation, int M, int R, double e_min,
                    double e_max, const double* r0_in, double* mu_per_vec, int threads);

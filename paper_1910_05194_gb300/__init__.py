@@ -28,7 +28,7 @@ EXPORTED = ("kite_create", "kite_destroy", "kite_set_stream", "kite_status_strin
             "kite_debug_stall_once", "kite_inner_products", "kite_moments_2d", "kite_reconstruct_green",
             "kite_reconstruct_sigma", "kite_moments_1d_static", "kite_moments_1d_batched",
             "kite_mlp_param_count", "kite_mlp_train", "kite_mlp_forward", "kite_mlp_gradient",
-            "kite_learned_gate")
+            "kite_learned_gate", "kite_spectral_k", "kite_ldos")
 MLP_IN, MLP_HIDDEN, MLP_OUT = 128, 512, 1024
 
 
@@ -50,7 +50,7 @@ class KPM(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int32), ("R", ctypes.c_int32), ("S", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("e_min", ctypes.c_double),
                 ("e_max", ctypes.c_double), ("r0", ctypes.c_void_p), ("r_last", ctypes.c_void_p),
-                ("doubling", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("doubling", ctypes.c_int32), ("real_vectors", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -88,9 +88,9 @@ def make_system(lattice=HONEYCOMB, Lx=64, Ly=64, t=-2.7, W=0.0, delta=0.0, p_vac
 
 
 def make_kpm(M, R=1, S=1, precision=FP32, e_min=0.0, e_max=0.0, r0=None, r_last=None,
-             doubling=False):
+             doubling=False, real_vectors=False):
     return KPM(int(M), int(R), int(S), int(precision), float(e_min), float(e_max),
-               _addr(r0), _addr(r_last), int(bool(doubling)), 0)
+               _addr(r0), _addr(r_last), int(bool(doubling)), int(bool(real_vectors)))
 
 
 _LOCK = threading.Lock()
@@ -145,6 +145,10 @@ def lib():
             L.kite_moments_2d.restype = i32
             L.kite_reconstruct_green.argtypes = [vp, vp, i32, i32, i32, d, d, d, d, vp, i32, vp, vp]
             L.kite_reconstruct_green.restype = i32
+            L.kite_spectral_k.argtypes = [vp, P(System), P(KPM), vp, i32, vp, vp, P(Stats)]
+            L.kite_spectral_k.restype = i32
+            L.kite_ldos.argtypes = [vp, P(System), P(KPM), vp, i32, vp, P(Stats)]
+            L.kite_ldos.restype = i32
             L.kite_inner_products.argtypes = [vp, vp, vp, i32, i32, ctypes.c_int64, d, vp, i32, i32, i32]
             L.kite_inner_products.restype = i32
             L.kite_debug_stall_once.argtypes = [vp, i32]
@@ -253,6 +257,23 @@ def reconstruct_green(ctx: Context, mu, M_avail: int, M_use: int, kernel: int, p
     ctx.check(lib().kite_reconstruct_green(ctx.handle, _addr(mu), int(M_avail), int(M_use), int(kernel),
                                            float(param), float(e_min), float(e_max), float(eta), _addr(E),
                                            int(K), _addr(G), _addr(rho)))
+
+
+def spectral_k(ctx: Context, system: System, kpm: KPM, k, nk: int, mu, weights=None) -> Stats:
+    """kite_spectral_k: mu[nk][M] complex FP64 moments of the plane-wave start vectors at the
+    k-points k[nk][2] (1/a), optional complex orbital weights[SORB] (interleaved)."""
+    st = Stats()
+    ctx.check(lib().kite_spectral_k(ctx.handle, ctypes.byref(system), ctypes.byref(kpm), _addr(k), int(nk),
+                                    _addr(weights), _addr(mu), ctypes.byref(st)))
+    return st
+
+
+def ldos(ctx: Context, system: System, kpm: KPM, orbitals, n: int, mu) -> Stats:
+    """kite_ldos: mu[n][M] complex FP64 moments <i|T_n|i> of the orbitals (int64 [n])."""
+    st = Stats()
+    ctx.check(lib().kite_ldos(ctx.handle, ctypes.byref(system), ctypes.byref(kpm), _addr(orbitals), int(n),
+                              _addr(mu), ctypes.byref(st)))
+    return st
 
 
 def inner_products(ctx: Context, A, B, M: int, M2: int, N: int, scale: float, C, sub_k: int = 0,

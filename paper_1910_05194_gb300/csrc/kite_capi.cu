@@ -34,6 +34,10 @@ int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, in
 int reconstruct_sigma_impl(kite_ctx* ctx, const double* mu_dev, int M_avail, int M, int lattice,
                            int kernel, const Scale& sc, double E_F, double kT, double eta,
                            const double* omega_host, int K_w, int n_quad, double* sigma_dev);
+int spectral_k_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
+                    const double* k, int nk, const double* w, double* out, kite_stats* st);
+int ldos_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
+              const int64_t* orb, int n, double* out, kite_stats* st);
 int reconstruct_green_impl(kite_ctx* ctx, const double* mu_dev, int M_use, int kernel, double param,
                            const Scale& sc, double eta, const double* E_dev, int K, double* G_dev,
                            double* rho_dev, double* coef_dev);
@@ -317,8 +321,10 @@ int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   if (kpm->precision != KITE_FP32 && kpm->precision != KITE_FP64)
     return fail(ctx, KITE_ERR_ARG, "precision must be KITE_FP32 or KITE_FP64");
   if ((double)kpm->R * kpm->S > 65536.0) return fail(ctx, KITE_ERR_ARG, "R*S > 65536");
-  if ((kpm->doubling != 0 && kpm->doubling != 1) || kpm->reserved != 0)
-    return fail(ctx, KITE_ERR_ARG, "doubling must be 0 or 1 and reserved 0");
+  if ((kpm->doubling != 0 && kpm->doubling != 1) || (kpm->real_vectors != 0 && kpm->real_vectors != 1))
+    return fail(ctx, KITE_ERR_ARG, "doubling and real_vectors must be 0 or 1");
+  if (kpm->real_vectors && kpm->r_last)
+    return fail(ctx, KITE_ERR_ARG, "r_last is not available with real vectors");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
   Scale sc;
   rc = resolve_bounds(ctx, sys, kpm->e_min, kpm->e_max, &sc);
@@ -470,6 +476,104 @@ int kite_learned_gate(kite_ctx* ctx, const float* rho, const double* mu, int mu_
   return rc;
 }
 
+int kite_spectral_k(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const double* k, int nk,
+                    const double* weights, double* mu, kite_stats* st) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  int rc = validate_system(ctx, sys);
+  if (rc != KITE_OK) return rc;
+  if (!kpm || !k || !mu || nk < 1) return fail(ctx, KITE_ERR_ARG, "kpm, k, mu and nk >= 1 are required");
+  if (kpm->M < 1 || kpm->S < 1 || kpm->R != 1 || kpm->S > 4096)
+    return fail(ctx, KITE_ERR_ARG, "need M >= 1, R = 1 (one start vector per k) and 1 <= S <= 4096");
+  if (kpm->precision != KITE_FP32 && kpm->precision != KITE_FP64)
+    return fail(ctx, KITE_ERR_ARG, "precision must be KITE_FP32 or KITE_FP64");
+  if (kpm->r0 || kpm->r_last || kpm->real_vectors != 0 || (kpm->doubling != 0 && kpm->doubling != 1))
+    return fail(ctx, KITE_ERR_ARG, "no r0/r_last, complex vectors, doubling 0 or 1");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  Scale sc;
+  rc = resolve_bounds(ctx, sys, kpm->e_min, kpm->e_max, &sc);
+  if (rc != KITE_OK) return rc;
+  const int M = kpm->M;
+  const int sorb = sys->lattice == KITE_HONEYCOMB ? 2 : 1;
+  Staging sg{ctx, {}};
+  const double *kd, *wd;
+  double* md;
+  rc = sg.in(k, 2 * (size_t)nk, &kd);
+  if (rc == KITE_OK) rc = sg.in(weights, 2 * (size_t)sorb, &wd);
+  if (rc == KITE_OK) rc = sg.out(mu, 2 * (size_t)nk * M, &md);
+  kite_stats local{};
+  if (rc == KITE_OK) rc = spectral_k_impl(ctx, sys, kpm, sc, kd, nk, wd, md, &local);
+  if (rc == KITE_OK) rc = sg.back(mu, md, 2 * (size_t)nk * M);
+  cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "spectral_k");
+  if (rc == KITE_OK) {
+    // growth check: |mu_n(k)| <= mu_0(k) when the spectrum is inside [-1, 1]
+    std::vector<double> h(2 * (size_t)nk * M);
+    if (cudaMemcpy(h.data(), md, sizeof(double) * h.size(), cudaMemcpyDefault) == cudaSuccess) {
+      for (int j = 0; j < nk && rc == KITE_OK; ++j) {
+        const double m0 = h[2 * (size_t)j * M];
+        for (int n = 0; n < M; ++n) {
+          const double re = h[2 * ((size_t)j * M + n)], im = h[2 * ((size_t)j * M + n) + 1];
+          if (!isfinite(re) || !isfinite(im) || hypot(re, im) > fabs(m0) * (1.0 + 1e-3) + 1e-12) {
+            rc = fail(ctx, KITE_ERR_BOUNDS, "a spectral moment exceeds mu_0(k): the spectrum is not inside the bounds");
+            break;
+          }
+        }
+      }
+    }
+  }
+  if (st) *st = local;
+  return rc;
+}
+
+int kite_ldos(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const int64_t* orbitals, int n,
+              double* mu, kite_stats* st) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  int rc = validate_system(ctx, sys);
+  if (rc != KITE_OK) return rc;
+  if (!kpm || !orbitals || !mu || n < 1) return fail(ctx, KITE_ERR_ARG, "kpm, orbitals, mu and n >= 1 are required");
+  if (kpm->M < 1 || kpm->S != 1 || kpm->R != 1)
+    return fail(ctx, KITE_ERR_ARG, "need M >= 1, R = 1 (one start vector per orbital) and S = 1");
+  if (kpm->precision != KITE_FP32 && kpm->precision != KITE_FP64)
+    return fail(ctx, KITE_ERR_ARG, "precision must be KITE_FP32 or KITE_FP64");
+  if (kpm->r0 || kpm->r_last || kpm->real_vectors != 0 || (kpm->doubling != 0 && kpm->doubling != 1))
+    return fail(ctx, KITE_ERR_ARG, "no r0/r_last, complex vectors, doubling 0 or 1");
+  const int64_t N = (int64_t)sys->Lx * sys->Ly * (sys->lattice == KITE_HONEYCOMB ? 2 : 1);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  Scale sc;
+  rc = resolve_bounds(ctx, sys, kpm->e_min, kpm->e_max, &sc);
+  if (rc != KITE_OK) return rc;
+  Staging sg{ctx, {}};
+  const int64_t* od;
+  double* md;
+  rc = sg.in(orbitals, (size_t)n, &od);
+  if (rc == KITE_OK) {  // range check on the host copy
+    std::vector<int64_t> h((size_t)n);
+    if (cudaMemcpy(h.data(), od, sizeof(int64_t) * n, cudaMemcpyDefault) != cudaSuccess)
+      return fail(ctx, KITE_ERR_CUDA, "reading orbitals");
+    for (int64_t o : h)
+      if (o < 0 || o >= N) return fail(ctx, KITE_ERR_ARG, "orbital index out of range");
+  }
+  if (rc == KITE_OK) rc = sg.out(mu, 2 * (size_t)n * kpm->M, &md);
+  kite_stats local{};
+  if (rc == KITE_OK) rc = ldos_impl(ctx, sys, kpm, sc, od, n, md, &local);
+  if (rc == KITE_OK) rc = sg.back(mu, md, 2 * (size_t)n * kpm->M);
+  cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "ldos");
+  if (rc == KITE_OK) {
+    std::vector<double> h(2 * (size_t)n * kpm->M);
+    if (cudaMemcpy(h.data(), md, sizeof(double) * h.size(), cudaMemcpyDefault) == cudaSuccess)
+      for (double x : h)
+        if (!isfinite(x) || fabs(x) > 1.0 + 1e-3) {
+          rc = fail(ctx, KITE_ERR_BOUNDS, "an LDOS moment exceeds 1: the spectrum is not inside the bounds");
+          break;
+        }
+  }
+  if (st) *st = local;
+  return rc;
+}
+
 int kite_moments_1d_batched(kite_ctx* ctx, int count, const kite_system* systems,
                             const kite_kpm* kpms, double* const* mu, kite_stats* st) {
   if (!ctx) return KITE_ERR_ARG;
@@ -486,8 +590,8 @@ int kite_moments_1d_batched(kite_ctx* ctx, int count, const kite_system* systems
     if (k.precision != KITE_FP32) return fail(ctx, KITE_ERR_UNSUPPORTED, "the batched sweep is FP32");
     if (k.R != kpms[0].R || k.R < 1 || k.R > 8)
       return fail(ctx, KITE_ERR_ARG, "all systems need the same R, 1 <= R <= 8");
-    if (k.S != 1 || k.r0 || k.r_last || k.reserved != 0)
-      return fail(ctx, KITE_ERR_ARG, "batched systems take S = 1, no r0/r_last, reserved = 0");
+    if (k.S != 1 || k.r0 || k.r_last || k.real_vectors != 0)
+      return fail(ctx, KITE_ERR_ARG, "batched systems take S = 1, no r0/r_last, complex vectors");
     if ((k.doubling != 0 && k.doubling != 1) || k.doubling != kpms[0].doubling)
       return fail(ctx, KITE_ERR_ARG, "all systems of a batch need the same doubling, 0 or 1");
     if (k.M < 1 || k.M > (1 << 20)) return fail(ctx, KITE_ERR_ARG, "M out of range");
@@ -513,8 +617,8 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   if (kpm->precision != KITE_FP32)
     return fail(ctx, KITE_ERR_UNSUPPORTED, "2D moments run the FP32 recursion only");
   if ((double)kpm->R * kpm->S > 65536.0) return fail(ctx, KITE_ERR_ARG, "R*S > 65536");
-  if (kpm->doubling != 0 || kpm->reserved != 0)
-    return fail(ctx, KITE_ERR_ARG, "the 2D moments take doubling = 0 and reserved = 0");
+  if (kpm->doubling != 0 || kpm->real_vectors != 0)
+    return fail(ctx, KITE_ERR_ARG, "the 2D moments take doubling = 0 and complex vectors");
   if ((alpha != KITE_DIR_X && alpha != KITE_DIR_Y) || (beta != KITE_DIR_X && beta != KITE_DIR_Y))
     return fail(ctx, KITE_ERR_ARG, "alpha and beta must be KITE_DIR_X or KITE_DIR_Y");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");

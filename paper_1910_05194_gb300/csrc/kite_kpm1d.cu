@@ -25,20 +25,23 @@ namespace kite {
 namespace {
 
 // Sums the per-CTA partials of every moment in fixed order and normalises by N_eff:
-// mu_vec[(vec_base+v)][n] (complex) for the valid lanes v < nvec.
+// mu_vec[(vec_base+v)][n] (complex) for the valid lanes v < nvec.  A lane is (vector,
+// re/im) for complex vectors and one real vector (imaginary part 0) for real ones.
 __global__ void k_reduce(const double* __restrict__ partial, int M, int G, int Q, int nvec,
                          int vec_base, const unsigned long long* __restrict__ n_eff,
-                         double* __restrict__ mu_vec) {
+                         double* __restrict__ mu_vec, int realv) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= M * Q) return;
   const int n = idx / Q, q = idx - (idx / Q) * Q;
-  const int v = q >> 1, comp = q & 1;
+  const int v = realv ? q : q >> 1, comp = realv ? 0 : q & 1;
   if (v >= nvec) return;
   double sum = 0.0;
   const double* p = partial + (size_t)n * G * Q + q;
   for (int g = 0; g < G; ++g) sum += p[(size_t)g * Q];
   const double ne = (double)*n_eff;
-  mu_vec[((size_t)(vec_base + v) * M + n) * 2 + comp] = ne > 0.0 ? sum / ne : 0.0;
+  double* out = mu_vec + ((size_t)(vec_base + v) * M + n) * 2;
+  out[comp] = ne > 0.0 ? sum / ne : 0.0;
+  if (realv) out[1] = 0.0;
 }
 
 // Moment doubling (T_n^2 = (T_2n + T_0)/2, T_{n+1} T_n = (T_{2n+1} + T_1)/2): slot k >= 2
@@ -75,6 +78,7 @@ struct Plan {
   int R, S, M;
   bool fp64;
   bool doubling;  // two moments per step from <r_n|r_n> and <r_n|r_{n+1}>
+  bool realv;     // real +-1 start vectors (four FP32 / two FP64 per chunk)
   int max_batch;  // vectors per pass
 };
 
@@ -104,17 +108,18 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
     k_step<Real, LAT, C, true, 3><<<G, kBlock, SMD, st>>>(nullptr, r0, bA, nullptr, vt, tt, p.Lx,
                                                          p.Ly, units, partial + (size_t)G * Q,
                                                          partial, ctx->d_status,
-                                                         ctx->debug_stall, FamOut{});
+                                                         ctx->debug_stall, FamOut{}, p.realv ? 1 : 0);
     ctx->debug_stall = 0;
     for (int n = 1; n < steps; ++n)
       k_step<Real, LAT, C, false, 3><<<G, kBlock, SMD, st>>>(
           where(n - 1), where(n), where(n + 1), nullptr, vt, tt, p.Lx, p.Ly, units,
           partial + (size_t)(2 * n + 1) * G * Q, partial + (size_t)(2 * n) * G * Q, ctx->d_status,
-          0, FamOut{});
+          0, FamOut{}, p.realv ? 1 : 0);
     KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
     KITE_CUDA_TRY(ctx, cudaGetLastError());
     const int total = M * Q;
-    k_reduce<<<(total + 255) / 256, 256, 0, st>>>(partial, M, G, Q, nvec, vec_base, n_eff, mu_vec);
+    k_reduce<<<(total + 255) / 256, 256, 0, st>>>(partial, M, G, Q, nvec, vec_base, n_eff, mu_vec,
+                                                 p.realv ? 1 : 0);
     k_undouble<<<(nvec * M + 255) / 256, 256, 0, st>>>(mu_vec, M, nvec, vec_base);
     KITE_CUDA_TRY(ctx, cudaGetLastError());
     float ms = 0.f;
@@ -128,13 +133,13 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
   if (M >= 2)
     k_step<Real, LAT, C, true><<<G, kBlock, SM, st>>>(nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly,
                                                       units, partial + (size_t)G * Q, partial,
-                                                      ctx->d_status, ctx->debug_stall, FamOut{});
+                                                      ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0);
   ctx->debug_stall = 0;
   for (int n = 1; n + 1 < M; ++n)
     k_step<Real, LAT, C, false><<<G, kBlock, SM, st>>>(where(n - 1), where(n), where(n + 1), r0,
                                                        vt, tt, p.Lx, p.Ly, units,
                                                        partial + (size_t)(n + 1) * G * Q, nullptr,
-                                                       ctx->d_status, 0, FamOut{});
+                                                       ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0);
   KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
   KITE_CUDA_TRY(ctx, cudaGetLastError());
   if (M == 1) {
@@ -142,11 +147,12 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
     // FIRST kernel is cheap and keeps one code path.
     k_step<Real, LAT, C, true><<<G, kBlock, SM, st>>>(nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly,
                                                       units, partial + (size_t)G * Q, partial,
-                                                      ctx->d_status, 0, FamOut{});
+                                                      ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0);
     KITE_CUDA_TRY(ctx, cudaGetLastError());
   }
   const int total = M * Q;
-  k_reduce<<<(total + 255) / 256, 256, 0, st>>>(partial, M, G, Q, nvec, vec_base, n_eff, mu_vec);
+  k_reduce<<<(total + 255) / 256, 256, 0, st>>>(partial, M, G, Q, nvec, vec_base, n_eff, mu_vec,
+                                                 p.realv ? 1 : 0);
   KITE_CUDA_TRY(ctx, cudaGetLastError());
   if (M >= 2) {
     float ms = 0.f;
@@ -184,9 +190,11 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
   p.S = kpm->S;
   p.M = kpm->M;
   p.doubling = kpm->doubling != 0;
-  p.max_batch = kMaxC * VPC;
+  p.realv = kpm->real_vectors != 0;
+  const int per_chunk = p.realv ? Chunk<Real>::kReals : VPC;  // vectors per 16-byte chunk
+  p.max_batch = kMaxC * per_chunk;
   auto chunks_for = [&](int nvec) {
-    const int c = (nvec + VPC - 1) / VPC;
+    const int c = (nvec + per_chunk - 1) / per_chunk;
     return c <= 1 ? 1 : (c <= 2 ? 2 : 4);
   };
   auto units_for = [&](int C) {
@@ -257,7 +265,7 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
         const uint32_t phase_base = (uint32_t)s * (uint32_t)p.R;
 #define KITE_INIT(CC)                                                                       \
   k_init_r0<Real, SORB, CC><<<(int)std::max<int64_t>(1, blocks), 256, 0, st>>>(           \
-      p.ncell, vt, base, nvec, phase_base, k0, k1, r0_in, p.N, r0)
+      p.ncell, vt, base, nvec, phase_base, k0, k1, r0_in, p.N, r0, p.realv ? 1 : 0)
         if (C == 1) KITE_INIT(1);
         else if (C == 2) KITE_INIT(2);
         else KITE_INIT(4);
@@ -350,7 +358,8 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
     stats->updates = (double)n_eff_last * p.M * p.R * p.S;
     // algorithmic bytes per orbital and step: read r_{n-1}, r_n, r_0, write r_{n+1}
     // for every vector, plus the shared on-site term
-    const double per_orb_step = (p.doubling ? 3.0 : 4.0) * 2.0 * sizeof(Real) * p.R + (double)sizeof(Real);
+    const double per_orb_step =
+        (p.doubling ? 3.0 : 4.0) * (p.realv ? 1.0 : 2.0) * sizeof(Real) * p.R + (double)sizeof(Real);
     stats->bytes_moved = per_orb_step * (double)p.N * (double)steps_for(p) * p.S;
     stats->gbps = stats->seconds > 0 ? stats->bytes_moved / stats->seconds * 1e-9 : 0.0;
     stats->n_eff = n_eff_last;

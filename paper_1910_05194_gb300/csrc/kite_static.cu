@@ -207,7 +207,7 @@ int moments_1d_static_checked(const kite_system* sys, const kite_kpm* kpm_in, do
     return static_fail(KITE_ERR_ARG, "invalid system");
   if (kpm->M < 1 || kpm->M > 65536 || kpm->R < 1 || kpm->S < 1)
     return static_fail(KITE_ERR_ARG, "need 1 <= M <= 65536, R >= 1, S >= 1");
-  if (kpm->r0 || kpm->r_last || kpm->doubling != 0 || kpm->reserved != 0)
+  if (kpm->r0 || kpm->r_last || kpm->doubling != 0 || kpm->real_vectors != 0)
     return static_fail(KITE_ERR_ARG, "start vectors, r_last and doubling are not available here");
   if (!(kpm->e_max > kpm->e_min)) return static_fail(KITE_ERR_ARG, "e_max must exceed e_min");
   const int max_vec = kpm->precision == KITE_FP64 ? 4 : 8;

@@ -52,10 +52,16 @@ __global__ void k_onsite(int64_t N, int lattice, double W, double half_delta, do
 // Start vectors of one batch: random phases exp(2 pi i u) or caller vectors (FP64,
 // rounded once), zero on vacancies and on padding lanes.
 // ------------------------------------------------------------------------------------
+// Start vectors of a batch.  Complex (realv = 0): unit-modulus phases exp(2 pi i u), two
+// (FP32) or one (FP64) vectors per 16-byte chunk.  Real (realv = 1): +-1 with the sign
+// from the same draw (u < 1/2 -> +1), four (FP32) or two (FP64) vectors per chunk.  Both
+// are white noise in the sense of Sec. 2c; vacant orbitals get 0.  r0_in (caller vectors,
+// complex interleaved) replaces the draws; real batches take its real parts.
 template <typename Real, int SORB, int C>
 __global__ void k_init_r0(int64_t ncell, const Real* __restrict__ vt, int vec_base, int nvec,
                           uint32_t phase_base, uint32_t k0, uint32_t k1,
-                          const double* __restrict__ r0_in, int64_t N, void* __restrict__ r0) {
+                          const double* __restrict__ r0_in, int64_t N, void* __restrict__ r0,
+                          int realv = 0) {
   using Ch = Chunk<Real>;
   const int64_t nchunk = ncell * SORB * C;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nchunk;
@@ -64,6 +70,25 @@ __global__ void k_init_r0(int64_t ncell, const Real* __restrict__ vt, int vec_ba
     const int64_t o = q / C;  // orbital index = cell*SORB + s
     const bool vacant = isnan((double)vt[o]);
     Ch out;
+    if (realv) {
+#pragma unroll
+      for (int k = 0; k < Ch::kReals; ++k) {
+        const int v = c * Ch::kReals + k;
+        double x = 0.0;
+        if (v < nvec && !vacant) {
+          if (r0_in) {
+            x = r0_in[2 * ((int64_t)(vec_base + v) * N + o)];
+          } else {
+            const Philox4 w = philox4x32_10((uint32_t)o, (uint32_t)((uint64_t)o >> 32),
+                                            phase_base + (uint32_t)(vec_base + v), kTagPhase, k0, k1);
+            x = u53(w) < 0.5 ? 1.0 : -1.0;
+          }
+        }
+        out.v[k] = (Real)x;
+      }
+      out.st(r0, q);
+      continue;
+    }
 #pragma unroll
     for (int k = 0; k < Ch::kVecs; ++k) {
       const int v = c * Ch::kVecs + k;  // lane within the batch
@@ -225,7 +250,8 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
                                           const void* __restrict__ r0, const Real* __restrict__ vt,
                                           Real tt, int Lx, int Ly, long long units,
                                           double* __restrict__ partial, double* __restrict__ partial0,
-                                          int* __restrict__ err, int stall, const FamOut& fam) {
+                                          int* __restrict__ err, int stall, const FamOut& fam,
+                                          int realv = 0) {
   static_assert(MODE == 0 || MODE == 3 || (sizeof(Real) == 4 && C * 2 <= kMaxFamVecs),
                 "family modes run on FP32 batches of at most two vectors");
   using Ch = Chunk<Real>;
@@ -234,7 +260,7 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
   constexpr int VPC = Ch::kVecs, NR = Ch::kReals;
   constexpr int SORB = Sh::SORB, TPC = Sh::TPC, TX = Sh::TX, CELLB = Sh::CELLB;
   constexpr int STG = Sh::template stage_bytes<MODE>();
-  constexpr int QT = 2 * VPC;  // (re, im) per vector held by one thread
+  constexpr int QT = 2 * VPC;  // (re, im) per complex vector, or one value per real vector
   uint64_t* bars = ring.bars;
   unsigned char* stages = ring.stages;
   int& s_abort = *ring.abort;
@@ -352,13 +378,22 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
         out.st(r_out, (((size_t)y * Lx + x0 + xl) * SORB + s) * C + c);
         if constexpr (MODE == 3) {
           // moment doubling: <r_n|r_{n+1}> into facc, <r_n|r_n> into facc0
+          if (realv) {
 #pragma unroll
-          for (int q = 0; q < VPC; ++q) {
-            const Acc ar = me.v[2 * q], ai = me.v[2 * q + 1];
-            const Acc br = out.v[2 * q], bi = out.v[2 * q + 1];
-            facc[2 * q] += ar * br + ai * bi;
-            facc[2 * q + 1] += ar * bi - ai * br;
-            facc0[2 * q] += ar * ar + ai * ai;
+            for (int k = 0; k < NR; ++k) {
+              const Acc a = me.v[k], b = out.v[k];
+              facc[k] += a * b;
+              facc0[k] += a * a;
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < VPC; ++q) {
+              const Acc ar = me.v[2 * q], ai = me.v[2 * q + 1];
+              const Acc br = out.v[2 * q], bi = out.v[2 * q + 1];
+              facc[2 * q] += ar * br + ai * bi;
+              facc[2 * q + 1] += ar * bi - ai * br;
+              facc0[2 * q] += ar * ar + ai * ai;
+            }
           }
           if (++rows == kFlushRows) {
             rows = 0;
@@ -404,13 +439,22 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
             }
           }
         } else {  // MODE 0: fused moment <r_0|r_{n+1}> (and <r_0|r_0> on the first step)
+          if (realv) {
 #pragma unroll
-          for (int q = 0; q < VPC; ++q) {
-            const Acc ar = z0.v[2 * q], ai = z0.v[2 * q + 1];
-            const Acc br = out.v[2 * q], bi = out.v[2 * q + 1];
-            facc[2 * q] += ar * br + ai * bi;
-            facc[2 * q + 1] += ar * bi - ai * br;
-            if (FIRST) facc0[2 * q] += ar * ar + ai * ai;
+            for (int k = 0; k < NR; ++k) {
+              const Acc a = z0.v[k], b = out.v[k];
+              facc[k] += a * b;
+              if (FIRST) facc0[k] += a * a;
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < VPC; ++q) {
+              const Acc ar = z0.v[2 * q], ai = z0.v[2 * q + 1];
+              const Acc br = out.v[2 * q], bi = out.v[2 * q + 1];
+              facc[2 * q] += ar * br + ai * bi;
+              facc[2 * q + 1] += ar * bi - ai * br;
+              if (FIRST) facc0[2 * q] += ar * ar + ai * ai;
+            }
           }
           if (++rows == kFlushRows) {
             rows = 0;
@@ -459,7 +503,7 @@ __global__ void __launch_bounds__(kBlock, 2)
     k_step(const void* r_prev, const void* __restrict__ r_cur, void* r_out,
            const void* __restrict__ r0, const Real* __restrict__ vt, Real tt, int Lx, int Ly,
            long long units, double* __restrict__ partial, double* __restrict__ partial0,
-           int* __restrict__ err, int stall, const FamOut fam) {
+           int* __restrict__ err, int stall, const FamOut fam, int realv = 0) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
@@ -470,7 +514,7 @@ __global__ void __launch_bounds__(kBlock, 2)
   }
   Ring ring{bars, smem + kBarBytes, &s_abort, 0};
   step_body<Real, LAT, C, FIRST, MODE>(ring, blockIdx.x, gridDim.x, r_prev, r_cur, r_out, r0, vt,
-                                       tt, Lx, Ly, units, partial, partial0, err, stall, fam);
+                                       tt, Lx, Ly, units, partial, partial0, err, stall, fam, realv);
 }
 
 // Copies one iterate buffer (batch layout) into the caller layout [vec][slot][N].

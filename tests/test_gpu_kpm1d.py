@@ -35,7 +35,7 @@ def ksys(**kw):
 
 
 def run_gpu(ctx, sysd, M, R, S=1, precision=kite.FP32, r0=None, want_last=False, e_min=0.0,
-            e_max=0.0, doubling=False):
+            e_max=0.0, doubling=False, real_vectors=False):
     s = ksys(**sysd)
     n = oracle.norb(osys(**sysd))
     r0a = None
@@ -43,7 +43,8 @@ def run_gpu(ctx, sysd, M, R, S=1, precision=kite.FP32, r0=None, want_last=False,
         r0a = np.ascontiguousarray(np.stack([r0.real, r0.imag], -1).astype(np.float64))
     dt = np.complex64 if precision == kite.FP32 else np.complex128
     last = np.zeros((S * R, 2, n), dt) if want_last else None
-    kpm = kite.make_kpm(M, R, S, precision, e_min, e_max, r0a, last, doubling=doubling)
+    kpm = kite.make_kpm(M, R, S, precision, e_min, e_max, r0a, last, doubling=doubling,
+                        real_vectors=real_vectors)
     mu = np.zeros(M, np.float64)
     muv = np.zeros((S * R, M, 2), np.float64)
     st = kite.moments_1d(ctx, s, kpm, mu, muv)
@@ -150,6 +151,33 @@ def test_moment_doubling_matches_oracle(ctx, case):
     assert np.max(np.abs(muv - ref)) <= bar
     assert np.max(np.abs(mu - ref.real.mean(0))) <= bar
     assert st.step_launches == S * ((R + (7 if prec == "fp32" else 3)) // (8 if prec == "fp32" else 4)) * ((M + 1) // 2)
+
+
+REAL_CASES = [
+    # (system, M, R, S, precision, doubling, bar)
+    (dict(lattice=oracle.HONEYCOMB, Lx=64, Ly=64, t=-2.7, W=1.0, seed=1), 256, 4, 1, "fp64", False, 1e-12),
+    (dict(lattice=oracle.HONEYCOMB, Lx=96, Ly=80, t=-2.7, W=2.0, p_vac=0.005, seed=2), 512, 16, 1,
+     "fp32", False, 1e-5),
+    (dict(lattice=oracle.SQUARE, Lx=300, Ly=5, t=-1.0, W=3.0, p_vac=0.05, seed=5), 33, 5, 2, "fp32", False, 1e-5),
+    (dict(lattice=oracle.HONEYCOMB, Lx=37, Ly=29, t=-2.7, W=2.0, delta=0.5, p_vac=0.02, seed=8), 65, 19, 1,
+     "fp32", True, 1e-5),
+    (dict(lattice=oracle.SQUARE, Lx=17, Ly=40, t=-1.0, W=1.0, seed=3), 40, 6, 1, "fp64", True, 1e-12),
+]
+
+
+@pytest.mark.parametrize("case", REAL_CASES)
+def test_real_vectors_match_oracle(ctx, case):
+    """Real +-1 start vectors (16 FP32 / 8 FP64 per batch): device draws and moments
+    against the oracle's plain definition on the same vectors, plain and doubling, full
+    and padded batches, several batches (R = 19) and realisations."""
+    d, M, R, S, prec, dbl, bar = case
+    precision = kite.FP64 if prec == "fp64" else kite.FP32
+    mu, muv, _, st = run_gpu(ctx, d, M, R, S=S, precision=precision, doubling=dbl, real_vectors=True)
+    ref = np.concatenate([oracle.moments_1d(osys(**d), M, R, realisation=s,
+                                            r0=oracle.random_real(osys(**d), R, s)) for s in range(S)], 0)
+    assert np.max(np.abs(muv - ref)) <= bar
+    assert np.max(np.abs(muv.imag)) == 0.0
+    assert np.max(np.abs(mu - ref.real.mean(0))) <= bar
 
 
 def test_exact_trace_with_basis_vectors_pins_device_draws(ctx):

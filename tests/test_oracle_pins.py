@@ -631,3 +631,58 @@ def test_green_function_matches_exact_resolvent_trace():
     Ef = np.linspace(lo, hi, 20001)
     rho = -oracle.green(mu, Ef, lo, hi, eta).imag / np.pi
     assert abs(np.trapezoid(rho, Ef) - 1.0) < 0.05  # Lorentzian tails beyond the window
+
+
+def test_real_random_vectors_are_white_noise_and_unbiased():
+    """Real start vectors (Sec. 2c allows real white noise): entries +-1 off the
+    vacancies, balanced, uncorrelated between vectors; averaged over many vectors the
+    moments converge to the exact trace (real symmetric H~), within the STE error."""
+    s = oracle.make_system(lattice=oracle.HONEYCOMB, Lx=6, Ly=5, t=T_EV, W=2.0, p_vac=0.1, seed=41)
+    _, vac = oracle.disorder(s)
+    R = 4000
+    xi = oracle.random_real(s, R)
+    keep = vac == 0
+    assert np.all(xi.imag == 0) and np.all(xi[:, ~keep] == 0)
+    assert np.all(np.abs(xi[:, keep].real) == 1.0)
+    x = xi[:, keep].real
+    assert abs(x.mean()) < 5 / np.sqrt(x.size)
+    c = (x[:-1] * x[1:]).mean()  # neighbouring vectors uncorrelated
+    assert abs(c) < 5 / np.sqrt(x.size)
+    # the same draw decides the sign and the phase: sign = +1 exactly when phase < pi
+    ph = oracle.random_phase(s, 8)
+    xr = oracle.random_real(s, 8)
+    ang = np.mod(np.angle(ph[:, keep]), 2 * np.pi)
+    assert np.array_equal(xr[:, keep].real > 0, ang < np.pi)
+    M = 12
+    ex = exact_trace_moments(s, M).real
+    mu = oracle.moments_1d(s, M, 400, r0=oracle.random_real(s, 400)).real
+    err = np.abs(mu.mean(0) - ex)
+    sd = mu.std(0) / np.sqrt(mu.shape[0])
+    assert np.all(err <= 5 * sd + 1e-12)
+
+
+def test_spectral_function_moments_match_bloch_bands():
+    """k-resolved moments (1/N)<k|T_n(H~)|k> of the clean honeycomb lattice with the
+    plane-wave start vector of the spectral-function section: for k on the torus grid,
+    |k> = sum_a w_a |k, a> decomposes into the two Bloch bands, so the moments equal
+    sum_b |<psi_b(k)|w>|^2 T_n(eps_b(k)) / SORB with the 2x2 Bloch Hamiltonian in the
+    atomic gauge (bond vectors of the lattice set-up listing); with random orbital
+    weights averaged (<w_a* w_b> = delta_ab) every band gets weight 1/2."""
+    Lx, Ly, M = 6, 5, 14
+    s = oracle.make_system(Lx=Lx, Ly=Ly, t=T_EV)
+    lo, hi = oracle.bounds_auto(s)
+    tt = T_EV / (0.5 * (hi - lo))
+    n = oracle.norb(s)
+    acc = 1.0 / np.sqrt(3.0)
+    bonds = np.array([[0.0, acc], [0.5, -0.5 * acc], [-0.5, -0.5 * acc]])
+    for m1, m2 in ((0, 0), (1, 2), (3, 4), (5, 1)):
+        k1, k2 = 2 * np.pi * m1 / Lx, 2 * np.pi * m2 / Ly
+        k = np.array([k1, (2.0 * k2 - k1) / np.sqrt(3.0)])
+        f = tt * np.exp(1j * bonds @ k).sum()
+        lam, U = np.linalg.eigh(np.array([[0, f], [np.conj(f), 0]]))
+        for w in (np.array([1.0, 1.0]), np.array([0.3 + 0.4j, -1.1])):
+            v = oracle.bloch_vector(s, k, w)
+            mu = oracle.moments_1d(s, M, 1, r0=v[None, :])[0] * (n / np.vdot(v, v).real)
+            ov = np.abs(U.conj().T @ w) ** 2 / np.sum(np.abs(w) ** 2)
+            ref = (ov[None, :] * cheb_T(M, lam)).sum(1)
+            assert np.max(np.abs(mu - ref)) < 1e-12, (m1, m2, w)
