@@ -217,6 +217,30 @@ int kite_spectral_k(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
 int kite_ldos(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const int64_t* orbitals,
               int n, double* mu, kite_stats* st);
 
+/* Wave-packet time evolution (the paper's spintronics section; hbar = 1, times in hbar/eV,
+ * i.e. t_fs = 0.6582 t):
+ *   |psi(t + dt)> = exp(-i H dt) |psi(t)>
+ *                 = exp(-i de_plus dt) [c_0 + 2 sum_{n=1}^{M-1} c_n T_n(H~)] |psi(t)>,
+ *   c_n = (-i)^n J_n(de_minus dt)
+ * (the Chebyshev propagator of Tal-Ezer and Kosloff that the paper cites; the printed
+ * (-1)^n is read as (-i)^n, which the expansion of exp(-i x tau) has).  M Chebyshev terms
+ * per step: the truncation error falls off like J_M(de_minus dt), negligible once
+ * M > 1.1 de_minus dt + 20.  Each step runs M - 1 stencil steps that also accumulate the
+ * series; vacant orbitals stay 0.
+ *   kpm     M terms per step, R wave functions, S = 1, precision (FP32 or FP64
+ *           recursion and accumulation), bounds; r0, r_last NULL, doubling 0
+ *   psi     [R][N] complex FP64 interleaved, host or device: psi(0) on entry,
+ *           psi(nsteps dt) on return
+ *   norms   [nsteps][R] FP64 <psi|psi> after every step (unitarity check), or NULL
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA, KITE_ERR_TIMEOUT. */
+int kite_propagate(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, double dt,
+                   int nsteps, double* psi, double* norms, kite_stats* st);
+
+/* The propagator's coefficients exp(-i de_plus dt) (2 - delta_n0) (-i)^n J_n(de_minus dt),
+ * n < M, for the window [e_min, e_max] (host computation, no GPU): coef [M][2] complex.
+ * Errors: KITE_ERR_ARG. */
+int kite_evolution_coeffs(int M, double dt, double e_min, double e_max, double* coef);
+
 /* Test hook for failure detection (no counterpart in the paper).  When `enable` is
  * non-zero, the first recursion step of the next kite_moments_1d call on this context
  * arms one shared-memory barrier of one CTA for 16 bytes more than it copies, so that

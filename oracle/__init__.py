@@ -92,6 +92,8 @@ def lib():
             L.orc_velocity.argtypes = [P(System), vp, d, i32, vp, vp]
             L.orc_moments_2d.argtypes = [P(System), i32, i32, i32, d, d, vp, vp, vp, vp, i32, i32, i32]
             L.orc_moments_2d.restype = i32
+            L.orc_chebyshev_sum.argtypes = [P(System), i32, d, d, i32, vp, vp, vp]
+            L.orc_chebyshev_sum.restype = i32
             L.orc_kernel_jackson.argtypes = [i32, vp]
             L.orc_kernel_lorentz.argtypes = [i32, d, vp]
             L.orc_dos.argtypes = [vp, i32, vp, d, d, vp, i32, vp]
@@ -347,6 +349,44 @@ def green(mu, E, e_min: float, e_max: float, eta: float, g=None):
     if g is not None:
         w = w * np.asarray(g, np.float64)
     return (w @ cpgf_coeffs(M, eps, eta / dm, +1)) / dm
+
+
+def chebyshev_sum(sys: System, coef, vec, realisation: int = 0, e_min=None, e_max=None):
+    """sum_n coef_n T_n(H~) vec (complex coef [M], vec [N]); vacant orbitals removed."""
+    lo, hi = _bounds(sys, e_min, e_max)
+    c = np.ascontiguousarray(np.stack([np.real(coef), np.imag(coef)], -1).astype(np.float64))
+    v = np.ascontiguousarray(np.stack([np.real(vec), np.imag(vec)], -1).astype(np.float64))
+    out = np.empty_like(v)
+    rc = lib().orc_chebyshev_sum(ctypes.byref(sys), int(realisation), lo, hi, int(c.shape[0]), _ptr(c), _ptr(v),
+                                 _ptr(out))
+    if rc != 0:
+        raise ValueError(f"orc_chebyshev_sum failed ({rc})")
+    return out[:, 0] + 1j * out[:, 1]
+
+
+def evolution_coeffs(M: int, dt: float, e_min: float, e_max: float):
+    """Chebyshev coefficients of exp(-i H dt) (hbar = 1, dt in hbar/eV) in H~ (the
+    wave-packet section, Tal-Ezer and Kosloff): exp(-i de_plus dt) (2 - delta_n0) (-i)^n
+    J_n(de_minus dt), the Bessel functions by scipy.  (The paper prints (-1)^n; the
+    expansion exp(-i x tau) = J_0(tau) + 2 sum_n (-i)^n J_n(tau) T_n(x) has (-i)^n.)"""
+    from scipy.special import jv
+    dm, dp = 0.5 * (e_max - e_min), 0.5 * (e_max + e_min)
+    n = np.arange(M)
+    c = np.where(n == 0, 1.0, 2.0) * (-1j) ** n * jv(n, dm * dt)
+    return np.exp(-1j * dp * dt) * c
+
+
+def propagate(sys: System, psi0, dt: float, nsteps: int, M: int, realisation: int = 0, e_min=None,
+              e_max=None):
+    """psi(nsteps dt) = U(dt)^nsteps psi0 with the truncated Chebyshev series per step;
+    returns the wave function after every step, [nsteps][N]."""
+    lo, hi = _bounds(sys, e_min, e_max)
+    c = evolution_coeffs(M, dt, lo, hi)
+    out, psi = [], np.asarray(psi0, np.complex128)
+    for _ in range(nsteps):
+        psi = chebyshev_sum(sys, c, psi, realisation, lo, hi)
+        out.append(psi)
+    return np.array(out)
 
 
 def unit_cell_factor(lattice: int):

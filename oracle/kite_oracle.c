@@ -317,6 +317,50 @@ static void orc_start_vectors(const orc_system* sys, int realisation, int R, con
   }
 }
 
+/* out = sum_{n<M} coef_n T_n(H~) in  (complex coef [M][2], in/out [N][2]); the plain
+ * recursion of Eq. e6 with vacant orbitals removed.  Used for the time-evolution operator
+ * of the wave-packet section: U(t) = exp(-i de_plus t) [c_0 + 2 sum_n c_n T_n(H~)],
+ * c_n = (-i)^n J_n(de_minus t). */
+int orc_chebyshev_sum(const orc_system* sys, int realisation, double e_min, double e_max, int M,
+                      const double* coef, const double* in, double* out) {
+  if (M < 1 || !(e_max > e_min)) return -1;
+  orc_ham h;
+  if (orc_ham_build(&h, sys, realisation, e_min, e_max)) return -2;
+  int64_t N = h.N;
+  double* prev = (double*)malloc(sizeof(double) * 2 * N);
+  double* cur = (double*)malloc(sizeof(double) * 2 * N);
+  double* nxt = (double*)malloc(sizeof(double) * 2 * N);
+  if (!prev || !cur || !nxt) return -2;
+  for (int64_t o = 0; o < N; ++o) {  /* T_0 in, vacancies removed */
+    double re = h.vac[o] ? 0.0 : in[2 * o], im = h.vac[o] ? 0.0 : in[2 * o + 1];
+    prev[2 * o] = re;
+    prev[2 * o + 1] = im;
+    out[2 * o] = coef[0] * re - coef[1] * im;
+    out[2 * o + 1] = coef[0] * im + coef[1] * re;
+  }
+  if (M > 1) orc_apply_h(&h, prev, cur);
+  for (int n = 1; n < M; ++n) {
+    const double cr = coef[2 * n], ci = coef[2 * n + 1];
+    for (int64_t o = 0; o < N; ++o) {
+      out[2 * o] += cr * cur[2 * o] - ci * cur[2 * o + 1];
+      out[2 * o + 1] += cr * cur[2 * o + 1] + ci * cur[2 * o];
+    }
+    if (n + 1 < M) {
+      orc_apply_h(&h, cur, nxt);
+      for (int64_t k = 0; k < 2 * N; ++k) nxt[k] = 2.0 * nxt[k] - prev[k];
+      double* t = prev;
+      prev = cur;
+      cur = nxt;
+      nxt = t;
+    }
+  }
+  free(prev);
+  free(cur);
+  free(nxt);
+  orc_ham_free(&h);
+  return 0;
+}
+
 int orc_moments_1d(const orc_system* sys, int realisation, int M, int R, double e_min,
                    double e_max, const double* r0_in, double* mu_per_vec, int threads) {
 #ifdef _OPENMP

@@ -64,6 +64,8 @@ int orc_moments_2d(const orc_system* sys, int realisation, int M, int R, double 
                    double e_max, const double* r0_in, double* mu_nm, double* a_fam,
                    double* b_fam, int dir_a, int dir_b, int threads);
 
+int orc_chebyshev_sum(const orc_system* sys, int realisation, double e_min, double e_max, int M,
+                      const double* coef, const double* in, double* out);
 void orc_kernel_jackson(int M, double* g);
 void orc_kernel_lorentz(int M, double lambda, double* g);
 void orc_dos(const double* mu, int M, const double* g, double e_min, double e_max,

@@ -28,7 +28,8 @@ EXPORTED = ("kite_create", "kite_destroy", "kite_set_stream", "kite_status_strin
             "kite_debug_stall_once", "kite_inner_products", "kite_moments_2d", "kite_reconstruct_green",
             "kite_reconstruct_sigma", "kite_moments_1d_static", "kite_moments_1d_batched",
             "kite_mlp_param_count", "kite_mlp_train", "kite_mlp_forward", "kite_mlp_gradient",
-            "kite_learned_gate", "kite_spectral_k", "kite_ldos")
+            "kite_learned_gate", "kite_spectral_k", "kite_ldos", "kite_propagate",
+            "kite_evolution_coeffs")
 MLP_IN, MLP_HIDDEN, MLP_OUT = 128, 512, 1024
 
 
@@ -149,6 +150,10 @@ def lib():
             L.kite_spectral_k.restype = i32
             L.kite_ldos.argtypes = [vp, P(System), P(KPM), vp, i32, vp, P(Stats)]
             L.kite_ldos.restype = i32
+            L.kite_propagate.argtypes = [vp, P(System), P(KPM), d, i32, vp, vp, P(Stats)]
+            L.kite_propagate.restype = i32
+            L.kite_evolution_coeffs.argtypes = [i32, d, d, d, vp]
+            L.kite_evolution_coeffs.restype = i32
             L.kite_inner_products.argtypes = [vp, vp, vp, i32, i32, ctypes.c_int64, d, vp, i32, i32, i32]
             L.kite_inner_products.restype = i32
             L.kite_debug_stall_once.argtypes = [vp, i32]
@@ -274,6 +279,25 @@ def ldos(ctx: Context, system: System, kpm: KPM, orbitals, n: int, mu) -> Stats:
     ctx.check(lib().kite_ldos(ctx.handle, ctypes.byref(system), ctypes.byref(kpm), _addr(orbitals), int(n),
                               _addr(mu), ctypes.byref(st)))
     return st
+
+
+def propagate(ctx: Context, system: System, kpm: KPM, dt: float, nsteps: int, psi, norms=None) -> Stats:
+    """kite_propagate: psi [R][N][2] FP64 (host or device) evolved in place by nsteps steps of
+    exp(-i H dt); norms [nsteps][R] (optional)."""
+    st = Stats()
+    ctx.check(lib().kite_propagate(ctx.handle, ctypes.byref(system), ctypes.byref(kpm), float(dt), int(nsteps),
+                                   _addr(psi), _addr(norms), ctypes.byref(st)))
+    return st
+
+
+def evolution_coeffs(M: int, dt: float, e_min: float, e_max: float):
+    """kite_evolution_coeffs (host): the propagator's Chebyshev coefficients, complex [M]."""
+    import numpy as _np
+    c = _np.zeros((int(M), 2))
+    rc = lib().kite_evolution_coeffs(int(M), float(dt), float(e_min), float(e_max), _addr(c))
+    if rc != 0:
+        raise KiteError(rc, "kite_evolution_coeffs")
+    return c[:, 0] + 1j * c[:, 1]
 
 
 def inner_products(ctx: Context, A, B, M: int, M2: int, N: int, scale: float, C, sub_k: int = 0,

@@ -38,6 +38,9 @@ int spectral_k_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
                     const double* k, int nk, const double* w, double* out, kite_stats* st);
 int ldos_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
               const int64_t* orb, int n, double* out, kite_stats* st);
+int propagate_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc, double dt,
+                   int nsteps, double* psi, double* norms, kite_stats* st);
+void evolution_coeffs(int M, double dt, double de_plus, double de_minus, double* coef);
 int reconstruct_green_impl(kite_ctx* ctx, const double* mu_dev, int M_use, int kernel, double param,
                            const Scale& sc, double eta, const double* E_dev, int K, double* G_dev,
                            double* rho_dev, double* coef_dev);
@@ -570,6 +573,48 @@ int kite_ldos(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
           break;
         }
   }
+  if (st) *st = local;
+  return rc;
+}
+
+int kite_evolution_coeffs(int M, double dt, double e_min, double e_max, double* coef) {
+  if (M < 1 || !coef || !(e_max > e_min) || !isfinite(dt) || dt < 0.0) return KITE_ERR_ARG;
+  evolution_coeffs(M, dt, 0.5 * (e_max + e_min), 0.5 * (e_max - e_min), coef);
+  return KITE_OK;
+}
+
+int kite_propagate(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, double dt, int nsteps, double* psi,
+                   double* norms, kite_stats* st) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  int rc = validate_system(ctx, sys);
+  if (rc != KITE_OK) return rc;
+  if (!kpm || !psi || nsteps < 1 || !isfinite(dt) || dt < 0.0)
+    return fail(ctx, KITE_ERR_ARG, "kpm, psi, nsteps >= 1 and dt >= 0 are required");
+  if (kpm->M < 1 || kpm->R < 1 || kpm->R > 65536 || kpm->S != 1)
+    return fail(ctx, KITE_ERR_ARG, "need M >= 1, 1 <= R <= 65536 wave functions and S = 1");
+  if (kpm->precision != KITE_FP32 && kpm->precision != KITE_FP64)
+    return fail(ctx, KITE_ERR_ARG, "precision must be KITE_FP32 or KITE_FP64");
+  if (kpm->r0 || kpm->r_last || kpm->doubling != 0 || kpm->real_vectors != 0)
+    return fail(ctx, KITE_ERR_ARG, "no r0/r_last (psi is the start), doubling 0, complex vectors");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  Scale sc;
+  rc = resolve_bounds(ctx, sys, kpm->e_min, kpm->e_max, &sc);
+  if (rc != KITE_OK) return rc;
+  const int64_t N = (int64_t)sys->Lx * sys->Ly * (sys->lattice == KITE_HONEYCOMB ? 2 : 1);
+  const size_t npsi = 2 * (size_t)kpm->R * N;
+  Staging sg{ctx, {}};
+  const double* pin;
+  double *pd, *nd = nullptr;
+  rc = sg.in((const double*)psi, npsi, &pin);
+  pd = const_cast<double*>(pin);  // psi is updated in place (staged copy for host memory)
+  if (rc == KITE_OK && norms) rc = sg.out(norms, (size_t)nsteps * kpm->R, &nd);
+  kite_stats local{};
+  if (rc == KITE_OK) rc = propagate_impl(ctx, sys, kpm, sc, dt, nsteps, pd, nd, &local);
+  if (rc == KITE_OK) rc = sg.back(psi, (const double*)pd, npsi);
+  if (rc == KITE_OK && norms) rc = sg.back(norms, (const double*)nd, (size_t)nsteps * kpm->R);
+  cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "propagate");
   if (st) *st = local;
   return rc;
 }

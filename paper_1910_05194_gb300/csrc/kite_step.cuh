@@ -171,6 +171,13 @@ struct StepShape {
 // rows `col` (b) and `col + M` (-i b) of the extended B family.  MODE 3 (moment doubling)
 // accumulates <r_n|r_{n+1}> and <r_n|r_n> instead of <r_0|r_{n+1}>; r_0 is not staged.
 constexpr int kMaxFamVecs = 2;
+
+// Chebyshev-series accumulation of MODE 4 (time evolution, the wave-packet section):
+// acc += (cr + i ci) * r_{n+1}, acc in the batch layout of the iterates.
+struct SeriesOut {
+  void* acc;
+  double cr, ci;
+};
 struct FamOut {
   __nv_bfloat16* hi[kMaxFamVecs];
   __nv_bfloat16* lo[kMaxFamVecs];
@@ -251,8 +258,8 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
                                           Real tt, int Lx, int Ly, long long units,
                                           double* __restrict__ partial, double* __restrict__ partial0,
                                           int* __restrict__ err, int stall, const FamOut& fam,
-                                          int realv = 0) {
-  static_assert(MODE == 0 || MODE == 3 || (sizeof(Real) == 4 && C * 2 <= kMaxFamVecs),
+                                          int realv = 0, const SeriesOut& ser = SeriesOut{}) {
+  static_assert(MODE == 0 || MODE == 3 || MODE == 4 || (sizeof(Real) == 4 && C * 2 <= kMaxFamVecs),
                 "family modes run on FP32 batches of at most two vectors");
   using Ch = Chunk<Real>;
   using Acc = typename AccT<Real>::T;
@@ -376,7 +383,18 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
           out.v[k] = vacant ? Real(0) : o;
         }
         out.st(r_out, (((size_t)y * Lx + x0 + xl) * SORB + s) * C + c);
-        if constexpr (MODE == 3) {
+        if constexpr (MODE == 4) {
+          const size_t qi = (((size_t)y * Lx + x0 + xl) * SORB + s) * C + c;
+          Ch a = Ch::ldg(ser.acc, qi);
+          const Real cr = (Real)ser.cr, ci = (Real)ser.ci;
+#pragma unroll
+          for (int q = 0; q < VPC; ++q) {
+            const Real br = out.v[2 * q], bi = out.v[2 * q + 1];
+            a.v[2 * q] += cr * br - ci * bi;
+            a.v[2 * q + 1] += cr * bi + ci * br;
+          }
+          a.st(ser.acc, qi);
+        } else if constexpr (MODE == 3) {
           // moment doubling: <r_n|r_{n+1}> into facc, <r_n|r_n> into facc0
           if (realv) {
 #pragma unroll
@@ -503,7 +521,8 @@ __global__ void __launch_bounds__(kBlock, 2)
     k_step(const void* r_prev, const void* __restrict__ r_cur, void* r_out,
            const void* __restrict__ r0, const Real* __restrict__ vt, Real tt, int Lx, int Ly,
            long long units, double* __restrict__ partial, double* __restrict__ partial0,
-           int* __restrict__ err, int stall, const FamOut fam, int realv = 0) {
+           int* __restrict__ err, int stall, const FamOut fam, int realv = 0,
+           const SeriesOut ser = SeriesOut{}) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
@@ -514,7 +533,7 @@ __global__ void __launch_bounds__(kBlock, 2)
   }
   Ring ring{bars, smem + kBarBytes, &s_abort, 0};
   step_body<Real, LAT, C, FIRST, MODE>(ring, blockIdx.x, gridDim.x, r_prev, r_cur, r_out, r0, vt,
-                                       tt, Lx, Ly, units, partial, partial0, err, stall, fam, realv);
+                                       tt, Lx, Ly, units, partial, partial0, err, stall, fam, realv, ser);
 }
 
 // Copies one iterate buffer (batch layout) into the caller layout [vec][slot][N].

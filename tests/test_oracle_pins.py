@@ -686,3 +686,33 @@ def test_spectral_function_moments_match_bloch_bands():
             ov = np.abs(U.conj().T @ w) ** 2 / np.sum(np.abs(w) ** 2)
             ref = (ov[None, :] * cheb_T(M, lam)).sum(1)
             assert np.max(np.abs(mu - ref)) < 1e-12, (m1, m2, w)
+
+
+def test_wave_packet_propagation_matches_dense_exponential():
+    """Time evolution by the Chebyshev series of the wave-packet section against the dense
+    matrix exponential exp(-i H t) of a small disordered lattice (hbar = 1, t in hbar/eV),
+    several steps; the norm is conserved.  A (-1)^n coefficient (the printed form) fails."""
+    from scipy.linalg import expm
+    s = oracle.make_system(lattice=oracle.HONEYCOMB, Lx=5, Ly=4, t=T_EV, W=1.5, p_vac=0.1, seed=44)
+    lo, hi = oracle.bounds_auto(s)
+    H, keep, vac = dense_h(s)
+    Hphys = H * 0.5 * (hi - lo) + np.eye(len(keep)) * 0.5 * (hi + lo)
+    n = oracle.norb(s)
+    g = np.random.Generator(np.random.PCG64(5))
+    psi0 = np.zeros(n, np.complex128)
+    psi0[keep] = g.standard_normal(len(keep)) + 1j * g.standard_normal(len(keep))
+    psi0 /= np.linalg.norm(psi0)
+    dt, steps, M = 0.7, 4, 60
+    out = oracle.propagate(s, psi0, dt, steps, M)
+    U = expm(-1j * Hphys * dt)
+    ref = psi0[keep]
+    for k in range(steps):
+        ref = U @ ref
+        assert np.max(np.abs(out[k][keep] - ref)) < 1e-11
+        assert abs(np.linalg.norm(out[k]) - 1.0) < 1e-11
+        assert np.all(out[k][vac != 0] == 0)
+    from scipy.special import jv
+    nn = np.arange(M)
+    printed = np.exp(-1j * 0.5 * (hi + lo) * dt) * np.where(nn == 0, 1.0, 2.0) * (-1.0) ** nn * jv(nn, 0.5 * (hi - lo) * dt)
+    bad = oracle.chebyshev_sum(s, printed, psi0)
+    assert np.max(np.abs(bad[keep] - U @ psi0[keep])) > 1e-3
