@@ -459,7 +459,8 @@ def main():
                            "M": M, "R": R, "n_eff": int(st.n_eff),
                            "l2": "inputs larger than L2 (three 2.1 GB vector buffers per step)",
                            "parallelism": f"{world} independent realisations" if world > 1 else "single GPU",
-                           "grid": st.grid, "block": st.block},
+                           "grid": st.grid, "block": st.block,
+                           "autotuned": {"ring_stages": st.ring_stages, "ctas_per_sm": st.ctas_per_sm}},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "moment_doubling": doubling, "real_vectors": realvec, "secondary": secondary,
                 "gpu_launches": launches_per_step * args.steps,

@@ -126,7 +126,7 @@ typedef struct {
 typedef struct {
   double seconds;       /* device time of the moment sweep (CUDA events)            */
   double updates;       /* orbital * moment * vector updates done (N_eff*(M-1)*R*S)  */
-  double bytes_moved;   /* algorithmic HBM bytes of the sweep (see DESIGN)           */
+  double bytes_moved;   /* algorithmic HBM bytes of the sweep (iterates read/written + on-site) */
   double gbps;          /* bytes_moved / seconds / 1e9                               */
   double max_abs_imag;  /* max_n |Im mu_n| of the vector average (0 for exact H~)    */
   double e_min, e_max;  /* bounds used (eV)                                          */
@@ -136,7 +136,9 @@ typedef struct {
   int64_t step_launches;/* number of recursion-step launches timed in step_seconds   */
   double step_bytes;    /* algorithmic bytes of those launches                       */
   double gemm_seconds;  /* 2D moments: device time of the tensor-core contraction    */
-  double gemm_flops;    /* 2D moments: tensor flops of the contraction (3 BF16 GEMMs) */
+  double gemm_flops;    /* 2D moments: tensor flops of the contraction (4 BF16 products) */
+  int32_t ring_stages;  /* step kernel: shared-memory ring depth used (autotuned)       */
+  int32_t ctas_per_sm;  /* step kernel: resident CTAs per SM used (autotuned)           */
 } kite_stats;
 
 typedef struct kite_ctx kite_ctx;

@@ -66,7 +66,7 @@ __device__ __forceinline__ bool team_barrier(unsigned int* ctr, unsigned int tar
 // step 0 writes <r_0|r_0>, <r_0|r_1> into slots 0, 1; step n >= 1 writes <r_n|r_n>,
 // <r_n|r_{n+1}> into slots 2n, 2n+1; k_breduce turns slots into moments.
 template <int LAT, int C, bool DBL>
-__global__ void __launch_bounds__(kBlock, 2)
+__global__ void __launch_bounds__(kBlock, 3)  // <= 85 registers: three CTAs fit when the stages do
     k_batched(const BSys* __restrict__ systems, const BTeam* __restrict__ teams,
               const int* __restrict__ order, const int* __restrict__ cta_team,
               unsigned int* __restrict__ counters, int* __restrict__ err, int stall) {

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 
 #include "kite_gb.h"
@@ -25,6 +26,9 @@ struct kite_ctx {
   // Device status word: kernels set it (never trap) when a bounded wait gives up.
   int* d_status = nullptr;
   int debug_stall = 0;  // test hook, see kite_debug_stall_once
+  // Autotuner cache: key (kernel family, precision, lattice, vectors per orbital, mode,
+  // size bucket) -> (ring depth, CTAs per SM) measured fastest on this context's GPU.
+  std::map<uint64_t, std::pair<int, int>> tune;
 };
 
 namespace kite {

@@ -12,6 +12,7 @@
 // contiguous 512-byte stretches of a row; x runs fastest (the memory layout along
 // a1 used by the paper, Sec. 5).
 #include <math.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <vector>
@@ -86,7 +87,7 @@ struct Plan {
 // also yields mu_2n and mu_2n+1, so steps n = 0 .. ceil(M/2) - 1 suffice
 inline int steps_for(const Plan& p) { return p.doubling ? (p.M + 1) / 2 : p.M - 1; }
 
-template <typename Real, int LAT, int C>
+template <typename Real, int LAT, int C, int NST>
 int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, void* bA,
                 void* bB, double* partial, int G, long long units, int nvec, int vec_base,
                 const unsigned long long* n_eff, double* mu_vec, void** last_prev,
@@ -99,19 +100,19 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
   // r_{n+1} overwrites r_{n-1} in place except at n = 1 (r_0 is kept for the moments).
   auto where = [&](int n) -> void* { return n == 0 ? r0 : ((n & 1) ? bA : bB); };
   KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
-  constexpr int SM = StepShape<LAT, C>::SMEM;
+  constexpr int SM = StepShape<LAT, C, NST>::SMEM;
   if (p.doubling) {
-    constexpr int SMD = StepShape<LAT, C>::SMEM_NR0;
+    constexpr int SMD = StepShape<LAT, C, NST>::SMEM_NR0;
     // step 0: r_1 = H~ r_0 with <r_0|r_0> -> slot 0 and <r_0|r_1> -> slot 1; step n >= 1
     // (r_{n+1} from r_n, r_{n-1}): <r_n|r_n> -> slot 2n, <r_n|r_{n+1}> -> slot 2n+1
     const int steps = steps_for(p);
-    k_step<Real, LAT, C, true, 3><<<G, kBlock, SMD, st>>>(nullptr, r0, bA, nullptr, vt, tt, p.Lx,
+    k_step<Real, LAT, C, true, 3, NST><<<G, kBlock, SMD, st>>>(nullptr, r0, bA, nullptr, vt, tt, p.Lx,
                                                          p.Ly, units, partial + (size_t)G * Q,
                                                          partial, ctx->d_status,
                                                          ctx->debug_stall, FamOut{}, p.realv ? 1 : 0);
     ctx->debug_stall = 0;
     for (int n = 1; n < steps; ++n)
-      k_step<Real, LAT, C, false, 3><<<G, kBlock, SMD, st>>>(
+      k_step<Real, LAT, C, false, 3, NST><<<G, kBlock, SMD, st>>>(
           where(n - 1), where(n), where(n + 1), nullptr, vt, tt, p.Lx, p.Ly, units,
           partial + (size_t)(2 * n + 1) * G * Q, partial + (size_t)(2 * n) * G * Q, ctx->d_status,
           0, FamOut{}, p.realv ? 1 : 0);
@@ -131,12 +132,12 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
     return KITE_OK;
   }
   if (M >= 2)
-    k_step<Real, LAT, C, true><<<G, kBlock, SM, st>>>(nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly,
+    k_step<Real, LAT, C, true, 0, NST><<<G, kBlock, SM, st>>>(nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly,
                                                       units, partial + (size_t)G * Q, partial,
                                                       ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0);
   ctx->debug_stall = 0;
   for (int n = 1; n + 1 < M; ++n)
-    k_step<Real, LAT, C, false><<<G, kBlock, SM, st>>>(where(n - 1), where(n), where(n + 1), r0,
+    k_step<Real, LAT, C, false, 0, NST><<<G, kBlock, SM, st>>>(where(n - 1), where(n), where(n + 1), r0,
                                                        vt, tt, p.Lx, p.Ly, units,
                                                        partial + (size_t)(n + 1) * G * Q, nullptr,
                                                        ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0);
@@ -145,7 +146,7 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
   if (M == 1) {
     // mu_0 alone: one FIRST pass would also write r_1; a plain dot is enough, but the
     // FIRST kernel is cheap and keeps one code path.
-    k_step<Real, LAT, C, true><<<G, kBlock, SM, st>>>(nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly,
+    k_step<Real, LAT, C, true, 0, NST><<<G, kBlock, SM, st>>>(nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly,
                                                       units, partial + (size_t)G * Q, partial,
                                                       ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0);
     KITE_CUDA_TRY(ctx, cudaGetLastError());
@@ -166,11 +167,78 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
   return KITE_OK;
 }
 
+// ---- autotuner: ring depth x resident CTAs per SM ------------------------------------
+// Candidates are timed on the caller's own buffers (a few non-first steps between r_0
+// and the two iterate buffers, which the sweep overwrites afterwards) and the fastest is
+// cached per (precision, lattice, vectors per orbital, mode, size bucket) on the context.
+// KITE_AUTOTUNE=0 keeps the default (8 stages, full occupancy).
+struct Tune {
+  int nst;  // ring depth: 4 or 8
+  int k;    // resident CTAs per SM
+};
+
+inline bool autotune_enabled() {
+  const char* e = getenv("KITE_AUTOTUNE");
+  return !(e && e[0] == '0');
+}
+
+template <typename Real, int LAT, int C, int MODE, int NST>
+float time_candidate(kite_ctx* ctx, int k, long long units, const Plan& p, const Real* vt, Real tt, void* r0,
+                     void* bA, void* bB, double* partial) {
+  constexpr int SMEM = StepShape<LAT, C, NST>::template smem_bytes<MODE>();
+  constexpr int Q = 2 * C * Chunk<Real>::kVecs;
+  const int G = grid_for<Real, LAT, C, false, MODE, NST>(ctx, units, k);
+  cudaStream_t st = ctx->stream;
+  auto launch = [&]() {
+    k_step<Real, LAT, C, false, MODE, NST><<<G, kBlock, SMEM, st>>>(
+        r0, bA, bB, MODE == 0 ? r0 : nullptr, vt, tt, p.Lx, p.Ly, units, partial + (size_t)2 * G * Q,
+        MODE == 3 ? partial + (size_t)G * Q : nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0);
+  };
+  launch();  // warm-up
+  cudaEventRecord(ctx->ev2, st);
+  for (int i = 0; i < 3; ++i) launch();
+  cudaEventRecord(ctx->ev3, st);
+  float ms = 1e30f;
+  if (cudaEventSynchronize(ctx->ev3) != cudaSuccess || cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev3) != cudaSuccess)
+    ms = 1e30f;
+  return ms;
+}
+
+template <typename Real, int LAT, int C, int MODE>
+Tune autotune(kite_ctx* ctx, long long units, const Plan& p, const Real* vt, Real tt, void* r0, void* bA,
+              void* bB, double* partial) {
+  Tune def{kStages, step_occupancy<Real, LAT, C, MODE, kStages>()};
+  if (!autotune_enabled() || units < 4LL * ctx->num_sms) return def;
+  int bucket = 0;
+  while ((1LL << (bucket + 1)) <= units) ++bucket;
+  const uint64_t key = ((uint64_t)1 << 56) | ((uint64_t)sizeof(Real) << 48) | ((uint64_t)LAT << 40) |
+                       ((uint64_t)C << 32) | ((uint64_t)MODE << 24) | ((uint64_t)p.realv << 16) | (uint64_t)bucket;
+  auto it = ctx->tune.find(key);
+  if (it != ctx->tune.end()) return Tune{it->second.first, it->second.second};
+  Tune best = def;
+  float best_ms = 1e30f;
+  const int o8 = step_occupancy<Real, LAT, C, MODE, 8>(), o4 = step_occupancy<Real, LAT, C, MODE, 4>();
+  for (int k = 1; k <= o8; ++k) {
+    const float ms = time_candidate<Real, LAT, C, MODE, 8>(ctx, k, units, p, vt, tt, r0, bA, bB, partial);
+    if (ms < best_ms) best_ms = ms, best = Tune{8, k};
+  }
+  for (int k = 1; k <= o4; ++k) {
+    const float ms = time_candidate<Real, LAT, C, MODE, 4>(ctx, k, units, p, vt, tt, r0, bA, bB, partial);
+    if (ms < best_ms * 0.98f) best_ms = ms, best = Tune{4, k};  // prefer the deeper ring on a tie
+  }
+  cudaGetLastError();
+  ctx->tune[key] = {best.nst, best.k};
+  return best;
+}
+
 template <typename Real, int LAT, int MODE>
-int grid_for_c(kite_ctx* ctx, int C, long long units) {
-  if (C == 1) return grid_for<Real, LAT, 1, false, MODE>(ctx, units);
-  if (C == 2) return grid_for<Real, LAT, 2, false, MODE>(ctx, units);
-  return grid_for<Real, LAT, 4, false, MODE>(ctx, units);
+int max_grid_c(kite_ctx* ctx, int C, long long units) {
+  auto g = [&](auto occ8, auto occ4) {
+    return (int)std::max(1LL, std::min((long long)ctx->num_sms * std::max(occ8, occ4), units));
+  };
+  if (C == 1) return g(step_occupancy<Real, LAT, 1, MODE, 8>(), step_occupancy<Real, LAT, 1, MODE, 4>());
+  if (C == 2) return g(step_occupancy<Real, LAT, 2, MODE, 8>(), step_occupancy<Real, LAT, 2, MODE, 4>());
+  return g(step_occupancy<Real, LAT, 4, MODE, 8>(), step_occupancy<Real, LAT, 4, MODE, 4>());
 }
 
 template <typename Real, int LAT>
@@ -203,8 +271,9 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
   };
   const int Cmax = chunks_for(std::min(p.R, p.max_batch));
   const int Ctail = chunks_for(p.R % p.max_batch == 0 ? std::min(p.R, p.max_batch) : p.R % p.max_batch);
+  // partials sized for the widest grid any ring depth may use (the autotuner's choice)
   auto grid_c = [&](int C) {
-    return p.doubling ? grid_for_c<Real, LAT, 3>(ctx, C, units_for(C)) : grid_for_c<Real, LAT, 0>(ctx, C, units_for(C));
+    return p.doubling ? max_grid_c<Real, LAT, 3>(ctx, C, units_for(C)) : max_grid_c<Real, LAT, 0>(ctx, C, units_for(C));
   };
   const int Gmax = std::max(grid_c(Cmax), grid_c(Ctail));
 
@@ -242,6 +311,7 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
   KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, st));
   int64_t n_eff_last = 0;
   int grid_used = 0;
+  Tune tune_used{kStages, 0};
   double step_s = 0.0, step_bytes = 0.0;
   int64_t step_n = 0;
   KITE_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
@@ -276,11 +346,18 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
       const int vec_base = s * p.R + base;
 #define KITE_SWEEP(CC)                                                                       \
   do {                                                                                       \
-    const int G = p.doubling ? grid_for<Real, LAT, CC, false, 3>(ctx, u)                     \
-                             : grid_for<Real, LAT, CC, false>(ctx, u);                        \
+    Tune t = p.doubling ? autotune<Real, LAT, CC, 3>(ctx, u, p, vt, tt, r0, bA, bB, partial)  \
+                        : autotune<Real, LAT, CC, 0>(ctx, u, p, vt, tt, r0, bA, bB, partial); \
+    const int G = t.nst == 4 ? (p.doubling ? grid_for<Real, LAT, CC, false, 3, 4>(ctx, u, t.k)   \
+                                           : grid_for<Real, LAT, CC, false, 0, 4>(ctx, u, t.k))  \
+                             : (p.doubling ? grid_for<Real, LAT, CC, false, 3, 8>(ctx, u, t.k)   \
+                                           : grid_for<Real, LAT, CC, false, 0, 8>(ctx, u, t.k)); \
     grid_used = G;                                                                           \
-    rc = sweep_batch<Real, LAT, CC>(ctx, p, vt, tt, r0, bA, bB, partial, G, u, nvec,         \
-                                    vec_base, ne, mu_vec, &lp, &lc, &step_s, &step_n);       \
+    tune_used = t;                                                                           \
+    rc = t.nst == 4 ? sweep_batch<Real, LAT, CC, 4>(ctx, p, vt, tt, r0, bA, bB, partial, G, u, nvec,  \
+                                                    vec_base, ne, mu_vec, &lp, &lc, &step_s, &step_n) \
+                    : sweep_batch<Real, LAT, CC, 8>(ctx, p, vt, tt, r0, bA, bB, partial, G, u, nvec,  \
+                                                    vec_base, ne, mu_vec, &lp, &lc, &step_s, &step_n); \
   } while (0)
       if (C == 1) KITE_SWEEP(1);
       else if (C == 2) KITE_SWEEP(2);
@@ -365,6 +442,8 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
     stats->n_eff = n_eff_last;
     stats->grid = grid_used;
     stats->block = kBlock;
+    stats->ring_stages = tune_used.nst;
+    stats->ctas_per_sm = grid_used / std::max(1, ctx->num_sms);
     stats->step_seconds = step_s;
     stats->step_launches = step_n;
     stats->step_bytes = step_bytes;

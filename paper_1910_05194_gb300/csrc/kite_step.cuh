@@ -141,10 +141,10 @@ struct AccT<double> {
 // x0+TX), and for interior rows also r_{n-1} and r_0 of the row.  Computing row y needs
 // the slots of rows y-1, y, y+1; the copy of row y+kStages-1 is issued as soon as row
 // y-1's slot is free, so ~6 rows (~75 KB per CTA) are always in flight.
-constexpr int kStages = 8;
+constexpr int kStages = 8;  // default ring depth (the autotuner may pick 4)
 constexpr int kBarBytes = 128;
 
-template <int LAT, int C>
+template <int LAT, int C, int NST = kStages>
 struct StepShape {
   static constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
   static constexpr int TPC = SORB * C;              // threads per cell
@@ -153,11 +153,11 @@ struct StepShape {
   static constexpr int ROWB = TX * CELLB;           // bytes of one row segment (4096)
   static constexpr int CURB = (TX + 2) * CELLB;     // r_n row segment with halo cells
   static constexpr int STAGEB = CURB + 2 * ROWB;    // + r_{n-1} and r_0
-  static constexpr int SMEM = kBarBytes + kStages * STAGEB;
+  static constexpr int SMEM = kBarBytes + NST * STAGEB;
   // modes that never stage r_0 (families, moment doubling) use shorter stages: a third
   // CTA fits on each SM
   static constexpr int STAGEB_NR0 = CURB + ROWB;
-  static constexpr int SMEM_NR0 = kBarBytes + kStages * STAGEB_NR0;
+  static constexpr int SMEM_NR0 = kBarBytes + NST * STAGEB_NR0;
   template <int MODE>
   static constexpr int stage_bytes() { return MODE == 0 ? STAGEB : STAGEB_NR0; }
   template <int MODE>
@@ -251,7 +251,7 @@ struct Ring {
 
 // One recursion step over this CTA's share [cta/ncta] of the units.  Returns false if a
 // bounded wait gave up (the CTA has drained its copies and set *err; stop using the ring).
-template <typename Real, int LAT, int C, bool FIRST, int MODE>
+template <typename Real, int LAT, int C, bool FIRST, int MODE, int NST = kStages>
 __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const void* r_prev,
                                           const void* __restrict__ r_cur, void* r_out,
                                           const void* __restrict__ r0, const Real* __restrict__ vt,
@@ -263,7 +263,7 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
                 "family modes run on FP32 batches of at most two vectors");
   using Ch = Chunk<Real>;
   using Acc = typename AccT<Real>::T;
-  using Sh = StepShape<LAT, C>;
+  using Sh = StepShape<LAT, C, NST>;
   constexpr int VPC = Ch::kVecs, NR = Ch::kReals;
   constexpr int SORB = Sh::SORB, TPC = Sh::TPC, TX = Sh::TX, CELLB = Sh::CELLB;
   constexpr int STG = Sh::template stage_bytes<MODE>();
@@ -306,7 +306,7 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
 
     auto issue = [&](int jj) {  // producer: thread 0 only
       const long long g = gslot + jj;
-      const int st = (int)(g % kStages);
+      const int st = (int)(g % NST);
       unsigned char* base = stages + st * STG;
       int row = yb - 1 + jj;
       row = row < 0 ? row + Ly : (row >= Ly ? row - Ly : row);
@@ -329,7 +329,7 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
       }
     };
     if (tid == 0)
-      for (int jj = 0; jj < min(kStages, nslots); ++jj) issue(jj);
+      for (int jj = 0; jj < min(NST, nslots); ++jj) issue(jj);
 
     const bool active = xl < txv;
     Real vnext = active ? vt[((size_t)yb * Lx + x0 + xl) * SORB + s] : Real(0);
@@ -338,16 +338,16 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
       bool ok = true;
       for (int jj = (i == 0 ? 0 : i + 2); jj <= i + 2; ++jj) {
         const long long g = gslot + jj;
-        ok = mbar_wait_bounded(&bars[g % kStages], (uint32_t)((g / kStages) & 1)) && ok;
+        ok = mbar_wait_bounded(&bars[g % NST], (uint32_t)((g / NST) & 1)) && ok;
       }
       if (!ok) s_abort = 1;
       const int y = yb + i;
       const Real v = vnext;
       if (active && i + 1 < nr) vnext = vt[((size_t)(y + 1) * Lx + x0 + xl) * SORB + s];
       if (ok && active) {
-        const unsigned char* up = stages + (int)((gslot + i) % kStages) * STG;
-        const unsigned char* mid = stages + (int)((gslot + i + 1) % kStages) * STG;
-        const unsigned char* dn = stages + (int)((gslot + i + 2) % kStages) * STG;
+        const unsigned char* up = stages + (int)((gslot + i) % NST) * STG;
+        const unsigned char* mid = stages + (int)((gslot + i + 1) % NST) * STG;
+        const unsigned char* dn = stages + (int)((gslot + i + 2) % NST) * STG;
         const Ch me = *reinterpret_cast<const Ch*>(mid + (xl + 1) * CELLB + choff);
         Ch n1, n2, n3, n4;
         if (LAT == KITE_HONEYCOMB) {
@@ -490,15 +490,15 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
         aborted = true;
         break;
       }
-      if (tid == 0 && i + kStages < nslots) issue(i + kStages);
+      if (tid == 0 && i + NST < nslots) issue(i + NST);
     }
     if (aborted) {
       // drain: wait (bounded) for this CTA's copies still in flight, then give up
       if (tid == 0) {
-        const int last = min(nslots, i + kStages) - 1;
+        const int last = min(nslots, i + NST) - 1;
         for (int jj = i; jj <= last; ++jj) {  // completed phases return at once
           const long long g = gslot + jj;
-          mbar_wait_bounded(&bars[g % kStages], (uint32_t)((g / kStages) & 1));
+          mbar_wait_bounded(&bars[g % NST], (uint32_t)((g / NST) & 1));
         }
         atomicExch(err, 1);
       }
@@ -516,7 +516,7 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
   return true;
 }
 
-template <typename Real, int LAT, int C, bool FIRST, int MODE = 0>
+template <typename Real, int LAT, int C, bool FIRST, int MODE = 0, int NST = kStages>
 __global__ void __launch_bounds__(kBlock, 2)
     k_step(const void* r_prev, const void* __restrict__ r_cur, void* r_out,
            const void* __restrict__ r0, const Real* __restrict__ vt, Real tt, int Lx, int Ly,
@@ -527,12 +527,12 @@ __global__ void __launch_bounds__(kBlock, 2)
   __shared__ int s_abort;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   if (threadIdx.x == 0) {
-    for (int k = 0; k < kStages; ++k) mbar_init(&bars[k], 1);
+    for (int k = 0; k < NST; ++k) mbar_init(&bars[k], 1);
     mbar_fence_init();
     s_abort = 0;
   }
   Ring ring{bars, smem + kBarBytes, &s_abort, 0};
-  step_body<Real, LAT, C, FIRST, MODE>(ring, blockIdx.x, gridDim.x, r_prev, r_cur, r_out, r0, vt,
+  step_body<Real, LAT, C, FIRST, MODE, NST>(ring, blockIdx.x, gridDim.x, r_prev, r_cur, r_out, r0, vt,
                                        tt, Lx, Ly, units, partial, partial0, err, stall, fam, realv, ser);
 }
 
@@ -561,21 +561,32 @@ __global__ void k_extract(int64_t ncell, const void* __restrict__ buf, int nvec,
 
 // Persistent grid of the step kernel of a mode: resident CTAs per SM x SMs, at most one
 // CTA per unit.  Also sets the kernels' dynamic shared-memory limit.
-template <typename Real, int LAT, int C, bool FIRST, int MODE = 0>
-int grid_for(kite_ctx* ctx, long long units) {
+// Resident CTAs per SM of the step kernel of a mode and ring depth (also sets the
+// kernels' dynamic shared-memory limit).
+template <typename Real, int LAT, int C, int MODE = 0, int NST = kStages>
+int step_occupancy() {
   static int occ = -1;  // per template instance; device-independent enough for one GPU type
   if (occ < 0) {
     int o = 0;
-    const int smem = StepShape<LAT, C>::template smem_bytes<MODE>();
-    cudaFuncSetAttribute(k_step<Real, LAT, C, true, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_step<Real, LAT, C, false, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_step<Real, LAT, C, FIRST, MODE>, kBlock, smem) !=
+    const int smem = StepShape<LAT, C, NST>::template smem_bytes<MODE>();
+    cudaFuncSetAttribute(k_step<Real, LAT, C, true, MODE, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_step<Real, LAT, C, false, MODE, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_step<Real, LAT, C, false, MODE, NST>, kBlock, smem) !=
             cudaSuccess ||
         o < 1)
       o = 1;
     occ = o;
   }
-  long long g = (long long)ctx->num_sms * occ;
+  return occ;
+}
+
+// Persistent grid of the step kernel: min(ctas_per_sm, occupancy) CTAs per SM (0 = the
+// occupancy), at most one CTA per unit.
+template <typename Real, int LAT, int C, bool FIRST, int MODE = 0, int NST = kStages>
+int grid_for(kite_ctx* ctx, long long units, int ctas_per_sm = 0) {
+  const int occ = step_occupancy<Real, LAT, C, MODE, NST>();
+  const int k = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+  long long g = (long long)ctx->num_sms * k;
   return (int)std::max(1LL, std::min(g, units));
 }
 

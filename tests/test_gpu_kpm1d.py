@@ -116,7 +116,7 @@ def test_config_small_fp64_moments(ctx):
     assert abs(mu[0] - 1.0) <= 1e-14
 
 
-def test_fp32_moments_within_north_star_tolerance(ctx):
+def test_fp32_moments_within_1e5_of_the_fp64_oracle(ctx):
     """Complex FP32 recursion, FP64 accumulation: max_n |mu_n - mu_n^oracle| <= 1e-5."""
     d = dict(lattice=oracle.HONEYCOMB, Lx=96, Ly=80, t=-2.7, W=2.0, p_vac=0.005, seed=2)
     M, R = 512, 8
