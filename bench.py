@@ -243,7 +243,8 @@ def secondary_legs(kite, ctx, peaks):
         kpms = [kite.make_kpm(sp["M"], 4, 1, kite.FP32, doubling=dbl) for sp in specs]
         st = kite.moments_1d_batched(ctx, systems, kpms, mus)
         res[name] = {"updates_per_s": st.updates / st.seconds, "seconds": st.seconds,
-                     "hbm_gbs": st.bytes_moved / st.seconds / 1e9, "grid": st.grid}
+                     "hbm_gbs": st.bytes_moved / st.seconds / 1e9, "grid": st.grid,
+                     "autotuned": {"ring_stages": st.ring_stages, "ctas_per_sm": st.ctas_per_sm}}
     res["updates"] = st.updates
     out["batched_256_square_systems_R4_fp32_one_graph_launch"] = res
     # 2D Kubo-Bastin moments: honeycomb 1024x1024, W = 1, M = 1024, R = 4 (xx)

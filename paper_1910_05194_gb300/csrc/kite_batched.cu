@@ -9,6 +9,8 @@
 // resident at once (cooperative launch), every barrier wait is bounded, and the whole
 // batch -- on-site draws, start vectors, the persistent sweep and the fixed-order moment
 // reductions -- is captured into one CUDA graph and launched once.
+#include <stdlib.h>
+
 #include <algorithm>
 #include <numeric>
 #include <vector>
@@ -65,17 +67,18 @@ __device__ __forceinline__ bool team_barrier(unsigned int* ctr, unsigned int tar
 // DBL: moment doubling for the whole batch (two moments per step, r_0 not re-read):
 // step 0 writes <r_0|r_0>, <r_0|r_1> into slots 0, 1; step n >= 1 writes <r_n|r_n>,
 // <r_n|r_{n+1}> into slots 2n, 2n+1; k_breduce turns slots into moments.
-template <int LAT, int C, bool DBL>
+// NST: ring depth.  mcap > 0 caps every system's steps (the autotuner's probe launches).
+template <int LAT, int C, bool DBL, int NST>
 __global__ void __launch_bounds__(kBlock, 3)  // <= 85 registers: three CTAs fit when the stages do
     k_batched(const BSys* __restrict__ systems, const BTeam* __restrict__ teams,
               const int* __restrict__ order, const int* __restrict__ cta_team,
-              unsigned int* __restrict__ counters, int* __restrict__ err, int stall) {
+              unsigned int* __restrict__ counters, int* __restrict__ err, int stall, int mcap) {
   constexpr int Q = 2 * C * 2;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   if (threadIdx.x == 0) {
-    for (int k = 0; k < kStages; ++k) mbar_init(&bars[k], 1);
+    for (int k = 0; k < NST; ++k) mbar_init(&bars[k], 1);
     mbar_fence_init();
     s_abort = 0;
   }
@@ -91,22 +94,23 @@ __global__ void __launch_bounds__(kBlock, 3)  // <= 85 registers: three CTAs fit
       return n == 0 ? const_cast<void*>(S.r0) : ((n & 1) ? S.bA : S.bB);
     };
     constexpr int MODE = DBL ? 3 : 0;
-    const int steps = DBL ? (S.M + 1) / 2 : max(S.M - 1, 1);
+    const int full = DBL ? (S.M + 1) / 2 : max(S.M - 1, 1);
+    const int steps = mcap > 0 ? min(full, mcap) : full;
     for (int n = 0; n < steps; ++n) {
       bool ok;
       if (n == 0)
-        ok = step_body<float, LAT, C, true, MODE>(ring, rank, T.ncta, nullptr, S.r0, S.bA, S.r0, S.vt,
+        ok = step_body<float, LAT, C, true, MODE, NST>(ring, rank, T.ncta, nullptr, S.r0, S.bA, S.r0, S.vt,
                                                   S.tt, S.Lx, S.Ly, S.units,
                                                   S.partial + (size_t)T.ncta * Q, S.partial, err, 0,
                                                   nofam);
       else if (DBL)
-        ok = step_body<float, LAT, C, false, MODE>(ring, rank, T.ncta, where(n - 1), where(n),
+        ok = step_body<float, LAT, C, false, MODE, NST>(ring, rank, T.ncta, where(n - 1), where(n),
                                                    where(n + 1), S.r0, S.vt, S.tt, S.Lx, S.Ly, S.units,
                                                    S.partial + (size_t)(2 * n + 1) * T.ncta * Q,
                                                    S.partial + (size_t)(2 * n) * T.ncta * Q, err, 0,
                                                    nofam);
       else
-        ok = step_body<float, LAT, C, false, MODE>(ring, rank, T.ncta, where(n - 1), where(n),
+        ok = step_body<float, LAT, C, false, MODE, NST>(ring, rank, T.ncta, where(n - 1), where(n),
                                                    where(n + 1), S.r0, S.vt, S.tt, S.Lx, S.Ly, S.units,
                                                    S.partial + (size_t)(n + 1) * T.ncta * Q, nullptr,
                                                    err, 0, nofam);
@@ -147,6 +151,11 @@ __global__ void k_breduce(const double* __restrict__ partial, int M, int G, int 
   const double ne = (double)*n_eff;
   const double v = slot_mean(partial, n, G, Q, nvec, ne);
   mu[n] = (dbl && n >= 2) ? 2.0 * v - slot_mean(partial, n & 1, G, Q, nvec, ne) : v;
+}
+
+inline bool autotune_enabled_batched() {
+  const char* e = getenv("KITE_AUTOTUNE");
+  return !(e && e[0] == '0');
 }
 
 struct Schedule {
@@ -198,33 +207,32 @@ Schedule plan_teams(const std::vector<double>& work, const std::vector<long long
   return sc;
 }
 
-template <int LAT, int C, bool DBL>
-int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm* kpm,
-                const std::vector<Scale>& scales, double* const* mu_out, kite_stats* stats) {
-  constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
-  constexpr int Q = 2 * C * 2;
-  using Sh = StepShape<LAT, C>;
-  cudaStream_t st = ctx->stream;
-  const int R = kpm[0].R;
-  auto steps_of = [](int M) { return DBL ? (M + 1) / 2 : std::max(M - 1, 1); };
-  // persistent grid: every CTA resident
-  constexpr int SMEM = Sh::template smem_bytes<DBL ? 3 : 0>();  // doubling stages no r_0
-  cudaFuncSetAttribute(k_batched<LAT, C, DBL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<LAT, C, DBL>, kBlock, SMEM) !=
-          cudaSuccess || occ < 1)
-    return fail(ctx, KITE_ERR_CUDA, "occupancy query for the batched kernel failed");
-  const int gmax = ctx->num_sms * occ;
-  std::vector<double> work(count);
-  std::vector<long long> units(count);
-  double total = 0.0;
-  for (int i = 0; i < count; ++i) {
-    units[i] = (long long)((sys[i].Lx + Sh::TX - 1) / Sh::TX) * sys[i].Ly;
-    work[i] = (double)units[i] * Sh::TX * steps_of(kpm[i].M);
-    total += work[i];
+// One candidate of the batched launch: ring depth, resident CTAs per SM, and the team
+// schedule that fits that grid.
+struct BPlan {
+  int nst = kStages, k = 0;
+  Schedule sc;
+};
+
+template <int LAT, int C, bool DBL, int NST>
+int batched_occupancy() {
+  static int occ = -1;
+  if (occ < 0) {
+    constexpr int SMEM = StepShape<LAT, C, NST>::template smem_bytes<DBL ? 3 : 0>();
+    cudaFuncSetAttribute(k_batched<LAT, C, DBL, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batched<LAT, C, DBL, NST>, kBlock, SMEM) != cudaSuccess)
+      o = 0;
+    occ = o;
   }
-  // smallest target share whose schedule fits the resident grid
-  double lo = total / gmax, hi = std::max(total, *std::max_element(work.begin(), work.end())) * 1.0001;
+  return occ;
+}
+
+// smallest target share whose schedule fits `gmax` resident CTAs
+inline Schedule fit_schedule(const std::vector<double>& work, const std::vector<long long>& units, int gmax) {
+  double total = 0.0, wmax = 0.0;
+  for (double w : work) total += w, wmax = std::max(wmax, w);
+  double lo = total / gmax, hi = std::max(total, wmax) * 1.0001;
   Schedule sc = plan_teams(work, units, hi);
   for (int it = 0; it < 60; ++it) {
     const double mid = 0.5 * (lo + hi);
@@ -236,16 +244,82 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
       lo = mid;
     }
   }
-  // work space: per system vt, three vector buffers, partials, counters
+  return sc;
+}
+
+template <int LAT, int C, bool DBL>
+cudaError_t launch_batched(kite_ctx* ctx, const BPlan& pl, const BSys* d_sys, const BTeam* d_teams,
+                           const int* d_ints, unsigned int* counters, int stall, int mcap) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(pl.sc.grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int* cta_team = d_ints + pl.sc.order.size();
+  if (pl.nst == 4) {
+    cfg.dynamicSmemBytes = StepShape<LAT, C, 4>::template smem_bytes<DBL ? 3 : 0>();
+    return cudaLaunchKernelEx(&cfg, k_batched<LAT, C, DBL, 4>, d_sys, d_teams, d_ints, cta_team, counters,
+                              ctx->d_status, stall, mcap);
+  }
+  cfg.dynamicSmemBytes = StepShape<LAT, C, 8>::template smem_bytes<DBL ? 3 : 0>();
+  return cudaLaunchKernelEx(&cfg, k_batched<LAT, C, DBL, 8>, d_sys, d_teams, d_ints, cta_team, counters,
+                            ctx->d_status, stall, mcap);
+}
+
+template <int LAT, int C, bool DBL>
+int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm* kpm,
+                const std::vector<Scale>& scales, double* const* mu_out, kite_stats* stats) {
+  constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
+  constexpr int Q = 2 * C * 2;
+  using Sh = StepShape<LAT, C>;  // TX and cell sizes do not depend on the ring depth
+  cudaStream_t st = ctx->stream;
+  const int R = kpm[0].R;
+  auto steps_of = [](int M) { return DBL ? (M + 1) / 2 : std::max(M - 1, 1); };
+  std::vector<double> work(count);
+  std::vector<long long> units(count);
+  double total = 0.0;
+  for (int i = 0; i < count; ++i) {
+    units[i] = (long long)((sys[i].Lx + Sh::TX - 1) / Sh::TX) * sys[i].Ly;
+    work[i] = (double)units[i] * Sh::TX * steps_of(kpm[i].M);
+    total += work[i];
+  }
+  // candidate plans: every (ring depth, CTAs per SM) whose grid is resident
+  std::vector<BPlan> cands;
+  const int occ8 = batched_occupancy<LAT, C, DBL, 8>(), occ4 = batched_occupancy<LAT, C, DBL, 4>();
+  if (occ8 < 1 && occ4 < 1) return fail(ctx, KITE_ERR_CUDA, "occupancy query for the batched kernel failed");
+  const bool tune = autotune_enabled_batched() && count > 1;
+  for (int nst : {8, 4}) {
+    const int occ = nst == 8 ? occ8 : occ4;
+    for (int k = tune ? 1 : occ; k <= occ; ++k) {
+      if (!tune && nst == 4) break;
+      BPlan pl;
+      pl.nst = nst;
+      pl.k = k;
+      pl.sc = fit_schedule(work, units, ctx->num_sms * k);
+      cands.push_back(std::move(pl));
+    }
+  }
+  // work space: per system vt, three vector buffers, partials for the widest team any
+  // candidate gives it, then counters and the schedule tables of the largest candidate
+  std::vector<int> max_ncta(count, 1);
+  size_t max_teams = 1, max_ints = 1;
+  for (const BPlan& pl : cands) {
+    for (int i = 0; i < count; ++i) max_ncta[i] = std::max(max_ncta[i], pl.sc.ncta_of[i]);
+    max_teams = std::max(max_teams, pl.sc.teams.size());
+    max_ints = std::max(max_ints, pl.sc.order.size() + pl.sc.cta_team.size());
+  }
   std::vector<size_t> off_vt(count), off_vec(count), off_part(count);
-  Carver probe(nullptr);
   auto lay = [&](Carver& k, bool record) {
     for (int i = 0; i < count; ++i) {
       const int64_t ncell = (int64_t)sys[i].Lx * sys[i].Ly, N = ncell * SORB;
       const size_t vb = (size_t)ncell * SORB * C * 16;
       char* a = k.take<char>(sizeof(float) * N);
       char* b = k.take<char>(3 * vb);
-      char* c = k.take<char>(sizeof(double) * (size_t)(std::max(kpm[i].M, 2) + 1) * sc.ncta_of[i] * Q);
+      char* c = k.take<char>(sizeof(double) * (size_t)(std::max(kpm[i].M, 2) + 1) * max_ncta[i] * Q);
       if (record) {
         off_vt[i] = (size_t)a;
         off_vec[i] = (size_t)b;
@@ -253,24 +327,28 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
       }
     }
   };
-  lay(probe, false);
-  probe.take<unsigned long long>(count);                  // n_eff
-  probe.take<unsigned int>(sc.teams.size());              // barrier counters
-  probe.take<BSys>(count);
-  probe.take<BTeam>(sc.teams.size());
-  probe.take<int>(sc.order.size() + sc.cta_team.size());
   size_t mu_total = 0;
   for (int i = 0; i < count; ++i) mu_total += (size_t)kpm[i].M;
-  probe.take<double>(mu_total);
+  auto tail = [&](Carver& k) {
+    k.take<unsigned long long>(count);  // n_eff
+    k.take<unsigned int>(max_teams);    // barrier counters
+    k.take<BSys>(count);
+    k.take<BTeam>(max_teams);
+    k.take<int>(max_ints);
+    k.take<double>(mu_total);
+  };
+  Carver probe(nullptr);
+  lay(probe, false);
+  tail(probe);
   int rc = ensure_ws(ctx, probe.used());
   if (rc != KITE_OK) return rc;
   Carver w(ctx->ws);
   lay(w, true);
   auto* ne = w.take<unsigned long long>(count);
-  auto* counters = w.take<unsigned int>(sc.teams.size());
+  auto* counters = w.take<unsigned int>(max_teams);
   auto* d_sys = w.take<BSys>(count);
-  auto* d_teams = w.take<BTeam>(sc.teams.size());
-  auto* d_ints = w.take<int>(sc.order.size() + sc.cta_team.size());
+  auto* d_teams = w.take<BTeam>(max_teams);
+  auto* d_ints = w.take<int>(max_ints);
   auto* d_mu = w.take<double>(mu_total);
 
   std::vector<BSys> hs(count);
@@ -293,56 +371,92 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
     mu_off[i] = mo;
     mo += (size_t)kpm[i].M;
   }
-  std::vector<int> ints(sc.order);
-  ints.insert(ints.end(), sc.cta_team.begin(), sc.cta_team.end());
   KITE_CUDA_TRY(ctx, cudaMemcpyAsync(d_sys, hs.data(), sizeof(BSys) * count, cudaMemcpyHostToDevice, st));
-  KITE_CUDA_TRY(ctx, cudaMemcpyAsync(d_teams, sc.teams.data(), sizeof(BTeam) * sc.teams.size(),
-                                     cudaMemcpyHostToDevice, st));
-  KITE_CUDA_TRY(ctx, cudaMemcpyAsync(d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, st));
-  KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));  // host vectors go out of scope below
+
+  // set-up kernels of every system (on-site draws and start vectors)
+  auto setup = [&]() -> cudaError_t {
+    cudaError_t ce = cudaMemsetAsync(ne, 0, sizeof(unsigned long long) * count, st);
+    for (int i = 0; i < count && ce == cudaSuccess; ++i) {
+      const int64_t ncell = (int64_t)sys[i].Lx * sys[i].Ly, N = ncell * SORB;
+      const double thr_d = floor(sys[i].p_vac * 4294967296.0);
+      const uint64_t vac_thr =
+          sys[i].p_vac <= 0.0 ? 0ull : (thr_d >= 4294967296.0 ? 4294967296ull : (uint64_t)thr_d);
+      const uint32_t k0 = (uint32_t)sys[i].seed, k1 = (uint32_t)(sys[i].seed >> 32);
+      const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->num_sms * 16);
+      k_onsite<float><<<std::max(1, blocks), 256, 0, st>>>(N, sys[i].lattice, sys[i].W, 0.5 * sys[i].delta,
+                                                           scales[i].de_plus, scales[i].de_minus, vac_thr, 0u,
+                                                           k0, k1, const_cast<float*>(hs[i].vt), ne + i);
+      k_init_r0<float, SORB, C><<<std::max(1, blocks), 256, 0, st>>>(ncell, hs[i].vt, 0, R, 0u, k0, k1,
+                                                                      nullptr, N, const_cast<void*>(hs[i].r0));
+      ce = cudaGetLastError();
+    }
+    return ce;
+  };
+  auto upload = [&](const BPlan& pl) -> int {
+    std::vector<int> ints(pl.sc.order);
+    ints.insert(ints.end(), pl.sc.cta_team.begin(), pl.sc.cta_team.end());
+    KITE_CUDA_TRY(ctx, cudaMemcpyAsync(d_teams, pl.sc.teams.data(), sizeof(BTeam) * pl.sc.teams.size(),
+                                       cudaMemcpyHostToDevice, st));
+    KITE_CUDA_TRY(ctx, cudaMemcpyAsync(d_ints, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, st));
+    KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));  // the host vectors go out of scope
+    return KITE_OK;
+  };
+
+  // ---- autotune: time every candidate on this batch with capped steps -------------------
+  int pick = (int)cands.size() - 1;  // untuned: 8 stages at full occupancy
+  if (tune && cands.size() > 1) {
+    double wmax = 0.0;
+    for (double x : work) wmax = std::max(wmax, x);
+    int b1 = 0, b2 = 0;
+    while ((double)(1ULL << (b1 + 1)) <= total) ++b1;
+    while ((double)(1ULL << (b2 + 1)) <= wmax) ++b2;
+    const uint64_t key = ((uint64_t)2 << 56) | ((uint64_t)LAT << 48) | ((uint64_t)C << 40) | ((uint64_t)DBL << 36) |
+                         ((uint64_t)std::min(count, 4095) << 20) | ((uint64_t)b1 << 10) | (uint64_t)b2;
+    auto it = ctx->tune.find(key);
+    bool found = false;
+    if (it != ctx->tune.end())
+      for (int c = 0; c < (int)cands.size(); ++c)
+        if (cands[c].nst == it->second.first && cands[c].k == it->second.second) pick = c, found = true;
+    if (!found) {
+      KITE_CUDA_TRY(ctx, setup());
+      const int mcap = DBL ? 4 : 8;
+      float best = 1e30f;
+      for (int c = 0; c < (int)cands.size(); ++c) {
+        if (upload(cands[c]) != KITE_OK) return KITE_ERR_CUDA;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up
+          KITE_CUDA_TRY(ctx, cudaMemsetAsync(counters, 0, sizeof(unsigned int) * cands[c].sc.teams.size(), st));
+          KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
+          cudaError_t ce = launch_batched<LAT, C, DBL>(ctx, cands[c], d_sys, d_teams, d_ints, counters, 0, mcap);
+          if (ce != cudaSuccess) return cuda_fail(ctx, ce, "autotune probe launch");
+          KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
+          KITE_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev3));
+          KITE_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev3));
+        }
+        // prefer the deeper ring and the default occupancy on near-ties
+        if (ms < best * 0.98f) best = ms, pick = c;
+      }
+      ctx->tune[key] = {cands[pick].nst, cands[pick].k};
+    }
+  }
+  const BPlan& pl = cands[pick];
+  if (upload(pl) != KITE_OK) return KITE_ERR_CUDA;
 
   // ---- capture the whole batch into one graph ----------------------------------------
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   KITE_CUDA_TRY(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  cudaError_t ce = cudaSuccess;
-  ce = cudaMemsetAsync(ne, 0, sizeof(unsigned long long) * count, st);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(counters, 0, sizeof(unsigned int) * sc.teams.size(), st);
+  cudaError_t ce = cudaMemsetAsync(counters, 0, sizeof(unsigned int) * pl.sc.teams.size(), st);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st);
-  for (int i = 0; i < count && ce == cudaSuccess; ++i) {
-    const int64_t ncell = (int64_t)sys[i].Lx * sys[i].Ly, N = ncell * SORB;
-    const double thr_d = floor(sys[i].p_vac * 4294967296.0);
-    const uint64_t vac_thr =
-        sys[i].p_vac <= 0.0 ? 0ull : (thr_d >= 4294967296.0 ? 4294967296ull : (uint64_t)thr_d);
-    const uint32_t k0 = (uint32_t)sys[i].seed, k1 = (uint32_t)(sys[i].seed >> 32);
-    const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->num_sms * 16);
-    k_onsite<float><<<std::max(1, blocks), 256, 0, st>>>(N, sys[i].lattice, sys[i].W, 0.5 * sys[i].delta,
-                                                         scales[i].de_plus, scales[i].de_minus, vac_thr,
-                                                         0u, k0, k1, const_cast<float*>(hs[i].vt), ne + i);
-    k_init_r0<float, SORB, C><<<std::max(1, blocks), 256, 0, st>>>(ncell, hs[i].vt, 0, R, 0u, k0, k1,
-                                                                    nullptr, N, const_cast<void*>(hs[i].r0));
-    ce = cudaGetLastError();
-  }
+  if (ce == cudaSuccess) ce = setup();
   if (ce == cudaSuccess) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(sc.grid);
-    cfg.blockDim = dim3(kBlock);
-    cfg.dynamicSmemBytes = SMEM;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
     const int stall = ctx->debug_stall;
     ctx->debug_stall = 0;
-    ce = cudaLaunchKernelEx(&cfg, k_batched<LAT, C, DBL>, (const BSys*)d_sys, (const BTeam*)d_teams,
-                            (const int*)d_ints, (const int*)(d_ints + sc.order.size()), counters,
-                            ctx->d_status, stall);
+    ce = launch_batched<LAT, C, DBL>(ctx, pl, d_sys, d_teams, d_ints, counters, stall, 0);
   }
   for (int i = 0; i < count && ce == cudaSuccess; ++i) {
     const int M = kpm[i].M;
-    k_breduce<<<(M + 255) / 256, 256, 0, st>>>(hs[i].partial, M, sc.ncta_of[i], Q, R, DBL ? 1 : 0, ne + i,
+    k_breduce<<<(M + 255) / 256, 256, 0, st>>>(hs[i].partial, M, pl.sc.ncta_of[i], Q, R, DBL ? 1 : 0, ne + i,
                                                d_mu + mu_off[i]);
     ce = cudaGetLastError();
   }
@@ -389,12 +503,14 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
     stats->updates = upd;
     stats->bytes_moved = bytes;
     stats->gbps = ms > 0 ? bytes / (1e-3 * ms) * 1e-9 : 0.0;
-    stats->grid = sc.grid;
+    stats->grid = pl.sc.grid;
     stats->block = kBlock;
     stats->step_seconds = 1e-3 * ms;
     stats->step_launches = 1;
     stats->step_bytes = bytes;
     stats->n_eff = (int64_t)ne_h[count - 1];
+    stats->ring_stages = pl.nst;
+    stats->ctas_per_sm = pl.k;
   }
   return KITE_OK;
 }
