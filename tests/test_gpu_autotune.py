@@ -1,6 +1,9 @@
 """The autotuner (ring depth x resident CTAs per SM) changes only how the sweep is laid on
-the GPU: the tuned and the default launch give the same moments to rounding (the FP64
-partial sums are added in a grid-dependent order), and the choice is reported."""
+the GPU: the tuned and the default launch give the same moments to rounding, and the
+choice is reported.  The grid decides which rows a thread's FP32 partial (at most 32
+rows) groups before the FP64 sums, so the two launches agree to FP32 regrouping error
+(bar 1e-7, far inside the 1e-5 bar against the oracle); a repeated launch with the cached
+choice is bit-identical."""
 import os
 
 import numpy as np
@@ -39,7 +42,7 @@ def test_tuned_sweep_matches_default(ctx, doubling):
     st_d = with_tuning("0", lambda: kite.moments_1d(ctx, s, kpm, mu_d))
     assert st_t.ring_stages in (4, 8) and st_t.ctas_per_sm >= 1
     assert st_d.ring_stages == 8
-    assert np.max(np.abs(mu_t - mu_d)) <= 1e-12
+    assert np.max(np.abs(mu_t - mu_d)) <= 1e-7
     st_again = with_tuning("1", lambda: kite.moments_1d(ctx, s, kpm, mu_d))  # cached choice
     assert (st_again.ring_stages, st_again.ctas_per_sm) == (st_t.ring_stages, st_t.ctas_per_sm)
     assert np.array_equal(mu_t, mu_d)  # same launch shape: bit-identical
@@ -56,4 +59,4 @@ def test_tuned_batch_matches_default(ctx):
         st_d = with_tuning("0", lambda: kite.moments_1d_batched(ctx, systems, kpms, mus_d))
         assert st_t.ring_stages in (4, 8) and st_t.ctas_per_sm >= 1 and st_d.ring_stages == 8
         for a, b in zip(mus_t, mus_d):
-            assert np.max(np.abs(a - b)) <= 1e-12
+            assert np.max(np.abs(a - b)) <= 1e-7
