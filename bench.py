@@ -244,7 +244,7 @@ def secondary_legs(kite, ctx, peaks):
         st = kite.moments_1d_batched(ctx, systems, kpms, mus)
         res[name] = {"updates_per_s": st.updates / st.seconds, "seconds": st.seconds,
                      "hbm_gbs": st.bytes_moved / st.seconds / 1e9, "grid": st.grid,
-                     "autotuned": {"ring_stages": st.ring_stages, "ctas_per_sm": st.ctas_per_sm}}
+                     "autotuned": {"ring_stages": st.ring_stages, "ctas_per_sm": st.ctas_per_sm, "steps_per_pass": st.steps_per_pass}}
     res["updates"] = st.updates
     out["batched_256_square_systems_R4_fp32_one_graph_launch"] = res
     # 2D Kubo-Bastin moments: honeycomb 1024x1024, W = 1, M = 1024, R = 4 (xx)
@@ -461,7 +461,7 @@ def main():
                            "l2": "inputs larger than L2 (three 2.1 GB vector buffers per step)",
                            "parallelism": f"{world} independent realisations" if world > 1 else "single GPU",
                            "grid": st.grid, "block": st.block,
-                           "autotuned": {"ring_stages": st.ring_stages, "ctas_per_sm": st.ctas_per_sm}},
+                           "autotuned": {"ring_stages": st.ring_stages, "ctas_per_sm": st.ctas_per_sm, "steps_per_pass": st.steps_per_pass}},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "moment_doubling": doubling, "real_vectors": realvec, "secondary": secondary,
                 "gpu_launches": launches_per_step * args.steps,

@@ -139,6 +139,9 @@ typedef struct {
   double gemm_flops;    /* 2D moments: tensor flops of the contraction (4 BF16 products) */
   int32_t ring_stages;  /* step kernel: shared-memory ring depth used (autotuned)       */
   int32_t ctas_per_sm;  /* step kernel: resident CTAs per SM used (autotuned)           */
+  int32_t steps_per_pass; /* step kernel: recursion steps fused per pass over the iterates
+                             (1, or 2 with temporal blocking; autotuned)                 */
+  int32_t reserved;
 } kite_stats;
 
 typedef struct kite_ctx kite_ctx;

@@ -63,7 +63,8 @@ class Stats(ctypes.Structure):
                 ("block", ctypes.c_int32), ("step_seconds", ctypes.c_double),
                 ("step_launches", ctypes.c_int64), ("step_bytes", ctypes.c_double),
                 ("gemm_seconds", ctypes.c_double), ("gemm_flops", ctypes.c_double),
-                ("ring_stages", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("ring_stages", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("steps_per_pass", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -15,12 +15,14 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "kite_device.cuh"
 #include "kite_internal.h"
 
 #include "kite_step.cuh"
+#include "kite_step2.cuh"
 
 namespace kite {
 namespace {
@@ -90,8 +92,8 @@ inline int steps_for(const Plan& p) { return p.doubling ? (p.M + 1) / 2 : p.M - 
 template <typename Real, int LAT, int C, int NST>
 int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, void* bA,
                 void* bB, double* partial, int G, long long units, int nvec, int vec_base,
-                const unsigned long long* n_eff, double* mu_vec, void** last_prev,
-                void** last_cur, double* step_seconds, int64_t* step_launches) {
+                const unsigned long long* n_eff, double* mu_vec, void** last_prev, void** last_cur,
+                double* step_seconds, int64_t* step_launches, double* step_bytes) {
   constexpr int VPC = Chunk<Real>::kVecs;
   constexpr int Q = 2 * C * VPC;
   cudaStream_t st = ctx->stream;
@@ -99,6 +101,10 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
   // r_0 lives in r0; r_n (n >= 1) lives in bA for odd n and in bB for even n, so
   // r_{n+1} overwrites r_{n-1} in place except at n = 1 (r_0 is kept for the moments).
   auto where = [&](int n) -> void* { return n == 0 ? r0 : ((n & 1) ? bA : bB); };
+  // algorithmic bytes of one launch: `vecs` iterate streams of the batch's chunks plus
+  // one read of the on-site term
+  const double chunk_bytes = 16.0 * StepShape<LAT, C, NST>::SORB * C * (double)p.ncell;
+  auto launch_bytes = [&](int vecs) { return vecs * chunk_bytes + (double)p.N * sizeof(Real); };
   KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
   constexpr int SM = StepShape<LAT, C, NST>::SMEM;
   if (p.doubling) {
@@ -128,6 +134,8 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
     KITE_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev3));
     *step_seconds += 1e-3 * ms;
     *step_launches += steps;
+    // doubling never re-reads r_0: r_{n-1}, r_n in, r_{n+1} out per later step
+    *step_bytes += (double)(steps - 1) * launch_bytes(3) + launch_bytes(2);
     *last_cur = *last_prev = nullptr;
     return KITE_OK;
   }
@@ -161,25 +169,129 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
     KITE_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev3));
     *step_seconds += 1e-3 * ms;
     *step_launches += M - 1;
+    *step_bytes += (double)(M - 2) * launch_bytes(4) + launch_bytes(2);
   }
   *last_cur = where(M - 1);
   *last_prev = where(M >= 2 ? M - 2 : 0);
   return KITE_OK;
 }
 
+// Temporal blocking of the plain moment sweep: after the first step, each pass takes
+// (r_{n-1}, r_n) to (r_{n+1}, r_{n+2}) and the moments n+1, n+2; an odd remainder takes one
+// plain step.  The first and remainder steps use the one-step kernel with a 4-slot ring on
+// the same grid (the partials of every moment have the same CTA count).
+template <typename Real, int LAT, int C, int NST2>
+int sweep_two(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, void* bA, void* bB,
+              void* bC, void* bD, double* partial, int G, long long units, int nvec, int vec_base,
+              const unsigned long long* n_eff, double* mu_vec, void** last_prev, void** last_cur,
+              double* step_seconds, int64_t* step_launches, double* step_bytes) {
+  constexpr int NST1 = 4;
+  constexpr int VPC = Chunk<Real>::kVecs;
+  constexpr int Q = 2 * C * VPC;
+  cudaStream_t st = ctx->stream;
+  const int M = p.M;
+  const double chunk_bytes = 16.0 * StepShape<LAT, C>::SORB * C * (double)p.ncell;
+  auto launch_bytes = [&](int vecs) { return vecs * chunk_bytes + (double)p.N * sizeof(Real); };
+  constexpr int SM = StepShape<LAT, C, NST1>::SMEM;
+  KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
+  // iterate k >= 1 lives in bufs[k mod 4]: a pass's outputs never alias its inputs
+  void* bufs[4] = {bC, bA, bB, bD};
+  auto w4 = [&](int n) -> void* { return n == 0 ? r0 : bufs[n & 3]; };
+  constexpr int SM2 = Step2Shape<LAT, C, NST2>::SMEM;
+  step_occupancy<Real, LAT, C, 0, NST1>();  // sets the kernels' shared-memory limits
+  step2_occupancy<Real, LAT, C, NST2>();
+  k_step<Real, LAT, C, true, 0, NST1><<<G, kBlock, SM, st>>>(nullptr, r0, w4(1), r0, vt, tt, p.Lx, p.Ly,
+                                                    units, partial + (size_t)G * Q, partial,
+                                                    ctx->d_status, ctx->debug_stall, FamOut{},
+                                                    p.realv ? 1 : 0);
+  ctx->debug_stall = 0;
+  int n = 1;
+  int64_t launches = 1;
+  double bytes = launch_bytes(2);  // r_0 in, r_1 out
+  for (; n + 2 <= M - 1; n += 2, ++launches) {
+    k_step2<Real, LAT, C, NST2><<<G, kBlock2, SM2, st>>>(
+        w4(n - 1), w4(n), w4(n + 1), w4(n + 2), r0, vt, tt, p.Lx, p.Ly, units,
+        partial + (size_t)(n + 1) * G * Q, partial + (size_t)(n + 2) * G * Q, ctx->d_status,
+        p.realv ? 1 : 0);
+    bytes += launch_bytes(5);  // r_{n-1}, r_n, r_0 in; r_{n+1}, r_{n+2} out
+  }
+  if (n + 1 <= M - 1) {
+    k_step<Real, LAT, C, false, 0, NST1><<<G, kBlock, SM, st>>>(
+        w4(n - 1), w4(n), w4(n + 1), r0, vt, tt, p.Lx, p.Ly, units, partial + (size_t)(n + 1) * G * Q,
+        nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0);
+    ++launches;
+    bytes += launch_bytes(4);
+  }
+  KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  const int total = M * Q;
+  k_reduce<<<(total + 255) / 256, 256, 0, st>>>(partial, M, G, Q, nvec, vec_base, n_eff, mu_vec,
+                                                 p.realv ? 1 : 0);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  float ms = 0.f;
+  KITE_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev3));
+  KITE_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev3));
+  *step_seconds += 1e-3 * ms;
+  *step_launches += launches;
+  *step_bytes += bytes;
+  *last_cur = w4(M - 1);
+  *last_prev = w4(M - 2);
+  return KITE_OK;
+}
+
 // ---- autotuner: ring depth x resident CTAs per SM ------------------------------------
-// Candidates are timed on the caller's own buffers (a few non-first steps between r_0
-// and the two iterate buffers, which the sweep overwrites afterwards) and the fastest is
-// cached per (precision, lattice, vectors per orbital, mode, size bucket) on the context.
-// KITE_AUTOTUNE=0 keeps the default (8 stages, full occupancy).
+// Candidates are timed on the caller's own buffers, which the sweep overwrites afterwards:
+// a few non-first steps from two iterate buffers with r_{n+1} written over r_{n-1} (the
+// sweep's four streams), and two-step passes from two iterate buffers into the other two.
+// The fastest per recursion step is cached per (precision, lattice, vectors per orbital,
+// mode, size bucket) on the context.  KITE_AUTOTUNE=0 keeps the default (8 stages, full
+// occupancy, one step per pass).
 struct Tune {
-  int nst;  // ring depth: 4 or 8
-  int k;    // resident CTAs per SM
+  int nst;       // ring depth: 4 or 8 (two-step pass: 4, 6 or 8)
+  int k;         // resident CTAs per SM
+  int two = 0;   // 1: two recursion steps per pass (temporal blocking)
 };
 
 inline bool autotune_enabled() {
   const char* e = getenv("KITE_AUTOTUNE");
   return !(e && e[0] == '0');
+}
+
+// KITE_PASS_STEPS=1 or 2 pins the steps per pass of the plain moment sweep (the autotuner
+// then chooses only the ring depth and occupancy); unset, both are candidates.
+inline int pass_steps_pinned() {
+  const char* e = getenv("KITE_PASS_STEPS");
+  return (e && (e[0] == '1' || e[0] == '2') && e[1] == 0) ? e[0] - '0' : 0;
+}
+
+template <typename Real, int LAT, int C, int NST>
+int step2_grid(kite_ctx* ctx, long long units, int ctas_per_sm = 0) {
+  const int occ = std::max(1, step2_occupancy<Real, LAT, C, NST>());
+  const int k = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+  return (int)std::max(1LL, std::min((long long)ctx->num_sms * k, units));
+}
+
+// Seconds per recursion step of the two-step pass: three launches = six steps.
+template <typename Real, int LAT, int C, int NST>
+float time_candidate2(kite_ctx* ctx, int k, long long units, const Plan& p, const Real* vt, Real tt,
+                      void* r0, void* bA, void* bB, void* bC, void* bD, double* partial) {
+  constexpr int SMEM = Step2Shape<LAT, C, NST>::SMEM;
+  constexpr int Q = 2 * C * Chunk<Real>::kVecs;
+  const int G = step2_grid<Real, LAT, C, NST>(ctx, units, k);
+  cudaStream_t st = ctx->stream;
+  auto launch = [&]() {
+    k_step2<Real, LAT, C, NST><<<G, kBlock2, SMEM, st>>>(bA, bB, bC, bD, r0, vt, tt, p.Lx, p.Ly, units,
+                                                        partial + (size_t)2 * G * Q, partial + (size_t)3 * G * Q,
+                                                        ctx->d_status, p.realv ? 1 : 0);
+  };
+  launch();  // warm-up
+  cudaEventRecord(ctx->ev2, st);
+  for (int i = 0; i < 3; ++i) launch();
+  cudaEventRecord(ctx->ev3, st);
+  float ms = 1e30f;
+  if (cudaEventSynchronize(ctx->ev3) != cudaSuccess || cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev3) != cudaSuccess)
+    return 1e30f;
+  return ms / 6.0f;
 }
 
 template <typename Real, int LAT, int C, int MODE, int NST>
@@ -190,8 +302,9 @@ float time_candidate(kite_ctx* ctx, int k, long long units, const Plan& p, const
   const int G = grid_for<Real, LAT, C, false, MODE, NST>(ctx, units, k);
   cudaStream_t st = ctx->stream;
   auto launch = [&]() {
+    // r_{n-1} = bA, r_n = bB, r_{n+1} over r_{n-1} in place, r_0 apart: the sweep's streams
     k_step<Real, LAT, C, false, MODE, NST><<<G, kBlock, SMEM, st>>>(
-        r0, bA, bB, MODE == 0 ? r0 : nullptr, vt, tt, p.Lx, p.Ly, units, partial + (size_t)2 * G * Q,
+        bA, bB, bA, MODE == 0 ? r0 : nullptr, vt, tt, p.Lx, p.Ly, units, partial + (size_t)2 * G * Q,
         MODE == 3 ? partial + (size_t)G * Q : nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0);
   };
   launch();  // warm-up
@@ -200,45 +313,84 @@ float time_candidate(kite_ctx* ctx, int k, long long units, const Plan& p, const
   cudaEventRecord(ctx->ev3, st);
   float ms = 1e30f;
   if (cudaEventSynchronize(ctx->ev3) != cudaSuccess || cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev3) != cudaSuccess)
-    ms = 1e30f;
-  return ms;
+    return 1e30f;
+  return ms / 3.0f;  // per recursion step
+}
+
+// The two-step pass is a candidate of the plain moment sweep (MODE 0) with enough moments
+// for at least one pass.
+template <int MODE>
+bool two_step_allowed(const Plan& p) {
+  return MODE == 0 && p.M >= 4 && pass_steps_pinned() != 1;
 }
 
 template <typename Real, int LAT, int C, int MODE>
 Tune autotune(kite_ctx* ctx, long long units, const Plan& p, const Real* vt, Real tt, void* r0, void* bA,
-              void* bB, double* partial) {
-  Tune def{kStages, step_occupancy<Real, LAT, C, MODE, kStages>()};
+              void* bB, void* bC, void* bD, double* partial) {
+  const bool two_ok = two_step_allowed<MODE>(p);
+  const bool two_only = two_ok && pass_steps_pinned() == 2;
+  Tune def{kStages, step_occupancy<Real, LAT, C, MODE, kStages>(), 0};
+  if (two_only) def = Tune{4, std::max(1, step2_occupancy<Real, LAT, C, 4>()), 1};
   if (!autotune_enabled() || units < 4LL * ctx->num_sms) return def;
   int bucket = 0;
   while ((1LL << (bucket + 1)) <= units) ++bucket;
   const uint64_t key = ((uint64_t)1 << 56) | ((uint64_t)sizeof(Real) << 48) | ((uint64_t)LAT << 40) |
-                       ((uint64_t)C << 32) | ((uint64_t)MODE << 24) | ((uint64_t)p.realv << 16) | (uint64_t)bucket;
+                       ((uint64_t)C << 32) | ((uint64_t)MODE << 24) | ((uint64_t)p.realv << 16) |
+                       ((uint64_t)(two_ok ? 1 + two_only : 0) << 20) | (uint64_t)bucket;
   auto it = ctx->tune.find(key);
-  if (it != ctx->tune.end()) return Tune{it->second.first, it->second.second};
+  if (it != ctx->tune.end()) return Tune{it->second.first & 0xff, it->second.second, it->second.first >> 8};
   Tune best = def;
   float best_ms = 1e30f;
-  const int o8 = step_occupancy<Real, LAT, C, MODE, 8>(), o4 = step_occupancy<Real, LAT, C, MODE, 4>();
-  for (int k = 1; k <= o8; ++k) {
-    const float ms = time_candidate<Real, LAT, C, MODE, 8>(ctx, k, units, p, vt, tt, r0, bA, bB, partial);
-    if (ms < best_ms) best_ms = ms, best = Tune{8, k};
+  if (!two_only) {
+    const int o8 = step_occupancy<Real, LAT, C, MODE, 8>(), o4 = step_occupancy<Real, LAT, C, MODE, 4>();
+    for (int k = 1; k <= o8; ++k) {
+      const float ms = time_candidate<Real, LAT, C, MODE, 8>(ctx, k, units, p, vt, tt, r0, bA, bB, partial);
+      if (ms < best_ms) best_ms = ms, best = Tune{8, k, 0};
+    }
+    for (int k = 1; k <= o4; ++k) {
+      const float ms = time_candidate<Real, LAT, C, MODE, 4>(ctx, k, units, p, vt, tt, r0, bA, bB, partial);
+      if (ms < best_ms * 0.98f) best_ms = ms, best = Tune{4, k, 0};  // prefer the deeper ring on a tie
+    }
   }
-  for (int k = 1; k <= o4; ++k) {
-    const float ms = time_candidate<Real, LAT, C, MODE, 4>(ctx, k, units, p, vt, tt, r0, bA, bB, partial);
-    if (ms < best_ms * 0.98f) best_ms = ms, best = Tune{4, k};  // prefer the deeper ring on a tie
+  if (two_ok) {
+    // per-step time of the pass against the one-step kernels' (the pass must win clearly:
+    // it needs two extra iterate buffers)
+    const float bar = two_only ? 1e30f : 0.97f * best_ms;
+    float best2 = bar;
+    const int o8 = step2_occupancy<Real, LAT, C, 8>(), o6 = step2_occupancy<Real, LAT, C, 6>(),
+              o4 = step2_occupancy<Real, LAT, C, 4>();
+    for (int k = 1; k <= o8; ++k) {
+      const float ms = time_candidate2<Real, LAT, C, 8>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
+      if (ms < best2) best2 = ms, best = Tune{8, k, 1};
+    }
+    for (int k = 1; k <= o6; ++k) {
+      const float ms = time_candidate2<Real, LAT, C, 6>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
+      if (ms < best2 * 0.98f) best2 = ms, best = Tune{6, k, 1};
+    }
+    for (int k = 1; k <= o4; ++k) {
+      const float ms = time_candidate2<Real, LAT, C, 4>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
+      if (ms < best2 * 0.98f) best2 = ms, best = Tune{4, k, 1};
+    }
   }
   cudaGetLastError();
-  ctx->tune[key] = {best.nst, best.k};
+  ctx->tune[key] = {best.nst | (best.two << 8), best.k};
   return best;
 }
 
 template <typename Real, int LAT, int MODE>
 int max_grid_c(kite_ctx* ctx, int C, long long units) {
-  auto g = [&](auto occ8, auto occ4) {
-    return (int)std::max(1LL, std::min((long long)ctx->num_sms * std::max(occ8, occ4), units));
+  auto g = [&](int occ) { return (int)std::max(1LL, std::min((long long)ctx->num_sms * occ, units)); };
+  auto occ = [&](auto cc) {
+    constexpr int CC = decltype(cc)::value;
+    int o = std::max(step_occupancy<Real, LAT, CC, MODE, 8>(), step_occupancy<Real, LAT, CC, MODE, 4>());
+    if (MODE == 0)
+      o = std::max({o, step2_occupancy<Real, LAT, CC, 8>(), step2_occupancy<Real, LAT, CC, 6>(),
+                    step2_occupancy<Real, LAT, CC, 4>()});
+    return o;
   };
-  if (C == 1) return g(step_occupancy<Real, LAT, 1, MODE, 8>(), step_occupancy<Real, LAT, 1, MODE, 4>());
-  if (C == 2) return g(step_occupancy<Real, LAT, 2, MODE, 8>(), step_occupancy<Real, LAT, 2, MODE, 4>());
-  return g(step_occupancy<Real, LAT, 4, MODE, 8>(), step_occupancy<Real, LAT, 4, MODE, 4>());
+  if (C == 1) return g(occ(std::integral_constant<int, 1>{}));
+  if (C == 2) return g(occ(std::integral_constant<int, 2>{}));
+  return g(occ(std::integral_constant<int, 4>{}));
 }
 
 template <typename Real, int LAT>
@@ -281,25 +433,30 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
   const size_t vec_bytes = (size_t)p.ncell * SORB * Cmax * 16;
   const size_t nvec_total = (size_t)p.R * p.S;
   Carver cv(nullptr);
-  auto plan_ws = [&](Carver& k, Real** vt, void** r0, void** bA, void** bB, double** partial,
-                     unsigned long long** ne, double** mu_vec) {
+  // two more iterate buffers when the two-step pass may run (its outputs never alias its
+  // inputs)
+  const bool two_possible = !p.doubling && p.M >= 4 && pass_steps_pinned() != 1;
+  auto plan_ws = [&](Carver& k, Real** vt, void** r0, void** bA, void** bB, void** bC, void** bD,
+                     double** partial, unsigned long long** ne, double** mu_vec) {
     *vt = k.take<Real>(p.N);
     *r0 = k.take<char>(vec_bytes);
     *bA = k.take<char>(vec_bytes);
     *bB = k.take<char>(vec_bytes);
+    *bC = two_possible ? k.take<char>(vec_bytes) : nullptr;
+    *bD = two_possible ? k.take<char>(vec_bytes) : nullptr;
     *partial = k.take<double>((size_t)(std::max(p.M, 2) + 1) * Gmax * 2 * Cmax * VPC);
     *ne = k.take<unsigned long long>(1);
     *mu_vec = k.take<double>(nvec_total * p.M * 2);
   };
   Real* vt;
-  void *r0, *bA, *bB;
+  void *r0, *bA, *bB, *bC, *bD;
   double *partial, *mu_vec;
   unsigned long long* ne;
-  plan_ws(cv, &vt, &r0, &bA, &bB, &partial, &ne, &mu_vec);
+  plan_ws(cv, &vt, &r0, &bA, &bB, &bC, &bD, &partial, &ne, &mu_vec);
   int rc = ensure_ws(ctx, cv.used());
   if (rc != KITE_OK) return rc;
   Carver real(ctx->ws);
-  plan_ws(real, &vt, &r0, &bA, &bB, &partial, &ne, &mu_vec);
+  plan_ws(real, &vt, &r0, &bA, &bB, &bC, &bD, &partial, &ne, &mu_vec);
   if (mu_vec_dev_ext) mu_vec = mu_vec_dev_ext;
 
   const Real tt = (Real)(sys->t / sc.de_minus);
@@ -344,40 +501,44 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
       }
       void *lp = nullptr, *lc = nullptr;
       const int vec_base = s * p.R + base;
-#define KITE_SWEEP(CC)                                                                       \
-  do {                                                                                       \
-    Tune t = p.doubling ? autotune<Real, LAT, CC, 3>(ctx, u, p, vt, tt, r0, bA, bB, partial)  \
-                        : autotune<Real, LAT, CC, 0>(ctx, u, p, vt, tt, r0, bA, bB, partial); \
-    const int G = t.nst == 4 ? (p.doubling ? grid_for<Real, LAT, CC, false, 3, 4>(ctx, u, t.k)   \
-                                           : grid_for<Real, LAT, CC, false, 0, 4>(ctx, u, t.k))  \
-                             : (p.doubling ? grid_for<Real, LAT, CC, false, 3, 8>(ctx, u, t.k)   \
-                                           : grid_for<Real, LAT, CC, false, 0, 8>(ctx, u, t.k)); \
-    grid_used = G;                                                                           \
-    tune_used = t;                                                                           \
-    rc = t.nst == 4 ? sweep_batch<Real, LAT, CC, 4>(ctx, p, vt, tt, r0, bA, bB, partial, G, u, nvec,  \
-                                                    vec_base, ne, mu_vec, &lp, &lc, &step_s, &step_n) \
-                    : sweep_batch<Real, LAT, CC, 8>(ctx, p, vt, tt, r0, bA, bB, partial, G, u, nvec,  \
-                                                    vec_base, ne, mu_vec, &lp, &lc, &step_s, &step_n); \
+#define KITE_SWEEP(CC)                                                                              \
+  do {                                                                                              \
+    Tune t = p.doubling ? autotune<Real, LAT, CC, 3>(ctx, u, p, vt, tt, r0, bA, bB, bC, bD, partial)  \
+                        : autotune<Real, LAT, CC, 0>(ctx, u, p, vt, tt, r0, bA, bB, bC, bD, partial); \
+    tune_used = t;                                                                                  \
+    if (t.two) {                                                                                    \
+      const int G = t.nst == 4   ? step2_grid<Real, LAT, CC, 4>(ctx, u, t.k)                        \
+                    : t.nst == 6 ? step2_grid<Real, LAT, CC, 6>(ctx, u, t.k)                        \
+                                 : step2_grid<Real, LAT, CC, 8>(ctx, u, t.k);                       \
+      grid_used = G;                                                                                \
+      auto run2 = [&](auto nst) {                                                                   \
+        return sweep_two<Real, LAT, CC, decltype(nst)::value>(ctx, p, vt, tt, r0, bA, bB, bC, bD,    \
+                                                               partial, G, u, nvec, vec_base, ne,    \
+                                                               mu_vec, &lp, &lc, &step_s, &step_n,   \
+                                                               &step_bytes);                         \
+      };                                                                                            \
+      rc = t.nst == 4   ? run2(std::integral_constant<int, 4>{})                                    \
+           : t.nst == 6 ? run2(std::integral_constant<int, 6>{})                                    \
+                        : run2(std::integral_constant<int, 8>{});                                   \
+    } else {                                                                                        \
+      const int G = t.nst == 4 ? (p.doubling ? grid_for<Real, LAT, CC, false, 3, 4>(ctx, u, t.k)      \
+                                             : grid_for<Real, LAT, CC, false, 0, 4>(ctx, u, t.k))     \
+                               : (p.doubling ? grid_for<Real, LAT, CC, false, 3, 8>(ctx, u, t.k)      \
+                                             : grid_for<Real, LAT, CC, false, 0, 8>(ctx, u, t.k));    \
+      grid_used = G;                                                                                \
+      rc = t.nst == 4 ? sweep_batch<Real, LAT, CC, 4>(ctx, p, vt, tt, r0, bA, bB, partial, G, u, nvec, \
+                                                      vec_base, ne, mu_vec, &lp, &lc, &step_s,       \
+                                                      &step_n, &step_bytes)                          \
+                      : sweep_batch<Real, LAT, CC, 8>(ctx, p, vt, tt, r0, bA, bB, partial, G, u, nvec, \
+                                                      vec_base, ne, mu_vec, &lp, &lc, &step_s,       \
+                                                      &step_n, &step_bytes);                         \
+    }                                                                                               \
   } while (0)
       if (C == 1) KITE_SWEEP(1);
       else if (C == 2) KITE_SWEEP(2);
       else KITE_SWEEP(4);
 #undef KITE_SWEEP
       if (rc != KITE_OK) return rc;
-      // algorithmic bytes of this batch's step launches: per orbital and step, read
-      // r_{n-1}, r_n, r_0 and write r_{n+1} for each of the batch's 16-byte chunks, and
-      // read the shared on-site term (the first step has no r_{n-1} and reads r_0 once)
-      if (p.doubling) {
-        // doubling never re-reads r_0: r_{n-1}, r_n in, r_{n+1} out per later step
-        const double chunk_bytes = 16.0 * SORB * C * (double)p.ncell;
-        const int steps = steps_for(p);
-        step_bytes += (double)(steps - 1) * (3.0 * chunk_bytes + (double)p.N * sizeof(Real)) +
-                      (2.0 * chunk_bytes + (double)p.N * sizeof(Real));
-      } else if (p.M >= 2) {
-        const double chunk_bytes = 16.0 * SORB * C * (double)p.ncell;
-        step_bytes += (double)(p.M - 2) * (4.0 * chunk_bytes + (double)p.N * sizeof(Real)) +
-                      (2.0 * chunk_bytes + (double)p.N * sizeof(Real));
-      }
       if (kpm->r_last && !p.doubling) {
         // extract into a device staging area or directly into a device destination
         const int64_t nchunk = p.ncell * SORB * C;
@@ -433,16 +594,17 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     stats->seconds = ms * 1e-3;
     stats->updates = (double)n_eff_last * p.M * p.R * p.S;
-    // algorithmic bytes per orbital and step: read r_{n-1}, r_n, r_0, write r_{n+1}
-    // for every vector, plus the shared on-site term
-    const double per_orb_step =
-        (p.doubling ? 3.0 : 4.0) * (p.realv ? 1.0 : 2.0) * sizeof(Real) * p.R + (double)sizeof(Real);
-    stats->bytes_moved = per_orb_step * (double)p.N * (double)steps_for(p) * p.S;
+    // algorithmic bytes of the step launches as scheduled: per launch, the iterate
+    // streams read and written (r_{n-1}, r_n, r_0 in and r_{n+1} out for a plain step;
+    // r_{n-1}, r_n, r_0 in and r_{n+1}, r_{n+2} out for a two-step pass; no r_0 with
+    // doubling) for each of the batch's 16-byte chunks, plus one read of the on-site term
+    stats->bytes_moved = step_bytes;
     stats->gbps = stats->seconds > 0 ? stats->bytes_moved / stats->seconds * 1e-9 : 0.0;
     stats->n_eff = n_eff_last;
     stats->grid = grid_used;
     stats->block = kBlock;
     stats->ring_stages = tune_used.nst;
+    stats->steps_per_pass = tune_used.two ? 2 : 1;
     stats->ctas_per_sm = grid_used / std::max(1, ctx->num_sms);
     stats->step_seconds = step_s;
     stats->step_launches = step_n;

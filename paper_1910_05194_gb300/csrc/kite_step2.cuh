@@ -1,0 +1,363 @@
+// kite_step2.cuh -- two recursion steps per pass (temporal blocking of the stencil sweep).
+//
+// From r_{n-1} and r_n one pass writes r_{n+1} = 2 H~ r_n - r_{n-1} and
+// r_{n+2} = 2 H~ r_{n+1} - r_n (Eq. e6) and accumulates <r_0|r_{n+1}> and <r_0|r_{n+2}>
+// (Eqs. e7/e8).  A CTA walks the rows of its share of a strip as in the one-step kernel;
+// while it computes row y of r_{n+1} it computes row y-1 of r_{n+2} from the three
+// r_{n+1} rows it keeps in shared memory.  r_{n+1} is therefore also computed on one
+// halo row above and below the CTA's rows and on one halo cell left and right of the
+// strip (redundantly: 2 of 34 cells, 2 of ~1700 rows), which needs r_n with a two-cell
+// halo.  Per orbital and pass the HBM traffic is r_{n-1}, r_n, r_0 in and r_{n+1},
+// r_{n+2} out: 5 vector reads/writes for two steps instead of 8.  The outputs go to two
+// buffers distinct from the inputs (the halo reads of neighbouring CTAs need r_n and
+// r_{n-1} unchanged during the pass).  Rounding sequence per site as in the one-step
+// kernel, so the iterates are bit-identical to two one-step launches.
+#pragma once
+
+#include "kite_step.cuh"
+
+namespace kite {
+namespace {
+
+template <int LAT, int C, int NST>
+struct Step2Shape {
+  using S1 = StepShape<LAT, C, NST>;
+  static constexpr int SORB = S1::SORB, TPC = S1::TPC, TX = S1::TX, CELLB = S1::CELLB;
+  static constexpr int RNB = (TX + 4) * CELLB;  // r_n row, two halo cells each side
+  static constexpr int RPB = (TX + 2) * CELLB;  // r_{n-1} row, one halo cell each side
+  static constexpr int R0B = TX * CELLB;        // r_0 row
+  static constexpr int STAGEB = RNB + RPB + R0B;
+  static constexpr int TILEB = (TX + 2) * CELLB;  // one r_{n+1} row of the tile ring
+  static constexpr int SMEM = kBarBytes + NST * STAGEB + 3 * TILEB;
+};
+
+// Threads: kBlock compute threads (one 16-byte chunk of an owned cell each, as in the
+// one-step kernel) and one more warp that computes the two halo cells of each r_{n+1} row
+// (left: tile cell 0, right: tile cell txv+1) and issues the bulk copies, so that the
+// compute warps carry equal work between the barriers.
+constexpr int kBlock2 = kBlock + 32;
+
+template <typename Real, int LAT, int C, int NST>
+__device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const void* __restrict__ r_prev,
+                                           const void* __restrict__ r_cur, void* __restrict__ out1,
+                                           void* __restrict__ out2, const void* __restrict__ r0,
+                                           const Real* __restrict__ vt, Real tt, int Lx, int Ly, long long units,
+                                           double* __restrict__ partial1, double* __restrict__ partial2,
+                                           int* __restrict__ err, int realv) {
+  using Ch = Chunk<Real>;
+  using Acc = typename AccT<Real>::T;
+  using Sh = Step2Shape<LAT, C, NST>;
+  constexpr int VPC = Ch::kVecs, NR = Ch::kReals;
+  constexpr int SORB = Sh::SORB, TPC = Sh::TPC, TX = Sh::TX, CELLB = Sh::CELLB;
+  constexpr int QT = 2 * VPC;
+  constexpr int kProducer = kBlock2 - 1;
+  uint64_t* bars = ring.bars;
+  unsigned char* stages = ring.stages;
+  unsigned char* tile = stages + NST * Sh::STAGEB;
+  int& s_abort = *ring.abort;
+
+  const int tid = threadIdx.x;
+  const bool compute = tid < kBlock;
+  // compute threads: owned cell xl; halo threads: halo cell hcell (0 left, 1 right)
+  const int hl = tid - kBlock;
+  const bool halo = !compute && hl < 2 * TPC;
+  const int xl = compute ? tid / TPC : 0;
+  const int hcell = halo ? hl / TPC : 0;
+  const int j = compute ? tid - xl * TPC : (halo ? hl - hcell * TPC : 0);
+  const int s = j / C;
+  const int c = j - s * C;
+  const int choff = (s * C + c) * 16;        // this thread's chunk inside a cell
+  const int nboff = ((1 - s) * C + c) * 16;  // same chunk, other sublattice
+
+  __syncthreads();
+
+  const long long u0 = units * (long long)cta / ncta;
+  const long long u1 = units * (long long)(cta + 1) / ncta;
+
+  double dacc1[QT], dacc2[QT];
+  Acc facc1[QT], facc2[QT];
+#pragma unroll
+  for (int k = 0; k < QT; ++k) dacc1[k] = dacc2[k] = 0.0, facc1[k] = facc2[k] = Acc(0);
+  int rows1 = 0, rows2 = 0;
+  long long gslot = ring.gslot;
+  bool aborted = false;
+
+  // periodic cell index; the copies below may start up to two cells left of the lattice
+  // and, on lattices narrower than the halo, wrap more than once
+  auto wrapx = [&](int x) {
+    x %= Lx;
+    return x < 0 ? x + Lx : x;
+  };
+  auto wrapy = [&](int y) { return y < 0 ? y + Ly : (y >= Ly ? y - Ly : y); };
+
+  for (long long u = u0; u < u1 && !aborted;) {
+    const int sx = (int)(u / Ly);
+    const int yb = (int)(u - (long long)sx * Ly);
+    const int nr = (int)min(u1 - u, (long long)(Ly - yb));
+    const int x0 = sx * TX;
+    const int txv = min(TX, Lx - x0);
+    const int nslots = nr + 4;  // r_n rows yb-2 .. yb+nr+1
+
+    // copies of `ncell` cells starting at global cell x (wrapped per cell when the run
+    // crosses the periodic boundary) into dst
+    auto copy_cells = [&](unsigned char* dst, const unsigned char* rowp, int x, int ncell, uint64_t* bar) {
+      int k = 0;
+      while (k < ncell) {
+        const int xs = wrapx(x + k);
+        int run = min(ncell - k, Lx - xs);
+        bulk_g2s(dst + (size_t)k * CELLB, rowp + (size_t)xs * CELLB, (uint32_t)run * CELLB, bar);
+        k += run;
+      }
+    };
+    auto issue = [&](int jj) {  // producer: slot for r_n row yb-2+jj
+      const long long g = gslot + jj;
+      const int st = (int)(g % NST);
+      unsigned char* base = stages + st * Sh::STAGEB;
+      int row = yb - 2 + jj;
+      while (row < 0) row += Ly;
+      while (row >= Ly) row -= Ly;
+      const bool need_prev = jj >= 1 && jj <= nr + 2;  // r_{n+1} rows yb-1 .. yb+nr
+      const bool need_r0 = jj >= 2 && jj <= nr + 1;    // owned rows
+      const uint32_t bytes = (uint32_t)(txv + 4) * CELLB + (need_prev ? (uint32_t)(txv + 2) * CELLB : 0u) +
+                             (need_r0 ? (uint32_t)txv * CELLB : 0u);
+      mbar_arrive_expect_tx(&bars[st], bytes);
+      const size_t roff = (size_t)row * Lx * CELLB;
+      copy_cells(base, static_cast<const unsigned char*>(r_cur) + roff, x0 - 2, txv + 4, &bars[st]);
+      if (need_prev)
+        copy_cells(base + Sh::RNB, static_cast<const unsigned char*>(r_prev) + roff, x0 - 1, txv + 2, &bars[st]);
+      if (need_r0)
+        bulk_g2s(base + Sh::RNB + Sh::RPB, static_cast<const unsigned char*>(r0) + roff + (size_t)x0 * CELLB,
+                 (uint32_t)txv * CELLB, &bars[st]);
+    };
+    if (tid == kProducer)
+      for (int jj = 0; jj < min(NST, nslots); ++jj) issue(jj);
+
+    // one r_{n+1} site: tile cell tx (global x0 - 1 + tx) of row y1 from the stages of
+    // rows y1-1, y1, y1+1 (up, mid, dn)
+    auto site1 = [&](const unsigned char* up, const unsigned char* mid, const unsigned char* dn, int tx,
+                     Real v) -> Ch {
+      const int si = tx + 1;  // index in the r_n stage (two halo cells on the left)
+      const Ch me = *reinterpret_cast<const Ch*>(mid + si * CELLB + choff);
+      Ch n1, n2, n3, n4;
+      if (LAT == KITE_HONEYCOMB) {
+        const unsigned char* other = s == 0 ? up : dn;
+        const int dxi = s == 0 ? si + 1 : si - 1;
+        n1 = *reinterpret_cast<const Ch*>(mid + si * CELLB + nboff);
+        n2 = *reinterpret_cast<const Ch*>(other + dxi * CELLB + nboff);
+        n3 = *reinterpret_cast<const Ch*>(other + si * CELLB + nboff);
+      } else {
+        n1 = *reinterpret_cast<const Ch*>(mid + (si - 1) * CELLB + choff);
+        n2 = *reinterpret_cast<const Ch*>(mid + (si + 1) * CELLB + choff);
+        n3 = *reinterpret_cast<const Ch*>(up + si * CELLB + choff);
+        n4 = *reinterpret_cast<const Ch*>(dn + si * CELLB + choff);
+      }
+      const Ch pv = *reinterpret_cast<const Ch*>(mid + Sh::RNB + tx * CELLB + choff);
+      const bool vacant = v != v;
+      Ch out;
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        Real sum = radd(n1.v[k], n2.v[k]);
+        sum = radd(sum, n3.v[k]);
+        if (LAT == KITE_SQUARE) sum = radd(sum, n4.v[k]);
+        const Real h = rfma(tt, sum, rmul(v, me.v[k]));
+        out.v[k] = vacant ? Real(0) : rfma(Real(2), h, -pv.v[k]);
+      }
+      return out;
+    };
+    // one r_{n+2} site of owned cell xl (tile cell xl+1) of row y2 from the tile rows
+    // y2-1, y2, y2+1 (tu, tm, td) and r_n of row y2 (stage mid2)
+    auto site2 = [&](const unsigned char* tu, const unsigned char* tm, const unsigned char* td,
+                     const unsigned char* mid2, Real v) -> Ch {
+      const int tx = xl + 1;
+      const Ch me = *reinterpret_cast<const Ch*>(tm + tx * CELLB + choff);
+      Ch n1, n2, n3, n4;
+      if (LAT == KITE_HONEYCOMB) {
+        const unsigned char* other = s == 0 ? tu : td;
+        const int dxi = s == 0 ? tx + 1 : tx - 1;
+        n1 = *reinterpret_cast<const Ch*>(tm + tx * CELLB + nboff);
+        n2 = *reinterpret_cast<const Ch*>(other + dxi * CELLB + nboff);
+        n3 = *reinterpret_cast<const Ch*>(other + tx * CELLB + nboff);
+      } else {
+        n1 = *reinterpret_cast<const Ch*>(tm + (tx - 1) * CELLB + choff);
+        n2 = *reinterpret_cast<const Ch*>(tm + (tx + 1) * CELLB + choff);
+        n3 = *reinterpret_cast<const Ch*>(tu + tx * CELLB + choff);
+        n4 = *reinterpret_cast<const Ch*>(td + tx * CELLB + choff);
+      }
+      const Ch pv = *reinterpret_cast<const Ch*>(mid2 + (tx + 1) * CELLB + choff);  // r_n, own cell
+      const bool vacant = v != v;
+      Ch out;
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        Real sum = radd(n1.v[k], n2.v[k]);
+        sum = radd(sum, n3.v[k]);
+        if (LAT == KITE_SQUARE) sum = radd(sum, n4.v[k]);
+        const Real h = rfma(tt, sum, rmul(v, me.v[k]));
+        out.v[k] = vacant ? Real(0) : rfma(Real(2), h, -pv.v[k]);
+      }
+      return out;
+    };
+    auto accumulate = [&](Acc(&facc)[QT], double(&dacc)[QT], int& rows, const Ch& z0, const Ch& out) {
+      if (realv) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) facc[k] += (Acc)z0.v[k] * (Acc)out.v[k];
+      } else {
+#pragma unroll
+        for (int q = 0; q < VPC; ++q) {
+          const Acc ar = z0.v[2 * q], ai = z0.v[2 * q + 1];
+          const Acc br = out.v[2 * q], bi = out.v[2 * q + 1];
+          facc[2 * q] += ar * br + ai * bi;
+          facc[2 * q + 1] += ar * bi - ai * br;
+        }
+      }
+      if (++rows == kFlushRows) {
+        rows = 0;
+#pragma unroll
+        for (int k = 0; k < QT; ++k) dacc[k] += (double)facc[k], facc[k] = Acc(0);
+      }
+    };
+
+    const bool active = compute && xl < txv;
+    // on-site terms prefetched one row ahead: the owned (or halo) cell of r_{n+1} row
+    // y1 = yb-1+i; r_{n+2} row y2 = y1-1 reuses the previous row's value
+    const int xv = active ? x0 + xl : (halo ? wrapx(x0 - 1 + (hcell ? txv + 1 : 0)) : 0);
+    const bool loads_v = active || halo;
+    const Real* vcol = vt + (size_t)xv * SORB + s;
+    const size_t vrow = (size_t)Lx * SORB;
+    auto vload = [&](int y) { return vcol[(size_t)wrapy(y) * vrow]; };
+    // this thread's chunk in the outputs: column offset + row * orow chunks
+    const size_t ocol = ((size_t)(x0 + xl) * SORB + s) * C + c;
+    const size_t orow = (size_t)Lx * SORB * C;
+    Real v1 = loads_v ? vload(yb - 1) : Real(0);
+    Real vprev = Real(0);
+    // stage of slot i (slots i, i+1, i+2 hold r_n rows y1-1, y1, y1+1) and tile rows of
+    // r_{n+1} rows y1-2, y1-1, y1
+    int st0 = (int)(gslot % NST);
+    // (tile rows rotate as byte offsets: pointers carried around the loop would hide
+    // from the compiler that they address shared memory)
+    int o0 = 0, o1 = Sh::TILEB, o2 = 2 * Sh::TILEB;
+    int i = 0;
+    for (; i < nr + 2; ++i) {
+      const Real v1n = (loads_v && i + 1 < nr + 2) ? vload(yb + i) : Real(0);
+      // r_{n+1} row y1 = yb-1+i needs r_n rows in slots i, i+1, i+2
+      bool ok = true;
+      if (compute || halo)
+        for (int jj = (i == 0 ? 0 : i + 2); jj <= i + 2; ++jj) {
+          const long long g = gslot + jj;
+          ok = mbar_wait_bounded_hint(&bars[g % NST], (uint32_t)((g / NST) & 1)) && ok;
+        }
+      if (!ok) s_abort = 1;
+      const int y1 = wrapy(yb - 1 + i);
+      const int st1 = st0 + 1 == NST ? 0 : st0 + 1;
+      const int st2 = st1 + 1 == NST ? 0 : st1 + 1;
+      const unsigned char* up = stages + st0 * Sh::STAGEB;
+      const unsigned char* mid = stages + st1 * Sh::STAGEB;
+      const unsigned char* dn = stages + st2 * Sh::STAGEB;
+      unsigned char* t2 = tile + o2;
+      if (ok && active) {  // own cell (tile cell xl+1)
+        const Ch o = site1(up, mid, dn, xl + 1, v1);
+        *reinterpret_cast<Ch*>(t2 + (xl + 1) * CELLB + choff) = o;
+        if (i >= 1 && i <= nr) {
+          o.st(out1, ocol + (size_t)y1 * orow);
+          const Ch z0 = *reinterpret_cast<const Ch*>(mid + Sh::RNB + Sh::RPB + xl * CELLB + choff);
+          accumulate(facc1, dacc1, rows1, z0, o);
+        }
+      }
+      if (ok && halo) {  // halo cell left (tile cell 0) or right (tile cell txv+1)
+        const int tx = hcell ? txv + 1 : 0;
+        *reinterpret_cast<Ch*>(t2 + tx * CELLB + choff) = site1(up, mid, dn, tx, v1);
+      }
+      __syncthreads();  // the r_{n+1} row is in the tile
+      if (s_abort) {
+        aborted = true;
+        break;
+      }
+      if (i >= 2 && active) {
+        // r_{n+2} row y2 = y1 - 1 from tile rows y1-2, y1-1, y1 and r_n row y2 (slot i)
+        const int y2 = y1 == 0 ? Ly - 1 : y1 - 1;
+        const Ch o = site2(tile + o0, tile + o1, t2, up, vprev);
+        o.st(out2, ocol + (size_t)y2 * orow);
+        const Ch z0 = *reinterpret_cast<const Ch*>(up + Sh::RNB + Sh::RPB + xl * CELLB + choff);
+        accumulate(facc2, dacc2, rows2, z0, o);
+      }
+      vprev = v1;
+      v1 = v1n;
+      st0 = st1;
+      const int of = o0;  // the oldest tile row takes the next r_{n+1} row
+      o0 = o1;
+      o1 = o2;
+      o2 = of;
+      __syncthreads();  // slot i and the oldest tile row are free
+      if (tid == kProducer && i + NST < nslots) issue(i + NST);
+    }
+    if (aborted) {
+      if (tid == kProducer) {
+        const int last = min(nslots, i + NST) - 1;
+        for (int jj = i; jj <= last; ++jj) {
+          const long long g = gslot + jj;
+          mbar_wait_bounded(&bars[g % NST], (uint32_t)((g / NST) & 1));
+        }
+        atomicExch(err, 1);
+      }
+      ring.gslot = gslot;
+      return false;
+    }
+    gslot += nslots;
+    u += nr;
+  }
+  ring.gslot = gslot;
+  // partial1 <- <r_0|r_{n+1}>, partial2 <- <r_0|r_{n+2}>: fixed-order sums over the compute
+  // threads holding each chunk (the ring is drained; its memory is reused)
+#pragma unroll
+  for (int k = 0; k < QT; ++k) dacc1[k] += (double)facc1[k], dacc2[k] += (double)facc2[k];
+  double(*red)[QT] = reinterpret_cast<double(*)[QT]>(stages);
+  constexpr int Q = C * QT;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (compute)
+#pragma unroll
+      for (int k = 0; k < QT; ++k) red[tid][k] = pass == 0 ? dacc1[k] : dacc2[k];
+    __syncthreads();
+    if (tid < Q) {
+      const int cc = tid / QT, k = tid - (tid / QT) * QT;
+      double sum = 0.0;
+      for (int t = cc; t < kBlock; t += C) sum += red[t][k];
+      (pass == 0 ? partial1 : partial2)[(size_t)cta * Q + tid] = sum;
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+template <typename Real, int LAT, int C, int NST>
+__global__ void __launch_bounds__(kBlock2, NST <= 4 ? 3 : 2)
+    k_step2(const void* r_prev, const void* __restrict__ r_cur, void* out1, void* out2,
+            const void* __restrict__ r0, const Real* __restrict__ vt, Real tt, int Lx, int Ly, long long units,
+            double* __restrict__ partial1, double* __restrict__ partial2, int* __restrict__ err, int realv) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_abort;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NST; ++k) mbar_init(&bars[k], 1);
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  Ring ring{bars, smem + kBarBytes, &s_abort, 0};
+  step2_body<Real, LAT, C, NST>(ring, blockIdx.x, gridDim.x, r_prev, r_cur, out1, out2, r0, vt, tt, Lx, Ly,
+                                units, partial1, partial2, err, realv);
+}
+
+template <typename Real, int LAT, int C, int NST>
+int step2_occupancy() {
+  static int occ = -1;
+  if (occ < 0) {
+    int o = 0;
+    const int smem = Step2Shape<LAT, C, NST>::SMEM;
+    cudaFuncSetAttribute(k_step2<Real, LAT, C, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_step2<Real, LAT, C, NST>, kBlock2, smem) != cudaSuccess)
+      o = 0;
+    occ = o;
+  }
+  return occ;
+}
+
+}  // namespace
+}  // namespace kite
