@@ -12,6 +12,11 @@
 // buffers distinct from the inputs (the halo reads of neighbouring CTAs need r_n and
 // r_{n-1} unchanged during the pass).  Rounding sequence per site as in the one-step
 // kernel, so the iterates are bit-identical to two one-step launches.
+//
+// Staging: the bulk-copy ring holds r_n (with the halo) and r_0 of each row; r_{n-1},
+// read once per site by the thread that owns it, is loaded from global memory into
+// registers one row ahead, which keeps the stages small enough for a ring of 4-6 rows at
+// three CTAs per SM.
 #pragma once
 
 #include "kite_step.cuh"
@@ -24,9 +29,8 @@ struct Step2Shape {
   using S1 = StepShape<LAT, C, NST>;
   static constexpr int SORB = S1::SORB, TPC = S1::TPC, TX = S1::TX, CELLB = S1::CELLB;
   static constexpr int RNB = (TX + 4) * CELLB;  // r_n row, two halo cells each side
-  static constexpr int RPB = (TX + 2) * CELLB;  // r_{n-1} row, one halo cell each side
   static constexpr int R0B = TX * CELLB;        // r_0 row
-  static constexpr int STAGEB = RNB + RPB + R0B;
+  static constexpr int STAGEB = RNB + R0B;      // (r_{n-1} is read once per site: registers)
   static constexpr int TILEB = (TX + 2) * CELLB;  // one r_{n+1} row of the tile ring
   static constexpr int SMEM = kBarBytes + NST * STAGEB + 3 * TILEB;
 };
@@ -116,26 +120,22 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
       int row = yb - 2 + jj;
       while (row < 0) row += Ly;
       while (row >= Ly) row -= Ly;
-      const bool need_prev = jj >= 1 && jj <= nr + 2;  // r_{n+1} rows yb-1 .. yb+nr
-      const bool need_r0 = jj >= 2 && jj <= nr + 1;    // owned rows
-      const uint32_t bytes = (uint32_t)(txv + 4) * CELLB + (need_prev ? (uint32_t)(txv + 2) * CELLB : 0u) +
-                             (need_r0 ? (uint32_t)txv * CELLB : 0u);
+      const bool need_r0 = jj >= 2 && jj <= nr + 1;  // owned rows
+      const uint32_t bytes = (uint32_t)(txv + 4) * CELLB + (need_r0 ? (uint32_t)txv * CELLB : 0u);
       mbar_arrive_expect_tx(&bars[st], bytes);
       const size_t roff = (size_t)row * Lx * CELLB;
       copy_cells(base, static_cast<const unsigned char*>(r_cur) + roff, x0 - 2, txv + 4, &bars[st]);
-      if (need_prev)
-        copy_cells(base + Sh::RNB, static_cast<const unsigned char*>(r_prev) + roff, x0 - 1, txv + 2, &bars[st]);
       if (need_r0)
-        bulk_g2s(base + Sh::RNB + Sh::RPB, static_cast<const unsigned char*>(r0) + roff + (size_t)x0 * CELLB,
+        bulk_g2s(base + Sh::RNB, static_cast<const unsigned char*>(r0) + roff + (size_t)x0 * CELLB,
                  (uint32_t)txv * CELLB, &bars[st]);
     };
     if (tid == kProducer)
       for (int jj = 0; jj < min(NST, nslots); ++jj) issue(jj);
 
     // one r_{n+1} site: tile cell tx (global x0 - 1 + tx) of row y1 from the stages of
-    // rows y1-1, y1, y1+1 (up, mid, dn)
+    // rows y1-1, y1, y1+1 (up, mid, dn) and r_{n-1} of the site (pv)
     auto site1 = [&](const unsigned char* up, const unsigned char* mid, const unsigned char* dn, int tx,
-                     Real v) -> Ch {
+                     Real v, const Ch& pv) -> Ch {
       const int si = tx + 1;  // index in the r_n stage (two halo cells on the left)
       const Ch me = *reinterpret_cast<const Ch*>(mid + si * CELLB + choff);
       Ch n1, n2, n3, n4;
@@ -151,7 +151,6 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         n3 = *reinterpret_cast<const Ch*>(up + si * CELLB + choff);
         n4 = *reinterpret_cast<const Ch*>(dn + si * CELLB + choff);
       }
-      const Ch pv = *reinterpret_cast<const Ch*>(mid + Sh::RNB + tx * CELLB + choff);
       const bool vacant = v != v;
       Ch out;
 #pragma unroll
@@ -229,6 +228,11 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
     const size_t orow = (size_t)Lx * SORB * C;
     Real v1 = loads_v ? vload(yb - 1) : Real(0);
     Real vprev = Real(0);
+    // r_{n-1} of the same cell, read straight from global memory one row ahead (it is
+    // used once, by this thread)
+    const size_t pcol = ((size_t)xv * SORB + s) * C + c;
+    auto pload = [&](int y) { return Ch::ldg(r_prev, pcol + (size_t)wrapy(y) * orow); };
+    Ch pv1 = loads_v ? pload(yb - 1) : Ch{};
     // stage of slot i (slots i, i+1, i+2 hold r_n rows y1-1, y1, y1+1) and tile rows of
     // r_{n+1} rows y1-2, y1-1, y1
     int st0 = (int)(gslot % NST);
@@ -238,6 +242,7 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
     int i = 0;
     for (; i < nr + 2; ++i) {
       const Real v1n = (loads_v && i + 1 < nr + 2) ? vload(yb + i) : Real(0);
+      const Ch pvn = (loads_v && i + 1 < nr + 2) ? pload(yb + i) : Ch{};
       // r_{n+1} row y1 = yb-1+i needs r_n rows in slots i, i+1, i+2
       bool ok = true;
       if (compute || halo)
@@ -254,17 +259,17 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
       const unsigned char* dn = stages + st2 * Sh::STAGEB;
       unsigned char* t2 = tile + o2;
       if (ok && active) {  // own cell (tile cell xl+1)
-        const Ch o = site1(up, mid, dn, xl + 1, v1);
+        const Ch o = site1(up, mid, dn, xl + 1, v1, pv1);
         *reinterpret_cast<Ch*>(t2 + (xl + 1) * CELLB + choff) = o;
         if (i >= 1 && i <= nr) {
           o.st(out1, ocol + (size_t)y1 * orow);
-          const Ch z0 = *reinterpret_cast<const Ch*>(mid + Sh::RNB + Sh::RPB + xl * CELLB + choff);
+          const Ch z0 = *reinterpret_cast<const Ch*>(mid + Sh::RNB + xl * CELLB + choff);
           accumulate(facc1, dacc1, rows1, z0, o);
         }
       }
       if (ok && halo) {  // halo cell left (tile cell 0) or right (tile cell txv+1)
         const int tx = hcell ? txv + 1 : 0;
-        *reinterpret_cast<Ch*>(t2 + tx * CELLB + choff) = site1(up, mid, dn, tx, v1);
+        *reinterpret_cast<Ch*>(t2 + tx * CELLB + choff) = site1(up, mid, dn, tx, v1, pv1);
       }
       __syncthreads();  // the r_{n+1} row is in the tile
       if (s_abort) {
@@ -276,11 +281,12 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         const int y2 = y1 == 0 ? Ly - 1 : y1 - 1;
         const Ch o = site2(tile + o0, tile + o1, t2, up, vprev);
         o.st(out2, ocol + (size_t)y2 * orow);
-        const Ch z0 = *reinterpret_cast<const Ch*>(up + Sh::RNB + Sh::RPB + xl * CELLB + choff);
+        const Ch z0 = *reinterpret_cast<const Ch*>(up + Sh::RNB + xl * CELLB + choff);
         accumulate(facc2, dacc2, rows2, z0, o);
       }
       vprev = v1;
       v1 = v1n;
+      pv1 = pvn;
       st0 = st1;
       const int of = o0;  // the oldest tile row takes the next r_{n+1} row
       o0 = o1;
@@ -328,7 +334,7 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
 }
 
 template <typename Real, int LAT, int C, int NST>
-__global__ void __launch_bounds__(kBlock2, NST <= 4 ? 3 : 2)
+__global__ void __launch_bounds__(kBlock2, 3 * Step2Shape<LAT, C, NST>::SMEM <= 227 * 1024 ? 3 : 2)
     k_step2(const void* r_prev, const void* __restrict__ r_cur, void* out1, void* out2,
             const void* __restrict__ r0, const Real* __restrict__ vt, Real tt, int Lx, int Ly, long long units,
             double* __restrict__ partial1, double* __restrict__ partial2, int* __restrict__ err, int realv) {
