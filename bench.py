@@ -129,20 +129,25 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+STEP_SOURCES = ("kite_kpm1d.cu", "kite_step.cuh", "kite_step2.cuh", "kite_device.cuh")
+
+
 def kernel_source_hash():
+    """Hash of the sources the 1D step kernels (one-step and two-step) are built from."""
     h = hashlib.sha1()
-    for fn in ("kite_kpm1d.cu", "kite_step.cuh", "kite_device.cuh"):
+    for fn in STEP_SOURCES:
         with open(os.path.join(ROOT, "paper_1910_05194_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(updates_per_launch: float):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, scaled
-    per update, if the kernel source still matches the one profiled (else None)."""
-    path = os.path.join(ROOT, "profiles", "kpm_step_traffic.json")
+def profiled_traffic(updates_per_launch: float, steps_per_pass: int):
+    """DRAM bytes per launch of the dominant step kernel (one-step, or the two-step pass)
+    from the committed ncu summary, scaled per update of the launch, if the kernel source
+    still matches the one profiled (else None)."""
+    name = "kpm_step2_traffic.json" if steps_per_pass == 2 else "kpm_step_traffic.json"
     try:
-        with open(path) as f:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             d = json.load(f)
     except Exception:
         return None
@@ -330,18 +335,26 @@ def main():
     ms = float(t_step.item())
     updates_per_step = float(st.n_eff) * M * R
     value = updates_per_step * world / (ms * 1e-3)
-    launches_per_step = 1 + 1 + (M - 1) + 1 + 1 + 2  # onsite, init, steps, reduce, average, dos x2
+    # onsite, init, recursion launches, reduce, average, dos x2
+    launches_per_step = 1 + 1 + step_n // args.steps + 1 + 1 + 2
     roofline = None
     if step_n > 0:
         peak, peak_kind = measured_peaks()
         achieved = step_bytes / step_s / 1e9
-        upd_per_launch = float(st.n_eff) * R
-        traffic = profiled_traffic(upd_per_launch)
+        two = st.steps_per_pass == 2
+        # updates of one launch: orbitals x vectors x recursion steps of the launch
+        upd_per_launch = float(st.n_eff) * R * (2 if two else 1)
+        traffic = profiled_traffic(upd_per_launch, st.steps_per_pass)
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": traffic,
-                    "kernel": "k_step<float, honeycomb, 4 chunks>",
+                    "kernel": ("k_step2<float, honeycomb, 4 chunks> (two recursion steps per pass)" if two
+                               else "k_step<float, honeycomb, 4 chunks>"),
                     "algorithmic_bytes_per_launch": step_bytes / step_n,
-                    "avg_launch_us": 1e6 * step_s / step_n, "peak_kind": peak_kind + " (copy test)"}
+                    "avg_launch_us": 1e6 * step_s / step_n, "peak_kind": peak_kind + " (copy test)",
+                    "note": ("a pass reads r_n-1, r_n, r_0 and writes r_n+1, r_n+2 (5 vector streams "
+                             "for 2 steps: 20.25 B/update at R=8, against 32.5 for one step per "
+                             "launch); frac is that smaller traffic over the copy peak" if two else
+                             "a step reads r_n-1, r_n, r_0 and writes r_n+1 (32.5 B/update at R=8)")}
 
     # ---- moment doubling on the same workload (two moments per recursion step) --------
     doubling = None

@@ -12,6 +12,7 @@
 // contiguous 512-byte stretches of a row; x runs fastest (the memory layout along
 // a1 used by the paper, Sec. 5).
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 
 #include <algorithm>
@@ -331,6 +332,20 @@ Tune autotune(kite_ctx* ctx, long long units, const Plan& p, const Real* vt, Rea
   const bool two_only = two_ok && pass_steps_pinned() == 2;
   Tune def{kStages, step_occupancy<Real, LAT, C, MODE, kStages>(), 0};
   if (two_only) def = Tune{4, std::max(1, step2_occupancy<Real, LAT, C, 4>()), 1};
+  // KITE_TUNE=<stages>x<CTAs per SM>[x2] pins one configuration (reproducible profiles):
+  // stages 4 or 8 (6 also for the two-step pass), x2 = the two-step pass
+  if (const char* e = getenv("KITE_TUNE")) {
+    int nst = 0, k = 0, two = 1;
+    if (sscanf(e, "%dx%dx%d", &nst, &k, &two) >= 2) {
+      const bool t2 = two == 2 && two_ok;
+      const int occ = t2 ? (nst == 4   ? step2_occupancy<Real, LAT, C, 4>()
+                            : nst == 6 ? step2_occupancy<Real, LAT, C, 6>()
+                            : nst == 8 ? step2_occupancy<Real, LAT, C, 8>() : 0)
+                         : (nst == 4   ? step_occupancy<Real, LAT, C, MODE, 4>()
+                            : nst == 8 ? step_occupancy<Real, LAT, C, MODE, 8>() : 0);
+      if (occ > 0 && k >= 1) return Tune{nst, std::min(k, occ), t2 ? 1 : 0};
+    }
+  }
   if (!autotune_enabled() || units < 4LL * ctx->num_sms) return def;
   int bucket = 0;
   while ((1LL << (bucket + 1)) <= units) ++bucket;
