@@ -90,6 +90,9 @@ typedef struct {
  *   r0         optional start vectors instead of random phases: [S*R][N] complex FP64,
  *              interleaved (re, im), host or device; entries on vacancies are ignored
  *              (the vacancy is removed from the Hilbert space).  NULL = random phases.
+ *              Page-locked host memory is read in place by the kernels (no copy);
+ *              pageable host memory is first copied to a context-owned device buffer.
+ *              The caller keeps r0 unchanged until the call returns.
  *   r_last     optional output: per vector the last two iterates (T_{M-2} r, T_{M-1} r)
  *              as [S*R][2][N] interleaved complex of the working precision (complex64
  *              for KITE_FP32, complex128 for KITE_FP64), host or device; for M = 1 both

@@ -107,6 +107,36 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+int device_view(kite_ctx* ctx, const void* p, size_t bytes, const void** out) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    a.type = cudaMemoryTypeUnregistered;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+    *out = p;
+    return KITE_OK;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+    *out = a.devicePointer;
+    return KITE_OK;
+  }
+  if (bytes > ctx->stage_bytes) {
+    KITE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->stage) cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    if (cudaMalloc(&ctx->stage, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, KITE_ERR_OOM, "staging buffer for caller start vectors");
+    }
+    ctx->stage_bytes = bytes;
+  }
+  KITE_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->stage, p, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  *out = ctx->stage;
+  return KITE_OK;
+}
+
 cudaError_t copy_in(kite_ctx* ctx, void* dst_dev, const void* src, size_t bytes) {
   return cudaMemcpyAsync(dst_dev, src, bytes, cudaMemcpyDefault, ctx->stream);
 }
@@ -273,6 +303,7 @@ void kite_destroy(kite_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->stage) cudaFree(ctx->stage);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->ev2) cudaEventDestroy(ctx->ev2);
@@ -336,18 +367,14 @@ int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   const int M = kpm->M;
   const size_t nvec = (size_t)kpm->R * kpm->S;
   const int64_t N = (int64_t)sys->Lx * sys->Ly * (sys->lattice == KITE_HONEYCOMB ? 2 : 1);
-  // Caller start vectors live in a separate allocation so the sweep's work space stays put.
+  // Caller start vectors: read in place (device or page-locked host memory) or staged in a
+  // buffer of their own, so the sweep's work space stays put.
   const double* r0_dev = nullptr;
-  void* r0_stage = nullptr;
   if (kpm->r0) {
-    if (is_device_ptr(kpm->r0)) {
-      r0_dev = kpm->r0;
-    } else {
-      const size_t bytes = nvec * (size_t)N * 2 * sizeof(double);
-      KITE_CUDA_TRY(ctx, cudaMallocAsync(&r0_stage, bytes, ctx->stream));
-      KITE_CUDA_TRY(ctx, copy_in(ctx, r0_stage, kpm->r0, bytes));
-      r0_dev = static_cast<const double*>(r0_stage);
-    }
+    const void* v = nullptr;
+    rc = device_view(ctx, kpm->r0, nvec * (size_t)N * 2 * sizeof(double), &v);
+    if (rc != KITE_OK) return rc;
+    r0_dev = static_cast<const double*>(v);
   }
   // outputs: device staging for mu, imag and per-vector moments
   double* out_dev = nullptr;
@@ -386,7 +413,6 @@ int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
     }
   }
   cudaFreeAsync(out_dev, ctx->stream);
-  if (r0_stage) cudaFreeAsync(r0_stage, ctx->stream);
   cudaStreamSynchronize(ctx->stream);
   if (st) *st = local;
   return rc;
@@ -674,16 +700,11 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   const size_t nvec = (size_t)kpm->R * kpm->S;
   const int64_t N = (int64_t)sys->Lx * sys->Ly * (sys->lattice == KITE_HONEYCOMB ? 2 : 1);
   const double* r0_dev = nullptr;
-  void* r0_stage = nullptr;
   if (kpm->r0) {
-    if (is_device_ptr(kpm->r0)) {
-      r0_dev = kpm->r0;
-    } else {
-      const size_t bytes = nvec * (size_t)N * 2 * sizeof(double);
-      KITE_CUDA_TRY(ctx, cudaMallocAsync(&r0_stage, bytes, ctx->stream));
-      KITE_CUDA_TRY(ctx, copy_in(ctx, r0_stage, kpm->r0, bytes));
-      r0_dev = static_cast<const double*>(r0_stage);
-    }
+    const void* v = nullptr;
+    rc = device_view(ctx, kpm->r0, nvec * (size_t)N * 2 * sizeof(double), &v);
+    if (rc != KITE_OK) return rc;
+    r0_dev = static_cast<const double*>(v);
   }
   const bool out_d = is_device_ptr(mu_nm);
   double* out_dev = mu_nm;
@@ -696,7 +717,6 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
     if (e != cudaSuccess) rc = cuda_fail(ctx, e, "copying mu_nm");
   }
   if (!out_d) cudaFreeAsync(out_dev, ctx->stream);
-  if (r0_stage) cudaFreeAsync(r0_stage, ctx->stream);
   cudaError_t es = cudaStreamSynchronize(ctx->stream);
   if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "moments_2d");
   local.e_min = sc.e_min;

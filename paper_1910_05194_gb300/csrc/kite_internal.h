@@ -22,6 +22,9 @@ struct kite_ctx {
   // Small pinned host staging area (moments, status words).
   void* pinned = nullptr;
   size_t pinned_bytes = 0;
+  // Device copy of pageable caller start vectors (grows on demand, freed at destroy).
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
   // Device status word: kernels set it (never trap) when a bounded wait gives up.
   int* d_status = nullptr;
@@ -43,6 +46,11 @@ int ensure_pinned(kite_ctx* ctx, size_t bytes);
 
 // True if p is device (or managed) memory of the current device.
 bool is_device_ptr(const void* p);
+
+// Device-side view of `bytes` of caller input: device memory as it is; page-locked host
+// memory through its mapped device address (kernels read it across the host link, no
+// copy); pageable host memory copied into the context's staging buffer on its stream.
+int device_view(kite_ctx* ctx, const void* p, size_t bytes, const void** out);
 
 // Copies `bytes` between caller memory (host or device) and device memory on the
 // context stream.
