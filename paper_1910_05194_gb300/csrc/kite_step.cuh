@@ -200,43 +200,56 @@ __device__ __forceinline__ void fam_store(const FamOut& f, int v, int row, int64
   *reinterpret_cast<__nv_bfloat162*>(f.lo[v] + idx) = __halves2bfloat162(l0, l1);
 }
 
-// CTA reduction of the per-thread moment partials in fixed order (the ring is drained, so
-// its memory is reused): lane (vector v = c*VPC + q, component) sums the threads holding
-// chunk c, in thread order.
+// Fixed-order CTA sums of per-thread FP64 partials, per 16-byte chunk c = tid % C of the
+// kBlock compute threads: a butterfly over the lanes of each warp that hold the same
+// chunk (offsets 16 .. C; both partners form the same sum, so every lane agrees), then
+// the kBlock/32 warp sums added in warp order.  Threads tid < C*QT write
+// out[c*QT + k].  Every thread of the CTA calls it (it synchronises once); `in_warp` is
+// false for whole warps that hold no partials.  `red` is free shared scratch of
+// (kBlock/32)*C*QT doubles.  The short dependency chain (log2(32/C) + kBlock/32 adds
+// instead of kBlock/C) matters for small systems, where a launch covers one row per CTA.
+template <int QT, int C>
+__device__ __forceinline__ void cta_lane_sums(const double (&d)[QT], bool in_warp, double* red, double* out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (in_warp) {
+    double v[QT];
+#pragma unroll
+    for (int k = 0; k < QT; ++k) v[k] = d[k];
+#pragma unroll
+    for (int off = 16; off >= C; off >>= 1)
+#pragma unroll
+      for (int k = 0; k < QT; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    if (lane < C)
+#pragma unroll
+      for (int k = 0; k < QT; ++k) red[(warp * C + lane) * QT + k] = v[k];
+  }
+  __syncthreads();
+  if (tid < C * QT) {
+    const int cc = tid / QT, k = tid - (tid / QT) * QT;
+    double sum = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) sum += red[(w * C + cc) * QT + k];
+    out[tid] = sum;
+  }
+}
+
+// CTA reduction of the per-thread moment partials (the ring is drained, so its memory is
+// reused): lane (vector v = c*VPC + q, component) of `partial` for this CTA.
 template <int QT, int C, typename Acc>
 __device__ __forceinline__ void moment_partials(double (&dacc)[QT], Acc (&facc)[QT],
                                                 double (&dacc0)[QT], Acc (&facc0)[QT], bool first,
                                                 unsigned char* stages, double* partial,
                                                 double* partial0, int cta) {
-  const int tid = threadIdx.x;
 #pragma unroll
   for (int k = 0; k < QT; ++k) {
     dacc[k] += (double)facc[k];
     if (first) dacc0[k] += (double)facc0[k];
   }
-
-  double(*red)[QT] = reinterpret_cast<double(*)[QT]>(stages);
+  double* red = reinterpret_cast<double*>(stages);
   constexpr int Q = C * QT;
-#pragma unroll
-  for (int k = 0; k < QT; ++k) red[tid][k] = dacc[k];
-  __syncthreads();
-  if (tid < Q) {
-    const int cc = tid / QT, k = tid - (tid / QT) * QT;
-    double sum = 0.0;
-    for (int t = cc; t < kBlock; t += C) sum += red[t][k];
-    partial[(size_t)cta * Q + tid] = sum;
-  }
+  cta_lane_sums<QT, C>(dacc, true, red, partial + (size_t)cta * Q);
   if (first) {
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < QT; ++k) red[tid][k] = dacc0[k];
-    __syncthreads();
-    if (tid < Q) {
-      const int cc = tid / QT, k = tid - (tid / QT) * QT;
-      double sum = 0.0;
-      for (int t = cc; t < kBlock; t += C) sum += red[t][k];
-      partial0[(size_t)cta * Q + tid] = sum;
-    }
+    cta_lane_sums<QT, C>(dacc0, true, red, partial0 + (size_t)cta * Q);
   }
 }
 

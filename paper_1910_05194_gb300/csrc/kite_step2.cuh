@@ -312,24 +312,15 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
   }
   ring.gslot = gslot;
   // partial1 <- <r_0|r_{n+1}>, partial2 <- <r_0|r_{n+2}>: fixed-order sums over the compute
-  // threads holding each chunk (the ring is drained; its memory is reused)
+  // threads holding each chunk, as in the one-step kernel (the ring is drained; its
+  // memory is reused)
 #pragma unroll
   for (int k = 0; k < QT; ++k) dacc1[k] += (double)facc1[k], dacc2[k] += (double)facc2[k];
-  double(*red)[QT] = reinterpret_cast<double(*)[QT]>(stages);
+  double* red = reinterpret_cast<double*>(stages);
   constexpr int Q = C * QT;
-  for (int pass = 0; pass < 2; ++pass) {
-    if (compute)
-#pragma unroll
-      for (int k = 0; k < QT; ++k) red[tid][k] = pass == 0 ? dacc1[k] : dacc2[k];
-    __syncthreads();
-    if (tid < Q) {
-      const int cc = tid / QT, k = tid - (tid / QT) * QT;
-      double sum = 0.0;
-      for (int t = cc; t < kBlock; t += C) sum += red[t][k];
-      (pass == 0 ? partial1 : partial2)[(size_t)cta * Q + tid] = sum;
-    }
-    __syncthreads();
-  }
+  cta_lane_sums<QT, C>(dacc1, compute, red, partial1 + (size_t)cta * Q);
+  __syncthreads();
+  cta_lane_sums<QT, C>(dacc2, compute, red, partial2 + (size_t)cta * Q);
   return true;
 }
 
