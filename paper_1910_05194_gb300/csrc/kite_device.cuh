@@ -195,6 +195,17 @@ __device__ __forceinline__ bool mbar_wait_bounded_hint(uint64_t* bar, uint32_t p
   }
 }
 
+// Programmatic dependent launch (sm_90+): a kernel launched with programmatic stream
+// serialisation may be scheduled while its predecessor on the stream still runs; it must
+// wait here, before it reads or writes any memory the predecessor touches, until that grid
+// has completed and its writes are visible.  In a kernel launched the ordinary way the wait
+// returns at once.  launch_dependents lets the successor be scheduled as soon as every CTA
+// of this grid has passed it (it then waits in griddep_wait, on the hardware).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Element (row, k) of a split-BF16 vector family stored K-blocked: the 64 K columns of one
 // block for all `rows` rows are contiguous ([K/64][rows][64]), so a TMA box of 64 columns
 // by 128 or 256 rows is one contiguous run of memory instead of rows spread Kp apart.

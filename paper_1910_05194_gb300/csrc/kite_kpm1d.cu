@@ -113,16 +113,15 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
     // step 0: r_1 = H~ r_0 with <r_0|r_0> -> slot 0 and <r_0|r_1> -> slot 1; step n >= 1
     // (r_{n+1} from r_n, r_{n-1}): <r_n|r_n> -> slot 2n, <r_n|r_{n+1}> -> slot 2n+1
     const int steps = steps_for(p);
-    k_step<Real, LAT, C, true, 3, NST><<<G, kBlock, SMD, st>>>(nullptr, r0, bA, nullptr, vt, tt, p.Lx,
-                                                         p.Ly, units, partial + (size_t)G * Q,
-                                                         partial, ctx->d_status,
-                                                         ctx->debug_stall, FamOut{}, p.realv ? 1 : 0);
+    launch_pdl(k_step<Real, LAT, C, true, 3, NST>, G, kBlock, SMD, st,
+        nullptr, r0, bA, nullptr, vt, tt, p.Lx, p.Ly, units,
+        partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
     ctx->debug_stall = 0;
     for (int n = 1; n < steps; ++n)
-      k_step<Real, LAT, C, false, 3, NST><<<G, kBlock, SMD, st>>>(
+      launch_pdl(k_step<Real, LAT, C, false, 3, NST>, G, kBlock, SMD, st,
           where(n - 1), where(n), where(n + 1), nullptr, vt, tt, p.Lx, p.Ly, units,
-          partial + (size_t)(2 * n + 1) * G * Q, partial + (size_t)(2 * n) * G * Q, ctx->d_status,
-          0, FamOut{}, p.realv ? 1 : 0);
+          partial + (size_t)(2 * n + 1) * G * Q,
+          partial + (size_t)(2 * n) * G * Q, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
     KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
     KITE_CUDA_TRY(ctx, cudaGetLastError());
     const int total = M * Q;
@@ -141,23 +140,22 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
     return KITE_OK;
   }
   if (M >= 2)
-    k_step<Real, LAT, C, true, 0, NST><<<G, kBlock, SM, st>>>(nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly,
-                                                      units, partial + (size_t)G * Q, partial,
-                                                      ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0);
+    launch_pdl(k_step<Real, LAT, C, true, 0, NST>, G, kBlock, SM, st,
+        nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly, units,
+        partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
   ctx->debug_stall = 0;
   for (int n = 1; n + 1 < M; ++n)
-    k_step<Real, LAT, C, false, 0, NST><<<G, kBlock, SM, st>>>(where(n - 1), where(n), where(n + 1), r0,
-                                                       vt, tt, p.Lx, p.Ly, units,
-                                                       partial + (size_t)(n + 1) * G * Q, nullptr,
-                                                       ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0);
+    launch_pdl(k_step<Real, LAT, C, false, 0, NST>, G, kBlock, SM, st,
+        where(n - 1), where(n), where(n + 1), r0, vt, tt, p.Lx, p.Ly, units,
+        partial + (size_t)(n + 1) * G * Q, nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
   KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
   KITE_CUDA_TRY(ctx, cudaGetLastError());
   if (M == 1) {
     // mu_0 alone: one FIRST pass would also write r_1; a plain dot is enough, but the
     // FIRST kernel is cheap and keeps one code path.
-    k_step<Real, LAT, C, true, 0, NST><<<G, kBlock, SM, st>>>(nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly,
-                                                      units, partial + (size_t)G * Q, partial,
-                                                      ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0);
+    launch_pdl(k_step<Real, LAT, C, true, 0, NST>, G, kBlock, SM, st,
+        nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly, units,
+        partial + (size_t)G * Q, partial, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
     KITE_CUDA_TRY(ctx, cudaGetLastError());
   }
   const int total = M * Q;
@@ -201,25 +199,24 @@ int sweep_two(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, v
   constexpr int SM2 = Step2Shape<LAT, C, NST2>::SMEM;
   step_occupancy<Real, LAT, C, 0, NST1>();  // sets the kernels' shared-memory limits
   step2_occupancy<Real, LAT, C, NST2>();
-  k_step<Real, LAT, C, true, 0, NST1><<<G, kBlock, SM, st>>>(nullptr, r0, w4(1), r0, vt, tt, p.Lx, p.Ly,
-                                                    units, partial + (size_t)G * Q, partial,
-                                                    ctx->d_status, ctx->debug_stall, FamOut{},
-                                                    p.realv ? 1 : 0);
+  launch_pdl(k_step<Real, LAT, C, true, 0, NST1>, G, kBlock, SM, st,
+      nullptr, r0, w4(1), r0, vt, tt, p.Lx, p.Ly, units,
+      partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
   ctx->debug_stall = 0;
   int n = 1;
   int64_t launches = 1;
   double bytes = launch_bytes(2);  // r_0 in, r_1 out
   for (; n + 2 <= M - 1; n += 2, ++launches) {
-    k_step2<Real, LAT, C, NST2><<<G, kBlock2, SM2, st>>>(
+    launch_pdl(k_step2<Real, LAT, C, NST2>, G, kBlock2, SM2, st,
         w4(n - 1), w4(n), w4(n + 1), w4(n + 2), r0, vt, tt, p.Lx, p.Ly, units,
-        partial + (size_t)(n + 1) * G * Q, partial + (size_t)(n + 2) * G * Q, ctx->d_status,
-        p.realv ? 1 : 0);
+        partial + (size_t)(n + 1) * G * Q,
+        partial + (size_t)(n + 2) * G * Q, ctx->d_status, p.realv ? 1 : 0);
     bytes += launch_bytes(5);  // r_{n-1}, r_n, r_0 in; r_{n+1}, r_{n+2} out
   }
   if (n + 1 <= M - 1) {
-    k_step<Real, LAT, C, false, 0, NST1><<<G, kBlock, SM, st>>>(
-        w4(n - 1), w4(n), w4(n + 1), r0, vt, tt, p.Lx, p.Ly, units, partial + (size_t)(n + 1) * G * Q,
-        nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0);
+    launch_pdl(k_step<Real, LAT, C, false, 0, NST1>, G, kBlock, SM, st,
+        w4(n - 1), w4(n), w4(n + 1), r0, vt, tt, p.Lx, p.Ly, units,
+        partial + (size_t)(n + 1) * G * Q, nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
     ++launches;
     bytes += launch_bytes(4);
   }
@@ -281,9 +278,9 @@ float time_candidate2(kite_ctx* ctx, int k, long long units, const Plan& p, cons
   const int G = step2_grid<Real, LAT, C, NST>(ctx, units, k);
   cudaStream_t st = ctx->stream;
   auto launch = [&]() {
-    k_step2<Real, LAT, C, NST><<<G, kBlock2, SMEM, st>>>(bA, bB, bC, bD, r0, vt, tt, p.Lx, p.Ly, units,
-                                                        partial + (size_t)2 * G * Q, partial + (size_t)3 * G * Q,
-                                                        ctx->d_status, p.realv ? 1 : 0);
+    launch_pdl(k_step2<Real, LAT, C, NST>, G, kBlock2, SMEM, st,
+        bA, bB, bC, bD, r0, vt, tt, p.Lx, p.Ly, units, partial + (size_t)2 * G * Q,
+        partial + (size_t)3 * G * Q, ctx->d_status, p.realv ? 1 : 0);
   };
   launch();  // warm-up
   cudaEventRecord(ctx->ev2, st);
@@ -304,9 +301,9 @@ float time_candidate(kite_ctx* ctx, int k, long long units, const Plan& p, const
   cudaStream_t st = ctx->stream;
   auto launch = [&]() {
     // r_{n-1} = bA, r_n = bB, r_{n+1} over r_{n-1} in place, r_0 apart: the sweep's streams
-    k_step<Real, LAT, C, false, MODE, NST><<<G, kBlock, SMEM, st>>>(
+    launch_pdl(k_step<Real, LAT, C, false, MODE, NST>, G, kBlock, SMEM, st,
         bA, bB, bA, MODE == 0 ? r0 : nullptr, vt, tt, p.Lx, p.Ly, units, partial + (size_t)2 * G * Q,
-        MODE == 3 ? partial + (size_t)G * Q : nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0);
+        MODE == 3 ? partial + (size_t)G * Q : nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
   };
   launch();  // warm-up
   cudaEventRecord(ctx->ev2, st);

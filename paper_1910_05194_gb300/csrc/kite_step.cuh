@@ -9,6 +9,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "kite_device.cuh"
 #include "kite_internal.h"
@@ -545,8 +546,29 @@ __global__ void __launch_bounds__(kBlock, 2)
     s_abort = 0;
   }
   Ring ring{bars, smem + kBarBytes, &s_abort, 0};
+  griddep_wait();  // the previous step's iterates and partials are complete
+  griddep_launch_dependents();
   step_body<Real, LAT, C, FIRST, MODE, NST>(ring, blockIdx.x, gridDim.x, r_prev, r_cur, r_out, r0, vt,
                                        tt, Lx, Ly, units, partial, partial0, err, stall, fam, realv, ser);
+}
+
+// Launch with programmatic stream serialisation: the kernel's set-up overlaps the end of
+// its predecessor on the stream (the step kernels call griddep_wait before any memory
+// access).  Arguments are converted to the kernel's parameter types.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // Copies one iterate buffer (batch layout) into the caller layout [vec][slot][N].

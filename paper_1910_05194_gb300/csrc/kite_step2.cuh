@@ -338,6 +338,8 @@ __global__ void __launch_bounds__(kBlock2, 3 * Step2Shape<LAT, C, NST>::SMEM <= 
     s_abort = 0;
   }
   Ring ring{bars, smem + kBarBytes, &s_abort, 0};
+  griddep_wait();  // the previous launch's iterates and partials are complete
+  griddep_launch_dependents();
   step2_body<Real, LAT, C, NST>(ring, blockIdx.x, gridDim.x, r_prev, r_cur, out1, out2, r0, vt, tt, Lx, Ly,
                                 units, partial1, partial2, err, realv);
 }
