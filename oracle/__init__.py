@@ -55,13 +55,19 @@ def build(force: bool = False) -> str:
 class System(ctypes.Structure):
     """Mirror of ``orc_system``: a periodic honeycomb or square lattice with disorder."""
     _fields_ = [("lattice", ctypes.c_int32), ("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32),
-                ("pad_", ctypes.c_int32), ("t", ctypes.c_double), ("W", ctypes.c_double),
+                ("disorder", ctypes.c_int32), ("t", ctypes.c_double), ("W", ctypes.c_double),
                 ("delta", ctypes.c_double), ("p_vac", ctypes.c_double),
                 ("seed", ctypes.c_uint64)]
 
 
-def make_system(lattice=HONEYCOMB, Lx=8, Ly=8, t=-2.7, W=0.0, delta=0.0, p_vac=0.0, seed=1):
-    return System(int(lattice), int(Lx), int(Ly), 0, float(t), float(W), float(delta),
+UNIFORM, GAUSSIAN = 0, 1
+
+
+def make_system(lattice=HONEYCOMB, Lx=8, Ly=8, t=-2.7, W=0.0, delta=0.0, p_vac=0.0, seed=1,
+                disorder=UNIFORM):
+    """W is the width of uniform disorder in [-W/2, W/2], or the standard deviation of
+    Gaussian disorder (disorder=GAUSSIAN)."""
+    return System(int(lattice), int(Lx), int(Ly), int(disorder), float(t), float(W), float(delta),
                   float(p_vac), int(seed))
 
 

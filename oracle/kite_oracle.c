@@ -66,6 +66,33 @@ static void orc_draw(const orc_system* sys, uint64_t o, uint32_t word2, uint32_t
   orc_philox4x32_10(ctr, key, out);
 }
 
+/* Largest |z| a Gaussian draw below can take: u1 >= 2^-53, so
+ * |z| <= sqrt(-2 ln 2^-53) = sqrt(106 ln 2) = 8.5717...; bounds use 8.58. */
+#define ORC_GAUSS_ZMAX 8.58
+
+/* On-site energy of orbital o from its disorder draw x (Sec. 4b: Anderson disorder,
+ * uniform in [-W/2, W/2]; the Python interface of Sec. 3d also offers Gaussian disorder
+ * with a mean and a standard deviation).  Gaussian: the Box-Muller transform of the
+ * 53-bit uniform u1 = 1 - u (in (0, 1]) and the 32-bit uniform u2 of the fourth word,
+ * z = sqrt(-2 ln u1) cos(2 pi u2), V = W z.  The staggered term adds +delta/2 on A and
+ * -delta/2 on B (a sublattice mean).  The third word decides vacancies. */
+static double orc_onsite(const orc_system* sys, int64_t o, const uint32_t x[4]) {
+  double u = orc_u53(x);
+  double v;
+  if (sys->disorder == 1) {
+    double u1 = 1.0 - u;
+    double u2 = (double)x[3] * 0x1p-32;
+    v = sys->W * (sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+  } else {
+    v = sys->W * (u - 0.5);
+  }
+  if (sys->lattice == 0 && sys->delta != 0.0) {
+    double half = 0.5 * sys->delta;
+    v = v + ((o & 1) == 0 ? half : -half);
+  }
+  return v;
+}
+
 /* ------------------------------------------------------------------------------ */
 /* Lattice geometry (Listing 1 of Sec. 3d: honeycomb with a1=[a,0], a2=[a/2,a*sqrt3/2], */
 /* A at [0,-acc/2], B at [0,acc/2], hoppings (0,0) A-B, (1,-1) A-B, (0,-1) A-B).       */
@@ -142,19 +169,21 @@ int orc_neighbours(const orc_system* sys, int64_t o, int64_t nb[4]) {
 /* Spectral bounds.  The paper rescales H into [-1,1] with the endpoints of the
  * spectrum (Eqs. rescalingH/rescalingE) and warns that estimated endpoints can be
  * wrong (Sec. 4b).  Gershgorin's theorem gives a rigorous enclosure:
- * |E| <= Z|t| + max|V|, with max|V| = W/2 + |delta|/2; a 1% margin is added. */
+ * |E| <= Z|t| + max|V|, with max|V| = W/2 + |delta|/2 (uniform) or
+ * ORC_GAUSS_ZMAX W + |delta|/2 (Gaussian: the largest draw the transform can give);
+ * a 1% margin is added. */
 void orc_bounds_auto(const orc_system* sys, double* e_min, double* e_max) {
   double Z = sys->lattice == 0 ? 3.0 : 4.0;
-  double vmax = 0.5 * fabs(sys->W) + (sys->lattice == 0 ? 0.5 * fabs(sys->delta) : 0.0);
+  double vd = sys->disorder == 1 ? ORC_GAUSS_ZMAX * fabs(sys->W) : 0.5 * fabs(sys->W);
+  double vmax = vd + (sys->lattice == 0 ? 0.5 * fabs(sys->delta) : 0.0);
   double b = (Z * fabs(sys->t) + vmax) * 1.01;
   *e_min = -b;
   *e_max = b;
 }
 
-/* On-site energies and vacancies for one disorder realisation.  Anderson disorder
- * is uniform in [-W/2, W/2] (Sec. 4b); the staggered term adds +delta/2 on A and
- * -delta/2 on B.  A vacancy removes the orbital (Sec. 3a: defects as position
- * lists); here each orbital is vacant with probability p_vac. */
+/* On-site energies and vacancies for one disorder realisation (orc_onsite).  A vacancy
+ * removes the orbital (Sec. 3a: defects as position lists); here each orbital is vacant
+ * with probability p_vac. */
 void orc_disorder(const orc_system* sys, int realisation, double* V, uint8_t* vac) {
   int64_t N = orc_norb(sys);
   double thr_d = floor(sys->p_vac * 4294967296.0);
@@ -162,13 +191,7 @@ void orc_disorder(const orc_system* sys, int realisation, double* V, uint8_t* va
   for (int64_t o = 0; o < N; ++o) {
     uint32_t x[4];
     orc_draw(sys, (uint64_t)o, (uint32_t)realisation, ORC_TAG_DISORDER, x);
-    double u = orc_u53(x);
-    double v = sys->W * (u - 0.5);
-    if (sys->lattice == 0 && sys->delta != 0.0) {
-      double half = 0.5 * sys->delta;
-      v = v + ((o & 1) == 0 ? half : -half);
-    }
-    V[o] = v;
+    V[o] = orc_onsite(sys, o, x);
     vac[o] = ((uint64_t)x[2] < thr) ? 1 : 0;
   }
 }
@@ -781,11 +804,7 @@ int orc_replica_window(const orc_system* sys, int realisation, int M, int R, dou
         gidx[l] = o;
         uint32_t x[4];
         orc_draw(sys, (uint64_t)o, (uint32_t)realisation, ORC_TAG_DISORDER, x);
-        double v = sys->W * (orc_u53(x) - 0.5);
-        if (sys->lattice == 0 && sys->delta != 0.0) {
-          double hd = 0.5 * sys->delta;
-          v = v + (s == 0 ? hd : -hd);
-        }
+        double v = orc_onsite(sys, o, x);
         vac[l] = ((uint64_t)x[2] < thr) ? 1 : 0;
         vt[l] = (v - de_plus) / de_minus;
         for (int r = 0; r < R; ++r) {

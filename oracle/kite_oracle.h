@@ -26,9 +26,9 @@ extern "C" {
 typedef struct {
   int32_t lattice;   /* 0 = honeycomb (Listing 1), 1 = square                          */
   int32_t Lx, Ly;    /* unit cells along a1 and a2                                      */
-  int32_t pad_;
+  int32_t disorder;  /* 0: uniform (Anderson) in [-W/2, W/2]; 1: Gaussian, mean 0, s.d. W */
   double t;          /* nearest-neighbour hopping (eV)                                  */
-  double W;          /* Anderson on-site disorder, uniform in [-W/2, W/2] (eV)          */
+  double W;          /* on-site disorder strength (eV): uniform width or Gaussian s.d.   */
   double delta;      /* staggered potential +delta/2 on A, -delta/2 on B (eV)          */
   double p_vac;      /* per-orbital vacancy probability                                 */
   uint64_t seed;

@@ -25,7 +25,10 @@ MUTATIONS = [
     ("conjugation dropped in <a|b>",
      "si += a[2 * o] * b[2 * o + 1] - a[2 * o + 1] * b[2 * o];",
      "si += a[2 * o] * b[2 * o + 1] + a[2 * o + 1] * b[2 * o];"),
-    ("disorder not centred", "double v = sys->W * (u - 0.5);", "double v = sys->W * u;"),
+    ("disorder not centred", "v = sys->W * (u - 0.5);", "v = sys->W * u;"),
+    ("Gaussian variance halved", "sqrt(-2.0 * log(u1))", "sqrt(-log(u1))"),
+    ("Gaussian angle from the radius word", "(double)x[3] * 0x1p-32", "(double)x[0] * 0x1p-32"),
+    ("Gaussian bound too tight", "#define ORC_GAUSS_ZMAX 8.58", "#define ORC_GAUSS_ZMAX 5.0"),
     ("velocity loses its sign", "double w = off[4 * o + k] * h->tt;",
      "double w = fabs(off[4 * o + k]) * h->tt;"),
     ("y bond offset sign", "dy[1] = 0.5 * acc;", "dy[1] = -0.5 * acc;"),

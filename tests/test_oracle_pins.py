@@ -98,6 +98,51 @@ def test_disorder_distribution_and_vacancies():
     assert np.all(oracle.disorder(sys1)[1] == 1)
 
 
+def test_gaussian_disorder_distribution_and_bound():
+    """Gaussian disorder (the Python interface's 'Gaussian' kind, Sec. 3d): V ~ N(0, W^2)
+    +/- delta/2 per sublattice: mean, variance and kurtosis of 131k draws within their
+    sampling errors, normal quantiles within a few per cent, every draw inside the
+    transform's largest value sqrt(106 ln 2) W, vacancies as for uniform disorder, and
+    the Gershgorin bounds built from that largest value."""
+    W, delta, p = 0.7, 0.4, 0.03
+    sys = oracle.make_system(Lx=256, Ly=256, W=W, delta=delta, p_vac=p, seed=12,
+                             disorder=oracle.GAUSSIAN)
+    V, vac = oracle.disorder(sys)
+    for v in (V[0::2] - delta / 2, V[1::2] + delta / 2):
+        n = v.size
+        z = v / W
+        assert abs(z.mean()) < 5 / math.sqrt(n)
+        assert abs(z.var() - 1.0) < 5 * math.sqrt(2.0 / n)
+        assert abs(np.mean(z ** 4) / z.var() ** 2 - 3.0) < 5 * math.sqrt(24.0 / n)
+        # P(|z| < 1) = erf(1/sqrt 2) = 0.6826895, P(|z| < 2) = 0.9544997
+        assert abs(np.mean(np.abs(z) < 1.0) - 0.6826895) < 0.01
+        assert abs(np.mean(np.abs(z) < 2.0) - 0.9544997) < 0.005
+        assert np.max(np.abs(z)) <= math.sqrt(106 * math.log(2))
+    assert abs(vac.mean() - p) < 5 * math.sqrt(p * (1 - p) / V.size)
+    lo, hi = oracle.bounds_auto(sys)
+    assert abs(hi - (3 * 2.7 + 8.58 * W + delta / 2) * 1.01) < 1e-12 and lo == -hi
+    # same seed, uniform kind: the same vacancies (third word), other on-site values
+    Vu, vacu = oracle.disorder(oracle.make_system(Lx=256, Ly=256, W=W, delta=delta, p_vac=p, seed=12))
+    assert np.array_equal(vacu, vac) and not np.allclose(Vu, V)
+
+
+def test_gaussian_disorder_enters_the_second_moment():
+    """Exact trace with Gaussian disorder (no vacancies): mu_2 = 2 Tr(H~^2)/N - 1 with
+    Tr(H~^2)/N = 3 t~^2 + <V~^2>, and <V^2> within its sampling error of W^2 + delta^2/4."""
+    W, delta = 0.9, 0.3
+    sys = oracle.make_system(Lx=8, Ly=6, W=W, delta=delta, seed=13, disorder=oracle.GAUSSIAN)
+    n = oracle.norb(sys)
+    lo, hi = oracle.bounds_auto(sys)
+    mu = oracle.moments_1d(sys, 3, n, r0=np.eye(n, dtype=np.complex128)).real.sum(0)
+    V, _ = oracle.disorder(sys)
+    tt = 2.7 / hi
+    assert abs(mu[0] - 1.0) < 1e-12 and abs(mu[1] - np.mean(V) / hi) < 1e-12
+    assert abs(mu[2] - (2 * (3 * tt * tt + np.mean((V / hi) ** 2)) - 1)) < 1e-12
+    big, _ = oracle.disorder(oracle.make_system(Lx=256, Ly=256, W=W, delta=delta, seed=14,
+                                                disorder=oracle.GAUSSIAN))
+    assert abs(np.mean(big ** 2) - (W * W + delta * delta / 4)) < 5 * W * W * math.sqrt(2.0 / big.size) + 0.01
+
+
 def test_random_phase_is_white_noise():
     """|xi| = 1 off vacancies, 0 on them; <xi> = 0, <xi xi> = 0, <|xi|^2> = 1 (Sec. 2c)."""
     sys = oracle.make_system(Lx=64, Ly=64, p_vac=0.02, seed=3)
