@@ -43,6 +43,8 @@ extern "C" {
 /* ---- enums -------------------------------------------------------------------- */
 #define KITE_HONEYCOMB 0 /* Listing 1: a1=[a,0], a2=[a/2, a sqrt3/2], two orbitals A, B   */
 #define KITE_SQUARE 1    /* one orbital per cell, four nearest neighbours               */
+#define KITE_DISORDER_UNIFORM 0
+#define KITE_DISORDER_GAUSSIAN 1
 
 #define KITE_FP32 0 /* complex FP32 recursion, FP64 moment accumulation above 32 terms */
 #define KITE_FP64 1 /* complex FP64 recursion                                           */
@@ -59,19 +61,25 @@ extern "C" {
  *   lattice  KITE_HONEYCOMB or KITE_SQUARE
  *   Lx, Ly   unit cells along a1, a2 (>= 1); boundaries are periodic in both
  *   t        nearest-neighbour hopping (eV)
- *   W        Anderson on-site disorder, V_o uniform in [-W/2, W/2] (eV), >= 0
+ *   disorder KITE_DISORDER_UNIFORM (Anderson, Sec. 4b) or KITE_DISORDER_GAUSSIAN (the
+ *            'Gaussian' kind of the Python interface, Sec. 3d)
+ *   W        on-site disorder strength (eV), >= 0: V_o uniform in [-W/2, W/2], or
+ *            Gaussian with mean 0 and standard deviation W
  *   delta    staggered potential: +delta/2 on A, -delta/2 on B (honeycomb only, eV)
  *   p_vac    probability that an orbital is a vacancy (removed with its bonds), [0,1]
  *   seed     key of the Philox4x32-10 counter-based generator that draws V_o, the
  *            vacancies and the random-phase vectors.  Realisation s, orbital o:
  *            counter (o_lo, o_hi, s, 1); vector v of realisation s: (o_lo, o_hi,
  *            s*R + v, 2).  u = (w0 * 2^21 + (w1 >> 11)) * 2^-53,
- *            V_o = W*(u - 1/2) [+- delta/2], vacant iff w2 < floor(p_vac * 2^32),
- *            phase vector entry exp(2 pi i u) (0 on vacancies). */
+ *            V_o = W*(u - 1/2) [+- delta/2] (uniform) or
+ *            V_o = W*(sqrt(-2 ln(1 - u)) * cos(2 pi w3 2^-32)) [+- delta/2] (Gaussian,
+ *            Box-Muller; |V_o - mean| <= sqrt(106 ln 2) W < 8.58 W), vacant iff
+ *            w2 < floor(p_vac * 2^32), phase vector entry exp(2 pi i u) (0 on
+ *            vacancies). */
 typedef struct {
   int32_t lattice;
   int32_t Lx, Ly;
-  int32_t reserved;
+  int32_t disorder;
   double t;
   double W;
   double delta;
@@ -86,7 +94,7 @@ typedef struct {
  *   S          disorder realisations (>= 1)
  *   precision  KITE_FP32 or KITE_FP64
  *   e_min, e_max  spectrum endpoints in eV; both 0 selects the Gershgorin enclosure
- *              +-(Z|t| + W/2 + |delta|/2) * 1.01 (kite_bounds)
+ *              +-(Z|t| + max|V - mean| + |delta|/2) * 1.01 (kite_bounds)
  *   r0         optional start vectors instead of random phases: [S*R][N] complex FP64,
  *              interleaved (re, im), host or device; entries on vacancies are ignored
  *              (the vacancy is removed from the Hilbert space).  NULL = random phases.
@@ -171,8 +179,9 @@ const char* kite_status_string(int status);
 const char* kite_last_error(const kite_ctx* ctx);
 
 /* Gershgorin spectrum enclosure used when e_min = e_max = 0 (Eqs. rescalingH/E and the
- * bound warning of Sec. 4b): e_max = -e_min = (Z|t| + W/2 + |delta|/2) * 1.01 with
- * Z = 3 (honeycomb) or 4 (square).  Host-only arithmetic in FP64.
+ * bound warning of Sec. 4b): e_max = -e_min = (Z|t| + Vmax + |delta|/2) * 1.01 with
+ * Z = 3 (honeycomb) or 4 (square) and Vmax = W/2 (uniform) or 8.58 W (Gaussian: the
+ * largest value its transform can give).  Host-only arithmetic in FP64.
  * Errors: KITE_ERR_ARG. */
 int kite_bounds(const kite_system* sys, double* e_min, double* e_max);
 

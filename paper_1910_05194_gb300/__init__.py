@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libkite_gb.so")
 OK = 0
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_BOUNDS, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 HONEYCOMB, SQUARE = 0, 1
+DISORDER_UNIFORM, DISORDER_GAUSSIAN = 0, 1
 FP32, FP64 = 0, 1
 KERNEL_NONE, KERNEL_JACKSON, KERNEL_LORENTZ = 0, 1, 2
 DIR_X, DIR_Y = 0, 1
@@ -42,7 +43,7 @@ class KiteError(RuntimeError):
 class System(ctypes.Structure):
     """``kite_system``: periodic honeycomb/square lattice with disorder."""
     _fields_ = [("lattice", ctypes.c_int32), ("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("t", ctypes.c_double), ("W", ctypes.c_double),
+                ("disorder", ctypes.c_int32), ("t", ctypes.c_double), ("W", ctypes.c_double),
                 ("delta", ctypes.c_double), ("p_vac", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
@@ -85,8 +86,11 @@ class MLPTrainCfg(ctypes.Structure):
                 ("weight_decay", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
-def make_system(lattice=HONEYCOMB, Lx=64, Ly=64, t=-2.7, W=0.0, delta=0.0, p_vac=0.0, seed=1):
-    return System(int(lattice), int(Lx), int(Ly), 0, float(t), float(W), float(delta),
+def make_system(lattice=HONEYCOMB, Lx=64, Ly=64, t=-2.7, W=0.0, delta=0.0, p_vac=0.0, seed=1,
+                disorder=0):
+    """W: width of uniform disorder in [-W/2, W/2] (disorder=DISORDER_UNIFORM) or standard
+    deviation of Gaussian disorder (disorder=DISORDER_GAUSSIAN)."""
+    return System(int(lattice), int(Lx), int(Ly), int(disorder), float(t), float(W), float(delta),
                   float(p_vac), int(seed))
 
 

@@ -385,7 +385,8 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
       const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->num_sms * 16);
       k_onsite<float><<<std::max(1, blocks), 256, 0, st>>>(N, sys[i].lattice, sys[i].W, 0.5 * sys[i].delta,
                                                            scales[i].de_plus, scales[i].de_minus, vac_thr, 0u,
-                                                           k0, k1, const_cast<float*>(hs[i].vt), ne + i);
+                                                           k0, k1, const_cast<float*>(hs[i].vt), ne + i,
+                                                           sys[i].disorder);
       k_init_r0<float, SORB, C><<<std::max(1, blocks), 256, 0, st>>>(ncell, hs[i].vt, 0, R, 0u, k0, k1,
                                                                       nullptr, N, const_cast<void*>(hs[i].r0));
       ce = cudaGetLastError();

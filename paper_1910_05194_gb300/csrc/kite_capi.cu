@@ -156,12 +156,16 @@ static int validate_system(kite_ctx* ctx, const kite_system* s) {
   if (!isfinite(s->t) || !isfinite(s->W) || !isfinite(s->delta) || s->W < 0.0)
     return fail(ctx, KITE_ERR_ARG, "t, W, delta must be finite and W >= 0");
   if (!(s->p_vac >= 0.0 && s->p_vac <= 1.0)) return fail(ctx, KITE_ERR_ARG, "p_vac outside [0,1]");
+  if (s->disorder != KITE_DISORDER_UNIFORM && s->disorder != KITE_DISORDER_GAUSSIAN)
+    return fail(ctx, KITE_ERR_ARG, "disorder must be KITE_DISORDER_UNIFORM or KITE_DISORDER_GAUSSIAN");
   return KITE_OK;
 }
 
 static void gershgorin(const kite_system* s, double* lo, double* hi) {
   const double Z = s->lattice == KITE_HONEYCOMB ? 3.0 : 4.0;
-  const double vmax = 0.5 * fabs(s->W) + (s->lattice == KITE_HONEYCOMB ? 0.5 * fabs(s->delta) : 0.0);
+  // Gaussian draws satisfy |z| <= sqrt(-2 ln 2^-53) = sqrt(106 ln 2) < 8.58 (k_onsite)
+  const double vd = s->disorder == KITE_DISORDER_GAUSSIAN ? 8.58 * fabs(s->W) : 0.5 * fabs(s->W);
+  const double vmax = vd + (s->lattice == KITE_HONEYCOMB ? 0.5 * fabs(s->delta) : 0.0);
   const double b = (Z * fabs(s->t) + vmax) * 1.01;
   *lo = -b;
   *hi = b;

@@ -490,7 +490,7 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
       const int64_t blocks = std::min<int64_t>((p.N + 255) / 256, (int64_t)ctx->num_sms * 16);
       k_onsite<Real><<<(int)std::max<int64_t>(1, blocks), 256, 0, st>>>(
           p.N, sys->lattice, sys->W, 0.5 * sys->delta, sc.de_plus, sc.de_minus, vac_thr,
-          (uint32_t)s, k0, k1, vt, ne);
+          (uint32_t)s, k0, k1, vt, ne, sys->disorder);
       KITE_CUDA_TRY(ctx, cudaGetLastError());
     }
     for (int base = 0; base < p.R; base += p.max_batch) {

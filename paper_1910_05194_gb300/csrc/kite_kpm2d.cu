@@ -174,7 +174,8 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
   for (int s = 0; s < Sreal; ++s) {
     KITE_CUDA_TRY(ctx, cudaMemsetAsync(ne, 0, sizeof(unsigned long long), st));
     k_onsite<float><<<blocks, 256, 0, st>>>(N, sys->lattice, sys->W, 0.5 * sys->delta, sc.de_plus,
-                                            sc.de_minus, vac_thr, (uint32_t)s, k0, k1, vt, ne);
+                                            sc.de_minus, vac_thr, (uint32_t)s, k0, k1, vt, ne,
+                                            sys->disorder);
     unsigned long long ne_host = 0;
     KITE_CUDA_TRY(ctx, cudaMemcpyAsync(&ne_host, ne, sizeof(ne_host), cudaMemcpyDeviceToHost, st));
     KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));

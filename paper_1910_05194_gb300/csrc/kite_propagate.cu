@@ -184,7 +184,7 @@ int propagate_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   KITE_CUDA_TRY(ctx, cudaMemsetAsync(ne, 0, sizeof(unsigned long long), st));
   KITE_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
   k_onsite<Real><<<nb, 256, 0, st>>>(N, sys->lattice, sys->W, 0.5 * sys->delta, sc.de_plus, sc.de_minus, vac_thr,
-                                      0u, k0, k1, vt, ne);
+                                      0u, k0, k1, vt, ne, sys->disorder);
   KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, st));
   const int batch = C * VPC;
   double step_s = 0.0;

@@ -147,7 +147,8 @@ int static_run(const kite_system* sys, const kite_kpm* kpm, double* mu, cudaStre
     if (cudaMemsetAsync(ne, 0, sizeof(unsigned long long), st) != cudaSuccess)
       return static_fail(KITE_ERR_CUDA, "clearing counter");
     k_onsite<Real><<<blocks, 256, 0, st>>>(N, sys->lattice, sys->W, 0.5 * sys->delta, de_plus,
-                                           de_minus, vac_thr, (uint32_t)s, k0, k1, vt, ne);
+                                           de_minus, vac_thr, (uint32_t)s, k0, k1, vt, ne,
+                                           sys->disorder);
     k_init_r0<Real, SORB, C><<<blocks, 256, 0, st>>>(ncell, vt, 0, R, (uint32_t)s * R, k0, k1,
                                                      nullptr, N, r0);
     auto where = [&](int n) -> void* { return n == 0 ? r0 : ((n & 1) ? bA : bB); };
@@ -203,7 +204,8 @@ int moments_1d_static_checked(const kite_system* sys, const kite_kpm* kpm_in, do
   }
   if (sys->lattice != KITE_HONEYCOMB && sys->lattice != KITE_SQUARE)
     return static_fail(KITE_ERR_ARG, "unknown lattice");
-  if (sys->Lx < 1 || sys->Ly < 1 || !(sys->p_vac >= 0.0 && sys->p_vac <= 1.0) || sys->W < 0.0)
+  if (sys->Lx < 1 || sys->Ly < 1 || !(sys->p_vac >= 0.0 && sys->p_vac <= 1.0) || sys->W < 0.0 ||
+      (sys->disorder != KITE_DISORDER_UNIFORM && sys->disorder != KITE_DISORDER_GAUSSIAN))
     return static_fail(KITE_ERR_ARG, "invalid system");
   if (kpm->M < 1 || kpm->M > 65536 || kpm->R < 1 || kpm->S < 1)
     return static_fail(KITE_ERR_ARG, "need 1 <= M <= 65536, R >= 1, S >= 1");

@@ -25,17 +25,28 @@ constexpr int kFlushRows = 32;  // FP32 moment partials are promoted to FP64 eve
 // vacancies, and the count of non-vacant orbitals.  Same draws and the same sequence
 // of correctly rounded FP64 operations as the problem statement in kite_gb.h.
 // ------------------------------------------------------------------------------------
+// Gaussian disorder (gaussian != 0): the Box-Muller transform of u1 = 1 - u (in (0, 1])
+// and the 32-bit uniform u2 of the fourth word, V = W (sqrt(-2 ln u1) cos(2 pi u2)),
+// with CUDA's FP64 log, sqrt and cos (each within an ulp of the host's libm).
 template <typename Real>
 __global__ void k_onsite(int64_t N, int lattice, double W, double half_delta, double de_plus,
                          double de_minus, uint64_t vac_thr, uint32_t realisation, uint32_t k0,
                          uint32_t k1, Real* __restrict__ vt,
-                         unsigned long long* __restrict__ n_eff) {
+                         unsigned long long* __restrict__ n_eff, int gaussian) {
   unsigned int count = 0;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < N;
        o += (int64_t)gridDim.x * blockDim.x) {
     const Philox4 x = philox4x32_10((uint32_t)o, (uint32_t)((uint64_t)o >> 32), realisation,
                                     kTagDisorder, k0, k1);
-    double v = __dmul_rn(W, __dsub_rn(u53(x), 0.5));
+    double v;
+    if (gaussian) {
+      const double u1 = __dsub_rn(1.0, u53(x));
+      const double u2 = __dmul_rn((double)x.w[3], 0x1p-32);
+      const double radius = sqrt(__dmul_rn(-2.0, log(u1)));
+      v = __dmul_rn(W, __dmul_rn(radius, cos(__dmul_rn(6.283185307179586, u2))));
+    } else {
+      v = __dmul_rn(W, __dsub_rn(u53(x), 0.5));
+    }
     if (lattice == KITE_HONEYCOMB && half_delta != 0.0)
       v = __dadd_rn(v, (o & 1) == 0 ? half_delta : -half_delta);
     const bool vacant = (uint64_t)x.w[2] < vac_thr;

@@ -48,6 +48,13 @@ def test_status_strings_and_host_bounds(built):
     assert hi == (4.0 + 1.5) * 1.01
     with pytest.raises(kite.KiteError):
         kite.bounds(kite.make_system(kite.HONEYCOMB, 0, 8))
+    # Gaussian disorder: the transform's largest draw, 8.58 standard deviations
+    g = dict(Lx=8, Ly=8, t=-2.7, W=0.4, delta=0.2)
+    lo, hi = kite.bounds(kite.make_system(kite.HONEYCOMB, disorder=kite.DISORDER_GAUSSIAN, **g))
+    assert (lo, hi) == oracle.bounds_auto(oracle.make_system(disorder=oracle.GAUSSIAN, **g))
+    assert abs(hi - (3 * 2.7 + 8.58 * 0.4 + 0.1) * 1.01) < 1e-14
+    with pytest.raises(kite.KiteError):
+        kite.bounds(kite.make_system(kite.HONEYCOMB, 8, 8, disorder=2))
 
 
 def test_context_creation_fails_cleanly_without_gpu(built):
