@@ -57,18 +57,20 @@ class System(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int32), ("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32),
                 ("disorder", ctypes.c_int32), ("t", ctypes.c_double), ("W", ctypes.c_double),
                 ("delta", ctypes.c_double), ("p_vac", ctypes.c_double),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("flux", ctypes.c_double)]
 
 
 UNIFORM, GAUSSIAN = 0, 1
 
 
 def make_system(lattice=HONEYCOMB, Lx=8, Ly=8, t=-2.7, W=0.0, delta=0.0, p_vac=0.0, seed=1,
-                disorder=UNIFORM):
+                disorder=UNIFORM, flux=0.0):
     """W is the width of uniform disorder in [-W/2, W/2], or the standard deviation of
-    Gaussian disorder (disorder=GAUSSIAN)."""
+    Gaussian disorder (disorder=GAUSSIAN); flux is the perpendicular magnetic flux per unit
+    cell in flux quanta (Landau gauge: flux * Ly even on the honeycomb, integer on the
+    square lattice)."""
     return System(int(lattice), int(Lx), int(Ly), int(disorder), float(t), float(W), float(delta),
-                  float(p_vac), int(seed))
+                  float(p_vac), int(seed), float(flux))
 
 
 def lib():

@@ -258,7 +258,33 @@ typedef struct {
   uint8_t* vac;
   double tt;     /* rescaled hopping */
   int64_t n_eff;
+  double* ph;    /* [N][4] (cos, sin) of the Peierls phase of each bond; NULL without field */
 } orc_ham;
+
+/* Magnetic field (Sec. "Magnetic Field": Peierls substitution on a periodic lattice).
+ * Landau gauge A = (-B y, 0): the hopping from orbital j to orbital o (bond offset
+ * (dx, dy) = r_o - r_j) becomes t exp(i theta) with
+ *   theta = (2 pi / Phi_0) int_{r_j}^{r_o} A . dl = -2 pi (flux / A_cell) (y_o - dy/2) dx,
+ * the line integral along the straight bond (y at its midpoint), flux = B A_cell / Phi_0
+ * per unit cell, A_cell = sqrt(3)/2 (honeycomb) or 1 (square) in units of a^2, and y_o
+ * the orbital's y coordinate.  The phases repeat after Ly rows only if
+ * flux * Ly * |dx| is an integer for every bond (|dx| = 1/2 on the honeycomb, 1 on the
+ * square lattice): otherwise the bonds across the y boundary would not be the
+ * conjugates of their reverses.  Bonds with dx = 0 carry no phase. */
+int orc_flux_fits(const orc_system* sys) {
+  if (sys->flux == 0.0) return 0;
+  double q = sys->flux * (double)sys->Ly * (sys->lattice == 0 ? 0.5 : 1.0);
+  return fabs(q - nearbyint(q)) <= 1e-9 * fmax(1.0, fabs(q)) ? 0 : -4;
+}
+
+static double orc_orbital_y(const orc_system* sys, int64_t o) {
+  if (sys->lattice == 0) {
+    int64_t cell = o >> 1, s = o & 1;
+    double acc = 1.0 / sqrt(3.0);
+    return 0.5 * sqrt(3.0) * (double)(cell / sys->Lx) + (s == 0 ? -0.5 : 0.5) * acc;
+  }
+  return (double)(o / sys->Lx);
+}
 
 static int orc_ham_build(orc_ham* h, const orc_system* sys, int realisation, double e_min,
                          double e_max) {
@@ -280,6 +306,22 @@ static int orc_ham_build(orc_ham* h, const orc_system* sys, int realisation, dou
     if (!h->vac[o]) h->n_eff++;
   }
   h->tt = sys->t / de_minus;
+  h->ph = NULL;
+  if (sys->flux != 0.0) {
+    if (orc_flux_fits(sys)) return -4;
+    h->ph = (double*)malloc(sizeof(double) * 8 * h->N);
+    if (!h->ph) return -2;
+    const double cell_area = sys->lattice == 0 ? 0.5 * sqrt(3.0) : 1.0;
+    const double k = -2.0 * 3.141592653589793 * sys->flux / cell_area;
+    for (int64_t o = 0; o < h->N; ++o) {
+      double yo = orc_orbital_y(sys, o);
+      for (int b = 0; b < 4; ++b) {
+        double th = b < h->Z ? k * (yo - 0.5 * h->dy[4 * o + b]) * h->dx[4 * o + b] : 0.0;
+        h->ph[8 * o + 2 * b] = cos(th);
+        h->ph[8 * o + 2 * b + 1] = sin(th);
+      }
+    }
+  }
   return 0;
 }
 
@@ -289,6 +331,7 @@ static void orc_ham_free(orc_ham* h) {
   free(h->dy);
   free(h->Vt);
   free(h->vac);
+  free(h->ph);
 }
 
 /* y = H~ x on the non-vacant orbitals (vacant rows and columns removed). */
@@ -304,8 +347,15 @@ static void orc_apply_h(const orc_ham* h, const double* x, double* y) {
     for (int k = 0; k < h->Z; ++k) {
       int64_t j = h->nb[4 * o + k];
       if (h->vac[j]) continue;
-      re += h->tt * x[2 * j];
-      im += h->tt * x[2 * j + 1];
+      double xr = x[2 * j], xi = x[2 * j + 1];
+      if (h->ph) { /* t exp(i theta) x_j */
+        double c = h->ph[8 * o + 2 * k], sn = h->ph[8 * o + 2 * k + 1];
+        double r2 = c * xr - sn * xi;
+        xi = sn * xr + c * xi;
+        xr = r2;
+      }
+      re += h->tt * xr;
+      im += h->tt * xi;
     }
     y[2 * o] = re;
     y[2 * o + 1] = im;
@@ -545,6 +595,7 @@ ORC_REPLICA(double, fma)
 int orc_replica_1d(const orc_system* sys, int realisation, int M, int R, double e_min,
                    double e_max, int precision, const double* r0_in, double* mu_per_vec,
                    void* r_last, int threads) {
+  if (sys->flux != 0.0) return -3; /* built without Peierls phases */
 #ifdef _OPENMP
   if (threads > 0) omp_set_num_threads(threads);
 #else
@@ -608,6 +659,7 @@ void orc_velocity(const orc_system* sys, const uint8_t* vac, double t_scaled, in
   h.dy = (double*)malloc(sizeof(double) * 4 * h.N);
   h.vac = (uint8_t*)vac;
   h.tt = t_scaled;
+  h.ph = NULL;
   for (int64_t o = 0; o < h.N; ++o)
     h.Z = orc_neighbours_geo(sys, o, h.nb + 4 * o, h.dx + 4 * o, h.dy + 4 * o);
   orc_apply_v(&h, dir, in, out);
@@ -649,6 +701,7 @@ static void orc_family(const orc_ham* h, int M, const double* start, double* fam
 int orc_moments_2d(const orc_system* sys, int realisation, int M, int R, double e_min,
                    double e_max, const double* r0_in, double* mu_nm, double* a_fam,
                    double* b_fam, int dir_a, int dir_b, int threads) {
+  if (sys->flux != 0.0) return -3; /* built without Peierls phases */
 #ifdef _OPENMP
   if (threads > 0) omp_set_num_threads(threads);
 #else
@@ -778,6 +831,7 @@ void orc_cpgf_coeff(int n, double eps, double eta, int sigma, double* re, double
 /* ------------------------------------------------------------------------------ */
 int orc_replica_window(const orc_system* sys, int realisation, int M, int R, double e_min,
                        double e_max, int precision, int x0, int y0, int half, void* out) {
+  if (sys->flux != 0.0) return -3; /* built without Peierls phases */
   if (M < 1 || R < 1 || half < M || !(e_max > e_min)) return -1;
   if (precision != 0 && precision != 1) return -1;
   const int sorb = sys->lattice == 0 ? 2 : 1;

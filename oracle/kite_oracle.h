@@ -32,7 +32,12 @@ typedef struct {
   double delta;      /* staggered potential +delta/2 on A, -delta/2 on B (eV)          */
   double p_vac;      /* per-orbital vacancy probability                                 */
   uint64_t seed;
+  double flux;       /* perpendicular magnetic flux per unit cell, in flux quanta h/e;   */
+                     /* flux * Ly must be even (honeycomb) or an integer (square)        */
 } orc_system;
+
+/* 0 if the flux fits the torus in the Landau gauge (see orc_flux_fits), else -4. */
+int orc_flux_fits(const orc_system* sys);
 
 /* Philox4x32-10 counter-based generator (Salmon et al., SC'11). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

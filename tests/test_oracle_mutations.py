@@ -29,6 +29,10 @@ MUTATIONS = [
     ("Gaussian variance halved", "sqrt(-2.0 * log(u1))", "sqrt(-log(u1))"),
     ("Gaussian angle from the radius word", "(double)x[3] * 0x1p-32", "(double)x[0] * 0x1p-32"),
     ("Gaussian bound too tight", "#define ORC_GAUSS_ZMAX 8.58", "#define ORC_GAUSS_ZMAX 5.0"),
+    ("Peierls phase without the bond midpoint", "k * (yo - 0.5 * h->dy[4 * o + b])", "k * (yo)"),
+    ("Peierls flux doubled", "* sys->flux / cell_area;", "* 2.0 * sys->flux / cell_area;"),
+    ("Peierls honeycomb cell area", "sys->lattice == 0 ? 0.5 * sqrt(3.0) : 1.0;", "1.0;"),
+    ("Peierls phase conjugated on one component", "xi = sn * xr + c * xi;", "xi = -sn * xr + c * xi;"),
     ("velocity loses its sign", "double w = off[4 * o + k] * h->tt;",
      "double w = fabs(off[4 * o + k]) * h->tt;"),
     ("y bond offset sign", "dy[1] = 0.5 * acc;", "dy[1] = -0.5 * acc;"),

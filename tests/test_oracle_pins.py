@@ -143,6 +143,81 @@ def test_gaussian_disorder_enters_the_second_moment():
     assert abs(np.mean(big ** 2) - (W * W + delta * delta / 4)) < 5 * W * W * math.sqrt(2.0 / big.size) + 0.01
 
 
+def dense_from_operator(sys):
+    """The oracle's own rescaled Hamiltonian as a dense matrix, column j = H~ e_j (its
+    Chebyshev sum with coefficients (0, 1))."""
+    n = oracle.norb(sys)
+    eye = np.eye(n, dtype=np.complex128)
+    return np.array([oracle.chebyshev_sum(sys, np.array([0.0, 1.0], complex), eye[:, j])
+                     for j in range(n)]).T
+
+
+def power_traces(sys, kmax):
+    """<x^k> = Tr(H~^k)/N for k <= kmax from exact-trace Chebyshev moments."""
+    mu = exact_trace_moments(sys, kmax + 1).real
+    # x^k in Chebyshev polynomials: coefficients from numpy's conversion
+    out = []
+    for k in range(kmax + 1):
+        c = np.polynomial.chebyshev.poly2cheb([0] * k + [1])
+        out.append(float(np.dot(c, mu[:k + 1])))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("lattice,flux", [(oracle.SQUARE, 0.25), (oracle.SQUARE, 0.375),
+                                          (oracle.HONEYCOMB, 0.25), (oracle.HONEYCOMB, 0.5)])
+def test_peierls_phases_hermitian_and_loop_traces(lattice, flux):
+    """Magnetic field by Peierls substitution (Sec. "Magnetic Field"): H~ stays Hermitian
+    on the torus, |H~_ij| = |t~|, and the flux enters only through closed loops: the
+    smallest loops enclose one unit cell (square plaquette: 4 bonds, 8 walks per site;
+    honeycomb hexagon: 6 bonds, 6 walks per site), so <x^4> (square) and <x^6>
+    (honeycomb) move by 8 t~^4 (cos 2 pi flux - 1) and 6 t~^6 (cos 2 pi flux - 1), and
+    the lower traces do not move.  Gauge-independent closed forms."""
+    t = -1.0 if lattice == oracle.SQUARE else T_EV
+    base = dict(lattice=lattice, Lx=8, Ly=8, t=t)
+    sysB = oracle.make_system(flux=flux, **base)
+    sys0 = oracle.make_system(**base)
+    H = dense_from_operator(sysB)
+    assert np.max(np.abs(H - H.conj().T)) < 1e-15
+    lo, hi = oracle.bounds_auto(sysB)
+    tt = abs(t) / hi
+    off = np.abs(H[~np.eye(H.shape[0], dtype=bool)])
+    assert np.all((off < 1e-15) | (np.abs(off - tt) < 1e-15))
+    pB, p0 = power_traces(sysB, 6), power_traces(sys0, 6)
+    c = math.cos(2 * math.pi * flux) - 1.0
+    if lattice == oracle.SQUARE:
+        assert np.max(np.abs(pB[:4] - p0[:4])) < 1e-13
+        assert abs(pB[4] - p0[4] - 8 * tt ** 4 * c) < 1e-13
+    else:
+        assert np.max(np.abs(pB[:6] - p0[:6])) < 1e-13
+        assert abs(pB[6] - p0[6] - 6 * tt ** 6 * c) < 1e-13
+
+
+def test_pi_flux_square_lattice_spectrum():
+    """Half a flux quantum per plaquette on the square lattice: the closed-form spectrum
+    E = +-2|t| sqrt(cos^2 kx + cos^2 ky), kx = 2 pi a/Lx, ky = 2 pi b/Ly, b < Ly/2
+    (two-row magnetic cell), against dense diagonalisation of the oracle's operator."""
+    Lx, Ly, t = 6, 8, -1.0
+    sys = oracle.make_system(lattice=oracle.SQUARE, Lx=Lx, Ly=Ly, t=t, flux=0.5)
+    lo, hi = oracle.bounds_auto(sys)
+    lam = np.sort(np.linalg.eigvalsh(dense_from_operator(sys)) * hi)
+    kx = 2 * np.pi * np.arange(Lx) / Lx
+    ky = 2 * np.pi * np.arange(Ly // 2) / Ly
+    KX, KY = np.meshgrid(kx, ky, indexing="ij")
+    e = (2 * abs(t) * np.sqrt(np.cos(KX) ** 2 + np.cos(KY) ** 2)).ravel()
+    ref = np.sort(np.concatenate([e, -e]))
+    assert np.max(np.abs(lam - ref)) < 1e-12
+
+
+def test_flux_must_fit_the_torus():
+    """The Landau-gauge phases repeat after Ly rows only for flux * Ly even (honeycomb)
+    or integer (square); other fluxes are refused."""
+    with pytest.raises(ValueError):
+        oracle.moments_1d(oracle.make_system(lattice=oracle.SQUARE, Lx=8, Ly=8, t=-1.0, flux=0.3), 4, 1)
+    with pytest.raises(ValueError):
+        oracle.moments_1d(oracle.make_system(Lx=8, Ly=8, flux=0.125), 4, 1)  # 0.125 * 8 = 1: odd
+    oracle.moments_1d(oracle.make_system(Lx=8, Ly=8, flux=0.25), 4, 1)
+
+
 def test_random_phase_is_white_noise():
     """|xi| = 1 off vacancies, 0 on them; <xi> = 0, <xi xi> = 0, <|xi|^2> = 1 (Sec. 2c)."""
     sys = oracle.make_system(Lx=64, Ly=64, p_vac=0.02, seed=3)
