@@ -75,7 +75,18 @@ extern "C" {
  *            V_o = W*(sqrt(-2 ln(1 - u)) * cos(2 pi w3 2^-32)) [+- delta/2] (Gaussian,
  *            Box-Muller; |V_o - mean| <= sqrt(106 ln 2) W < 8.58 W), vacant iff
  *            w2 < floor(p_vac * 2^32), phase vector entry exp(2 pi i u) (0 on
- *            vacancies). */
+ *            vacancies).
+ *   flux     perpendicular magnetic field (Sec. "Magnetic Field", Peierls substitution)
+ *            as flux quanta h/e per unit cell; 0 = no field.  Landau gauge A = (-B y, 0):
+ *            the hopping from orbital j to o, bond offset (dx, dy) = r_o - r_j in units
+ *            of a, becomes t exp(i theta), theta = -2 pi (flux/A_cell)(y_o - dy/2) dx,
+ *            A_cell = sqrt(3)/2 (honeycomb) or 1 (square), y_o the orbital's y
+ *            coordinate (cell (x, y) at x a1 + y a2, a1 = (1, 0), a2 = (1/2, sqrt3/2),
+ *            A at (0, -a_cc/2), B at (0, +a_cc/2), a_cc = 1/sqrt3).  On the torus
+ *            flux * Ly must be even (honeycomb) or an integer (square);
+ *            kite_flux_nearest gives the nearest such flux.  Accepted by
+ *            kite_moments_1d (complex start vectors), kite_spectral_k and kite_ldos;
+ *            the other calls return KITE_ERR_ARG for a nonzero flux. */
 typedef struct {
   int32_t lattice;
   int32_t Lx, Ly;
@@ -85,6 +96,7 @@ typedef struct {
   double delta;
   double p_vac;
   uint64_t seed;
+  double flux;
 } kite_system;
 
 /* Chebyshev expansion parameters (the calculation settings of Sec. 3d: num_moments,
@@ -184,6 +196,12 @@ const char* kite_last_error(const kite_ctx* ctx);
  * largest value its transform can give).  Host-only arithmetic in FP64.
  * Errors: KITE_ERR_ARG. */
 int kite_bounds(const kite_system* sys, double* e_min, double* e_max);
+
+/* The flux per unit cell closest to `flux` that the torus of `sys` admits in the Landau
+ * gauge (flux * Ly even on the honeycomb, integer on the square lattice); the field KITE
+ * "best matches" to a requested one (Sec. "Magnetic Field").  sys->flux is ignored.
+ * Host-only.  Errors: KITE_ERR_ARG. */
+int kite_flux_nearest(const kite_system* sys, double flux, double* out);
 
 /* ---- 1D moments ----------------------------------------------------------------- */
 

@@ -30,7 +30,7 @@ EXPORTED = ("kite_create", "kite_destroy", "kite_set_stream", "kite_status_strin
             "kite_reconstruct_sigma", "kite_moments_1d_static", "kite_moments_1d_batched",
             "kite_mlp_param_count", "kite_mlp_train", "kite_mlp_forward", "kite_mlp_gradient",
             "kite_learned_gate", "kite_spectral_k", "kite_ldos", "kite_propagate",
-            "kite_evolution_coeffs")
+            "kite_evolution_coeffs", "kite_flux_nearest")
 MLP_IN, MLP_HIDDEN, MLP_OUT = 128, 512, 1024
 
 
@@ -44,7 +44,8 @@ class System(ctypes.Structure):
     """``kite_system``: periodic honeycomb/square lattice with disorder."""
     _fields_ = [("lattice", ctypes.c_int32), ("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32),
                 ("disorder", ctypes.c_int32), ("t", ctypes.c_double), ("W", ctypes.c_double),
-                ("delta", ctypes.c_double), ("p_vac", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("delta", ctypes.c_double), ("p_vac", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("flux", ctypes.c_double)]
 
 
 class KPM(ctypes.Structure):
@@ -87,11 +88,12 @@ class MLPTrainCfg(ctypes.Structure):
 
 
 def make_system(lattice=HONEYCOMB, Lx=64, Ly=64, t=-2.7, W=0.0, delta=0.0, p_vac=0.0, seed=1,
-                disorder=0):
+                disorder=0, flux=0.0):
     """W: width of uniform disorder in [-W/2, W/2] (disorder=DISORDER_UNIFORM) or standard
-    deviation of Gaussian disorder (disorder=DISORDER_GAUSSIAN)."""
+    deviation of Gaussian disorder (disorder=DISORDER_GAUSSIAN); flux: perpendicular
+    magnetic flux quanta per unit cell (see flux_nearest)."""
     return System(int(lattice), int(Lx), int(Ly), int(disorder), float(t), float(W), float(delta),
-                  float(p_vac), int(seed))
+                  float(p_vac), int(seed), float(flux))
 
 
 def make_kpm(M, R=1, S=1, precision=FP32, e_min=0.0, e_max=0.0, r0=None, r_last=None,
@@ -127,6 +129,8 @@ def lib():
             L.kite_last_error.restype = ctypes.c_char_p
             L.kite_bounds.argtypes = [P(System), P(d), P(d)]
             L.kite_bounds.restype = i32
+            L.kite_flux_nearest.argtypes = [P(System), d, P(d)]
+            L.kite_flux_nearest.restype = i32
             L.kite_moments_1d.argtypes = [vp, P(System), P(KPM), vp, vp, P(Stats)]
             L.kite_moments_1d.restype = i32
             L.kite_reconstruct_dos.argtypes = [vp, vp, i32, i32, i32, d, d, d, vp, i32, vp]
@@ -231,6 +235,15 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+def flux_nearest(system: System, flux: float) -> float:
+    """kite_flux_nearest: the admissible flux per unit cell closest to `flux`."""
+    out = ctypes.c_double()
+    rc = lib().kite_flux_nearest(ctypes.byref(system), ctypes.c_double(flux), ctypes.byref(out))
+    if rc != OK:
+        raise KiteError(rc, "kite_flux_nearest")
+    return out.value
 
 
 def bounds(system: System):

@@ -145,6 +145,20 @@ cudaError_t copy_out(kite_ctx* ctx, void* dst, const void* src_dev, size_t bytes
   return cudaMemcpyAsync(dst, src_dev, bytes, cudaMemcpyDefault, ctx->stream);
 }
 
+// Landau-gauge Peierls phases repeat after Ly rows iff flux * Ly * |dx| is an integer for
+// every bond: |dx| = 1/2 (honeycomb) or 1 (square), i.e. flux * Ly even or integer.
+static double flux_quantum_step(const kite_system* s) {
+  return (s->lattice == KITE_HONEYCOMB ? 2.0 : 1.0) / (double)s->Ly;
+}
+static bool flux_fits(const kite_system* s) {
+  const double q = s->flux / flux_quantum_step(s);
+  return fabs(q - nearbyint(q)) <= 1e-9 * fmax(1.0, fabs(q));
+}
+static double nearest_flux(const kite_system* s, double flux) {
+  const double step = flux_quantum_step(s);
+  return nearbyint(flux / step) * step;
+}
+
 static int validate_system(kite_ctx* ctx, const kite_system* s) {
   if (!s) return fail(ctx, KITE_ERR_ARG, "system is NULL");
   if (s->lattice != KITE_HONEYCOMB && s->lattice != KITE_SQUARE)
@@ -158,6 +172,15 @@ static int validate_system(kite_ctx* ctx, const kite_system* s) {
   if (!(s->p_vac >= 0.0 && s->p_vac <= 1.0)) return fail(ctx, KITE_ERR_ARG, "p_vac outside [0,1]");
   if (s->disorder != KITE_DISORDER_UNIFORM && s->disorder != KITE_DISORDER_GAUSSIAN)
     return fail(ctx, KITE_ERR_ARG, "disorder must be KITE_DISORDER_UNIFORM or KITE_DISORDER_GAUSSIAN");
+  if (!isfinite(s->flux)) return fail(ctx, KITE_ERR_ARG, "flux must be finite");
+  if (s->flux != 0.0 && !flux_fits(s)) {
+    char msg[160];
+    snprintf(msg, sizeof msg,
+             "flux %.9g per cell does not fit the torus in the Landau gauge (flux * Ly must be %s); "
+             "nearest: %.9g",
+             s->flux, s->lattice == KITE_HONEYCOMB ? "even" : "an integer", nearest_flux(s, s->flux));
+    return fail(ctx, KITE_ERR_ARG, msg);
+  }
   return KITE_OK;
 }
 
@@ -347,6 +370,13 @@ int kite_bounds(const kite_system* sys, double* e_min, double* e_max) {
   return KITE_OK;
 }
 
+int kite_flux_nearest(const kite_system* sys, double flux, double* out) {
+  if (!sys || !out || !isfinite(flux)) return KITE_ERR_ARG;
+  if ((sys->lattice != KITE_HONEYCOMB && sys->lattice != KITE_SQUARE) || sys->Ly < 1) return KITE_ERR_ARG;
+  *out = nearest_flux(sys, flux);
+  return KITE_OK;
+}
+
 int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, double* mu,
                     double* mu_per_vec, kite_stats* st) {
   if (!ctx) return KITE_ERR_ARG;
@@ -359,6 +389,8 @@ int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   if (kpm->precision != KITE_FP32 && kpm->precision != KITE_FP64)
     return fail(ctx, KITE_ERR_ARG, "precision must be KITE_FP32 or KITE_FP64");
   if ((double)kpm->R * kpm->S > 65536.0) return fail(ctx, KITE_ERR_ARG, "R*S > 65536");
+  if (sys->flux != 0.0 && kpm->real_vectors)
+    return fail(ctx, KITE_ERR_ARG, "a magnetic field makes H complex: use complex start vectors");
   if ((kpm->doubling != 0 && kpm->doubling != 1) || (kpm->real_vectors != 0 && kpm->real_vectors != 1))
     return fail(ctx, KITE_ERR_ARG, "doubling and real_vectors must be 0 or 1");
   if (kpm->real_vectors && kpm->r_last)
@@ -627,6 +659,7 @@ int kite_propagate(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, d
     return fail(ctx, KITE_ERR_ARG, "precision must be KITE_FP32 or KITE_FP64");
   if (kpm->r0 || kpm->r_last || kpm->doubling != 0 || kpm->real_vectors != 0)
     return fail(ctx, KITE_ERR_ARG, "no r0/r_last (psi is the start), doubling 0, complex vectors");
+  if (sys->flux != 0.0) return fail(ctx, KITE_ERR_ARG, "time evolution takes no magnetic field");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
   Scale sc;
   rc = resolve_bounds(ctx, sys, kpm->e_min, kpm->e_max, &sc);
@@ -662,6 +695,7 @@ int kite_moments_1d_batched(kite_ctx* ctx, int count, const kite_system* systems
     if (!mu[i]) return fail(ctx, KITE_ERR_ARG, "mu[" + std::to_string(i) + "] is NULL");
     if (systems[i].lattice != systems[0].lattice)
       return fail(ctx, KITE_ERR_ARG, "all systems of a batch must share the lattice kind");
+    if (systems[i].flux != 0.0) return fail(ctx, KITE_ERR_ARG, "the batched sweep takes no magnetic field");
     if (k.precision != KITE_FP32) return fail(ctx, KITE_ERR_UNSUPPORTED, "the batched sweep is FP32");
     if (k.R != kpms[0].R || k.R < 1 || k.R > 8)
       return fail(ctx, KITE_ERR_ARG, "all systems need the same R, 1 <= R <= 8");
@@ -687,6 +721,7 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   int rc = validate_system(ctx, sys);
   if (rc != KITE_OK) return rc;
   if (!kpm || !mu_nm) return fail(ctx, KITE_ERR_ARG, "kpm and mu_nm are required");
+  if (sys->flux != 0.0) return fail(ctx, KITE_ERR_ARG, "2D moments take no magnetic field");
   if (kpm->M < 1 || kpm->R < 1 || kpm->S < 1 || kpm->M > 65536)
     return fail(ctx, KITE_ERR_ARG, "need 1 <= M <= 65536, R >= 1, S >= 1");
   if (kpm->precision != KITE_FP32)

@@ -72,6 +72,29 @@ struct Carver {
   size_t used() const { return (off + 255) & ~size_t(255); }
 };
 
+// One vector batch of the 1D sweep in a magnetic field (kite_field.cu): the step launches
+// only; the caller reduces the partials as for the plain sweep.
+struct FieldSweep {
+  int fp64, lattice, C, doubling;
+  int Lx, Ly, M;
+  long long units;
+  int G;       // persistent grid (the partials hold G rows per moment slot)
+  int stall;   // test hook of the first launch (kite_debug_stall_once)
+  int64_t ncell, N;
+  const void* vt;
+  double tt;
+  void *r0, *bA, *bB;
+  double* partial;
+  const void* phase;  // [Ly][sublattice][2 bonds][cos, sin] of the working precision
+  // outputs
+  void *last_prev, *last_cur;
+  double seconds, bytes;
+  int64_t launches;
+};
+int field_phases(kite_ctx* ctx, const kite_system* sys, int fp64, void* table);
+int field_occupancy(int fp64, int lattice, int C, int doubling);
+int field_sweep(kite_ctx* ctx, FieldSweep* a);
+
 // Rescaling of Eqs. rescalingH/rescalingE.
 struct Scale {
   double e_min, e_max, de_plus, de_minus;

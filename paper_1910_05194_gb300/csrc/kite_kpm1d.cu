@@ -83,6 +83,7 @@ struct Plan {
   bool fp64;
   bool doubling;  // two moments per step from <r_n|r_n> and <r_n|r_{n+1}>
   bool realv;     // real +-1 start vectors (four FP32 / two FP64 per chunk)
+  bool field;     // Peierls phases of a perpendicular magnetic field (kite_field.cu)
   int max_batch;  // vectors per pass
 };
 
@@ -115,13 +116,13 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
     const int steps = steps_for(p);
     launch_pdl(k_step<Real, LAT, C, true, 3, NST>, G, kBlock, SMD, st,
         nullptr, r0, bA, nullptr, vt, tt, p.Lx, p.Ly, units,
-        partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
+        partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
     ctx->debug_stall = 0;
     for (int n = 1; n < steps; ++n)
       launch_pdl(k_step<Real, LAT, C, false, 3, NST>, G, kBlock, SMD, st,
           where(n - 1), where(n), where(n + 1), nullptr, vt, tt, p.Lx, p.Ly, units,
           partial + (size_t)(2 * n + 1) * G * Q,
-          partial + (size_t)(2 * n) * G * Q, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
+          partial + (size_t)(2 * n) * G * Q, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
     KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
     KITE_CUDA_TRY(ctx, cudaGetLastError());
     const int total = M * Q;
@@ -142,12 +143,12 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
   if (M >= 2)
     launch_pdl(k_step<Real, LAT, C, true, 0, NST>, G, kBlock, SM, st,
         nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly, units,
-        partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
+        partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
   ctx->debug_stall = 0;
   for (int n = 1; n + 1 < M; ++n)
     launch_pdl(k_step<Real, LAT, C, false, 0, NST>, G, kBlock, SM, st,
         where(n - 1), where(n), where(n + 1), r0, vt, tt, p.Lx, p.Ly, units,
-        partial + (size_t)(n + 1) * G * Q, nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
+        partial + (size_t)(n + 1) * G * Q, nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
   KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
   KITE_CUDA_TRY(ctx, cudaGetLastError());
   if (M == 1) {
@@ -155,7 +156,7 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
     // FIRST kernel is cheap and keeps one code path.
     launch_pdl(k_step<Real, LAT, C, true, 0, NST>, G, kBlock, SM, st,
         nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly, units,
-        partial + (size_t)G * Q, partial, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
+        partial + (size_t)G * Q, partial, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
     KITE_CUDA_TRY(ctx, cudaGetLastError());
   }
   const int total = M * Q;
@@ -201,7 +202,7 @@ int sweep_two(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, v
   step2_occupancy<Real, LAT, C, NST2>();
   launch_pdl(k_step<Real, LAT, C, true, 0, NST1>, G, kBlock, SM, st,
       nullptr, r0, w4(1), r0, vt, tt, p.Lx, p.Ly, units,
-      partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
+      partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
   ctx->debug_stall = 0;
   int n = 1;
   int64_t launches = 1;
@@ -216,7 +217,7 @@ int sweep_two(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, v
   if (n + 1 <= M - 1) {
     launch_pdl(k_step<Real, LAT, C, false, 0, NST1>, G, kBlock, SM, st,
         w4(n - 1), w4(n), w4(n + 1), r0, vt, tt, p.Lx, p.Ly, units,
-        partial + (size_t)(n + 1) * G * Q, nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
+        partial + (size_t)(n + 1) * G * Q, nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
     ++launches;
     bytes += launch_bytes(4);
   }
@@ -303,7 +304,7 @@ float time_candidate(kite_ctx* ctx, int k, long long units, const Plan& p, const
     // r_{n-1} = bA, r_n = bB, r_{n+1} over r_{n-1} in place, r_0 apart: the sweep's streams
     launch_pdl(k_step<Real, LAT, C, false, MODE, NST>, G, kBlock, SMEM, st,
         bA, bB, bA, MODE == 0 ? r0 : nullptr, vt, tt, p.Lx, p.Ly, units, partial + (size_t)2 * G * Q,
-        MODE == 3 ? partial + (size_t)G * Q : nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{});
+        MODE == 3 ? partial + (size_t)G * Q : nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
   };
   launch();  // warm-up
   cudaEventRecord(ctx->ev2, st);
@@ -319,7 +320,7 @@ float time_candidate(kite_ctx* ctx, int k, long long units, const Plan& p, const
 // for at least one pass.
 template <int MODE>
 bool two_step_allowed(const Plan& p) {
-  return MODE == 0 && p.M >= 4 && pass_steps_pinned() != 1;
+  return MODE == 0 && p.M >= 4 && !p.field && pass_steps_pinned() != 1;
 }
 
 template <typename Real, int LAT, int C, int MODE>
@@ -423,6 +424,7 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
   p.M = kpm->M;
   p.doubling = kpm->doubling != 0;
   p.realv = kpm->real_vectors != 0;
+  p.field = sys->flux != 0.0;
   const int per_chunk = p.realv ? Chunk<Real>::kReals : VPC;  // vectors per 16-byte chunk
   p.max_batch = kMaxC * per_chunk;
   auto chunks_for = [&](int nvec) {
@@ -447,10 +449,11 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
   Carver cv(nullptr);
   // two more iterate buffers when the two-step pass may run (its outputs never alias its
   // inputs)
-  const bool two_possible = !p.doubling && p.M >= 4 && pass_steps_pinned() != 1;
+  const bool two_possible = !p.doubling && p.M >= 4 && !p.field && pass_steps_pinned() != 1;
   auto plan_ws = [&](Carver& k, Real** vt, void** r0, void** bA, void** bB, void** bC, void** bD,
-                     double** partial, unsigned long long** ne, double** mu_vec) {
+                     double** partial, unsigned long long** ne, double** mu_vec, Real** phase) {
     *vt = k.take<Real>(p.N);
+    *phase = p.field ? k.take<Real>((size_t)p.Ly * SORB * 4) : nullptr;
     *r0 = k.take<char>(vec_bytes);
     *bA = k.take<char>(vec_bytes);
     *bB = k.take<char>(vec_bytes);
@@ -464,11 +467,16 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
   void *r0, *bA, *bB, *bC, *bD;
   double *partial, *mu_vec;
   unsigned long long* ne;
-  plan_ws(cv, &vt, &r0, &bA, &bB, &bC, &bD, &partial, &ne, &mu_vec);
+  Real* phase;
+  plan_ws(cv, &vt, &r0, &bA, &bB, &bC, &bD, &partial, &ne, &mu_vec, &phase);
   int rc = ensure_ws(ctx, cv.used());
   if (rc != KITE_OK) return rc;
   Carver real(ctx->ws);
-  plan_ws(real, &vt, &r0, &bA, &bB, &bC, &bD, &partial, &ne, &mu_vec);
+  plan_ws(real, &vt, &r0, &bA, &bB, &bC, &bD, &partial, &ne, &mu_vec, &phase);
+  if (p.field) {
+    rc = field_phases(ctx, sys, sizeof(Real) == 8, phase);
+    if (rc != KITE_OK) return rc;
+  }
   if (mu_vec_dev_ext) mu_vec = mu_vec_dev_ext;
 
   const Real tt = (Real)(sys->t / sc.de_minus);
@@ -546,7 +554,45 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
                                                       &step_n, &step_bytes);                         \
     }                                                                                               \
   } while (0)
-      if (C == 1) KITE_SWEEP(1);
+      if (p.field) {
+        // magnetic field: the one-step sweep with Peierls phases (kite_field.cu)
+        const int occ = field_occupancy(sizeof(Real) == 8, LAT, C, p.doubling);
+        FieldSweep fs{};
+        fs.fp64 = sizeof(Real) == 8;
+        fs.lattice = LAT;
+        fs.C = C;
+        fs.doubling = p.doubling;
+        fs.Lx = p.Lx;
+        fs.Ly = p.Ly;
+        fs.M = p.M;
+        fs.units = u;
+        fs.G = (int)std::max(1LL, std::min({(long long)ctx->num_sms * occ, u, (long long)Gmax}));
+        fs.stall = ctx->debug_stall;
+        fs.ncell = p.ncell;
+        fs.N = p.N;
+        fs.vt = vt;
+        fs.tt = (double)tt;
+        fs.r0 = r0;
+        fs.bA = bA;
+        fs.bB = bB;
+        fs.partial = partial;
+        fs.phase = phase;
+        ctx->debug_stall = 0;
+        rc = field_sweep(ctx, &fs);
+        if (rc != KITE_OK) return rc;
+        const int Q = 2 * C * VPC;
+        k_reduce<<<(p.M * Q + 255) / 256, 256, 0, st>>>(partial, p.M, fs.G, Q, nvec, vec_base, ne, mu_vec,
+                                                       0);
+        if (p.doubling) k_undouble<<<(nvec * p.M + 255) / 256, 256, 0, st>>>(mu_vec, p.M, nvec, vec_base);
+        KITE_CUDA_TRY(ctx, cudaGetLastError());
+        lp = fs.last_prev;
+        lc = fs.last_cur;
+        step_s += fs.seconds;
+        step_n += fs.launches;
+        step_bytes += fs.bytes;
+        grid_used = fs.G;
+        tune_used = Tune{8, occ, 0};
+      } else if (C == 1) KITE_SWEEP(1);
       else if (C == 2) KITE_SWEEP(2);
       else KITE_SWEEP(4);
 #undef KITE_SWEEP

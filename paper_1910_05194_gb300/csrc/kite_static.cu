@@ -207,6 +207,7 @@ int moments_1d_static_checked(const kite_system* sys, const kite_kpm* kpm_in, do
   if (sys->Lx < 1 || sys->Ly < 1 || !(sys->p_vac >= 0.0 && sys->p_vac <= 1.0) || sys->W < 0.0 ||
       (sys->disorder != KITE_DISORDER_UNIFORM && sys->disorder != KITE_DISORDER_GAUSSIAN))
     return static_fail(KITE_ERR_ARG, "invalid system");
+  if (sys->flux != 0.0) return static_fail(KITE_ERR_ARG, "the allocation-free call takes no magnetic field");
   if (kpm->M < 1 || kpm->M > 65536 || kpm->R < 1 || kpm->S < 1)
     return static_fail(KITE_ERR_ARG, "need 1 <= M <= 65536, R >= 1, S >= 1");
   if (kpm->r0 || kpm->r_last || kpm->doubling != 0 || kpm->real_vectors != 0)

@@ -276,14 +276,19 @@ struct Ring {
 
 // One recursion step over this CTA's share [cta/ncta] of the units.  Returns false if a
 // bounded wait gave up (the CTA has drained its copies and set *err; stop using the ring).
-template <typename Real, int LAT, int C, bool FIRST, int MODE, int NST = kStages>
+// FIELD: Peierls phases of a perpendicular magnetic field (complex vectors only).  phase
+// holds, per row y and sublattice s, (cos, sin) of the two bonds with an x component,
+// [y][s][bond][2]: honeycomb bonds n2, n3, square bonds n1, n2 in the order of the
+// neighbour loads below; the neighbour value is rotated before the sum.
+template <typename Real, int LAT, int C, bool FIRST, int MODE, int NST = kStages, bool FIELD = false>
 __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const void* r_prev,
                                           const void* __restrict__ r_cur, void* r_out,
                                           const void* __restrict__ r0, const Real* __restrict__ vt,
                                           Real tt, int Lx, int Ly, long long units,
                                           double* __restrict__ partial, double* __restrict__ partial0,
                                           int* __restrict__ err, int stall, const FamOut& fam,
-                                          int realv = 0, const SeriesOut& ser = SeriesOut{}) {
+                                          int realv = 0, const SeriesOut& ser = SeriesOut{},
+                                          const Real* __restrict__ phase = nullptr) {
   static_assert(MODE == 0 || MODE == 3 || MODE == 4 || (sizeof(Real) == 4 && C * 2 <= kMaxFamVecs),
                 "family modes run on FP32 batches of at most two vectors");
   using Ch = Chunk<Real>;
@@ -369,6 +374,14 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
       const int y = yb + i;
       const Real v = vnext;
       if (active && i + 1 < nr) vnext = vt[((size_t)(y + 1) * Lx + x0 + xl) * SORB + s];
+      Real pc0 = Real(1), ps0 = Real(0), pc1 = Real(1), ps1 = Real(0);
+      if constexpr (FIELD) {
+        const Real* p4 = phase + ((size_t)y * SORB + s) * 4;
+        pc0 = __ldg(p4);
+        ps0 = __ldg(p4 + 1);
+        pc1 = __ldg(p4 + 2);
+        ps1 = __ldg(p4 + 3);
+      }
       if (ok && active) {
         const unsigned char* up = stages + (int)((gslot + i) % NST) * STG;
         const unsigned char* mid = stages + (int)((gslot + i + 1) % NST) * STG;
@@ -387,6 +400,24 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
           n2 = *reinterpret_cast<const Ch*>(mid + (xl + 2) * CELLB + choff);
           n3 = *reinterpret_cast<const Ch*>(up + (xl + 1) * CELLB + choff);
           n4 = *reinterpret_cast<const Ch*>(dn + (xl + 1) * CELLB + choff);
+        }
+        if constexpr (FIELD) {
+          // t exp(i theta) r_j: rotate the neighbours across bonds with an x component
+          auto rot = [&](Ch& n, Real cph, Real sph) {
+#pragma unroll
+            for (int q = 0; q < VPC; ++q) {
+              const Real re = n.v[2 * q], im = n.v[2 * q + 1];
+              n.v[2 * q] = rfma(cph, re, -rmul(sph, im));
+              n.v[2 * q + 1] = rfma(sph, re, rmul(cph, im));
+            }
+          };
+          if (LAT == KITE_HONEYCOMB) {
+            rot(n2, pc0, ps0);
+            rot(n3, pc1, ps1);
+          } else {
+            rot(n1, pc0, ps0);
+            rot(n2, pc1, ps1);
+          }
         }
         Ch pv, z0;
         if (FIRST) {
@@ -541,13 +572,13 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
   return true;
 }
 
-template <typename Real, int LAT, int C, bool FIRST, int MODE = 0, int NST = kStages>
+template <typename Real, int LAT, int C, bool FIRST, int MODE = 0, int NST = kStages, bool FIELD = false>
 __global__ void __launch_bounds__(kBlock, 2)
     k_step(const void* r_prev, const void* __restrict__ r_cur, void* r_out,
            const void* __restrict__ r0, const Real* __restrict__ vt, Real tt, int Lx, int Ly,
            long long units, double* __restrict__ partial, double* __restrict__ partial0,
            int* __restrict__ err, int stall, const FamOut fam, int realv = 0,
-           const SeriesOut ser = SeriesOut{}) {
+           const SeriesOut ser = SeriesOut{}, const void* phase = nullptr) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
@@ -559,8 +590,9 @@ __global__ void __launch_bounds__(kBlock, 2)
   Ring ring{bars, smem + kBarBytes, &s_abort, 0};
   griddep_wait();  // the previous step's iterates and partials are complete
   griddep_launch_dependents();
-  step_body<Real, LAT, C, FIRST, MODE, NST>(ring, blockIdx.x, gridDim.x, r_prev, r_cur, r_out, r0, vt,
-                                       tt, Lx, Ly, units, partial, partial0, err, stall, fam, realv, ser);
+  step_body<Real, LAT, C, FIRST, MODE, NST, FIELD>(ring, blockIdx.x, gridDim.x, r_prev, r_cur, r_out, r0,
+                                                   vt, tt, Lx, Ly, units, partial, partial0, err, stall,
+                                                   fam, realv, ser, static_cast<const Real*>(phase));
 }
 
 // Launch with programmatic stream serialisation: the kernel's set-up overlaps the end of
