@@ -402,6 +402,36 @@ def unit_cell_factor(lattice: int):
     return 2.0 * 2.0 / np.sqrt(3.0) if lattice == HONEYCOMB else 1.0
 
 
+def sigma_dc(mu_nm, E, e_min: float, e_max: float, lattice: int, kernel: str = "jackson", lam: float = 4.0):
+    """Longitudinal DC conductivity at T = 0 in units of e^2/hbar per spin: the omega -> 0
+    limit of the Kubo formula (Eq. conductivity_1st_order), where only states at the Fermi
+    energy contribute (Kubo-Greenwood),
+      sigma(E) = pi hbar e^2 / Omega Tr[v delta(E - H) v delta(E - H)],
+    with v = -i (de_minus a / hbar) h~, delta(E - H) = delta(e - H~)/de_minus and each delta
+    function expanded in M Chebyshev terms with the kernel (Sec. 2a):
+      sigma(E) = pi (n_orb a^2/Omega_c) sum_nm c_n(e) c_m(e) mu_nm,
+      c_n(e) = g_n (2 - d_n0) T_n(e) / (pi sqrt(1 - e^2)),   e = (E - de_plus)/de_minus,
+    mu_nm = <r|v T_n v T_m|r>/N the 2D moments (v = -i h~).  0 outside |e| < 1."""
+    mu = np.asarray(mu_nm, np.complex128)
+    M = mu.shape[0]
+    dm, dp = 0.5 * (e_max - e_min), 0.5 * (e_max + e_min)
+    if kernel == "jackson":
+        g = kernel_jackson(M)
+    elif kernel == "lorentz":
+        g = kernel_lorentz(M, lam)
+    else:
+        g = np.ones(M)
+    w = np.where(np.arange(M) == 0, 1.0, 2.0) * g
+    out = np.zeros(len(E))
+    for k, Ek in enumerate(np.asarray(E, np.float64)):
+        e = (Ek - dp) / dm
+        if not abs(e) < 1.0:
+            continue
+        c = w * np.cos(np.arange(M) * np.arccos(e)) / (np.pi * np.sqrt(1.0 - e * e))
+        out[k] = np.pi * unit_cell_factor(lattice) * float(np.real(c @ mu @ c))
+    return out
+
+
 def sigma_xx(mu_nm, omega, e_min: float, e_max: float, E_F: float, eta: float, lattice: int,
              kernel: str = "jackson", n_quad: int = 0, gamma_n=None, kT: float = 0.0):
     """First-order optical conductivity sigma_xx(omega) in units of e^2/hbar (T = 0),
