@@ -480,6 +480,24 @@ int kite_reconstruct_green(kite_ctx* ctx, const double* mu, int M_avail, int M_u
                            double param, double e_min, double e_max, double eta,
                            const double* E, int K, double* G, double* rho);
 
+/* Longitudinal DC conductivity at T = 0 in units of e^2/hbar per spin (Kubo-Greenwood:
+ * the omega -> 0 limit of Eq. conductivity_1st_order, where only states at the Fermi
+ * energy contribute) from the 2D moments mu_nm = <r|v T_n v T_m|r>/N of kite_moments_2d
+ * with alpha = beta:
+ *   sigma(E) = pi (n_orb a^2/Omega_c) sum_{n,m < M_use} c_n(e) c_m(e) Re mu_nm,
+ *   c_n(e) = (2 - delta_n0) g_n T_n(e) / (pi sqrt(1 - e^2)),  e = (E - de_plus)/de_minus,
+ * i.e. pi hbar e^2/Omega Tr[v delta(E-H) v delta(E-H)] with both delta functions expanded
+ * in M_use kernel-damped Chebyshev terms (Sec. 2a); 0 outside the spectrum window.
+ * n_orb a^2/Omega_c = 4/sqrt(3) (honeycomb), 1 (square).  FP64 on the GPU, fixed-order
+ * sums.  The Fermi-sea (Hall) term of the DC Kubo-Bastin formula is not part of it.
+ *   mu_nm   [M_avail][M_avail] complex FP64, host or device; the leading M_use block is used
+ *   kernel  KITE_KERNEL_NONE / _JACKSON / _LORENTZ (param = lambda)
+ *   E       [K] Fermi energies (eV), host or device;  sigma  [K] FP64, host or device
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
+int kite_reconstruct_sigma_dc(kite_ctx* ctx, const double* mu_nm, int M_avail, int M_use, int lattice,
+                              int kernel, double param, double e_min, double e_max, const double* E, int K,
+                              double* sigma);
+
 /* First-order optical conductivity sigma_xx(omega) in units of e^2/hbar from the 2D
  * moments of kite_moments_2d (Sec. 2b, Eqs. Gammanm and conductivity_1st_order, in
  * rescaled units w = hbar omega / de_minus, eta in eV):

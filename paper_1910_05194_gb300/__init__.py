@@ -30,7 +30,7 @@ EXPORTED = ("kite_create", "kite_destroy", "kite_set_stream", "kite_status_strin
             "kite_reconstruct_sigma", "kite_moments_1d_static", "kite_moments_1d_batched",
             "kite_mlp_param_count", "kite_mlp_train", "kite_mlp_forward", "kite_mlp_gradient",
             "kite_learned_gate", "kite_spectral_k", "kite_ldos", "kite_propagate",
-            "kite_evolution_coeffs", "kite_flux_nearest")
+            "kite_evolution_coeffs", "kite_flux_nearest", "kite_reconstruct_sigma_dc")
 MLP_IN, MLP_HIDDEN, MLP_OUT = 128, 512, 1024
 
 
@@ -138,6 +138,8 @@ def lib():
             L.kite_reconstruct_sigma.argtypes = [vp, vp, i32, i32, i32, i32, d, d, d, d, d, vp,
                                                  i32, i32, vp]
             L.kite_reconstruct_sigma.restype = i32
+            L.kite_reconstruct_sigma_dc.argtypes = [vp, vp, i32, i32, i32, i32, d, d, d, vp, i32, vp]
+            L.kite_reconstruct_sigma_dc.restype = i32
             L.kite_moments_1d_static.argtypes = [P(System), P(KPM), vp, vp, ctypes.c_char_p, i32]
             L.kite_moments_1d_static.restype = i32
             L.kite_moments_1d_batched.argtypes = [vp, i32, P(System), P(KPM), P(vp), P(Stats)]
@@ -244,6 +246,15 @@ def flux_nearest(system: System, flux: float) -> float:
     if rc != OK:
         raise KiteError(rc, "kite_flux_nearest")
     return out.value
+
+
+def reconstruct_sigma_dc(ctx: Context, mu_nm, M_avail: int, M_use: int, lattice: int, kernel: int,
+                         param: float, e_min: float, e_max: float, E, K: int, sigma):
+    """kite_reconstruct_sigma_dc: T = 0 longitudinal DC conductivity (e^2/hbar per spin)
+    at the Fermi energies E from the 2D moments mu_nm ([M_avail][M_avail] complex)."""
+    ctx.check(lib().kite_reconstruct_sigma_dc(ctx.handle, _addr(mu_nm), int(M_avail), int(M_use), int(lattice),
+                                              int(kernel), float(param), float(e_min), float(e_max), _addr(E),
+                                              int(K), _addr(sigma)))
 
 
 def bounds(system: System):

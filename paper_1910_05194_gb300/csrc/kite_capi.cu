@@ -31,6 +31,9 @@ int moments_2d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
                     int beta, double* mu_nm_dev, kite_stats* st, const double* r0_dev_all);
 int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
                         double scale, double* C, int sub_kb, int fold, int nprod);
+int reconstruct_sigma_dc_impl(kite_ctx* ctx, const double* mu_dev, int M_avail, int M, int kernel, double param,
+                              int lattice, const Scale& sc, const double* E_dev, int K, double* sigma_dev,
+                              double* w);
 int reconstruct_sigma_impl(kite_ctx* ctx, const double* mu_dev, int M_avail, int M, int lattice,
                            int kernel, const Scale& sc, double E_F, double kT, double eta,
                            const double* omega_host, int K_w, int n_quad, double* sigma_dev);
@@ -880,6 +883,47 @@ int kite_reconstruct_green(kite_ctx* ctx, const double* mu, int M_avail, int M_u
   if (rc == KITE_OK && rho) rc = sg.back(rho, rho_dev, (size_t)K);
   cudaError_t es = cudaStreamSynchronize(ctx->stream);
   if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "reconstruct_green");
+  return rc;
+}
+
+int kite_reconstruct_sigma_dc(kite_ctx* ctx, const double* mu_nm, int M_avail, int M_use, int lattice,
+                              int kernel, double param, double e_min, double e_max, const double* E, int K,
+                              double* sigma) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  if (!mu_nm || !E || !sigma || K < 0 || M_avail < 1 || M_use < 1 || M_use > M_avail || M_use > 16384)
+    return fail(ctx, KITE_ERR_ARG, "need mu_nm, E, sigma and 1 <= M_use <= min(M_avail, 16384), K >= 0");
+  if (lattice != KITE_HONEYCOMB && lattice != KITE_SQUARE) return fail(ctx, KITE_ERR_ARG, "unknown lattice");
+  if (kernel != KITE_KERNEL_NONE && kernel != KITE_KERNEL_JACKSON && kernel != KITE_KERNEL_LORENTZ)
+    return fail(ctx, KITE_ERR_ARG, "unknown kernel");
+  if (kernel == KITE_KERNEL_LORENTZ && !(param > 0.0))
+    return fail(ctx, KITE_ERR_ARG, "Lorentz kernel needs lambda > 0");
+  if (!(e_max > e_min)) return fail(ctx, KITE_ERR_ARG, "e_max must exceed e_min");
+  if (K == 0) return KITE_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  Scale sc{e_min, e_max, 0.5 * (e_max + e_min), 0.5 * (e_max - e_min)};
+  const bool mu_d = is_device_ptr(mu_nm), E_d = is_device_ptr(E), s_d = is_device_ptr(sigma);
+  const size_t mu_doubles = mu_d ? 0 : 2 * (size_t)M_avail * M_avail;
+  double* buf = nullptr;
+  KITE_CUDA_TRY(ctx, cudaMallocAsync((void**)&buf, sizeof(double) * (mu_doubles + (size_t)M_use + 2 * (size_t)K),
+                                     ctx->stream));
+  const double* mu_dev = mu_d ? mu_nm : buf;
+  double* w = buf + mu_doubles;
+  double* E_dev = E_d ? const_cast<double*>(E) : w + M_use;
+  double* s_dev = s_d ? sigma : w + M_use + K;
+  cudaError_t e = cudaSuccess;
+  if (!mu_d) e = copy_in(ctx, buf, mu_nm, mu_doubles * sizeof(double));
+  if (e == cudaSuccess && !E_d) e = copy_in(ctx, E_dev, E, (size_t)K * sizeof(double));
+  int rc = e == cudaSuccess ? KITE_OK : cuda_fail(ctx, e, "copying inputs");
+  if (rc == KITE_OK)
+    rc = reconstruct_sigma_dc_impl(ctx, mu_dev, M_avail, M_use, kernel, param, lattice, sc, E_dev, K, s_dev, w);
+  if (rc == KITE_OK && !s_d) {
+    e = copy_out(ctx, sigma, s_dev, (size_t)K * sizeof(double));
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "copying sigma");
+  }
+  cudaFreeAsync(buf, ctx->stream);
+  cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "reconstruct_sigma_dc");
   return rc;
 }
 

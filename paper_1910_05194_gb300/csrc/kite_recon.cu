@@ -6,6 +6,8 @@
 // truncated at M terms (Eq. e8a) and damped by a kernel g_n (Sec. 2a).
 #include <math.h>
 
+#include <algorithm>
+
 #include <vector>
 
 #include "kite_internal.h"
@@ -292,6 +294,60 @@ __global__ void k_sig_omega(const double* __restrict__ U, const double* __restri
   }
 }
 
+// ---- DC conductivity (Kubo-Greenwood, T = 0) ---------------------------------------
+// One block per energy (grid-stride): the kernel-damped delta coefficients
+// c_n = w_n T_n(e) / (pi sqrt(1 - e^2)), w_n = (2 - delta_n0) g_n, in shared memory; each
+// warp contracts whole rows, s = sum_n c_n sum_m Re(mu_nm) c_m, then a fixed-order sum
+// over the warps.  sigma_k = pi ucf s (0 outside |e| < 1).  FP64 throughout.
+__global__ void k_sigma_dc(const double* __restrict__ mu, int M_avail, int M, const double* __restrict__ w,
+                           double de_plus, double de_minus, const double* __restrict__ E, int K, double ucf,
+                           double* __restrict__ sigma) {
+  extern __shared__ double c[];  // [M] + [blockDim/32]
+  double* wsum = c + M;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int k = blockIdx.x; k < K; k += gridDim.x) {
+    const double e = (E[k] - de_plus) / de_minus;
+    if (!(fabs(e) < 1.0)) {
+      if (threadIdx.x == 0) sigma[k] = 0.0;
+      continue;  // uniform across the block
+    }
+    const double th = acos(e), den = 3.141592653589793 * sqrt(1.0 - e * e);
+    for (int n = threadIdx.x; n < M; n += blockDim.x) c[n] = w[n] * cos((double)n * th) / den;
+    __syncthreads();
+    double acc = 0.0;
+    for (int n = warp; n < M; n += nwarp) {
+      const double* row = mu + 2 * (size_t)n * M_avail;
+      double r = 0.0;
+      for (int m = lane; m < M; m += 32) r += row[2 * m] * c[m];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+      acc += c[n] * r;
+    }
+    if (lane == 0) wsum[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int q = 0; q < nwarp; ++q) sum += wsum[q];
+      sigma[k] = 3.141592653589793 * ucf * sum;
+    }
+    __syncthreads();
+  }
+}
+
+// w_n = (2 - delta_n0) g_n for the kernel built for M terms
+__global__ void k_dc_weights(int M, int kernel, double param, double* __restrict__ w) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= M) return;
+  double g = 1.0;
+  if (kernel == KITE_KERNEL_JACKSON) {
+    const double q = 3.141592653589793 / (double)(M + 1);
+    g = ((double)(M - n + 1) * cos(q * n) + sin(q * n) * (cos(q) / sin(q))) / (double)(M + 1);
+  } else if (kernel == KITE_KERNEL_LORENTZ) {
+    g = sinh(param * (1.0 - (double)n / (double)M)) / sinh(param);
+  }
+  w[n] = (n == 0 ? 1.0 : 2.0) * g;
+}
+
 }  // namespace
 
 // Gauss-Legendre nodes/weights on [-1, 1] (Newton iteration on P_K from the three-term
@@ -374,6 +430,29 @@ int reconstruct_sigma_impl(kite_ctx* ctx, const double* mu_dev, int M_avail, int
   }
   cudaFreeAsync(buf, st);
   return rc;
+}
+
+}  // namespace kite
+
+namespace kite {
+
+// sigma_DC(E_k) for K energies from the leading M x M block of mu_nm (device pointers);
+// w is device scratch of M doubles.
+int reconstruct_sigma_dc_impl(kite_ctx* ctx, const double* mu_dev, int M_avail, int M, int kernel, double param,
+                              int lattice, const Scale& sc, const double* E_dev, int K, double* sigma_dev,
+                              double* w) {
+  cudaStream_t st = ctx->stream;
+  k_dc_weights<<<(M + 255) / 256, 256, 0, st>>>(M, kernel, param, w);
+  const int block = 256;
+  const size_t smem = sizeof(double) * ((size_t)M + block / 32);
+  if (smem > 48 * 1024)
+    KITE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sigma_dc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = std::max(1, std::min(K, ctx->num_sms * 4));
+  const double ucf = lattice == KITE_HONEYCOMB ? 2.0 * 2.0 / sqrt(3.0) : 1.0;
+  k_sigma_dc<<<grid, block, smem, st>>>(mu_dev, M_avail, M, w, sc.de_plus, sc.de_minus, E_dev, K, ucf,
+                                         sigma_dev);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  return KITE_OK;
 }
 
 }  // namespace kite
