@@ -5,10 +5,13 @@ CPU, never in the tree), rebuilds it, and re-runs the pin suite against the muta
 at least one pin has to fail.  This is what makes the pins evidence rather than
 restatements of the oracle.
 """
+import concurrent.futures as cf
 import os
 import shutil
 import subprocess
 import sys
+import tempfile
+from pathlib import Path
 
 import pytest
 
@@ -49,7 +52,7 @@ MUTATIONS = [
 ]
 
 
-def run_pins_on_copy(tmp_path, old, new):
+def run_pins_on_copy(tmp_path, old, new, threads=None):
     src_dir = os.path.join(ROOT, "oracle")
     dst = tmp_path / "oracle"
     dst.mkdir()
@@ -62,6 +65,8 @@ def run_pins_on_copy(tmp_path, old, new):
     (dst / "kite_oracle.c").write_text(src.replace(old, new, 1))
     shutil.copy(os.path.join(ROOT, "tests", "test_oracle_pins.py"), tmp_path / "test_oracle_pins.py")
     env = dict(os.environ, PYTHONPATH=str(tmp_path))
+    if threads:
+        env["OMP_NUM_THREADS"] = str(threads)
     return subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
                            "-p", "no:randomly", str(tmp_path / "test_oracle_pins.py")],
                           cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
@@ -74,8 +79,29 @@ def test_unmutated_copy_passes(tmp_path):
     assert r.returncode == 0, r.stdout[-3000:]
 
 
+@pytest.fixture(scope="module")
+def mutant_runs():
+    """Every mutant's pin run, side by side (each in its own copy and process, a few
+    OpenMP threads each), so the module takes about as long as one run."""
+    cores = os.cpu_count() or 1
+    workers = max(1, min(len(MUTATIONS), cores // 2))
+    base = Path(tempfile.mkdtemp(prefix="oracle_mutants_"))
+
+    def one(i):
+        d = base / f"m{i}"
+        d.mkdir()
+        return run_pins_on_copy(d, MUTATIONS[i][1], MUTATIONS[i][2], threads=2)
+
+    try:
+        with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+            results = list(ex.map(one, range(len(MUTATIONS))))
+    finally:
+        shutil.rmtree(base, ignore_errors=True)
+    return {MUTATIONS[i][0]: r for i, r in enumerate(results)}
+
+
 @pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pins_catch_planted_mistake(tmp_path, name, old, new):
-    r = run_pins_on_copy(tmp_path, old, new)
+def test_pins_catch_planted_mistake(mutant_runs, name, old, new):
+    r = mutant_runs[name]
     assert r.returncode != 0, f"no pin caught mutation '{name}':\n{r.stdout[-2000:]}"
     assert "failed" in r.stdout, r.stdout[-2000:]
