@@ -512,6 +512,7 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
     stats->n_eff = (int64_t)ne_h[count - 1];
     stats->ring_stages = pl.nst;
     stats->ctas_per_sm = pl.k;
+    stats->steps_per_pass = 1;
   }
   return KITE_OK;
 }
