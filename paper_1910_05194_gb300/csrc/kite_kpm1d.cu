@@ -246,7 +246,7 @@ int sweep_two(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, v
 // mode, size bucket) on the context.  KITE_AUTOTUNE=0 keeps the default (8 stages, full
 // occupancy, one step per pass).
 struct Tune {
-  int nst;       // ring depth: 4 or 8 (two-step pass: 4, 6 or 8)
+  int nst;       // ring depth: 4 or 8 (two-step pass: 5, 6 or 8)
   int k;         // resident CTAs per SM
   int two = 0;   // 1: two recursion steps per pass (temporal blocking)
 };
@@ -329,14 +329,14 @@ Tune autotune(kite_ctx* ctx, long long units, const Plan& p, const Real* vt, Rea
   const bool two_ok = two_step_allowed<MODE>(p);
   const bool two_only = two_ok && pass_steps_pinned() == 2;
   Tune def{kStages, step_occupancy<Real, LAT, C, MODE, kStages>(), 0};
-  if (two_only) def = Tune{4, std::max(1, step2_occupancy<Real, LAT, C, 4>()), 1};
+  if (two_only) def = Tune{5, std::max(1, step2_occupancy<Real, LAT, C, 5>()), 1};
   // KITE_TUNE=<stages>x<CTAs per SM>[x2] pins one configuration (reproducible profiles):
-  // stages 4 or 8 (6 also for the two-step pass), x2 = the two-step pass
+  // stages 4 or 8 (5, 6 or 8 for the two-step pass), x2 = the two-step pass
   if (const char* e = getenv("KITE_TUNE")) {
     int nst = 0, k = 0, two = 1;
     if (sscanf(e, "%dx%dx%d", &nst, &k, &two) >= 2) {
       const bool t2 = two == 2 && two_ok;
-      const int occ = t2 ? (nst == 4   ? step2_occupancy<Real, LAT, C, 4>()
+      const int occ = t2 ? (nst == 5   ? step2_occupancy<Real, LAT, C, 5>()
                             : nst == 6 ? step2_occupancy<Real, LAT, C, 6>()
                             : nst == 8 ? step2_occupancy<Real, LAT, C, 8>() : 0)
                          : (nst == 4   ? step_occupancy<Real, LAT, C, MODE, 4>()
@@ -371,7 +371,7 @@ Tune autotune(kite_ctx* ctx, long long units, const Plan& p, const Real* vt, Rea
     const float bar = two_only ? 1e30f : 0.97f * best_ms;
     float best2 = bar;
     const int o8 = step2_occupancy<Real, LAT, C, 8>(), o6 = step2_occupancy<Real, LAT, C, 6>(),
-              o4 = step2_occupancy<Real, LAT, C, 4>();
+              o5 = step2_occupancy<Real, LAT, C, 5>();
     for (int k = 1; k <= o8; ++k) {
       const float ms = time_candidate2<Real, LAT, C, 8>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
       if (ms < best2) best2 = ms, best = Tune{8, k, 1};
@@ -380,9 +380,9 @@ Tune autotune(kite_ctx* ctx, long long units, const Plan& p, const Real* vt, Rea
       const float ms = time_candidate2<Real, LAT, C, 6>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
       if (ms < best2 * 0.98f) best2 = ms, best = Tune{6, k, 1};
     }
-    for (int k = 1; k <= o4; ++k) {
-      const float ms = time_candidate2<Real, LAT, C, 4>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
-      if (ms < best2 * 0.98f) best2 = ms, best = Tune{4, k, 1};
+    for (int k = 1; k <= o5; ++k) {
+      const float ms = time_candidate2<Real, LAT, C, 5>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
+      if (ms < best2 * 0.98f) best2 = ms, best = Tune{5, k, 1};
     }
   }
   cudaGetLastError();
@@ -398,7 +398,7 @@ int max_grid_c(kite_ctx* ctx, int C, long long units) {
     int o = std::max(step_occupancy<Real, LAT, CC, MODE, 8>(), step_occupancy<Real, LAT, CC, MODE, 4>());
     if (MODE == 0)
       o = std::max({o, step2_occupancy<Real, LAT, CC, 8>(), step2_occupancy<Real, LAT, CC, 6>(),
-                    step2_occupancy<Real, LAT, CC, 4>()});
+                    step2_occupancy<Real, LAT, CC, 5>()});
     return o;
   };
   if (C == 1) return g(occ(std::integral_constant<int, 1>{}));
@@ -527,7 +527,7 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
                         : autotune<Real, LAT, CC, 0>(ctx, u, p, vt, tt, r0, bA, bB, bC, bD, partial); \
     tune_used = t;                                                                                  \
     if (t.two) {                                                                                    \
-      const int G = t.nst == 4   ? step2_grid<Real, LAT, CC, 4>(ctx, u, t.k)                        \
+      const int G = t.nst == 5   ? step2_grid<Real, LAT, CC, 5>(ctx, u, t.k)                        \
                     : t.nst == 6 ? step2_grid<Real, LAT, CC, 6>(ctx, u, t.k)                        \
                                  : step2_grid<Real, LAT, CC, 8>(ctx, u, t.k);                       \
       grid_used = G;                                                                                \
@@ -537,7 +537,7 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
                                                                mu_vec, &lp, &lc, &step_s, &step_n,   \
                                                                &step_bytes);                         \
       };                                                                                            \
-      rc = t.nst == 4   ? run2(std::integral_constant<int, 4>{})                                    \
+      rc = t.nst == 5   ? run2(std::integral_constant<int, 5>{})                                    \
            : t.nst == 6 ? run2(std::integral_constant<int, 6>{})                                    \
                         : run2(std::integral_constant<int, 8>{});                                   \
     } else {                                                                                        \

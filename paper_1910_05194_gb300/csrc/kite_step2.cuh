@@ -32,7 +32,7 @@ struct Step2Shape {
   static constexpr int R0B = TX * CELLB;        // r_0 row
   static constexpr int STAGEB = RNB + R0B;      // (r_{n-1} is read once per site: registers)
   static constexpr int TILEB = (TX + 2) * CELLB;  // one r_{n+1} row of the tile ring
-  static constexpr int SMEM = kBarBytes + NST * STAGEB + 3 * TILEB;
+  static constexpr int SMEM = kBarBytes + NST * STAGEB + 4 * TILEB;
 };
 
 // Threads: kBlock compute threads (one 16-byte chunk of an owned cell each, as in the
@@ -227,78 +227,86 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
     const size_t ocol = ((size_t)(x0 + xl) * SORB + s) * C + c;
     const size_t orow = (size_t)Lx * SORB * C;
     Real v1 = loads_v ? vload(yb - 1) : Real(0);
-    Real vprev = Real(0);
     // r_{n-1} of the same cell, read straight from global memory one row ahead (it is
     // used once, by this thread)
     const size_t pcol = ((size_t)xv * SORB + s) * C + c;
     auto pload = [&](int y) { return Ch::ldg(r_prev, pcol + (size_t)wrapy(y) * orow); };
     Ch pv1 = loads_v ? pload(yb - 1) : Ch{};
-    // stage of slot i (slots i, i+1, i+2 hold r_n rows y1-1, y1, y1+1) and tile rows of
-    // r_{n+1} rows y1-2, y1-1, y1
-    int st0 = (int)(gslot % NST);
-    // (tile rows rotate as byte offsets: pointers carried around the loop would hide
-    // from the compiler that they address shared memory)
-    int o0 = 0, o1 = Sh::TILEB, o2 = 2 * Sh::TILEB;
+    // One barrier per row: iteration i computes r_{n+1} row yb-1+i (slots i, i+1, i+2 hold
+    // r_n rows yb-2+i .. yb+i) into tile row i mod 4, and r_{n+2} row yb-3+i from the three
+    // tile rows written by the previous iterations, with r_n and r_0 of that row from slot
+    // i-1.  Slot i-1 is free after iteration i.  (Tile rows rotate as byte offsets: pointers
+    // carried around the loop would hide from the compiler that they address shared memory.)
+    int st0 = (int)(gslot % NST);           // stage of slot i
+    int stm = st0 == 0 ? NST - 1 : st0 - 1;  // stage of slot i-1
+    int o0 = 0, o1 = Sh::TILEB, o2 = 2 * Sh::TILEB, o3 = 3 * Sh::TILEB;  // tile rows i-3 .. i
+    Real vm1 = Real(0), vm2 = Real(0);  // on-site terms of the rows of iterations i-1, i-2
+    int issued = min(NST, nslots);      // slots issued so far (producer's count)
     int i = 0;
-    for (; i < nr + 2; ++i) {
-      const Real v1n = (loads_v && i + 1 < nr + 2) ? vload(yb + i) : Real(0);
-      const Ch pvn = (loads_v && i + 1 < nr + 2) ? pload(yb + i) : Ch{};
-      // r_{n+1} row y1 = yb-1+i needs r_n rows in slots i, i+1, i+2
+    for (; i < nr + 3; ++i) {
+      const bool do1 = i < nr + 2;  // r_{n+1} row yb-1+i
+      const bool do2 = i >= 3;      // r_{n+2} row yb-3+i
+      const bool more = loads_v && i + 1 < nr + 2;
+      const Real v1n = more ? vload(yb + i) : Real(0);
+      const Ch pvn = more ? pload(yb + i) : Ch{};
       bool ok = true;
-      if (compute || halo)
+      if (do1 && (compute || halo))
         for (int jj = (i == 0 ? 0 : i + 2); jj <= i + 2; ++jj) {
           const long long g = gslot + jj;
           ok = mbar_wait_bounded_hint(&bars[g % NST], (uint32_t)((g / NST) & 1)) && ok;
         }
       if (!ok) s_abort = 1;
-      const int y1 = wrapy(yb - 1 + i);
       const int st1 = st0 + 1 == NST ? 0 : st0 + 1;
       const int st2 = st1 + 1 == NST ? 0 : st1 + 1;
       const unsigned char* up = stages + st0 * Sh::STAGEB;
       const unsigned char* mid = stages + st1 * Sh::STAGEB;
       const unsigned char* dn = stages + st2 * Sh::STAGEB;
-      unsigned char* t2 = tile + o2;
-      if (ok && active) {  // own cell (tile cell xl+1)
+      unsigned char* t3 = tile + o3;
+      if (do1 && ok && active) {  // own cell (tile cell xl+1)
         const Ch o = site1(up, mid, dn, xl + 1, v1, pv1);
-        *reinterpret_cast<Ch*>(t2 + (xl + 1) * CELLB + choff) = o;
+        *reinterpret_cast<Ch*>(t3 + (xl + 1) * CELLB + choff) = o;
         if (i >= 1 && i <= nr) {
-          o.st(out1, ocol + (size_t)y1 * orow);
+          o.st(out1, ocol + (size_t)wrapy(yb - 1 + i) * orow);
           const Ch z0 = *reinterpret_cast<const Ch*>(mid + Sh::RNB + xl * CELLB + choff);
           accumulate(facc1, dacc1, rows1, z0, o);
         }
       }
-      if (ok && halo) {  // halo cell left (tile cell 0) or right (tile cell txv+1)
+      if (do1 && ok && halo) {  // halo cell left (tile cell 0) or right (tile cell txv+1)
         const int tx = hcell ? txv + 1 : 0;
-        *reinterpret_cast<Ch*>(t2 + tx * CELLB + choff) = site1(up, mid, dn, tx, v1, pv1);
+        *reinterpret_cast<Ch*>(t3 + tx * CELLB + choff) = site1(up, mid, dn, tx, v1, pv1);
       }
-      __syncthreads();  // the r_{n+1} row is in the tile
-      if (s_abort) {
-        aborted = true;
-        break;
-      }
-      if (i >= 2 && active) {
-        // r_{n+2} row y2 = y1 - 1 from tile rows y1-2, y1-1, y1 and r_n row y2 (slot i)
-        const int y2 = y1 == 0 ? Ly - 1 : y1 - 1;
-        const Ch o = site2(tile + o0, tile + o1, t2, up, vprev);
-        o.st(out2, ocol + (size_t)y2 * orow);
-        const Ch z0 = *reinterpret_cast<const Ch*>(up + Sh::RNB + xl * CELLB + choff);
+      if (do2 && ok && active) {
+        // r_{n+2} row y2 = yb-3+i from tile rows y2-1, y2, y2+1 and r_n, r_0 of row y2
+        const unsigned char* prev = stages + stm * Sh::STAGEB;
+        const Ch o = site2(tile + o0, tile + o1, tile + o2, prev, vm2);
+        o.st(out2, ocol + (size_t)(yb - 3 + i) * orow);
+        const Ch z0 = *reinterpret_cast<const Ch*>(prev + Sh::RNB + xl * CELLB + choff);
         accumulate(facc2, dacc2, rows2, z0, o);
       }
-      vprev = v1;
+      vm2 = vm1;
+      vm1 = v1;
       v1 = v1n;
       pv1 = pvn;
+      stm = st0;
       st0 = st1;
       const int of = o0;  // the oldest tile row takes the next r_{n+1} row
       o0 = o1;
       o1 = o2;
-      o2 = of;
-      __syncthreads();  // slot i and the oldest tile row are free
-      if (tid == kProducer && i + NST < nslots) issue(i + NST);
+      o2 = o3;
+      o3 = of;
+      __syncthreads();  // the tile row is complete; slot i-1 and the oldest tile row are free
+      if (s_abort) {
+        aborted = true;
+        break;
+      }
+      if (tid == kProducer && i >= 1 && i - 1 + NST < nslots) {
+        issue(i - 1 + NST);
+        issued = i + NST;
+      }
     }
     if (aborted) {
       if (tid == kProducer) {
-        const int last = min(nslots, i + NST) - 1;
-        for (int jj = i; jj <= last; ++jj) {
+        for (int jj = i; jj < issued; ++jj) {  // completed phases return at once
           const long long g = gslot + jj;
           mbar_wait_bounded(&bars[g % NST], (uint32_t)((g / NST) & 1));
         }
