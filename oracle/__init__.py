@@ -432,6 +432,62 @@ def sigma_dc(mu_nm, E, e_min: float, e_max: float, lattice: int, kernel: str = "
     return out
 
 
+def sigma_dc_bastin(mu_nm, E_F, e_min: float, e_max: float, eta: float, lattice: int,
+                    kernel: str = "jackson", lam: float = 4.0, n_quad: int = 0, kT: float = 0.0):
+    """DC conductivity tensor element sigma_ab(E_F) in units of e^2/hbar per spin from the
+    Kubo-Bastin formula (the omega -> 0 response of Sec. 2b, full-spectral form of the
+    Hall-conductivity example): with f the Fermi function,
+      sigma_ab = i hbar e^2/Omega int de f(e) Tr[v_a delta(e - H) v_b dG^R/de
+                                                - v_a dG^A/de v_b delta(e - H)],
+    rescaled (v = -i (de_minus a/hbar) h~) and expanded in Chebyshev polynomials:
+      sigma_ab = Re{ i (n_orb a^2/Omega_c) int de f(e) sum_nm mu_nm
+                        [Delta_n(e) dG^R_m(e) - dG^A_n(e) Delta_m(e)] },
+      Delta_n(e) = k_n (2 - d_n0) T_n(e) / (pi sqrt(1 - e^2)),
+      G^{R/A}_m(e) = k_m g^{+-}_m(e +- i eta) / (1 + d_m0)     (CPGF, Eq. green_function_cheb_expansionb),
+      d g_m/dz = g_m(z) [sigma i m / sqrt(1 - z^2) + z / (1 - z^2)],
+    mu_nm = <r|v_a T_n v_b T_m|r>/N the 2D moments, k_n the kernel (None: k_n = 1), eta
+    (eV) the CPGF broadening that keeps the integrand regular at the band edges.  The
+    Fermi sea runs over the rescaled band [-1, e_F] (kT > 0: the whole band weighted by the
+    Fermi function), by Gauss-Legendre quadrature in theta, e = cos(theta).  E_F: array."""
+    mu = np.asarray(mu_nm, np.complex128)
+    M = mu.shape[0]
+    dm, dp = 0.5 * (e_max - e_min), 0.5 * (e_max + e_min)
+    if kernel == "jackson":
+        k = kernel_jackson(M)
+    elif kernel == "lorentz":
+        k = kernel_lorentz(M, lam)
+    else:
+        k = np.ones(M)
+    n = np.arange(M)
+    kw = k * np.where(n == 0, 0.5, 1.0)
+    A = mu * kw[:, None] * kw[None, :]   # kernel and 1/(1 + d_n0) of both series
+    et = eta / dm
+    K = n_quad if n_quad > 0 else 2 * M + 64
+    x, w = np.polynomial.legendre.leggauss(K)
+    out = np.zeros(len(np.atleast_1d(E_F)))
+    for i, Ef in enumerate(np.atleast_1d(np.asarray(E_F, np.float64))):
+        eF = (Ef - dp) / dm
+        if kT <= 0.0 and eF <= -1.0:
+            continue
+        thF = np.arccos(min(eF, 1.0)) if kT <= 0.0 else 0.0
+        theta = thF + (np.pi - thF) * 0.5 * (x + 1.0)
+        wq = w * 0.5 * (np.pi - thF)
+        e = np.cos(theta)
+        if kT > 0.0:
+            wq = wq / (1.0 + np.exp((e * dm + dp - Ef) / kT))
+        # Delta_n(e) de without k_n and 1/(1 + d_n0) (those sit in A): (2/pi) cos(n theta) dtheta
+        D = (2.0 / np.pi) * np.cos(n[:, None] * theta[None, :]) * wq[None, :]
+        dG = []
+        for sg in (+1, -1):
+            z = e + 1j * sg * et
+            s1 = np.sqrt(1.0 - z * z)
+            dG.append(cpgf_coeffs(M, e, et, sg) * (sg * 1j * n[:, None] / s1[None, :]
+                                                  + (z / (s1 * s1))[None, :]))
+        S = np.sum(D * (A @ dG[0])) - np.sum(dG[1] * (A @ D))
+        out[i] = float(np.real(1j * unit_cell_factor(lattice) * S))
+    return out
+
+
 def sigma_xx(mu_nm, omega, e_min: float, e_max: float, E_F: float, eta: float, lattice: int,
              kernel: str = "jackson", n_quad: int = 0, gamma_n=None, kT: float = 0.0):
     """First-order optical conductivity sigma_xx(omega) in units of e^2/hbar (T = 0),

@@ -286,6 +286,27 @@ static double orc_orbital_y(const orc_system* sys, int64_t o) {
   return (double)(o / sys->Lx);
 }
 
+/* Peierls phases of every bond of h (geometry already filled in), or h->ph = NULL without
+ * a field.  0, -2 (allocation) or -4 (flux does not fit the torus). */
+static int orc_ham_phases(orc_ham* h, const orc_system* sys) {
+  h->ph = NULL;
+  if (sys->flux == 0.0) return 0;
+  if (orc_flux_fits(sys)) return -4;
+  h->ph = (double*)malloc(sizeof(double) * 8 * h->N);
+  if (!h->ph) return -2;
+  const double cell_area = sys->lattice == 0 ? 0.5 * sqrt(3.0) : 1.0;
+  const double k = -2.0 * 3.141592653589793 * sys->flux / cell_area;
+  for (int64_t o = 0; o < h->N; ++o) {
+    double yo = orc_orbital_y(sys, o);
+    for (int b = 0; b < 4; ++b) {
+      double th = b < h->Z ? k * (yo - 0.5 * h->dy[4 * o + b]) * h->dx[4 * o + b] : 0.0;
+      h->ph[8 * o + 2 * b] = cos(th);
+      h->ph[8 * o + 2 * b + 1] = sin(th);
+    }
+  }
+  return 0;
+}
+
 static int orc_ham_build(orc_ham* h, const orc_system* sys, int realisation, double e_min,
                          double e_max) {
   h->N = orc_norb(sys);
@@ -306,23 +327,7 @@ static int orc_ham_build(orc_ham* h, const orc_system* sys, int realisation, dou
     if (!h->vac[o]) h->n_eff++;
   }
   h->tt = sys->t / de_minus;
-  h->ph = NULL;
-  if (sys->flux != 0.0) {
-    if (orc_flux_fits(sys)) return -4;
-    h->ph = (double*)malloc(sizeof(double) * 8 * h->N);
-    if (!h->ph) return -2;
-    const double cell_area = sys->lattice == 0 ? 0.5 * sqrt(3.0) : 1.0;
-    const double k = -2.0 * 3.141592653589793 * sys->flux / cell_area;
-    for (int64_t o = 0; o < h->N; ++o) {
-      double yo = orc_orbital_y(sys, o);
-      for (int b = 0; b < 4; ++b) {
-        double th = b < h->Z ? k * (yo - 0.5 * h->dy[4 * o + b]) * h->dx[4 * o + b] : 0.0;
-        h->ph[8 * o + 2 * b] = cos(th);
-        h->ph[8 * o + 2 * b + 1] = sin(th);
-      }
-    }
-  }
-  return 0;
+  return orc_ham_phases(h, sys);
 }
 
 static void orc_ham_free(orc_ham* h) {
@@ -641,8 +646,15 @@ static void orc_apply_v(const orc_ham* h, int dir, const double* x, double* y) {
         int64_t j = h->nb[4 * o + k];
         if (h->vac[j]) continue;
         double w = off[4 * o + k] * h->tt;
-        re += w * x[2 * j];
-        im += w * x[2 * j + 1];
+        double xr = x[2 * j], xi = x[2 * j + 1];
+        if (h->ph) { /* [r, H~]_oj = (r_o - r_j) t~ exp(i theta_oj) */
+          double c = h->ph[8 * o + 2 * k], sn = h->ph[8 * o + 2 * k + 1];
+          double r2 = c * xr - sn * xi;
+          xi = sn * xr + c * xi;
+          xr = r2;
+        }
+        re += w * xr;
+        im += w * xi;
       }
     }
     y[2 * o] = re;
@@ -659,13 +671,13 @@ void orc_velocity(const orc_system* sys, const uint8_t* vac, double t_scaled, in
   h.dy = (double*)malloc(sizeof(double) * 4 * h.N);
   h.vac = (uint8_t*)vac;
   h.tt = t_scaled;
-  h.ph = NULL;
   for (int64_t o = 0; o < h.N; ++o)
     h.Z = orc_neighbours_geo(sys, o, h.nb + 4 * o, h.dx + 4 * o, h.dy + 4 * o);
-  orc_apply_v(&h, dir, in, out);
+  if (orc_ham_phases(&h, sys) == 0) orc_apply_v(&h, dir, in, out);
   free(h.nb);
   free(h.dx);
   free(h.dy);
+  free(h.ph);
 }
 
 void orc_velocity_x(const orc_system* sys, const uint8_t* vac, double t_scaled,
@@ -701,7 +713,6 @@ static void orc_family(const orc_ham* h, int M, const double* start, double* fam
 int orc_moments_2d(const orc_system* sys, int realisation, int M, int R, double e_min,
                    double e_max, const double* r0_in, double* mu_nm, double* a_fam,
                    double* b_fam, int dir_a, int dir_b, int threads) {
-  if (sys->flux != 0.0) return -3; /* built without Peierls phases */
 #ifdef _OPENMP
   if (threads > 0) omp_set_num_threads(threads);
 #else

@@ -705,6 +705,136 @@ def test_dc_conductivity_is_the_zero_frequency_limit_of_the_optical_one():
         assert dc > 0.1 and abs(opt / dc - 1.0) < 0.1, (E_F, dc, opt)
 
 
+def dense_v(sys, direction):
+    """v~ = -i h~ (h~ = [r_dir, H~]) of the oracle as a dense matrix, with its field phases."""
+    lo, hi = oracle.bounds_auto(sys)
+    n = oracle.norb(sys)
+    _, vac = oracle.disorder(sys)
+    eye = np.eye(n, dtype=np.complex128)
+    cols = [oracle.velocity(sys, vac, sys.t / (0.5 * (hi - lo)), eye[:, j], direction) for j in range(n)]
+    return -1j * np.array(cols).T
+
+
+def tknn_sigma_xy(H, vx, vy, eF, ucf):
+    """T = 0 Kubo formula in the eigenbasis (the textbook TKNN sum),
+    sigma_xy = -2 (n_orb a^2/Omega_c)/N sum_{a occupied, b empty} Im[(vx)_ab (vy)_ba] / (e_a - e_b)^2,
+    in units of e^2/hbar (rescaled energies and velocities: the ratio is scale free)."""
+    lam, U = np.linalg.eigh(H)
+    X, Y = U.conj().T @ vx @ U, U.conj().T @ vy @ U
+    a, b = np.where(lam < eF)[0], np.where(lam >= eF)[0]
+    d = lam[a][:, None] - lam[b][None, :]
+    return -2.0 * ucf / H.shape[0] * float(np.sum(np.imag(X[np.ix_(a, b)] * Y[np.ix_(b, a)].T) / d ** 2))
+
+
+@pytest.mark.parametrize("lattice,flux", [(oracle.HONEYCOMB, 0.25), (oracle.SQUARE, 0.375)])
+def test_velocity_in_a_field_is_the_position_commutator(lattice, flux):
+    """v = i[H, r]/hbar holds with the Peierls phases: every element of h~ = [r, H~] is the
+    minimum-image bond vector r_i - r_j times the element of the oracle's rescaled H~ (taken
+    from its recursion, with disorder and vacancies), so the velocity carries the same
+    phases as the Hamiltonian; built from the orbital positions, not the bond tables."""
+    t = -1.0 if lattice == oracle.SQUARE else T_EV
+    sys = oracle.make_system(lattice=lattice, Lx=6, Ly=8, t=t, W=1.0, p_vac=0.05, seed=4, flux=flux)
+    H = dense_from_operator(sys)
+    P = oracle.orbital_positions(sys)
+    if lattice == oracle.HONEYCOMB:
+        T1, T2 = np.array([sys.Lx, 0.0]), np.array([0.5 * sys.Ly, 0.5 * math.sqrt(3.0) * sys.Ly])
+    else:
+        T1, T2 = np.array([sys.Lx, 0.0]), np.array([0.0, sys.Ly])
+    d0 = P[:, None, :] - P[None, :, :]
+    best = d0.copy()
+    for i in (-1, 0, 1):
+        for j in (-1, 0, 1):
+            c = d0 + i * T1 + j * T2
+            shorter = np.sum(c * c, -1) < np.sum(best * best, -1)
+            best[shorter] = c[shorter]
+    for direction in (0, 1):
+        h = 1j * dense_v(sys, direction)
+        assert np.max(np.abs(h - best[..., direction] * H)) < 1e-14
+        assert np.max(np.abs(h + h.conj().T)) < 1e-15
+
+
+def bastin_eigenbasis(H, vx, vy, eF, eta, M, ucf, kT=0.0, dm=1.0, K=20001):
+    """sigma_xy of the Kubo-Bastin formula with the exact broadened resolvent derivative
+    -1/(e +- i eta - e_a)^2 and the M-term Chebyshev delta function (no kernel), in the
+    eigenbasis; Simpson quadrature in theta over the Fermi sea (kT > 0: the whole band
+    with Fermi weights, energies in units of dm)."""
+    n = H.shape[0]
+    lam, U = np.linalg.eigh(H)
+    X = (U.conj().T @ vx @ U) * (U.conj().T @ vy @ U).T      # X_ab = (vx)_ab (vy)_ba
+    thF = np.arccos(eF) if kT <= 0.0 else 0.0
+    th = np.linspace(thF, np.pi, K)
+    wk = np.full(K, 2.0)
+    wk[1:-1:2] = 4.0
+    wk[0] = wk[-1] = 1.0
+    wk *= (th[1] - th[0]) / 3.0
+    e = np.cos(th)
+    if kT > 0.0:
+        wk = wk / (1.0 + np.exp((e - eF) * dm / kT))
+    cm = np.where(np.arange(M) == 0, 1.0, 2.0) / np.pi
+    Dk = (cheb_T(M, lam) * cm[:, None]).T @ np.cos(np.arange(M)[:, None] * th[None, :]) * wk[None, :]
+    GR = -1.0 / (e[None, :] + 1j * eta - lam[:, None]) ** 2
+    GA = -1.0 / (e[None, :] - 1j * eta - lam[:, None]) ** 2
+    T1 = np.sum(GR * (X @ Dk))
+    T2 = np.sum(Dk * (X @ GA))
+    return float(np.real(1j * ucf / n * (T1 - T2)))
+
+
+def test_bastin_dc_matches_eigenstate_formula():
+    """DC Kubo-Bastin (sigma_xy and sigma_xx, T = 0 and kT > 0) of a tiny disordered
+    honeycomb in a field against the eigenbasis evaluation with exact resolvent
+    derivatives: the CPGF derivative coefficients, the Delta_n series, the order of the
+    velocities in mu_nm and the Fermi-sea limits are all checked at once (the broadening
+    makes the CPGF series converge exponentially: M = 400 terms are exact to about 1e-11)."""
+    sys = oracle.make_system(Lx=4, Ly=4, t=T_EV, W=1.0, seed=3, flux=0.5)
+    lo, hi = oracle.bounds_auto(sys)
+    dm = 0.5 * (hi - lo)
+    n = oracle.norb(sys)
+    M, eta = 400, 0.6
+    H = dense_from_operator(sys)
+    vx, vy = dense_v(sys, 0), dense_v(sys, 1)
+    ucf = oracle.unit_cell_factor(oracle.HONEYCOMB)
+    eye = np.eye(n, dtype=np.complex128)
+    for (a, b), (A, B) in (((0, 1), (vx, vy)), ((0, 0), (vx, vx))):
+        mu = oracle.moments_2d(sys, M, n, r0=eye, alpha=a, beta=b) * n
+        for E_F, kT in ((-2.0, 0.0), (0.7, 0.0), (0.7, 0.3)):
+            got = oracle.sigma_dc_bastin(mu, [E_F], lo, hi, eta, oracle.HONEYCOMB, kernel=None,
+                                         n_quad=1000, kT=kT)[0]
+            ref = bastin_eigenbasis(H, A, B, E_F / dm, eta / dm, M, ucf, kT=kT, dm=dm)
+            assert abs(got - ref) <= 2e-10, ((a, b), E_F, kT, got, ref)
+    assert oracle.sigma_dc_bastin(mu, [lo - 1.0], lo, hi, eta, oracle.HONEYCOMB)[0] == 0.0
+
+
+def test_quantum_hall_plateau():
+    """Graphene in a field with E_F in the gap above the zero Landau level: the textbook
+    Kubo (TKNN) sum on the oracle's dense H~ and field velocities gives sigma_xy = -e^2/h
+    per spin (one filled level of the Dirac sequence (2n + 1) e^2/h per spin, valleys
+    summed; 1/(2 pi) in units of e^2/hbar) to 0.5 % on a 16 x 16 torus, and -e^2/h
+    mirrored below it; the Kubo-Bastin reconstruction from the exact-trace moments of an
+    8 x 16 torus converges to that torus's TKNN value as M grows (Jackson kernel, small
+    eta), and sigma_xx vanishes in the gap."""
+    ucf = oracle.unit_cell_factor(oracle.HONEYCOMB)
+    big = oracle.make_system(Lx=16, Ly=16, t=T_EV, flux=0.125)
+    lo, hi = oracle.bounds_auto(big)
+    dm = 0.5 * (hi - lo)
+    Hb, vxb, vyb = dense_from_operator(big), dense_v(big, 0), dense_v(big, 1)
+    for E_F, sign in ((1.35, -1.0), (-1.35, 1.0)):   # the gap spans 0.26 - 2.44 eV
+        q = tknn_sigma_xy(Hb, vxb, vyb, E_F / dm, ucf) * 2 * math.pi
+        assert abs(q - sign) < 5e-3, (E_F, q)
+    sys = oracle.make_system(Lx=8, Ly=16, t=T_EV, flux=0.125)
+    n = oracle.norb(sys)
+    H, vx, vy = dense_from_operator(sys), dense_v(sys, 0), dense_v(sys, 1)
+    ref = tknn_sigma_xy(H, vx, vy, 1.35 / dm, ucf)
+    eye = np.eye(n, dtype=np.complex128)
+    err = []
+    for M in (96, 192):
+        mu = oracle.moments_2d(sys, M, n, r0=eye, alpha=0, beta=1) * n
+        err.append(abs(oracle.sigma_dc_bastin(mu, [1.35], lo, hi, 0.01, oracle.HONEYCOMB)[0] / ref - 1))
+    assert err[1] < 0.03 and err[1] < 0.7 * err[0], err
+    mu = oracle.moments_2d(sys, 192, n, r0=eye) * n
+    sxx = oracle.sigma_dc_bastin(mu, [1.35], lo, hi, 0.01, oracle.HONEYCOMB)[0]
+    assert abs(sxx) < 0.02 * abs(ref), sxx
+
+
 def test_mlp_gradient_matches_finite_differences():
     """The reference MLP's analytic gradient against central differences in FP64 (small
     widths; points kept away from the ReLU and |.| kinks)."""
