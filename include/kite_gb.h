@@ -85,7 +85,8 @@ extern "C" {
  *            A at (0, -a_cc/2), B at (0, +a_cc/2), a_cc = 1/sqrt3).  On the torus
  *            flux * Ly must be even (honeycomb) or an integer (square);
  *            kite_flux_nearest gives the nearest such flux.  Accepted by
- *            kite_moments_1d (complex start vectors), kite_spectral_k and kite_ldos;
+ *            kite_moments_1d (complex start vectors), kite_moments_2d (the velocity
+ *            h~ = [r, H~] carries the same bond phases), kite_spectral_k and kite_ldos;
  *            the other calls return KITE_ERR_ARG for a nonzero flux. */
 typedef struct {
   int32_t lattice;
@@ -489,7 +490,8 @@ int kite_reconstruct_green(kite_ctx* ctx, const double* mu, int M_avail, int M_u
  * i.e. pi hbar e^2/Omega Tr[v delta(E-H) v delta(E-H)] with both delta functions expanded
  * in M_use kernel-damped Chebyshev terms (Sec. 2a); 0 outside the spectrum window.
  * n_orb a^2/Omega_c = 4/sqrt(3) (honeycomb), 1 (square).  FP64 on the GPU, fixed-order
- * sums.  The Fermi-sea (Hall) term of the DC Kubo-Bastin formula is not part of it.
+ * sums.  The Fermi-sea (Hall) term of the DC Kubo-Bastin formula is not part of it: see
+ * kite_reconstruct_sigma_dc_bastin.
  *   mu_nm   [M_avail][M_avail] complex FP64, host or device; the leading M_use block is used
  *   kernel  KITE_KERNEL_NONE / _JACKSON / _LORENTZ (param = lambda)
  *   E       [K] Fermi energies (eV), host or device;  sigma  [K] FP64, host or device
@@ -497,6 +499,30 @@ int kite_reconstruct_green(kite_ctx* ctx, const double* mu, int M_avail, int M_u
 int kite_reconstruct_sigma_dc(kite_ctx* ctx, const double* mu_nm, int M_avail, int M_use, int lattice,
                               int kernel, double param, double e_min, double e_max, const double* E, int K,
                               double* sigma);
+
+/* DC conductivity tensor element sigma_ab(E_F) in units of e^2/hbar per spin from the
+ * Kubo-Bastin formula with its Fermi-sea term (the Hall conductivity of the quantum
+ * anomalous Hall example and the omega -> 0 limit of Sec. 2b), from the 2D moments
+ * mu_nm = <r|v_a T_n v_b T_m|r>/N of kite_moments_2d(alpha = a, beta = b):
+ *   sigma_ab = Re{ i (n_orb a^2/Omega_c) int de f(e) sum_nm mu_nm
+ *                    [Delta_n(e) dG^R_m(e)/de - dG^A_n(e)/de Delta_m(e)] },
+ *   Delta_n(e) = k_n (2 - d_n0) T_n(e) / (pi sqrt(1 - e^2)),
+ *   G^{R/A}_m(e) = k_m g^{+-}_m(e +- i eta~) / (1 + d_m0),
+ * with the CPGF coefficients g of Eq. green_function_cheb_expansionb, eta~ = eta/de_minus,
+ * k_n the kernel (KITE_KERNEL_NONE: 1) and f the Fermi function.  The finite eta keeps
+ * the integrand regular at the band edges; the Fermi sea is the rescaled band [-1, e_F]
+ * (kT = 0) or the whole band weighted by f (kT > 0, eV), integrated by Gauss-Legendre
+ * quadrature in theta (e = cos theta) with n_quad nodes per energy (0: 2 M_use + 64).
+ * With a magnetic field in the moments it gives the quantum Hall plateaus.  FP64 on the
+ * GPU; two M_use x M_use x n_quad GEMMs per Fermi energy.
+ *   mu_nm  [M_avail][M_avail] complex FP64, host or device; the leading M_use block is used
+ *   kernel KITE_KERNEL_NONE / _JACKSON / _LORENTZ (param = lambda)
+ *   eta    broadening in eV (> 0);  kT  temperature in eV (>= 0)
+ *   E_F    [K] Fermi energies (eV), host or device;  sigma  [K] FP64, host or device
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
+int kite_reconstruct_sigma_dc_bastin(kite_ctx* ctx, const double* mu_nm, int M_avail, int M_use, int lattice,
+                                     int kernel, double param, double e_min, double e_max, double eta, double kT,
+                                     const double* E_F, int K, int n_quad, double* sigma);
 
 /* First-order optical conductivity sigma_xx(omega) in units of e^2/hbar from the 2D
  * moments of kite_moments_2d (Sec. 2b, Eqs. Gammanm and conductivity_1st_order, in

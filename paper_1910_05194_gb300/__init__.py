@@ -30,7 +30,8 @@ EXPORTED = ("kite_create", "kite_destroy", "kite_set_stream", "kite_status_strin
             "kite_reconstruct_sigma", "kite_moments_1d_static", "kite_moments_1d_batched",
             "kite_mlp_param_count", "kite_mlp_train", "kite_mlp_forward", "kite_mlp_gradient",
             "kite_learned_gate", "kite_spectral_k", "kite_ldos", "kite_propagate",
-            "kite_evolution_coeffs", "kite_flux_nearest", "kite_reconstruct_sigma_dc")
+            "kite_evolution_coeffs", "kite_flux_nearest", "kite_reconstruct_sigma_dc",
+            "kite_reconstruct_sigma_dc_bastin")
 MLP_IN, MLP_HIDDEN, MLP_OUT = 128, 512, 1024
 
 
@@ -140,6 +141,9 @@ def lib():
             L.kite_reconstruct_sigma.restype = i32
             L.kite_reconstruct_sigma_dc.argtypes = [vp, vp, i32, i32, i32, i32, d, d, d, vp, i32, vp]
             L.kite_reconstruct_sigma_dc.restype = i32
+            L.kite_reconstruct_sigma_dc_bastin.argtypes = [vp, vp, i32, i32, i32, i32, d, d, d, d, d, vp, i32,
+                                                           i32, vp]
+            L.kite_reconstruct_sigma_dc_bastin.restype = i32
             L.kite_moments_1d_static.argtypes = [P(System), P(KPM), vp, vp, ctypes.c_char_p, i32]
             L.kite_moments_1d_static.restype = i32
             L.kite_moments_1d_batched.argtypes = [vp, i32, P(System), P(KPM), P(vp), P(Stats)]
@@ -255,6 +259,17 @@ def reconstruct_sigma_dc(ctx: Context, mu_nm, M_avail: int, M_use: int, lattice:
     ctx.check(lib().kite_reconstruct_sigma_dc(ctx.handle, _addr(mu_nm), int(M_avail), int(M_use), int(lattice),
                                               int(kernel), float(param), float(e_min), float(e_max), _addr(E),
                                               int(K), _addr(sigma)))
+
+
+def reconstruct_sigma_dc_bastin(ctx: Context, mu_nm, M_avail: int, M_use: int, lattice: int, kernel: int,
+                                param: float, e_min: float, e_max: float, eta: float, kT: float, E_F, K: int,
+                                sigma, n_quad: int = 0):
+    """kite_reconstruct_sigma_dc_bastin: DC sigma_ab (e^2/hbar per spin, Fermi sea included:
+    the Hall conductivity for a != b) at the Fermi energies E_F from the 2D moments."""
+    ctx.check(lib().kite_reconstruct_sigma_dc_bastin(ctx.handle, _addr(mu_nm), int(M_avail), int(M_use),
+                                                     int(lattice), int(kernel), float(param), float(e_min),
+                                                     float(e_max), float(eta), float(kT), _addr(E_F), int(K),
+                                                     int(n_quad), _addr(sigma)))
 
 
 def bounds(system: System):

@@ -34,6 +34,9 @@ int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, in
 int reconstruct_sigma_dc_impl(kite_ctx* ctx, const double* mu_dev, int M_avail, int M, int kernel, double param,
                               int lattice, const Scale& sc, const double* E_dev, int K, double* sigma_dev,
                               double* w);
+int reconstruct_sigma_bastin_impl(kite_ctx* ctx, const double* mu_dev, int M_avail, int M, int lattice,
+                                  int kernel, double param, const Scale& sc, double eta, double kT,
+                                  const double* E_host, int K_E, int n_quad, double* sigma_dev);
 int reconstruct_sigma_impl(kite_ctx* ctx, const double* mu_dev, int M_avail, int M, int lattice,
                            int kernel, const Scale& sc, double E_F, double kT, double eta,
                            const double* omega_host, int K_w, int n_quad, double* sigma_dev);
@@ -724,7 +727,6 @@ int kite_moments_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   int rc = validate_system(ctx, sys);
   if (rc != KITE_OK) return rc;
   if (!kpm || !mu_nm) return fail(ctx, KITE_ERR_ARG, "kpm and mu_nm are required");
-  if (sys->flux != 0.0) return fail(ctx, KITE_ERR_ARG, "2D moments take no magnetic field");
   if (kpm->M < 1 || kpm->R < 1 || kpm->S < 1 || kpm->M > 65536)
     return fail(ctx, KITE_ERR_ARG, "need 1 <= M <= 65536, R >= 1, S >= 1");
   if (kpm->precision != KITE_FP32)
@@ -924,6 +926,52 @@ int kite_reconstruct_sigma_dc(kite_ctx* ctx, const double* mu_nm, int M_avail, i
   cudaFreeAsync(buf, ctx->stream);
   cudaError_t es = cudaStreamSynchronize(ctx->stream);
   if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "reconstruct_sigma_dc");
+  return rc;
+}
+
+int kite_reconstruct_sigma_dc_bastin(kite_ctx* ctx, const double* mu_nm, int M_avail, int M_use, int lattice,
+                                     int kernel, double param, double e_min, double e_max, double eta, double kT,
+                                     const double* E_F, int K, int n_quad, double* sigma) {
+  if (!ctx) return KITE_ERR_ARG;
+  ctx->last_error.clear();
+  if (!mu_nm || !E_F || !sigma || K < 0 || M_avail < 1 || M_use < 1 || M_use > M_avail || M_use > 16384)
+    return fail(ctx, KITE_ERR_ARG, "need mu_nm, E_F, sigma and 1 <= M_use <= min(M_avail, 16384), K >= 0");
+  if (lattice != KITE_HONEYCOMB && lattice != KITE_SQUARE) return fail(ctx, KITE_ERR_ARG, "unknown lattice");
+  if (kernel != KITE_KERNEL_NONE && kernel != KITE_KERNEL_JACKSON && kernel != KITE_KERNEL_LORENTZ)
+    return fail(ctx, KITE_ERR_ARG, "unknown kernel");
+  if (kernel == KITE_KERNEL_LORENTZ && !(param > 0.0))
+    return fail(ctx, KITE_ERR_ARG, "Lorentz kernel needs lambda > 0");
+  if (!(e_max > e_min) || !isfinite(e_min) || !isfinite(e_max))
+    return fail(ctx, KITE_ERR_ARG, "need finite e_min < e_max");
+  if (!(eta > 0.0) || !isfinite(eta)) return fail(ctx, KITE_ERR_ARG, "eta must be finite and > 0");
+  if (!(kT >= 0.0) || !isfinite(kT)) return fail(ctx, KITE_ERR_ARG, "kT must be finite and >= 0");
+  if (n_quad < 0 || n_quad > (1 << 20)) return fail(ctx, KITE_ERR_ARG, "need 0 <= n_quad <= 2^20");
+  if (K == 0) return KITE_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
+  Scale sc{e_min, e_max, 0.5 * (e_max + e_min), 0.5 * (e_max - e_min)};
+  std::vector<double> E_host((size_t)K);
+  const bool mu_d = is_device_ptr(mu_nm), s_d = is_device_ptr(sigma);
+  cudaError_t e = cudaMemcpy(E_host.data(), E_F, (size_t)K * sizeof(double), cudaMemcpyDefault);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reading E_F");
+  for (int i = 0; i < K; ++i)
+    if (!isfinite(E_host[i])) return fail(ctx, KITE_ERR_ARG, "E_F must be finite");
+  const size_t mu_doubles = mu_d ? 0 : 2 * (size_t)M_avail * M_avail;
+  double* buf = nullptr;
+  KITE_CUDA_TRY(ctx, cudaMallocAsync((void**)&buf, sizeof(double) * (mu_doubles + (size_t)K), ctx->stream));
+  const double* mu_dev = mu_d ? mu_nm : buf;
+  double* s_dev = s_d ? sigma : buf + mu_doubles;
+  if (!mu_d) e = copy_in(ctx, buf, mu_nm, mu_doubles * sizeof(double));
+  int rc = e == cudaSuccess ? KITE_OK : cuda_fail(ctx, e, "copying mu_nm");
+  if (rc == KITE_OK)
+    rc = reconstruct_sigma_bastin_impl(ctx, mu_dev, M_avail, M_use, lattice, kernel, param, sc, eta, kT,
+                                       E_host.data(), K, n_quad, s_dev);
+  if (rc == KITE_OK && !s_d) {
+    e = copy_out(ctx, sigma, s_dev, (size_t)K * sizeof(double));
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "copying sigma");
+  }
+  cudaFreeAsync(buf, ctx->stream);
+  cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  if (rc == KITE_OK && es != cudaSuccess) rc = cuda_fail(ctx, es, "reconstruct_sigma_dc_bastin");
   return rc;
 }
 

@@ -11,6 +11,13 @@
 // recursion from r_0, each step writing h~b r_n (from the neighbours it already staged)
 // as the rows b_n and -i b_n.  The tensor-core contraction (kite_gemm.cu) then gives
 // Re and Im of <a_n|b_m> in one real GEMM per vector.
+//
+// In a perpendicular magnetic field (Peierls substitution, Sec. "Magnetic Field") both
+// H~ and h~ carry the phase exp(i theta_oj) of each bond with an x component:
+// h~_oj = (r_o - r_j) t~ exp(i theta_oj), the same gauge as the Hamiltonian, so that
+// v = i[H, r]/hbar.  The step kernel's FIELD variant rotates the neighbour values before
+// both the stencil sum and the velocity, and k_velocity rotates them the same way.
+#include "kite_internal.h"
 #include "kite_step.cuh"
 
 namespace kite {
@@ -31,9 +38,16 @@ constexpr int kGemmProducts = 4; // hi*hi + hi*lo + lo*hi + lo*lo
 // h~ = [r_dir, H~] applied to a whole FP32 batch (one chunk = two vectors).  mode 1: writes
 // the result as row `col` of the A family (and to out_vec if given); mode 2: rows `col`
 // and `col + M` of the extended B family.  Bond offsets as in the step kernel's MODE 2.
+// phase (or null: no field): the step kernel's table [y][s][bond][cos, sin] of the two
+// bonds with an x component (honeycomb n2, n3; square n1, n2).
 template <int LAT>
 __global__ void k_velocity(const float4* __restrict__ in, float4* __restrict__ out_vec,
-                           const float* __restrict__ vt, int Lx, int Ly, int mode, const FamOut fam) {
+                           const float* __restrict__ vt, int Lx, int Ly, int mode, const FamOut fam,
+                           const float* __restrict__ phase) {
+  auto rot = [](float4 n, float c, float sn) {  // exp(i theta) on both vectors of the chunk
+    return make_float4(fmaf(c, n.x, -(sn * n.y)), fmaf(sn, n.x, c * n.y), fmaf(c, n.z, -(sn * n.w)),
+                       fmaf(sn, n.z, c * n.w));
+  };
   constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
   const int64_t norb = (int64_t)Lx * Ly * SORB;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < norb;
@@ -49,8 +63,13 @@ __global__ void k_velocity(const float4* __restrict__ in, float4* __restrict__ o
       const int so = 1 - s;
       const int ny = s == 0 ? ym : yp, nx = s == 0 ? xp : xm;
       const float4 n1 = __ldg(in + cell * 2 + so);
-      const float4 n2 = __ldg(in + ((int64_t)ny * Lx + nx) * 2 + so);
-      const float4 n3 = __ldg(in + ((int64_t)ny * Lx + x) * 2 + so);
+      float4 n2 = __ldg(in + ((int64_t)ny * Lx + nx) * 2 + so);
+      float4 n3 = __ldg(in + ((int64_t)ny * Lx + x) * 2 + so);
+      if (phase) {
+        const float* p4 = phase + ((size_t)y * 2 + s) * 4;
+        n2 = rot(n2, __ldg(p4), __ldg(p4 + 1));
+        n3 = rot(n3, __ldg(p4 + 2), __ldg(p4 + 3));
+      }
       const float sg = s == 0 ? fam.tvel : -fam.tvel;
       if (fam.dir == 0)
         v = make_float4(sg * (n3.x - n2.x), sg * (n3.y - n2.y), sg * (n3.z - n2.z), sg * (n3.w - n2.w));
@@ -58,8 +77,13 @@ __global__ void k_velocity(const float4* __restrict__ in, float4* __restrict__ o
         v = make_float4(sg * ((n2.x + n3.x) - 2.f * n1.x), sg * ((n2.y + n3.y) - 2.f * n1.y),
                         sg * ((n2.z + n3.z) - 2.f * n1.z), sg * ((n2.w + n3.w) - 2.f * n1.w));
     } else {
-      const float4 n1 = __ldg(in + (fam.dir == 0 ? (int64_t)y * Lx + xm : (int64_t)ym * Lx + x));
-      const float4 n2 = __ldg(in + (fam.dir == 0 ? (int64_t)y * Lx + xp : (int64_t)yp * Lx + x));
+      float4 n1 = __ldg(in + (fam.dir == 0 ? (int64_t)y * Lx + xm : (int64_t)ym * Lx + x));
+      float4 n2 = __ldg(in + (fam.dir == 0 ? (int64_t)y * Lx + xp : (int64_t)yp * Lx + x));
+      if (phase && fam.dir == 0) {  // the y bonds carry no phase in the Landau gauge
+        const float* p4 = phase + (size_t)y * 4;
+        n1 = rot(n1, __ldg(p4), __ldg(p4 + 1));
+        n2 = rot(n2, __ldg(p4 + 2), __ldg(p4 + 3));
+      }
       const float t = fam.tvel;
       v = make_float4(t * (n1.x - n2.x), t * (n1.y - n2.y), t * (n1.z - n2.z), t * (n1.w - n2.w));
     }
@@ -77,7 +101,7 @@ __global__ void k_velocity(const float4* __restrict__ in, float4* __restrict__ o
   }
 }
 
-template <int LAT>
+template <int LAT, bool FIELD>
 int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc, int alpha,
            int beta, double* mu_nm_dev, kite_stats* stats, const double* r0_dev_all) {
   constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
@@ -87,7 +111,8 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
   const int64_t ncell = (int64_t)sys->Lx * sys->Ly, N = ncell * SORB;
   const int64_t Kp = ((2 * N + 63) / 64) * 64;
   const int VB = 2;
-  const int G = grid_for<float, LAT, C, false, 1>(ctx, (long long)((sys->Lx + Sh::TX - 1) / Sh::TX) * sys->Ly);
+  const int G =
+      grid_for<float, LAT, C, false, 1, kStages, FIELD>(ctx, (long long)((sys->Lx + Sh::TX - 1) / Sh::TX) * sys->Ly);
   const long long units = (long long)((sys->Lx + Sh::TX - 1) / Sh::TX) * sys->Ly;
   const int Sg = plan_gemm_splits(ctx, M, 2 * M, Kp);
   const size_t vec_bytes = (size_t)ncell * SORB * C * 16;
@@ -95,8 +120,9 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
 
   auto layout = [&](Carver& k, float** vt, void** r0, void** bA, void** bB,
                     __nv_bfloat16** Ah, __nv_bfloat16** Al, __nv_bfloat16** Bh,
-                    __nv_bfloat16** Bl, double** part, unsigned long long** ne) {
+                    __nv_bfloat16** Bl, double** part, unsigned long long** ne, float** ph) {
     *vt = k.take<float>(N);
+    *ph = FIELD ? k.take<float>((size_t)sys->Ly * SORB * 4) : nullptr;
     *r0 = k.take<char>(vec_bytes);
     *bA = k.take<char>(vec_bytes);
     *bB = k.take<char>(vec_bytes);
@@ -114,15 +140,20 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
   __nv_bfloat16 *Ah[VB], *Al[VB], *Bh[VB], *Bl[VB];
   double* part;
   unsigned long long* ne;
+  float* ph;
   {
     Carver probe(nullptr);
-    layout(probe, &vt, &r0, &bA, &bB, Ah, Al, Bh, Bl, &part, &ne);
+    layout(probe, &vt, &r0, &bA, &bB, Ah, Al, Bh, Bl, &part, &ne, &ph);
     int rc = ensure_ws(ctx, probe.used());
     if (rc != KITE_OK) return rc;
   }
   Carver w(ctx->ws);
-  layout(w, &vt, &r0, &bA, &bB, Ah, Al, Bh, Bl, &part, &ne);
+  layout(w, &vt, &r0, &bA, &bB, Ah, Al, Bh, Bl, &part, &ne, &ph);
   cudaStream_t st = ctx->stream;
+  if (FIELD) {
+    int rc = field_phases(ctx, sys, 0, ph);
+    if (rc != KITE_OK) return rc;
+  }
   if (Kp > 2 * N) {  // zero the K padding (the tail of the last K block of every row) once
     const int64_t k0 = 2 * N;  // first padded column; Kp - k0 < 64, all in the last block
     const size_t width = (size_t)(Kp - k0) * 2;
@@ -148,10 +179,14 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
   const uint32_t k0 = (uint32_t)sys->seed, k1 = (uint32_t)(sys->seed >> 32);
   const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->num_sms * 16);
   constexpr int SM = Sh::SMEM_NR0;  // the family modes never stage r_0
-  cudaFuncSetAttribute(k_step<float, LAT, C, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
-  cudaFuncSetAttribute(k_step<float, LAT, C, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
-  cudaFuncSetAttribute(k_step<float, LAT, C, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
-  cudaFuncSetAttribute(k_step<float, LAT, C, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
+  cudaFuncSetAttribute(k_step<float, LAT, C, true, 1, kStages, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       SM);
+  cudaFuncSetAttribute(k_step<float, LAT, C, false, 1, kStages, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       SM);
+  cudaFuncSetAttribute(k_step<float, LAT, C, true, 2, kStages, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       SM);
+  cudaFuncSetAttribute(k_step<float, LAT, C, false, 2, kStages, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       SM);
 
   FamOut fa{}, fb{};
   for (int v = 0; v < VB; ++v) {
@@ -191,35 +226,35 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
       // A family: a_0 = h~alpha r_0 (row 0, and the recursion's start vector in bB)
       fa.col = 0;
       k_velocity<LAT><<<blocks, 256, 0, st>>>(static_cast<const float4*>(r0),
-                                              static_cast<float4*>(bB), vt, sys->Lx, sys->Ly, 1, fa);
+                                              static_cast<float4*>(bB), vt, sys->Lx, sys->Ly, 1, fa, ph);
       auto whereA = [&](int n) -> void* { return (n & 1) ? bA : bB; };
       for (int n = 0; n + 1 < M; ++n) {
         fa.col = n + 1;
         if (n == 0)
-          k_step<float, LAT, C, true, 1><<<G, kBlock, SM, st>>>(
+          k_step<float, LAT, C, true, 1, kStages, FIELD><<<G, kBlock, SM, st>>>(
               nullptr, whereA(0), whereA(1), nullptr, vt, tt, sys->Lx, sys->Ly, units, nullptr,
-              nullptr, ctx->d_status, 0, fa);
+              nullptr, ctx->d_status, 0, fa, 0, SeriesOut{}, ph);
         else
-          k_step<float, LAT, C, false, 1><<<G, kBlock, SM, st>>>(
+          k_step<float, LAT, C, false, 1, kStages, FIELD><<<G, kBlock, SM, st>>>(
               whereA(n - 1), whereA(n), whereA(n + 1), nullptr, vt, tt, sys->Lx, sys->Ly, units,
-              nullptr, nullptr, ctx->d_status, 0, fa);
+              nullptr, nullptr, ctx->d_status, 0, fa, 0, SeriesOut{}, ph);
       }
       // B family: recursion from r_0; step n writes b_n = h~beta r_n
       auto whereB = [&](int n) -> void* { return n == 0 ? r0 : ((n & 1) ? bA : bB); };
       for (int n = 0; n + 1 < M; ++n) {
         fb.col = n;
         if (n == 0)
-          k_step<float, LAT, C, true, 2><<<G, kBlock, SM, st>>>(
+          k_step<float, LAT, C, true, 2, kStages, FIELD><<<G, kBlock, SM, st>>>(
               nullptr, whereB(0), whereB(1), nullptr, vt, tt, sys->Lx, sys->Ly, units, nullptr,
-              nullptr, ctx->d_status, 0, fb);
+              nullptr, ctx->d_status, 0, fb, 0, SeriesOut{}, ph);
         else
-          k_step<float, LAT, C, false, 2><<<G, kBlock, SM, st>>>(
+          k_step<float, LAT, C, false, 2, kStages, FIELD><<<G, kBlock, SM, st>>>(
               whereB(n - 1), whereB(n), whereB(n + 1), nullptr, vt, tt, sys->Lx, sys->Ly, units,
-              nullptr, nullptr, ctx->d_status, 0, fb);
+              nullptr, nullptr, ctx->d_status, 0, fb, 0, SeriesOut{}, ph);
       }
       fb.col = M - 1;
       k_velocity<LAT><<<blocks, 256, 0, st>>>(static_cast<const float4*>(whereB(M - 1)), nullptr, vt,
-                                              sys->Lx, sys->Ly, 2, fb);
+                                              sys->Lx, sys->Ly, 2, fb, ph);
       KITE_CUDA_TRY(ctx, cudaGetLastError());
       KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, st));
       // contraction, one vector at a time, accumulated in FP64
@@ -264,9 +299,12 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
 
 int moments_2d_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc, int alpha,
                     int beta, double* mu_nm_dev, kite_stats* st, const double* r0_dev_all) {
-  if (sys->lattice == KITE_HONEYCOMB)
-    return run_2d<KITE_HONEYCOMB>(ctx, sys, kpm, sc, alpha, beta, mu_nm_dev, st, r0_dev_all);
-  return run_2d<KITE_SQUARE>(ctx, sys, kpm, sc, alpha, beta, mu_nm_dev, st, r0_dev_all);
+  const bool hc = sys->lattice == KITE_HONEYCOMB;
+  if (sys->flux != 0.0)
+    return hc ? run_2d<KITE_HONEYCOMB, true>(ctx, sys, kpm, sc, alpha, beta, mu_nm_dev, st, r0_dev_all)
+              : run_2d<KITE_SQUARE, true>(ctx, sys, kpm, sc, alpha, beta, mu_nm_dev, st, r0_dev_all);
+  return hc ? run_2d<KITE_HONEYCOMB, false>(ctx, sys, kpm, sc, alpha, beta, mu_nm_dev, st, r0_dev_all)
+            : run_2d<KITE_SQUARE, false>(ctx, sys, kpm, sc, alpha, beta, mu_nm_dev, st, r0_dev_all);
 }
 
 }  // namespace kite

@@ -456,3 +456,158 @@ int reconstruct_sigma_dc_impl(kite_ctx* ctx, const double* mu_dev, int M_avail, 
 }
 
 }  // namespace kite
+
+// ====================================================================================
+// DC conductivity tensor from the Kubo-Bastin formula, Fermi sea included (the Hall
+// conductivity of the paper's quantum anomalous Hall example, Sec. 2b at omega -> 0):
+//   sigma_ab(E_F) = Re{ i ucf int de f(e) sum_nm mu_nm [Delta_n(e) dG^R_m(e) - dG^A_n(e) Delta_m(e)] }
+// with Delta_n(e) de = k_n (2 - d_n0)/pi cos(n theta) d theta (e = cos theta), the CPGF
+// coefficients G^{R/A}_m(e) = k_m g^{+-}_m(e +- i eta)/(1 + d_m0) (Eq.
+// green_function_cheb_expansionb) and their derivatives
+//   d g_m/dz = g_m(z) [s i m / sqrt(1 - z^2) + z / (1 - z^2)]   (s = +1 retarded, -1 advanced).
+// A_nm = mu_nm k_n k_m / ((1 + d_n0)(1 + d_m0)).  Each Fermi energy has its own
+// Gauss-Legendre nodes theta_k on [theta_F, pi] (kT > 0: [0, pi] with Fermi weights);
+// D[n][k] = (2/pi) cos(n theta_k) w_k, U = A^T D, W = A D (FP64 GEMMs), and per node
+//   F_k = sum_m dG^R_m(e_k) U[m][k] - sum_n dG^A_n(e_k) W[n][k],
+// the CPGF terms geometric, g_m = g_0 q^m with q = z - s i sqrt(1 - z^2), summed as
+// S0 = sum_m g_m X_m and S1 = sum_m m g_m X_m:  sum_m dg_m X_m = s i S1 / r + z S0 / r^2,
+// r = sqrt(1 - z^2).  sigma = Re(i ucf sum_k F_k) = -ucf Im(sum_k F_k), each energy's
+// node sum in a fixed order.  Cost: two M x M x (K nodes) GEMMs per energy.
+// ====================================================================================
+namespace kite {
+namespace {
+
+__global__ void k_bastin_gamma(const double* __restrict__ mu, int M_avail, int M, const double* __restrict__ w,
+                               double* __restrict__ A) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)M * M) return;
+  const int n = (int)(e / M), m = (int)(e - (e / M) * M);
+  // w_n = (2 - d_n0) k_n, so w_n / 2 = k_n / (1 + d_n0)
+  const double f = 0.25 * w[n] * w[m];
+  const double* p = mu + 2 * ((int64_t)n * M_avail + m);
+  A[2 * e] = f * p[0];
+  A[2 * e + 1] = f * p[1];
+}
+
+__global__ void k_bastin_nodes(const double* __restrict__ U, const double* __restrict__ W,
+                               const double* __restrict__ theta, int M, int64_t Kt, double eta_t,
+                               double* __restrict__ F) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Kt; k += (int64_t)gridDim.x * blockDim.x) {
+    const double e = cos(theta[k]);
+    cplx tot = {0.0, 0.0};
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      const double s = sgn == 0 ? 1.0 : -1.0;
+      const cplx z = {e, s * eta_t};
+      const cplx r = csqrt_p({1.0 - (z.re * z.re - z.im * z.im), -2.0 * z.re * z.im});
+      const cplx q = {z.re + s * r.im, z.im - s * r.re};  // z - s i r
+      cplx g = cdiv({0.0, -2.0 * s}, r);
+      const double* X = sgn == 0 ? U : W;
+      cplx S0 = {0.0, 0.0}, S1 = {0.0, 0.0};
+      for (int m = 0; m < M; ++m) {
+        const cplx x = {X[2 * ((int64_t)m * Kt + k)], X[2 * ((int64_t)m * Kt + k) + 1]};
+        const cplx gx = cmul(g, x);
+        S0.re += gx.re;
+        S0.im += gx.im;
+        S1.re += (double)m * gx.re;
+        S1.im += (double)m * gx.im;
+        g = cmul(g, q);
+      }
+      const cplx a = cdiv(S1, r);
+      const cplx b = cdiv(cmul(z, S0), cmul(r, r));
+      const cplx d = {-s * a.im + b.re, s * a.re + b.im};  // s i a + b
+      tot.re += s * d.re;
+      tot.im += s * d.im;
+    }
+    F[2 * k] = tot.re;
+    F[2 * k + 1] = tot.im;
+  }
+}
+
+// one block per energy: sigma = -ucf * sum_k Im F_k over that energy's K nodes
+__global__ void k_bastin_sum(const double* __restrict__ F, int K, double ucf, double* __restrict__ sigma) {
+  const double* f = F + 2 * (int64_t)blockIdx.x * K;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) acc += f[2 * k + 1];
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sigma[blockIdx.x] = -ucf * red[0];
+}
+
+}  // namespace
+
+int reconstruct_sigma_bastin_impl(kite_ctx* ctx, const double* mu_dev, int M_avail, int M, int lattice,
+                                  int kernel, double param, const Scale& sc, double eta, double kT,
+                                  const double* E_host, int K_E, int n_quad, double* sigma_dev) {
+  const int K = n_quad > 0 ? n_quad : 2 * M + 64;
+  std::vector<double> x(K), w0(K);
+  gauss_legendre(K, x.data(), w0.data());
+  // energies per batch: D (M K), U and W (2 M K each), theta, weights, F (2 K) doubles
+  const size_t per_energy = (size_t)K * (5 * (size_t)M + 4);
+  const size_t budget = (size_t)1 << 27;  // doubles (1 GiB)
+  const int EB = (int)std::max<size_t>(1, std::min<size_t>((size_t)K_E, budget / per_energy));
+  const size_t Kt_max = (size_t)EB * K;
+  const size_t nA = 2 * (size_t)M * M;
+  const size_t total = nA + (size_t)M + Kt_max * (5 * (size_t)M + 4);
+  double* buf = nullptr;
+  KITE_CUDA_TRY(ctx, cudaMallocAsync((void**)&buf, total * sizeof(double), ctx->stream));
+  double* A = buf;
+  double* wk = A + nA;
+  double* D = wk + M;
+  double* U = D + (size_t)M * Kt_max;
+  double* W = U + 2 * (size_t)M * Kt_max;
+  double* th_d = W + 2 * (size_t)M * Kt_max;
+  double* wq_d = th_d + Kt_max;
+  double* F = wq_d + Kt_max;
+  cudaStream_t st = ctx->stream;
+  const double pi = 3.141592653589793;
+  const double ucf = lattice == KITE_HONEYCOMB ? 4.0 / sqrt(3.0) : 1.0;
+  k_dc_weights<<<(M + 255) / 256, 256, 0, st>>>(M, kernel, param, wk);
+  k_bastin_gamma<<<(int)(((int64_t)M * M + 255) / 256), 256, 0, st>>>(mu_dev, M_avail, M, wk, A);
+  cudaError_t e = cudaGetLastError();
+  int rc = e == cudaSuccess ? KITE_OK : cuda_fail(ctx, e, "Bastin set-up");
+  std::vector<double> th(Kt_max), wq(Kt_max);
+  for (int b = 0; b < K_E && rc == KITE_OK; b += EB) {
+    const int nb = std::min(EB, K_E - b);
+    const int64_t Kt = (int64_t)nb * K;
+    for (int i = 0; i < nb; ++i) {
+      const double EF = E_host[b + i];
+      const double eF = (EF - sc.de_plus) / sc.de_minus;
+      const double thF = kT > 0.0 ? 0.0 : acos(fmin(1.0, fmax(-1.0, eF)));
+      for (int k = 0; k < K; ++k) {
+        double t = thF + (pi - thF) * 0.5 * (x[k] + 1.0), ww = w0[k] * 0.5 * (pi - thF);
+        if (kT > 0.0) ww /= (1.0 + exp((cos(t) * sc.de_minus + sc.de_plus - EF) / kT));
+        th[(size_t)i * K + k] = t;
+        wq[(size_t)i * K + k] = ww;
+      }
+    }
+    e = cudaMemcpyAsync(th_d, th.data(), Kt * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(wq_d, wq.data(), Kt * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(ctx, e, "Bastin nodes");
+      break;
+    }
+    k_sig_dmat<<<(int)(((int64_t)M * Kt + 255) / 256), 256, 0, st>>>(th_d, wq_d, M, (int)Kt, D);
+    dim3 blk(16, 16), grd((unsigned)((Kt + 15) / 16), (unsigned)((M + 15) / 16));
+    k_zgemm_real<<<grd, blk, 0, st>>>(A, 1, D, M, (int)Kt, U);  // U[m][k] = sum_n A_nm D[n][k]
+    k_zgemm_real<<<grd, blk, 0, st>>>(A, 0, D, M, (int)Kt, W);  // W[n][k] = sum_m A_nm D[m][k]
+    const int nblk = (int)std::min<int64_t>((Kt + 255) / 256, (int64_t)ctx->num_sms * 8);
+    k_bastin_nodes<<<nblk, 256, 0, st>>>(U, W, th_d, M, Kt, eta / sc.de_minus, F);
+    k_bastin_sum<<<nb, 256, 0, st>>>(F, K, ucf, sigma_dev + b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "Bastin kernels");
+    // the host node arrays are refilled next batch: let this batch's copies finish
+    if (rc == KITE_OK && b + EB < K_E) {
+      e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) rc = cuda_fail(ctx, e, "Bastin batch");
+    }
+  }
+  cudaFreeAsync(buf, st);
+  return rc;
+}
+
+}  // namespace kite

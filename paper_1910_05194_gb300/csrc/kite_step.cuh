@@ -637,20 +637,20 @@ __global__ void k_extract(int64_t ncell, const void* __restrict__ buf, int nvec,
 }
 
 
-// Persistent grid of the step kernel of a mode: resident CTAs per SM x SMs, at most one
-// CTA per unit.  Also sets the kernels' dynamic shared-memory limit.
 // Resident CTAs per SM of the step kernel of a mode and ring depth (also sets the
 // kernels' dynamic shared-memory limit).
-template <typename Real, int LAT, int C, int MODE = 0, int NST = kStages>
+template <typename Real, int LAT, int C, int MODE = 0, int NST = kStages, bool FIELD = false>
 int step_occupancy() {
   static int occ = -1;  // per template instance; device-independent enough for one GPU type
   if (occ < 0) {
     int o = 0;
     const int smem = StepShape<LAT, C, NST>::template smem_bytes<MODE>();
-    cudaFuncSetAttribute(k_step<Real, LAT, C, true, MODE, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_step<Real, LAT, C, false, MODE, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_step<Real, LAT, C, false, MODE, NST>, kBlock, smem) !=
-            cudaSuccess ||
+    cudaFuncSetAttribute(k_step<Real, LAT, C, true, MODE, NST, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    cudaFuncSetAttribute(k_step<Real, LAT, C, false, MODE, NST, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_step<Real, LAT, C, false, MODE, NST, FIELD>, kBlock,
+                                                      smem) != cudaSuccess ||
         o < 1)
       o = 1;
     occ = o;
@@ -660,9 +660,9 @@ int step_occupancy() {
 
 // Persistent grid of the step kernel: min(ctas_per_sm, occupancy) CTAs per SM (0 = the
 // occupancy), at most one CTA per unit.
-template <typename Real, int LAT, int C, bool FIRST, int MODE = 0, int NST = kStages>
+template <typename Real, int LAT, int C, bool FIRST, int MODE = 0, int NST = kStages, bool FIELD = false>
 int grid_for(kite_ctx* ctx, long long units, int ctas_per_sm = 0) {
-  const int occ = step_occupancy<Real, LAT, C, MODE, NST>();
+  const int occ = step_occupancy<Real, LAT, C, MODE, NST, FIELD>();
   const int k = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
   long long g = (long long)ctx->num_sms * k;
   return (int)std::max(1LL, std::min(g, units));

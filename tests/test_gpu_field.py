@@ -127,5 +127,3 @@ def test_calls_without_field_support_refuse_a_field(ctx):
         kite.moments_1d_batched(ctx, [s], [kite.make_kpm(8, 2, 1, kite.FP32)], [np.zeros(8)])
     with pytest.raises(kite.KiteError):
         kite.moments_1d_static(s, kite.make_kpm(8, 2, 1, kite.FP32), np.zeros(8))
-    with pytest.raises(kite.KiteError):
-        kite.moments_2d(ctx, s, kite.make_kpm(8, 1, 1, kite.FP32), np.zeros((8, 8, 2)))
