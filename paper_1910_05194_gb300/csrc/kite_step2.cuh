@@ -86,9 +86,11 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
   long long gslot = ring.gslot;
   bool aborted = false;
 
-  // periodic cell index; the copies below may start up to two cells left of the lattice
-  // and, on lattices narrower than the halo, wrap more than once
+  // periodic cell index of x in [-2, Lx + 1] (the copies below start up to two cells left
+  // of the lattice and end up to two right of it); lattices of at most four cells, which
+  // the halo may wrap more than once, take the modulo
   auto wrapx = [&](int x) {
+    if (Lx > 4) return x < 0 ? x + Lx : (x >= Lx ? x - Lx : x);
     x %= Lx;
     return x < 0 ? x + Lx : x;
   };
@@ -113,9 +115,7 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         k += run;
       }
     };
-    auto issue = [&](int jj) {  // producer: slot for r_n row yb-2+jj
-      const long long g = gslot + jj;
-      const int st = (int)(g % NST);
+    auto issue = [&](int jj, int st) {  // producer: slot jj (r_n row yb-2+jj) into stage st
       unsigned char* base = stages + st * Sh::STAGEB;
       int row = yb - 2 + jj;
       while (row < 0) row += Ly;
@@ -129,8 +129,10 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         bulk_g2s(base + Sh::RNB, static_cast<const unsigned char*>(r0) + roff + (size_t)x0 * CELLB,
                  (uint32_t)txv * CELLB, &bars[st]);
     };
-    if (tid == kProducer)
-      for (int jj = 0; jj < min(NST, nslots); ++jj) issue(jj);
+    if (tid == kProducer) {
+      int st = (int)(gslot % NST);
+      for (int jj = 0; jj < min(NST, nslots); ++jj, st = st + 1 == NST ? 0 : st + 1) issue(jj, st);
+    }
 
     // one r_{n+1} site: tile cell tx (global x0 - 1 + tx) of row y1 from the stages of
     // rows y1-1, y1, y1+1 (up, mid, dn) and r_{n-1} of the site (pv)
@@ -221,17 +223,20 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
     const int xv = active ? x0 + xl : (halo ? wrapx(x0 - 1 + (hcell ? txv + 1 : 0)) : 0);
     const bool loads_v = active || halo;
     const Real* vcol = vt + (size_t)xv * SORB + s;
-    const size_t vrow = (size_t)Lx * SORB;
+    const uint32_t vrow = (uint32_t)Lx * SORB;
     auto vload = [&](int y) { return vcol[(size_t)wrapy(y) * vrow]; };
-    // this thread's chunk in the outputs: column offset + row * orow chunks
+    // this thread's chunk in the outputs: column offset + row * orow chunks (orow fits 32
+    // bits; row * orow is formed in 64 bits)
     const size_t ocol = ((size_t)(x0 + xl) * SORB + s) * C + c;
-    const size_t orow = (size_t)Lx * SORB * C;
+    const uint32_t orow = (uint32_t)Lx * SORB * C;
     Real v1 = loads_v ? vload(yb - 1) : Real(0);
     // r_{n-1} of the same cell, read straight from global memory one row ahead (it is
     // used once, by this thread)
     const size_t pcol = ((size_t)xv * SORB + s) * C + c;
-    auto pload = [&](int y) { return Ch::ldg(r_prev, pcol + (size_t)wrapy(y) * orow); };
-    Ch pv1 = loads_v ? pload(yb - 1) : Ch{};
+    Ch pv1 = loads_v ? Ch::ldg(r_prev, pcol + (size_t)wrapy(yb - 1) * orow) : Ch{};
+    // the prefetch row yn = yb + i of r_{n-1} and the on-site terms, wrapped as it advances
+    // (the stored rows yb-1+i and yb-3+i are owned rows whenever they are stored)
+    int yn = yb;
     // One barrier per row: iteration i computes r_{n+1} row yb-1+i (slots i, i+1, i+2 hold
     // r_n rows yb-2+i .. yb+i) into tile row i mod 4, and r_{n+2} row yb-3+i from the three
     // tile rows written by the previous iterations, with r_n and r_0 of that row from slot
@@ -242,22 +247,25 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
     int o0 = 0, o1 = Sh::TILEB, o2 = 2 * Sh::TILEB, o3 = 3 * Sh::TILEB;  // tile rows i-3 .. i
     Real vm1 = Real(0), vm2 = Real(0);  // on-site terms of the rows of iterations i-1, i-2
     int issued = min(NST, nslots);      // slots issued so far (producer's count)
+    uint32_t par2 = (uint32_t)(((gslot + 2) / NST) & 1);  // phase parity of slot i+2
     int i = 0;
     for (; i < nr + 3; ++i) {
       const bool do1 = i < nr + 2;  // r_{n+1} row yb-1+i
       const bool do2 = i >= 3;      // r_{n+2} row yb-3+i
       const bool more = loads_v && i + 1 < nr + 2;
-      const Real v1n = more ? vload(yb + i) : Real(0);
-      const Ch pvn = more ? pload(yb + i) : Ch{};
-      bool ok = true;
-      if (do1 && (compute || halo))
-        for (int jj = (i == 0 ? 0 : i + 2); jj <= i + 2; ++jj) {
-          const long long g = gslot + jj;
-          ok = mbar_wait_bounded_hint(&bars[g % NST], (uint32_t)((g / NST) & 1)) && ok;
-        }
-      if (!ok) s_abort = 1;
+      const Real v1n = more ? vcol[(size_t)(uint32_t)yn * vrow] : Real(0);
+      const Ch pvn = more ? Ch::ldg(r_prev, pcol + (size_t)(uint32_t)yn * orow) : Ch{};
       const int st1 = st0 + 1 == NST ? 0 : st0 + 1;
       const int st2 = st1 + 1 == NST ? 0 : st1 + 1;
+      bool ok = true;
+      if (do1 && (compute || halo)) {
+        if (i == 0)
+          for (int jj = 0; jj < 2; ++jj) {
+            const long long g = gslot + jj;
+            ok = mbar_wait_bounded_hint(&bars[g % NST], (uint32_t)((g / NST) & 1)) && ok;
+          }
+        ok = mbar_wait_bounded_hint(&bars[st2], par2) && ok;
+      }
       const unsigned char* up = stages + st0 * Sh::STAGEB;
       const unsigned char* mid = stages + st1 * Sh::STAGEB;
       const unsigned char* dn = stages + st2 * Sh::STAGEB;
@@ -266,7 +274,7 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         const Ch o = site1(up, mid, dn, xl + 1, v1, pv1);
         *reinterpret_cast<Ch*>(t3 + (xl + 1) * CELLB + choff) = o;
         if (i >= 1 && i <= nr) {
-          o.st(out1, ocol + (size_t)wrapy(yb - 1 + i) * orow);
+          o.st(out1, ocol + (size_t)(uint32_t)(yb - 1 + i) * orow);
           const Ch z0 = *reinterpret_cast<const Ch*>(mid + Sh::RNB + xl * CELLB + choff);
           accumulate(facc1, dacc1, rows1, z0, o);
         }
@@ -279,7 +287,7 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         // r_{n+2} row y2 = yb-3+i from tile rows y2-1, y2, y2+1 and r_n, r_0 of row y2
         const unsigned char* prev = stages + stm * Sh::STAGEB;
         const Ch o = site2(tile + o0, tile + o1, tile + o2, prev, vm2);
-        o.st(out2, ocol + (size_t)(yb - 3 + i) * orow);
+        o.st(out2, ocol + (size_t)(uint32_t)(yb - 3 + i) * orow);
         const Ch z0 = *reinterpret_cast<const Ch*>(prev + Sh::RNB + xl * CELLB + choff);
         accumulate(facc2, dacc2, rows2, z0, o);
       }
@@ -287,22 +295,25 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
       vm1 = v1;
       v1 = v1n;
       pv1 = pvn;
-      stm = st0;
-      st0 = st1;
+      if (st2 == NST - 1) par2 ^= 1u;  // slot i+3 starts the ring's next round
+      yn = yn + 1 == Ly ? 0 : yn + 1;
       const int of = o0;  // the oldest tile row takes the next r_{n+1} row
       o0 = o1;
       o1 = o2;
       o2 = o3;
       o3 = of;
+      if (!ok) s_abort = 1;
       __syncthreads();  // the tile row is complete; slot i-1 and the oldest tile row are free
       if (s_abort) {
         aborted = true;
         break;
       }
       if (tid == kProducer && i >= 1 && i - 1 + NST < nslots) {
-        issue(i - 1 + NST);
+        issue(i - 1 + NST, stm);  // slot i-1's stage
         issued = i + NST;
       }
+      stm = st0;
+      st0 = st1;
     }
     if (aborted) {
       if (tid == kProducer) {
