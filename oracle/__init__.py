@@ -53,24 +53,27 @@ def build(force: bool = False) -> str:
 
 
 class System(ctypes.Structure):
-    """Mirror of ``orc_system``: a periodic honeycomb or square lattice with disorder."""
+    """Mirror of ``orc_system``: a honeycomb or square lattice with disorder, periodic or
+    with open boundaries."""
     _fields_ = [("lattice", ctypes.c_int32), ("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32),
                 ("disorder", ctypes.c_int32), ("t", ctypes.c_double), ("W", ctypes.c_double),
                 ("delta", ctypes.c_double), ("p_vac", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("flux", ctypes.c_double)]
+                ("seed", ctypes.c_uint64), ("flux", ctypes.c_double), ("open_x", ctypes.c_int32),
+                ("open_y", ctypes.c_int32)]
 
 
 UNIFORM, GAUSSIAN = 0, 1
 
 
 def make_system(lattice=HONEYCOMB, Lx=8, Ly=8, t=-2.7, W=0.0, delta=0.0, p_vac=0.0, seed=1,
-                disorder=UNIFORM, flux=0.0):
+                disorder=UNIFORM, flux=0.0, open_x=0, open_y=0):
     """W is the width of uniform disorder in [-W/2, W/2], or the standard deviation of
     Gaussian disorder (disorder=GAUSSIAN); flux is the perpendicular magnetic flux per unit
     cell in flux quanta (Landau gauge: flux * Ly even on the honeycomb, integer on the
-    square lattice)."""
+    square lattice, when y is periodic); open_x / open_y drop the bonds that wrap around
+    the torus along a1 / a2 (open boundaries)."""
     return System(int(lattice), int(Lx), int(Ly), int(disorder), float(t), float(W), float(delta),
-                  float(p_vac), int(seed), float(flux))
+                  float(p_vac), int(seed), float(flux), int(bool(open_x)), int(bool(open_y)))
 
 
 def lib():
@@ -127,9 +130,10 @@ def norb(sys: System) -> int:
 
 
 def neighbours(sys: System, o: int):
+    """Neighbour orbitals of o (bonds across an open boundary left out)."""
     nb = (ctypes.c_int64 * 4)()
     z = lib().orc_neighbours(ctypes.byref(sys), int(o), nb)
-    return [int(nb[k]) for k in range(z)]
+    return [int(nb[k]) for k in range(z) if nb[k] >= 0]
 
 
 def bounds_auto(sys: System):

@@ -114,7 +114,9 @@ static int64_t orc_wrap(int64_t v, int64_t L) {
  * lattice constant a.  Honeycomb (the paper's lattice set-up listing): a1 = (1, 0),
  * a2 = (1/2, sqrt(3)/2), A at (0, -a_cc/2) and B at (0, +a_cc/2) in each cell with
  * a_cc = 1/sqrt(3); bonds A(x,y) - B(x+dx1, y+dx2) for cell offsets (0,0), (1,-1), (0,-1).
- * Square: a1 = (1, 0), a2 = (0, 1). */
+ * Square: a1 = (1, 0), a2 = (0, 1).  Periodic boundaries wrap the cell indices; with an
+ * open boundary (the configuration's boundaries flag set to False, Sec. 3d) a bond whose
+ * cell offset leaves [0, L) along that direction is absent: its neighbour index is -1. */
 static int orc_neighbours_geo(const orc_system* sys, int64_t o, int64_t nb[4], double dx[4],
                               double dy[4]) {
   int64_t Lx = sys->Lx, Ly = sys->Ly;
@@ -122,10 +124,13 @@ static int orc_neighbours_geo(const orc_system* sys, int64_t o, int64_t nb[4], d
     const double acc = 1.0 / sqrt(3.0);
     int64_t cell = o >> 1, s = o & 1;
     int64_t x = cell % Lx, y = cell / Lx;
+    const int ox = sys->open_x, oy = sys->open_y;
     if (s == 0) { /* A(x,y) -> B(x,y), B(x+1,y-1), B(x,y-1) */
       nb[0] = 2 * (y * Lx + x) + 1;
       nb[1] = 2 * (orc_wrap(y - 1, Ly) * Lx + orc_wrap(x + 1, Lx)) + 1;
       nb[2] = 2 * (orc_wrap(y - 1, Ly) * Lx + x) + 1;
+      if ((ox && x + 1 == Lx) || (oy && y == 0)) nb[1] = -1;
+      if (oy && y == 0) nb[2] = -1;
       dx[0] = 0.0;
       dx[1] = -0.5;
       dx[2] = 0.5;
@@ -136,6 +141,8 @@ static int orc_neighbours_geo(const orc_system* sys, int64_t o, int64_t nb[4], d
       nb[0] = 2 * (y * Lx + x);
       nb[1] = 2 * (orc_wrap(y + 1, Ly) * Lx + orc_wrap(x - 1, Lx));
       nb[2] = 2 * (orc_wrap(y + 1, Ly) * Lx + x);
+      if ((ox && x == 0) || (oy && y + 1 == Ly)) nb[1] = -1;
+      if (oy && y + 1 == Ly) nb[2] = -1;
       dx[0] = 0.0;
       dx[1] = 0.5;
       dx[2] = -0.5;
@@ -146,10 +153,10 @@ static int orc_neighbours_geo(const orc_system* sys, int64_t o, int64_t nb[4], d
     return 3;
   }
   int64_t x = o % Lx, y = o / Lx;
-  nb[0] = y * Lx + orc_wrap(x - 1, Lx);
-  nb[1] = y * Lx + orc_wrap(x + 1, Lx);
-  nb[2] = orc_wrap(y - 1, Ly) * Lx + x;
-  nb[3] = orc_wrap(y + 1, Ly) * Lx + x;
+  nb[0] = (sys->open_x && x == 0) ? -1 : y * Lx + orc_wrap(x - 1, Lx);
+  nb[1] = (sys->open_x && x + 1 == Lx) ? -1 : y * Lx + orc_wrap(x + 1, Lx);
+  nb[2] = (sys->open_y && y == 0) ? -1 : orc_wrap(y - 1, Ly) * Lx + x;
+  nb[3] = (sys->open_y && y + 1 == Ly) ? -1 : orc_wrap(y + 1, Ly) * Lx + x;
   dx[0] = 1.0;
   dx[1] = -1.0;
   dx[2] = 0.0;
@@ -272,7 +279,7 @@ typedef struct {
  * square lattice): otherwise the bonds across the y boundary would not be the
  * conjugates of their reverses.  Bonds with dx = 0 carry no phase. */
 int orc_flux_fits(const orc_system* sys) {
-  if (sys->flux == 0.0) return 0;
+  if (sys->flux == 0.0 || sys->open_y) return 0; /* no bond wraps in y: any flux fits */
   double q = sys->flux * (double)sys->Ly * (sys->lattice == 0 ? 0.5 : 1.0);
   return fabs(q - nearbyint(q)) <= 1e-9 * fmax(1.0, fabs(q)) ? 0 : -4;
 }
@@ -351,7 +358,7 @@ static void orc_apply_h(const orc_ham* h, const double* x, double* y) {
     double re = h->Vt[o] * x[2 * o], im = h->Vt[o] * x[2 * o + 1];
     for (int k = 0; k < h->Z; ++k) {
       int64_t j = h->nb[4 * o + k];
-      if (h->vac[j]) continue;
+      if (j < 0 || h->vac[j]) continue; /* no bond across an open boundary */
       double xr = x[2 * j], xi = x[2 * j + 1];
       if (h->ph) { /* t exp(i theta) x_j */
         double c = h->ph[8 * o + 2 * k], sn = h->ph[8 * o + 2 * k + 1];
@@ -497,7 +504,8 @@ int orc_moments_1d(const orc_system* sys, int realisation, int M, int R, double 
 /* this project pins the order of operations of one site update so that any         */
 /* implementation of it can be compared bit for bit:                                */
 /*   s  = (nb1 + nb2) + nb3  [+ nb4 on the square lattice], neighbours in the order */
-/*        of orc_neighbours_dx, vacant neighbours read as zero;                      */
+/*        of orc_neighbours_dx, vacant neighbours and absent bonds (open boundaries) */
+/*        read as zero;                                                              */
 /*   h  = fma(t~, s, V~ * r_self)          (one rounding for the product V~*r);      */
 /*   r1 = h;   r_{n+1} = fma(2, h, -r_{n-1});   vacant orbitals stay exactly zero.   */
 /* V~ and t~ are computed in FP64 and rounded once to the working precision; start  */
@@ -514,9 +522,11 @@ int orc_moments_1d(const orc_system* sys, int realisation, int M, int R, double 
         if (h->vac[o]) {                                                                     \
           v = (REAL)0;                                                                       \
         } else {                                                                             \
-          REAL s = cur[2 * h->nb[4 * o + 0] + c] + cur[2 * h->nb[4 * o + 1] + c];            \
-          s = s + cur[2 * h->nb[4 * o + 2] + c];                                             \
-          if (h->Z == 4) s = s + cur[2 * h->nb[4 * o + 3] + c];                              \
+          const int64_t* q = h->nb + 4 * o;                                                  \
+          REAL s = (q[0] < 0 ? (REAL)0 : cur[2 * q[0] + c]) +                                \
+                   (q[1] < 0 ? (REAL)0 : cur[2 * q[1] + c]);                                 \
+          s = s + (q[2] < 0 ? (REAL)0 : cur[2 * q[2] + c]);                                  \
+          if (h->Z == 4) s = s + (q[3] < 0 ? (REAL)0 : cur[2 * q[3] + c]);                   \
           REAL p = vt[o] * cur[2 * o + c];                                                   \
           REAL hv = FMA(tt, s, p);                                                           \
           v = first ? hv : FMA((REAL)2, hv, -prev[2 * o + c]);                               \
@@ -644,7 +654,7 @@ static void orc_apply_v(const orc_ham* h, int dir, const double* x, double* y) {
     if (!h->vac[o]) {
       for (int k = 0; k < h->Z; ++k) {
         int64_t j = h->nb[4 * o + k];
-        if (h->vac[j]) continue;
+        if (j < 0 || h->vac[j]) continue;
         double w = off[4 * o + k] * h->tt;
         double xr = x[2 * j], xi = x[2 * j + 1];
         if (h->ph) { /* [r, H~]_oj = (r_o - r_j) t~ exp(i theta_oj) */
@@ -843,6 +853,7 @@ void orc_cpgf_coeff(int n, double eps, double eta, int sigma, double* re, double
 int orc_replica_window(const orc_system* sys, int realisation, int M, int R, double e_min,
                        double e_max, int precision, int x0, int y0, int half, void* out) {
   if (sys->flux != 0.0) return -3; /* built without Peierls phases */
+  if (sys->open_x || sys->open_y) return -3; /* periodic lattices only */
   if (M < 1 || R < 1 || half < M || !(e_max > e_min)) return -1;
   if (precision != 0 && precision != 1) return -1;
   const int sorb = sys->lattice == 0 ? 2 : 1;

@@ -33,7 +33,10 @@ typedef struct {
   double p_vac;      /* per-orbital vacancy probability                                 */
   uint64_t seed;
   double flux;       /* perpendicular magnetic flux per unit cell, in flux quanta h/e;   */
-                     /* flux * Ly must be even (honeycomb) or an integer (square)        */
+                     /* flux * Ly must be even (honeycomb) or an integer (square) when   */
+                     /* y is periodic                                                    */
+  int32_t open_x;    /* 1: open boundary along a1 (the bonds that wrap in x are absent)  */
+  int32_t open_y;    /* 1: open boundary along a2 (the bonds that wrap in y are absent)  */
 } orc_system;
 
 /* 0 if the flux fits the torus in the Landau gauge (see orc_flux_fits), else -4. */

@@ -50,6 +50,11 @@ MUTATIONS = [
     ("normalised by N instead of N_eff", "if (!h->vac[o]) h->n_eff++;", "h->n_eff++;"),
     ("vacancy draw ignored", "vac[o] = ((uint64_t)x[2] < thr) ? 1 : 0;", "vac[o] = 0;"),
     ("velocity without the Peierls phases", "if (h->ph) { /* [r, H~]_oj", "if (0) { /* [r, H~]_oj"),
+    ("open x drops the wrong honeycomb bond", "if ((ox && x + 1 == Lx) || (oy && y == 0)) nb[1] = -1;",
+     "if ((ox && x + 1 == Lx) || (oy && y == 0)) nb[2] = -1;"),
+    ("open y ignored on the square lattice", "nb[2] = (sys->open_y && y == 0) ? -1 :", "nb[2] = (0 && y == 0) ? -1 :"),
+    ("flux check ignores an open y boundary", "if (sys->flux == 0.0 || sys->open_y) return 0;",
+     "if (sys->flux == 0.0) return 0;"),
     ("Bastin derivative without the band-edge term", "+ (z / (s1 * s1))[None, :]))",
      "+ 0.0 * (z / (s1 * s1))[None, :]))", "__init__.py"),
     ("Bastin advanced term on the retarded branch", "for sg in (+1, -1):", "for sg in (+1, +1):",

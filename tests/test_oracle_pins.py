@@ -218,6 +218,84 @@ def test_flux_must_fit_the_torus():
     oracle.moments_1d(oracle.make_system(Lx=8, Ly=8, flux=0.25), 4, 1)
 
 
+def wrap_classes(sys):
+    """For every pair of orbitals, which periodic images separate them at the shortest
+    distance: (m, n) with r_i - r_j + m T1 + n T2 minimal, T1 = Lx a1, T2 = Ly a2.  A bond
+    with m != 0 wraps around x, n != 0 around y (positions from the orbital set-up)."""
+    P = oracle.orbital_positions(sys)
+    if sys.lattice == oracle.HONEYCOMB:
+        T1, T2 = np.array([sys.Lx, 0.0]), np.array([0.5 * sys.Ly, 0.5 * math.sqrt(3.0) * sys.Ly])
+    else:
+        T1, T2 = np.array([sys.Lx, 0.0]), np.array([0.0, sys.Ly])
+    d0 = P[:, None, :] - P[None, :, :]
+    best = np.sum(d0 * d0, -1)
+    cls = np.zeros(best.shape + (2,), int)
+    for m in (-1, 0, 1):
+        for k in (-1, 0, 1):
+            c = d0 + m * T1 + k * T2
+            dd = np.sum(c * c, -1)
+            better = dd < best - 1e-9
+            best[better] = dd[better]
+            cls[better] = (m, k)
+    return cls
+
+
+@pytest.mark.parametrize("lattice", [oracle.HONEYCOMB, oracle.SQUARE])
+@pytest.mark.parametrize("ox,oy", [(1, 0), (0, 1), (1, 1)])
+def test_open_boundaries_remove_exactly_the_wrapping_bonds(lattice, ox, oy):
+    """Open boundaries (the configuration's boundaries flag): H~ of the open lattice is the
+    periodic H~ (pinned by the Bloch tests) without the bonds that wrap around the torus
+    along the open directions, those bonds found geometrically from the orbital positions
+    and the torus periods; disorder, vacancies and every other bond unchanged."""
+    t = -1.0 if lattice == oracle.SQUARE else T_EV
+    base = dict(lattice=lattice, Lx=5, Ly=4, t=t, W=1.0, p_vac=0.05, seed=6)
+    per = oracle.make_system(**base)
+    opn = oracle.make_system(open_x=ox, open_y=oy, **base)
+    Hp, Ho = dense_from_operator(per), dense_from_operator(opn)
+    cls = wrap_classes(per)
+    cut = ((cls[..., 0] != 0) & bool(ox)) | ((cls[..., 1] != 0) & bool(oy))
+    expect = np.where(cut, 0.0, Hp)
+    assert np.max(np.abs(Ho - expect)) == 0.0
+    assert np.count_nonzero(Hp[cut]) > 0  # the test removes something
+    for d in (0, 1):  # the velocity loses the same bonds
+        assert np.max(np.abs(dense_v(opn, d) - np.where(cut, 0.0, dense_v(per, d)))) == 0.0
+
+
+def test_open_square_lattice_spectrum():
+    """Clean square lattice with open boundaries: standing waves, E = 2t cos(pi m/(L+1))
+    along an open direction and 2t cos(2 pi k/L) along a periodic one (textbook)."""
+    for ox, oy in ((1, 0), (1, 1)):
+        Lx, Ly, t = 7, 6, -1.0
+        sys = oracle.make_system(lattice=oracle.SQUARE, Lx=Lx, Ly=Ly, t=t, open_x=ox, open_y=oy)
+        lo, hi = oracle.bounds_auto(sys)
+        lam = np.sort(np.linalg.eigvalsh(dense_from_operator(sys)) * hi)
+        ex = 2 * t * np.cos(np.pi * np.arange(1, Lx + 1) / (Lx + 1))
+        ey = (2 * t * np.cos(np.pi * np.arange(1, Ly + 1) / (Ly + 1)) if oy
+              else 2 * t * np.cos(2 * np.pi * np.arange(Ly) / Ly))
+        ref = np.sort((ex[:, None] + ey[None, :]).ravel())
+        assert np.max(np.abs(lam - ref)) < 1e-12
+
+
+def test_field_with_an_open_boundary():
+    """A field on a lattice open along y needs no commensurate flux (no bond wraps in y):
+    H~ stays Hermitian and every plaquette inside encloses the flux, so <x^4> of the square
+    lattice moves by 8 t~^4 (cos 2 pi flux - 1) per plaquette, Lx (Ly - 1) of them."""
+    Lx, Ly, t, flux = 6, 5, -1.0, 0.1
+    sysB = oracle.make_system(lattice=oracle.SQUARE, Lx=Lx, Ly=Ly, t=t, flux=flux, open_y=1)
+    sys0 = oracle.make_system(lattice=oracle.SQUARE, Lx=Lx, Ly=Ly, t=t, open_y=1)
+    H = dense_from_operator(sysB)
+    assert np.max(np.abs(H - H.conj().T)) < 1e-15
+    lo, hi = oracle.bounds_auto(sysB)
+    tt = abs(t) / hi
+    n = Lx * Ly
+    pB, p0 = power_traces(sysB, 4), power_traces(sys0, 4)
+    assert np.max(np.abs(pB[:4] - p0[:4])) < 1e-13
+    shift = 8 * tt ** 4 * (math.cos(2 * math.pi * flux) - 1) * Lx * (Ly - 1) / n
+    assert abs(pB[4] - p0[4] - shift) < 1e-13
+    with pytest.raises(ValueError):  # periodic in y, the same flux does not fit
+        oracle.moments_1d(oracle.make_system(lattice=oracle.SQUARE, Lx=Lx, Ly=Ly, t=t, flux=flux), 4, 1)
+
+
 def test_random_phase_is_white_noise():
     """|xi| = 1 off vacancies, 0 on them; <xi> = 0, <xi xi> = 0, <|xi|^2> = 1 (Sec. 2c)."""
     sys = oracle.make_system(Lx=64, Ly=64, p_vac=0.02, seed=3)
