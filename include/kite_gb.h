@@ -59,7 +59,7 @@ extern "C" {
  * Orbitals are numbered o = 2*(y*Lx + x) + s for the honeycomb lattice (s = 0 for A,
  * 1 for B) and o = y*Lx + x for the square lattice; N = number of orbitals.
  *   lattice  KITE_HONEYCOMB or KITE_SQUARE
- *   Lx, Ly   unit cells along a1, a2 (>= 1); boundaries are periodic in both
+ *   Lx, Ly   unit cells along a1, a2 (>= 1)
  *   t        nearest-neighbour hopping (eV)
  *   disorder KITE_DISORDER_UNIFORM (Anderson, Sec. 4b) or KITE_DISORDER_GAUSSIAN (the
  *            'Gaussian' kind of the Python interface, Sec. 3d)
@@ -82,12 +82,21 @@ extern "C" {
  *            of a, becomes t exp(i theta), theta = -2 pi (flux/A_cell)(y_o - dy/2) dx,
  *            A_cell = sqrt(3)/2 (honeycomb) or 1 (square), y_o the orbital's y
  *            coordinate (cell (x, y) at x a1 + y a2, a1 = (1, 0), a2 = (1/2, sqrt3/2),
- *            A at (0, -a_cc/2), B at (0, +a_cc/2), a_cc = 1/sqrt3).  On the torus
+ *            A at (0, -a_cc/2), B at (0, +a_cc/2), a_cc = 1/sqrt3).  With y periodic
  *            flux * Ly must be even (honeycomb) or an integer (square);
- *            kite_flux_nearest gives the nearest such flux.  Accepted by
+ *            kite_flux_nearest gives the nearest such flux; with y open any flux
+ *            fits.  Accepted by
  *            kite_moments_1d (complex start vectors), kite_moments_2d (the velocity
  *            h~ = [r, H~] carries the same bond phases), kite_spectral_k and kite_ldos;
- *            the other calls return KITE_ERR_ARG for a nonzero flux. */
+ *            the other calls return KITE_ERR_ARG for a nonzero flux.
+ *   open_x, open_y  boundaries along a1, a2 (the configuration's boundaries flag,
+ *            Sec. 3d): 0 = periodic, 1 = open (the bonds that would wrap around
+ *            the torus are absent: honeycomb A(Lx-1, y) - B(0, y-1) for x, A(x, 0) -
+ *            B(x, -1) and A(x, 0) - B(x+1, -1) for y; square the wrapping x or y
+ *            bonds).  Orbital indexing and draws are the same as on the torus.
+ *            Accepted by kite_moments_1d, kite_moments_2d, kite_spectral_k,
+ *            kite_ldos and kite_propagate; kite_moments_1d_batched and
+ *            kite_moments_1d_static return KITE_ERR_ARG for an open boundary. */
 typedef struct {
   int32_t lattice;
   int32_t Lx, Ly;
@@ -98,6 +107,7 @@ typedef struct {
   double p_vac;
   uint64_t seed;
   double flux;
+  int32_t open_x, open_y;
 } kite_system;
 
 /* Chebyshev expansion parameters (the calculation settings of Sec. 3d: num_moments,

@@ -42,11 +42,11 @@ class KiteError(RuntimeError):
 
 
 class System(ctypes.Structure):
-    """``kite_system``: periodic honeycomb/square lattice with disorder."""
+    """``kite_system``: honeycomb/square lattice with disorder, periodic or open."""
     _fields_ = [("lattice", ctypes.c_int32), ("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32),
                 ("disorder", ctypes.c_int32), ("t", ctypes.c_double), ("W", ctypes.c_double),
                 ("delta", ctypes.c_double), ("p_vac", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("flux", ctypes.c_double)]
+                ("flux", ctypes.c_double), ("open_x", ctypes.c_int32), ("open_y", ctypes.c_int32)]
 
 
 class KPM(ctypes.Structure):
@@ -89,12 +89,13 @@ class MLPTrainCfg(ctypes.Structure):
 
 
 def make_system(lattice=HONEYCOMB, Lx=64, Ly=64, t=-2.7, W=0.0, delta=0.0, p_vac=0.0, seed=1,
-                disorder=0, flux=0.0):
+                disorder=0, flux=0.0, open_x=0, open_y=0):
     """W: width of uniform disorder in [-W/2, W/2] (disorder=DISORDER_UNIFORM) or standard
     deviation of Gaussian disorder (disorder=DISORDER_GAUSSIAN); flux: perpendicular
-    magnetic flux quanta per unit cell (see flux_nearest)."""
+    magnetic flux quanta per unit cell (see flux_nearest); open_x / open_y: open
+    boundaries along a1 / a2 (the bonds that wrap around the torus are absent)."""
     return System(int(lattice), int(Lx), int(Ly), int(disorder), float(t), float(W), float(delta),
-                  float(p_vac), int(seed), float(flux))
+                  float(p_vac), int(seed), float(flux), int(bool(open_x)), int(bool(open_y)))
 
 
 def make_kpm(M, R=1, S=1, precision=FP32, e_min=0.0, e_max=0.0, r0=None, r_last=None,

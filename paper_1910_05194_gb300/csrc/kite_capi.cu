@@ -90,6 +90,30 @@ int ensure_ws(kite_ctx* ctx, size_t bytes) {
   return KITE_OK;
 }
 
+int open_zeros(kite_ctx* ctx, const kite_system* sys, const void** out) {
+  *out = nullptr;
+  if (!sys->open_x && !sys->open_y) return KITE_OK;
+  const size_t bytes = ((size_t)sys->Lx + 64) * 128;
+  if (bytes > ctx->zeros_bytes) {
+    if (ctx->zeros) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(ctx->zeros);
+      ctx->zeros = nullptr;
+      ctx->zeros_bytes = 0;
+    }
+    if (cudaMalloc(&ctx->zeros, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->zeros = nullptr;
+      return fail(ctx, KITE_ERR_OOM, "zero row of the open boundaries could not be allocated");
+    }
+    cudaError_t e = cudaMemsetAsync(ctx->zeros, 0, bytes, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "zero row");
+    ctx->zeros_bytes = bytes;
+  }
+  *out = ctx->zeros;
+  return KITE_OK;
+}
+
 int ensure_pinned(kite_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->pinned_bytes) return KITE_OK;
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -157,10 +181,12 @@ static double flux_quantum_step(const kite_system* s) {
   return (s->lattice == KITE_HONEYCOMB ? 2.0 : 1.0) / (double)s->Ly;
 }
 static bool flux_fits(const kite_system* s) {
+  if (s->open_y) return true;  // no bond wraps in y: any flux
   const double q = s->flux / flux_quantum_step(s);
   return fabs(q - nearbyint(q)) <= 1e-9 * fmax(1.0, fabs(q));
 }
 static double nearest_flux(const kite_system* s, double flux) {
+  if (s->open_y) return flux;
   const double step = flux_quantum_step(s);
   return nearbyint(flux / step) * step;
 }
@@ -170,6 +196,8 @@ static int validate_system(kite_ctx* ctx, const kite_system* s) {
   if (s->lattice != KITE_HONEYCOMB && s->lattice != KITE_SQUARE)
     return fail(ctx, KITE_ERR_ARG, "unknown lattice");
   if (s->Lx < 1 || s->Ly < 1) return fail(ctx, KITE_ERR_ARG, "Lx and Ly must be >= 1");
+  if ((s->open_x != 0 && s->open_x != 1) || (s->open_y != 0 && s->open_y != 1))
+    return fail(ctx, KITE_ERR_ARG, "open_x and open_y must be 0 (periodic) or 1 (open)");
   const double cells = (double)s->Lx * (double)s->Ly;
   if (cells * (s->lattice == KITE_HONEYCOMB ? 2 : 1) > 4.0e9)
     return fail(ctx, KITE_ERR_ARG, "more than 4e9 orbitals");
@@ -337,6 +365,7 @@ void kite_destroy(kite_ctx* ctx) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->zeros) cudaFree(ctx->zeros);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->ev2) cudaEventDestroy(ctx->ev2);
@@ -702,6 +731,8 @@ int kite_moments_1d_batched(kite_ctx* ctx, int count, const kite_system* systems
     if (systems[i].lattice != systems[0].lattice)
       return fail(ctx, KITE_ERR_ARG, "all systems of a batch must share the lattice kind");
     if (systems[i].flux != 0.0) return fail(ctx, KITE_ERR_ARG, "the batched sweep takes no magnetic field");
+    if (systems[i].open_x || systems[i].open_y)
+      return fail(ctx, KITE_ERR_ARG, "the batched sweep takes periodic boundaries only");
     if (k.precision != KITE_FP32) return fail(ctx, KITE_ERR_UNSUPPORTED, "the batched sweep is FP32");
     if (k.R != kpms[0].R || k.R < 1 || k.R > 8)
       return fail(ctx, KITE_ERR_ARG, "all systems need the same R, 1 <= R <= 8");

@@ -84,6 +84,10 @@ int sweep_field_t(kite_ctx* ctx, FieldSweep* a) {
   const int G = a->G, M = a->M;
   const Real tt = (Real)a->tt;
   const Real* vt = static_cast<const Real*>(a->vt);
+  Open open;
+  open.zero = static_cast<const unsigned char*>(a->zero);
+  open.x = a->open_x;
+  open.y = a->open_y;
   auto slot = [&](int k) { return a->partial + (size_t)k * G * Q; };
   // r_0 in r0; r_n (n >= 1) in bA (odd n) or bB (even n); r_{n+1} overwrites r_{n-1}
   auto where = [&](int n) -> void* { return n == 0 ? a->r0 : ((n & 1) ? a->bA : a->bB); };
@@ -96,26 +100,26 @@ int sweep_field_t(kite_ctx* ctx, FieldSweep* a) {
     const int steps = (M + 1) / 2;
     launch_pdl(k_step<Real, LAT, C, true, 3, NST, true>, G, kBlock, SM, st, nullptr, a->r0, a->bA, nullptr,
                vt, tt, a->Lx, a->Ly, a->units, slot(1), slot(0), ctx->d_status, a->stall, FamOut{}, 0,
-               SeriesOut{}, a->phase);
+               SeriesOut{}, a->phase, open);
     launches = 1;
     bytes = launch_bytes(2);
     for (int n = 1; n < steps; ++n, ++launches) {
       launch_pdl(k_step<Real, LAT, C, false, 3, NST, true>, G, kBlock, SM, st, where(n - 1), where(n),
                  where(n + 1), nullptr, vt, tt, a->Lx, a->Ly, a->units, slot(2 * n + 1), slot(2 * n),
-                 ctx->d_status, 0, FamOut{}, 0, SeriesOut{}, a->phase);
+                 ctx->d_status, 0, FamOut{}, 0, SeriesOut{}, a->phase, open);
       bytes += launch_bytes(3);
     }
     a->last_prev = a->last_cur = nullptr;
   } else {
     launch_pdl(k_step<Real, LAT, C, true, 0, NST, true>, G, kBlock, SM, st, nullptr, a->r0, a->bA, a->r0, vt,
                tt, a->Lx, a->Ly, a->units, slot(1), slot(0), ctx->d_status, a->stall, FamOut{}, 0,
-               SeriesOut{}, a->phase);
+               SeriesOut{}, a->phase, open);
     launches = 1;
     bytes = launch_bytes(2);
     for (int n = 1; n + 1 < M; ++n, ++launches) {
       launch_pdl(k_step<Real, LAT, C, false, 0, NST, true>, G, kBlock, SM, st, where(n - 1), where(n),
                  where(n + 1), a->r0, vt, tt, a->Lx, a->Ly, a->units, slot(n + 1), nullptr, ctx->d_status, 0,
-                 FamOut{}, 0, SeriesOut{}, a->phase);
+                 FamOut{}, 0, SeriesOut{}, a->phase, open);
       bytes += launch_bytes(4);
     }
     a->last_cur = where(M - 1);

@@ -25,6 +25,9 @@ struct kite_ctx {
   // Device copy of pageable caller start vectors (grows on demand, freed at destroy).
   void* stage = nullptr;
   size_t stage_bytes = 0;
+  // Device zeros: the neighbour rows and cells across an open boundary (grows on demand).
+  void* zeros = nullptr;
+  size_t zeros_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
   // Device status word: kernels set it (never trap) when a bounded wait gives up.
   int* d_status = nullptr;
@@ -43,6 +46,9 @@ int cuda_fail(kite_ctx* ctx, cudaError_t e, const char* what);
 // Ensures at least `bytes` of device work space; returns KITE_OK / KITE_ERR_OOM.
 int ensure_ws(kite_ctx* ctx, size_t bytes);
 int ensure_pinned(kite_ctx* ctx, size_t bytes);
+// Device zeros of the system's open boundaries (one row of the widest cell, 128 bytes per
+// cell, plus a margin for narrow lattices): *out = null for a periodic lattice.
+int open_zeros(kite_ctx* ctx, const kite_system* sys, const void** out);
 
 // True if p is device (or managed) memory of the current device.
 bool is_device_ptr(const void* p);
@@ -86,6 +92,8 @@ struct FieldSweep {
   void *r0, *bA, *bB;
   double* partial;
   const void* phase;  // [Ly][sublattice][2 bonds][cos, sin] of the working precision
+  const void* zero;   // open boundaries: device zeros of at least one row, else null
+  int open_x, open_y;
   // outputs
   void *last_prev, *last_cur;
   double seconds, bytes;

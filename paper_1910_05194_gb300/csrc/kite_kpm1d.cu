@@ -85,6 +85,7 @@ struct Plan {
   bool realv;     // real +-1 start vectors (four FP32 / two FP64 per chunk)
   bool field;     // Peierls phases of a perpendicular magnetic field (kite_field.cu)
   int max_batch;  // vectors per pass
+  Open open;      // open boundaries and their zero buffer
 };
 
 // recursion steps that write r_{n+1}: M - 1 plainly; with doubling, the step from r_n
@@ -116,13 +117,13 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
     const int steps = steps_for(p);
     launch_pdl(k_step<Real, LAT, C, true, 3, NST>, G, kBlock, SMD, st,
         nullptr, r0, bA, nullptr, vt, tt, p.Lx, p.Ly, units,
-        partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
+        partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr, p.open);
     ctx->debug_stall = 0;
     for (int n = 1; n < steps; ++n)
       launch_pdl(k_step<Real, LAT, C, false, 3, NST>, G, kBlock, SMD, st,
           where(n - 1), where(n), where(n + 1), nullptr, vt, tt, p.Lx, p.Ly, units,
           partial + (size_t)(2 * n + 1) * G * Q,
-          partial + (size_t)(2 * n) * G * Q, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
+          partial + (size_t)(2 * n) * G * Q, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr, p.open);
     KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
     KITE_CUDA_TRY(ctx, cudaGetLastError());
     const int total = M * Q;
@@ -143,12 +144,12 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
   if (M >= 2)
     launch_pdl(k_step<Real, LAT, C, true, 0, NST>, G, kBlock, SM, st,
         nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly, units,
-        partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
+        partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr, p.open);
   ctx->debug_stall = 0;
   for (int n = 1; n + 1 < M; ++n)
     launch_pdl(k_step<Real, LAT, C, false, 0, NST>, G, kBlock, SM, st,
         where(n - 1), where(n), where(n + 1), r0, vt, tt, p.Lx, p.Ly, units,
-        partial + (size_t)(n + 1) * G * Q, nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
+        partial + (size_t)(n + 1) * G * Q, nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr, p.open);
   KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
   KITE_CUDA_TRY(ctx, cudaGetLastError());
   if (M == 1) {
@@ -156,7 +157,7 @@ int sweep_batch(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
     // FIRST kernel is cheap and keeps one code path.
     launch_pdl(k_step<Real, LAT, C, true, 0, NST>, G, kBlock, SM, st,
         nullptr, r0, bA, r0, vt, tt, p.Lx, p.Ly, units,
-        partial + (size_t)G * Q, partial, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
+        partial + (size_t)G * Q, partial, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr, p.open);
     KITE_CUDA_TRY(ctx, cudaGetLastError());
   }
   const int total = M * Q;
@@ -202,7 +203,7 @@ int sweep_two(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, v
   step2_occupancy<Real, LAT, C, NST2>();
   launch_pdl(k_step<Real, LAT, C, true, 0, NST1>, G, kBlock, SM, st,
       nullptr, r0, w4(1), r0, vt, tt, p.Lx, p.Ly, units,
-      partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
+      partial + (size_t)G * Q, partial, ctx->d_status, ctx->debug_stall, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr, p.open);
   ctx->debug_stall = 0;
   int n = 1;
   int64_t launches = 1;
@@ -211,13 +212,13 @@ int sweep_two(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, v
     launch_pdl(k_step2<Real, LAT, C, NST2>, G, kBlock2, SM2, st,
         w4(n - 1), w4(n), w4(n + 1), w4(n + 2), r0, vt, tt, p.Lx, p.Ly, units,
         partial + (size_t)(n + 1) * G * Q,
-        partial + (size_t)(n + 2) * G * Q, ctx->d_status, p.realv ? 1 : 0);
+        partial + (size_t)(n + 2) * G * Q, ctx->d_status, p.realv ? 1 : 0, p.open);
     bytes += launch_bytes(5);  // r_{n-1}, r_n, r_0 in; r_{n+1}, r_{n+2} out
   }
   if (n + 1 <= M - 1) {
     launch_pdl(k_step<Real, LAT, C, false, 0, NST1>, G, kBlock, SM, st,
         w4(n - 1), w4(n), w4(n + 1), r0, vt, tt, p.Lx, p.Ly, units,
-        partial + (size_t)(n + 1) * G * Q, nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
+        partial + (size_t)(n + 1) * G * Q, nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr, p.open);
     ++launches;
     bytes += launch_bytes(4);
   }
@@ -281,7 +282,7 @@ float time_candidate2(kite_ctx* ctx, int k, long long units, const Plan& p, cons
   auto launch = [&]() {
     launch_pdl(k_step2<Real, LAT, C, NST>, G, kBlock2, SMEM, st,
         bA, bB, bC, bD, r0, vt, tt, p.Lx, p.Ly, units, partial + (size_t)2 * G * Q,
-        partial + (size_t)3 * G * Q, ctx->d_status, p.realv ? 1 : 0);
+        partial + (size_t)3 * G * Q, ctx->d_status, p.realv ? 1 : 0, p.open);
   };
   launch();  // warm-up
   cudaEventRecord(ctx->ev2, st);
@@ -304,7 +305,7 @@ float time_candidate(kite_ctx* ctx, int k, long long units, const Plan& p, const
     // r_{n-1} = bA, r_n = bB, r_{n+1} over r_{n-1} in place, r_0 apart: the sweep's streams
     launch_pdl(k_step<Real, LAT, C, false, MODE, NST>, G, kBlock, SMEM, st,
         bA, bB, bA, MODE == 0 ? r0 : nullptr, vt, tt, p.Lx, p.Ly, units, partial + (size_t)2 * G * Q,
-        MODE == 3 ? partial + (size_t)G * Q : nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr);
+        MODE == 3 ? partial + (size_t)G * Q : nullptr, ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr, p.open);
   };
   launch();  // warm-up
   cudaEventRecord(ctx->ev2, st);
@@ -425,6 +426,14 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
   p.doubling = kpm->doubling != 0;
   p.realv = kpm->real_vectors != 0;
   p.field = sys->flux != 0.0;
+  {
+    const void* z = nullptr;
+    const int rc = open_zeros(ctx, sys, &z);
+    if (rc != KITE_OK) return rc;
+    p.open.zero = static_cast<const unsigned char*>(z);
+    p.open.x = sys->open_x;
+    p.open.y = sys->open_y;
+  }
   const int per_chunk = p.realv ? Chunk<Real>::kReals : VPC;  // vectors per 16-byte chunk
   p.max_batch = kMaxC * per_chunk;
   auto chunks_for = [&](int nvec) {
@@ -568,6 +577,9 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
         fs.units = u;
         fs.G = (int)std::max(1LL, std::min({(long long)ctx->num_sms * occ, u, (long long)Gmax}));
         fs.stall = ctx->debug_stall;
+        fs.zero = p.open.zero;
+        fs.open_x = p.open.x;
+        fs.open_y = p.open.y;
         fs.ncell = p.ncell;
         fs.N = p.N;
         fs.vt = vt;

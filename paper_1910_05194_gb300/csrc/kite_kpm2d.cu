@@ -43,7 +43,8 @@ constexpr int kGemmProducts = 4; // hi*hi + hi*lo + lo*hi + lo*lo
 template <int LAT>
 __global__ void k_velocity(const float4* __restrict__ in, float4* __restrict__ out_vec,
                            const float* __restrict__ vt, int Lx, int Ly, int mode, const FamOut fam,
-                           const float* __restrict__ phase) {
+                           const float* __restrict__ phase, int open_x, int open_y) {
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   auto rot = [](float4 n, float c, float sn) {  // exp(i theta) on both vectors of the chunk
     return make_float4(fmaf(c, n.x, -(sn * n.y)), fmaf(sn, n.x, c * n.y), fmaf(c, n.z, -(sn * n.w)),
                        fmaf(sn, n.z, c * n.w));
@@ -65,6 +66,11 @@ __global__ void k_velocity(const float4* __restrict__ in, float4* __restrict__ o
       const float4 n1 = __ldg(in + cell * 2 + so);
       float4 n2 = __ldg(in + ((int64_t)ny * Lx + nx) * 2 + so);
       float4 n3 = __ldg(in + ((int64_t)ny * Lx + x) * 2 + so);
+      // bonds across an open boundary: A's n2 leaves at x = Lx-1 or y = 0, n3 at y = 0;
+      // B's n2 at x = 0 or y = Ly-1, n3 at y = Ly-1
+      const bool cy = open_y && (s == 0 ? y == 0 : y + 1 == Ly);
+      if (cy || (open_x && (s == 0 ? x + 1 == Lx : x == 0))) n2 = z4;
+      if (cy) n3 = z4;
       if (phase) {
         const float* p4 = phase + ((size_t)y * 2 + s) * 4;
         n2 = rot(n2, __ldg(p4), __ldg(p4 + 1));
@@ -79,6 +85,8 @@ __global__ void k_velocity(const float4* __restrict__ in, float4* __restrict__ o
     } else {
       float4 n1 = __ldg(in + (fam.dir == 0 ? (int64_t)y * Lx + xm : (int64_t)ym * Lx + x));
       float4 n2 = __ldg(in + (fam.dir == 0 ? (int64_t)y * Lx + xp : (int64_t)yp * Lx + x));
+      if (fam.dir == 0 ? open_x && x == 0 : open_y && y == 0) n1 = z4;
+      if (fam.dir == 0 ? open_x && x + 1 == Lx : open_y && y + 1 == Ly) n2 = z4;
       if (phase && fam.dir == 0) {  // the y bonds carry no phase in the Landau gauge
         const float* p4 = phase + (size_t)y * 4;
         n1 = rot(n1, __ldg(p4), __ldg(p4 + 1));
@@ -154,6 +162,15 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
     int rc = field_phases(ctx, sys, 0, ph);
     if (rc != KITE_OK) return rc;
   }
+  Open open;
+  {
+    const void* z = nullptr;
+    int rc = open_zeros(ctx, sys, &z);
+    if (rc != KITE_OK) return rc;
+    open.zero = static_cast<const unsigned char*>(z);
+    open.x = sys->open_x;
+    open.y = sys->open_y;
+  }
   if (Kp > 2 * N) {  // zero the K padding (the tail of the last K block of every row) once
     const int64_t k0 = 2 * N;  // first padded column; Kp - k0 < 64, all in the last block
     const size_t width = (size_t)(Kp - k0) * 2;
@@ -226,18 +243,19 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
       // A family: a_0 = h~alpha r_0 (row 0, and the recursion's start vector in bB)
       fa.col = 0;
       k_velocity<LAT><<<blocks, 256, 0, st>>>(static_cast<const float4*>(r0),
-                                              static_cast<float4*>(bB), vt, sys->Lx, sys->Ly, 1, fa, ph);
+                                              static_cast<float4*>(bB), vt, sys->Lx, sys->Ly, 1, fa, ph,
+                                              open.x, open.y);
       auto whereA = [&](int n) -> void* { return (n & 1) ? bA : bB; };
       for (int n = 0; n + 1 < M; ++n) {
         fa.col = n + 1;
         if (n == 0)
           k_step<float, LAT, C, true, 1, kStages, FIELD><<<G, kBlock, SM, st>>>(
               nullptr, whereA(0), whereA(1), nullptr, vt, tt, sys->Lx, sys->Ly, units, nullptr,
-              nullptr, ctx->d_status, 0, fa, 0, SeriesOut{}, ph);
+              nullptr, ctx->d_status, 0, fa, 0, SeriesOut{}, ph, open);
         else
           k_step<float, LAT, C, false, 1, kStages, FIELD><<<G, kBlock, SM, st>>>(
               whereA(n - 1), whereA(n), whereA(n + 1), nullptr, vt, tt, sys->Lx, sys->Ly, units,
-              nullptr, nullptr, ctx->d_status, 0, fa, 0, SeriesOut{}, ph);
+              nullptr, nullptr, ctx->d_status, 0, fa, 0, SeriesOut{}, ph, open);
       }
       // B family: recursion from r_0; step n writes b_n = h~beta r_n
       auto whereB = [&](int n) -> void* { return n == 0 ? r0 : ((n & 1) ? bA : bB); };
@@ -246,15 +264,15 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
         if (n == 0)
           k_step<float, LAT, C, true, 2, kStages, FIELD><<<G, kBlock, SM, st>>>(
               nullptr, whereB(0), whereB(1), nullptr, vt, tt, sys->Lx, sys->Ly, units, nullptr,
-              nullptr, ctx->d_status, 0, fb, 0, SeriesOut{}, ph);
+              nullptr, ctx->d_status, 0, fb, 0, SeriesOut{}, ph, open);
         else
           k_step<float, LAT, C, false, 2, kStages, FIELD><<<G, kBlock, SM, st>>>(
               whereB(n - 1), whereB(n), whereB(n + 1), nullptr, vt, tt, sys->Lx, sys->Ly, units,
-              nullptr, nullptr, ctx->d_status, 0, fb, 0, SeriesOut{}, ph);
+              nullptr, nullptr, ctx->d_status, 0, fb, 0, SeriesOut{}, ph, open);
       }
       fb.col = M - 1;
       k_velocity<LAT><<<blocks, 256, 0, st>>>(static_cast<const float4*>(whereB(M - 1)), nullptr, vt,
-                                              sys->Lx, sys->Ly, 2, fb, ph);
+                                              sys->Lx, sys->Ly, 2, fb, ph, open.x, open.y);
       KITE_CUDA_TRY(ctx, cudaGetLastError());
       KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, st));
       // contraction, one vector at a time, accumulated in FP64

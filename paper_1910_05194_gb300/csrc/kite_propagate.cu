@@ -174,6 +174,15 @@ int propagate_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   Carver w(ctx->ws);
   lay(w, &vt, &r0, &bA, &bB, &acc, &part, &ne);
   cudaStream_t st = ctx->stream;
+  Open open;
+  {
+    const void* z = nullptr;
+    rc = open_zeros(ctx, sys, &z);
+    if (rc != KITE_OK) return rc;
+    open.zero = static_cast<const unsigned char*>(z);
+    open.x = sys->open_x;
+    open.y = sys->open_y;
+  }
   std::vector<double> coef(2 * (size_t)M);
   evolution_coeffs(M, dt, sc.de_plus, sc.de_minus, coef.data());
   const Real tt = (Real)(sys->t / sc.de_minus);
@@ -201,11 +210,12 @@ int propagate_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
       if (M >= 2)
         k_step<Real, LAT, C, true, 4><<<G, kBlock, SM, st>>>(nullptr, cur, bA, nullptr, vt, tt, sys->Lx, sys->Ly,
                                                              units, nullptr, nullptr, ctx->d_status, 0, FamOut{}, 0,
-                                                             SeriesOut{nxt, coef[2], coef[3]});
+                                                             SeriesOut{nxt, coef[2], coef[3]}, nullptr, open);
       for (int n = 1; n + 1 < M; ++n)
         k_step<Real, LAT, C, false, 4><<<G, kBlock, SM, st>>>(
             where(n - 1), where(n), where(n + 1), nullptr, vt, tt, sys->Lx, sys->Ly, units, nullptr, nullptr,
-            ctx->d_status, 0, FamOut{}, 0, SeriesOut{nxt, coef[2 * (n + 1)], coef[2 * (n + 1) + 1]});
+            ctx->d_status, 0, FamOut{}, 0, SeriesOut{nxt, coef[2 * (n + 1)], coef[2 * (n + 1) + 1]}, nullptr,
+            open);
       launches += std::max(0, M - 1);
       KITE_CUDA_TRY(ctx, cudaGetLastError());
       std::swap(cur, nxt);

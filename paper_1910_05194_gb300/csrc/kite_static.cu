@@ -208,6 +208,8 @@ int moments_1d_static_checked(const kite_system* sys, const kite_kpm* kpm_in, do
       (sys->disorder != KITE_DISORDER_UNIFORM && sys->disorder != KITE_DISORDER_GAUSSIAN))
     return static_fail(KITE_ERR_ARG, "invalid system");
   if (sys->flux != 0.0) return static_fail(KITE_ERR_ARG, "the allocation-free call takes no magnetic field");
+  if (sys->open_x || sys->open_y)
+    return static_fail(KITE_ERR_ARG, "the allocation-free call takes periodic boundaries only");
   if (kpm->M < 1 || kpm->M > 65536 || kpm->R < 1 || kpm->S < 1)
     return static_fail(KITE_ERR_ARG, "need 1 <= M <= 65536, R >= 1, S >= 1");
   if (kpm->r0 || kpm->r_last || kpm->doubling != 0 || kpm->real_vectors != 0)

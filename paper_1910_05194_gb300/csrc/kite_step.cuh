@@ -266,6 +266,16 @@ __device__ __forceinline__ void moment_partials(double (&dacc)[QT], Acc (&facc)[
 }
 
 
+// Open boundaries (the configuration's boundaries flag set to False): a bond whose cell
+// offset leaves the lattice along an open direction is absent.  The kernels stage the
+// neighbour cells and rows across such a boundary from `zero` (a device buffer of zeros
+// at least one row long, Lx * cells bytes) instead of the wrapped ones, so the stencil
+// and the velocity see a zero neighbour.
+struct Open {
+  const unsigned char* zero = nullptr;
+  int x = 0, y = 0;
+};
+
 // Per-CTA state of the shared-memory ring; a persistent launch keeps it across steps.
 struct Ring {
   uint64_t* bars;
@@ -288,7 +298,8 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
                                           double* __restrict__ partial, double* __restrict__ partial0,
                                           int* __restrict__ err, int stall, const FamOut& fam,
                                           int realv = 0, const SeriesOut& ser = SeriesOut{},
-                                          const Real* __restrict__ phase = nullptr) {
+                                          const Real* __restrict__ phase = nullptr,
+                                          const Open& open = Open{}) {
   static_assert(MODE == 0 || MODE == 3 || MODE == 4 || (sizeof(Real) == 4 && C * 2 <= kMaxFamVecs),
                 "family modes run on FP32 batches of at most two vectors");
   using Ch = Chunk<Real>;
@@ -339,6 +350,7 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
       const int st = (int)(g % NST);
       unsigned char* base = stages + st * STG;
       int row = yb - 1 + jj;
+      const bool wrapped = row < 0 || row >= Ly;
       row = row < 0 ? row + Ly : (row >= Ly ? row - Ly : row);
       const bool interior = !FIRST && jj >= 1 && jj <= nr;
       const uint32_t main_b = (uint32_t)txv * CELLB;
@@ -346,10 +358,14 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
       uint32_t bytes = main_b + 2 * CELLB + (interior ? (MODE == 0 ? 2 : 1) * main_b : 0);
       if (stall && cta == 0 && g == 0) bytes += 16;  // test hook: never completes
       mbar_arrive_expect_tx(&bars[st], bytes);
-      const unsigned char* rowp = static_cast<const unsigned char*>(r_cur) + (size_t)row * Lx * CELLB;
+      // a row or halo cell across an open boundary comes from the zero buffer
+      const unsigned char* rowp = (open.y && wrapped)
+                                      ? open.zero
+                                      : static_cast<const unsigned char*>(r_cur) + (size_t)row * Lx * CELLB;
       bulk_g2s(base + CELLB, rowp + (size_t)x0 * CELLB, main_b, &bars[st]);
-      bulk_g2s(base, rowp + (size_t)xlh * CELLB, CELLB, &bars[st]);
-      bulk_g2s(base + (size_t)(txv + 1) * CELLB, rowp + (size_t)xrh * CELLB, CELLB, &bars[st]);
+      bulk_g2s(base, (open.x && x0 == 0) ? open.zero : rowp + (size_t)xlh * CELLB, CELLB, &bars[st]);
+      bulk_g2s(base + (size_t)(txv + 1) * CELLB,
+               (open.x && x0 + txv == Lx) ? open.zero : rowp + (size_t)xrh * CELLB, CELLB, &bars[st]);
       if (interior) {
         const size_t off = ((size_t)row * Lx + x0) * CELLB;
         bulk_g2s(base + Sh::CURB, static_cast<const unsigned char*>(r_prev) + off, main_b, &bars[st]);
@@ -578,7 +594,7 @@ __global__ void __launch_bounds__(kBlock, 2)
            const void* __restrict__ r0, const Real* __restrict__ vt, Real tt, int Lx, int Ly,
            long long units, double* __restrict__ partial, double* __restrict__ partial0,
            int* __restrict__ err, int stall, const FamOut fam, int realv = 0,
-           const SeriesOut ser = SeriesOut{}, const void* phase = nullptr) {
+           const SeriesOut ser = SeriesOut{}, const void* phase = nullptr, const Open open = Open{}) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
@@ -592,7 +608,7 @@ __global__ void __launch_bounds__(kBlock, 2)
   griddep_launch_dependents();
   step_body<Real, LAT, C, FIRST, MODE, NST, FIELD>(ring, blockIdx.x, gridDim.x, r_prev, r_cur, r_out, r0,
                                                    vt, tt, Lx, Ly, units, partial, partial0, err, stall,
-                                                   fam, realv, ser, static_cast<const Real*>(phase));
+                                                   fam, realv, ser, static_cast<const Real*>(phase), open);
 }
 
 // Launch with programmatic stream serialisation: the kernel's set-up overlaps the end of
