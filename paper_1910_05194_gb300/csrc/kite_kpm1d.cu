@@ -212,7 +212,7 @@ int sweep_two(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, v
     launch_pdl(k_step2<Real, LAT, C, NST2>, G, kBlock2, SM2, st,
         w4(n - 1), w4(n), w4(n + 1), w4(n + 2), r0, vt, tt, p.Lx, p.Ly, units,
         partial + (size_t)(n + 1) * G * Q,
-        partial + (size_t)(n + 2) * G * Q, ctx->d_status, p.realv ? 1 : 0, p.open);
+        partial + (size_t)(n + 2) * G * Q, ctx->d_status, p.realv ? 1 : 0);
     bytes += launch_bytes(5);  // r_{n-1}, r_n, r_0 in; r_{n+1}, r_{n+2} out
   }
   if (n + 1 <= M - 1) {
@@ -282,7 +282,7 @@ float time_candidate2(kite_ctx* ctx, int k, long long units, const Plan& p, cons
   auto launch = [&]() {
     launch_pdl(k_step2<Real, LAT, C, NST>, G, kBlock2, SMEM, st,
         bA, bB, bC, bD, r0, vt, tt, p.Lx, p.Ly, units, partial + (size_t)2 * G * Q,
-        partial + (size_t)3 * G * Q, ctx->d_status, p.realv ? 1 : 0, p.open);
+        partial + (size_t)3 * G * Q, ctx->d_status, p.realv ? 1 : 0);
   };
   launch();  // warm-up
   cudaEventRecord(ctx->ev2, st);
@@ -321,7 +321,9 @@ float time_candidate(kite_ctx* ctx, int k, long long units, const Plan& p, const
 // for at least one pass.
 template <int MODE>
 bool two_step_allowed(const Plan& p) {
-  return MODE == 0 && p.M >= 4 && !p.field && pass_steps_pinned() != 1;
+  // a field or an open boundary takes the one-step kernel (its variants stage the
+  // neighbours the pass would have to rotate or zero in its halo)
+  return MODE == 0 && p.M >= 4 && !p.field && !p.open.x && !p.open.y && pass_steps_pinned() != 1;
 }
 
 template <typename Real, int LAT, int C, int MODE>

@@ -47,7 +47,7 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
                                            void* __restrict__ out2, const void* __restrict__ r0,
                                            const Real* __restrict__ vt, Real tt, int Lx, int Ly, long long units,
                                            double* __restrict__ partial1, double* __restrict__ partial2,
-                                           int* __restrict__ err, int realv, const Open& open) {
+                                           int* __restrict__ err, int realv) {
   using Ch = Chunk<Real>;
   using Acc = typename AccT<Real>::T;
   using Sh = Step2Shape<LAT, C, NST>;
@@ -105,18 +105,11 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
     const int nslots = nr + 4;  // r_n rows yb-2 .. yb+nr+1
 
     // copies of `ncell` cells starting at global cell x (wrapped per cell when the run
-    // crosses the periodic boundary; across an open boundary, from the zero buffer) into dst
+    // crosses the periodic boundary) into dst
     auto copy_cells = [&](unsigned char* dst, const unsigned char* rowp, int x, int ncell, uint64_t* bar) {
       int k = 0;
       while (k < ncell) {
-        const int xg = x + k;
-        if (open.x && (xg < 0 || xg >= Lx)) {
-          const int run = xg < 0 ? min(ncell - k, -xg) : ncell - k;
-          bulk_g2s(dst + (size_t)k * CELLB, open.zero, (uint32_t)run * CELLB, bar);
-          k += run;
-          continue;
-        }
-        const int xs = wrapx(xg);
+        const int xs = wrapx(x + k);
         int run = min(ncell - k, Lx - xs);
         bulk_g2s(dst + (size_t)k * CELLB, rowp + (size_t)xs * CELLB, (uint32_t)run * CELLB, bar);
         k += run;
@@ -125,15 +118,13 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
     auto issue = [&](int jj, int st) {  // producer: slot jj (r_n row yb-2+jj) into stage st
       unsigned char* base = stages + st * Sh::STAGEB;
       int row = yb - 2 + jj;
-      const bool wrapped = row < 0 || row >= Ly;
       while (row < 0) row += Ly;
       while (row >= Ly) row -= Ly;
       const bool need_r0 = jj >= 2 && jj <= nr + 1;  // owned rows
       const uint32_t bytes = (uint32_t)(txv + 4) * CELLB + (need_r0 ? (uint32_t)txv * CELLB : 0u);
       mbar_arrive_expect_tx(&bars[st], bytes);
       const size_t roff = (size_t)row * Lx * CELLB;
-      copy_cells(base, (open.y && wrapped) ? open.zero : static_cast<const unsigned char*>(r_cur) + roff, x0 - 2,
-                 txv + 4, &bars[st]);
+      copy_cells(base, static_cast<const unsigned char*>(r_cur) + roff, x0 - 2, txv + 4, &bars[st]);
       if (need_r0)
         bulk_g2s(base + Sh::RNB, static_cast<const unsigned char*>(r0) + roff + (size_t)x0 * CELLB,
                  (uint32_t)txv * CELLB, &bars[st]);
@@ -279,11 +270,8 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
       const unsigned char* mid = stages + st1 * Sh::STAGEB;
       const unsigned char* dn = stages + st2 * Sh::STAGEB;
       unsigned char* t3 = tile + o3;
-      // an r_{n+1} halo row or cell across an open boundary is not a neighbour: zero
-      const bool zrow = open.y && ((i == 0 && yb == 0) || (i == nr + 1 && yb + nr == Ly));
       if (do1 && ok && active) {  // own cell (tile cell xl+1)
-        Ch o = site1(up, mid, dn, xl + 1, v1, pv1);
-        if (zrow) o = Ch{};
+        const Ch o = site1(up, mid, dn, xl + 1, v1, pv1);
         *reinterpret_cast<Ch*>(t3 + (xl + 1) * CELLB + choff) = o;
         if (i >= 1 && i <= nr) {
           o.st(out1, ocol + (size_t)(uint32_t)(yb - 1 + i) * orow);
@@ -293,8 +281,7 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
       }
       if (do1 && ok && halo) {  // halo cell left (tile cell 0) or right (tile cell txv+1)
         const int tx = hcell ? txv + 1 : 0;
-        const bool zcell = zrow || (open.x && (hcell ? x0 + txv == Lx : x0 == 0));
-        *reinterpret_cast<Ch*>(t3 + tx * CELLB + choff) = zcell ? Ch{} : site1(up, mid, dn, tx, v1, pv1);
+        *reinterpret_cast<Ch*>(t3 + tx * CELLB + choff) = site1(up, mid, dn, tx, v1, pv1);
       }
       if (do2 && ok && active) {
         // r_{n+2} row y2 = yb-3+i from tile rows y2-1, y2, y2+1 and r_n, r_0 of row y2
@@ -360,8 +347,7 @@ template <typename Real, int LAT, int C, int NST>
 __global__ void __launch_bounds__(kBlock2, 3 * Step2Shape<LAT, C, NST>::SMEM <= 227 * 1024 ? 3 : 2)
     k_step2(const void* r_prev, const void* __restrict__ r_cur, void* out1, void* out2,
             const void* __restrict__ r0, const Real* __restrict__ vt, Real tt, int Lx, int Ly, long long units,
-            double* __restrict__ partial1, double* __restrict__ partial2, int* __restrict__ err, int realv,
-            const Open open) {
+            double* __restrict__ partial1, double* __restrict__ partial2, int* __restrict__ err, int realv) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
@@ -374,7 +360,7 @@ __global__ void __launch_bounds__(kBlock2, 3 * Step2Shape<LAT, C, NST>::SMEM <= 
   griddep_wait();  // the previous launch's iterates and partials are complete
   griddep_launch_dependents();
   step2_body<Real, LAT, C, NST>(ring, blockIdx.x, gridDim.x, r_prev, r_cur, out1, out2, r0, vt, tt, Lx, Ly,
-                                units, partial1, partial2, err, realv, open);
+                                units, partial1, partial2, err, realv);
 }
 
 template <typename Real, int LAT, int C, int NST>
