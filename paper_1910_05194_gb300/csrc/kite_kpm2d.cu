@@ -249,11 +249,11 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
       for (int n = 0; n + 1 < M; ++n) {
         fa.col = n + 1;
         if (n == 0)
-          k_step<float, LAT, C, true, 1, kStages, FIELD><<<G, kBlock, SM, st>>>(
+          launch_pdl(k_step<float, LAT, C, true, 1, kStages, FIELD>, G, kBlock, SM, st,
               nullptr, whereA(0), whereA(1), nullptr, vt, tt, sys->Lx, sys->Ly, units, nullptr,
               nullptr, ctx->d_status, 0, fa, 0, SeriesOut{}, ph, open);
         else
-          k_step<float, LAT, C, false, 1, kStages, FIELD><<<G, kBlock, SM, st>>>(
+          launch_pdl(k_step<float, LAT, C, false, 1, kStages, FIELD>, G, kBlock, SM, st,
               whereA(n - 1), whereA(n), whereA(n + 1), nullptr, vt, tt, sys->Lx, sys->Ly, units,
               nullptr, nullptr, ctx->d_status, 0, fa, 0, SeriesOut{}, ph, open);
       }
@@ -262,11 +262,11 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
       for (int n = 0; n + 1 < M; ++n) {
         fb.col = n;
         if (n == 0)
-          k_step<float, LAT, C, true, 2, kStages, FIELD><<<G, kBlock, SM, st>>>(
+          launch_pdl(k_step<float, LAT, C, true, 2, kStages, FIELD>, G, kBlock, SM, st,
               nullptr, whereB(0), whereB(1), nullptr, vt, tt, sys->Lx, sys->Ly, units, nullptr,
               nullptr, ctx->d_status, 0, fb, 0, SeriesOut{}, ph, open);
         else
-          k_step<float, LAT, C, false, 2, kStages, FIELD><<<G, kBlock, SM, st>>>(
+          launch_pdl(k_step<float, LAT, C, false, 2, kStages, FIELD>, G, kBlock, SM, st,
               whereB(n - 1), whereB(n), whereB(n + 1), nullptr, vt, tt, sys->Lx, sys->Ly, units,
               nullptr, nullptr, ctx->d_status, 0, fb, 0, SeriesOut{}, ph, open);
       }
