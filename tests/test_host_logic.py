@@ -22,3 +22,24 @@ def test_evolution_coefficients_match_oracle(lib_loaded, M, dt, lo, hi):
     got = kite.evolution_coeffs(M, dt, lo, hi)
     ref = oracle.evolution_coeffs(M, dt, lo, hi)
     assert np.max(np.abs(got - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_flux_commensurability_and_open_boundaries(lib_loaded):
+    """The admissible fluxes of the Landau gauge on the torus (flux * Ly even on the
+    honeycomb, integer on the square lattice) and none with y open; the bounds of an open
+    lattice equal the oracle's (the Gershgorin enclosure does not depend on the
+    boundaries); a boundary flag other than 0 or 1 is refused."""
+    hc = kite.make_system(kite.HONEYCOMB, 16, 16, -2.7, 0.0)
+    assert kite.flux_nearest(hc, 0.1) == 0.125
+    sq = kite.make_system(kite.SQUARE, 16, 20, -1.0, 0.0)
+    assert abs(kite.flux_nearest(sq, 0.16) - 0.15) < 1e-15
+    assert kite.flux_nearest(kite.make_system(kite.HONEYCOMB, 16, 16, -2.7, 0.0, open_y=1), 0.1) == 0.1
+    assert kite.flux_nearest(kite.make_system(kite.HONEYCOMB, 16, 16, -2.7, 0.0, open_x=1), 0.1) == 0.125
+    for lat, t in ((kite.HONEYCOMB, -2.7), (kite.SQUARE, -1.0)):
+        d = dict(lattice=lat, Lx=9, Ly=7, t=t, W=1.3, delta=0.2 if lat == kite.HONEYCOMB else 0.0,
+                 open_x=1, open_y=1)
+        assert kite.bounds(kite.make_system(**d)) == oracle.bounds_auto(oracle.make_system(**d))
+    bad = kite.make_system(kite.SQUARE, 8, 8, -1.0, 0.0)
+    bad.open_y = 3
+    with pytest.raises(kite.KiteError):
+        kite.bounds(bad)
