@@ -87,8 +87,8 @@ extern "C" {
  *            kite_flux_nearest gives the nearest such flux; with y open any flux
  *            fits.  Accepted by
  *            kite_moments_1d (complex start vectors), kite_moments_2d (the velocity
- *            h~ = [r, H~] carries the same bond phases), kite_spectral_k and kite_ldos;
- *            the other calls return KITE_ERR_ARG for a nonzero flux.
+ *            h~ = [r, H~] carries the same bond phases), kite_spectral_k, kite_ldos and
+ *            kite_propagate; the other calls return KITE_ERR_ARG for a nonzero flux.
  *   open_x, open_y  boundaries along a1, a2 (the configuration's boundaries flag,
  *            Sec. 3d): 0 = periodic, 1 = open (the bonds that would wrap around
  *            the torus are absent: honeycomb A(Lx-1, y) - B(0, y-1) for x, A(x, 0) -
@@ -272,7 +272,8 @@ int kite_ldos(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
  * (-1)^n is read as (-i)^n, which the expansion of exp(-i x tau) has).  M Chebyshev terms
  * per step: the truncation error falls off like J_M(de_minus dt), negligible once
  * M > 1.1 de_minus dt + 20.  Each step runs M - 1 stencil steps that also accumulate the
- * series; vacant orbitals stay 0.
+ * series; vacant orbitals stay 0.  A magnetic field (sys->flux) and open boundaries
+ * enter H as in the moment sweeps.
  *   kpm     M terms per step, R wave functions, S = 1, precision (FP32 or FP64
  *           recursion and accumulation), bounds; r0, r_last NULL, doubling 0
  *   psi     [R][N] complex FP64 interleaved, host or device: psi(0) on entry,

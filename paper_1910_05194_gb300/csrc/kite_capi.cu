@@ -694,7 +694,6 @@ int kite_propagate(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, d
     return fail(ctx, KITE_ERR_ARG, "precision must be KITE_FP32 or KITE_FP64");
   if (kpm->r0 || kpm->r_last || kpm->doubling != 0 || kpm->real_vectors != 0)
     return fail(ctx, KITE_ERR_ARG, "no r0/r_last (psi is the start), doubling 0, complex vectors");
-  if (sys->flux != 0.0) return fail(ctx, KITE_ERR_ARG, "time evolution takes no magnetic field");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, KITE_ERR_CUDA, "cudaSetDevice");
   Scale sc;
   rc = resolve_bounds(ctx, sys, kpm->e_min, kpm->e_max, &sc);

@@ -139,7 +139,7 @@ __global__ void k_extract64(int64_t ncell, const void* __restrict__ buf, int nve
   }
 }
 
-template <typename Real, int LAT, int C>
+template <typename Real, int LAT, int C, bool FIELD>
 int propagate_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc, double dt,
                     int nsteps, double* psi, double* norms, kite_stats* stats) {
   constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
@@ -151,12 +151,13 @@ int propagate_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   const int64_t nchunk = ncell * SORB * C;
   const size_t vb = (size_t)nchunk * 16;
   const long long units = (long long)((sys->Lx + Sh::TX - 1) / Sh::TX) * sys->Ly;
-  const int G = grid_for<Real, LAT, C, false, 4>(ctx, units);
+  const int G = grid_for<Real, LAT, C, false, 4, kStages, FIELD>(ctx, units);
   const int nb = (int)std::min<int64_t>((nchunk + 255) / 256, (int64_t)ctx->num_sms * 8);
   Carver probe(nullptr);
   auto lay = [&](Carver& k, Real** vt, void** r0, void** bA, void** bB, void** acc, double** part,
-                 unsigned long long** ne) {
+                 unsigned long long** ne, Real** ph) {
     *vt = k.take<Real>(N);
+    *ph = FIELD ? k.take<Real>((size_t)sys->Ly * SORB * 4) : nullptr;
     *r0 = k.take<char>(vb);
     *bA = k.take<char>(vb);
     *bB = k.take<char>(vb);
@@ -168,12 +169,17 @@ int propagate_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
   void *r0, *bA, *bB, *acc;
   double* part;
   unsigned long long* ne;
-  lay(probe, &vt, &r0, &bA, &bB, &acc, &part, &ne);
+  Real* ph;
+  lay(probe, &vt, &r0, &bA, &bB, &acc, &part, &ne, &ph);
   int rc = ensure_ws(ctx, probe.used());
   if (rc != KITE_OK) return rc;
   Carver w(ctx->ws);
-  lay(w, &vt, &r0, &bA, &bB, &acc, &part, &ne);
+  lay(w, &vt, &r0, &bA, &bB, &acc, &part, &ne, &ph);
   cudaStream_t st = ctx->stream;
+  if (FIELD) {  // Peierls phases of the bonds with an x component, per row and sublattice
+    rc = field_phases(ctx, sys, sizeof(Real) == 8, ph);
+    if (rc != KITE_OK) return rc;
+  }
   Open open;
   {
     const void* z = nullptr;
@@ -208,14 +214,13 @@ int propagate_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
       auto where = [&](int n) -> void* { return n == 0 ? cur : ((n & 1) ? bA : bB); };
       k_series_init<Real><<<nb, 256, 0, st>>>(nchunk, cur, nxt, coef[0], coef[1]);
       if (M >= 2)
-        k_step<Real, LAT, C, true, 4><<<G, kBlock, SM, st>>>(nullptr, cur, bA, nullptr, vt, tt, sys->Lx, sys->Ly,
-                                                             units, nullptr, nullptr, ctx->d_status, 0, FamOut{}, 0,
-                                                             SeriesOut{nxt, coef[2], coef[3]}, nullptr, open);
+        k_step<Real, LAT, C, true, 4, kStages, FIELD><<<G, kBlock, SM, st>>>(
+            nullptr, cur, bA, nullptr, vt, tt, sys->Lx, sys->Ly, units, nullptr, nullptr, ctx->d_status, 0, FamOut{},
+            0, SeriesOut{nxt, coef[2], coef[3]}, ph, open);
       for (int n = 1; n + 1 < M; ++n)
-        k_step<Real, LAT, C, false, 4><<<G, kBlock, SM, st>>>(
+        k_step<Real, LAT, C, false, 4, kStages, FIELD><<<G, kBlock, SM, st>>>(
             where(n - 1), where(n), where(n + 1), nullptr, vt, tt, sys->Lx, sys->Ly, units, nullptr, nullptr,
-            ctx->d_status, 0, FamOut{}, 0, SeriesOut{nxt, coef[2 * (n + 1)], coef[2 * (n + 1) + 1]}, nullptr,
-            open);
+            ctx->d_status, 0, FamOut{}, 0, SeriesOut{nxt, coef[2 * (n + 1)], coef[2 * (n + 1) + 1]}, ph, open);
       launches += std::max(0, M - 1);
       KITE_CUDA_TRY(ctx, cudaGetLastError());
       std::swap(cur, nxt);
@@ -259,7 +264,9 @@ int propagate_impl(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, c
   const int per = fp64 ? 1 : 2;
   const int c = (std::min(kpm->R, 4 * per) + per - 1) / per;
   const int C = c <= 1 ? 1 : (c <= 2 ? 2 : 4);
-#define KITE_P(REAL, LATV, CC) propagate_typed<REAL, LATV, CC>(ctx, sys, kpm, sc, dt, nsteps, psi, norms, st)
+#define KITE_P(REAL, LATV, CC)                                                                     \
+  (sys->flux != 0.0 ? propagate_typed<REAL, LATV, CC, true>(ctx, sys, kpm, sc, dt, nsteps, psi, norms, st) \
+                    : propagate_typed<REAL, LATV, CC, false>(ctx, sys, kpm, sc, dt, nsteps, psi, norms, st))
 #define KITE_PC(REAL, LATV) (C == 1 ? KITE_P(REAL, LATV, 1) : (C == 2 ? KITE_P(REAL, LATV, 2) : KITE_P(REAL, LATV, 4)))
   if (sys->lattice == KITE_HONEYCOMB) return fp64 ? KITE_PC(double, KITE_HONEYCOMB) : KITE_PC(float, KITE_HONEYCOMB);
   return fp64 ? KITE_PC(double, KITE_SQUARE) : KITE_PC(float, KITE_SQUARE);

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+import synth
 
 pytestmark = pytest.mark.gpu
 
@@ -127,3 +128,25 @@ def test_calls_without_field_support_refuse_a_field(ctx):
         kite.moments_1d_batched(ctx, [s], [kite.make_kpm(8, 2, 1, kite.FP32)], [np.zeros(8)])
     with pytest.raises(kite.KiteError):
         kite.moments_1d_static(s, kite.make_kpm(8, 2, 1, kite.FP32), np.zeros(8))
+
+
+@pytest.mark.parametrize("prec,bar", [(kite.FP64, 1e-10), (kite.FP32, 2e-5)])
+@pytest.mark.parametrize("lattice,Ly,flux,oy", [(oracle.HONEYCOMB, 16, 2 / 16, 0), (oracle.SQUARE, 20, 3 / 20, 0),
+                                                 (oracle.SQUARE, 15, 0.07, 1)])
+def test_wave_packet_evolution_in_a_field(ctx, lattice, Ly, flux, oy, prec, bar):
+    """exp(-i H dt) with the Peierls phases (and with y open, a flux that does not fit the
+    torus) against the oracle's Chebyshev propagator on its own field Hamiltonian; the
+    norm is conserved."""
+    t = -2.7 if lattice == oracle.HONEYCOMB else -1.0
+    d = dict(lattice=lattice, Lx=30, Ly=Ly, t=t, W=0.5, p_vac=0.02, seed=12, flux=flux, open_y=oy)
+    o = oracle.make_system(**d)
+    n = oracle.norb(o)
+    R, dt, steps, M = 2, 0.6, 3, 48
+    psi0 = synth.unit_phase_vectors(n, R, seed=4) / np.sqrt(n)
+    psi = np.ascontiguousarray(np.stack([psi0.real, psi0.imag], -1))
+    norms = np.zeros((steps, R))
+    kite.propagate(ctx, kite.make_system(**d), kite.make_kpm(M, R, 1, prec), dt, steps, psi, norms)
+    for r in range(R):
+        ref = oracle.propagate(o, psi0[r], dt, steps, M)
+        assert np.max(np.abs(psi[r, :, 0] + 1j * psi[r, :, 1] - ref[-1])) <= bar * max(1.0, np.max(np.abs(ref[-1])))
+        assert np.max(np.abs(norms[:, r] - np.sum(np.abs(ref) ** 2, axis=1))) <= (1e-10 if prec == kite.FP64 else 1e-5)
