@@ -207,13 +207,29 @@ def cpu_baseline_leg(args, kite, ctx, n_eff_gpu):
     _, vac = oracle.disorder(s)
     n_eff = int((vac == 0).sum())
     mu = np.zeros(M)
-    kite.moments_1d(ctx, kite.make_system(lattice=0, Lx=args.Lx, Ly=args.Ly, t=WORKLOAD["t"],
-                                          W=WORKLOAD["W"], p_vac=WORKLOAD["p_vac"], seed=2),
-                    kite.make_kpm(M, R, 1, kite.FP32), mu)
+    ks = kite.make_system(lattice=0, Lx=args.Lx, Ly=args.Ly, t=WORKLOAD["t"], W=WORKLOAD["W"],
+                          p_vac=WORKLOAD["p_vac"], seed=2)
+    kite.moments_1d(ctx, ks, kite.make_kpm(M, R, 1, kite.FP32), mu)
+    # DOS error of the GPU path on the sample: L1 distance of the Jackson DOS (per orbital
+    # per eV) from the GPU's FP32 moments and from the oracle's FP64 moments
+    lo, hi = kite.bounds(ks)
+    E = np.linspace(lo * 0.999, hi * 0.999, 2001)
+    rho = np.zeros(E.size)
+    kite.reconstruct_dos(ctx, mu, M, M, kite.KERNEL_JACKSON, 0.0, lo, hi, E, E.size, rho)
+    rho_ref = oracle.dos(mu_ref.real.mean(0), E, lo, hi, oracle.kernel_jackson(M))
+    l1 = float(np.sum(np.abs(rho - rho_ref)[:-1] * np.diff(E)))
+    # one core, on a smaller sample of the same lattice
+    M1, R1 = 4, 1
+    t0 = time.perf_counter()
+    oracle.moments_1d(s, M1, R1, threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": n_eff * M * R / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"full {args.Lx}x{args.Ly} lattice, M={M}, R={R}, FP64 oracle (C, OpenMP), "
                       f"{dt:.1f} s wall",
+            "value_1core": n_eff * M1 * R1 / dt1,
+            "sample_1core": f"full {args.Lx}x{args.Ly} lattice, M={M1}, R={R1}, one thread, {dt1:.1f} s wall",
             "max_abs_dmu_gpu_fp32_vs_oracle_on_sample": float(np.max(np.abs(mu - mu_ref.real.mean(0)))),
+            "dos_l1_gpu_fp32_vs_oracle_on_sample": l1,
             "n_eff_match": bool(n_eff == n_eff_gpu)}
 
 
@@ -261,6 +277,36 @@ def secondary_legs(kite, ctx, peaks):
     st = kite.moments_2d(ctx, s4, kite.make_kpm(1024, 4, 1, kite.FP32), mu_nm)
     wall = time.perf_counter() - t0
     tflops = st.gemm_flops / st.gemm_seconds / 1e12
+    # FP64 recursion on the full lattice (fewer moments to bound the time): HBM bytes and
+    # FP64 arithmetic against their measured peaks (FP64: a cuBLAS DGEMM through torch)
+    a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        torch.matmul(a, a)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        torch.matmul(a, a)
+    torch.cuda.synchronize()
+    fp64_tflops = 3 * 2 * 4096.0 ** 3 / (time.perf_counter() - t0) / 1e12
+    del a
+    s2 = kite.make_system(kite.HONEYCOMB, WORKLOAD["Lx"], WORKLOAD["Ly"], WORKLOAD["t"], WORKLOAD["W"], 0.0,
+                          WORKLOAD["p_vac"], 2)
+    mu2 = torch.zeros(256, dtype=torch.float64, device="cuda")
+    kpm2 = kite.make_kpm(256, WORKLOAD["R"], 1, kite.FP64)
+    kite.moments_1d(ctx, s2, kpm2, mu2)  # tunes
+    st = kite.moments_1d(ctx, s2, kpm2, mu2)
+    upd = st.n_eff * 255.0 * WORKLOAD["R"]
+    # per update: the stencil (2 adds, 1 mul, 2 FMA per component) and the moment (2 FMA per
+    # component pair) = 2 * 7 + 8 = 22 FP64 flops
+    gbs = st.step_bytes / st.step_seconds / 1e9
+    tfl = 22.0 * upd / st.step_seconds / 1e12
+    out["large_dos_honeycomb_4096x4096_M256_R8_fp64"] = {
+        "updates_per_s": upd / st.step_seconds, "step_seconds": st.step_seconds,
+        "hbm_gbs": gbs, "hbm_frac": gbs / peaks.get("hbm_gbs", 6800.0), "fp64_tflops": tfl,
+        "fp64_peak_tflops_dgemm": fp64_tflops, "fp64_frac": tfl / fp64_tflops,
+        "bound": "fp64" if tfl / fp64_tflops > gbs / peaks.get("hbm_gbs", 6800.0) else "hbm",
+        "autotuned": {"ring_stages": st.ring_stages, "ctas_per_sm": st.ctas_per_sm,
+                      "steps_per_pass": st.steps_per_pass}}
     out["kubo_bastin_honeycomb_1024x1024_M1024_R4"] = {
         "wall_s": wall, "families_s": st.step_seconds, "contraction_s": st.gemm_seconds,
         "contraction_tflops": tflops, "bf16_peak_tflops": peaks.get("bf16_tflops"),
