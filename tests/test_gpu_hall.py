@@ -125,11 +125,15 @@ def test_quantum_hall_plateau_on_the_device(ctx):
     """Graphene 128 x 128 at 1/8 flux quantum per cell: with E_F in the gap between the
     n = 0 and n = 1 Landau levels (0.26 - 2.44 eV) sigma_xy = -e^2/h per spin
     (-1/(2 pi) e^2/hbar), +e^2/h in the mirror gap below zero, flat across the gap, and
-    sigma_xx vanishes there."""
+    sigma_xx vanishes there; in the gaps near the band edges (1 and 2 of the 16 subbands
+    filled, or 2 and 1 empty) the Chern numbers of the Diophantine equation, -1, -2 and
+    +2, +1 e^2/h."""
     s = kite.make_system(kite.HONEYCOMB, 128, 128, -2.7, 0.0, flux=0.125)
     lo, hi = kite.bounds(s)
     M, R = 256, 4
     E = np.array([-1.8, -1.35, -0.8, 0.8, 1.35, 1.8])
+    edge_E, edge_sigma = np.array([-6.95, -5.9, 5.9, 6.95]), np.array([-1.0, -2.0, 2.0, 1.0])
+    E = np.concatenate([E, edge_E])
     out = {}
     for a, b in ((0, 1), (0, 0)):
         mu = np.zeros((M, M, 2))
@@ -139,8 +143,9 @@ def test_quantum_hall_plateau_on_the_device(ctx):
                                          E, E.size, sig)
         out[(a, b)] = sig * 2 * math.pi
     q = out[(0, 1)]
-    assert np.all(np.abs(q[:3] - 1.0) < 0.03) and np.all(np.abs(q[3:] + 1.0) < 0.03), q
-    assert np.max(np.abs(out[(0, 0)])) < 0.05, out[(0, 0)]
+    assert np.all(np.abs(q[:3] - 1.0) < 0.03) and np.all(np.abs(q[3:6] + 1.0) < 0.03), q
+    assert np.all(np.abs(q[6:] - edge_sigma) < 0.06), q
+    assert np.max(np.abs(out[(0, 0)][:6])) < 0.05, out[(0, 0)]
 
 
 def test_bastin_rejects_bad_arguments(ctx):

@@ -886,8 +886,9 @@ def test_quantum_hall_plateau():
     """Graphene in a field with E_F in the gap above the zero Landau level: the textbook
     Kubo (TKNN) sum on the oracle's dense H~ and field velocities gives sigma_xy = -e^2/h
     per spin (one filled level of the Dirac sequence (2n + 1) e^2/h per spin, valleys
-    summed; 1/(2 pi) in units of e^2/hbar) to 0.5 % on a 16 x 16 torus, and -e^2/h
-    mirrored below it; the Kubo-Bastin reconstruction from the exact-trace moments of an
+    summed; 1/(2 pi) in units of e^2/hbar) to 0.5 % on a 16 x 16 torus, and +e^2/h
+    mirrored below it; every other gap of the spectrum carries the Chern number of the
+    Diophantine equation; the Kubo-Bastin reconstruction from the exact-trace moments of an
     8 x 16 torus converges to that torus's TKNN value as M grows (Jackson kernel, small
     eta), and sigma_xx vanishes in the gap."""
     ucf = oracle.unit_cell_factor(oracle.HONEYCOMB)
@@ -898,6 +899,17 @@ def test_quantum_hall_plateau():
     for E_F, sign in ((1.35, -1.0), (-1.35, 1.0)):   # the gap spans 0.26 - 2.44 eV
         q = tknn_sigma_xy(Hb, vxb, vyb, E_F / dm, ucf) * 2 * math.pi
         assert abs(q - sign) < 5e-3, (E_F, q)
+    # every gap of the flux-1/8 spectrum: with r of the 2q = 16 subbands per cell filled, the
+    # Diophantine equation r = q s + p t (p/q = 1/8, |t| <= q/2) fixes the Chern number t,
+    # and sigma_xy = -t e^2/h per spin (TKNN 1982)
+    lam = np.sort(np.linalg.eigvalsh(Hb))
+    n_cells = 16 * 16
+    for r in (1, 2, 7, 9, 14, 15):
+        k = r * n_cells // 8  # states below the gap: r subbands of n_cells / q states
+        assert lam[k] - lam[k - 1] > 0.05, r  # a gap
+        t_r = next(t for t in range(-4, 5) if (r - t) % 8 == 0)
+        q = tknn_sigma_xy(Hb, vxb, vyb, 0.5 * (lam[k] + lam[k - 1]), ucf) * 2 * math.pi
+        assert abs(q + t_r) < 1e-2, (r, q, t_r)
     sys = oracle.make_system(Lx=8, Ly=16, t=T_EV, flux=0.125)
     n = oracle.norb(sys)
     H, vx, vy = dense_from_operator(sys), dense_v(sys, 0), dense_v(sys, 1)
