@@ -86,9 +86,10 @@ extern "C" {
  *            flux * Ly must be even (honeycomb) or an integer (square);
  *            kite_flux_nearest gives the nearest such flux; with y open any flux
  *            fits.  Accepted by
- *            kite_moments_1d (complex start vectors), kite_moments_2d (the velocity
- *            h~ = [r, H~] carries the same bond phases), kite_spectral_k, kite_ldos and
- *            kite_propagate; the other calls return KITE_ERR_ARG for a nonzero flux.
+ *            kite_moments_1d (complex start vectors), kite_moments_1d_batched (each
+ *            system its own flux), kite_moments_2d (the velocity h~ = [r, H~] carries
+ *            the same bond phases), kite_spectral_k, kite_ldos and kite_propagate;
+ *            kite_moments_1d_static returns KITE_ERR_ARG for a nonzero flux.
  *   open_x, open_y  boundaries along a1, a2 (the configuration's boundaries flag,
  *            Sec. 3d): 0 = periodic, 1 = open (the bonds that would wrap around
  *            the torus are absent: honeycomb A(Lx-1, y) - B(0, y-1) for x, A(x, 0) -
@@ -347,8 +348,10 @@ int kite_inner_products(kite_ctx* ctx, const float* A, const float* B, int M, in
 /* Moments of many independent systems in one persistent, graph-captured launch (the S
  * realisations and the independent samples of Eq. PcomplexityFactor, batched).  Each
  * system i gives mu_i[n] = (1/R) sum_r <r|T_n(H~_i)|r>/N_eff,i for n < M_i, as
- * kite_moments_1d with S = 1.  Systems may differ in size, disorder, seed, bounds and M;
- * they share the lattice kind, R (1..8) and precision (KITE_FP32).  The CTAs of one
+ * kite_moments_1d with S = 1.  Systems may differ in size, disorder, seed, bounds, M and
+ * magnetic flux (a batch with a field in any system runs the Peierls variant of the
+ * stencil, flux 0 as identity rotations); they share the lattice kind, R (1..8),
+ * periodic boundaries and precision (KITE_FP32).  The CTAs of one
  * resident grid are grouped into teams: large systems get several CTAs that meet at a
  * bounded global barrier after each step, small ones share single-CTA teams.  The
  * set-up kernels, the sweep and the reductions are captured in one CUDA graph.

@@ -25,6 +25,7 @@ struct BSys {
   void* bA;
   void* bB;
   const float* vt;
+  const float* phase;  // Peierls phases [Ly][sublattice][2 bonds][cos, sin] (field batches)
   double* partial;  // [max(M,2)][ncta][Q]
   float tt;
   int Lx, Ly, M;
@@ -68,7 +69,10 @@ __device__ __forceinline__ bool team_barrier(unsigned int* ctr, unsigned int tar
 // step 0 writes <r_0|r_0>, <r_0|r_1> into slots 0, 1; step n >= 1 writes <r_n|r_n>,
 // <r_n|r_{n+1}> into slots 2n, 2n+1; k_breduce turns slots into moments.
 // NST: ring depth.  mcap > 0 caps every system's steps (the autotuner's probe launches).
-template <int LAT, int C, bool DBL, int NST>
+// FIELD: a batch with a magnetic field in any system runs the stencil's Peierls variant for
+// all of them (a system without a field has the phase table of flux 0: rotations by
+// (1, 0), which leave every value unchanged).
+template <int LAT, int C, bool DBL, int NST, bool FIELD = false>
 __global__ void __launch_bounds__(kBlock, 3)  // <= 85 registers: three CTAs fit when the stages do
     k_batched(const BSys* __restrict__ systems, const BTeam* __restrict__ teams,
               const int* __restrict__ order, const int* __restrict__ cta_team,
@@ -99,21 +103,21 @@ __global__ void __launch_bounds__(kBlock, 3)  // <= 85 registers: three CTAs fit
     for (int n = 0; n < steps; ++n) {
       bool ok;
       if (n == 0)
-        ok = step_body<float, LAT, C, true, MODE, NST>(ring, rank, T.ncta, nullptr, S.r0, S.bA, S.r0, S.vt,
-                                                  S.tt, S.Lx, S.Ly, S.units,
-                                                  S.partial + (size_t)T.ncta * Q, S.partial, err, 0,
-                                                  nofam);
+        ok = step_body<float, LAT, C, true, MODE, NST, FIELD>(ring, rank, T.ncta, nullptr, S.r0, S.bA, S.r0,
+                                                         S.vt, S.tt, S.Lx, S.Ly, S.units,
+                                                         S.partial + (size_t)T.ncta * Q, S.partial, err, 0,
+                                                         nofam, 0, SeriesOut{}, S.phase);
       else if (DBL)
-        ok = step_body<float, LAT, C, false, MODE, NST>(ring, rank, T.ncta, where(n - 1), where(n),
-                                                   where(n + 1), S.r0, S.vt, S.tt, S.Lx, S.Ly, S.units,
-                                                   S.partial + (size_t)(2 * n + 1) * T.ncta * Q,
-                                                   S.partial + (size_t)(2 * n) * T.ncta * Q, err, 0,
-                                                   nofam);
+        ok = step_body<float, LAT, C, false, MODE, NST, FIELD>(ring, rank, T.ncta, where(n - 1), where(n),
+                                                          where(n + 1), S.r0, S.vt, S.tt, S.Lx, S.Ly, S.units,
+                                                          S.partial + (size_t)(2 * n + 1) * T.ncta * Q,
+                                                          S.partial + (size_t)(2 * n) * T.ncta * Q, err, 0,
+                                                          nofam, 0, SeriesOut{}, S.phase);
       else
-        ok = step_body<float, LAT, C, false, MODE, NST>(ring, rank, T.ncta, where(n - 1), where(n),
-                                                   where(n + 1), S.r0, S.vt, S.tt, S.Lx, S.Ly, S.units,
-                                                   S.partial + (size_t)(n + 1) * T.ncta * Q, nullptr,
-                                                   err, 0, nofam);
+        ok = step_body<float, LAT, C, false, MODE, NST, FIELD>(ring, rank, T.ncta, where(n - 1), where(n),
+                                                          where(n + 1), S.r0, S.vt, S.tt, S.Lx, S.Ly, S.units,
+                                                          S.partial + (size_t)(n + 1) * T.ncta * Q, nullptr,
+                                                          err, 0, nofam, 0, SeriesOut{}, S.phase);
       if (!ok) return;
       // step_body reused the ring's shared memory for its reduction (generic-proxy
       // writes); order them before the next step's bulk copies into the same memory
@@ -214,14 +218,15 @@ struct BPlan {
   Schedule sc;
 };
 
-template <int LAT, int C, bool DBL, int NST>
+template <int LAT, int C, bool DBL, int NST, bool FIELD>
 int batched_occupancy() {
   static int occ = -1;
   if (occ < 0) {
     constexpr int SMEM = StepShape<LAT, C, NST>::template smem_bytes<DBL ? 3 : 0>();
-    cudaFuncSetAttribute(k_batched<LAT, C, DBL, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    cudaFuncSetAttribute(k_batched<LAT, C, DBL, NST, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batched<LAT, C, DBL, NST>, kBlock, SMEM) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batched<LAT, C, DBL, NST, FIELD>, kBlock, SMEM) !=
+        cudaSuccess)
       o = 0;
     occ = o;
   }
@@ -247,7 +252,7 @@ inline Schedule fit_schedule(const std::vector<double>& work, const std::vector<
   return sc;
 }
 
-template <int LAT, int C, bool DBL>
+template <int LAT, int C, bool DBL, bool FIELD>
 cudaError_t launch_batched(kite_ctx* ctx, const BPlan& pl, const BSys* d_sys, const BTeam* d_teams,
                            const int* d_ints, unsigned int* counters, int stall, int mcap) {
   cudaLaunchConfig_t cfg = {};
@@ -262,15 +267,15 @@ cudaError_t launch_batched(kite_ctx* ctx, const BPlan& pl, const BSys* d_sys, co
   const int* cta_team = d_ints + pl.sc.order.size();
   if (pl.nst == 4) {
     cfg.dynamicSmemBytes = StepShape<LAT, C, 4>::template smem_bytes<DBL ? 3 : 0>();
-    return cudaLaunchKernelEx(&cfg, k_batched<LAT, C, DBL, 4>, d_sys, d_teams, d_ints, cta_team, counters,
+    return cudaLaunchKernelEx(&cfg, k_batched<LAT, C, DBL, 4, FIELD>, d_sys, d_teams, d_ints, cta_team, counters,
                               ctx->d_status, stall, mcap);
   }
   cfg.dynamicSmemBytes = StepShape<LAT, C, 8>::template smem_bytes<DBL ? 3 : 0>();
-  return cudaLaunchKernelEx(&cfg, k_batched<LAT, C, DBL, 8>, d_sys, d_teams, d_ints, cta_team, counters,
+  return cudaLaunchKernelEx(&cfg, k_batched<LAT, C, DBL, 8, FIELD>, d_sys, d_teams, d_ints, cta_team, counters,
                             ctx->d_status, stall, mcap);
 }
 
-template <int LAT, int C, bool DBL>
+template <int LAT, int C, bool DBL, bool FIELD>
 int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm* kpm,
                 const std::vector<Scale>& scales, double* const* mu_out, kite_stats* stats) {
   constexpr int SORB = (LAT == KITE_HONEYCOMB) ? 2 : 1;
@@ -289,7 +294,7 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
   }
   // candidate plans: every (ring depth, CTAs per SM) whose grid is resident
   std::vector<BPlan> cands;
-  const int occ8 = batched_occupancy<LAT, C, DBL, 8>(), occ4 = batched_occupancy<LAT, C, DBL, 4>();
+  const int occ8 = batched_occupancy<LAT, C, DBL, 8, FIELD>(), occ4 = batched_occupancy<LAT, C, DBL, 4, FIELD>();
   if (occ8 < 1 && occ4 < 1) return fail(ctx, KITE_ERR_CUDA, "occupancy query for the batched kernel failed");
   const bool tune = autotune_enabled_batched() && count > 1;
   for (int nst : {8, 4}) {
@@ -312,12 +317,16 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
     max_teams = std::max(max_teams, pl.sc.teams.size());
     max_ints = std::max(max_ints, pl.sc.order.size() + pl.sc.cta_team.size());
   }
-  std::vector<size_t> off_vt(count), off_vec(count), off_part(count);
+  std::vector<size_t> off_vt(count), off_vec(count), off_part(count), off_ph(count, 0);
   auto lay = [&](Carver& k, bool record) {
     for (int i = 0; i < count; ++i) {
       const int64_t ncell = (int64_t)sys[i].Lx * sys[i].Ly, N = ncell * SORB;
       const size_t vb = (size_t)ncell * SORB * C * 16;
       char* a = k.take<char>(sizeof(float) * N);
+      if (FIELD) {
+        char* ph = k.take<char>(sizeof(float) * (size_t)sys[i].Ly * SORB * 4);
+        if (record) off_ph[i] = (size_t)ph;
+      }
       char* b = k.take<char>(3 * vb);
       char* c = k.take<char>(sizeof(double) * (size_t)(std::max(kpm[i].M, 2) + 1) * max_ncta[i] * Q);
       if (record) {
@@ -359,6 +368,7 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
     const size_t vb = (size_t)ncell * SORB * C * 16;
     char* vec = reinterpret_cast<char*>(off_vec[i]);
     hs[i].vt = reinterpret_cast<const float*>(off_vt[i]);
+    hs[i].phase = reinterpret_cast<const float*>(off_ph[i]);
     hs[i].r0 = vec;
     hs[i].bA = vec + vb;
     hs[i].bB = vec + 2 * vb;
@@ -372,6 +382,10 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
     mo += (size_t)kpm[i].M;
   }
   KITE_CUDA_TRY(ctx, cudaMemcpyAsync(d_sys, hs.data(), sizeof(BSys) * count, cudaMemcpyHostToDevice, st));
+  for (int i = 0; FIELD && i < count; ++i) {  // phase tables (flux 0: the identity rotations)
+    rc = field_phases(ctx, &sys[i], 0, const_cast<float*>(hs[i].phase));
+    if (rc != KITE_OK) return rc;
+  }
 
   // set-up kernels of every system (on-site draws and start vectors)
   auto setup = [&]() -> cudaError_t {
@@ -412,6 +426,7 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
     while ((double)(1ULL << (b1 + 1)) <= total) ++b1;
     while ((double)(1ULL << (b2 + 1)) <= wmax) ++b2;
     const uint64_t key = ((uint64_t)2 << 56) | ((uint64_t)LAT << 48) | ((uint64_t)C << 40) | ((uint64_t)DBL << 36) |
+                         ((uint64_t)FIELD << 35) |
                          ((uint64_t)std::min(count, 4095) << 20) | ((uint64_t)b1 << 10) | (uint64_t)b2;
     auto it = ctx->tune.find(key);
     bool found = false;
@@ -428,7 +443,7 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
         for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up
           KITE_CUDA_TRY(ctx, cudaMemsetAsync(counters, 0, sizeof(unsigned int) * cands[c].sc.teams.size(), st));
           KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
-          cudaError_t ce = launch_batched<LAT, C, DBL>(ctx, cands[c], d_sys, d_teams, d_ints, counters, 0, mcap);
+          cudaError_t ce = launch_batched<LAT, C, DBL, FIELD>(ctx, cands[c], d_sys, d_teams, d_ints, counters, 0, mcap);
           if (ce != cudaSuccess) return cuda_fail(ctx, ce, "autotune probe launch");
           KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
           KITE_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev3));
@@ -453,7 +468,7 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
   if (ce == cudaSuccess) {
     const int stall = ctx->debug_stall;
     ctx->debug_stall = 0;
-    ce = launch_batched<LAT, C, DBL>(ctx, pl, d_sys, d_teams, d_ints, counters, stall, 0);
+    ce = launch_batched<LAT, C, DBL, FIELD>(ctx, pl, d_sys, d_teams, d_ints, counters, stall, 0);
   }
   for (int i = 0; i < count && ce == cudaSuccess; ++i) {
     const int M = kpm[i].M;
@@ -525,12 +540,16 @@ int moments_1d_batched_impl(kite_ctx* ctx, int count, const kite_system* sys, co
   const int c = (R + 1) / 2;
   const int C = c <= 1 ? 1 : (c <= 2 ? 2 : 4);
   const bool hc = sys[0].lattice == KITE_HONEYCOMB;
-#define KITE_B(LATV, CC)                                                       \
-  (kpm[0].doubling ? run_batched<LATV, CC, true>(ctx, count, sys, kpm, scales, mu, st) \
-                   : run_batched<LATV, CC, false>(ctx, count, sys, kpm, scales, mu, st))
+  bool field = false;
+  for (int i = 0; i < count; ++i) field = field || sys[i].flux != 0.0;
+#define KITE_BF(LATV, CC, DB)                                                                 \
+  (field ? run_batched<LATV, CC, DB, true>(ctx, count, sys, kpm, scales, mu, st)              \
+         : run_batched<LATV, CC, DB, false>(ctx, count, sys, kpm, scales, mu, st))
+#define KITE_B(LATV, CC) (kpm[0].doubling ? KITE_BF(LATV, CC, true) : KITE_BF(LATV, CC, false))
   if (hc) return C == 1 ? KITE_B(KITE_HONEYCOMB, 1) : (C == 2 ? KITE_B(KITE_HONEYCOMB, 2) : KITE_B(KITE_HONEYCOMB, 4));
   return C == 1 ? KITE_B(KITE_SQUARE, 1) : (C == 2 ? KITE_B(KITE_SQUARE, 2) : KITE_B(KITE_SQUARE, 4));
 #undef KITE_B
+#undef KITE_BF
 }
 
 }  // namespace kite

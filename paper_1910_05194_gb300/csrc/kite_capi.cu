@@ -729,7 +729,6 @@ int kite_moments_1d_batched(kite_ctx* ctx, int count, const kite_system* systems
     if (!mu[i]) return fail(ctx, KITE_ERR_ARG, "mu[" + std::to_string(i) + "] is NULL");
     if (systems[i].lattice != systems[0].lattice)
       return fail(ctx, KITE_ERR_ARG, "all systems of a batch must share the lattice kind");
-    if (systems[i].flux != 0.0) return fail(ctx, KITE_ERR_ARG, "the batched sweep takes no magnetic field");
     if (systems[i].open_x || systems[i].open_y)
       return fail(ctx, KITE_ERR_ARG, "the batched sweep takes periodic boundaries only");
     if (k.precision != KITE_FP32) return fail(ctx, KITE_ERR_UNSUPPORTED, "the batched sweep is FP32");

@@ -125,8 +125,6 @@ def test_calls_without_field_support_refuse_a_field(ctx):
     with pytest.raises(kite.KiteError):
         kite.moments_1d(ctx, s, kite.make_kpm(8, 2, 1, kite.FP32, real_vectors=True), np.zeros(8))
     with pytest.raises(kite.KiteError):
-        kite.moments_1d_batched(ctx, [s], [kite.make_kpm(8, 2, 1, kite.FP32)], [np.zeros(8)])
-    with pytest.raises(kite.KiteError):
         kite.moments_1d_static(s, kite.make_kpm(8, 2, 1, kite.FP32), np.zeros(8))
 
 
@@ -150,3 +148,21 @@ def test_wave_packet_evolution_in_a_field(ctx, lattice, Ly, flux, oy, prec, bar)
         ref = oracle.propagate(o, psi0[r], dt, steps, M)
         assert np.max(np.abs(psi[r, :, 0] + 1j * psi[r, :, 1] - ref[-1])) <= bar * max(1.0, np.max(np.abs(ref[-1])))
         assert np.max(np.abs(norms[:, r] - np.sum(np.abs(ref) ** 2, axis=1))) <= (1e-10 if prec == kite.FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("doubling", [False, True])
+def test_batched_sweep_with_fields(ctx, doubling):
+    """One persistent launch over systems with different fluxes (one without a field, whose
+    phases are identity rotations): each against the oracle's plain moments in its field."""
+    specs = [(40, 20, 0.15, 1.0, 11), (24, 10, 0.0, 2.0, 12), (96, 8, 0.5, 0.5, 13), (16, 16, 0.25, 1.5, 14)]
+    pairs = []
+    for Lx, Ly, flux, W, seed in specs:
+        d = dict(lattice=oracle.SQUARE, Lx=Lx, Ly=Ly, t=-1.0, W=W, p_vac=0.02, seed=seed, flux=flux)
+        pairs.append((kite.make_system(**d), oracle.make_system(**d)))
+    M, R = 64, 4
+    mus = [np.zeros(M) for _ in pairs]
+    kite.moments_1d_batched(ctx, [p[0] for p in pairs],
+                            [kite.make_kpm(M, R, 1, kite.FP32, doubling=doubling) for _ in pairs], mus)
+    for (k, o), mu in zip(pairs, mus):
+        ref = oracle.moments_1d(o, M, R).real.mean(0)
+        assert np.max(np.abs(mu - ref)) <= 1e-5
