@@ -268,15 +268,7 @@ def secondary_legs(kite, ctx, peaks):
                      "autotuned": {"ring_stages": st.ring_stages, "ctas_per_sm": st.ctas_per_sm, "steps_per_pass": st.steps_per_pass}}
     res["updates"] = st.updates
     out["batched_256_square_systems_R4_fp32_one_graph_launch"] = res
-    # 2D Kubo-Bastin moments: honeycomb 1024x1024, W = 1, M = 1024, R = 4 (xx)
-    s4 = kite.make_system(kite.HONEYCOMB, 1024, 1024, -2.7, 1.0, 0.0, 0.0, 4)
     import torch
-    mu_nm = torch.zeros((1024, 1024, 2), dtype=torch.float64, device="cuda")
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st = kite.moments_2d(ctx, s4, kite.make_kpm(1024, 4, 1, kite.FP32), mu_nm)
-    wall = time.perf_counter() - t0
-    tflops = st.gemm_flops / st.gemm_seconds / 1e12
     # FP64 recursion on the full lattice (fewer moments to bound the time): HBM bytes and
     # FP64 arithmetic against their measured peaks (FP64: a cuBLAS DGEMM through torch)
     a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
@@ -294,19 +286,28 @@ def secondary_legs(kite, ctx, peaks):
     mu2 = torch.zeros(256, dtype=torch.float64, device="cuda")
     kpm2 = kite.make_kpm(256, WORKLOAD["R"], 1, kite.FP64)
     kite.moments_1d(ctx, s2, kpm2, mu2)  # tunes
-    st = kite.moments_1d(ctx, s2, kpm2, mu2)
-    upd = st.n_eff * 255.0 * WORKLOAD["R"]
+    st64 = kite.moments_1d(ctx, s2, kpm2, mu2)
+    upd = st64.n_eff * 255.0 * WORKLOAD["R"]
     # per update: the stencil (2 adds, 1 mul, 2 FMA per component) and the moment (2 FMA per
     # component pair) = 2 * 7 + 8 = 22 FP64 flops
-    gbs = st.step_bytes / st.step_seconds / 1e9
-    tfl = 22.0 * upd / st.step_seconds / 1e12
+    gbs = st64.step_bytes / st64.step_seconds / 1e9
+    tfl = 22.0 * upd / st64.step_seconds / 1e12
     out["large_dos_honeycomb_4096x4096_M256_R8_fp64"] = {
-        "updates_per_s": upd / st.step_seconds, "step_seconds": st.step_seconds,
+        "updates_per_s": upd / st64.step_seconds, "step_seconds": st64.step_seconds,
         "hbm_gbs": gbs, "hbm_frac": gbs / peaks.get("hbm_gbs", 6800.0), "fp64_tflops": tfl,
         "fp64_peak_tflops_dgemm": fp64_tflops, "fp64_frac": tfl / fp64_tflops,
         "bound": "fp64" if tfl / fp64_tflops > gbs / peaks.get("hbm_gbs", 6800.0) else "hbm",
-        "autotuned": {"ring_stages": st.ring_stages, "ctas_per_sm": st.ctas_per_sm,
-                      "steps_per_pass": st.steps_per_pass}}
+        "autotuned": {"ring_stages": st64.ring_stages, "ctas_per_sm": st64.ctas_per_sm,
+                      "steps_per_pass": st64.steps_per_pass}}
+    # 2D Kubo-Bastin moments: honeycomb 1024x1024, W = 1, M = 1024, R = 4 (xx)
+    s4 = kite.make_system(kite.HONEYCOMB, 1024, 1024, -2.7, 1.0, 0.0, 0.0, 4)
+    import torch
+    mu_nm = torch.zeros((1024, 1024, 2), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = kite.moments_2d(ctx, s4, kite.make_kpm(1024, 4, 1, kite.FP32), mu_nm)
+    wall = time.perf_counter() - t0
+    tflops = st.gemm_flops / st.gemm_seconds / 1e12
     out["kubo_bastin_honeycomb_1024x1024_M1024_R4"] = {
         "wall_s": wall, "families_s": st.step_seconds, "contraction_s": st.gemm_seconds,
         "contraction_tflops": tflops, "bf16_peak_tflops": peaks.get("bf16_tflops"),
