@@ -59,6 +59,12 @@ MUTATIONS = [
      "+ 0.0 * (z / (s1 * s1))[None, :]))", "__init__.py"),
     ("Bastin advanced term on the retarded branch", "for sg in (+1, -1):", "for sg in (+1, +1):",
      "__init__.py"),
+    ("Kubo-Greenwood delta functions without the (2 - d_n0) weight",
+     "w = np.where(np.arange(M) == 0, 1.0, 2.0) * g", "w = np.where(np.arange(M) == 0, 1.0, 1.0) * g", "__init__.py"),
+    ("optical conductivity with the sign of Gamma flipped", "G = -mu * w0[:, None] * w0[None, :]",
+     "G = mu * w0[:, None] * w0[None, :]", "__init__.py"),
+    ("honeycomb unit-cell factor halved", "return 2.0 * 2.0 / np.sqrt(3.0) if lattice == HONEYCOMB else 1.0",
+     "return 2.0 / np.sqrt(3.0) if lattice == HONEYCOMB else 1.0", "__init__.py"),
     ("Bastin Fermi sea from the top of the band", "theta = thF + (np.pi - thF) * 0.5 * (x + 1.0)\n        wq = w *",
      "theta = thF * 0.5 * (x + 1.0)\n        wq = w *", "__init__.py"),
 ]
