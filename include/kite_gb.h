@@ -55,7 +55,7 @@ extern "C" {
 
 /* ---- problem description -------------------------------------------------------- */
 
-/* A periodic tight-binding lattice with disorder (Sec. 3d, Listings 1-3; Sec. 4b).
+/* A tight-binding lattice with disorder, periodic or open (Sec. 3d, Listings 1-3; Sec. 4b).
  * Orbitals are numbered o = 2*(y*Lx + x) + s for the honeycomb lattice (s = 0 for A,
  * 1 for B) and o = y*Lx + x for the square lattice; N = number of orbitals.
  *   lattice  KITE_HONEYCOMB or KITE_SQUARE
