@@ -1078,6 +1078,31 @@ def test_spectral_function_moments_match_bloch_bands():
             assert np.max(np.abs(mu - ref)) < 1e-12, (m1, m2, w)
 
 
+@pytest.mark.parametrize("lattice,flux,oy", [(oracle.HONEYCOMB, 0.25, 0), (oracle.SQUARE, 0.13, 1)])
+def test_wave_packet_propagation_in_a_field_matches_dense_exponential(lattice, flux, oy):
+    """The propagator with the Peierls Hamiltonian (complex H, pinned by the loop traces and
+    the position commutator) against scipy's matrix exponential of the same dense H~, on a
+    torus and on a strip open in y with an incommensurate flux; the norm is conserved."""
+    from scipy.linalg import expm
+    t = -1.0 if lattice == oracle.SQUARE else T_EV
+    s = oracle.make_system(lattice=lattice, Lx=6, Ly=8, t=t, W=1.0, seed=45, flux=flux, open_y=oy)
+    lo, hi = oracle.bounds_auto(s)
+    H = dense_from_operator(s)
+    n = H.shape[0]
+    Hphys = H * 0.5 * (hi - lo) + np.eye(n) * 0.5 * (hi + lo)
+    g = np.random.Generator(np.random.PCG64(6))
+    psi0 = g.standard_normal(n) + 1j * g.standard_normal(n)
+    psi0 /= np.linalg.norm(psi0)
+    dt, steps, M = 0.6, 3, 60
+    out = oracle.propagate(s, psi0, dt, steps, M)
+    U = expm(-1j * Hphys * dt)
+    ref = psi0
+    for k in range(steps):
+        ref = U @ ref
+        assert np.max(np.abs(out[k] - ref)) < 1e-11
+        assert abs(np.linalg.norm(out[k]) - 1.0) < 1e-11
+
+
 def test_wave_packet_propagation_matches_dense_exponential():
     """Time evolution by the Chebyshev series of the wave-packet section against the dense
     matrix exponential exp(-i H t) of a small disordered lattice (hbar = 1, t in hbar/eV),
