@@ -85,7 +85,7 @@ def run_pins_on_copy(tmp_path, old, new, threads=None, target="kite_oracle.c"):
     env = dict(os.environ, PYTHONPATH=str(tmp_path))
     if threads:
         env["OMP_NUM_THREADS"] = str(threads)
-    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                            "-p", "no:randomly", str(tmp_path / "test_oracle_pins.py")],
                           cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
 
