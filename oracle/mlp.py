@@ -130,3 +130,9 @@ def adamw_step(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=1e-4):
     vh = v / (1 - beta2 ** t)
     p = p - lr * (mh / (np.sqrt(vh) + eps) + wd * p)
     return p, m, v
+
+
+def cosine_lr(t, total, lr):
+    """Learning rate of optimiser step t (1-based) of `total` steps: a cosine decay from lr
+    towards zero, lr (1 + cos(pi (t - 1) / total)) / 2."""
+    return lr * 0.5 * (1.0 + np.cos(np.pi * (t - 1) / max(1, total)))

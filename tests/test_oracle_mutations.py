@@ -67,6 +67,11 @@ MUTATIONS = [
      "return 2.0 / np.sqrt(3.0) if lattice == HONEYCOMB else 1.0", "__init__.py"),
     ("Bastin Fermi sea from the top of the band", "theta = thF + (np.pi - thF) * 0.5 * (x + 1.0)\n        wq = w *",
      "theta = thF * 0.5 * (x + 1.0)\n        wq = w *", "__init__.py"),
+    ("Philox Weyl constant off by one", "k1 += 0xBB67AE85u;", "k1 += 0xBB67AE86u;"),
+    ("AdamW bias correction on the first moment only", "vh = v / (1 - beta2 ** t)", "vh = v", "mlp.py"),
+    ("AdamW second moment decayed at the first moment's rate", "v = beta2 * v + (1 - beta2) * g * g",
+     "v = beta1 * v + (1 - beta1) * g * g", "mlp.py"),
+    ("cosine schedule one step late", "np.pi * (t - 1) / max(1, total)", "np.pi * t / max(1, total)", "mlp.py"),
 ]
 
 
@@ -82,6 +87,7 @@ def run_pins_on_copy(tmp_path, old, new, threads=None, target="kite_oracle.c"):
     assert old in src, f"mutation anchor missing: {old}"
     (dst / target).write_text(src.replace(old, new, 1))
     shutil.copy(os.path.join(ROOT, "tests", "test_oracle_pins.py"), tmp_path / "test_oracle_pins.py")
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), tmp_path / "golden")
     env = dict(os.environ, PYTHONPATH=str(tmp_path))
     if threads:
         env["OMP_NUM_THREADS"] = str(threads)

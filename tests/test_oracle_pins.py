@@ -8,6 +8,7 @@ rule.  A dropped term, a wrong sign, a transposed index or an inverted prefactor
 the oracle fails at least one of them.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -76,6 +77,18 @@ def test_philox_white_noise_statistics():
     assert len({tuple(w) for w in words.tolist()}) == len(words)
     # the key changes the stream
     assert oracle.philox([0, 0, 7, 1], [123, 0]) != oracle.philox([0, 0, 7, 1], [124, 0])
+
+
+def test_philox_known_answer_vectors():
+    """The generator's published known-answer vectors (all-zero, all-ones and pi-digit
+    blocks; Salmon et al., SC'11) reproduced word for word: a wrong multiplier, Weyl
+    constant, round count or word order changes every output word."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        w = [int(x, 16) for x in r]
+        assert oracle.philox(w[0:4], w[4:6]) == w[6:10], r
 
 
 def test_disorder_distribution_and_vacancies():
@@ -952,6 +965,66 @@ def test_mlp_adamw_first_step_is_sign_step():
     g = np.array([0.3, -1e-3, 2.0])
     p1, m, v = mlp.adamw_step(p, g, np.zeros(3), np.zeros(3), 1, lr=0.01, wd=0.1, eps=1e-12)
     assert np.allclose(p1, p - 0.01 * (np.sign(g) + 0.1 * p), atol=1e-10)
+
+
+def test_mlp_adamw_constant_gradient_moves_by_lr_every_step():
+    """A constant gradient g with no weight decay: m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2
+    exactly, so both bias corrections recover g and g^2 and every step moves each parameter
+    by lr * sign(g) (up to eps) -- at t = 1, 2, 3, 10 and 100.  Correcting only m, or with
+    the wrong power of b2, leaves a factor sqrt(1 - b2^t) that this catches."""
+    from oracle import mlp
+    g = np.array([0.7, -3e-3, 2.0, -40.0])
+    p = np.array([1.0, -2.0, 0.5, 0.0])
+    m, v = np.zeros(4), np.zeros(4)
+    lr = 0.01
+    for t in range(1, 101):
+        p_new, m, v = mlp.adamw_step(p, g, m, v, t, lr=lr, wd=0.0, eps=1e-14)
+        if t in (1, 2, 3, 10, 100):
+            assert np.allclose(m, (1 - 0.9 ** t) * g, rtol=1e-12)
+            assert np.allclose(v, (1 - 0.999 ** t) * g * g, rtol=1e-12)
+            assert np.allclose(p_new - p, -lr * np.sign(g), rtol=1e-9, atol=0)
+        p = p_new
+
+
+def test_mlp_adamw_two_steps_by_hand():
+    """g = 1 then g = 0 (no weight decay), worked by hand: after step 2 the bias-corrected
+    moments are m^ = b1 (1 - b1) / (1 - b1^2) = b1 / (1 + b1) = 9/19 and
+    v^ = b2 (1 - b2) / (1 - b2^2) = b2 / (1 + b2) = 999/1999, so the second step moves the
+    parameter by lr (9/19) / sqrt(999/1999)."""
+    from oracle import mlp
+    lr = 0.1
+    p1, m, v = mlp.adamw_step(np.array([0.0]), np.array([1.0]), np.zeros(1), np.zeros(1), 1, lr=lr, wd=0.0,
+                              eps=0.0)
+    assert p1[0] == pytest.approx(-lr, rel=1e-15)
+    p2, m, v = mlp.adamw_step(p1, np.array([0.0]), m, v, 2, lr=lr, wd=0.0, eps=0.0)
+    assert m[0] == pytest.approx(0.9 * 0.1, rel=1e-14)
+    assert v[0] == pytest.approx(0.999 * 0.001, rel=1e-14)
+    assert p2[0] - p1[0] == pytest.approx(-lr * (9.0 / 19.0) / math.sqrt(999.0 / 1999.0), rel=1e-12)
+
+
+def test_mlp_adamw_weight_decay_is_decoupled():
+    """With a zero gradient the moments stay zero and only the decoupled decay acts:
+    p -> p (1 - lr wd).  Decay folded into the gradient (L2 regularisation through Adam)
+    would instead move every parameter by lr sign(p)."""
+    from oracle import mlp
+    p = np.array([1.0, -2.0, 0.5])
+    p1, m, v = mlp.adamw_step(p, np.zeros(3), np.zeros(3), np.zeros(3), 1, lr=0.01, wd=0.1)
+    assert np.all(m == 0) and np.all(v == 0)
+    assert np.allclose(p1, p * (1 - 0.01 * 0.1), rtol=1e-15)
+
+
+def test_mlp_cosine_schedule_closed_form():
+    """The learning rate of step t of T (t = 1..T) falls from lr as lr (1 + cos(pi (t-1)/T))/2:
+    lr at t = 1, lr/2 half way (t = T/2 + 1), lr (2 + sqrt2)/4 a quarter of the way, and it
+    decreases strictly towards 0 (reached one step after the last)."""
+    from oracle import mlp
+    T, lr = 40, 3e-3
+    assert mlp.cosine_lr(1, T, lr) == lr
+    assert mlp.cosine_lr(T // 2 + 1, T, lr) == pytest.approx(lr / 2, rel=1e-14)
+    assert mlp.cosine_lr(T // 4 + 1, T, lr) == pytest.approx(lr * (2 + math.sqrt(2)) / 4, rel=1e-14)
+    seq = [mlp.cosine_lr(t, T, lr) for t in range(1, T + 2)]
+    assert all(a > b for a, b in zip(seq, seq[1:]))
+    assert seq[-1] == pytest.approx(0.0, abs=1e-18)
 
 
 def test_bf16_rounding_ties_to_even_and_matches_torch():
