@@ -437,6 +437,92 @@ int kite_learned_gate(kite_ctx* ctx, const float* rho, const double* mu, int mu_
                       int kcheck, double e_min, double e_max, double tol, int* flags,
                       double* deviation);
 
+/* One AdamW step of kite_mlp_train on caller arrays (for checks of the optimiser): with
+ * the learning rate lr_t = lr (1 + cos(pi (t - 1) / total)) / 2 of step t (1-based) of a
+ * cosine schedule over `total` steps and the bias corrections c1 = 1 - 0.9^t,
+ * c2 = 1 - 0.999^t, every element i is updated in place as
+ *   m = 0.9 m + 0.1 g,  v = 0.999 v + 0.001 g^2,
+ *   p = p - lr_t ((m / c1) / (sqrt(v / c2) + 1e-8) + weight_decay p)
+ * in FP32 -- the update kite_mlp_train applies after each batch (decoupled weight decay,
+ * Loshchilov and Hutter).  params, m, v [n] FP32 (updated), grad [n] FP32; all host or
+ * device.  Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
+int kite_mlp_adamw_step(kite_ctx* ctx, float* params, const float* grad, float* m, float* v, int64_t n,
+                        int t, int total, double lr, double weight_decay);
+
+/* ---- learned reconstruction: trained model objects ------------------------------- */
+
+/* A trained learned reconstructor owned by the library: its FP32 parameters, its input
+ * normalisation (per-moment shift and scale, computed on the device from the training
+ * set) and the energy window of its output grid, all in device memory of the GPU it was
+ * trained on.  Created by kite_learned_train or kite_model_import, released by
+ * kite_model_destroy; usable with any context on that GPU. */
+typedef struct kite_model kite_model;
+
+typedef struct {
+  int32_t epochs;        /* passes over the training set (>= 1)                          */
+  int32_t batch;         /* rows per optimiser step (>= 1)                               */
+  double lr;             /* peak learning rate of the cosine schedule (> 0)             */
+  double weight_decay;   /* AdamW decoupled weight decay (>= 0)                          */
+  uint64_t seed;         /* shuffling; and the initial weights when init is NULL         */
+  double e_min, e_max;   /* energy window (eV) of the moments and of the output grid     */
+  const float* init;     /* [P] initial parameters (host or device), or NULL: He-uniform
+                            weights drawn on the device from `seed` (Philox4x32-10,
+                            counter (i_lo, i_hi, 0, 3)), zero biases                      */
+  double head_scale;     /* NULL init only: the last layer's weights scaled by this
+                            (0 = 1); a small value starts the residual network at its prior */
+} kite_learned_cfg;
+
+/* Trains a learned reconstructor on X [n][KITE_MLP_IN] (the first KITE_MLP_IN raw moments
+ * mu_k of each training system, FP32) -> Y [n][KITE_MLP_OUT] (its density of states per eV
+ * on the midpoint grid eps_j = -1 + (2j+1)/KITE_MLP_OUT of [e_min, e_max], from many more
+ * moments).  The inputs are normalised by the training set's per-moment mean and
+ * population standard deviation (floored at 1e-4), computed on the device; the network
+ * learns the residual on the Jackson reconstruction of the same moments (KITE_PRIOR_JACKSON);
+ * training is kite_mlp_train's (mean absolute error, AdamW, cosine schedule).
+ *   X, Y        host or device
+ *   out         receives the new model (NULL on failure)
+ *   loss_curve  [epochs] mean training loss per epoch (host), or NULL
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
+int kite_learned_train(kite_ctx* ctx, const float* X, const float* Y, int n, const kite_learned_cfg* cfg,
+                       kite_model** out, float* loss_curve);
+
+/* Densities of states from moments with the learned reconstructor, gated, with the plain
+ * path as fallback -- in one call:
+ *   1. rho_i = prior + network of the first KITE_MLP_IN moments of row i of mu;
+ *   2. the consistency gate of kite_learned_gate: the first kcheck Chebyshev moments of
+ *      rho_i must match mu_i within gate_tol (max abs difference), else row i falls back;
+ *   3. a fallen-back row is replaced by the plain path's Jackson DOS from M_plain moments
+ *      (Eq. e8a), on the same grid: with `systems` given, kite_moments_1d of systems[i]
+ *      with plain_kpm (its M replaced by M_plain and its window by the model's) followed by
+ *      kite_reconstruct_dos; with systems NULL, kite_reconstruct_dos of the first M_plain
+ *      moments of mu's own row (then M_plain <= mu_ld).
+ *   mu        [n][mu_ld] raw moments (FP64), host or device; mu_ld >= max(KITE_MLP_IN, kcheck),
+ *             computed on the model's window
+ *   gate_tol  >= 0; 0 sends every row whose moments are not reproduced exactly to the
+ *             fallback (a forced fallback)
+ *   systems   [n] (host) or NULL;  plain_kpm  required with systems (R, S, precision)
+ *   rho       [n][KITE_MLP_OUT] FP32 per eV on the model's midpoint grid, host or device
+ *   fell_back [n] 1 where the fallback replaced the prediction, host or device
+ *   deviation [n] the gate's max |m_k - mu_k| per row, host or device, or NULL
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA, KITE_ERR_BOUNDS, KITE_ERR_TIMEOUT. */
+int kite_learned_dos(kite_ctx* ctx, const kite_model* model, const double* mu, int mu_ld, int n,
+                     double gate_tol, int kcheck, int M_plain, const kite_system* systems,
+                     const kite_kpm* plain_kpm, float* rho, int* fell_back, double* deviation);
+
+/* Copies a model's parameters [P], shift [KITE_MLP_IN], scale [KITE_MLP_IN] (each host or
+ * device, or NULL) and window [2] = (e_min, e_max) (host, or NULL) out.
+ * Errors: KITE_ERR_ARG, KITE_ERR_CUDA. */
+int kite_model_export(const kite_model* model, float* params, float* shift, float* scale, double* window);
+
+/* A model from saved parts (as kite_model_export gives them): params [P], shift and scale
+ * [KITE_MLP_IN] (host or device; NULL = 0 and 1), window e_min < e_max.
+ * Errors: KITE_ERR_ARG, KITE_ERR_OOM, KITE_ERR_CUDA. */
+int kite_model_import(kite_ctx* ctx, const float* params, const float* shift, const float* scale, double e_min,
+                      double e_max, kite_model** out);
+
+/* Releases a model (NULL is a no-op). */
+void kite_model_destroy(kite_model* model);
+
 /* ---- 1D moments without allocation (no counterpart in the paper) ------------------ */
 
 /* kite_moments_1d for callers that cannot allocate device memory at the moment they need
@@ -454,7 +540,11 @@ int kite_learned_gate(kite_ctx* ctx, const float* rho, const double* mu, int mu_
  *   err, err_len optional buffer for a one-line reason when the call fails
  * A system whose intermediates do not fit in 32 MiB is rejected with KITE_ERR_ARG and a
  * message giving the size it needs.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * device address (cudaGetSymbolAddress); the CUDA runtime loads the library's device code
+ * lazily, so that first call is also when the 32 MiB are reserved on the device (and the
+ * kernels' code is loaded): make it once at start-up, before the caller's framework
+ * reserves the GPU's memory, and before any stream capture.  The address is looked up
+ * again only if the device's context has been replaced (e.g. after cudaDeviceReset).
  * All calls share the array, which keeps the previous call's contents: each call clears
  * what must start at zero, but calls that overlap on the GPU (other streams or host
  * threads) race on it and must be serialised by the caller.

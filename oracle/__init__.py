@@ -103,6 +103,9 @@ def lib():
             L.orc_velocity.argtypes = [P(System), vp, d, i32, vp, vp]
             L.orc_moments_2d.argtypes = [P(System), i32, i32, i32, d, d, vp, vp, vp, vp, i32, i32, i32]
             L.orc_moments_2d.restype = i32
+            L.orc_moments_2d_panels.argtypes = [P(System), i32, i32, i32, d, d, vp, i32, vp, i32, i32, i32, vp, vp,
+                                                i32]
+            L.orc_moments_2d_panels.restype = i32
             L.orc_chebyshev_sum.argtypes = [P(System), i32, d, d, i32, vp, vp, vp]
             L.orc_chebyshev_sum.restype = i32
             L.orc_kernel_jackson.argtypes = [i32, vp]
@@ -280,6 +283,23 @@ def moments_2d(sys: System, M: int, R: int, realisation: int = 0, e_min=None, e_
     if want_families:
         return out, A[..., 0] + 1j * A[..., 1], B[..., 0] + 1j * B[..., 1]
     return out
+
+
+def moments_2d_panels(sys: System, M: int, R: int, rows, cols, realisation: int = 0, e_min=None, e_max=None,
+                      threads: int = 0, alpha: int = 0, beta: int = 0):
+    """Rows and columns of mu_nm (as moments_2d) without storing the families: returns
+    (P_rows [len(rows)][M], P_cols [M][len(cols)]) complex with P_rows[i][m] = mu_{rows[i], m}
+    and P_cols[n][j] = mu_{n, cols[j]}."""
+    lo, hi = _bounds(sys, e_min, e_max)
+    r = np.ascontiguousarray(rows, np.int32)
+    c = np.ascontiguousarray(cols, np.int32)
+    pr = np.empty((len(r), M, 2), np.float64)
+    pc = np.empty((M, len(c), 2), np.float64)
+    rc = lib().orc_moments_2d_panels(ctypes.byref(sys), int(realisation), int(M), int(R), lo, hi, _ptr(r), len(r),
+                                     _ptr(c), len(c), int(alpha), int(beta), _ptr(pr), _ptr(pc), int(threads))
+    if rc != 0:
+        raise ValueError(f"orc_moments_2d_panels failed ({rc})")
+    return pr[..., 0] + 1j * pr[..., 1], pc[..., 0] + 1j * pc[..., 1]
 
 
 def kernel_jackson(M: int):

@@ -778,6 +778,100 @@ int orc_moments_2d(const orc_system* sys, int realisation, int M, int R, double 
   return 0;
 }
 
+/* Selected rows and columns of the same mu_nm, for lattices whose families do not fit
+ * in memory: rows[i] < M give out_rows[i][m] = mu_{rows[i], m} for every m < M, and
+ * cols[j] < M give out_cols[n][j] = mu_{n, cols[j]} for every n < M.  Per vector, in
+ * three passes of the plain recursion: the a-recursion keeps the a_n of the chosen rows;
+ * the T_m r recursion forms every b_m = h~b T_m r, dots it with the kept a's and keeps the
+ * b_m of the chosen columns; a second a-recursion dots every a_n with the kept b's. */
+int orc_moments_2d_panels(const orc_system* sys, int realisation, int M, int R, double e_min,
+                          double e_max, const int* rows, int nrows, const int* cols, int ncols,
+                          int dir_a, int dir_b, double* out_rows, double* out_cols, int threads) {
+#ifdef _OPENMP
+  if (threads > 0) omp_set_num_threads(threads);
+#else
+  (void)threads;
+#endif
+  if (M < 1 || R < 1 || nrows < 0 || ncols < 0 || !(e_max > e_min)) return -1;
+  for (int i = 0; i < nrows; ++i)
+    if (rows[i] < 0 || rows[i] >= M) return -1;
+  for (int j = 0; j < ncols; ++j)
+    if (cols[j] < 0 || cols[j] >= M) return -1;
+  orc_ham h;
+  if (orc_ham_build(&h, sys, realisation, e_min, e_max)) return -2;
+  int64_t N = h.N;
+  double* r0 = (double*)malloc(sizeof(double) * 2 * N * R);
+  double* keep_a = (double*)malloc(sizeof(double) * 2 * N * (nrows > 0 ? nrows : 1));
+  double* keep_b = (double*)malloc(sizeof(double) * 2 * N * (ncols > 0 ? ncols : 1));
+  double* start = (double*)malloc(sizeof(double) * 2 * N);
+  double* prev = (double*)malloc(sizeof(double) * 2 * N);
+  double* cur = (double*)malloc(sizeof(double) * 2 * N);
+  double* nxt = (double*)malloc(sizeof(double) * 2 * N);
+  double* b = (double*)malloc(sizeof(double) * 2 * N);
+  if (!r0 || !keep_a || !keep_b || !start || !prev || !cur || !nxt || !b) return -2;
+  orc_start_vectors(sys, realisation, R, &h, NULL, r0);
+  memset(out_rows, 0, sizeof(double) * 2 * (int64_t)nrows * M);
+  memset(out_cols, 0, sizeof(double) * 2 * (int64_t)M * ncols);
+  double inv = h.n_eff > 0 ? 1.0 / ((double)h.n_eff * (double)R) : 0.0;
+  for (int r = 0; r < R; ++r) {
+    const double* v0 = r0 + 2 * (int64_t)r * N;
+    for (int pass = 0; pass < 3; ++pass) {
+      /* passes 0 and 2 run T_n (h~a r); pass 1 runs T_m r */
+      if (pass == 1) memcpy(start, v0, sizeof(double) * 2 * N);
+      else orc_apply_v(&h, dir_a, v0, start);
+      memcpy(prev, start, sizeof(double) * 2 * N);
+      for (int n = 0; n < M; ++n) {
+        const double* x; /* T_n start */
+        if (n == 0) {
+          x = prev;
+        } else if (n == 1) {
+          orc_apply_h(&h, prev, cur);
+          x = cur;
+        } else {
+          orc_apply_h(&h, cur, nxt);
+          for (int64_t k = 0; k < 2 * N; ++k) nxt[k] = 2.0 * nxt[k] - prev[k];
+          double* t = prev;
+          prev = cur;
+          cur = nxt;
+          nxt = t;
+          x = cur;
+        }
+        if (pass == 0) {
+          for (int i = 0; i < nrows; ++i)
+            if (rows[i] == n) memcpy(keep_a + 2 * N * (int64_t)i, x, sizeof(double) * 2 * N);
+        } else if (pass == 1) {
+          orc_apply_v(&h, dir_b, x, b); /* b_n = h~b T_n r */
+          for (int i = 0; i < nrows; ++i) {
+            double sr, si;
+            orc_dot(N, keep_a + 2 * N * (int64_t)i, b, &sr, &si);
+            out_rows[2 * ((int64_t)i * M + n)] += sr * inv;
+            out_rows[2 * ((int64_t)i * M + n) + 1] += si * inv;
+          }
+          for (int j = 0; j < ncols; ++j)
+            if (cols[j] == n) memcpy(keep_b + 2 * N * (int64_t)j, b, sizeof(double) * 2 * N);
+        } else {
+          for (int j = 0; j < ncols; ++j) {
+            double sr, si;
+            orc_dot(N, x, keep_b + 2 * N * (int64_t)j, &sr, &si);
+            out_cols[2 * ((int64_t)n * ncols + j)] += sr * inv;
+            out_cols[2 * ((int64_t)n * ncols + j) + 1] += si * inv;
+          }
+        }
+      }
+    }
+  }
+  free(r0);
+  free(keep_a);
+  free(keep_b);
+  free(start);
+  free(prev);
+  free(cur);
+  free(nxt);
+  free(b);
+  orc_ham_free(&h);
+  return 0;
+}
+
 /* ------------------------------------------------------------------------------ */
 /* Reconstruction.                                                                   */
 /* ------------------------------------------------------------------------------ */

@@ -71,6 +71,9 @@ void orc_velocity(const orc_system* sys, const uint8_t* vac, double t_scaled, in
 int orc_moments_2d(const orc_system* sys, int realisation, int M, int R, double e_min,
                    double e_max, const double* r0_in, double* mu_nm, double* a_fam,
                    double* b_fam, int dir_a, int dir_b, int threads);
+int orc_moments_2d_panels(const orc_system* sys, int realisation, int M, int R, double e_min,
+                          double e_max, const int* rows, int nrows, const int* cols, int ncols,
+                          int dir_a, int dir_b, double* out_rows, double* out_cols, int threads);
 
 int orc_chebyshev_sum(const orc_system* sys, int realisation, double e_min, double e_max, int M,
                       const double* coef, const double* in, double* out);

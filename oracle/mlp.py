@@ -90,20 +90,24 @@ def loss(p, X, T, n_in=IN, n_hid=HID, n_out=OUT, act_round=None):
     return float(np.mean(np.abs(Y - np.asarray(T, np.float64))))
 
 
-def grad(p, X, T, n_in=IN, n_hid=HID, n_out=OUT, act_round=None):
+def grad(p, X, T, n_in=IN, n_hid=HID, n_out=OUT, act_round=None, delta_round=None):
     """Analytic gradient of `loss` by the chain rule (sign(0) taken as 0; the activation
-    rounding, if any, is passed through as the identity)."""
+    rounding, if any, is passed through as the identity).  delta_round (or None) is applied
+    to the back-propagated deltas dY, dZ2 and dZ1, modelling the precision in which they are
+    stored between layers; the weight and bias gradients are then exact sums of the stored
+    deltas."""
     W1, b1, W2, b2, W3, b3 = unpack(p, n_in, n_hid, n_out)
     Y, (X, Z1, H1, Z2, H2) = forward(p, X, n_in, n_hid, n_out, act_round)
-    dY = np.sign(Y - np.asarray(T, np.float64)) / Y.size
+    rd = (lambda a: a) if delta_round is None else delta_round
+    dY = rd(np.sign(Y - np.asarray(T, np.float64)) / Y.size)
     dW3 = dY.T @ H2
     db3 = dY.sum(0)
     dH2 = dY @ W3
-    dZ2 = dH2 * (H2 > 0)
+    dZ2 = rd(dH2 * (H2 > 0))
     dW2 = dZ2.T @ H1
     db2 = dZ2.sum(0)
     dH1 = dZ2 @ W2
-    dZ1 = dH1 * (H1 > 0)
+    dZ1 = rd(dH1 * (H1 > 0))
     dW1 = dZ1.T @ X
     db1 = dZ1.sum(0)
     return np.concatenate([g.ravel() for g in (dW1, db1, dW2, db2, dW3, db3)])

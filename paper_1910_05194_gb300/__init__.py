@@ -31,7 +31,8 @@ EXPORTED = ("kite_create", "kite_destroy", "kite_set_stream", "kite_status_strin
             "kite_mlp_param_count", "kite_mlp_train", "kite_mlp_forward", "kite_mlp_gradient",
             "kite_learned_gate", "kite_spectral_k", "kite_ldos", "kite_propagate",
             "kite_evolution_coeffs", "kite_flux_nearest", "kite_reconstruct_sigma_dc",
-            "kite_reconstruct_sigma_dc_bastin")
+            "kite_reconstruct_sigma_dc_bastin", "kite_mlp_adamw_step", "kite_learned_train",
+            "kite_learned_dos", "kite_model_export", "kite_model_import", "kite_model_destroy")
 MLP_IN, MLP_HIDDEN, MLP_OUT = 128, 512, 1024
 
 
@@ -86,6 +87,13 @@ class MLPTrainCfg(ctypes.Structure):
     """``kite_mlp_train_cfg``."""
     _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_double),
                 ("weight_decay", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class LearnedCfg(ctypes.Structure):
+    """``kite_learned_cfg``."""
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_double),
+                ("weight_decay", ctypes.c_double), ("seed", ctypes.c_uint64), ("e_min", ctypes.c_double),
+                ("e_max", ctypes.c_double), ("init", ctypes.c_void_p), ("head_scale", ctypes.c_double)]
 
 
 def make_system(lattice=HONEYCOMB, Lx=64, Ly=64, t=-2.7, W=0.0, delta=0.0, p_vac=0.0, seed=1,
@@ -159,6 +167,18 @@ def lib():
             L.kite_mlp_gradient.restype = i32
             L.kite_learned_gate.argtypes = [vp, vp, vp, i32, i32, i32, d, d, d, vp, vp]
             L.kite_learned_gate.restype = i32
+            L.kite_mlp_adamw_step.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int64, i32, i32, d, d]
+            L.kite_mlp_adamw_step.restype = i32
+            L.kite_learned_train.argtypes = [vp, vp, vp, i32, P(LearnedCfg), P(vp), vp]
+            L.kite_learned_train.restype = i32
+            L.kite_learned_dos.argtypes = [vp, vp, vp, i32, i32, d, i32, i32, vp, P(KPM), vp, vp, vp]
+            L.kite_learned_dos.restype = i32
+            L.kite_model_export.argtypes = [vp, vp, vp, vp, vp]
+            L.kite_model_export.restype = i32
+            L.kite_model_import.argtypes = [vp, vp, vp, vp, d, d, P(vp)]
+            L.kite_model_import.restype = i32
+            L.kite_model_destroy.argtypes = [vp]
+            L.kite_model_destroy.restype = None
             L.kite_moments_2d.argtypes = [vp, P(System), P(KPM), i32, i32, vp, P(Stats)]
             L.kite_moments_2d.restype = i32
             L.kite_reconstruct_green.argtypes = [vp, vp, i32, i32, i32, d, d, d, d, vp, i32, vp, vp]
@@ -434,3 +454,79 @@ def learned_gate(ctx: Context, rho, mu, mu_ld: int, n: int, kcheck: int, e_min: 
     ctx.check(lib().kite_learned_gate(ctx.handle, _addr(rho), _addr(mu), int(mu_ld), int(n), int(kcheck),
                                       float(e_min), float(e_max), float(tol), _addr(flags),
                                       _addr(deviation)))
+
+
+def mlp_adamw_step(ctx: Context, params, grad, m, v, n: int, t: int, total: int, lr: float,
+                   weight_decay: float):
+    """kite_mlp_adamw_step: optimiser step t of `total` (cosine schedule from lr) on FP32
+    params, m, v [n] in place, with the gradient grad [n]."""
+    ctx.check(lib().kite_mlp_adamw_step(ctx.handle, _addr(params), _addr(grad), _addr(m), _addr(v), int(n),
+                                        int(t), int(total), float(lr), float(weight_decay)))
+
+
+class Model:
+    """A ``kite_model``: a trained learned reconstructor owned by the library."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def export(self):
+        """(params [P], shift [IN], scale [IN], (e_min, e_max)) copied out of the model."""
+        import numpy as _np
+        p = _np.zeros(mlp_param_count(), _np.float32)
+        sh = _np.zeros(MLP_IN, _np.float32)
+        sc = _np.zeros(MLP_IN, _np.float32)
+        w = _np.zeros(2)
+        rc = lib().kite_model_export(self._h, _addr(p), _addr(sh), _addr(sc), _addr(w))
+        if rc != OK:
+            raise KiteError(rc, "kite_model_export")
+        return p, sh, sc, (float(w[0]), float(w[1]))
+
+    def close(self):
+        if self._h:
+            lib().kite_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def learned_train(ctx: Context, X, Y, n: int, e_min: float, e_max: float, epochs=200, batch=256, lr=1e-3,
+                  weight_decay=1e-4, seed=0, init=None, head_scale=0.0, loss_curve=None) -> Model:
+    """kite_learned_train: a model trained on X [n][IN] -> Y [n][OUT] (density per eV on the
+    midpoint grid of [e_min, e_max]); init = initial parameters or None (drawn on the device)."""
+    cfg = LearnedCfg(int(epochs), int(batch), float(lr), float(weight_decay), int(seed), float(e_min),
+                     float(e_max), _addr(init), float(head_scale))
+    h = ctypes.c_void_p()
+    ctx.check(lib().kite_learned_train(ctx.handle, _addr(X), _addr(Y), int(n), ctypes.byref(cfg), ctypes.byref(h),
+                                       _addr(loss_curve)))
+    return Model(h)
+
+
+def model_import(ctx: Context, params, e_min: float, e_max: float, shift=None, scale=None) -> Model:
+    """kite_model_import: a model from saved parameters, normalisation and window."""
+    h = ctypes.c_void_p()
+    ctx.check(lib().kite_model_import(ctx.handle, _addr(params), _addr(shift), _addr(scale), float(e_min),
+                                      float(e_max), ctypes.byref(h)))
+    return Model(h)
+
+
+def learned_dos(ctx: Context, model: Model, mu, mu_ld: int, n: int, gate_tol: float, kcheck: int, M_plain: int,
+                rho, fell_back, deviation=None, systems=None, plain_kpm: KPM = None):
+    """kite_learned_dos: network + consistency gate + plain fallback in one call.
+    mu [n][mu_ld] FP64; rho [n][OUT] FP32; fell_back [n] int32; systems: sequence of System
+    (the fallback reruns their moments with plain_kpm at M_plain) or None (the fallback uses
+    mu's own first M_plain moments)."""
+    sa = None
+    if systems is not None:
+        sa = (System * len(systems))(*systems)
+    ctx.check(lib().kite_learned_dos(ctx.handle, model.handle, _addr(mu), int(mu_ld), int(n), float(gate_tol),
+                                     int(kcheck), int(M_plain), sa, ctypes.byref(plain_kpm) if plain_kpm else None,
+                                     _addr(rho), _addr(fell_back), _addr(deviation)))

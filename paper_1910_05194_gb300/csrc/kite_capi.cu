@@ -241,47 +241,6 @@ int resolve_bounds(kite_ctx* ctx, const kite_system* sys, double e_min, double e
   return KITE_OK;
 }
 
-// Device views of caller buffers: device pointers pass through; host buffers are staged
-// in one stream-ordered allocation released at the end of the call.
-struct Staging {
-  kite_ctx* ctx;
-  std::vector<void*> owned;
-  ~Staging() {
-    for (void* p : owned) cudaFreeAsync(p, ctx->stream);
-  }
-  template <typename T>
-  int in(const T* src, size_t count, const T** out) {
-    if (!src || is_device_ptr(src)) {
-      *out = src;
-      return KITE_OK;
-    }
-    void* d = nullptr;
-    KITE_CUDA_TRY(ctx, cudaMallocAsync(&d, sizeof(T) * std::max<size_t>(count, 1), ctx->stream));
-    owned.push_back(d);
-    KITE_CUDA_TRY(ctx, copy_in(ctx, d, src, sizeof(T) * count));
-    *out = static_cast<const T*>(d);
-    return KITE_OK;
-  }
-  template <typename T>
-  int out(T* dst, size_t count, T** dev) {
-    if (!dst || is_device_ptr(dst)) {
-      *dev = dst;
-      return KITE_OK;
-    }
-    void* d = nullptr;
-    KITE_CUDA_TRY(ctx, cudaMallocAsync(&d, sizeof(T) * std::max<size_t>(count, 1), ctx->stream));
-    owned.push_back(d);
-    *dev = static_cast<T*>(d);
-    return KITE_OK;
-  }
-  template <typename T>
-  int back(T* dst, const T* dev, size_t count) {
-    if (!dst || dst == dev) return KITE_OK;
-    KITE_CUDA_TRY(ctx, copy_out(ctx, dst, dev, sizeof(T) * count));
-    return KITE_OK;
-  }
-};
-
 int check_prior(kite_ctx* ctx, const kite_mlp_prior* prior) {
   if (!prior) return KITE_OK;
   if ((prior->kind != KITE_PRIOR_NONE && prior->kind != KITE_PRIOR_JACKSON) || prior->reserved != 0 ||

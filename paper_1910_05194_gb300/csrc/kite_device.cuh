@@ -40,7 +40,7 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
   return r;
 }
 
-enum : uint32_t { kTagDisorder = 1u, kTagPhase = 2u };
+enum : uint32_t { kTagDisorder = 1u, kTagPhase = 2u, kTagInit = 3u };
 
 // 53-bit uniform in [0,1): exact in FP64.
 __device__ __forceinline__ double u53(const Philox4& x) {

@@ -5,8 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <map>
 #include <string>
+#include <vector>
 
 #include "kite_gb.h"
 
@@ -103,6 +105,12 @@ int field_phases(kite_ctx* ctx, const kite_system* sys, int fp64, void* table);
 int field_occupancy(int fp64, int lattice, int C, int doubling);
 int field_sweep(kite_ctx* ctx, FieldSweep* a);
 
+// AdamW step coefficients of the learned reconstructor's training (kite_mlp.cu).
+struct AdamwCoeffs {
+  float lr, c1, c2;
+};
+AdamwCoeffs adamw_coeffs(int t, int total, double lr);
+
 // Rescaling of Eqs. rescalingH/rescalingE.
 struct Scale {
   double e_min, e_max, de_plus, de_minus;
@@ -116,3 +124,56 @@ int resolve_bounds(kite_ctx* ctx, const kite_system* sys, double e_min, double e
     cudaError_t kite_e_ = (expr);                             \
     if (kite_e_ != cudaSuccess) return kite::cuda_fail(ctx, kite_e_, #expr); \
   } while (0)
+
+namespace kite {
+
+// Device views of caller buffers: device pointers pass through; host buffers are staged
+// in one stream-ordered allocation released at the end of the call.
+struct Staging {
+  kite_ctx* ctx;
+  std::vector<void*> owned;
+  ~Staging() {
+    for (void* p : owned) cudaFreeAsync(p, ctx->stream);
+  }
+  template <typename T>
+  int in(const T* src, size_t count, const T** out) {
+    if (!src || is_device_ptr(src)) {
+      *out = src;
+      return KITE_OK;
+    }
+    void* d = nullptr;
+    KITE_CUDA_TRY(ctx, cudaMallocAsync(&d, sizeof(T) * std::max<size_t>(count, 1), ctx->stream));
+    owned.push_back(d);
+    KITE_CUDA_TRY(ctx, copy_in(ctx, d, src, sizeof(T) * count));
+    *out = static_cast<const T*>(d);
+    return KITE_OK;
+  }
+  template <typename T>
+  int out(T* dst, size_t count, T** dev) {
+    if (!dst || is_device_ptr(dst)) {
+      *dev = dst;
+      return KITE_OK;
+    }
+    void* d = nullptr;
+    KITE_CUDA_TRY(ctx, cudaMallocAsync(&d, sizeof(T) * std::max<size_t>(count, 1), ctx->stream));
+    owned.push_back(d);
+    *dev = static_cast<T*>(d);
+    return KITE_OK;
+  }
+  template <typename T>
+  int scratch(size_t count, T** dev) {
+    void* d = nullptr;
+    KITE_CUDA_TRY(ctx, cudaMallocAsync(&d, sizeof(T) * std::max<size_t>(count, 1), ctx->stream));
+    owned.push_back(d);
+    *dev = static_cast<T*>(d);
+    return KITE_OK;
+  }
+  template <typename T>
+  int back(T* dst, const T* dev, size_t count) {
+    if (!dst || dst == dev) return KITE_OK;
+    KITE_CUDA_TRY(ctx, copy_out(ctx, dst, dev, sizeof(T) * count));
+    return KITE_OK;
+  }
+};
+
+}  // namespace kite

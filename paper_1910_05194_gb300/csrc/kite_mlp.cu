@@ -19,12 +19,15 @@
 #include <random>
 #include <vector>
 
+#include "kite_device.cuh"
 #include "kite_internal.h"
 
 namespace kite {
 namespace {
 
 constexpr int IN = KITE_MLP_IN, HID = KITE_MLP_HIDDEN, OUT = KITE_MLP_OUT;
+constexpr double kBeta1 = 0.9, kBeta2 = 0.999;
+constexpr float kAdamEps = 1e-8f;
 constexpr int64_t kOffW1 = 0, kOffB1 = kOffW1 + (int64_t)HID * IN, kOffW2 = kOffB1 + HID,
                   kOffB2 = kOffW2 + (int64_t)HID * HID, kOffW3 = kOffB2 + HID,
                   kOffB3 = kOffW3 + (int64_t)OUT * HID, kParams = kOffB3 + OUT;
@@ -200,20 +203,87 @@ __global__ void k_mlp_colsum(const __nv_bfloat16* __restrict__ D, int M, int N, 
   db[n] = s;
 }
 
-// AdamW (decoupled weight decay) on FP32 master weights; refreshes the BF16 copy
+// AdamW (decoupled weight decay) on FP32 master weights; refreshes the BF16 copy (if any)
+// (1 - b1 and 1 - b2 come from the host, rounded once from FP64: 1 - 0.999f in FP32 would
+// be 1.3e-5 away from 0.001.)
 __global__ void k_mlp_adamw(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, __nv_bfloat16* __restrict__ pb, int64_t n, float lr,
-                            float b1, float b2, float eps, float wd, float c1, float c2) {
+                            float b1, float omb1, float b2, float omb2, float eps, float wd, float c1, float c2) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    const float mi = b1 * m[i] + omb1 * gi;
+    const float vi = b2 * v[i] + omb2 * gi * gi;
     m[i] = mi;
     v[i] = vi;
     const float upd = (mi / c1) / (sqrtf(vi / c2) + eps) + wd * p[i];
     p[i] -= lr * upd;
-    pb[i] = __float2bfloat16(p[i]);
+    if (pb) pb[i] = __float2bfloat16(p[i]);
   }
+}
+
+// Initial parameters drawn on the device: He-uniform weights W ~ U[-lim, lim] with
+// lim = sqrt(6 / fan_in) (times head_scale for the last layer), zero biases.  The uniform
+// u in [0,1) is the 53-bit draw of Philox4x32-10 at counter (i_lo, i_hi, 0, kTagInit),
+// key = seed.
+__global__ void k_mlp_init(float* __restrict__ p, uint64_t seed, float head_scale) {
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < kParams; i += (int64_t)gridDim.x * blockDim.x) {
+    float lim = 0.0f;
+    if (i < kOffB1) lim = sqrtf(6.0f / IN);
+    else if (i >= kOffW2 && i < kOffB2) lim = sqrtf(6.0f / HID);
+    else if (i >= kOffW3 && i < kOffB3) lim = sqrtf(6.0f / HID) * head_scale;
+    if (lim == 0.0f) {
+      p[i] = 0.0f;
+      continue;
+    }
+    const Philox4 x = philox4x32_10((uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0u, kTagInit, k0, k1);
+    p[i] = (float)((2.0 * u53(x) - 1.0) * (double)lim);
+  }
+}
+
+// Per-column statistics of X [n][IN] for the input normalisation: shift = mean,
+// scale = 1 / max(std, floor) with the population standard deviation, FP64 sums in a fixed
+// order (one block per column, a strided partial per thread, then a tree).
+__global__ void __launch_bounds__(256) k_mlp_colstats(const float* __restrict__ X, int n, float sd_floor,
+                                                      float* __restrict__ shift, float* __restrict__ scale) {
+  __shared__ double s1[256], s2[256];
+  const int c = blockIdx.x;
+  double a = 0.0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) a += (double)X[(int64_t)r * IN + c];
+  s1[threadIdx.x] = a;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) s1[threadIdx.x] += s1[threadIdx.x + st];
+    __syncthreads();
+  }
+  const double mean = s1[0] / n;
+  double b = 0.0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const double d = (double)X[(int64_t)r * IN + c] - mean;
+    b += d * d;
+  }
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) s2[threadIdx.x] += s2[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    shift[c] = (float)mean;
+    scale[c] = (float)(1.0 / fmax(sqrt(s2[0] / n), (double)sd_floor));
+  }
+}
+
+// X [n][IN] FP32 = the first IN entries of each row of mu [n][mu_ld] (FP64)
+__global__ void k_mlp_take_inputs(const double* __restrict__ mu, int mu_ld, int n, float* __restrict__ X) {
+  const int64_t total = (int64_t)n * IN;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    X[e] = (float)mu[(e / IN) * mu_ld + e % IN];
+}
+
+// dst [K] FP32 = src [K] FP64 (round to nearest)
+__global__ void k_mlp_narrow(const double* __restrict__ src, int K, float* __restrict__ dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x) dst[i] = (float)src[i];
 }
 
 __global__ void k_mlp_tobf16(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, int64_t n) {
@@ -337,6 +407,28 @@ int carve_net(kite_ctx* ctx, int rows, Net* net, float** extra, size_t extra_flo
 
 int64_t mlp_param_count() { return kParams; }
 
+// Learning rate and bias corrections of optimiser step t (1-based) of `total`: the cosine
+// schedule lr (1 + cos(pi (t - 1) / total)) / 2 and c1 = 1 - b1^t, c2 = 1 - b2^t of AdamW.
+AdamwCoeffs adamw_coeffs(int t, int total, double lr) {
+  AdamwCoeffs c;
+  c.lr = (float)(lr * 0.5 * (1.0 + std::cos(3.141592653589793 * (t - 1) / std::max(1, total))));
+  c.c1 = (float)(1.0 - std::pow(kBeta1, t));
+  c.c2 = (float)(1.0 - std::pow(kBeta2, t));
+  return c;
+}
+
+// One optimiser step on device arrays (the update kite_mlp_train applies after each batch).
+int mlp_adamw_step_impl(kite_ctx* ctx, float* p, const float* g, float* m, float* v, int64_t n, int t, int total,
+                        double lr, double wd) {
+  const AdamwCoeffs c = adamw_coeffs(t, total, lr);
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8);
+  k_mlp_adamw<<<std::max(1, blocks), 256, 0, ctx->stream>>>(p, g, m, v, nullptr, n, c.lr, (float)kBeta1,
+                                                             (float)(1.0 - kBeta1), (float)kBeta2,
+                                                             (float)(1.0 - kBeta2), kAdamEps, (float)wd, c.c1, c.c2);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  return KITE_OK;
+}
+
 // Full-batch gradient of the mean L1 loss (for checks): params, X [n][IN], T [n][OUT] device.
 int mlp_gradient_impl(kite_ctx* ctx, const float* params, const float* X, const float* T, int n,
                       const float* shift, const float* scale, float* grad, double* loss) {
@@ -428,11 +520,10 @@ int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const f
       forward(st, net, p32, rows);
       backward(st, net, rows, lsum, lblocks);
       ++t;
-      // cosine learning-rate schedule
-      const double lr = cfg->lr * 0.5 * (1.0 + std::cos(3.141592653589793 * (t - 1) / std::max(1, total)));
-      const float c1 = (float)(1.0 - std::pow(0.9, t)), c2 = (float)(1.0 - std::pow(0.999, t));
-      k_mlp_adamw<<<1024, 256, 0, st>>>(p32, net.grad, m, v, net.pb, kParams, (float)lr, 0.9f, 0.999f, 1e-8f,
-                                        (float)cfg->weight_decay, c1, c2);
+      const AdamwCoeffs c = adamw_coeffs(t, total, cfg->lr);
+      k_mlp_adamw<<<1024, 256, 0, st>>>(p32, net.grad, m, v, net.pb, kParams, c.lr, (float)kBeta1,
+                                        (float)(1.0 - kBeta1), (float)kBeta2, (float)(1.0 - kBeta2), kAdamEps,
+                                        (float)cfg->weight_decay, c.c1, c.c2);
       KITE_CUDA_TRY(ctx, cudaGetLastError());
       KITE_CUDA_TRY(ctx, cudaMemcpyAsync(ls.data(), lsum, sizeof(double) * lblocks, cudaMemcpyDeviceToHost, st));
       KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));  // d_idx / order reuse
@@ -442,6 +533,31 @@ int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const f
   }
   KITE_CUDA_TRY(ctx, cudaMemcpyAsync(params, p32, sizeof(float) * kParams, cudaMemcpyDefault, st));
   KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  return KITE_OK;
+}
+
+int mlp_init_impl(kite_ctx* ctx, uint64_t seed, double head_scale, float* p) {
+  k_mlp_init<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(p, seed, (float)head_scale);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  return KITE_OK;
+}
+
+int mlp_norm_impl(kite_ctx* ctx, const float* X, int n, double sd_floor, float* shift, float* scale) {
+  k_mlp_colstats<<<IN, 256, 0, ctx->stream>>>(X, n, (float)sd_floor, shift, scale);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  return KITE_OK;
+}
+
+int mlp_take_inputs_impl(kite_ctx* ctx, const double* mu, int mu_ld, int n, float* X) {
+  const int blocks = (int)std::min<int64_t>(((int64_t)n * IN + 255) / 256, (int64_t)ctx->num_sms * 8);
+  k_mlp_take_inputs<<<std::max(1, blocks), 256, 0, ctx->stream>>>(mu, mu_ld, n, X);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  return KITE_OK;
+}
+
+int mlp_narrow_impl(kite_ctx* ctx, const double* src, int K, float* dst) {
+  k_mlp_narrow<<<(K + 255) / 256, 256, 0, ctx->stream>>>(src, K, dst);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
   return KITE_OK;
 }
 

@@ -28,7 +28,13 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mutex;
-void* g_static_ptr[kMaxDevices] = {};  // device address of g_static_scratch, per device
+// device address of g_static_scratch per device, with the id of the context it was taken
+// in (0 when the driver cannot report context ids)
+struct StaticAddr {
+  void* ptr = nullptr;
+  unsigned long long ctx_id = 0;
+};
+StaticAddr g_static_addr[kMaxDevices];
 
 // Error text goes to the caller's buffer (if any) with snprintf: no allocation.
 struct ErrBuf {
@@ -47,21 +53,56 @@ int static_fail(int status, const char* fmt, ...) {
   return status;
 }
 
-// Device address of the scratch array on the current device (first call per device
-// resolves it with cudaGetSymbolAddress; in host code the symbol is only a stand-in).
+// Id of the calling thread's current CUDA context (driver calls cuCtxGetCurrent and
+// cuCtxGetId, looked up through the runtime so the library does not link the driver
+// library); 0 if unavailable.  A new context on a device (after cudaDeviceReset, for
+// example) has a new id, so a cached address is never used across contexts.
+unsigned long long current_ctx_id() {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<GetCurrent>(f1);
+      get_id = reinterpret_cast<GetId>(f2);
+    }
+    cudaGetLastError();
+    looked_up = true;
+  }
+  void* c = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&c) != 0 || !c || get_id(c, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device.  The first call on a device
+// (and the first after that device's context was replaced) resolves it with
+// cudaGetSymbolAddress; in host code the symbol is only a stand-in.  On that first call
+// the runtime loads this library's device code on the device, which reserves the array.
 int static_scratch(int device, void** out) {
   if (device < 0 || device >= kMaxDevices) return static_fail(KITE_ERR_ARG, "device index out of range");
   std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (!g_static_ptr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return static_fail(KITE_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-    }
-    g_static_ptr[device] = p;
+  StaticAddr& a = g_static_addr[device];
+  if (a.ptr && a.ctx_id != 0 && current_ctx_id() == a.ctx_id) {
+    *out = a.ptr;
+    return KITE_OK;
   }
-  *out = g_static_ptr[device];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return static_fail(KITE_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+  }
+  a.ptr = p;
+  a.ctx_id = current_ctx_id();
+  *out = p;
   return KITE_OK;
 }
 

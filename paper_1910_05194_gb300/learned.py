@@ -5,9 +5,10 @@ Chebyshev (kernel polynomial) reconstruction scales as the inverse number of mom
 sharp density of states needs many moments.  This module trains the library's perceptron
 (kite_mlp_train) to map the first 128 moments of a system to the density that the Jackson
 reconstruction reaches with many more (M_hi) moments, as a residual on the Jackson
-reconstruction from the same 128 moments (kite_mlp_prior).  Inference (kite_mlp_forward)
-is followed by the label-free consistency gate (kite_learned_gate); flagged systems fall
-back to the plain path: moments at a high order and the Jackson reconstruction.
+reconstruction from the same 128 moments (kite_learned_train, which also computes the input
+normalisation on the device).  kite_learned_dos then runs the network, the label-free
+consistency gate and, for flagged systems, the plain path (moments at a high order and
+their Jackson reconstruction) in one call.
 
 Every step runs in the library's kernels; this file only marshals arrays between calls.
 
@@ -25,9 +26,8 @@ import time
 
 import numpy as np
 
-from . import (FP32, FP64, HONEYCOMB, KERNEL_JACKSON, MLP_IN, MLP_OUT, Context, jackson_prior,
-               learned_gate, make_kpm, make_system, mlp_forward, mlp_param_count, mlp_train,
-               moments_1d, moments_1d_batched, reconstruct_dos)
+from . import (FP32, FP64, HONEYCOMB, KERNEL_JACKSON, MLP_IN, MLP_OUT, Context, learned_dos, learned_train,
+               make_kpm, make_system, mlp_param_count, moments_1d, moments_1d_batched, reconstruct_dos)
 
 T_HOP = -2.7
 
@@ -86,40 +86,29 @@ def l1_error(rho, ref, e_min: float, e_max: float) -> np.ndarray:
     return np.sum(np.abs(np.asarray(rho, np.float64) - np.asarray(ref, np.float64)), axis=1) * dE
 
 
-def input_norm(X: np.ndarray):
-    """Fixed per-index input normalisation from the training set: (x - mean) / std, with
-    std floored at 1e-4 (mu_0 = 1 for every sample maps to 0).  Returns (shift, scale).
-    Without centring, moments whose mean is far from zero relative to their spread give
-    pre-activations so large that the ReLU units die early in training."""
-    shift = X.mean(0).astype(np.float32)
-    scale = (1.0 / np.maximum(X.std(0), 1e-4)).astype(np.float32)
-    return shift, scale
-
-
-def train(ctx: Context, X, T, e_min: float, e_max: float, params, epochs=200, batch=256, lr=1e-3,
-          weight_decay=1e-4, seed=0):
-    """Trains `params` in place as a residual on the Jackson prior; returns (norm, curve)
-    with norm = (shift, scale) of the inputs."""
-    norm = input_norm(X)
+def train(ctx: Context, X, T, e_min: float, e_max: float, init=None, epochs=200, batch=256, lr=1e-3,
+          weight_decay=1e-4, seed=0, head_scale=0.01):
+    """kite_learned_train: a model trained on X [n][IN] -> T [n][OUT] as a residual on the
+    Jackson prior, with its input normalisation computed on the device; returns
+    (model, loss curve)."""
     curve = np.zeros(epochs, np.float32)
-    mlp_train(ctx, np.ascontiguousarray(X, np.float32), np.ascontiguousarray(T, np.float32), X.shape[0],
-              params, epochs=epochs, batch=batch, lr=lr, weight_decay=weight_decay, seed=seed, shift=norm[0],
-              scale=norm[1], loss_curve=curve, prior=jackson_prior(e_min, e_max))
-    return norm, curve
+    model = learned_train(ctx, np.ascontiguousarray(X, np.float32), np.ascontiguousarray(T, np.float32),
+                          X.shape[0], e_min, e_max, epochs=epochs, batch=batch, lr=lr, weight_decay=weight_decay,
+                          seed=seed, init=init, head_scale=head_scale, loss_curve=curve)
+    return model, curve
 
 
-def infer(ctx: Context, params, norm, mu, e_min: float, e_max: float, kcheck: int = 16,
-          tol: float = 0.02):
-    """Learned densities [n][OUT] (per eV, midpoint grid) from the first MLP_IN moments of
-    each row of mu, with the consistency gate: returns (rho, flags, deviation)."""
-    n = mu.shape[0]
-    X = np.ascontiguousarray(mu[:, :MLP_IN], np.float32)
+def infer(ctx: Context, model, mu, kcheck: int = 16, tol: float = 0.02, M_plain: int = None):
+    """kite_learned_dos on the moment rows mu [n][M]: densities [n][OUT] (per eV, midpoint
+    grid) from the network, gated; flagged rows fall back to the Jackson reconstruction of the
+    row's own first M_plain moments (default: all of them).  tol = inf gives the network
+    alone.  Returns (rho, flags, deviation)."""
+    mu = np.ascontiguousarray(mu, np.float64)
+    n, ld = mu.shape
     rho = np.zeros((n, MLP_OUT), np.float32)
-    mlp_forward(ctx, params, X, n, rho, shift=norm[0], scale=norm[1], prior=jackson_prior(e_min, e_max))
     flags = np.zeros(n, np.int32)
     dev = np.zeros(n)
-    learned_gate(ctx, rho, np.ascontiguousarray(mu, np.float64), mu.shape[1], n, kcheck, e_min, e_max,
-                 tol, flags, dev)
+    learned_dos(ctx, model, mu, ld, n, tol, kcheck, M_plain or ld, rho, flags, dev)
     return rho, flags, dev
 
 
@@ -132,94 +121,111 @@ def plain_dos(ctx: Context, system, M: int, R: int, e_min: float, e_max: float,
     return jackson_dos(ctx, mu[None, :], M, e_min, e_max)[0]
 
 
-def reconstruct(ctx: Context, systems, params, norm, R: int, e_min: float, e_max: float,
-                M_fallback: int, kcheck: int = 16, tol: float = 0.02):
-    """The learned path with fallback: 128 FP32 moments per system in one batched launch
-    (moment doubling), the network, the gate, and the plain FP64 path at M_fallback for
-    flagged systems.
+def reconstruct(ctx: Context, systems, model, R: int, e_min: float, e_max: float, M_fallback: int,
+                kcheck: int = 16, tol: float = 0.02):
+    """The learned path with fallback: MLP_IN FP32 moments per system in one batched launch
+    (moment doubling), then kite_learned_dos (network, gate, and for flagged systems the plain
+    FP64 path at M_fallback: kite_moments_1d + kite_reconstruct_dos).
     Returns (rho [n][OUT], flags)."""
     mu, _ = batched_moments(ctx, systems, MLP_IN, R, e_min, e_max)
-    rho, flags, _ = infer(ctx, params, norm, mu, e_min, e_max, kcheck, tol)
-    for i in np.nonzero(flags)[0]:
-        rho[i] = plain_dos(ctx, systems[i], M_fallback, R, e_min, e_max)
+    n = len(systems)
+    rho = np.zeros((n, MLP_OUT), np.float32)
+    flags = np.zeros(n, np.int32)
+    learned_dos(ctx, model, mu, MLP_IN, n, tol, kcheck, M_fallback, rho, flags, systems=systems,
+                plain_kpm=make_kpm(M_fallback, R, 1, FP64, e_min, e_max))
     return rho, flags
 
 
-def main(argv=None):
+def noise_floor(ctx: Context, systems, M: int, R: int, e_min: float, e_max: float, targets) -> float:
+    """Mean L1 error that the R-vector stochastic estimate carries in the targets themselves:
+    for each system the per-vector moments (kite_moments_1d) are split into two halves of R/2
+    vectors; the Jackson DOS of the two half-averages differ with twice the standard deviation
+    of the R-vector average's error, so half their L1 distance estimates the targets' noise.
+    No function of the input moments can predict that noise."""
+    if R < 2 or R % 2:
+        return float("nan")
+    out = []
+    for i, s in enumerate(systems):
+        mu = np.zeros(M)
+        per = np.zeros((R, M, 2))
+        moments_1d(ctx, s, make_kpm(M, R, 1, FP32, e_min, e_max), mu, per)
+        halves = np.stack([per[:R // 2, :, 0].mean(0), per[R // 2:, :, 0].mean(0)])
+        d = jackson_dos(ctx, halves, M, e_min, e_max)
+        out.append(0.5 * l1_error(d[:1], d[1:], e_min, e_max)[0])
+    return float(np.mean(out))
+
+
+def run(ctx: Context, n_train=20000, n_test=2000, L=256, M_hi=4096, R=4, epochs=200, batch=256, lr=1e-3,
+        chunk=4000, time_sample=200, noise_sample=100, seed=5_000_000):
+    """The whole workflow on seeded synthetic systems: dataset (batched FP32 moments with
+    doubling at M_hi and their Jackson DOS as targets), training (kite_learned_train),
+    held-out L1 of the network against the Jackson reconstruction from the same MLP_IN
+    moments and the targets' own noise floor, the plain order M_plain that reaches the
+    network's held-out L1, the gate, and the wall time of the learned path against the plain
+    FP64 path and the batched FP32 path at M_plain.  Returns a dict of the figures."""
     import synth
 
-    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--n-train", type=int, default=20000)
-    ap.add_argument("--n-test", type=int, default=2000)
-    ap.add_argument("--L", type=int, default=256)
-    ap.add_argument("--M-hi", type=int, default=4096)
-    ap.add_argument("--R", type=int, default=2)
-    ap.add_argument("--epochs", type=int, default=200)
-    ap.add_argument("--batch", type=int, default=256)
-    ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--chunk", type=int, default=4000)
-    ap.add_argument("--time-sample", type=int, default=200, help="held-out systems timed on each path")
-    ap.add_argument("--seed", type=int, default=5_000_000)
-    a = ap.parse_args(argv)
-
-    ctx = Context(0)
     e_min, e_max = window(1.0, 4.0)
-    specs = synth.learned_dos_systems(a.n_train + a.n_test, a.seed, L=a.L)
+    specs = synth.learned_dos_systems(n_train + n_test, seed, L=L)
     systems = to_systems(specs)
     t0 = time.perf_counter()
-    mu, t_mom = batched_moments(ctx, systems, a.M_hi, a.R, e_min, e_max, a.chunk)
-    T = jackson_dos(ctx, mu, a.M_hi, e_min, e_max)
+    mu, t_mom = batched_moments(ctx, systems, M_hi, R, e_min, e_max, chunk)
+    T = jackson_dos(ctx, mu, M_hi, e_min, e_max)
     t_data = time.perf_counter() - t0
-    ntr = a.n_train
+    ntr = n_train
     X = mu[:, :MLP_IN].astype(np.float32)
 
-    params = synth.mlp_init(a.seed + 1, head_scale=0.01)
+    params = synth.mlp_init(seed + 1, head_scale=0.01)
     assert params.size == mlp_param_count()
     t0 = time.perf_counter()
-    norm, curve = train(ctx, X[:ntr], T[:ntr], e_min, e_max, params, epochs=a.epochs, batch=a.batch,
-                        lr=a.lr, seed=a.seed)
+    model, curve = train(ctx, X[:ntr], T[:ntr], e_min, e_max, init=params, epochs=epochs, batch=batch, lr=lr,
+                         seed=seed)
     t_train = time.perf_counter() - t0
 
     test_mu, test_T = mu[ntr:], T[ntr:]
     base = jackson_dos(ctx, test_mu, MLP_IN, e_min, e_max)
-    rho, flags, dev = infer(ctx, params, norm, test_mu, e_min, e_max)
+    rho, _, _ = infer(ctx, model, test_mu, tol=float("inf"))
+    _, flags, dev = infer(ctx, model, test_mu)
     l1_net = l1_error(rho, test_T, e_min, e_max)
     l1_base = l1_error(base, test_T, e_min, e_max)
     # the plain path's order that reaches the network's held-out L1 error
     M_list = [m for m in (128, 160, 192, 256, 320, 384, 448, 512, 640, 768, 1024, 1536, 2048, 3072, 4096)
-              if m <= a.M_hi]
+              if m <= M_hi]
     l1_by_M = {}
     M_plain = None
     for m in M_list:
         l1_by_M[m] = float(np.mean(l1_error(jackson_dos(ctx, test_mu, m, e_min, e_max), test_T, e_min, e_max)))
         if M_plain is None and l1_by_M[m] <= float(np.mean(l1_net)):
             M_plain = m
+    floor = noise_floor(ctx, systems[ntr:ntr + noise_sample], M_hi, R, e_min, e_max, test_T)
     # wall time on a held-out sample: learned path (batched FP32 M=128 + network + gate)
     # against the plain FP64 path at M_plain (and the batched FP32 path at M_plain)
-    ts = systems[ntr:ntr + a.time_sample]
+    ts = systems[ntr:ntr + time_sample]
     res = {}
     if M_plain is not None:
-        reconstruct(ctx, ts[:4], params, norm, a.R, e_min, e_max, M_plain)  # warm-up
+        reconstruct(ctx, ts[:4], model, R, e_min, e_max, M_plain)  # warm-up
         t0 = time.perf_counter()
-        _, fl = reconstruct(ctx, ts, params, norm, a.R, e_min, e_max, M_plain)
+        _, fl = reconstruct(ctx, ts, model, R, e_min, e_max, M_plain)
         res["learned_s"] = time.perf_counter() - t0
         res["learned_flagged"] = int(np.sum(fl))
-        plain_dos(ctx, ts[0], M_plain, a.R, e_min, e_max)  # warm-up
+        plain_dos(ctx, ts[0], M_plain, R, e_min, e_max)  # warm-up
         t0 = time.perf_counter()
         for s in ts:
-            plain_dos(ctx, s, M_plain, a.R, e_min, e_max)
+            plain_dos(ctx, s, M_plain, R, e_min, e_max)
         res["plain_fp64_s"] = time.perf_counter() - t0
         t0 = time.perf_counter()
-        mu_p, _ = batched_moments(ctx, ts, M_plain, a.R, e_min, e_max)
+        mu_p, _ = batched_moments(ctx, ts, M_plain, R, e_min, e_max)
         jackson_dos(ctx, mu_p, M_plain, e_min, e_max)
         res["plain_fp32_batched_doubling_s"] = time.perf_counter() - t0
+    model.close()
     out = {
-        "workload": f"learned_dos_honeycomb_{a.L}x{a.L}_train{a.n_train}_test{a.n_test}_Mhi{a.M_hi}_R{a.R}",
+        "workload": f"learned_dos_honeycomb_{L}x{L}_train{n_train}_test{n_test}_Mhi{M_hi}_R{R}",
         "window_eV": [e_min, e_max],
         "dataset_s": t_data, "dataset_moment_s": t_mom,
-        "dataset_updates": float(len(systems)) * 2 * a.L * a.L * a.M_hi * a.R,
-        "train_s": t_train, "epochs": a.epochs, "loss_first": float(curve[0]), "loss_last": float(curve[-1]),
+        "dataset_updates": float(len(systems)) * 2 * L * L * M_hi * R,
+        "train_s": t_train, "epochs": epochs, "loss_first": float(curve[0]), "loss_last": float(curve[-1]),
         "heldout_l1_network": float(np.mean(l1_net)), "heldout_l1_jackson128": float(np.mean(l1_base)),
+        "heldout_l1_noise_floor": floor, "noise_sample": min(noise_sample, n_test),
         "gain": float(np.mean(l1_base) / np.mean(l1_net)),
         "network_better_fraction": float(np.mean(l1_net < l1_base)),
         "gate_tol": 0.02, "gate_flagged": int(np.sum(flags)), "gate_dev_median": float(np.median(dev)),
@@ -227,6 +233,28 @@ def main(argv=None):
     }
     if "learned_s" in res:
         out["speedup_vs_plain_fp64"] = res["plain_fp64_s"] / res["learned_s"]
+        out["speedup_vs_batched_fp32"] = res["plain_fp32_batched_doubling_s"] / res["learned_s"]
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--n-train", type=int, default=20000)
+    ap.add_argument("--n-test", type=int, default=2000)
+    ap.add_argument("--L", type=int, default=256)
+    ap.add_argument("--M-hi", type=int, default=4096)
+    ap.add_argument("--R", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=200)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--chunk", type=int, default=4000)
+    ap.add_argument("--time-sample", type=int, default=200, help="held-out systems timed on each path")
+    ap.add_argument("--noise-sample", type=int, default=100, help="held-out systems for the noise floor")
+    ap.add_argument("--seed", type=int, default=5_000_000)
+    a = ap.parse_args(argv)
+    ctx = Context(0)
+    out = run(ctx, a.n_train, a.n_test, a.L, a.M_hi, a.R, a.epochs, a.batch, a.lr, a.chunk, a.time_sample,
+              a.noise_sample, a.seed)
     print(json.dumps(out), flush=True)
     ctx.close()
 

@@ -94,3 +94,12 @@ def test_256_system_workload(ctx):
         assert np.max(np.abs(mus_d[i] - mus[i])) <= 2e-5, specs[i]
     for i in cheap:
         assert np.max(np.abs(mus_d[i] - oracle_mu(specs[i]))) <= 1e-5, specs[i]
+    # the largest system of the batch (side 996, M = 4096: a multi-CTA team through 4095
+    # team barriers), every moment against the oracle
+    big = max(range(256), key=lambda i: specs[i]["L"] ** 2 * specs[i]["M"])
+    assert specs[big]["M"] == 4096
+    ref = oracle_mu(specs[big])
+    print(f"largest system {specs[big]}: max |dmu| {np.max(np.abs(mus[big] - ref)):.2e} (plain), "
+          f"{np.max(np.abs(mus_d[big] - ref)):.2e} (doubling)")
+    assert np.max(np.abs(mus[big] - ref)) <= 1e-5
+    assert np.max(np.abs(mus_d[big] - ref)) <= 1e-5

@@ -1057,6 +1057,47 @@ def test_mlp_activation_rounding_moves_only_the_stored_values():
     assert 0 < np.max(np.abs(Y - Yp)) <= 1e-2 * np.max(np.abs(Yp))
 
 
+@pytest.mark.parametrize("alpha,beta", [(0, 0), (0, 1)])
+def test_moments_2d_panels_equal_the_triple_loop(alpha, beta):
+    """The panel routine (rows and columns of mu_nm from the streamed recursion, for
+    lattices whose families do not fit in memory) gives the same numbers as the plain
+    triple loop over stored families, which the exact-diagonalisation and Bloch-velocity
+    pins fix; vacancies, several vectors, rows and columns at both ends."""
+    s = oracle.make_system(lattice=oracle.HONEYCOMB, Lx=11, Ly=9, t=T_EV, W=1.0, p_vac=0.03, seed=5)
+    M = 37
+    full = oracle.moments_2d(s, M, 3, alpha=alpha, beta=beta)
+    rows, cols = [0, 1, 17, 36], [0, 5, 35, 36]
+    pr, pc = oracle.moments_2d_panels(s, M, 3, rows, cols, alpha=alpha, beta=beta)
+    scale = np.max(np.abs(full))
+    assert np.max(np.abs(pr - full[rows, :])) <= 1e-13 * scale
+    assert np.max(np.abs(pc - full[:, cols])) <= 1e-13 * scale
+
+
+def test_mlp_delta_rounding_moves_only_the_stored_deltas():
+    """With delta_round the gradient equals the chain rule written out layer by layer on the
+    rounded deltas (weight gradients = stored deltas times stored activations), and it moves
+    the gradient by no more than the rounding of those deltas."""
+    from oracle import mlp
+    ni, nh, no = 6, 10, 4
+    p = mlp.init_params(7, ni, nh, no) + 0.003
+    g = np.random.Generator(np.random.PCG64(8))
+    X = g.standard_normal((5, ni))
+    T = g.standard_normal((5, no)) * 4.0
+    W1, b1, W2, b2, W3, b3 = mlp.unpack(p, ni, nh, no)
+    r = mlp.round_bf16
+    H1 = r(np.maximum(X @ W1.T + b1, 0))
+    H2 = r(np.maximum(H1 @ W2.T + b2, 0))
+    Y = H2 @ W3.T + b3
+    dY = r(np.sign(Y - T) / Y.size)
+    dZ2 = r((dY @ W3) * (H2 > 0))
+    dZ1 = r((dZ2 @ W2) * (H1 > 0))
+    want = np.concatenate([a.ravel() for a in (dZ1.T @ X, dZ1.sum(0), dZ2.T @ H1, dZ2.sum(0), dY.T @ H2, dY.sum(0))])
+    got = mlp.grad(p, X, T, ni, nh, no, act_round=r, delta_round=r)
+    assert np.array_equal(got, want)
+    plain = mlp.grad(p, X, T, ni, nh, no, act_round=r)
+    assert 0 < np.max(np.abs(got - plain)) <= 1e-2 * np.max(np.abs(plain))
+
+
 def test_mlp_prior_closed_forms():
     """The residual prior (Jackson reconstruction on the midpoint grid): mu = (1, 0, ...)
     gives 1/(pi a sqrt(1 - eps^2)) exactly (g_0 = 1); moments of a point spectrum
