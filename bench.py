@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-doubling", action="store_true")
     p.add_argument("--no-secondary", action="store_true")
+    p.add_argument("--no-learned", action="store_true")
     return p.parse_args()
 
 
@@ -205,24 +206,39 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _median_time(fn, runs=3):
+    ts = []
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        fn()
+        ts.append(time.perf_counter() - t0)
+    return float(np.median(ts))
+
+
 def cpu_baseline_leg(args, kite, ctx, n_eff_gpu):
-    """Oracle timed on the host cores on a bounded sample of the workload, plus the
-    moment error of the GPU path on that same sample."""
+    """The oracle timed on the host cores on a bounded sample of the workload (median of
+    three runs on all cores and on one core), the GPU's error against the oracle on that
+    sample in FP32 and FP64, and the FP32 error at the workload's full order M = 2048 on a
+    lattice the oracle finishes in seconds."""
     import oracle
     cores = os.cpu_count() or 1
     sysd = dict(lattice=0, Lx=args.Lx, Ly=args.Ly, t=WORKLOAD["t"], W=WORKLOAD["W"],
                 p_vac=WORKLOAD["p_vac"], seed=2)
-    M, R = 16, 2
     s = oracle.make_system(**sysd)
-    t0 = time.perf_counter()
-    mu_ref = oracle.moments_1d(s, M, R, threads=cores)
-    dt = time.perf_counter() - t0
     _, vac = oracle.disorder(s)
     n_eff = int((vac == 0).sum())
-    mu = np.zeros(M)
+    M, R = 8, 2
+    res = {}
+    dt = _median_time(lambda: res.__setitem__("mu", oracle.moments_1d(s, M, R, threads=cores)))
+    mu_ref = res["mu"]
+    M1, R1 = 2, 1
+    dt1 = _median_time(lambda: oracle.moments_1d(s, M1, R1, threads=1))
     ks = kite.make_system(lattice=0, Lx=args.Lx, Ly=args.Ly, t=WORKLOAD["t"], W=WORKLOAD["W"],
                           p_vac=WORKLOAD["p_vac"], seed=2)
+    mu = np.zeros(M)
     kite.moments_1d(ctx, ks, kite.make_kpm(M, R, 1, kite.FP32), mu)
+    mu64 = np.zeros(M)
+    kite.moments_1d(ctx, ks, kite.make_kpm(M, R, 1, kite.FP64), mu64)
     # DOS error of the GPU path on the sample: L1 distance of the Jackson DOS (per orbital
     # per eV) from the GPU's FP32 moments and from the oracle's FP64 moments
     lo, hi = kite.bounds(ks)
@@ -231,19 +247,88 @@ def cpu_baseline_leg(args, kite, ctx, n_eff_gpu):
     kite.reconstruct_dos(ctx, mu, M, M, kite.KERNEL_JACKSON, 0.0, lo, hi, E, E.size, rho)
     rho_ref = oracle.dos(mu_ref.real.mean(0), E, lo, hi, oracle.kernel_jackson(M))
     l1 = float(np.sum(np.abs(rho - rho_ref)[:-1] * np.diff(E)))
-    # one core, on a smaller sample of the same lattice
-    M1, R1 = 4, 1
-    t0 = time.perf_counter()
-    oracle.moments_1d(s, M1, R1, threads=1)
-    dt1 = time.perf_counter() - t0
+    # the full order on a 256 x 256 lattice of the same kind (FP32 rounding grows with n)
+    d256 = dict(sysd, Lx=256, Ly=256)
+    M2, R2 = WORKLOAD["M"], WORKLOAD["R"]
+    ref2 = oracle.moments_1d(oracle.make_system(**d256), M2, R2, threads=cores).real.mean(0)
+    mu2 = np.zeros(M2)
+    st2 = kite.moments_1d(ctx, kite.make_system(**d256), kite.make_kpm(M2, R2, 1, kite.FP32), mu2)
     return {"value": n_eff * M * R / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"full {args.Lx}x{args.Ly} lattice, M={M}, R={R}, FP64 oracle (C, OpenMP), "
-                      f"{dt:.1f} s wall",
+                      f"median of 3 runs: {dt:.2f} s",
             "value_1core": n_eff * M1 * R1 / dt1,
-            "sample_1core": f"full {args.Lx}x{args.Ly} lattice, M={M1}, R={R1}, one thread, {dt1:.1f} s wall",
+            "sample_1core": f"full {args.Lx}x{args.Ly} lattice, M={M1}, R={R1}, one thread, median of 3: {dt1:.2f} s",
             "max_abs_dmu_gpu_fp32_vs_oracle_on_sample": float(np.max(np.abs(mu - mu_ref.real.mean(0)))),
+            "max_abs_dmu_gpu_fp64_vs_oracle_on_sample": float(np.max(np.abs(mu64 - mu_ref.real.mean(0)))),
             "dos_l1_gpu_fp32_vs_oracle_on_sample": l1,
+            "fp32_error_at_full_order": {
+                "lattice": "honeycomb 256x256, same W, vacancies and seed", "M": M2, "R": R2,
+                "max_abs_dmu_vs_oracle": float(np.max(np.abs(mu2 - ref2))),
+                "steps_per_pass": st2.steps_per_pass},
             "n_eff_match": bool(n_eff == n_eff_gpu)}
+
+
+def cpu_baselines_per_config(kite, ctx):
+    """The oracle on every other configuration, all host cores and one core (median of
+    three where a run takes seconds), on bounded samples extrapolated linearly in the work
+    (the paper's moment-scaling table shows run time linear in M); each entry says what it
+    ran and which values are extrapolated."""
+    import oracle
+    import synth
+    from paper_1910_05194_gb300 import learned
+    cores = os.cpu_count() or 1
+    out = {}
+    # small FP64 DOS: the whole workload
+    b = (3 * 2.7 + 0.5) * 1.01
+    s1 = oracle.make_system(lattice=0, Lx=64, Ly=64, t=-2.7, W=1.0, seed=1)
+    upd1 = 8192 * 256 * 4
+    t_all = _median_time(lambda: oracle.moments_1d(s1, 256, 4, e_min=-b, e_max=b, threads=cores))
+    t_one = _median_time(lambda: oracle.moments_1d(s1, 256, 4, e_min=-b, e_max=b, threads=1))
+    out["small_dos_honeycomb_64x64_M256_R4_fp64"] = {
+        "seconds_per_call_all_cores": t_all, "seconds_per_call_1core": t_one,
+        "updates_per_s_all_cores": upd1 / t_all, "updates_per_s_1core": upd1 / t_one,
+        "sample": "the whole call (median of 3)"}
+    # batched: three systems of the workload at M = 64, extrapolated to the workload's updates
+    specs = synth.batched_square_systems(256, seed=3)
+    total = float(sum(sp["L"] ** 2 * sp["M"] * 4 for sp in specs))
+    pick = specs[:3]
+    sy = [oracle.make_system(lattice=1, Lx=sp["L"], Ly=sp["L"], t=-1.0, W=sp["W"], seed=sp["seed"]) for sp in pick]
+    upd3 = float(sum(sp["L"] ** 2 * 64 * 4 for sp in pick))
+    t3 = _median_time(lambda: [oracle.moments_1d(x, 64, 4, threads=cores) for x in sy])
+    t3_1 = _median_time(lambda: oracle.moments_1d(sy[0], 16, 4, threads=1), runs=1)
+    rate1 = pick[0]["L"] ** 2 * 16 * 4 / t3_1
+    out["batched_256_square_systems_R4"] = {
+        "updates_per_s_all_cores": upd3 / t3, "updates_per_s_1core": rate1,
+        "workload_updates": total, "extrapolated_workload_s_all_cores": total / (upd3 / t3),
+        "extrapolated_workload_s_1core": total / rate1,
+        "sample": f"systems L={[sp['L'] for sp in pick]} at M=64, R=4 (median of 3); one core: the first at "
+                  "M=16; workload time extrapolated linearly in updates"}
+    # Kubo-Bastin 1024 x 1024, M = 1024: the oracle's 8-row + 8-column panels per vector
+    s4 = oracle.make_system(lattice=0, Lx=1024, Ly=1024, t=-2.7, W=1.0, seed=4)
+    t0 = time.perf_counter()
+    rows = [0, 1, 127, 128, 511, 640, 1000, 1023]
+    cols = [0, 2, 129, 255, 256, 513, 767, 1023]
+    pr, pc = oracle.moments_2d_panels(s4, 1024, 1, rows, cols, threads=cores)
+    t4 = time.perf_counter() - t0
+    full4 = t4 * (1024 / 16) * 4
+    out["kubo_bastin_honeycomb_1024x1024_M1024_R4"] = {
+        "panel_s_all_cores": t4, "panel_sample": "8 rows + 8 columns of mu_nm, M=1024, one vector (one run)",
+        "extrapolated_full_s_all_cores": full4,
+        "extrapolation": "full M x M: the panels' dot products dominate, so M/16 panel runs per vector, 4 vectors; "
+                         "one core: scaled by the all-cores/one-core ratio of the large-DOS samples"}
+    # learned DOS workload: the plain FP64 high-M path per sample (one 256 x 256 system)
+    e_min, e_max = learned.window(1.0, 4.0)
+    sp5 = synth.learned_dos_systems(1, 5_000_000, L=256)[0]
+    s5 = oracle.make_system(lattice=0, Lx=256, Ly=256, t=learned.T_HOP, W=sp5["W"], delta=sp5["delta"],
+                            p_vac=sp5["p_vac"], seed=sp5["seed"])
+    t5 = _median_time(lambda: oracle.moments_1d(s5, 1024, 4, e_min=e_min, e_max=e_max, threads=cores))
+    t5_1 = _median_time(lambda: oracle.moments_1d(s5, 64, 4, e_min=e_min, e_max=e_max, threads=1), runs=1)
+    out["learned_dos_honeycomb_256x256_plain_fp64_per_sample"] = {
+        "seconds_M1024_R4_all_cores": t5, "extrapolated_seconds_M4096_R4_all_cores": 4 * t5,
+        "seconds_M64_R4_1core": t5_1, "extrapolated_seconds_M4096_R4_1core": 64 * t5_1,
+        "sample": "one held-out-distribution system, oracle moments at M=1024 (median of 3) and M=64 on one core, "
+                  "extrapolated linearly in M"}
+    return out, (rows, cols, pr, pc)
 
 
 def secondary_legs(kite, ctx, peaks):
@@ -314,19 +399,53 @@ def secondary_legs(kite, ctx, peaks):
                       "steps_per_pass": st64.steps_per_pass}}
     # 2D Kubo-Bastin moments: honeycomb 1024x1024, W = 1, M = 1024, R = 4 (xx)
     s4 = kite.make_system(kite.HONEYCOMB, 1024, 1024, -2.7, 1.0, 0.0, 0.0, 4)
-    import torch
     mu_nm = torch.zeros((1024, 1024, 2), dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st = kite.moments_2d(ctx, s4, kite.make_kpm(1024, 4, 1, kite.FP32), mu_nm)
     wall = time.perf_counter() - t0
     tflops = st.gemm_flops / st.gemm_seconds / 1e12
+    fam_gbs = st.step_bytes / st.step_seconds / 1e9
+    hbm = peaks.get("hbm_gbs", 6800.0)
     out["kubo_bastin_honeycomb_1024x1024_M1024_R4"] = {
         "wall_s": wall, "families_s": st.step_seconds, "contraction_s": st.gemm_seconds,
+        "families_bytes": st.step_bytes, "families_gbs": fam_gbs, "families_frac_of_hbm": fam_gbs / hbm,
+        "families_bytes_note": "per orbital and step: A step 32 B per vector (r_n-1, r_n, r_n+1, a_n+1 as BF16 hi+lo), "
+                               "B step 40 B per vector (b_n and -i b_n as hi+lo), plus 4 B of on-site term per step",
         "contraction_tflops": tflops, "bf16_peak_tflops": peaks.get("bf16_tflops"),
         "contraction_frac_of_burst": tflops / peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None,
         "contraction_frac_of_sustained": (tflops / peaks["bf16_tflops_sustained"]
                                           if peaks.get("bf16_tflops_sustained") else None)}
+    return out
+
+
+def kubo_bastin_panel_error(kite, ctx, panels):
+    """mu_nm of the full-size Kubo-Bastin workload (one vector) against the oracle's eight
+    rows and eight columns (computed in the CPU baseline): max |error| / max |mu|."""
+    import torch
+    rows, cols, pr, pc = panels
+    s4 = kite.make_system(kite.HONEYCOMB, 1024, 1024, -2.7, 1.0, 0.0, 0.0, 4)
+    mu = torch.zeros((1024, 1024, 2), dtype=torch.float64, device="cuda")
+    kite.moments_2d(ctx, s4, kite.make_kpm(1024, 1, 1, kite.FP32), mu)
+    m = mu.cpu().numpy()
+    m = m[..., 0] + 1j * m[..., 1]
+    scale = float(np.max(np.abs(m)))
+    err = max(float(np.max(np.abs(m[rows, :] - pr))), float(np.max(np.abs(m[:, cols] - pc))))
+    return {"max_abs_err_over_max_mu": err / scale, "rows": rows, "cols": cols, "M": 1024, "R": 1,
+            "oracle": "FP64 plain recursion, each row/column dotted against stored a_n or b_m"}
+
+
+def learned_leg(kite, ctx):
+    """A bounded run of the learned-DOS workload (its sizes in the result): dataset, training
+    on the GPU, held-out L1 of the network against Jackson-128 and the targets' noise floor,
+    the plain order reaching the network's L1, and the wall time of the learned path (FP32
+    moments + network + gate + fallback) against the plain FP64 path and the batched FP32
+    path at that order."""
+    from paper_1910_05194_gb300 import learned
+    t0 = time.perf_counter()
+    out = learned.run(ctx, n_train=2000, n_test=200, L=256, M_hi=4096, R=4, epochs=200, batch=256, lr=1e-3,
+                      chunk=2200, time_sample=200, noise_sample=50)
+    out["leg_wall_s"] = time.perf_counter() - t0
     return out
 
 
@@ -508,8 +627,13 @@ def main():
                "path": "kite_moments_1d(host start vectors, host mu) + kite_reconstruct_dos(host E, host rho)"}
 
     cpu = None
+    panels = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_leg(args, kite, ctx, st.n_eff)
+        cpu["per_config"], panels = cpu_baselines_per_config(kite, ctx)
+        kb = cpu["per_config"]["kubo_bastin_honeycomb_1024x1024_M1024_R4"]
+        one_core_ratio = cpu["value"] / cpu["value_1core"]
+        kb["extrapolated_full_s_1core"] = kb["extrapolated_full_s_all_cores"] * one_core_ratio
     secondary = None
     if rank == 0 and world == 1 and not args.no_secondary:
         try:
@@ -518,6 +642,15 @@ def main():
         except Exception:
             peaks = {}
         secondary = secondary_legs(kite, ctx, peaks)
+        if cpu is not None:
+            secondary["large_dos_honeycomb_4096x4096_M256_R8_fp64"]["max_abs_dmu_vs_oracle_on_sample"] = \
+                cpu["max_abs_dmu_gpu_fp64_vs_oracle_on_sample"]
+            secondary["large_dos_honeycomb_4096x4096_M256_R8_fp64"]["oracle_sample"] = cpu["sample"]
+        if panels is not None:
+            secondary["kubo_bastin_honeycomb_1024x1024_M1024_R4"]["mu_nm_panel_error"] = \
+                kubo_bastin_panel_error(kite, ctx, panels)
+        if not args.no_learned:
+            secondary["learned"] = learned_leg(kite, ctx)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -221,7 +221,7 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
   fa.tvel = tvel_of(alpha);
   fb.tvel = tvel_of(beta);
 
-  double gemm_s = 0.0, rec_s = 0.0;
+  double gemm_s = 0.0, rec_s = 0.0, fam_bytes = 0.0;
   int64_t n_eff = 0;
   for (int s = 0; s < Sreal; ++s) {
     KITE_CUDA_TRY(ctx, cudaMemsetAsync(ne, 0, sizeof(unsigned long long), st));
@@ -292,6 +292,11 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
       cudaEventElapsedTime(&ms_gemm, ctx->ev2, ctx->ev3);
       rec_s += 1e-3 * ms_rec;
       gemm_s += 1e-3 * ms_gemm;
+      // algorithmic bytes of the family steps, per orbital and step: the A step reads
+      // r_{n-1}, r_n and writes r_{n+1} (8 B each per vector) and a_{n+1} as BF16 hi + lo
+      // (8 B per vector); the B step the same three iterates and b_n, -i b_n as hi + lo
+      // (16 B per vector); each step reads the on-site term once (4 B)
+      fam_bytes += (double)(M > 1 ? M - 1 : 0) * (double)N * ((32.0 + 40.0) * nvec + 2 * 4.0);
     }
   }
   int status_host = 0;
@@ -302,6 +307,7 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
     stats->seconds = rec_s + gemm_s;
     stats->step_seconds = rec_s;
     stats->step_launches = (int64_t)Sreal * ((R + VB - 1) / VB) * 2 * (M > 1 ? M - 1 : 0);
+    stats->step_bytes = fam_bytes;
     stats->gemm_seconds = gemm_s;
     // kGemmProducts BF16 products of an M x 2M x Kp real GEMM per vector
     stats->gemm_flops = (double)kGemmProducts * 2.0 * (double)M * (2.0 * M) * (double)Kp * R * Sreal;
