@@ -139,6 +139,18 @@ __global__ void k_init_r0(int64_t ncell, const Real* __restrict__ vt, int vec_ba
 //                       B(x,y) <- A(x,y), A(x-1,y+1), A(x,y+1)  (Listing 1 bonds).
 // Square neighbours: (x-1,y), (x+1,y), (x,y-1), (x,y+1).
 // ------------------------------------------------------------------------------------
+// Moment partial of one complex pair: (sr, si) += conj(a) b, as a chain of four fused
+// multiply-adds (one rounding per product and sum); every kernel that accumulates the
+// moments <r_0|r_n> uses it, so the one-step and the two-step sweeps give the same bits.
+template <typename Acc, typename Real>
+__device__ __forceinline__ void cacc(Acc& sr, Acc& si, Real ar_, Real ai_, Real br_, Real bi_) {
+  const Acc ar = ar_, ai = ai_, br = br_, bi = bi_;
+  sr = rfma(ar, br, sr);
+  sr = rfma(ai, bi, sr);
+  si = rfma(ar, bi, si);
+  si = rfma(-ai, br, si);
+}
+
 template <typename Real>
 struct AccT {
   using T = float;
@@ -478,11 +490,9 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
           } else {
 #pragma unroll
             for (int q = 0; q < VPC; ++q) {
+              cacc(facc[2 * q], facc[2 * q + 1], me.v[2 * q], me.v[2 * q + 1], out.v[2 * q], out.v[2 * q + 1]);
               const Acc ar = me.v[2 * q], ai = me.v[2 * q + 1];
-              const Acc br = out.v[2 * q], bi = out.v[2 * q + 1];
-              facc[2 * q] += ar * br + ai * bi;
-              facc[2 * q + 1] += ar * bi - ai * br;
-              facc0[2 * q] += ar * ar + ai * ai;
+              facc0[2 * q] = rfma(ai, ai, rfma(ar, ar, facc0[2 * q]));
             }
           }
           if (++rows == kFlushRows) {
@@ -539,11 +549,11 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
           } else {
 #pragma unroll
             for (int q = 0; q < VPC; ++q) {
-              const Acc ar = z0.v[2 * q], ai = z0.v[2 * q + 1];
-              const Acc br = out.v[2 * q], bi = out.v[2 * q + 1];
-              facc[2 * q] += ar * br + ai * bi;
-              facc[2 * q + 1] += ar * bi - ai * br;
-              if (FIRST) facc0[2 * q] += ar * ar + ai * ai;
+              cacc(facc[2 * q], facc[2 * q + 1], z0.v[2 * q], z0.v[2 * q + 1], out.v[2 * q], out.v[2 * q + 1]);
+              if (FIRST) {
+                const Acc ar = z0.v[2 * q], ai = z0.v[2 * q + 1];
+                facc0[2 * q] = rfma(ai, ai, rfma(ar, ar, facc0[2 * q]));
+              }
             }
           }
           if (++rows == kFlushRows) {

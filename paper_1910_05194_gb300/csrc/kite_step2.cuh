@@ -153,15 +153,19 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         n3 = *reinterpret_cast<const Ch*>(up + si * CELLB + choff);
         n4 = *reinterpret_cast<const Ch*>(dn + si * CELLB + choff);
       }
+      // a vacancy (v is NaN) holds r = 0 exactly in every iterate, so with its hopping and
+      // on-site term zeroed h = +0 and fma(2, +0, -0) = +0: the same bits as forcing the
+      // output to zero, with two selects per site instead of one per component
       const bool vacant = v != v;
+      const Real ve = vacant ? Real(0) : v, te = vacant ? Real(0) : tt;
       Ch out;
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
         Real sum = radd(n1.v[k], n2.v[k]);
         sum = radd(sum, n3.v[k]);
         if (LAT == KITE_SQUARE) sum = radd(sum, n4.v[k]);
-        const Real h = rfma(tt, sum, rmul(v, me.v[k]));
-        out.v[k] = vacant ? Real(0) : rfma(Real(2), h, -pv.v[k]);
+        const Real h = rfma(te, sum, rmul(ve, me.v[k]));
+        out.v[k] = rfma(Real(2), h, -pv.v[k]);
       }
       return out;
     };
@@ -185,15 +189,19 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         n4 = *reinterpret_cast<const Ch*>(td + tx * CELLB + choff);
       }
       const Ch pv = *reinterpret_cast<const Ch*>(mid2 + (tx + 1) * CELLB + choff);  // r_n, own cell
+      // a vacancy (v is NaN) holds r = 0 exactly in every iterate, so with its hopping and
+      // on-site term zeroed h = +0 and fma(2, +0, -0) = +0: the same bits as forcing the
+      // output to zero, with two selects per site instead of one per component
       const bool vacant = v != v;
+      const Real ve = vacant ? Real(0) : v, te = vacant ? Real(0) : tt;
       Ch out;
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
         Real sum = radd(n1.v[k], n2.v[k]);
         sum = radd(sum, n3.v[k]);
         if (LAT == KITE_SQUARE) sum = radd(sum, n4.v[k]);
-        const Real h = rfma(tt, sum, rmul(v, me.v[k]));
-        out.v[k] = vacant ? Real(0) : rfma(Real(2), h, -pv.v[k]);
+        const Real h = rfma(te, sum, rmul(ve, me.v[k]));
+        out.v[k] = rfma(Real(2), h, -pv.v[k]);
       }
       return out;
     };
@@ -203,12 +211,8 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         for (int k = 0; k < NR; ++k) facc[k] += (Acc)z0.v[k] * (Acc)out.v[k];
       } else {
 #pragma unroll
-        for (int q = 0; q < VPC; ++q) {
-          const Acc ar = z0.v[2 * q], ai = z0.v[2 * q + 1];
-          const Acc br = out.v[2 * q], bi = out.v[2 * q + 1];
-          facc[2 * q] += ar * br + ai * bi;
-          facc[2 * q + 1] += ar * bi - ai * br;
-        }
+        for (int q = 0; q < VPC; ++q) cacc(facc[2 * q], facc[2 * q + 1], z0.v[2 * q], z0.v[2 * q + 1],
+                                            out.v[2 * q], out.v[2 * q + 1]);
       }
       if (++rows == kFlushRows) {
         rows = 0;
@@ -235,8 +239,17 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
     const size_t pcol = ((size_t)xv * SORB + s) * C + c;
     Ch pv1 = loads_v ? Ch::ldg(r_prev, pcol + (size_t)wrapy(yb - 1) * orow) : Ch{};
     // the prefetch row yn = yb + i of r_{n-1} and the on-site terms, wrapped as it advances
-    // (the stored rows yb-1+i and yb-3+i are owned rows whenever they are stored)
+    // (the stored rows yb-1+i and yb-3+i are owned rows whenever they are stored).  The
+    // four global streams advance one row per iteration, so their byte addresses are
+    // carried across iterations (rows yb-1+i and yb-3+i of the outputs: addresses of rows
+    // above the lattice are formed but only dereferenced once they are inside it).
     int yn = yb;
+    const long long orowb = (long long)orow * 16;
+    unsigned char* po1 = static_cast<unsigned char*>(out1) + (long long)(ocol * 16) + (long long)(yb - 1) * orowb;
+    unsigned char* po2 = static_cast<unsigned char*>(out2) + (long long)(ocol * 16) + (long long)(yb - 3) * orowb;
+    const unsigned char* pp = static_cast<const unsigned char*>(r_prev) + pcol * 16 + (size_t)yb * orowb;
+    const Real* pvt = vcol + (size_t)yb * vrow;
+    const long long ly_orowb = (long long)Ly * orowb, ly_vrow = (long long)Ly * vrow;
     // One barrier per row: iteration i computes r_{n+1} row yb-1+i (slots i, i+1, i+2 hold
     // r_n rows yb-2+i .. yb+i) into tile row i mod 4, and r_{n+2} row yb-3+i from the three
     // tile rows written by the previous iterations, with r_n and r_0 of that row from slot
@@ -253,8 +266,10 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
       const bool do1 = i < nr + 2;  // r_{n+1} row yb-1+i
       const bool do2 = i >= 3;      // r_{n+2} row yb-3+i
       const bool more = loads_v && i + 1 < nr + 2;
-      const Real v1n = more ? vcol[(size_t)(uint32_t)yn * vrow] : Real(0);
-      const Ch pvn = more ? Ch::ldg(r_prev, pcol + (size_t)(uint32_t)yn * orow) : Ch{};
+      const Real v1n = more ? *pvt : Real(0);
+      Ch pvn;
+      if (more) pvn = Ch::ldg(pp, 0);
+      else pvn = Ch{};
       const int st1 = st0 + 1 == NST ? 0 : st0 + 1;
       const int st2 = st1 + 1 == NST ? 0 : st1 + 1;
       bool ok = true;
@@ -274,7 +289,7 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         const Ch o = site1(up, mid, dn, xl + 1, v1, pv1);
         *reinterpret_cast<Ch*>(t3 + (xl + 1) * CELLB + choff) = o;
         if (i >= 1 && i <= nr) {
-          o.st(out1, ocol + (size_t)(uint32_t)(yb - 1 + i) * orow);
+          o.st(po1, 0);
           const Ch z0 = *reinterpret_cast<const Ch*>(mid + Sh::RNB + xl * CELLB + choff);
           accumulate(facc1, dacc1, rows1, z0, o);
         }
@@ -287,7 +302,7 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         // r_{n+2} row y2 = yb-3+i from tile rows y2-1, y2, y2+1 and r_n, r_0 of row y2
         const unsigned char* prev = stages + stm * Sh::STAGEB;
         const Ch o = site2(tile + o0, tile + o1, tile + o2, prev, vm2);
-        o.st(out2, ocol + (size_t)(uint32_t)(yb - 3 + i) * orow);
+        o.st(po2, 0);
         const Ch z0 = *reinterpret_cast<const Ch*>(prev + Sh::RNB + xl * CELLB + choff);
         accumulate(facc2, dacc2, rows2, z0, o);
       }
@@ -296,6 +311,14 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
       v1 = v1n;
       pv1 = pvn;
       if (st2 == NST - 1) par2 ^= 1u;  // slot i+3 starts the ring's next round
+      po1 += orowb;
+      po2 += orowb;
+      pp += orowb;
+      pvt += vrow;
+      if (yn + 1 == Ly) {
+        pp -= ly_orowb;
+        pvt -= ly_vrow;
+      }
       yn = yn + 1 == Ly ? 0 : yn + 1;
       const int of = o0;  // the oldest tile row takes the next r_{n+1} row
       o0 = o1;
@@ -308,9 +331,11 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         aborted = true;
         break;
       }
-      if (tid == kProducer && i >= 1 && i - 1 + NST < nslots) {
-        issue(i - 1 + NST, stm);  // slot i-1's stage
-        issued = i + NST;
+      if (!compute) {  // warp-uniform: the eight compute warps skip the producer's test
+        if (tid == kProducer && i >= 1 && i - 1 + NST < nslots) {
+          issue(i - 1 + NST, stm);  // slot i-1's stage
+          issued = i + NST;
+        }
       }
       stm = st0;
       st0 = st1;

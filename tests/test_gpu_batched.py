@@ -81,8 +81,10 @@ def test_256_system_workload(ctx):
     print(f"256 systems: {st.updates:.3e} updates in {st.seconds:.3f} s = "
           f"{st.updates / st.seconds:.3e} updates/s, grid {st.grid}")
     for sp, mu in zip(specs, mus):
+        # |mu_n| <= 1 in exact arithmetic (|T_n| <= 1 on the rescaled spectrum, unit-norm
+        # vectors); the FP32 partial sums round at ~1e-7, hence the same 1e-6 as for mu_0
         assert abs(mu[0] - 1.0) <= 1e-6
-        assert np.all(np.abs(mu) <= 1.0)
+        assert np.all(np.abs(mu) <= 1.0 + 1e-6)
     # the systems the CPU oracle finishes quickly: every moment
     cheap = sorted(range(256), key=lambda i: specs[i]["L"] ** 2 * specs[i]["M"])[:6]
     for i in cheap:
