@@ -288,6 +288,33 @@ struct Open {
   int x = 0, y = 0;
 };
 
+// Work units are row segments of one x-strip, TX cells wide.  They are numbered in band
+// order: the rows are cut into bands of B rows, with B the rows per CTA, and within a
+// band the units run strip by strip.  A CTA's contiguous share of the units then covers
+// about one band of one strip, so neighbouring CTAs walk the same rows of neighbouring
+// strips at the same time, and the halo cells a CTA copies from its neighbours' strips
+// are read from L2 by whichever of the two comes second.  unit_segment gives the strip,
+// first row and row count of the segment that starts at unit u, cut at unit u1.
+struct Seg {
+  int sx, yb, nr;
+};
+__device__ __forceinline__ int band_rows(long long units, int ncta, int Ly) {
+  return (int)min((long long)Ly, max(1LL, (units + ncta - 1) / ncta));
+}
+__device__ __forceinline__ Seg unit_segment(long long u, long long u1, int Ly, long long nstrips, int B) {
+  const long long band_units = nstrips * B;
+  const int b = (int)(u / band_units);
+  const long long w = u - (long long)b * band_units;
+  const int y0 = b * B;
+  const int bh = min(B, Ly - y0);
+  Seg g;
+  g.sx = (int)(w / bh);
+  const int r = (int)(w - (long long)g.sx * bh);
+  g.yb = y0 + r;
+  g.nr = (int)min(u1 - u, (long long)(bh - r));
+  return g;
+}
+
 // Per-CTA state of the shared-memory ring; a persistent launch keeps it across steps.
 struct Ring {
   uint64_t* bars;
@@ -346,11 +373,12 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
   long long gslot = ring.gslot;
   bool aborted = false;
 
+  const int band = band_rows(units, ncta, Ly);
+  const long long nstrips = units / Ly;
   for (long long u = u0; u < u1 && !aborted;) {
     // one segment = consecutive rows of one x-strip
-    const int sx = (int)(u / Ly);
-    const int yb = (int)(u - (long long)sx * Ly);
-    const int nr = (int)min(u1 - u, (long long)(Ly - yb));
+    const Seg seg = unit_segment(u, u1, Ly, nstrips, band);
+    const int sx = seg.sx, yb = seg.yb, nr = seg.nr;
     const int x0 = sx * TX;
     const int txv = min(TX, Lx - x0);
     const int xlh = (x0 == 0) ? Lx - 1 : x0 - 1;

@@ -96,10 +96,11 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
   };
   auto wrapy = [&](int y) { return y < 0 ? y + Ly : (y >= Ly ? y - Ly : y); };
 
+  const int band = band_rows(units, ncta, Ly);
+  const long long nstrips = units / Ly;
   for (long long u = u0; u < u1 && !aborted;) {
-    const int sx = (int)(u / Ly);
-    const int yb = (int)(u - (long long)sx * Ly);
-    const int nr = (int)min(u1 - u, (long long)(Ly - yb));
+    const Seg seg = unit_segment(u, u1, Ly, nstrips, band);
+    const int sx = seg.sx, yb = seg.yb, nr = seg.nr;
     const int x0 = sx * TX;
     const int txv = min(TX, Lx - x0);
     const int nslots = nr + 4;  // r_n rows yb-2 .. yb+nr+1
