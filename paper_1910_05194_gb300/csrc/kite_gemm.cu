@@ -24,18 +24,37 @@
 namespace kite {
 namespace {
 
+#ifndef KITE_GEMM_BN
+#define KITE_GEMM_BN 256
+#endif
+#ifndef KITE_GEMM_STAGES
+#define KITE_GEMM_STAGES 4
+#endif
+// 32-column stages (64-byte swizzle) in a four-deep ring measured faster than 64-column
+// stages in a two-deep one: the same 192 KB in flight, refilled at half the granularity
+#ifndef KITE_GEMM_BK
+#define KITE_GEMM_BK 32
+#endif
 constexpr int kBM = 128;                       // rows of A per tile (UMMA M)
-constexpr int kBN = 256;                       // rows of B per tile (UMMA N)
-constexpr int kBK = 64;                        // K per stage = one 128-byte swizzle row
+constexpr int kBN = KITE_GEMM_BN;              // rows of B per tile (UMMA N)
+constexpr int kKB = 64;                        // K columns per block of the K-blocked families
+constexpr int kBK = KITE_GEMM_BK;              // K per stage: one 128-byte (64) or 64-byte (32) swizzle row
+constexpr int kSub = kKB / kBK;                // stages per family K block
 constexpr int kUK = 16;                        // K per tcgen05.mma of kind::f16
-constexpr int kGStages = 2;
-constexpr int kATile = kBM * kBK * 2;          // 16 KB
-constexpr int kBTile = kBN * kBK * 2;          // 32 KB
+static_assert(kBK == 64 || kBK == 32, "stage K must be 64 or 32");
+constexpr int kGStages = KITE_GEMM_STAGES;
+constexpr int kATile = kBM * kBK * 2;          // 8 KB at kBK = 32
+constexpr int kBTile = kBN * kBK * 2;          // 16 KB
 constexpr int kStageBytes = 2 * kATile + 2 * kBTile;   // A hi, A lo, B hi, B lo
-constexpr int kEpiWarps = 8;                   // two per TMEM lane quarter, 128 columns each
+#ifndef KITE_GEMM_EPI_WARPS
+#define KITE_GEMM_EPI_WARPS 8
+#endif
+constexpr int kEpiWarps = KITE_GEMM_EPI_WARPS;  // 4 or 8: one or two per TMEM lane quarter
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
 constexpr int kAccCols = kBN;                  // FP32 accumulator columns per buffer
 constexpr int kTmemCols = 2 * kAccCols;        // double-buffered accumulator
+constexpr int kHalfCols = kAccCols * 4 / kEpiWarps;  // columns of one epilogue warp
+static_assert(kHalfCols % 32 == 0, "epilogue works on 32-column blocks");
 constexpr int kEpiPitch = 33;                  // floats per transposed row (bank-conflict free)
 constexpr int kEpiBytes = kEpiWarps * 32 * kEpiPitch * 4;
 constexpr int kGemmSmem = 1024 + kGStages * kStageBytes + kEpiBytes + 256;
@@ -50,22 +69,26 @@ constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
 // swizzle: start address >> 4 (bits 0-13), leading byte offset (unused with swizzle,
 // 16 B), stride byte offset = 1024 B between 8-row groups (bits 32-45), descriptor
 // version 1 (bit 46), swizzle mode 2 = 128 B (bits 61-63).
+// With a 64-byte swizzle (32-column stages) the 8-row groups are 512 B apart and the
+// swizzle mode is 4.
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)(16u >> 4) << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)((8u * kBK * 2u) >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)(kBK == 64 ? 2 : 4) << 61;
   return d;
 }
 
-// One box of a K-blocked family: 64 columns (x = 0) of rows [y, y + box) in K block z.
+// One box of a K-blocked family: kBK columns of rows [y, y + box) at stage block kb (family
+// K block kb / kSub, columns (kb % kSub) * kBK: a multiple of 32 bf16, 64 bytes).
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint64_t* bar,
-                                            int y, int z) {
+                                            int y, int kb) {
+  const int z = kb / kSub, x = (kb - z * kSub) * kBK;
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"((uint64_t)map), "r"(0), "r"(y), "r"(z), "r"(smem_u32(bar))
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -293,8 +316,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int q = warp & 3;                           // TMEM lane quarter this warp may access
     const int half = (warp - 2) / 4;                  // which 128 of the 256 columns
     float* tile = epi + (warp - 2) * 32 * kEpiPitch;
-    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * (kAccCols / 2));
-    float d2[4][32];
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * kHalfCols);
+    constexpr int kBlk = kHalfCols / 32;
+    float d2[kBlk][32];
     int acc = 0;
     uint32_t aph = 0;
     bool ok = true;
@@ -307,7 +331,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       bool first = true;
       int nsub = 0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < kBlk; ++j)
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) d2[j][jj] = 0.f;
       for (int kc = kb0; kc < kb1; kc += a.sub_kb) {
@@ -317,7 +341,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
         tc_fence_after();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 2 * kBlk; ++j) {
           uint32_t r[16];
           tmem_ld_32x16(lane_base + (uint32_t)(acc * kAccCols + j * 16), r);
 #pragma unroll
@@ -330,16 +354,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         // flush d2 into the FP64 partials: transpose 32 rows x 32 columns through shared
         // memory so that a warp's FP64 loads and stores run along a row
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < kBlk; ++j) {
 #pragma unroll
           for (int jj = 0; jj < 32; ++jj) tile[lane * kEpiPitch + jj] = d2[j][jj];
           __syncwarp();
-          const int col = tn * kBN + half * (kAccCols / 2) + j * 32 + lane;
+          const int col = tn * kBN + half * kHalfCols + j * 32 + lane;
           const bool colok = col < a.Nrows;
           double* p = pbase + col;
 #pragma unroll
           for (int jj = 0; jj < 32; ++jj) d2[j][jj] = 0.f;
-#pragma unroll
+#pragma unroll 1  // unrolled, the 32 rows' addresses stay live and the epilogue spills
           for (int h = 0; h < 32; h += 8) {
             double old[8];  // 8 loads in flight before any use
 #pragma unroll
@@ -448,12 +472,13 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode(kite_ctx* ctx) {
 int make_map(kite_ctx* ctx, CUtensorMap* m, const void* ptr, int64_t Kp, int rows, int box_rows) {
   auto enc = get_encode(ctx);
   if (!enc) return fail(ctx, KITE_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
-  cuuint64_t dims[3] = {(cuuint64_t)kBK, (cuuint64_t)rows, (cuuint64_t)(Kp / kBK)};
-  cuuint64_t strides[2] = {(cuuint64_t)kBK * 2, (cuuint64_t)rows * kBK * 2};
+  cuuint64_t dims[3] = {(cuuint64_t)kKB, (cuuint64_t)rows, (cuuint64_t)(Kp / kKB)};
+  cuuint64_t strides[2] = {(cuuint64_t)kKB * 2, (cuuint64_t)rows * kKB * 2};
   cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   kBK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
     return fail(ctx, KITE_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
@@ -469,7 +494,7 @@ int make_map(kite_ctx* ctx, CUtensorMap* m, const void* ptr, int64_t Kp, int row
 int plan_gemm_splits(kite_ctx* ctx, int Mrows, int Nrows, int64_t Kp) {
   const int TM = (Mrows + kBM - 1) / kBM, TN = (Nrows + kBN - 1) / kBN;
   const int T = TM * TN;
-  const int kb_total = (int)(Kp / kBK);
+  const int kb_total = (int)(Kp / kKB);
   // splits so that items fill whole waves of the persistent grid, at least 2 K blocks each
   int best = 1;
   for (int s = 1; s <= std::max(1, kb_total / 2); ++s) {
@@ -483,7 +508,7 @@ int plan_gemm_splits(kite_ctx* ctx, int Mrows, int Nrows, int64_t Kp) {
 int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void* Bhi,
                     const void* Blo, int Mrows, int Nrows, int64_t Kp, int S, int sub_kb,
                     int fold, int nprod, double* part, int* S_used) {
-  if (Kp % kBK != 0) return fail(ctx, KITE_ERR_ARG, "K must be padded to a multiple of 64");
+  if (Kp % kKB != 0) return fail(ctx, KITE_ERR_ARG, "K must be padded to a multiple of 64");
   CUtensorMap mAh, mAl, mBh, mBl;
   int rc;
   if ((rc = make_map(ctx, &mAh, Ahi, Kp, Mrows, kBM)) != KITE_OK) return rc;
@@ -493,13 +518,16 @@ int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void*
   GemmArgs a;
   a.TN = (Nrows + kBN - 1) / kBN;
   a.T = ((Mrows + kBM - 1) / kBM) * a.TN;
-  a.kb_total = (int)(Kp / kBK);
-  a.S = std::max(1, std::min(S, a.kb_total));
-  a.kb_per_item = (a.kb_total + a.S - 1) / a.S;
-  a.S = (a.kb_total + a.kb_per_item - 1) / a.kb_per_item;  // every split has >= 1 K block
+  // splits and sub-chunks are planned in family K blocks (64 columns) and run in stages
+  const int kb64 = (int)(Kp / kKB);
+  a.S = std::max(1, std::min(S, kb64));
+  const int per64 = (kb64 + a.S - 1) / a.S;
+  a.S = (kb64 + per64 - 1) / per64;  // every split has >= 1 K block
+  a.kb_total = kb64 * kSub;
+  a.kb_per_item = per64 * kSub;
   a.items = a.S * a.T;
   *S_used = a.S;  // the reduction must sum exactly the splits written here
-  a.sub_kb = std::max(1, sub_kb);
+  a.sub_kb = std::max(1, sub_kb) * kSub;
   a.fold = std::max(1, fold);
   a.nprod = nprod == 3 ? 3 : 4;
   a.Mrows = Mrows;
@@ -532,7 +560,7 @@ int reduce_cplx(kite_ctx* ctx, const double* part, int S, int M, int M2, double 
 // FP32 (device), C [M][M2] complex FP64 (device).
 int inner_products_impl(kite_ctx* ctx, const float* A, const float* B, int M, int M2, int64_t N,
                         double scale, double* C, int sub_kb, int fold, int nprod) {
-  const int64_t Kp = ((2 * N + kBK - 1) / kBK) * kBK;
+  const int64_t Kp = ((2 * N + kKB - 1) / kKB) * kKB;
   const int Nrows = 2 * M2;
   const int S = plan_gemm_splits(ctx, M, Nrows, Kp);
   const size_t a_bytes = (size_t)M * Kp * 2, b_bytes = (size_t)Nrows * Kp * 2;

@@ -298,8 +298,16 @@ struct Open {
 struct Seg {
   int sx, yb, nr;
 };
+// Band order pays off for long shares (measured on GB300 with 456 CTAs: 647 and 1150 rows
+// per CTA, 1-3 % faster per pass); for shares of up to ~300 rows the plain strip-major
+// order (bands of Ly rows) was 2-6 % faster, so band order starts at 512 rows per CTA.
+#ifndef KITE_BAND_MIN_ROWS
+#define KITE_BAND_MIN_ROWS 512
+#endif
 __device__ __forceinline__ int band_rows(long long units, int ncta, int Ly) {
-  return (int)min((long long)Ly, max(1LL, (units + ncta - 1) / ncta));
+  const long long per = max(1LL, (units + ncta - 1) / ncta);
+  if (per < KITE_BAND_MIN_ROWS) return Ly;  // short shares: strip-major order
+  return (int)min((long long)Ly, per);
 }
 __device__ __forceinline__ Seg unit_segment(long long u, long long u1, int Ly, long long nstrips, int B) {
   const long long band_units = nstrips * B;
