@@ -11,16 +11,18 @@
 // Parameter layout (one flat FP32 vector): W1[H][IN], b1[H], W2[H][H], b2[H], W3[OUT][H],
 // b3[OUT], row-major.
 #include <cuda_bf16.h>
-#include <mma.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <mutex>
 #include <numeric>
 #include <random>
 #include <vector>
 
 #include "kite_device.cuh"
 #include "kite_internal.h"
+#include "kite_tc.cuh"
 
 namespace kite {
 namespace {
@@ -33,10 +35,15 @@ constexpr int64_t kOffW1 = 0, kOffB1 = kOffW1 + (int64_t)HID * IN, kOffW2 = kOff
                   kOffB3 = kOffW3 + (int64_t)OUT * HID, kParams = kOffB3 + OUT;
 
 // ------------------------------------------------------------------------------------
-// GEMM on the tensor cores (BF16 in, FP32 accumulate): C[m][n] = sum_k A(m,k) B(k,n)
-//   A(m,k) = transA ? A[k*lda + m] : A[m*lda + k];  B(k,n) = transB ? B[n*ldb + k] : B[k*ldb + n]
-// Epilogue: + bias[n]; relu; mask by mask[m][n] > 0; store FP32 (C32) and/or BF16 (C16).
-// 64x64 CTA tile, 4 warps of 32x32 (2x2 WMMA 16x16x16 fragments), K step 32 via smem.
+// GEMM on the 5th-generation tensor cores, BF16 in, FP32 accumulate in TMEM:
+//   C[m][n] = sum_k A[m][k] B[n][k]   (A [M][lda], B [N][ldb], both K contiguous)
+// Epilogue: alpha * C + bias[n] + add[m][n]; relu; zero where mask[m][n] <= 0; store FP32
+// (C32) and/or BF16 (C16) with leading dimension ldc.  One 128 x 128 output tile per CTA:
+// warp 0 issues the TMA loads (128-byte swizzle, 64-column K blocks, zero fill outside
+// the matrices) into a four-stage ring, warp 1 allocates 128 TMEM columns and one lane
+// issues tcgen05.mma (M = N = 128, K = 16), warps 2-5 read the accumulator back
+// (tcgen05.ld, one TMEM lane quarter each) and apply the epilogue.  The backward pass
+// turns its transposed products into this form with explicit transposes (k_mlp_transpose).
 // ------------------------------------------------------------------------------------
 struct GemmEpi {
   const float* bias;
@@ -49,66 +56,150 @@ struct GemmEpi {
   float alpha;
 };
 
-__global__ void __launch_bounds__(128) k_mlp_gemm(const __nv_bfloat16* __restrict__ A, int lda, int transA,
-                                                  const __nv_bfloat16* __restrict__ B, int ldb, int transB,
-                                                  int M, int N, int K, const GemmEpi ep) {
-  using namespace nvcuda;
-  constexpr int BM = 64, BN = 64, BK = 32, PA = BK + 8, PB = BN + 8, PC = BN + 4;
-  __shared__ __align__(32) __nv_bfloat16 As[BM][PA];
-  __shared__ __align__(32) __nv_bfloat16 Bs[BK][PB];
-  __shared__ __align__(32) float Cs[BM][PC];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[2][2];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) wmma::fill_fragment(acc[i][j], 0.0f);
-  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-  for (int k0 = 0; k0 < K; k0 += BK) {
-    for (int e = tid; e < BM * BK; e += 128) {
-      const int r = transA ? e % BM : e / BK, c = transA ? e / BM : e % BK;
-      const int gm = m0 + r, gk = k0 + c;
-      As[r][c] = (gm < M && gk < K) ? (transA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk]) : zero;
+constexpr int kTM = 128, kTN = 128, kTK = 64, kTStages = 4;
+constexpr int kTATile = kTM * kTK * 2, kTBTile = kTN * kTK * 2;  // 16 KB each
+constexpr int kTStage = kTATile + kTBTile;
+constexpr int kTThreads = 64 + 128;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kTSmem = 1024 + kTStages * kTStage + 256;
+constexpr int kTPitch = kTN + 1;  // floats per row of the epilogue's staging tile (conflict-free)
+static_assert(kTM * kTPitch * 4 <= kTStages * kTStage, "the epilogue tile reuses the operand stages");
+constexpr uint32_t kTIdesc = idesc_bf16_f32(kTM, kTN);
+
+__global__ void __launch_bounds__(kTThreads, 1)
+    k_mlp_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, int M, int N, int K,
+             const GemmEpi ep, int* __restrict__ err) {
+  extern __shared__ unsigned char tsmem_raw[];
+  const uint32_t raw = smem_u32(tsmem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // 128-byte swizzle atoms repeat every 1024 B
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tsmem_raw + (base - raw) + kTStages * kTStage);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kTStages;
+  uint64_t* tfull = bars + 2 * kTStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kTStages + 1);
+  __shared__ int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tn = blockIdx.x, tm = blockIdx.y;
+  const int nk = (K + kTK - 1) / kTK;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kTStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
     }
-    for (int e = tid; e < BK * BN; e += 128) {
-      const int r = transB ? e % BK : e / BN, c = transB ? e / BK : e % BN;
-      const int gk = k0 + r, gn = n0 + c;
-      Bs[r][c] = (gk < K && gn < N) ? (transB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn]) : zero;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; kk += 16) {
-      wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, wmma::row_major> fa[2];
-      wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, wmma::row_major> fb[2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) wmma::load_matrix_sync(fa[i], &As[wm + 16 * i][kk], PA);
-#pragma unroll
-      for (int j = 0; j < 2; ++j) wmma::load_matrix_sync(fb[j], &Bs[kk][wn + 16 * j], PB);
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
-    }
-    __syncthreads();
+    mbar_init(tfull, 1);
+    mbar_fence_init();
+    s_abort = 0;
   }
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-      wmma::store_matrix_sync(&Cs[wm + 16 * i][wn + 16 * j], acc[i][j], PC, wmma::mem_row_major);
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
   __syncthreads();
-  for (int e = tid; e < BM * BN; e += 128) {
-    const int r = e / BN, c = e % BN, gm = m0 + r, gn = n0 + c;
-    if (gm >= M || gn >= N) continue;
-    float v = ep.alpha * Cs[r][c];
-    if (ep.bias) v += ep.bias[gn];
-    if (ep.add) v += ep.add[(int64_t)gm * ep.ldc + gn];
-    if (ep.relu) v = fmaxf(v, 0.0f);
-    if (ep.mask && !(__bfloat162float(ep.mask[(int64_t)gm * ep.ldc + gn]) > 0.0f)) v = 0.0f;
-    if (ep.C32) ep.C32[(int64_t)gm * ep.ldc + gn] = v;
-    if (ep.C16) ep.C16[(int64_t)gm * ep.ldc + gn] = __float2bfloat16(v);
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      int pend[kTStages];
+      for (int i = 0; i < kTStages; ++i) pend[i] = -1;
+      bool ok = true;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int st = kb % kTStages;
+        const uint32_t ph = (uint32_t)((kb / kTStages) & 1);
+        if (!wait_or_abort(&empty[st], ph ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(&full[st], kTStage);
+        const uint32_t sb = base + st * kTStage;
+        tma_load_2d(sb, &tA, &full[st], kb * kTK, tm * kTM);
+        tma_load_2d(sb + kTATile, &tB, &full[st], kb * kTK, tn * kTN);
+        pend[st] = (int)ph;
+      }
+      if (!ok)  // drain: the last copies issued on every stage land before the CTA exits
+        for (int i = 0; i < kTStages; ++i)
+          if (pend[i] >= 0) mbar_wait_bounded(&full[i], (uint32_t)pend[i]);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      bool ok = true;
+      for (int kb = 0; kb < nk && ok; ++kb) {
+        const int st = kb % kTStages;
+        if (!wait_or_abort(&full[st], (uint32_t)((kb / kTStages) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sb = base + st * kTStage;
+#pragma unroll
+        for (int kk = 0; kk < kTK / 16; ++kk)
+          umma_f16(tmem, desc_k128(sb + kk * 32), desc_k128(sb + kTATile + kk * 32), kTIdesc,
+                   (kb > 0 || kk > 0) ? 1u : 0u);
+        umma_commit(&empty[st]);  // the stage is reusable once these MMAs have read it
+      }
+      umma_commit(tfull);  // every MMA issued (none if aborted) has completed
+    }
+  } else {  // epilogue: TMEM lane quarter q holds rows q*32 .. q*32+31 of the tile
+    // The accumulator goes through shared memory (the operand stages are free once every
+    // MMA has completed), so that the epilogue's loads and stores run along rows: lane l
+    // of a warp handles columns l, l+32, l+64, l+96 of each of its quarter's rows.
+    const int q = warp & 3;
+    float* tile = reinterpret_cast<float*>(tsmem_raw + (base - raw)) + q * 32 * kTPitch;
+    if (wait_or_abort(tfull, 0, abort_flag) && !*abort_flag) {
+      tc_fence_after();
+#pragma unroll 1
+      for (int j = 0; j < kTN / 32; ++j) {
+        uint32_t r[32];
+        tmem_ld_32x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(j * 32), r);
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) tile[lane * kTPitch + j * 32 + jj] = __uint_as_float(r[jj]);
+      }
+      __syncwarp();
+#pragma unroll 1
+      for (int rr = 0; rr < 32; ++rr) {
+        const int m = tm * kTM + q * 32 + rr;
+        if (m >= M) break;
+        const int64_t row = (int64_t)m * ep.ldc;
+#pragma unroll
+        for (int c4 = 0; c4 < kTN / 32; ++c4) {
+          const int cl = c4 * 32 + lane, n = tn * kTN + cl;
+          if (n >= N) continue;
+          float v = ep.alpha * tile[rr * kTPitch + cl];
+          if (ep.bias) v += ep.bias[n];
+          if (ep.add) v += ep.add[row + n];
+          if (ep.relu) v = fmaxf(v, 0.0f);
+          if (ep.mask && !(__bfloat162float(ep.mask[row + n]) > 0.0f)) v = 0.0f;
+          if (ep.C32) ep.C32[row + n] = v;
+          if (ep.C16) ep.C16[row + n] = __float2bfloat16(v);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (s_abort && threadIdx.x == 0) atomicExch(err, 1);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTN) : "memory");
+  }
+}
+
+// out[c][r] = in[r][c] for r < rows, c < cols (BF16, 32 x 32 tiles through shared memory)
+__global__ void k_mlp_transpose(const __nv_bfloat16* __restrict__ in, int rows, int cols, int ldin,
+                                __nv_bfloat16* __restrict__ out, int ldout) {
+  __shared__ __nv_bfloat16 t[32][34];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    t[k][threadIdx.x] = (r < rows && c < cols) ? in[(int64_t)r * ldin + c] : __float2bfloat16(0.0f);
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int c = c0 + k, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) out[(int64_t)c * ldout + r] = t[threadIdx.x][k];
   }
 }
 
@@ -322,14 +413,84 @@ __global__ void k_mlp_gate(const float* __restrict__ rho, const double* __restri
 
 struct Net {
   __nv_bfloat16* pb;  // bf16 parameters
+  __nv_bfloat16 *W2t, *W3t;  // bf16 transposes of W2 [H][H] and W3 [OUT][H]: [H][H], [H][OUT]
   __nv_bfloat16 *X, *H1, *H2, *dY, *dZ2, *dZ1;
+  // transposes of the activations and deltas, [features][ldr] with ldr = rows rounded up
+  // to a multiple of 8 (the tensor maps' row pitch must be a multiple of 16 bytes)
+  __nv_bfloat16 *Xt, *H1t, *H2t, *dYt, *dZ2t, *dZ1t;
+  int ldr;
   float *Y, *T, *grad;
 };
 
-void gemm(cudaStream_t st, const __nv_bfloat16* A, int lda, int tA, const __nv_bfloat16* B, int ldb, int tB,
-          int M, int N, int K, GemmEpi ep) {
-  dim3 grid((N + 63) / 64, (M + 63) / 64);
-  k_mlp_gemm<<<grid, 128, 0, st>>>(A, lda, tA, B, ldb, tB, M, N, K, ep);
+// Tensor maps of the operands: [rows][cols] bf16 with row pitch ld elements, boxes of 64
+// columns x 128 rows, 128-byte swizzle.  Encoding is host work, so maps are cached by
+// (address, shape, pitch), which fully determines them.
+struct MapKey {
+  const void* p;
+  int rows, cols, ld;
+  bool operator==(const MapKey& o) const { return p == o.p && rows == o.rows && cols == o.cols && ld == o.ld; }
+};
+struct MapEntry {
+  MapKey key;
+  CUtensorMap map;
+};
+std::mutex g_map_mutex;
+std::vector<MapEntry> g_maps;
+
+int operand_map(kite_ctx* ctx, const __nv_bfloat16* p, int rows, int cols, int ld, CUtensorMap* out) {
+  const MapKey key{p, rows, cols, ld};
+  std::lock_guard<std::mutex> lock(g_map_mutex);
+  for (const MapEntry& e : g_maps)
+    if (e.key == key) {
+      *out = e.map;
+      return KITE_OK;
+    }
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(ctx, KITE_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)kTM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(p), dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, KITE_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  if (g_maps.size() >= 256) g_maps.erase(g_maps.begin());
+  g_maps.push_back(MapEntry{key, m});
+  *out = m;
+  return KITE_OK;
+}
+
+// C = A B^T on the tensor cores: A [M][K] (pitch lda), B [N][K] (pitch ldb), see k_mlp_tc.
+int gemm(kite_ctx* ctx, cudaStream_t st, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M,
+         int N, int K, GemmEpi ep) {
+  if (M < 1 || N < 1 || K < 1) return KITE_OK;
+  static bool attr = false;
+  if (!attr) {
+    KITE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTSmem));
+    attr = true;
+  }
+  CUtensorMap mA, mB;
+  int rc = operand_map(ctx, A, M, K, lda, &mA);
+  if (rc == KITE_OK) rc = operand_map(ctx, B, N, K, ldb, &mB);
+  if (rc != KITE_OK) return rc;
+  dim3 grid((N + kTN - 1) / kTN, (M + kTM - 1) / kTM);
+  k_mlp_tc<<<grid, kTThreads, kTSmem, st>>>(mA, mB, M, N, K, ep, ctx->d_status);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  return KITE_OK;
+}
+
+void transpose(cudaStream_t st, const __nv_bfloat16* in, int rows, int cols, int ldin, __nv_bfloat16* out,
+               int ldout) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+  k_mlp_transpose<<<grid, block, 0, st>>>(in, rows, cols, ldin, out, ldout);
+}
+
+// bf16 transposes of W2 and W3 after the bf16 parameters changed
+void refresh_wt(cudaStream_t st, const Net& net) {
+  transpose(st, net.pb + kOffW2, HID, HID, HID, net.W2t, HID);
+  transpose(st, net.pb + kOffW3, OUT, HID, HID, net.W3t, OUT);
 }
 
 GemmEpi epi(float* C32, __nv_bfloat16* C16, int ldc, const float* bias = nullptr, int relu = 0,
@@ -347,12 +508,14 @@ GemmEpi epi(float* C32, __nv_bfloat16* C16, int ldc, const float* bias = nullptr
 }
 
 // forward on rows already in net.X (BF16, scaled); writes net.Y (FP32) = network (+ add)
-void forward(cudaStream_t st, const Net& net, const float* p32, int rows, const float* add = nullptr) {
-  gemm(st, net.X, IN, 0, net.pb + kOffW1, IN, 1, rows, HID, IN, epi(nullptr, net.H1, HID, p32 + kOffB1, 1));
-  gemm(st, net.H1, HID, 0, net.pb + kOffW2, HID, 1, rows, HID, HID, epi(nullptr, net.H2, HID, p32 + kOffB2, 1));
+int forward(kite_ctx* ctx, cudaStream_t st, const Net& net, const float* p32, int rows, const float* add = nullptr) {
+  int rc = gemm(ctx, st, net.X, IN, net.pb + kOffW1, IN, rows, HID, IN, epi(nullptr, net.H1, HID, p32 + kOffB1, 1));
+  if (rc == KITE_OK)
+    rc = gemm(ctx, st, net.H1, HID, net.pb + kOffW2, HID, rows, HID, HID, epi(nullptr, net.H2, HID, p32 + kOffB2, 1));
   GemmEpi e3 = epi(net.Y, nullptr, OUT, p32 + kOffB3);
   e3.add = add;
-  gemm(st, net.H2, HID, 0, net.pb + kOffW3, HID, 1, rows, OUT, HID, e3);
+  if (rc == KITE_OK) rc = gemm(ctx, st, net.H2, HID, net.pb + kOffW3, HID, rows, OUT, HID, e3);
+  return rc;
 }
 
 bool use_prior(const kite_mlp_prior* prior) { return prior && prior->kind == KITE_PRIOR_JACKSON; }
@@ -363,31 +526,70 @@ void launch_prior(cudaStream_t st, int num_sms, const float* X, int rows, const 
   k_mlp_prior<<<blocks, 256, 0, st>>>(X, rows, prior_coef(), 1.0 / (3.141592653589793 * a), P);
 }
 
-// backward of the mean L1 loss over rows x OUT; gradient into net.grad
-void backward(cudaStream_t st, const Net& net, int rows, double* lsum, int lblocks) {
+// backward of the mean L1 loss over rows x OUT; gradient into net.grad.  Each product with
+// a transposed operand takes the transposes of activations, deltas or weights, so that
+// every GEMM is A B^T with both operands K-contiguous.
+int backward(kite_ctx* ctx, cudaStream_t st, const Net& net, int rows, double* lsum, int lblocks) {
   const int64_t n = (int64_t)rows * OUT;
+  const int ldr = net.ldr;
   k_mlp_l1grad<<<lblocks, 256, 0, st>>>(net.Y, net.T, n, 1.0f / (float)n, net.dY, lsum);
   float* g = net.grad;
-  gemm(st, net.dY, OUT, 1, net.H2, HID, 0, OUT, HID, rows, epi(g + kOffW3, nullptr, HID));
+  transpose(st, net.dY, rows, OUT, OUT, net.dYt, ldr);
+  transpose(st, net.H2, rows, HID, HID, net.H2t, ldr);
+  // dW3 [OUT][H] = dY^T H2
+  int rc = gemm(ctx, st, net.dYt, ldr, net.H2t, ldr, OUT, HID, rows, epi(g + kOffW3, nullptr, HID));
   k_mlp_colsum<<<(OUT + 255) / 256, 256, 0, st>>>(net.dY, rows, OUT, g + kOffB3);
-  gemm(st, net.dY, OUT, 0, net.pb + kOffW3, HID, 0, rows, HID, OUT, epi(nullptr, net.dZ2, HID, nullptr, 0, net.H2));
-  gemm(st, net.dZ2, HID, 1, net.H1, HID, 0, HID, HID, rows, epi(g + kOffW2, nullptr, HID));
+  // dZ2 [rows][H] = (dY W3) masked by H2 > 0
+  if (rc == KITE_OK)
+    rc = gemm(ctx, st, net.dY, OUT, net.W3t, OUT, rows, HID, OUT, epi(nullptr, net.dZ2, HID, nullptr, 0, net.H2));
+  transpose(st, net.dZ2, rows, HID, HID, net.dZ2t, ldr);
+  transpose(st, net.H1, rows, HID, HID, net.H1t, ldr);
+  // dW2 [H][H] = dZ2^T H1
+  if (rc == KITE_OK) rc = gemm(ctx, st, net.dZ2t, ldr, net.H1t, ldr, HID, HID, rows, epi(g + kOffW2, nullptr, HID));
   k_mlp_colsum<<<(HID + 255) / 256, 256, 0, st>>>(net.dZ2, rows, HID, g + kOffB2);
-  gemm(st, net.dZ2, HID, 0, net.pb + kOffW2, HID, 0, rows, HID, HID, epi(nullptr, net.dZ1, HID, nullptr, 0, net.H1));
-  gemm(st, net.dZ1, HID, 1, net.X, IN, 0, HID, IN, rows, epi(g + kOffW1, nullptr, IN));
+  // dZ1 [rows][H] = (dZ2 W2) masked by H1 > 0
+  if (rc == KITE_OK)
+    rc = gemm(ctx, st, net.dZ2, HID, net.W2t, HID, rows, HID, HID, epi(nullptr, net.dZ1, HID, nullptr, 0, net.H1));
+  transpose(st, net.dZ1, rows, HID, HID, net.dZ1t, ldr);
+  transpose(st, net.X, rows, IN, IN, net.Xt, ldr);
+  // dW1 [H][IN] = dZ1^T X
+  if (rc == KITE_OK) rc = gemm(ctx, st, net.dZ1t, ldr, net.Xt, ldr, HID, IN, rows, epi(g + kOffW1, nullptr, IN));
   k_mlp_colsum<<<(HID + 255) / 256, 256, 0, st>>>(net.dZ1, rows, HID, g + kOffB1);
+  return rc;
+}
+
+// The GEMM kernels set the context's status word when a bounded wait gives up.
+int clear_status(kite_ctx* ctx) {
+  KITE_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+  return KITE_OK;
+}
+int read_status(kite_ctx* ctx) {
+  int h = 0;
+  KITE_CUDA_TRY(ctx, cudaMemcpyAsync(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  KITE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return h ? fail(ctx, KITE_ERR_TIMEOUT, "a bounded wait gave up in the perceptron's GEMM") : KITE_OK;
 }
 
 int carve_net(kite_ctx* ctx, int rows, Net* net, float** extra, size_t extra_floats) {
   Carver probe(nullptr);
+  const int ldr = (rows + 7) / 8 * 8;
   auto lay = [&](Carver& k, Net& n, float** ex) {
     n.pb = k.take<__nv_bfloat16>(kParams);
+    n.W2t = k.take<__nv_bfloat16>((size_t)HID * HID);
+    n.W3t = k.take<__nv_bfloat16>((size_t)HID * OUT);
     n.X = k.take<__nv_bfloat16>((size_t)rows * IN);
     n.H1 = k.take<__nv_bfloat16>((size_t)rows * HID);
     n.H2 = k.take<__nv_bfloat16>((size_t)rows * HID);
     n.dY = k.take<__nv_bfloat16>((size_t)rows * OUT);
     n.dZ2 = k.take<__nv_bfloat16>((size_t)rows * HID);
     n.dZ1 = k.take<__nv_bfloat16>((size_t)rows * HID);
+    n.ldr = ldr;
+    n.Xt = k.take<__nv_bfloat16>((size_t)IN * ldr);
+    n.H1t = k.take<__nv_bfloat16>((size_t)HID * ldr);
+    n.H2t = k.take<__nv_bfloat16>((size_t)HID * ldr);
+    n.dYt = k.take<__nv_bfloat16>((size_t)OUT * ldr);
+    n.dZ2t = k.take<__nv_bfloat16>((size_t)HID * ldr);
+    n.dZ1t = k.take<__nv_bfloat16>((size_t)HID * ldr);
     n.Y = k.take<float>((size_t)rows * OUT);
     n.T = k.take<float>((size_t)rows * OUT);
     n.grad = k.take<float>(kParams);
@@ -439,17 +641,21 @@ int mlp_gradient_impl(kite_ctx* ctx, const float* params, const float* X, const 
   cudaStream_t st = ctx->stream;
   float* p32 = ex;
   double* lsum = reinterpret_cast<double*>(ex + kParams);
+  if ((rc = clear_status(ctx)) != KITE_OK) return rc;
   KITE_CUDA_TRY(ctx, cudaMemcpyAsync(p32, params, sizeof(float) * kParams, cudaMemcpyDefault, st));
   k_mlp_tobf16<<<1024, 256, 0, st>>>(p32, net.pb, kParams);
+  refresh_wt(st, net);
   k_mlp_gather<<<1024, 256, 0, st>>>(X, nullptr, n, IN, shift, scale, net.X, T, net.T, OUT);
-  forward(st, net, p32, n);
   const int lblocks = 256;
-  backward(st, net, n, lsum, lblocks);
+  rc = forward(ctx, st, net, p32, n);
+  if (rc == KITE_OK) rc = backward(ctx, st, net, n, lsum, lblocks);
+  if (rc != KITE_OK) return rc;
   KITE_CUDA_TRY(ctx, cudaGetLastError());
   KITE_CUDA_TRY(ctx, cudaMemcpyAsync(grad, net.grad, sizeof(float) * kParams, cudaMemcpyDefault, st));
   std::vector<double> ls(lblocks);
   KITE_CUDA_TRY(ctx, cudaMemcpyAsync(ls.data(), lsum, sizeof(double) * lblocks, cudaMemcpyDeviceToHost, st));
   KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if ((rc = read_status(ctx)) != KITE_OK) return rc;
   if (loss) *loss = std::accumulate(ls.begin(), ls.end(), 0.0) / ((double)n * OUT);
   return KITE_OK;
 }
@@ -464,6 +670,7 @@ int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, 
   int rc = carve_net(ctx, std::min(n, chunk), &net, &ex, kParams + (pri ? (size_t)std::min(n, chunk) * OUT : 0));
   if (rc != KITE_OK) return rc;
   cudaStream_t st = ctx->stream;
+  if ((rc = clear_status(ctx)) != KITE_OK) return rc;
   KITE_CUDA_TRY(ctx, cudaMemcpyAsync(ex, params, sizeof(float) * kParams, cudaMemcpyDefault, st));
   k_mlp_tobf16<<<1024, 256, 0, st>>>(ex, net.pb, kParams);
   for (int r0 = 0; r0 < n; r0 += chunk) {
@@ -472,12 +679,12 @@ int mlp_forward_impl(kite_ctx* ctx, const float* params, const float* X, int n, 
                                        nullptr, 0);
     float* P = pri ? ex + kParams : nullptr;
     if (pri) launch_prior(st, ctx->num_sms, X + (int64_t)r0 * IN, rows, prior, P);
-    forward(st, net, ex, rows, P);
+    rc = forward(ctx, st, net, ex, rows, P);
+    if (rc != KITE_OK) return rc;
     KITE_CUDA_TRY(ctx, cudaMemcpyAsync(Y + (int64_t)r0 * OUT, net.Y, sizeof(float) * rows * OUT, cudaMemcpyDefault, st));
   }
   KITE_CUDA_TRY(ctx, cudaGetLastError());
-  KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-  return KITE_OK;
+  return read_status(ctx);
 }
 
 int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const float* shift, const float* scale,
@@ -487,53 +694,57 @@ int mlp_train_impl(kite_ctx* ctx, const float* X, const float* T, int n, const f
   Net net;
   float* ex;
   const bool pri = use_prior(prior);
-  int rc = carve_net(ctx, bs, &net, &ex, 3 * kParams + 4096 + (size_t)bs + (pri ? (size_t)n * OUT : 0));
+  const size_t lsum_floats = 2 * (size_t)128 * ((n + bs - 1) / bs);  // FP64 partial sums of every step
+  const size_t idx_floats = ((size_t)n + 63) / 64 * 64;
+  int rc = carve_net(ctx, bs, &net, &ex, 3 * kParams + lsum_floats + idx_floats + (pri ? (size_t)n * OUT : 0));
   if (rc != KITE_OK) return rc;
   cudaStream_t st = ctx->stream;
   float* p32 = ex;
   float* m = ex + kParams;
   float* v = ex + 2 * kParams;
   double* lsum = reinterpret_cast<double*>(ex + 3 * kParams);
-  int* d_idx = reinterpret_cast<int*>(ex + 3 * kParams + 4096);
+  int* d_idx = reinterpret_cast<int*>(ex + 3 * kParams + lsum_floats);
   // the prior of every training row, once; the batches gather T - prior as targets
-  float* P = pri ? ex + 3 * kParams + 4096 + bs : nullptr;
+  float* P = pri ? ex + 3 * kParams + lsum_floats + idx_floats : nullptr;
+  if ((rc = clear_status(ctx)) != KITE_OK) return rc;
   if (pri) launch_prior(st, ctx->num_sms, X, n, prior, P);
   KITE_CUDA_TRY(ctx, cudaMemcpyAsync(p32, params, sizeof(float) * kParams, cudaMemcpyDefault, st));
   KITE_CUDA_TRY(ctx, cudaMemsetAsync(m, 0, sizeof(float) * 2 * kParams, st));
   k_mlp_tobf16<<<1024, 256, 0, st>>>(p32, net.pb, kParams);
+  refresh_wt(st, net);
   std::mt19937_64 rng(cfg->seed);
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   const int steps_per_epoch = (n + bs - 1) / bs;
   const int total = cfg->epochs * steps_per_epoch;
   const int lblocks = 128;
-  std::vector<double> ls(lblocks);
+  // per epoch: the shuffled order goes up once, every step's partial loss sums stay on the
+  // device, and the host reads them (and synchronises) once at the end of the epoch
+  std::vector<double> ls((size_t)lblocks * steps_per_epoch);
   int t = 0;
   for (int ep = 0; ep < cfg->epochs; ++ep) {
     std::shuffle(order.begin(), order.end(), rng);
-    double epoch_loss = 0.0;
+    KITE_CUDA_TRY(ctx, cudaMemcpyAsync(d_idx, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
     for (int b = 0; b < steps_per_epoch; ++b) {
       const int rows = std::min(bs, n - b * bs);
-      KITE_CUDA_TRY(ctx, cudaMemcpyAsync(d_idx, order.data() + (size_t)b * bs, sizeof(int) * rows,
-                                         cudaMemcpyHostToDevice, st));
-      k_mlp_gather<<<512, 256, 0, st>>>(X, d_idx, rows, IN, shift, scale, net.X, T, net.T, OUT, P);
-      forward(st, net, p32, rows);
-      backward(st, net, rows, lsum, lblocks);
+      k_mlp_gather<<<512, 256, 0, st>>>(X, d_idx + (size_t)b * bs, rows, IN, shift, scale, net.X, T, net.T, OUT, P);
+      rc = forward(ctx, st, net, p32, rows);
+      if (rc == KITE_OK) rc = backward(ctx, st, net, rows, lsum + (size_t)b * lblocks, lblocks);
+      if (rc != KITE_OK) return rc;
       ++t;
       const AdamwCoeffs c = adamw_coeffs(t, total, cfg->lr);
       k_mlp_adamw<<<1024, 256, 0, st>>>(p32, net.grad, m, v, net.pb, kParams, c.lr, (float)kBeta1,
                                         (float)(1.0 - kBeta1), (float)kBeta2, (float)(1.0 - kBeta2), kAdamEps,
                                         (float)cfg->weight_decay, c.c1, c.c2);
+      refresh_wt(st, net);
       KITE_CUDA_TRY(ctx, cudaGetLastError());
-      KITE_CUDA_TRY(ctx, cudaMemcpyAsync(ls.data(), lsum, sizeof(double) * lblocks, cudaMemcpyDeviceToHost, st));
-      KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));  // d_idx / order reuse
-      epoch_loss += std::accumulate(ls.begin(), ls.end(), 0.0);
     }
-    if (loss_curve) loss_curve[ep] = (float)(epoch_loss / ((double)n * OUT));
+    KITE_CUDA_TRY(ctx, cudaMemcpyAsync(ls.data(), lsum, sizeof(double) * ls.size(), cudaMemcpyDeviceToHost, st));
+    KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));  // the order buffer and ls are reused
+    if (loss_curve) loss_curve[ep] = (float)(std::accumulate(ls.begin(), ls.end(), 0.0) / ((double)n * OUT));
   }
   KITE_CUDA_TRY(ctx, cudaMemcpyAsync(params, p32, sizeof(float) * kParams, cudaMemcpyDefault, st));
-  KITE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-  return KITE_OK;
+  return read_status(ctx);
 }
 
 int mlp_init_impl(kite_ctx* ctx, uint64_t seed, double head_scale, float* p) {
