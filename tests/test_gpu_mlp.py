@@ -293,3 +293,44 @@ def test_gate_flags_out_of_distribution_inputs(ctx):
     dev = np.zeros(2)
     kite.learned_gate(ctx, rho, np.ascontiguousarray(mus), mus.shape[1], 2, 16, e_min, e_max, 0.02, flags, dev)
     assert flags.tolist() == [0, 1], dev
+
+
+def test_model_import_export_and_argument_errors(ctx):
+    """A model rebuilt from its exported parts gives the same densities; the learned calls
+    refuse inconsistent arguments with KITE_ERR_ARG and leave the context usable."""
+    e_min, e_max = -10.0, 10.0
+    g = np.random.Generator(np.random.PCG64(51))
+    X = g.standard_normal((64, omlp.IN)).astype(np.float32)
+    Y = np.abs(g.standard_normal((64, omlp.OUT))).astype(np.float32)
+    m1 = kite.learned_train(ctx, X, Y, 64, e_min, e_max, epochs=2, batch=32, seed=5, head_scale=0.1)
+    p, sh, sc, win = m1.export()
+    m2 = kite.model_import(ctx, p, win[0], win[1], shift=sh, scale=sc)
+    mu = np.zeros((8, 200))
+    mu[:, 0] = 1.0
+    mu[:, 1:omlp.IN] = 0.01 * g.standard_normal((8, omlp.IN - 1))
+    out = []
+    for m in (m1, m2):
+        rho = np.zeros((8, omlp.OUT), np.float32)
+        flags = np.zeros(8, np.int32)
+        kite.learned_dos(ctx, m, mu, 200, 8, float("inf"), 16, 64, rho, flags)
+        out.append(rho)
+    assert np.array_equal(out[0], out[1])
+    rho = np.zeros((8, omlp.OUT), np.float32)
+    flags = np.zeros(8, np.int32)
+    for bad in (dict(mu_ld=100), dict(kcheck=0), dict(M_plain=300), dict(gate_tol=-1.0)):
+        a = dict(mu_ld=200, kcheck=16, M_plain=64, gate_tol=0.02)
+        a.update(bad)
+        with pytest.raises(kite.KiteError) as e:
+            kite.learned_dos(ctx, m1, mu, a["mu_ld"], 8, a["gate_tol"], a["kcheck"], a["M_plain"], rho, flags)
+        assert e.value.status == kite.ERR_ARG, bad
+    with pytest.raises(kite.KiteError) as e:  # systems without the plain path's parameters
+        kite.learned_dos(ctx, m1, mu, 200, 8, 0.0, 16, 64, rho, flags,
+                         systems=[kite.make_system(kite.HONEYCOMB, 8, 8, -2.7)] * 8)
+    assert e.value.status == kite.ERR_ARG
+    with pytest.raises(kite.KiteError) as e:
+        kite.learned_train(ctx, X, Y, 64, 1.0, -1.0)  # empty window
+    assert e.value.status == kite.ERR_ARG
+    kite.learned_dos(ctx, m1, mu, 200, 8, float("inf"), 16, 64, rho, flags)  # still usable
+    assert np.array_equal(rho, out[0])
+    m1.close()
+    m2.close()
