@@ -124,6 +124,14 @@ __device__ __forceinline__ double quiet_nan<double>() {
   return __longlong_as_double(0x7ff8000000000000ll);
 }
 
+// A vacancy's on-site term is a NaN.  In FP64 the test runs on the integer pipe (|bits|
+// above the infinity pattern) rather than as an FP64 comparison: GB300's FP64 pipe is the
+// bound of the FP64 recursion.
+__device__ __forceinline__ bool is_vacancy(float v) { return v != v; }
+__device__ __forceinline__ bool is_vacancy(double v) {
+  return (unsigned long long)(__double_as_longlong(v) & 0x7fffffffffffffffll) > 0x7ff0000000000000ull;
+}
+
 }  // namespace kite
 
 namespace kite {

@@ -491,7 +491,7 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
           if (MODE == 0)
             z0 = *reinterpret_cast<const Ch*>(mid + Sh::CURB + Sh::ROWB + xl * CELLB + choff);
         }
-        const bool vacant = v != v;
+        const bool vacant = is_vacancy(v);
         Ch out;
 #pragma unroll
         for (int k = 0; k < NR; ++k) {

@@ -157,7 +157,7 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
       // a vacancy (v is NaN) holds r = 0 exactly in every iterate, so with its hopping and
       // on-site term zeroed h = +0 and fma(2, +0, -0) = +0: the same bits as forcing the
       // output to zero, with two selects per site instead of one per component
-      const bool vacant = v != v;
+      const bool vacant = is_vacancy(v);
       const Real ve = vacant ? Real(0) : v, te = vacant ? Real(0) : tt;
       Ch out;
 #pragma unroll
@@ -193,7 +193,7 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
       // a vacancy (v is NaN) holds r = 0 exactly in every iterate, so with its hopping and
       // on-site term zeroed h = +0 and fma(2, +0, -0) = +0: the same bits as forcing the
       // output to zero, with two selects per site instead of one per component
-      const bool vacant = v != v;
+      const bool vacant = is_vacancy(v);
       const Real ve = vacant ? Real(0) : v, te = vacant ? Real(0) : tt;
       Ch out;
 #pragma unroll
