@@ -17,6 +17,8 @@
 // h~_oj = (r_o - r_j) t~ exp(i theta_oj), the same gauge as the Hamiltonian, so that
 // v = i[H, r]/hbar.  The step kernel's FIELD variant rotates the neighbour values before
 // both the stencil sum and the velocity, and k_velocity rotates them the same way.
+#include <stdlib.h>
+
 #include "kite_internal.h"
 #include "kite_step.cuh"
 
@@ -31,6 +33,15 @@ int reduce_cplx(kite_ctx* ctx, const double* part, int S, int M, int M2, double 
 
 namespace {
 
+// Ring depth and CTAs per SM of the family step kernels, measured on the optical
+// conductivity workload (1024^2, two vectors per batch): four stages at five CTAs per SM
+// moved 5.88 TB/s, eight stages at three 5.55 TB/s, five or six stages at four 5.54-5.75.
+// KITE_FAM_CPS=<CTAs per SM> overrides the CTA count (it is capped at the occupancy).
+#ifndef KITE_FAM_STAGES
+#define KITE_FAM_STAGES 4
+#endif
+constexpr int kFamStages = KITE_FAM_STAGES;
+constexpr int kFamCtasPerSm = 5;
 constexpr int kGemmSubKb = 8;   // 512 products per FP32 accumulation sub-chunk (TMEM)
 constexpr int kGemmFold = 16;   // sub-chunks summed in FP32 registers before FP64
 constexpr int kGemmProducts = 4; // hi*hi + hi*lo + lo*hi + lo*lo
@@ -119,8 +130,9 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
   const int64_t ncell = (int64_t)sys->Lx * sys->Ly, N = ncell * SORB;
   const int64_t Kp = ((2 * N + 63) / 64) * 64;
   const int VB = 2;
-  const int G =
-      grid_for<float, LAT, C, false, 1, kStages, FIELD>(ctx, (long long)((sys->Lx + Sh::TX - 1) / Sh::TX) * sys->Ly);
+  const char* fam_cps = getenv("KITE_FAM_CPS");
+  const int G = grid_for<float, LAT, C, false, 1, kFamStages, FIELD>(
+      ctx, (long long)((sys->Lx + Sh::TX - 1) / Sh::TX) * sys->Ly, fam_cps ? atoi(fam_cps) : kFamCtasPerSm);
   const long long units = (long long)((sys->Lx + Sh::TX - 1) / Sh::TX) * sys->Ly;
   const int Sg = plan_gemm_splits(ctx, M, 2 * M, Kp);
   const size_t vec_bytes = (size_t)ncell * SORB * C * 16;
@@ -195,14 +207,14 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
       sys->p_vac <= 0.0 ? 0ull : (thr_d >= 4294967296.0 ? 4294967296ull : (uint64_t)thr_d);
   const uint32_t k0 = (uint32_t)sys->seed, k1 = (uint32_t)(sys->seed >> 32);
   const int blocks = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->num_sms * 16);
-  constexpr int SM = Sh::SMEM_NR0;  // the family modes never stage r_0
-  cudaFuncSetAttribute(k_step<float, LAT, C, true, 1, kStages, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  constexpr int SM = StepShape<LAT, C, kFamStages>::SMEM_NR0;  // the family modes never stage r_0
+  cudaFuncSetAttribute(k_step<float, LAT, C, true, 1, kFamStages, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        SM);
-  cudaFuncSetAttribute(k_step<float, LAT, C, false, 1, kStages, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_step<float, LAT, C, false, 1, kFamStages, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        SM);
-  cudaFuncSetAttribute(k_step<float, LAT, C, true, 2, kStages, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_step<float, LAT, C, true, 2, kFamStages, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        SM);
-  cudaFuncSetAttribute(k_step<float, LAT, C, false, 2, kStages, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_step<float, LAT, C, false, 2, kFamStages, FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        SM);
 
   FamOut fa{}, fb{};
@@ -249,11 +261,11 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
       for (int n = 0; n + 1 < M; ++n) {
         fa.col = n + 1;
         if (n == 0)
-          launch_pdl(k_step<float, LAT, C, true, 1, kStages, FIELD>, G, kBlock, SM, st,
+          launch_pdl(k_step<float, LAT, C, true, 1, kFamStages, FIELD>, G, kBlock, SM, st,
               nullptr, whereA(0), whereA(1), nullptr, vt, tt, sys->Lx, sys->Ly, units, nullptr,
               nullptr, ctx->d_status, 0, fa, 0, SeriesOut{}, ph, open);
         else
-          launch_pdl(k_step<float, LAT, C, false, 1, kStages, FIELD>, G, kBlock, SM, st,
+          launch_pdl(k_step<float, LAT, C, false, 1, kFamStages, FIELD>, G, kBlock, SM, st,
               whereA(n - 1), whereA(n), whereA(n + 1), nullptr, vt, tt, sys->Lx, sys->Ly, units,
               nullptr, nullptr, ctx->d_status, 0, fa, 0, SeriesOut{}, ph, open);
       }
@@ -262,11 +274,11 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
       for (int n = 0; n + 1 < M; ++n) {
         fb.col = n;
         if (n == 0)
-          launch_pdl(k_step<float, LAT, C, true, 2, kStages, FIELD>, G, kBlock, SM, st,
+          launch_pdl(k_step<float, LAT, C, true, 2, kFamStages, FIELD>, G, kBlock, SM, st,
               nullptr, whereB(0), whereB(1), nullptr, vt, tt, sys->Lx, sys->Ly, units, nullptr,
               nullptr, ctx->d_status, 0, fb, 0, SeriesOut{}, ph, open);
         else
-          launch_pdl(k_step<float, LAT, C, false, 2, kStages, FIELD>, G, kBlock, SM, st,
+          launch_pdl(k_step<float, LAT, C, false, 2, kFamStages, FIELD>, G, kBlock, SM, st,
               whereB(n - 1), whereB(n), whereB(n + 1), nullptr, vt, tt, sys->Lx, sys->Ly, units,
               nullptr, nullptr, ctx->d_status, 0, fb, 0, SeriesOut{}, ph, open);
       }
