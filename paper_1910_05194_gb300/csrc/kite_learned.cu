@@ -250,19 +250,22 @@ int kite_learned_dos(kite_ctx* ctx, const kite_model* model, const double* mu, i
 
 int kite_model_export(const kite_model* model, float* params, float* shift, float* scale, double* window) {
   if (!model) return KITE_ERR_ARG;
-  if (cudaSetDevice(model->device) != cudaSuccess) return KITE_ERR_CUDA;
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(model->device) != cudaSuccess) return KITE_ERR_CUDA;
   const int64_t P = mlp_param_count();
+  int rc = KITE_OK;
   if (params && cudaMemcpy(params, model->params, sizeof(float) * (size_t)P, cudaMemcpyDefault) != cudaSuccess)
-    return KITE_ERR_CUDA;
-  if (shift && cudaMemcpy(shift, model->shift, sizeof(float) * IN, cudaMemcpyDefault) != cudaSuccess)
-    return KITE_ERR_CUDA;
-  if (scale && cudaMemcpy(scale, model->scale, sizeof(float) * IN, cudaMemcpyDefault) != cudaSuccess)
-    return KITE_ERR_CUDA;
-  if (window) {
+    rc = KITE_ERR_CUDA;
+  if (rc == KITE_OK && shift && cudaMemcpy(shift, model->shift, sizeof(float) * IN, cudaMemcpyDefault) != cudaSuccess)
+    rc = KITE_ERR_CUDA;
+  if (rc == KITE_OK && scale && cudaMemcpy(scale, model->scale, sizeof(float) * IN, cudaMemcpyDefault) != cudaSuccess)
+    rc = KITE_ERR_CUDA;
+  if (rc == KITE_OK && window) {
     window[0] = model->e_min;
     window[1] = model->e_max;
   }
-  return KITE_OK;
+  cudaSetDevice(prev);  // the caller's current device is left as it was
+  return rc;
 }
 
 int kite_model_import(kite_ctx* ctx, const float* params, const float* shift, const float* scale, double e_min,
@@ -292,8 +295,11 @@ int kite_model_import(kite_ctx* ctx, const float* params, const float* shift, co
 
 void kite_model_destroy(kite_model* model) {
   if (!model) return;
+  int prev = 0;
+  const bool had = cudaGetDevice(&prev) == cudaSuccess;
   cudaSetDevice(model->device);
   if (model->buf) cudaFree(model->buf);
+  if (had) cudaSetDevice(prev);
   delete model;
 }
 
