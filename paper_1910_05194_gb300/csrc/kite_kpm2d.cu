@@ -45,6 +45,12 @@ constexpr int kFamCtasPerSm = 5;
 constexpr int kGemmSubKb = 8;   // 512 products per FP32 accumulation sub-chunk (TMEM)
 constexpr int kGemmFold = 16;   // sub-chunks summed in FP32 registers before FP64
 constexpr int kGemmProducts = 4; // hi*hi + hi*lo + lo*hi + lo*lo
+// KITE_GEMM_PRODUCTS=3 drops lo*lo (a quarter less tensor work, a one-signed bias of up to
+// ~5e-6 relative on aligned products); the default keeps all four
+inline int gemm_products() {
+  const char* e = getenv("KITE_GEMM_PRODUCTS");
+  return (e && e[0] == '3' && e[1] == 0) ? 3 : kGemmProducts;
+}
 
 // h~ = [r_dir, H~] applied to a whole FP32 batch (one chunk = two vectors).  mode 1: writes
 // the result as row `col` of the A family (and to out_vec if given); mode 2: rows `col`
@@ -292,7 +298,7 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
       for (int v = 0; v < nvec; ++v) {
         int S_used = 0;
         int rc = gemm_split_bf16(ctx, Ah[v], Al[v], Bh[v], Bl[v], M, 2 * M, Kp, Sg, kGemmSubKb, kGemmFold,
-                                 kGemmProducts, part, &S_used);
+                                 gemm_products(), part, &S_used);
         if (rc != KITE_OK) return rc;
         rc = reduce_cplx(ctx, part, S_used, M, M, scale, mu_nm_dev, true);
         if (rc != KITE_OK) return rc;
@@ -321,8 +327,8 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
     stats->step_launches = (int64_t)Sreal * ((R + VB - 1) / VB) * 2 * (M > 1 ? M - 1 : 0);
     stats->step_bytes = fam_bytes;
     stats->gemm_seconds = gemm_s;
-    // kGemmProducts BF16 products of an M x 2M x Kp real GEMM per vector
-    stats->gemm_flops = (double)kGemmProducts * 2.0 * (double)M * (2.0 * M) * (double)Kp * R * Sreal;
+    // BF16 products (four, or three) of an M x 2M x Kp real GEMM per vector
+    stats->gemm_flops = (double)gemm_products() * 2.0 * (double)M * (2.0 * M) * (double)Kp * R * Sreal;
     stats->updates = (double)n_eff * M * R * Sreal * 2.0;
     stats->n_eff = n_eff;
     stats->grid = G;
