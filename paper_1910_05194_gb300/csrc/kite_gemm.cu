@@ -102,6 +102,38 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t 
       : "memory");
 }
 
+// The same box multicast to the CTAs of `mask` in the cluster: the data lands at the same
+// shared-memory offset in each, whose mbarrier at `bar`'s offset receives the bytes.
+__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int y, int kb,
+                                               uint16_t mask) {
+  const int z = kb / kSub, x = (kb - z * kSub) * kBK;
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+// Arrives on the mbarrier at `bar`'s offset in every CTA of `mask` once this thread's
+// tcgen05 operations complete.
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ int cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return (int)r;
+}
+
 struct GemmArgs {
   int T;            // output tiles = TM * TN
   int TN;           // tiles along the B rows
@@ -118,6 +150,11 @@ struct GemmArgs {
   int* err;
 };
 
+// MC: clusters of two CTAs on tiles with the same B rows (tile rows 2p and 2p+1 of A):
+// each CTA loads its own A tile and half of the shared B tile, multicast to both, so a
+// CTA pulls 2/3 of the operand bytes per stage from L2; a stage is refilled once both
+// CTAs' MMAs have released it (their commits arrive on both CTAs' `empty` barriers).
+template <bool MC>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_gemm_split_bf16(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                       const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
@@ -138,10 +175,24 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // work items: one output tile (MC: a pair of tiles, this CTA's being row 2p + rank) and
+  // one K split each, split-major across the persistent grid (MC: across the clusters)
+  const int crank = MC ? cluster_rank() : 0;
+  const int cid = MC ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int ncl = MC ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int nitems = MC ? a.items / 2 : a.items;
+  const int Tw = MC ? a.T / 2 : a.T;  // work tiles per split
+  auto coords = [&](int it, int& s, int& tm, int& tn) {
+    s = it / Tw;
+    const int t = it - s * Tw;
+    tm = t / a.TN;
+    tn = t - tm * a.TN;
+    if (MC) tm = 2 * tm + crank;
+  };
   if (threadIdx.x == 0) {
     for (int i = 0; i < kGStages; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
+      mbar_init(&empty[i], MC ? 2 : 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
@@ -160,6 +211,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if (MC) cluster_sync();  // the peer's barriers are initialised before any multicast arrives
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   volatile int* abort_flag = &s_abort;
@@ -171,9 +223,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       bool ok = true;
       int pend[kGStages];  // parity of the last phase issued on each stage (-1: none)
       for (int i = 0; i < kGStages; ++i) pend[i] = -1;
-      for (int item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
-        const int s = item / a.T, t = item - (item / a.T) * a.T;
-        const int tm = t / a.TN, tn = t - (t / a.TN) * a.TN;
+      for (int item = cid; item < nitems && ok; item += ncl) {
+        int s, tm, tn;
+        coords(item, s, tm, tn);
         const int kb0 = s * a.kb_per_item, kb1 = min(a.kb_total, kb0 + a.kb_per_item);
         for (int kb = kb0; kb < kb1; ++kb) {
           if (!wait_or_abort(&empty[st], ph ^ 1u, abort_flag)) {
@@ -184,8 +236,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           const uint32_t sb = base + st * kStageBytes;
           tma_load_3d(sb, &tmAh, &full[st], tm * kBM, kb);
           tma_load_3d(sb + kATile, &tmAl, &full[st], tm * kBM, kb);
-          tma_load_3d(sb + 2 * kATile, &tmBh, &full[st], tn * kBN, kb);
-          tma_load_3d(sb + 2 * kATile + kBTile, &tmBl, &full[st], tn * kBN, kb);
+          if (MC) {  // this CTA's half of the B rows, to both CTAs of the pair
+            const uint32_t hoff = (uint32_t)crank * (kBTile / 2);
+            tma_load_3d_mc(sb + 2 * kATile + hoff, &tmBh, &full[st], tn * kBN + crank * (kBN / 2), kb, 3);
+            tma_load_3d_mc(sb + 2 * kATile + kBTile + hoff, &tmBl, &full[st], tn * kBN + crank * (kBN / 2), kb, 3);
+          } else {
+            tma_load_3d(sb + 2 * kATile, &tmBh, &full[st], tn * kBN, kb);
+            tma_load_3d(sb + 2 * kATile + kBTile, &tmBl, &full[st], tn * kBN, kb);
+          }
           pend[st] = (int)ph;
           if (++st == kGStages) st = 0, ph ^= 1u;
         }
@@ -201,8 +259,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       int st = 0, acc = 0;
       uint32_t ph = 0, aph = 0;
       bool ok = true;
-      for (int item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
-        const int s = item / a.T;
+      for (int item = cid; item < nitems && ok; item += ncl) {
+        int s, tm, tn;
+        coords(item, s, tm, tn);
         const int kb0 = s * a.kb_per_item, kb1 = min(a.kb_total, kb0 + a.kb_per_item);
         for (int kc = kb0; kc < kb1 && ok; kc += a.sub_kb) {
           if (!wait_or_abort(&tempty[acc], aph ^ 1u, abort_flag)) {
@@ -231,7 +290,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
               umma_bf16(d, al, bh, 1u);
               if (a.nprod == 4) umma_bf16(d, al, bl, 1u);
             }
-            umma_commit(&empty[st]);  // stage reusable once these MMAs have read it
+            if (MC)
+              umma_commit_mc(&empty[st], 3);  // both CTAs' B halves sit in this stage
+            else
+              umma_commit(&empty[st]);  // stage reusable once these MMAs have read it
             if (++st == kGStages) st = 0, ph ^= 1u;
           }
           if (!ok) break;
@@ -259,9 +321,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     int acc = 0;
     uint32_t aph = 0;
     bool ok = true;
-    for (int item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
-      const int s = item / a.T, t = item - (item / a.T) * a.T;
-      const int tm = t / a.TN, tn = t - (t / a.TN) * a.TN;
+    for (int item = cid; item < nitems && ok; item += ncl) {
+      int s, tm, tn;
+      coords(item, s, tm, tn);
       const int kb0 = s * a.kb_per_item, kb1 = min(a.kb_total, kb0 + a.kb_per_item);
       const int row0 = tm * kBM + q * 32;
       double* pbase = a.part + ((size_t)s * a.Mrows + row0) * a.Nrows;
@@ -321,6 +383,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
   __syncthreads();
   if (s_abort && threadIdx.x == 0) atomicExch(a.err, 1);
+  // MC: neither CTA leaves while the other may still multicast into it or arrive on its
+  // barriers (every wait above is bounded, so both reach this point)
+  if (MC) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -426,19 +491,22 @@ int plan_gemm_splits(kite_ctx* ctx, int Mrows, int Nrows, int64_t Kp) {
   return best;
 }
 
+// The CTA-pair variant (B tiles multicast within a two-CTA cluster, a third fewer operand
+// bytes per CTA from L2) gave the same results bit for bit but was not faster on the
+// 1024^2, M = 1024 contraction (1690 against 1715 TFLOP/s): the loads are not what holds
+// the kernel below the tensor peak.  It stays selectable at build time.
+#ifndef KITE_GEMM_MULTICAST
+#define KITE_GEMM_MULTICAST 0
+#endif
+
 int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void* Bhi,
                     const void* Blo, int Mrows, int Nrows, int64_t Kp, int S, int sub_kb,
                     int fold, int nprod, double* part, int* S_used) {
   if (Kp % kKB != 0) return fail(ctx, KITE_ERR_ARG, "K must be padded to a multiple of 64");
-  CUtensorMap mAh, mAl, mBh, mBl;
-  int rc;
-  if ((rc = make_map(ctx, &mAh, Ahi, Kp, Mrows, kBM)) != KITE_OK) return rc;
-  if ((rc = make_map(ctx, &mAl, Alo, Kp, Mrows, kBM)) != KITE_OK) return rc;
-  if ((rc = make_map(ctx, &mBh, Bhi, Kp, Nrows, kBN)) != KITE_OK) return rc;
-  if ((rc = make_map(ctx, &mBl, Blo, Kp, Nrows, kBN)) != KITE_OK) return rc;
   GemmArgs a;
   a.TN = (Nrows + kBN - 1) / kBN;
-  a.T = ((Mrows + kBM - 1) / kBM) * a.TN;
+  const int TM = (Mrows + kBM - 1) / kBM;
+  a.T = TM * a.TN;
   // splits and sub-chunks are planned in family K blocks (64 columns) and run in stages
   const int kb64 = (int)(Kp / kKB);
   a.S = std::max(1, std::min(S, kb64));
@@ -455,15 +523,53 @@ int gemm_split_bf16(kite_ctx* ctx, const void* Ahi, const void* Alo, const void*
   a.Nrows = Nrows;
   a.part = part;
   a.err = ctx->d_status;
+  // CTA pairs sharing B tiles need an even number of A tile rows and room for whole pairs
+  static int max_pairs = -1;
+  const bool mc = KITE_GEMM_MULTICAST && TM % 2 == 0 && ctx->num_sms >= 2;
   static bool attr = false;
   if (!attr) {
-    KITE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_gemm_split_bf16,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
+    KITE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_gemm_split_bf16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kGemmSmem));
+    KITE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_gemm_split_bf16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kGemmSmem));
     attr = true;
   }
-  const int grid = std::min(a.items, ctx->num_sms);
-  k_gemm_split_bf16<<<grid, kGemmThreads, kGemmSmem, ctx->stream>>>(mAh, mAl, mBh, mBl, a);
-  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  CUtensorMap mAh, mAl, mBh, mBl;
+  int rc;
+  const int bbox = mc ? kBN / 2 : kBN;  // each CTA of a pair loads half of the B tile
+  if ((rc = make_map(ctx, &mAh, Ahi, Kp, Mrows, kBM)) != KITE_OK) return rc;
+  if ((rc = make_map(ctx, &mAl, Alo, Kp, Mrows, kBM)) != KITE_OK) return rc;
+  if ((rc = make_map(ctx, &mBh, Bhi, Kp, Nrows, bbox)) != KITE_OK) return rc;
+  if ((rc = make_map(ctx, &mBl, Blo, Kp, Nrows, bbox)) != KITE_OK) return rc;
+  if (!mc) {
+    const int grid = std::min(a.items, ctx->num_sms);
+    k_gemm_split_bf16<false><<<grid, kGemmThreads, kGemmSmem, ctx->stream>>>(mAh, mAl, mBh, mBl, a);
+    KITE_CUDA_TRY(ctx, cudaGetLastError());
+    return KITE_OK;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kGemmThreads);
+  cfg.dynamicSmemBytes = kGemmSmem;
+  cfg.stream = ctx->stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (max_pairs < 0) {  // pairs that can be resident at once (SMs pair up within a GPC)
+    int n = 0;
+    cfg.gridDim = dim3((unsigned)(ctx->num_sms & ~1));
+    if (cudaOccupancyMaxActiveClusters(&n, k_gemm_split_bf16<true>, &cfg) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = ctx->num_sms / 2;
+    }
+    max_pairs = n;
+  }
+  const int pairs = std::max(1, std::min(a.items / 2, std::min(max_pairs, ctx->num_sms / 2)));
+  cfg.gridDim = dim3((unsigned)(2 * pairs));
+  KITE_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, k_gemm_split_bf16<true>, mAh, mAl, mBh, mBl, a));
   return KITE_OK;
 }
 
