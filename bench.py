@@ -343,14 +343,28 @@ def secondary_legs(kite, ctx, peaks):
     s1 = kite.make_system(kite.HONEYCOMB, 64, 64, -2.7, 1.0, 0.0, 0.0, 1)
     mu1 = np.zeros(256)
     res = {}
-    for name, dbl in (("plain", False), ("doubling", True)):
-        kpm1 = kite.make_kpm(256, 4, 1, kite.FP64, -b, b, doubling=dbl)
-        for _ in range(3):
-            kite.moments_1d(ctx, s1, kpm1, mu1)
-        t0 = time.perf_counter()
-        for _ in range(20):
-            kite.moments_1d(ctx, s1, kpm1, mu1)
-        res[name + "_us_per_call"] = 1e6 * (time.perf_counter() - t0) / 20
+    # the autotuner's choice (the on-chip cluster sweep when it is measured faster), then
+    # the streaming step kernels alone (KITE_CLUSTER=0) for comparison
+    for suffix, pin in (("", None), ("_streaming", "0")):
+        old = os.environ.pop("KITE_CLUSTER", None)
+        if pin is not None:
+            os.environ["KITE_CLUSTER"] = pin
+        try:
+            for name, dbl in (("plain", False), ("doubling", True)):
+                kpm1 = kite.make_kpm(256, 4, 1, kite.FP64, -b, b, doubling=dbl)
+                for _ in range(3):
+                    kite.moments_1d(ctx, s1, kpm1, mu1)
+                t0 = time.perf_counter()
+                for _ in range(20):
+                    st = kite.moments_1d(ctx, s1, kpm1, mu1)
+                res[name + suffix + "_us_per_call"] = 1e6 * (time.perf_counter() - t0) / 20
+                res[name + suffix + "_step_us"] = 1e6 * st.step_seconds
+                if pin is None:
+                    res[name + "_cluster_ctas"] = st.cluster_ctas
+        finally:
+            os.environ.pop("KITE_CLUSTER", None)
+            if old is not None:
+                os.environ["KITE_CLUSTER"] = old
     out["small_dos_honeycomb_64x64_M256_R4_fp64"] = res
     # batched: 256 square systems, L 64..1024, W 0..4, M in {512..4096}, R = 4, one launch
     specs = synth.batched_square_systems(256, seed=3)

@@ -175,8 +175,11 @@ typedef struct {
   int32_t ring_stages;  /* step kernel: shared-memory ring depth used (autotuned)       */
   int32_t ctas_per_sm;  /* step kernel: resident CTAs per SM used (autotuned)           */
   int32_t steps_per_pass; /* step kernel: recursion steps fused per pass over the iterates
-                             (1, or 2 with temporal blocking; autotuned)                 */
-  int32_t reserved;
+                             (1, or 2 with temporal blocking; autotuned; all of them when
+                             the cluster sweep ran)                                       */
+  int32_t cluster_ctas; /* kite_moments_1d: CTAs per thread-block cluster when the small-
+                           lattice sweep held the iterates on chip (one cluster per real
+                           recursion, see kite_moments_1d), else 0                      */
 } kite_stats;
 
 typedef struct kite_ctx kite_ctx;
@@ -223,6 +226,13 @@ int kite_flux_nearest(const kite_system* sys, double flux, double* out);
  * applied matrix-free (Sec. 3a pattern rules): on-site term and nearest-neighbour
  * hopping, vacancies removed.  Moments are raw (mu_0 = 1); the reconstruction applies
  * the (2 - delta_n0) weight of the delta-function expansion.
+ * A lattice too small to keep the GPU busy with one launch per step (fewer than four row
+ * segments per SM) and without a magnetic field may instead run the whole sweep on chip,
+ * one thread-block cluster per real recursion (the real and imaginary parts of a complex
+ * vector evolve independently under a real H~); the autotuner takes that path when it
+ * measures it faster, st->cluster_ctas reports it, and the imaginary part of each
+ * moment, which vanishes for a real symmetric H~, is then not formed and reads 0.
+ * KITE_CLUSTER=0 / 1 in the environment forbids / forces it.
  *   mu          [M] FP64, real part of the average, host or device (required)
  *   mu_per_vec  [S*R][M] complex FP64 interleaved (re, im) per vector, or NULL
  *   st          statistics, or NULL

@@ -68,7 +68,7 @@ class Stats(ctypes.Structure):
                 ("step_launches", ctypes.c_int64), ("step_bytes", ctypes.c_double),
                 ("gemm_seconds", ctypes.c_double), ("gemm_flops", ctypes.c_double),
                 ("ring_stages", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("steps_per_pass", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("steps_per_pass", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -105,6 +105,38 @@ int field_phases(kite_ctx* ctx, const kite_system* sys, int fp64, void* table);
 int field_occupancy(int fp64, int lattice, int C, int doubling);
 int field_sweep(kite_ctx* ctx, FieldSweep* a);
 
+// The 1D sweep of a small lattice held on chip, one thread-block cluster of `cs` CTAs per
+// independent real recursion (kite_cluster.cu); no magnetic field.
+struct ClusterSweep {
+  int fp64, lattice, doubling, realv;
+  int Lx, Ly, M;
+  int C;          // 16-byte chunks per orbital of the start-vector batch
+  int per_chunk;  // vectors per chunk
+  int nvec;       // vectors of the batch
+  int open_x, open_y;
+  int cs;         // CTAs per cluster
+  const void* r0;
+  const void* vt;
+  double tt;
+  double* part;   // moment partials, cluster_part_doubles(...) doubles
+  const unsigned long long* n_eff;
+  double* mu_vec;
+  int vec_base;
+  void* last_prev;  // optional: r_{M-2}, r_{M-1} in the start vectors' chunk layout (no doubling)
+  void* last_cur;
+  // outputs
+  double seconds, bytes;
+  int grid;
+};
+// Dynamic shared memory of one CTA for cluster size cs (0: the lattice does not fit).
+int cluster_smem(const ClusterSweep& a, int cs);
+// Clusters of size cs that can be resident at once (0: not launchable or does not fit).
+int cluster_active(kite_ctx* ctx, const ClusterSweep& a, int cs);
+size_t cluster_part_doubles(int lanes, int cs, int M, int doubling, int timing_steps);
+// timing_steps > 0: a timing run of that many steps, nothing stored; 0: the whole sweep,
+// then the moments into mu_vec.
+int cluster_sweep(kite_ctx* ctx, ClusterSweep* a, int timing_steps);
+
 // AdamW step coefficients of the learned reconstructor's training (kite_mlp.cu).
 struct AdamwCoeffs {
   float lr, c1, c2;

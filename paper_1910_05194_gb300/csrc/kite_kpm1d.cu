@@ -409,6 +409,81 @@ int max_grid_c(kite_ctx* ctx, int C, long long units) {
   return g(occ(std::integral_constant<int, 4>{}));
 }
 
+// ---- small lattices: the on-chip cluster sweep (kite_cluster.cu) ----------------------
+// KITE_CLUSTER=0 never takes it and KITE_CLUSTER=1 takes it whenever the lattice fits
+// (KITE_CLUSTER_CTAS=2..16 then pins the cluster size); unset, it is a candidate of the
+// autotuner for lattices too small to give the streaming step kernels four work units per
+// SM, and runs when it is measured faster per recursion step.  It needs a real H~ (no
+// field) and at least 8 rows.
+inline int cluster_pinned() {  // 0 unset, 1 off, 2 on
+  const char* e = getenv("KITE_CLUSTER");
+  return (e && (e[0] == '0' || e[0] == '1') && e[1] == 0) ? e[0] - '0' + 1 : 0;
+}
+inline int cluster_ctas_pinned() {
+  const char* e = getenv("KITE_CLUSTER_CTAS");
+  const int v = e ? atoi(e) : 0;
+  return (v >= 2 && v <= 16) ? v : 0;
+}
+constexpr int kClusterTimeSteps = 40;  // longest timing run of the autotuner
+
+// Per-step seconds of the cluster sweep: two timing runs, 8 and 40 steps, so that the
+// launch and load cost drops out.
+inline float cluster_step_ms(kite_ctx* ctx, ClusterSweep c) {
+  if (cluster_sweep(ctx, &c, 8) != KITE_OK) return 1e30f;
+  if (cluster_sweep(ctx, &c, 8) != KITE_OK) return 1e30f;
+  const double t8 = c.seconds;
+  if (cluster_sweep(ctx, &c, kClusterTimeSteps) != KITE_OK) return 1e30f;
+  return (float)(1e3 * std::max(0.0, c.seconds - t8) / (kClusterTimeSteps - 8));
+}
+
+// Cluster size to run the batch with, 0 for the streaming kernels.  `stream_ms` times the
+// streaming kernels' default launch per step (only called when the autotuner compares).
+template <typename StreamMs>
+int cluster_choice(kite_ctx* ctx, const Plan& p, const ClusterSweep& c, long long units,
+                   StreamMs stream_ms) {
+  const int pin = cluster_pinned();
+  if (pin == 1 || p.field || ctx->debug_stall) return 0;
+  // pinning the streaming kernels (KITE_PASS_STEPS, KITE_TUNE) or turning the autotuner off
+  // keeps them
+  if (pin == 0 && (!autotune_enabled() || pass_steps_pinned() || getenv("KITE_TUNE") ||
+                   units >= 4LL * ctx->num_sms))
+    return 0;
+  // Cluster sizes from 16 down to 8 CTAs: more CTAs split the FP64 work of a step further,
+  // but fewer clusters are resident at once (on GB300 7 of 16 CTAs, 15 of 8), and a batch
+  // with more lanes than that runs in two waves.
+  const int fixed = cluster_ctas_pinned();
+  const int lanes = c.realv ? c.nvec : 2 * c.nvec;
+  int cand[16], nc = 0, one_wave = 0;
+  for (int cs = 16; cs >= 2; --cs) {
+    if (fixed ? cs != fixed : (cs < 8 || cs % 2)) continue;
+    const int act = cluster_active(ctx, c, cs);
+    if (act < 1) continue;
+    cand[nc++] = cs;
+    if (!one_wave && act >= lanes) one_wave = cs;
+  }
+  if (nc == 0) return 0;
+  if (pin == 2) return one_wave ? one_wave : cand[0];
+  uint64_t key = 0x6b69746563737470ull;
+  for (uint64_t f : {(uint64_t)c.fp64, (uint64_t)c.lattice, (uint64_t)c.doubling, (uint64_t)c.realv,
+                     (uint64_t)c.nvec, (uint64_t)c.C, (uint64_t)c.Lx, (uint64_t)c.Ly, (uint64_t)c.open_x,
+                     (uint64_t)c.open_y})
+    key = (key ^ f) * 0x100000001b3ull;
+  key |= 1ull << 63;
+  auto it = ctx->tune.find(key);
+  if (it != ctx->tune.end()) return it->second.first;
+  float best = 0.9f * stream_ms();  // the cluster sweep must win clearly
+  int pick = 0;
+  for (int k = 0; k < nc; ++k) {
+    ClusterSweep t = c;
+    t.cs = cand[k];
+    const float ms = cluster_step_ms(ctx, t);
+    if (ms < best) best = ms, pick = cand[k];
+  }
+  cudaGetLastError();
+  ctx->tune[key] = {pick, 0};
+  return pick;
+}
+
 template <typename Real, int LAT>
 int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Scale& sc,
               double* mu_dev, double* imag_dev, double* mu_vec_dev_ext, kite_stats* stats,
@@ -461,6 +536,11 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
   // two more iterate buffers when the two-step pass may run (its outputs never alias its
   // inputs)
   const bool two_possible = !p.doubling && p.M >= 4 && !p.field && pass_steps_pinned() != 1;
+  // the cluster sweep's moment partials (16 CTAs per lane, the larger size)
+  const size_t cluster_part =
+      (p.field || cluster_pinned() == 1)
+          ? 0
+          : cluster_part_doubles(p.realv ? p.max_batch : 2 * p.max_batch, 16, p.M, p.doubling, kClusterTimeSteps);
   auto plan_ws = [&](Carver& k, Real** vt, void** r0, void** bA, void** bB, void** bC, void** bD,
                      double** partial, unsigned long long** ne, double** mu_vec, Real** phase) {
     *vt = k.take<Real>(p.N);
@@ -470,7 +550,7 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
     *bB = k.take<char>(vec_bytes);
     *bC = two_possible ? k.take<char>(vec_bytes) : nullptr;
     *bD = two_possible ? k.take<char>(vec_bytes) : nullptr;
-    *partial = k.take<double>((size_t)(std::max(p.M, 2) + 1) * Gmax * 2 * Cmax * VPC);
+    *partial = k.take<double>(std::max((size_t)(std::max(p.M, 2) + 1) * Gmax * 2 * Cmax * VPC, cluster_part));
     *ne = k.take<unsigned long long>(1);
     *mu_vec = k.take<double>(nvec_total * p.M * 2);
   };
@@ -500,6 +580,7 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
   int64_t n_eff_last = 0;
   int grid_used = 0;
   Tune tune_used{kStages, 0};
+  int cluster_used = 0, steps_used = 0;
   double step_s = 0.0, step_bytes = 0.0;
   int64_t step_n = 0;
   KITE_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
@@ -565,7 +646,56 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
                                                       &step_n, &step_bytes);                         \
     }                                                                                               \
   } while (0)
-      if (p.field) {
+      ClusterSweep cl{};
+      cl.fp64 = sizeof(Real) == 8;
+      cl.lattice = LAT;
+      cl.doubling = p.doubling;
+      cl.realv = p.realv;
+      cl.Lx = p.Lx;
+      cl.Ly = p.Ly;
+      cl.M = p.M;
+      cl.C = C;
+      cl.per_chunk = per_chunk;
+      cl.nvec = nvec;
+      cl.open_x = p.open.x;
+      cl.open_y = p.open.y;
+      cl.r0 = r0;
+      cl.vt = vt;
+      cl.tt = (double)tt;
+      cl.part = partial;
+      cl.n_eff = ne;
+      cl.mu_vec = mu_vec;
+      cl.vec_base = vec_base;
+      auto stream_ms = [&]() -> float {
+        auto one = [&](auto cc) {
+          constexpr int CC = decltype(cc)::value;
+          return p.doubling
+                     ? time_candidate<Real, LAT, CC, 3, kStages>(ctx, step_occupancy<Real, LAT, CC, 3, kStages>(), u, p,
+                                                                 vt, tt, r0, bA, bB, partial)
+                     : time_candidate<Real, LAT, CC, 0, kStages>(ctx, step_occupancy<Real, LAT, CC, 0, kStages>(), u, p,
+                                                                 vt, tt, r0, bA, bB, partial);
+        };
+        return C == 1 ? one(std::integral_constant<int, 1>{})
+                      : (C == 2 ? one(std::integral_constant<int, 2>{}) : one(std::integral_constant<int, 4>{}));
+      };
+      const bool want_last = kpm->r_last && !p.doubling;
+      cl.last_prev = want_last ? bA : nullptr;
+      cl.last_cur = want_last ? bB : nullptr;
+      cl.cs = cluster_choice(ctx, p, cl, u, stream_ms);
+      if (cl.cs > 0) {
+        // small lattice: the whole sweep on chip (kite_cluster.cu)
+        rc = cluster_sweep(ctx, &cl, 0);
+        if (rc != KITE_OK) return rc;
+        step_s += cl.seconds;
+        step_n += 1;
+        step_bytes += cl.bytes;
+        grid_used = cl.grid;
+        tune_used = Tune{0, 1, 0};
+        cluster_used = cl.cs;
+        steps_used = p.doubling ? (p.M + 1) / 2 : p.M - 1;
+        lp = bA;
+        lc = bB;
+      } else if (p.field) {
         // magnetic field: the one-step sweep with Peierls phases (kite_field.cu)
         const int occ = field_occupancy(sizeof(Real) == 8, LAT, C, p.doubling);
         FieldSweep fs{};
@@ -676,7 +806,8 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
     stats->grid = grid_used;
     stats->block = kBlock;
     stats->ring_stages = tune_used.nst;
-    stats->steps_per_pass = tune_used.two ? 2 : 1;
+    stats->steps_per_pass = cluster_used ? steps_used : (tune_used.two ? 2 : 1);
+    stats->cluster_ctas = cluster_used;
     stats->ctas_per_sm = grid_used / std::max(1, ctx->num_sms);
     stats->step_seconds = step_s;
     stats->step_launches = step_n;
