@@ -127,6 +127,21 @@ int ensure_pinned(kite_ctx* ctx, size_t bytes) {
   return KITE_OK;
 }
 
+int ensure_aux(kite_ctx* ctx) {
+  if (ctx->aux) return KITE_OK;
+  if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess) {
+    ctx->aux = nullptr;
+    cudaGetLastError();
+    return fail(ctx, KITE_ERR_CUDA, "second stream");
+  }
+  if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, KITE_ERR_CUDA, "fork/join events");
+  }
+  return KITE_OK;
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -321,6 +336,12 @@ void kite_destroy(kite_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->aux) {
+    cudaStreamSynchronize(ctx->aux);
+    cudaStreamDestroy(ctx->aux);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->stage) cudaFree(ctx->stage);

@@ -31,6 +31,10 @@ struct kite_ctx {
   void* zeros = nullptr;
   size_t zeros_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+  // Second stream for independent launch sequences that run side by side (the 2D path's
+  // two vector families), with the events that fork it from and join it to `stream`.
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // Device status word: kernels set it (never trap) when a bounded wait gives up.
   int* d_status = nullptr;
   int debug_stall = 0;  // test hook, see kite_debug_stall_once
@@ -48,6 +52,8 @@ int cuda_fail(kite_ctx* ctx, cudaError_t e, const char* what);
 // Ensures at least `bytes` of device work space; returns KITE_OK / KITE_ERR_OOM.
 int ensure_ws(kite_ctx* ctx, size_t bytes);
 int ensure_pinned(kite_ctx* ctx, size_t bytes);
+// Creates the context's second stream and its fork/join events on first use.
+int ensure_aux(kite_ctx* ctx);
 // Device zeros of the system's open boundaries (one row of the widest cell, 128 bytes per
 // cell, plus a margin for narrow lattices): *out = null for a periodic lattice.
 int open_zeros(kite_ctx* ctx, const kite_system* sys, const void** out);

@@ -47,6 +47,13 @@ constexpr int kGemmFold = 16;   // sub-chunks summed in FP32 registers before FP
 constexpr int kGemmProducts = 4; // hi*hi + hi*lo + lo*hi + lo*lo
 // KITE_GEMM_PRODUCTS=3 drops lo*lo (a quarter less tensor work, a one-signed bias of up to
 // ~5e-6 relative on aligned products); the default keeps all four
+// The A and B families are independent recursions: by default their step launches run on
+// two streams side by side, so that one family's launch fills the ramp and tail of the
+// other's (KITE_FAM_STREAMS=1 keeps them in sequence on one stream).
+inline bool fam_two_streams() {
+  const char* e = getenv("KITE_FAM_STREAMS");
+  return !(e && e[0] == '1' && e[1] == 0);
+}
 inline int gemm_products() {
   const char* e = getenv("KITE_GEMM_PRODUCTS");
   return (e && e[0] == '3' && e[1] == 0) ? 3 : kGemmProducts;
@@ -144,7 +151,8 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
   const size_t vec_bytes = (size_t)ncell * SORB * C * 16;
   const size_t famA = (size_t)M * Kp, famB = (size_t)2 * M * Kp;  // bf16 elements per array
 
-  auto layout = [&](Carver& k, float** vt, void** r0, void** bA, void** bB,
+  const bool two = fam_two_streams();
+  auto layout = [&](Carver& k, float** vt, void** r0, void** bA, void** bB, void** bC, void** bD,
                     __nv_bfloat16** Ah, __nv_bfloat16** Al, __nv_bfloat16** Bh,
                     __nv_bfloat16** Bl, double** part, unsigned long long** ne, float** ph) {
     *vt = k.take<float>(N);
@@ -152,6 +160,9 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
     *r0 = k.take<char>(vec_bytes);
     *bA = k.take<char>(vec_bytes);
     *bB = k.take<char>(vec_bytes);
+    // the B family's own iterates when the families run side by side
+    *bC = two ? k.take<char>(vec_bytes) : *bA;
+    *bD = two ? k.take<char>(vec_bytes) : *bB;
     for (int v = 0; v < VB; ++v) {
       Ah[v] = k.take<__nv_bfloat16>(famA);
       Al[v] = k.take<__nv_bfloat16>(famA);
@@ -162,19 +173,23 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
     *ne = k.take<unsigned long long>(1);
   };
   float* vt;
-  void *r0, *bA, *bB;
+  void *r0, *bA, *bB, *bC, *bD;
   __nv_bfloat16 *Ah[VB], *Al[VB], *Bh[VB], *Bl[VB];
   double* part;
   unsigned long long* ne;
   float* ph;
   {
     Carver probe(nullptr);
-    layout(probe, &vt, &r0, &bA, &bB, Ah, Al, Bh, Bl, &part, &ne, &ph);
+    layout(probe, &vt, &r0, &bA, &bB, &bC, &bD, Ah, Al, Bh, Bl, &part, &ne, &ph);
     int rc = ensure_ws(ctx, probe.used());
     if (rc != KITE_OK) return rc;
   }
   Carver w(ctx->ws);
-  layout(w, &vt, &r0, &bA, &bB, Ah, Al, Bh, Bl, &part, &ne, &ph);
+  layout(w, &vt, &r0, &bA, &bB, &bC, &bD, Ah, Al, Bh, Bl, &part, &ne, &ph);
+  if (two) {
+    const int rc = ensure_aux(ctx);
+    if (rc != KITE_OK) return rc;
+  }
   cudaStream_t st = ctx->stream;
   if (FIELD) {
     int rc = field_phases(ctx, sys, 0, ph);
@@ -258,6 +273,13 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
                                                          k0, k1, r0_in, N, r0);
       KITE_CUDA_TRY(ctx, cudaGetLastError());
       KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, st));
+      // fork: the B family's launches go to the second stream once r_0 is written
+      cudaStream_t sb = st;
+      if (two) {
+        KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, st));
+        KITE_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+        sb = ctx->aux;
+      }
       // A family: a_0 = h~alpha r_0 (row 0, and the recursion's start vector in bB)
       fa.col = 0;
       k_velocity<LAT><<<blocks, 256, 0, st>>>(static_cast<const float4*>(r0),
@@ -276,22 +298,26 @@ int run_2d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const Sca
               nullptr, nullptr, ctx->d_status, 0, fa, 0, SeriesOut{}, ph, open);
       }
       // B family: recursion from r_0; step n writes b_n = h~beta r_n
-      auto whereB = [&](int n) -> void* { return n == 0 ? r0 : ((n & 1) ? bA : bB); };
+      auto whereB = [&](int n) -> void* { return n == 0 ? r0 : ((n & 1) ? bC : bD); };
       for (int n = 0; n + 1 < M; ++n) {
         fb.col = n;
         if (n == 0)
-          launch_pdl(k_step<float, LAT, C, true, 2, kFamStages, FIELD>, G, kBlock, SM, st,
+          launch_pdl(k_step<float, LAT, C, true, 2, kFamStages, FIELD>, G, kBlock, SM, sb,
               nullptr, whereB(0), whereB(1), nullptr, vt, tt, sys->Lx, sys->Ly, units, nullptr,
               nullptr, ctx->d_status, 0, fb, 0, SeriesOut{}, ph, open);
         else
-          launch_pdl(k_step<float, LAT, C, false, 2, kFamStages, FIELD>, G, kBlock, SM, st,
+          launch_pdl(k_step<float, LAT, C, false, 2, kFamStages, FIELD>, G, kBlock, SM, sb,
               whereB(n - 1), whereB(n), whereB(n + 1), nullptr, vt, tt, sys->Lx, sys->Ly, units,
               nullptr, nullptr, ctx->d_status, 0, fb, 0, SeriesOut{}, ph, open);
       }
       fb.col = M - 1;
-      k_velocity<LAT><<<blocks, 256, 0, st>>>(static_cast<const float4*>(whereB(M - 1)), nullptr, vt,
+      k_velocity<LAT><<<blocks, 256, 0, sb>>>(static_cast<const float4*>(whereB(M - 1)), nullptr, vt,
                                               sys->Lx, sys->Ly, 2, fb, ph, open.x, open.y);
       KITE_CUDA_TRY(ctx, cudaGetLastError());
+      if (two) {  // join: the contraction needs both families
+        KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_join, sb));
+        KITE_CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0));
+      }
       KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, st));
       // contraction, one vector at a time, accumulated in FP64
       KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
