@@ -163,7 +163,9 @@ typedef struct {
   double updates;       /* orbital * moment * vector updates done (N_eff*(M-1)*R*S)  */
   double bytes_moved;   /* algorithmic HBM bytes of the sweep (iterates read/written + on-site) */
   double gbps;          /* bytes_moved / seconds / 1e9                               */
-  double max_abs_imag;  /* max_n |Im mu_n| of the vector average (0 for exact H~)    */
+  double max_abs_imag;  /* max_n |Im mu_n| of the vector average (0 for exact H~; the
+                           FP64 sweeps and the on-chip cluster sweep do not form the
+                           imaginary part, which vanishes for a Hermitian H~, and read 0) */
   double e_min, e_max;  /* bounds used (eV)                                          */
   int64_t n_eff;        /* non-vacant orbitals of the last realisation               */
   int32_t grid, block;  /* launch shape of the sweep kernel                           */

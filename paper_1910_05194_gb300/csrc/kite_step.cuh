@@ -139,16 +139,22 @@ __global__ void k_init_r0(int64_t ncell, const Real* __restrict__ vt, int vec_ba
 //                       B(x,y) <- A(x,y), A(x-1,y+1), A(x,y+1)  (Listing 1 bonds).
 // Square neighbours: (x-1,y), (x+1,y), (x,y-1), (x,y+1).
 // ------------------------------------------------------------------------------------
-// Moment partial of one complex pair: (sr, si) += conj(a) b, as a chain of four fused
+// Moment partial of one complex pair: (sr, si) += conj(a) b, as a chain of fused
 // multiply-adds (one rounding per product and sum); every kernel that accumulates the
 // moments <r_0|r_n> uses it, so the one-step and the two-step sweeps give the same bits.
+// The FP64 sweeps, bound by GB300's FP64 pipe, form the real part only: the imaginary
+// part of <r|T_n(H~)|r> (and of <r_n|r_n>, <r_n|r_{n+1}>) vanishes for a Hermitian H~, so
+// si stays 0 and two of the update's fourteen FP64 operations go.  The FP32 sweeps keep
+// it (their ALU work is free under the HBM bound) as a rounding diagnostic.
 template <typename Acc, typename Real>
 __device__ __forceinline__ void cacc(Acc& sr, Acc& si, Real ar_, Real ai_, Real br_, Real bi_) {
   const Acc ar = ar_, ai = ai_, br = br_, bi = bi_;
   sr = rfma(ar, br, sr);
   sr = rfma(ai, bi, sr);
-  si = rfma(ar, bi, si);
-  si = rfma(-ai, br, si);
+  if constexpr (sizeof(Real) == 4) {
+    si = rfma(ar, bi, si);
+    si = rfma(-ai, br, si);
+  }
 }
 
 template <typename Real>
