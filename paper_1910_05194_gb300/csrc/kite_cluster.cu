@@ -26,7 +26,7 @@
 // (s = (n1 + n2) + n3 [+ n4]; h = fma(t~, s, V~ * r_n); r_{n+1} = fma(2, h, -r_{n-1});
 // vacancies 0), so the iterates are the same bits.  The moment of each step is summed per
 // thread over its sites, then over the 32 lanes of a warp by a transpose through shared
-// memory every 32 moments (one FP64 add per moment and thread instead of a shuffle tree),
+// memory every 16 moments (two FP64 adds per moment and thread instead of a shuffle tree),
 // and the per-warp sums go to global memory; one small kernel adds them in a fixed order
 // (deterministic) and divides by N_eff.
 //
@@ -36,6 +36,10 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <set>
+#include <tuple>
 
 #include "kite_device.cuh"
 #include "kite_internal.h"
@@ -43,10 +47,16 @@
 namespace kite {
 namespace {
 
-constexpr int kCBlock = 256;
+// 512 threads: one CTA per SM, so the SM's latency hiding (FP64 results, shared and
+// distributed shared memory) comes from the warps of this CTA alone
+#ifndef KITE_CLUSTER_BLOCK
+#define KITE_CLUSTER_BLOCK 512
+#endif
+constexpr int kCBlock = KITE_CLUSTER_BLOCK;
 constexpr int kCWarps = kCBlock / 32;
-constexpr int kWbStride = 33;  // doubles per moment row of a warp's transpose buffer
-constexpr int kWbBytes = kCWarps * 32 * kWbStride * 8;
+constexpr int kSlots = 16;     // moments per transpose of a warp's buffer
+constexpr int kWbStride = 33;  // doubles per moment row of a warp's transpose buffer (padded)
+constexpr int kWbBytes = kCWarps * kSlots * kWbStride * 8;
 
 template <typename Real>
 struct CAcc {
@@ -128,7 +138,7 @@ __global__ void __launch_bounds__(kCBlock, 1) k_cluster_sweep(const ClusterArgs<
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rowlen = a.Lx * SORB;
   const int cap = a.rows_max * rowlen;
-  double* wb = reinterpret_cast<double*>(smem) + warp * 32 * kWbStride;
+  double* wb = reinterpret_cast<double*>(smem) + warp * kSlots * kWbStride;
   Real* Z = reinterpret_cast<Real*>(smem + kWbBytes);  // r_0 (MODE 0)
   Real* B0 = Z + cap;                                  // r_n for even n
   Real* B1 = B0 + cap;                                 // r_n for odd n
@@ -157,8 +167,8 @@ __global__ void __launch_bounds__(kCBlock, 1) k_cluster_sweep(const ClusterArgs<
     __syncwarp();
   };
   auto emit = [&](int slot, Acc val) {
-    wb[(slot & 31) * kWbStride + lane] = (double)val;
-    if ((slot & 31) == 31) flush(slot - 31, 32);
+    wb[(slot % kSlots) * kWbStride + lane] = (double)val;
+    if (slot % kSlots == kSlots - 1) flush(slot - (kSlots - 1), kSlots);
   };
 
   // this CTA's rows of the lane's r_0 and of the on-site terms
@@ -188,10 +198,17 @@ __global__ void __launch_bounds__(kCBlock, 1) k_cluster_sweep(const ClusterArgs<
       return cur[rr * rowlen + ii];
     };
     Acc acc = Acc(0), acc2 = Acc(0);
-    auto site = [&](int o) {
+    // One site in two halves: the loads (neighbour sum, r_n, r_{n-1}, on-site term, r_0),
+    // then the arithmetic and the store.  Two sites per thread are loaded before either is
+    // stored, so that their shared-memory and FP64 latencies overlap.
+    struct In {
+      Real sum, me, pv, vo, z;
+    };
+    auto load = [&](int o) -> In {
       const int r = o / rowlen, i = o - r * rowlen;
       const int y = y0 + r;
-      const Real me = cur[o];
+      In q;
+      q.me = cur[o];
       Real n1, n2, n3, n4 = Real(0);
       if (LAT == KITE_HONEYCOMB) {
         const int x = i >> 1;
@@ -216,19 +233,39 @@ __global__ void __launch_bounds__(kCBlock, 1) k_cluster_sweep(const ClusterArgs<
         n3 = (a.open_y && y == 0) ? Real(0) : at(r - 1, x);
         n4 = (a.open_y && y == a.Ly - 1) ? Real(0) : at(r + 1, x);
       }
-      Real sum = radd(n1, n2);
-      sum = radd(sum, n3);
-      if (LAT == KITE_SQUARE) sum = radd(sum, n4);
-      const Real vo = V[o];
-      const Real h = rfma(a.tt, sum, rmul(vo, me));
-      const Real nx = n == 0 ? h : rfma(Real(2), h, -out[o]);
-      const Real w = is_vacancy(vo) ? Real(0) : nx;
+      q.sum = radd(n1, n2);
+      q.sum = radd(q.sum, n3);
+      if (LAT == KITE_SQUARE) q.sum = radd(q.sum, n4);
+      q.vo = V[o];
+      q.pv = n == 0 ? Real(0) : out[o];
+      q.z = MODE == 0 ? Z[o] : Real(0);
+      return q;
+    };
+    auto finish = [&](int o, const In& q) {
+      const Real h = rfma(a.tt, q.sum, rmul(q.vo, q.me));
+      const Real nx = n == 0 ? h : rfma(Real(2), h, -q.pv);
+      const Real w = is_vacancy(q.vo) ? Real(0) : nx;
       out[o] = w;
       if (MODE == 0) {
-        acc = rfma((Acc)Z[o], (Acc)w, acc);
+        acc = rfma((Acc)q.z, (Acc)w, acc);
       } else {
-        acc = rfma((Acc)me, (Acc)w, acc);
-        acc2 = rfma((Acc)me, (Acc)me, acc2);
+        acc = rfma((Acc)q.me, (Acc)w, acc);
+        acc2 = rfma((Acc)q.me, (Acc)q.me, acc2);
+      }
+    };
+    // sites f(k) for k = tid, tid + kCBlock, ... < cnt, two at a time
+    auto sweep = [&](int cnt, auto f) {
+      int k = tid;
+      for (; k + kCBlock < cnt; k += 2 * kCBlock) {
+        const int o1 = f(k), o2 = f(k + kCBlock);
+        const In q1 = load(o1);
+        const In q2 = load(o2);
+        finish(o1, q1);
+        finish(o2, q2);
+      }
+      if (k < cnt) {
+        const int o1 = f(k);
+        finish(o1, load(o1));
       }
     };
 #if KITE_CLUSTER_SPLIT
@@ -237,11 +274,11 @@ __global__ void __launch_bounds__(kCBlock, 1) k_cluster_sweep(const ClusterArgs<
     // while the other CTAs catch up.  The CTA barrier before the wait makes the interior
     // rows, written after the arrival, complete for this CTA's own next step.
     const int nb = (nr == 1 ? 1 : 2) * rowlen;
-    for (int k = tid; k < nb; k += kCBlock) site(k < rowlen ? k : (nr - 1) * rowlen + (k - rowlen));
+    sweep(nb, [&](int k) { return k < rowlen ? k : (nr - 1) * rowlen + (k - rowlen); });
     cluster_arrive();
-    for (int o = rowlen + tid; o < (nr - 1) * rowlen; o += kCBlock) site(o);
+    sweep((nr - 2) * rowlen, [&](int k) { return rowlen + k; });
 #else
-    for (int o = tid; o < count; o += kCBlock) site(o);
+    sweep(count, [&](int k) { return k; });
 #endif
     if (MODE == 0) {
       emit(n + 1, acc);
@@ -257,7 +294,7 @@ __global__ void __launch_bounds__(kCBlock, 1) k_cluster_sweep(const ClusterArgs<
 #endif
   }
   const int last = MODE == 0 ? a.steps : (a.steps > 0 ? 2 * a.steps - 1 : 0);
-  if ((last & 31) != 31) flush(last & ~31, (last & 31) + 1);
+  if (last % kSlots != kSlots - 1) flush(last - last % kSlots, last % kSlots + 1);
   if (a.last_cur) {  // the last two iterates (after the final barrier: nothing writes them)
     const Real* rc = (a.steps & 1) ? B1 : B0;
     const Real* rp = a.steps == 0 ? B0 : (((a.steps - 1) & 1) ? B1 : B0);
@@ -340,9 +377,19 @@ bool cluster_config(kite_ctx* ctx, const ClusterSweep& a, int cs, cudaLaunchConf
     return false;
   const int smem = std::min(227 * 1024, std::max(need, per_sm / 2 + 1024));
   *fn = kernel_for(a.fp64, a.lattice, a.doubling);
-  if (cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-      cudaFuncSetAttribute(*fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-    return false;
+  {
+    // the kernel attributes once per kernel and device (the shared-memory limit at its
+    // maximum: the launch's own request decides the occupancy)
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done.count({*fn, ctx->device})) {
+      if (cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess ||
+          cudaFuncSetAttribute(*fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        return false;
+      done.insert({*fn, ctx->device});
+    }
+  }
   const int lanes = a.realv ? a.nvec : 2 * a.nvec;
   *cfg = cudaLaunchConfig_t{};
   cfg->gridDim = dim3((unsigned)(lanes * cs), 1, 1);
@@ -368,10 +415,23 @@ int cluster_active(kite_ctx* ctx, const ClusterSweep& a, int cs) {
     cudaGetLastError();
     return 0;
   }
+  // resident clusters of this kernel, size and shared memory, cached per device
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, int, size_t>, int> cache;
+  const auto key = std::make_tuple(fn, ctx->device, cs, cfg.dynamicSmemBytes);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
   int active = 0;
   if (cudaOccupancyMaxActiveClusters(&active, fn, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
+  }
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = active;
   }
 #ifdef KITE_CLUSTER_PROBE
   fprintf(stderr, "cluster size %d: %d clusters resident, smem %zu\n", cs, active, cfg.dynamicSmemBytes);
