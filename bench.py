@@ -400,11 +400,11 @@ def secondary_legs(kite, ctx, peaks):
     kite.moments_1d(ctx, s2, kpm2, mu2)  # tunes
     st64 = kite.moments_1d(ctx, s2, kpm2, mu2)
     upd = st64.n_eff * 255.0 * WORKLOAD["R"]
-    # per update: the stencil (2 adds, 1 mul, 2 FMA per component) and the real part of the
-    # moment (2 FMA; the imaginary part vanishes for a Hermitian H~ and is not formed)
-    # = 2 * 7 + 4 = 18 FP64 flops in 12 FP64 operations
+    # per update: the stencil (2 adds and 2 FMA per component: 2t~ s + (2V~ r_n - r_{n-1}))
+    # and the real part of the moment (2 FMA; the imaginary part vanishes for a Hermitian H~
+    # and is not formed) = 2 * 6 + 4 = 16 FP64 flops in 10 FP64 operations
     gbs = st64.step_bytes / st64.step_seconds / 1e9
-    tfl = 18.0 * upd / st64.step_seconds / 1e12
+    tfl = 16.0 * upd / st64.step_seconds / 1e12
     out["large_dos_honeycomb_4096x4096_M256_R8_fp64"] = {
         "updates_per_s": upd / st64.step_seconds, "step_seconds": st64.step_seconds,
         "hbm_gbs": gbs, "hbm_frac": gbs / peaks.get("hbm_gbs", 6800.0), "fp64_tflops": tfl,

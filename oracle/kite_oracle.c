@@ -506,10 +506,13 @@ int orc_moments_1d(const orc_system* sys, int realisation, int M, int R, double 
 /*   s  = (nb1 + nb2) + nb3  [+ nb4 on the square lattice], neighbours in the order */
 /*        of orc_neighbours_dx, vacant neighbours and absent bonds (open boundaries) */
 /*        read as zero;                                                              */
-/*   h  = fma(t~, s, V~ * r_self)          (one rounding for the product V~*r);      */
-/*   r1 = h;   r_{n+1} = fma(2, h, -r_{n-1});   vacant orbitals stay exactly zero.   */
-/* V~ and t~ are computed in FP64 and rounded once to the working precision; start  */
-/* vectors are rounded once.  Moments are accumulated in FP64 (order-free).          */
+/*   r_1     = fma(t~, s, V~ * r_self)     (one rounding for the product V~*r);     */
+/*   r_{n+1} = fma(2t~, s, fma(2V~, r_self, -r_{n-1}))  for n >= 1,                  */
+/* i.e. Eq. e6's 2 H~ r_n - r_{n-1} with the factor 2 taken into t~ and V~ (exact    */
+/* in binary floating point) and the subtraction fused with the on-site product;   */
+/* vacant orbitals stay exactly zero.  V~ and t~ are computed in FP64 and rounded   */
+/* once to the working precision; start vectors are rounded once.  Moments are     */
+/* accumulated in FP64 (order-free).                                                 */
 /* ------------------------------------------------------------------------------ */
 #define ORC_REPLICA(REAL, FMA)                                                               \
   static void orc_replica_step_##REAL(const orc_ham* h, REAL tt, const REAL* vt,            \
@@ -527,9 +530,13 @@ int orc_moments_1d(const orc_system* sys, int realisation, int M, int R, double 
                    (q[1] < 0 ? (REAL)0 : cur[2 * q[1] + c]);                                 \
           s = s + (q[2] < 0 ? (REAL)0 : cur[2 * q[2] + c]);                                  \
           if (h->Z == 4) s = s + (q[3] < 0 ? (REAL)0 : cur[2 * q[3] + c]);                   \
-          REAL p = vt[o] * cur[2 * o + c];                                                   \
-          REAL hv = FMA(tt, s, p);                                                           \
-          v = first ? hv : FMA((REAL)2, hv, -prev[2 * o + c]);                               \
+          if (first) {                                                                       \
+            REAL p = vt[o] * cur[2 * o + c];                                                 \
+            v = FMA(tt, s, p);                                                               \
+          } else {                                                                           \
+            REAL tt2 = tt + tt, vt2 = vt[o] + vt[o];                                         \
+            v = FMA(tt2, s, FMA(vt2, cur[2 * o + c], -prev[2 * o + c]));                     \
+          }                                                                                  \
         }                                                                                    \
         out[2 * o + c] = v;                                                                  \
       }                                                                                      \
@@ -1038,9 +1045,13 @@ int orc_replica_window(const orc_system* sys, int realisation, int M, int R, dou
               REAL s = n1 + n2;                                                             \
               s = s + n3;                                                                   \
               if (Z == 4) s = s + (q[3] < 0 ? (REAL)0 : cur[2 * q[3] + cc]);                \
-              REAL p = (REAL)vt[l] * cur[2 * l + cc];                                       \
-              REAL hv = FMA(tr, s, p);                                                      \
-              v = n == 0 ? hv : FMA((REAL)2, hv, -prev[2 * l + cc]);                        \
+              REAL vr = (REAL)vt[l];                                                        \
+              if (n == 0) {                                                                 \
+                v = FMA(tr, s, vr * cur[2 * l + cc]);                                       \
+              } else {                                                                      \
+                REAL tr2 = tr + tr, vr2 = vr + vr;                                          \
+                v = FMA(tr2, s, FMA(vr2, cur[2 * l + cc], -prev[2 * l + cc]));              \
+              }                                                                             \
             }                                                                               \
             nxt[2 * l + cc] = v;                                                            \
           }                                                                                 \

@@ -23,8 +23,8 @@
 //     reads the r_n that the next step overwrites.
 //
 // The site update is the streaming kernels' own rounding sequence, component by component
-// (s = (n1 + n2) + n3 [+ n4]; h = fma(t~, s, V~ * r_n); r_{n+1} = fma(2, h, -r_{n-1});
-// vacancies 0), so the iterates are the same bits.  The moment of each step is summed per
+// (s = (n1 + n2) + n3 [+ n4]; r_1 = fma(t~, s, V~ * r_0); r_{n+1} = fma(2t~, s, fma(2V~,
+// r_n, -r_{n-1})); vacancies 0), so the iterates are the same bits.  The moment of each step is summed per
 // thread over its sites, then over the 32 lanes of a warp by a transpose through shared
 // memory every 16 moments (two FP64 adds per moment and thread instead of a shuffle tree),
 // and the per-warp sums go to global memory; one small kernel adds them in a fixed order
@@ -40,6 +40,7 @@
 #include <mutex>
 #include <set>
 #include <tuple>
+#include <type_traits>
 
 #include "kite_device.cuh"
 #include "kite_internal.h"
@@ -108,7 +109,7 @@ __device__ __forceinline__ int row0_of(int c, int Ly, int n) { return c * (Ly / 
 template <typename Real>
 struct ClusterArgs {
   const Real* r0;  // the batch's start vectors, 16-byte chunks, C per orbital
-  const Real* vt;  // rescaled on-site term per orbital, NaN at a vacancy
+  const Real* vt;  // twice the rescaled on-site term per orbital, NaN at a vacancy
   Real tt;         // rescaled hopping
   int Lx, Ly, C;
   int per_chunk;   // vectors per chunk (complex: 2 FP32 / 1 FP64; real: 4 / 2)
@@ -187,7 +188,11 @@ __global__ void __launch_bounds__(kCBlock, 1) k_cluster_sweep(const ClusterArgs<
   const uint32_t p0 = cluster_addr(B0, prev), p1 = cluster_addr(B1, prev);
   const uint32_t q0 = cluster_addr(B0, next), q1 = cluster_addr(B1, next);
   const uint32_t prow = (uint32_t)(prev_last * rowlen * (int)sizeof(Real));
-  for (int n = 0; n < a.steps; ++n) {
+  const Real tt2 = a.tt + a.tt;  // exact
+  // one recursion step; the first (r_1 = H~ r_0) is its own instance so that the other
+  // steps carry no select between the two formulas
+  auto step = [&](auto first_tag, int n) {
+    constexpr bool FIRST = decltype(first_tag)::value;
     const Real* cur = (n & 1) ? B1 : B0;
     Real* out = (n & 1) ? B0 : B1;
     const uint32_t pc = ((n & 1) ? p1 : p0) + prow, qc = (n & 1) ? q1 : q0;
@@ -237,20 +242,21 @@ __global__ void __launch_bounds__(kCBlock, 1) k_cluster_sweep(const ClusterArgs<
       q.sum = radd(q.sum, n3);
       if (LAT == KITE_SQUARE) q.sum = radd(q.sum, n4);
       q.vo = V[o];
-      q.pv = n == 0 ? Real(0) : out[o];
+      q.pv = FIRST ? Real(0) : out[o];
       q.z = MODE == 0 ? Z[o] : Real(0);
       return q;
     };
     auto finish = [&](int o, const In& q) {
-      const Real h = rfma(a.tt, q.sum, rmul(q.vo, q.me));
-      const Real nx = n == 0 ? h : rfma(Real(2), h, -q.pv);
+      // r_1 = t~ s + V~ r_0; r_{n+1} = 2t~ s + (2V~ r_n - r_{n-1}) (V holds 2V~)
+      const Real nx = FIRST ? rfma(a.tt, q.sum, rmul(Real(0.5) * q.vo, q.me))
+                            : rfma(tt2, q.sum, rfma(q.vo, q.me, -q.pv));
       const Real w = is_vacancy(q.vo) ? Real(0) : nx;
       out[o] = w;
       if (MODE == 0) {
         acc = rfma((Acc)q.z, (Acc)w, acc);
       } else {
         acc = rfma((Acc)q.me, (Acc)w, acc);
-        acc2 = rfma((Acc)q.me, (Acc)q.me, acc2);
+        if (!FIRST) acc2 = rfma((Acc)q.me, (Acc)q.me, acc2);  // <r_0|r_0> is slot 0 already
       }
     };
     // sites f(k) for k = tid, tid + kCBlock, ... < cnt, two at a time
@@ -292,7 +298,9 @@ __global__ void __launch_bounds__(kCBlock, 1) k_cluster_sweep(const ClusterArgs<
 #else
     cluster_barrier();  // r_{n+1} complete everywhere; nobody reads r_n any more
 #endif
-  }
+  };
+  if (a.steps > 0) step(std::true_type{}, 0);
+  for (int n = 1; n < a.steps; ++n) step(std::false_type{}, n);
   const int last = MODE == 0 ? a.steps : (a.steps > 0 ? 2 * a.steps - 1 : 0);
   if (last % kSlots != kSlots - 1) flush(last - last % kSlots, last % kSlots + 1);
   if (a.last_cur) {  // the last two iterates (after the final barrier: nothing writes them)
@@ -306,27 +314,45 @@ __global__ void __launch_bounds__(kCBlock, 1) k_cluster_sweep(const ClusterArgs<
   }
 }
 
-// mu_vec[(vec_base + v)][n] = (sum over the vector's lanes, CTAs and warps of slot n) / N_eff
-// in a fixed order; with doubling, mu_n = 2 slot_n - slot_(n mod 2) for n >= 2.
-__global__ void k_cluster_reduce(const double* __restrict__ part, int lanes_per_vec, int nvec, int ncta,
-                                 int slots, int M, int doubling, int vec_base,
-                                 const unsigned long long* __restrict__ n_eff, double* __restrict__ mu_vec) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nvec * M) return;
-  const int v = idx / M, n = idx - v * M;
-  auto slot_sum = [&](int k) {
-    double s = 0.0;
-    for (int c = 0; c < lanes_per_vec; ++c)
-      for (int g = 0; g < ncta * kCWarps; ++g)
-        s += part[((size_t)(v * lanes_per_vec + c) * ncta * kCWarps + g) * slots + k];
-    return s;
-  };
-  double s = slot_sum(n);
-  if (doubling && n >= 2) s = 2.0 * s - slot_sum(n & 1);
-  const double ne = (double)*n_eff;
-  double* out = mu_vec + ((size_t)(vec_base + v) * M + n) * 2;
-  out[0] = ne > 0.0 ? s / ne : 0.0;
-  out[1] = 0.0;
+// mu_vec[(vec_base + v)][n] = (sum over the vector's lanes, CTAs and warps of slot n) / N_eff;
+// with doubling, mu_n = 2 slot_n - slot_(n mod 2) for n >= 2.  One block per (vector, n):
+// the FP64 adds are spread over the whole GPU (a thread per moment would leave them on a
+// few SMs of GB300's narrow FP64 pipe).  Fixed order: thread t adds terms t, t + 128, ...,
+// then a fixed butterfly within each warp and the four warp sums in order.
+constexpr int kRedBlock = 128;
+__global__ void __launch_bounds__(kRedBlock) k_cluster_reduce(const double* __restrict__ part, int lanes_per_vec,
+                                                              int ncta, int slots, int M, int doubling, int vec_base,
+                                                              const unsigned long long* __restrict__ n_eff,
+                                                              double* __restrict__ mu_vec) {
+  __shared__ double wsum[2][kRedBlock / 32];
+  const int v = blockIdx.y, n = blockIdx.x;
+  const int per_lane = ncta * kCWarps, terms = lanes_per_vec * per_lane;
+  const double* base = part + (size_t)v * terms * slots;  // the vector's lanes are adjacent
+  const bool two = doubling && n >= 2;
+  double s0 = 0.0, s1 = 0.0;
+  for (int g = threadIdx.x; g < terms; g += kRedBlock) {
+    s0 += base[(size_t)g * slots + n];
+    if (two) s1 += base[(size_t)g * slots + (n & 1)];
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, d);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, d);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    wsum[0][threadIdx.x >> 5] = s0;
+    wsum[1][threadIdx.x >> 5] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kRedBlock / 32; ++w) a += wsum[0][w], b += wsum[1][w];
+    const double sum = two ? 2.0 * a - b : a;
+    const double ne = (double)*n_eff;
+    double* out = mu_vec + ((size_t)(vec_base + v) * M + n) * 2;
+    out[0] = ne > 0.0 ? sum / ne : 0.0;
+    out[1] = 0.0;
+  }
 }
 
 template <typename Real, int LAT, int MODE>
@@ -478,9 +504,8 @@ int cluster_sweep(kite_ctx* ctx, ClusterSweep* a, int timing_steps) {
   KITE_CUDA_TRY(ctx, a->fp64 ? launch(double(), part) : launch(float(), part));
   KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, ctx->stream));
   if (timing_steps == 0) {
-    const int total = a->nvec * a->M;
-    k_cluster_reduce<<<(total + 255) / 256, 256, 0, ctx->stream>>>(
-        a->part, a->realv ? 1 : 2, a->nvec, cs, slots, a->M, a->doubling, a->vec_base, a->n_eff, a->mu_vec);
+    k_cluster_reduce<<<dim3((unsigned)a->M, (unsigned)a->nvec), kRedBlock, 0, ctx->stream>>>(
+        a->part, a->realv ? 1 : 2, cs, slots, a->M, a->doubling, a->vec_base, a->n_eff, a->mu_vec);
     KITE_CUDA_TRY(ctx, cudaGetLastError());
   }
   float ms = 0.f;

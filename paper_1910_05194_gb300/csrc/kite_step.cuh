@@ -51,7 +51,10 @@ __global__ void k_onsite(int64_t N, int lattice, double W, double half_delta, do
       v = __dadd_rn(v, (o & 1) == 0 ? half_delta : -half_delta);
     const bool vacant = (uint64_t)x.w[2] < vac_thr;
     const double vtil = __ddiv_rn(__dsub_rn(v, de_plus), de_minus);
-    vt[o] = vacant ? quiet_nan<Real>() : (Real)vtil;
+    // stored doubled, 2 V~ (exact: V~ is rounded once to the working precision first), the
+    // factor the recursion's 2 H~ r_n needs; the first step halves it back (exact again)
+    const Real vr = (Real)vtil;
+    vt[o] = vacant ? quiet_nan<Real>() : vr + vr;
     count += vacant ? 0u : 1u;
   }
   // integer sums are order independent: warp-aggregate, one atomic per warp
@@ -360,6 +363,7 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
   using Sh = StepShape<LAT, C, NST>;
   constexpr int VPC = Ch::kVecs, NR = Ch::kReals;
   constexpr int SORB = Sh::SORB, TPC = Sh::TPC, TX = Sh::TX, CELLB = Sh::CELLB;
+  const Real tt2 = tt + tt;  // exact
   constexpr int STG = Sh::template stage_bytes<MODE>();
   constexpr int QT = 2 * VPC;  // (re, im) per complex vector, or one value per real vector
   uint64_t* bars = ring.bars;
@@ -504,8 +508,9 @@ __device__ __forceinline__ bool step_body(Ring& ring, int cta, int ncta, const v
           Real sum = radd(n1.v[k], n2.v[k]);
           sum = radd(sum, n3.v[k]);
           if (LAT == KITE_SQUARE) sum = radd(sum, n4.v[k]);
-          const Real h = rfma(tt, sum, rmul(v, me.v[k]));
-          const Real o = FIRST ? h : rfma(Real(2), h, -pv.v[k]);
+          // r_1 = t~ s + V~ r_0; r_{n+1} = 2t~ s + (2V~ r_n - r_{n-1}) (v holds 2V~)
+          const Real o = FIRST ? rfma(tt, sum, rmul(Real(0.5) * v, me.v[k]))
+                               : rfma(tt2, sum, rfma(v, me.v[k], -pv.v[k]));
           out.v[k] = vacant ? Real(0) : o;
         }
         out.st(r_out, (((size_t)y * Lx + x0 + xl) * SORB + s) * C + c);

@@ -51,6 +51,7 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
   using Ch = Chunk<Real>;
   using Acc = typename AccT<Real>::T;
   using Sh = Step2Shape<LAT, C, NST>;
+  const Real tt2 = tt + tt;  // exact; the on-site terms vt hold 2 V~
   constexpr int VPC = Ch::kVecs, NR = Ch::kReals;
   constexpr int SORB = Sh::SORB, TPC = Sh::TPC, TX = Sh::TX, CELLB = Sh::CELLB;
   constexpr int QT = 2 * VPC;
@@ -155,18 +156,17 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         n4 = *reinterpret_cast<const Ch*>(dn + si * CELLB + choff);
       }
       // a vacancy (v is NaN) holds r = 0 exactly in every iterate, so with its hopping and
-      // on-site term zeroed h = +0 and fma(2, +0, -0) = +0: the same bits as forcing the
+      // on-site term zeroed fma(0, s, fma(0, +0, -0)) = +0: the same bits as forcing the
       // output to zero, with two selects per site instead of one per component
       const bool vacant = is_vacancy(v);
-      const Real ve = vacant ? Real(0) : v, te = vacant ? Real(0) : tt;
+      const Real ve = vacant ? Real(0) : v, te = vacant ? Real(0) : tt2;
       Ch out;
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
         Real sum = radd(n1.v[k], n2.v[k]);
         sum = radd(sum, n3.v[k]);
         if (LAT == KITE_SQUARE) sum = radd(sum, n4.v[k]);
-        const Real h = rfma(te, sum, rmul(ve, me.v[k]));
-        out.v[k] = rfma(Real(2), h, -pv.v[k]);
+        out.v[k] = rfma(te, sum, rfma(ve, me.v[k], -pv.v[k]));  // 2t~ s + (2V~ r_n - r_{n-1})
       }
       return out;
     };
@@ -191,18 +191,17 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
       }
       const Ch pv = *reinterpret_cast<const Ch*>(mid2 + (tx + 1) * CELLB + choff);  // r_n, own cell
       // a vacancy (v is NaN) holds r = 0 exactly in every iterate, so with its hopping and
-      // on-site term zeroed h = +0 and fma(2, +0, -0) = +0: the same bits as forcing the
+      // on-site term zeroed fma(0, s, fma(0, +0, -0)) = +0: the same bits as forcing the
       // output to zero, with two selects per site instead of one per component
       const bool vacant = is_vacancy(v);
-      const Real ve = vacant ? Real(0) : v, te = vacant ? Real(0) : tt;
+      const Real ve = vacant ? Real(0) : v, te = vacant ? Real(0) : tt2;
       Ch out;
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
         Real sum = radd(n1.v[k], n2.v[k]);
         sum = radd(sum, n3.v[k]);
         if (LAT == KITE_SQUARE) sum = radd(sum, n4.v[k]);
-        const Real h = rfma(te, sum, rmul(ve, me.v[k]));
-        out.v[k] = rfma(Real(2), h, -pv.v[k]);
+        out.v[k] = rfma(te, sum, rfma(ve, me.v[k], -pv.v[k]));  // 2t~ s + (2V~ r_n - r_{n-1})
       }
       return out;
     };
