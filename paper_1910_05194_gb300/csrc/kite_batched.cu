@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "kite_step.cuh"
+#include "kite_step2.cuh"
 
 namespace kite {
 namespace {
@@ -24,6 +25,8 @@ struct BSys {
   const void* r0;
   void* bA;
   void* bB;
+  void* bC;  // two more iterate buffers for the two-step pass (null without it)
+  void* bD;
   const float* vt;
   const float* phase;  // Peierls phases [Ly][sublattice][2 bonds][cos, sin] (field batches)
   double* partial;  // [max(M,2)][ncta][Q]
@@ -135,6 +138,71 @@ __global__ void __launch_bounds__(kBlock, 3)  // <= 85 registers: three CTAs fit
   }
 }
 
+// The batched sweep with temporal blocking (plain moments, no field), after a one-step
+// launch of k_batched has written every system's r_1 (and the moments 0, 1): passes of two
+// steps (r_{n-1}, r_n) -> (r_{n+1}, r_{n+2}) with the moments n+1, n+2 (the two-step body
+// of kite_step2.cuh) and a team barrier after each.  When r_1 .. r_last leaves an odd step,
+// the last pass also computes r_{last+1} (its moment lands in the spare slot M, unread), so
+// the kernel holds the two-step body alone.
+// Iterate k >= 1 lives in buffer k mod 4 so that a pass's outputs never alias its inputs.
+template <int LAT, int C, int NST>
+struct Batched2Shape {
+  static constexpr int SMEM = Step2Shape<LAT, C, NST>::SMEM;
+};
+
+// Two CTAs per SM: the per-system state that the persistent loop carries around the pass
+// costs registers that the one-launch-per-pass kernel takes from its parameters; squeezed
+// to three CTAs per SM (72 registers) it spills, and measured 1.35e11 against 2.23e11
+// updates/s on the 256-system square-lattice batch.
+#ifndef KITE_BATCHED2_MIN_CTAS
+#define KITE_BATCHED2_MIN_CTAS 2
+#endif
+template <int LAT, int C, int NST>
+__global__ void __launch_bounds__(kBlock2, KITE_BATCHED2_MIN_CTAS)
+    k_batched2(const BSys* __restrict__ systems, const BTeam* __restrict__ teams,
+               const int* __restrict__ order, const int* __restrict__ cta_team,
+               unsigned int* __restrict__ counters, int* __restrict__ err, int stall, int mcap) {
+  constexpr int Q = 2 * C * 2;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_abort;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NST; ++k) mbar_init(&bars[k], 1);
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  Ring ring{bars, smem + kBarBytes, &s_abort, 0};
+  const int team = cta_team[blockIdx.x];
+  const BTeam T = teams[team];
+  const int rank = blockIdx.x - T.cta0;
+  unsigned int arrived = 0;
+  auto sync_team = [&]() -> bool {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (T.ncta > 1) {
+      arrived += (unsigned int)T.ncta;
+      const bool skip = stall && team == 0 && rank == 0 && arrived == (unsigned int)T.ncta;
+      return team_barrier(counters + team, arrived, skip, err, &s_abort);
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    return true;
+  };
+  for (int i = 0; i < T.nsys; ++i) {
+    const BSys S = systems[order[T.sys0 + i]];
+    void* const bufs[4] = {S.bC, S.bA, S.bB, S.bD};
+    auto w4 = [&](int n) -> void* { return n == 0 ? const_cast<void*>(S.r0) : bufs[n & 3]; };
+    auto slot = [&](int k) { return S.partial + (size_t)k * T.ncta * Q; };
+    const int full = max(S.M - 1, 1);
+    const int last = mcap > 0 ? min(full, mcap) : full;  // iterates r_1 .. r_last
+    for (int n = 1; n + 1 <= last; n += 2) {
+      if (!step2_body<float, LAT, C, NST>(ring, rank, T.ncta, w4(n - 1), w4(n), w4(n + 1), w4(n + 2), S.r0,
+                                          S.vt, S.tt, S.Lx, S.Ly, S.units, slot(n + 1), slot(n + 2), err, 0))
+        return;
+      if (!sync_team()) return;
+    }
+  }
+}
+
 // mean over the vectors of slot k's real part, CTA partials summed in fixed order
 __device__ double slot_mean(const double* __restrict__ partial, int k, int G, int Q, int nvec, double ne) {
   double acc = 0.0;
@@ -215,8 +283,32 @@ Schedule plan_teams(const std::vector<double>& work, const std::vector<long long
 // schedule that fits that grid.
 struct BPlan {
   int nst = kStages, k = 0;
+  int two = 0;  // 1: the two-step kernel (k_batched2)
   Schedule sc;
 };
+
+// KITE_PASS_STEPS=1 or 2 pins one or two recursion steps per pass (as for kite_moments_1d)
+inline int batched_pass_steps_pinned() {
+  const char* e = getenv("KITE_PASS_STEPS");
+  return (e && (e[0] == '1' || e[0] == '2') && e[1] == 0) ? e[0] - '0' : 0;
+}
+
+template <int LAT, int C, int NST>
+int batched2_occupancy() {
+  static int occ = -1;
+  if (occ < 0) {
+    constexpr int SMEM = Batched2Shape<LAT, C, NST>::SMEM;
+    int o = 0;
+    if (SMEM > 227 * 1024 ||
+        cudaFuncSetAttribute(k_batched2<LAT, C, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batched2<LAT, C, NST>, kBlock2, SMEM) != cudaSuccess)
+      o = 0;
+    cudaGetLastError();
+    occ = o;
+  }
+  return occ;
+}
 
 template <int LAT, int C, bool DBL, int NST, bool FIELD>
 int batched_occupancy() {
@@ -265,6 +357,28 @@ cudaError_t launch_batched(kite_ctx* ctx, const BPlan& pl, const BSys* d_sys, co
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const int* cta_team = d_ints + pl.sc.order.size();
+  if constexpr (!DBL && !FIELD) {
+    if (pl.two) {
+      // every system's first step with the one-step kernel (capped at one step), then the
+      // passes; the team barrier counters start again from zero
+      cfg.dynamicSmemBytes = StepShape<LAT, C, 4>::template smem_bytes<0>();
+      cudaError_t ce = cudaLaunchKernelEx(&cfg, k_batched<LAT, C, false, 4, false>, d_sys, d_teams, d_ints, cta_team,
+                                          counters, ctx->d_status, stall, 1);
+      if (ce == cudaSuccess)
+        ce = cudaMemsetAsync(counters, 0, sizeof(unsigned int) * pl.sc.teams.size(), ctx->stream);
+      if (ce != cudaSuccess) return ce;
+      cfg.blockDim = dim3(kBlock2);
+      auto go = [&](auto nst) {
+        constexpr int NST = decltype(nst)::value;
+        cfg.dynamicSmemBytes = Batched2Shape<LAT, C, NST>::SMEM;
+        return cudaLaunchKernelEx(&cfg, k_batched2<LAT, C, NST>, d_sys, d_teams, d_ints, cta_team, counters,
+                                  ctx->d_status, 0, mcap);
+      };
+      return pl.nst == 5   ? go(std::integral_constant<int, 5>{})
+             : pl.nst == 6 ? go(std::integral_constant<int, 6>{})
+                           : go(std::integral_constant<int, 8>{});
+    }
+  }
   if (pl.nst == 4) {
     cfg.dynamicSmemBytes = StepShape<LAT, C, 4>::template smem_bytes<DBL ? 3 : 0>();
     return cudaLaunchKernelEx(&cfg, k_batched<LAT, C, DBL, 4, FIELD>, d_sys, d_teams, d_ints, cta_team, counters,
@@ -297,17 +411,40 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
   const int occ8 = batched_occupancy<LAT, C, DBL, 8, FIELD>(), occ4 = batched_occupancy<LAT, C, DBL, 4, FIELD>();
   if (occ8 < 1 && occ4 < 1) return fail(ctx, KITE_ERR_CUDA, "occupancy query for the batched kernel failed");
   const bool tune = autotune_enabled_batched() && count > 1;
-  for (int nst : {8, 4}) {
-    const int occ = nst == 8 ? occ8 : occ4;
-    for (int k = tune ? 1 : occ; k <= occ; ++k) {
-      if (!tune && nst == 4) break;
-      BPlan pl;
-      pl.nst = nst;
-      pl.k = k;
-      pl.sc = fit_schedule(work, units, ctx->num_sms * k);
-      cands.push_back(std::move(pl));
+  const int pin = batched_pass_steps_pinned();
+  // the two-step kernel: plain moments without a field, every system with M >= 4
+  bool two_ok = !DBL && !FIELD && pin != 1;
+  for (int i = 0; i < count; ++i) two_ok = two_ok && kpm[i].M >= 4;
+  if (pin != 2 || !two_ok) {
+    for (int nst : {8, 4}) {
+      const int occ = nst == 8 ? occ8 : occ4;
+      for (int k = tune ? 1 : occ; k <= occ; ++k) {
+        if (!tune && nst == 4) break;
+        BPlan pl;
+        pl.nst = nst;
+        pl.k = k;
+        pl.sc = fit_schedule(work, units, ctx->num_sms * k);
+        cands.push_back(std::move(pl));
+      }
     }
   }
+  if (two_ok && (tune || pin == 2)) {
+    for (int nst : {8, 6, 5}) {
+      const int occ = nst == 8 ? batched2_occupancy<LAT, C, 8>()
+                               : (nst == 6 ? batched2_occupancy<LAT, C, 6>() : batched2_occupancy<LAT, C, 5>());
+      // (the first-step launch runs the one-step kernel with four stages on the same grid)
+      for (int k = std::min(2, occ); k <= std::min(occ, occ4); ++k) {
+        BPlan pl;
+        pl.nst = nst;
+        pl.k = k;
+        pl.two = 1;
+        pl.sc = fit_schedule(work, units, ctx->num_sms * k);
+        cands.push_back(std::move(pl));
+      }
+    }
+  }
+  if (cands.empty()) return fail(ctx, KITE_ERR_CUDA, "no launch configuration of the batched kernel fits");
+  const bool has_two = std::any_of(cands.begin(), cands.end(), [](const BPlan& p) { return p.two != 0; });
   // work space: per system vt, three vector buffers, partials for the widest team any
   // candidate gives it, then counters and the schedule tables of the largest candidate
   std::vector<int> max_ncta(count, 1);
@@ -327,7 +464,7 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
         char* ph = k.take<char>(sizeof(float) * (size_t)sys[i].Ly * SORB * 4);
         if (record) off_ph[i] = (size_t)ph;
       }
-      char* b = k.take<char>(3 * vb);
+      char* b = k.take<char>((has_two ? 5 : 3) * vb);
       char* c = k.take<char>(sizeof(double) * (size_t)(std::max(kpm[i].M, 2) + 1) * max_ncta[i] * Q);
       if (record) {
         off_vt[i] = (size_t)a;
@@ -372,6 +509,8 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
     hs[i].r0 = vec;
     hs[i].bA = vec + vb;
     hs[i].bB = vec + 2 * vb;
+    hs[i].bC = has_two ? vec + 3 * vb : nullptr;
+    hs[i].bD = has_two ? vec + 4 * vb : nullptr;
     hs[i].partial = reinterpret_cast<double*>(off_part[i]);
     hs[i].tt = (float)(sys[i].t / scales[i].de_minus);
     hs[i].Lx = sys[i].Lx;
@@ -418,7 +557,11 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
   };
 
   // ---- autotune: time every candidate on this batch with capped steps -------------------
-  int pick = (int)cands.size() - 1;  // untuned: 8 stages at full occupancy
+  // untuned: 8 stages at full occupancy (the last one-step plan), or the pinned two-step one
+  int pick = 0;
+  for (int c = 0; c < (int)cands.size(); ++c)
+    if (!cands[c].two) pick = c;
+  if (cands[pick].two) pick = (int)cands.size() - 1;
   if (tune && cands.size() > 1) {
     double wmax = 0.0;
     for (double x : work) wmax = std::max(wmax, x);
@@ -426,33 +569,53 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
     while ((double)(1ULL << (b1 + 1)) <= total) ++b1;
     while ((double)(1ULL << (b2 + 1)) <= wmax) ++b2;
     const uint64_t key = ((uint64_t)2 << 56) | ((uint64_t)LAT << 48) | ((uint64_t)C << 40) | ((uint64_t)DBL << 36) |
-                         ((uint64_t)FIELD << 35) |
+                         ((uint64_t)FIELD << 35) | ((uint64_t)(two_ok ? 1 + (pin == 2) : 0) << 32) |
                          ((uint64_t)std::min(count, 4095) << 20) | ((uint64_t)b1 << 10) | (uint64_t)b2;
     auto it = ctx->tune.find(key);
     bool found = false;
     if (it != ctx->tune.end())
       for (int c = 0; c < (int)cands.size(); ++c)
-        if (cands[c].nst == it->second.first && cands[c].k == it->second.second) pick = c, found = true;
+        if ((cands[c].nst | (cands[c].two << 8)) == it->second.first && cands[c].k == it->second.second)
+          pick = c, found = true;
     if (!found) {
       KITE_CUDA_TRY(ctx, setup());
-      const int mcap = DBL ? 4 : 8;
-      float best = 1e30f;
-      for (int c = 0; c < (int)cands.size(); ++c) {
+      // one capped sweep of candidate c (the first launch warms up, the second is timed)
+      auto probe = [&](int c, int mcap, float* ms) -> int {
         if (upload(cands[c]) != KITE_OK) return KITE_ERR_CUDA;
-        float ms = 1e30f;
-        for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up
+        for (int rep = 0; rep < 2; ++rep) {
           KITE_CUDA_TRY(ctx, cudaMemsetAsync(counters, 0, sizeof(unsigned int) * cands[c].sc.teams.size(), st));
           KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
           cudaError_t ce = launch_batched<LAT, C, DBL, FIELD>(ctx, cands[c], d_sys, d_teams, d_ints, counters, 0, mcap);
           if (ce != cudaSuccess) return cuda_fail(ctx, ce, "autotune probe launch");
           KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
           KITE_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev3));
-          KITE_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev3));
+          KITE_CUDA_TRY(ctx, cudaEventElapsedTime(ms, ctx->ev2, ctx->ev3));
         }
+        return KITE_OK;
+      };
+      // every candidate on a short capped sweep; the best one-step and the best two-step
+      // plan are then compared per recursion step (a longer sweep minus the short one), since
+      // a short sweep over-weights the two-step kernel's single first step
+      const int mshort = DBL ? 4 : 8, mlong = 40;
+      float best1 = 1e30f, best2 = 1e30f;
+      int pick1 = -1, pick2 = -1;
+      for (int c = 0; c < (int)cands.size(); ++c) {
+        float ms = 1e30f;
+        if (probe(c, mshort, &ms) != KITE_OK) return KITE_ERR_CUDA;
         // prefer the deeper ring and the default occupancy on near-ties
-        if (ms < best * 0.98f) best = ms, pick = c;
+        if (cands[c].two) {
+          if (ms < best2 * 0.98f) best2 = ms, pick2 = c;
+        } else if (ms < best1 * 0.98f) {
+          best1 = ms, pick1 = c;
+        }
       }
-      ctx->tune[key] = {cands[pick].nst, cands[pick].k};
+      pick = pick1 >= 0 ? pick1 : pick2;
+      if (pick1 >= 0 && pick2 >= 0) {
+        float l1 = 1e30f, l2 = 1e30f;
+        if (probe(pick1, mlong, &l1) != KITE_OK || probe(pick2, mlong, &l2) != KITE_OK) return KITE_ERR_CUDA;
+        if (l2 - best2 < 0.97f * (l1 - best1)) pick = pick2;
+      }
+      ctx->tune[key] = {cands[pick].nst | (cands[pick].two << 8), cands[pick].k};
     }
   }
   const BPlan& pl = cands[pick];
@@ -512,22 +675,30 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
     for (int i = 0; i < count; ++i) {
       const double N = (double)sys[i].Lx * sys[i].Ly * SORB;
       upd += (double)ne_h[i] * kpm[i].M * R;
-      // per orbital and step: r_{n-1}, r_n (and r_0 without doubling) in, r_{n+1} out, on-site
-      bytes += ((DBL ? 3.0 : 4.0) * 8.0 * R + 4.0) * N * (DBL ? steps_of(kpm[i].M) : std::max(kpm[i].M - 1, 0));
+      if (pl.two) {
+        // first step: r_0 in, r_1 out; a pass: r_{n-1}, r_n, r_0 in, r_{n+1}, r_{n+2} out; the
+        // on-site term once per step or pass
+        // (an odd last step runs as a whole pass)
+        const int last = std::max(kpm[i].M - 1, 1), passes = last / 2;
+        bytes += (2.0 * 8.0 * R + 4.0) * N + passes * (5.0 * 8.0 * R + 4.0) * N;
+      } else {
+        // per orbital and step: r_{n-1}, r_n (and r_0 without doubling) in, r_{n+1} out, on-site
+        bytes += ((DBL ? 3.0 : 4.0) * 8.0 * R + 4.0) * N * (DBL ? steps_of(kpm[i].M) : std::max(kpm[i].M - 1, 0));
+      }
     }
     stats->seconds = 1e-3 * ms;
     stats->updates = upd;
     stats->bytes_moved = bytes;
     stats->gbps = ms > 0 ? bytes / (1e-3 * ms) * 1e-9 : 0.0;
     stats->grid = pl.sc.grid;
-    stats->block = kBlock;
+    stats->block = pl.two ? kBlock2 : kBlock;
     stats->step_seconds = 1e-3 * ms;
     stats->step_launches = 1;
     stats->step_bytes = bytes;
     stats->n_eff = (int64_t)ne_h[count - 1];
     stats->ring_stages = pl.nst;
     stats->ctas_per_sm = pl.k;
-    stats->steps_per_pass = 1;
+    stats->steps_per_pass = pl.two ? 2 : 1;
   }
   return KITE_OK;
 }
