@@ -463,8 +463,7 @@ int kite_moments_1d(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, 
                   "rescaled Hamiltonian is not inside [-1,1]");
     }
   }
-  cudaFreeAsync(out_dev, ctx->stream);
-  cudaStreamSynchronize(ctx->stream);
+  cudaFreeAsync(out_dev, ctx->stream);  // stream-ordered: the copies above have completed
   if (st) *st = local;
   return rc;
 }

@@ -775,6 +775,16 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
         }
       }
     }
+  }
+  {
+    const int nv = (int)nvec_total;
+    k_average<<<(p.M + 255) / 256, 256, 0, st>>>(mu_vec, nv, p.M, mu_dev, imag_dev);
+    KITE_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, st));
+  {
+    // one read-back for the whole call: the status word collects every realisation's
+    // bounded waits, and `ne` holds the last realisation's N_eff
     unsigned long long ne_host = 0;
     int status_host = 0;
     KITE_CUDA_TRY(ctx, cudaMemcpyAsync(&ne_host, ne, sizeof(ne_host), cudaMemcpyDeviceToHost, st));
@@ -784,13 +794,6 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
       return fail(ctx, KITE_ERR_TIMEOUT, "a bounded wait on a bulk copy gave up in the step kernel");
     n_eff_last = (int64_t)ne_host;
   }
-  {
-    const int nv = (int)nvec_total;
-    k_average<<<(p.M + 255) / 256, 256, 0, st>>>(mu_vec, nv, p.M, mu_dev, imag_dev);
-    KITE_CUDA_TRY(ctx, cudaGetLastError());
-  }
-  KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, st));
-  KITE_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev1));
   if (stats) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
