@@ -20,8 +20,10 @@ def ctx():
     c.close()
 
 
-def batch(ctx, specs, R=4, doubling=False):
-    systems = [kite.make_system(kite.SQUARE, sp["L"], sp.get("Ly", sp["L"]), -1.0, sp["W"], 0.0,
+def batch(ctx, specs, R=4, doubling=False, lattice=None):
+    lat = kite.SQUARE if lattice is None else lattice
+    t = -1.0 if lat == kite.SQUARE else -2.7
+    systems = [kite.make_system(lat, sp["L"], sp.get("Ly", sp["L"]), t, sp["W"], 0.0,
                                 sp.get("p", 0.0), sp["seed"]) for sp in specs]
     kpms = [kite.make_kpm(sp["M"], R, 1, kite.FP32, doubling=doubling) for sp in specs]
     mus = [np.zeros(sp["M"]) for sp in specs]
@@ -29,8 +31,10 @@ def batch(ctx, specs, R=4, doubling=False):
     return mus, st
 
 
-def oracle_mu(sp, R=4):
-    s = oracle.make_system(lattice=oracle.SQUARE, Lx=sp["L"], Ly=sp.get("Ly", sp["L"]), t=-1.0,
+def oracle_mu(sp, R=4, lattice=None):
+    lat = oracle.SQUARE if lattice is None else lattice
+    t = -1.0 if lat == oracle.SQUARE else -2.7
+    s = oracle.make_system(lattice=lat, Lx=sp["L"], Ly=sp.get("Ly", sp["L"]), t=t,
                            W=sp["W"], p_vac=sp.get("p", 0.0), seed=sp["seed"])
     return oracle.moments_1d(s, sp["M"], R).real.mean(0)
 
@@ -79,6 +83,24 @@ def test_mixed_batch_pinned_steps_per_pass(ctx, steps, monkeypatch):
     assert st.steps_per_pass == int(steps)
     for sp, mu in zip(specs, mus):
         assert np.max(np.abs(mu - oracle_mu(sp))) <= 1e-5, sp
+
+
+@pytest.mark.parametrize("steps,doubling,R", [("1", False, 8), ("2", False, 8), ("2", False, 3),
+                                              (None, True, 8)])
+def test_honeycomb_batch_against_oracle(ctx, steps, doubling, R, monkeypatch):
+    """A honeycomb batch (two sublattices per cell; R = 8: four chunks per orbital, R = 3:
+    a padded batch) with one or two steps per pass or moment doubling, vacancies, a
+    multi-CTA team and packed teams: every system within 1e-5 of the oracle."""
+    specs = [dict(L=300, Ly=200, W=2.0, M=64, seed=31, p=0.01), dict(L=24, Ly=9, W=1.0, M=33, seed=32),
+             dict(L=70, W=3.0, M=50, seed=33, p=0.02), dict(L=13, W=0.5, M=8, seed=34),
+             dict(L=45, Ly=30, W=1.5, M=97, seed=35)]
+    if steps is not None:
+        monkeypatch.setenv("KITE_PASS_STEPS", steps)
+    mus, st = batch(ctx, specs, R=R, doubling=doubling, lattice=kite.HONEYCOMB)
+    if steps is not None:
+        assert st.steps_per_pass == int(steps)
+    for sp, mu in zip(specs, mus):
+        assert np.max(np.abs(mu - oracle_mu(sp, R, lattice=oracle.HONEYCOMB))) <= 1e-5, sp
 
 
 def test_team_barrier_timeout_is_reported(ctx):
