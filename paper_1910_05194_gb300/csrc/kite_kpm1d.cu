@@ -24,6 +24,7 @@
 
 #include "kite_step.cuh"
 #include "kite_step2.cuh"
+#include "kite_step3.cuh"
 
 namespace kite {
 namespace {
@@ -239,6 +240,109 @@ int sweep_two(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, v
   return KITE_OK;
 }
 
+// Deeper temporal blocking: after the first step, each pass takes (r_{n-1}, r_n) to
+// (r_{n+2}, r_{n+3}) with the moments n+1 .. n+3 (r_{n+1} stays on chip); the last one or
+// two steps take the one-step kernel or the two-step pass.  Every launch runs on the same
+// grid (the partials of every moment have the same CTA count).
+template <typename Real, int LAT, int C, int NST3>
+int sweep_three(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, void* bA, void* bB,
+                void* bC, void* bD, double* partial, int G, long long units, int nvec, int vec_base,
+                const unsigned long long* n_eff, double* mu_vec, void** last_prev, void** last_cur,
+                double* step_seconds, int64_t* step_launches, double* step_bytes) {
+  constexpr int NST1 = 4, NST2 = 6;
+  constexpr int VPC = Chunk<Real>::kVecs;
+  constexpr int Q = 2 * C * VPC;
+  cudaStream_t st = ctx->stream;
+  const int M = p.M;
+  const double chunk_bytes = 16.0 * StepShape<LAT, C>::SORB * C * (double)p.ncell;
+  auto launch_bytes = [&](int vecs) { return vecs * chunk_bytes + (double)p.N * sizeof(Real); };
+  constexpr int SM1 = StepShape<LAT, C, NST1>::SMEM, SM2 = Step2Shape<LAT, C, NST2>::SMEM,
+                SM3 = Step3Shape<LAT, C, NST3>::SMEM;
+  step_occupancy<Real, LAT, C, 0, NST1>();  // sets the kernels' shared-memory limits
+  step2_occupancy<Real, LAT, C, NST2>();
+  step3_occupancy<Real, LAT, C, NST3>();
+  KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
+  auto slot = [&](int k) { return partial + (size_t)k * G * Q; };
+  // r_0 stays in its own buffer; the iterates move between the four others
+  void* prev = r0;
+  void* cur = bA;
+  void* spare[3] = {bB, bC, bD};
+  launch_pdl(k_step<Real, LAT, C, true, 0, NST1>, G, kBlock, SM1, st,
+      nullptr, r0, cur, r0, vt, tt, p.Lx, p.Ly, units, slot(1), slot(0), ctx->d_status, ctx->debug_stall,
+      FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr, p.open);
+  ctx->debug_stall = 0;
+  int64_t launches = 1;
+  double bytes = launch_bytes(2);
+  // buffers free for outputs: the spares, plus prev once it is no longer r_0
+  auto take_free = [&](void* keep1, void* keep2, void** o1, void** o2) {
+    void* cand[4] = {spare[0], spare[1], spare[2], prev};
+    int n = 0;
+    for (void* b : cand) {
+      if (!b || b == r0 || b == keep1 || b == keep2) continue;
+      if (n == 0) *o1 = b;
+      else if (n == 1) *o2 = b;
+      ++n;
+      if (n == 2) break;
+    }
+  };
+  auto rotate = [&](void* np, void* nc) {
+    // the new (prev, cur) pair; every other non-r_0 buffer is spare
+    void* all[4] = {bA, bB, bC, bD};
+    int k = 0;
+    for (void* b : all)
+      if (b != np && b != nc) spare[k++] = b;
+    if (k < 3) spare[2] = nullptr;
+    prev = np;
+    cur = nc;
+  };
+  int n = 1;  // r_n = cur
+  for (; n + 3 <= M - 1; n += 3, ++launches) {
+    void *o2 = nullptr, *o3 = nullptr;
+    take_free(prev, cur, &o2, &o3);
+    launch_pdl(k_step3<Real, LAT, C, NST3>, G, kBlock3, SM3, st,
+        prev, cur, o2, o3, r0, vt, tt, p.Lx, p.Ly, units, slot(n + 1), slot(n + 2), slot(n + 3),
+        ctx->d_status, p.realv ? 1 : 0);
+    bytes += launch_bytes(5);  // r_{n-1}, r_n, r_0 in; r_{n+2}, r_{n+3} out
+    rotate(o2, o3);
+  }
+  if (n + 2 <= M - 1) {
+    void *o1 = nullptr, *o2 = nullptr;
+    take_free(prev, cur, &o1, &o2);
+    launch_pdl(k_step2<Real, LAT, C, NST2>, G, kBlock2, SM2, st,
+        prev, cur, o1, o2, r0, vt, tt, p.Lx, p.Ly, units, slot(n + 1), slot(n + 2), ctx->d_status,
+        p.realv ? 1 : 0);
+    bytes += launch_bytes(5);
+    rotate(o1, o2);
+    n += 2;
+    ++launches;
+  } else if (n + 1 <= M - 1) {
+    void *o1 = nullptr, *o2 = nullptr;
+    take_free(prev, cur, &o1, &o2);
+    launch_pdl(k_step<Real, LAT, C, false, 0, NST1>, G, kBlock, SM1, st,
+        prev, cur, o1, r0, vt, tt, p.Lx, p.Ly, units, slot(n + 1), nullptr, ctx->d_status, 0, FamOut{},
+        p.realv ? 1 : 0, SeriesOut{}, nullptr, p.open);
+    bytes += launch_bytes(4);
+    rotate(cur, o1);
+    n += 1;
+    ++launches;
+  }
+  KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  const int total = M * Q;
+  k_reduce<<<(total + 255) / 256, 256, 0, st>>>(partial, M, G, Q, nvec, vec_base, n_eff, mu_vec,
+                                                 p.realv ? 1 : 0);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  float ms = 0.f;
+  KITE_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev3));
+  KITE_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev3));
+  *step_seconds += 1e-3 * ms;
+  *step_launches += launches;
+  *step_bytes += bytes;
+  *last_cur = cur;
+  *last_prev = prev;
+  return KITE_OK;
+}
+
 // ---- autotuner: ring depth x resident CTAs per SM ------------------------------------
 // Candidates are timed on the caller's own buffers, which the sweep overwrites afterwards:
 // a few non-first steps from two iterate buffers with r_{n+1} written over r_{n-1} (the
@@ -257,11 +361,11 @@ inline bool autotune_enabled() {
   return !(e && e[0] == '0');
 }
 
-// KITE_PASS_STEPS=1 or 2 pins the steps per pass of the plain moment sweep (the autotuner
-// then chooses only the ring depth and occupancy); unset, both are candidates.
+// KITE_PASS_STEPS=1, 2 or 3 pins the steps per pass of the plain moment sweep (the
+// autotuner then chooses only the ring depth and occupancy); unset, all are candidates.
 inline int pass_steps_pinned() {
   const char* e = getenv("KITE_PASS_STEPS");
-  return (e && (e[0] == '1' || e[0] == '2') && e[1] == 0) ? e[0] - '0' : 0;
+  return (e && (e[0] == '1' || e[0] == '2' || e[0] == '3') && e[1] == 0) ? e[0] - '0' : 0;
 }
 
 template <typename Real, int LAT, int C, int NST>
@@ -292,6 +396,36 @@ float time_candidate2(kite_ctx* ctx, int k, long long units, const Plan& p, cons
   if (cudaEventSynchronize(ctx->ev3) != cudaSuccess || cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev3) != cudaSuccess)
     return 1e30f;
   return ms / 6.0f;
+}
+
+template <typename Real, int LAT, int C, int NST>
+int step3_grid(kite_ctx* ctx, long long units, int ctas_per_sm = 0) {
+  const int occ = std::max(1, step3_occupancy<Real, LAT, C, NST>());
+  const int k = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+  return (int)std::max(1LL, std::min((long long)ctx->num_sms * k, units));
+}
+
+// Seconds per recursion step of the three-step pass: three launches = nine steps.
+template <typename Real, int LAT, int C, int NST>
+float time_candidate3(kite_ctx* ctx, int k, long long units, const Plan& p, const Real* vt, Real tt,
+                      void* r0, void* bA, void* bB, void* bC, void* bD, double* partial) {
+  constexpr int SMEM = Step3Shape<LAT, C, NST>::SMEM;
+  constexpr int Q = 2 * C * Chunk<Real>::kVecs;
+  const int G = step3_grid<Real, LAT, C, NST>(ctx, units, k);
+  cudaStream_t st = ctx->stream;
+  auto launch = [&]() {
+    launch_pdl(k_step3<Real, LAT, C, NST>, G, kBlock3, SMEM, st,
+        bA, bB, bC, bD, r0, vt, tt, p.Lx, p.Ly, units, partial + (size_t)2 * G * Q,
+        partial + (size_t)3 * G * Q, partial + (size_t)4 * G * Q, ctx->d_status, p.realv ? 1 : 0);
+  };
+  launch();  // warm-up
+  cudaEventRecord(ctx->ev2, st);
+  for (int i = 0; i < 3; ++i) launch();
+  cudaEventRecord(ctx->ev3, st);
+  float ms = 1e30f;
+  if (cudaEventSynchronize(ctx->ev3) != cudaSuccess || cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev3) != cudaSuccess)
+    return 1e30f;
+  return ms / 9.0f;
 }
 
 template <typename Real, int LAT, int C, int MODE, int NST>
@@ -331,13 +465,25 @@ Tune autotune(kite_ctx* ctx, long long units, const Plan& p, const Real* vt, Rea
               void* bB, void* bC, void* bD, double* partial) {
   const bool two_ok = two_step_allowed<MODE>(p);
   const bool two_only = two_ok && pass_steps_pinned() == 2;
+  // the three-step pass (at least one pass after the first step) runs only when pinned
+  // (KITE_PASS_STEPS=3 or KITE_TUNE=...x3): on GB300 it measured slower than the two-step
+  // pass wherever the two differ (2.5e11 against 3.2e11 updates/s on the 4096^2 workload:
+  // at two CTAs per SM its latency is not hidden), so the autotuner does not time it
+  const bool three_ok = two_ok && p.M >= 5;
+  const bool three_only = three_ok && pass_steps_pinned() == 3;
   Tune def{kStages, step_occupancy<Real, LAT, C, MODE, kStages>(), 0};
   if (two_only) def = Tune{5, std::max(1, step2_occupancy<Real, LAT, C, 5>()), 1};
-  // KITE_TUNE=<stages>x<CTAs per SM>[x2] pins one configuration (reproducible profiles):
-  // stages 4 or 8 (5, 6 or 8 for the two-step pass), x2 = the two-step pass
+  if (three_only) def = Tune{8, std::max(1, step3_occupancy<Real, LAT, C, 8>()), 2};
+  // KITE_TUNE=<stages>x<CTAs per SM>[x2|x3] pins one configuration (reproducible
+  // profiles): stages 4 or 8 (5, 6 or 8 for the two-step pass, 7 or 8 for the three-step
+  // pass), x2 / x3 = two / three steps per pass
   if (const char* e = getenv("KITE_TUNE")) {
     int nst = 0, k = 0, two = 1;
     if (sscanf(e, "%dx%dx%d", &nst, &k, &two) >= 2) {
+      if (two == 3 && three_ok) {
+        const int occ = nst == 7 ? step3_occupancy<Real, LAT, C, 7>() : nst == 8 ? step3_occupancy<Real, LAT, C, 8>() : 0;
+        if (occ > 0 && k >= 1) return Tune{nst, std::min(k, occ), 2};
+      }
       const bool t2 = two == 2 && two_ok;
       const int occ = t2 ? (nst == 5   ? step2_occupancy<Real, LAT, C, 5>()
                             : nst == 6 ? step2_occupancy<Real, LAT, C, 6>()
@@ -352,12 +498,13 @@ Tune autotune(kite_ctx* ctx, long long units, const Plan& p, const Real* vt, Rea
   while ((1LL << (bucket + 1)) <= units) ++bucket;
   const uint64_t key = ((uint64_t)1 << 56) | ((uint64_t)sizeof(Real) << 48) | ((uint64_t)LAT << 40) |
                        ((uint64_t)C << 32) | ((uint64_t)MODE << 24) | ((uint64_t)p.realv << 16) |
-                       ((uint64_t)(two_ok ? 1 + two_only : 0) << 20) | (uint64_t)bucket;
+                       ((uint64_t)(two_ok ? 1 + two_only : 0) << 20) |
+                       ((uint64_t)three_only << 22) | (uint64_t)bucket;
   auto it = ctx->tune.find(key);
   if (it != ctx->tune.end()) return Tune{it->second.first & 0xff, it->second.second, it->second.first >> 8};
   Tune best = def;
-  float best_ms = 1e30f;
-  if (!two_only) {
+  float best_ms = 1e30f, best2 = 1e30f;
+  if (!two_only && !three_only) {
     const int o8 = step_occupancy<Real, LAT, C, MODE, 8>(), o4 = step_occupancy<Real, LAT, C, MODE, 4>();
     for (int k = 1; k <= o8; ++k) {
       const float ms = time_candidate<Real, LAT, C, MODE, 8>(ctx, k, units, p, vt, tt, r0, bA, bB, partial);
@@ -368,11 +515,11 @@ Tune autotune(kite_ctx* ctx, long long units, const Plan& p, const Real* vt, Rea
       if (ms < best_ms * 0.98f) best_ms = ms, best = Tune{4, k, 0};  // prefer the deeper ring on a tie
     }
   }
-  if (two_ok) {
+  if (two_ok && !three_only) {
     // per-step time of the pass against the one-step kernels' (the pass must win clearly:
     // it needs two extra iterate buffers)
     const float bar = two_only ? 1e30f : 0.97f * best_ms;
-    float best2 = bar;
+    best2 = bar;
     const int o8 = step2_occupancy<Real, LAT, C, 8>(), o6 = step2_occupancy<Real, LAT, C, 6>(),
               o5 = step2_occupancy<Real, LAT, C, 5>();
     for (int k = 1; k <= o8; ++k) {
@@ -386,6 +533,18 @@ Tune autotune(kite_ctx* ctx, long long units, const Plan& p, const Real* vt, Rea
     for (int k = 1; k <= o5; ++k) {
       const float ms = time_candidate2<Real, LAT, C, 5>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
       if (ms < best2 * 0.98f) best2 = ms, best = Tune{5, k, 1};
+    }
+  }
+  if (three_only) {
+    float best3 = 1e30f;
+    const int o8 = step3_occupancy<Real, LAT, C, 8>(), o7 = step3_occupancy<Real, LAT, C, 7>();
+    for (int k = 1; k <= o8; ++k) {
+      const float ms = time_candidate3<Real, LAT, C, 8>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
+      if (ms < best3) best3 = ms, best = Tune{8, k, 2};
+    }
+    for (int k = 1; k <= o7; ++k) {
+      const float ms = time_candidate3<Real, LAT, C, 7>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
+      if (ms < best3 * 0.98f) best3 = ms, best = Tune{7, k, 2};
     }
   }
   cudaGetLastError();
@@ -618,7 +777,18 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
     Tune t = p.doubling ? autotune<Real, LAT, CC, 3>(ctx, u, p, vt, tt, r0, bA, bB, bC, bD, partial)  \
                         : autotune<Real, LAT, CC, 0>(ctx, u, p, vt, tt, r0, bA, bB, bC, bD, partial); \
     tune_used = t;                                                                                  \
-    if (t.two) {                                                                                    \
+    if (t.two == 2) {                                                                               \
+      const int G = t.nst == 7 ? step3_grid<Real, LAT, CC, 7>(ctx, u, t.k)                          \
+                               : step3_grid<Real, LAT, CC, 8>(ctx, u, t.k);                         \
+      grid_used = G;                                                                                \
+      auto run3 = [&](auto nst) {                                                                   \
+        return sweep_three<Real, LAT, CC, decltype(nst)::value>(ctx, p, vt, tt, r0, bA, bB, bC, bD,  \
+                                                                 partial, G, u, nvec, vec_base, ne,  \
+                                                                 mu_vec, &lp, &lc, &step_s, &step_n, \
+                                                                 &step_bytes);                       \
+      };                                                                                            \
+      rc = t.nst == 7 ? run3(std::integral_constant<int, 7>{}) : run3(std::integral_constant<int, 8>{}); \
+    } else if (t.two) {                                                                             \
       const int G = t.nst == 5   ? step2_grid<Real, LAT, CC, 5>(ctx, u, t.k)                        \
                     : t.nst == 6 ? step2_grid<Real, LAT, CC, 6>(ctx, u, t.k)                        \
                                  : step2_grid<Real, LAT, CC, 8>(ctx, u, t.k);                       \
@@ -809,7 +979,7 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
     stats->grid = grid_used;
     stats->block = kBlock;
     stats->ring_stages = tune_used.nst;
-    stats->steps_per_pass = cluster_used ? steps_used : (tune_used.two ? 2 : 1);
+    stats->steps_per_pass = cluster_used ? steps_used : tune_used.two + 1;
     stats->cluster_ctas = cluster_used;
     stats->ctas_per_sm = grid_used / std::max(1, ctx->num_sms);
     stats->step_seconds = step_s;
