@@ -186,6 +186,20 @@ typedef struct {
 
 typedef struct kite_ctx kite_ctx;
 
+/* ---- environment switches ---------------------------------------------------------
+ * Read at each call; none changes a result beyond FP32 regrouping of the moment sums
+ * (the iterates are the same bits whatever the launch shape).
+ *   KITE_AUTOTUNE=0       no timing of launch shapes: 8-stage rings at full occupancy, one
+ *                         recursion step per launch, no cluster sweep
+ *   KITE_TUNE=SxK[x2|x3]  pins the 1D sweep's ring depth S, CTAs per SM K and steps per pass
+ *   KITE_PASS_STEPS=1|2|3 pins the steps per pass (1D and batched sweeps; 3: 1D only)
+ *   KITE_CLUSTER=0|1      forbids / forces the on-chip cluster sweep of small lattices
+ *                         (KITE_CLUSTER_CTAS=2..16 pins its CTAs per cluster)
+ *   KITE_FAM_STREAMS=1    the 2D path's two vector families in sequence on one stream
+ *   KITE_FAM_CPS=K        CTAs per SM of the 2D family steps
+ *   KITE_GEMM_PRODUCTS=3  drops the lo x lo product of the split-BF16 contraction
+ *                         (a quarter less tensor work, ~5e-6 relative bias) */
+
 /* ---- context -------------------------------------------------------------------- */
 
 /* Creates a context on CUDA device `device`, bound to `cuda_stream` (a cudaStream_t;
