@@ -187,8 +187,9 @@ typedef struct {
 typedef struct kite_ctx kite_ctx;
 
 /* ---- environment switches ---------------------------------------------------------
- * Read at each call; none changes a result beyond FP32 regrouping of the moment sums
- * (the iterates are the same bits whatever the launch shape).
+ * Read at each call.  The iterates are the same bits whatever the launch shape, and the
+ * moments differ only by the regrouping of FP32 partial sums, except where noted (the
+ * cluster sweep reports the vanishing imaginary part as 0; KITE_GEMM_PRODUCTS=3).
  *   KITE_AUTOTUNE=0       no timing of launch shapes: 8-stage rings at full occupancy, one
  *                         recursion step per launch, no cluster sweep
  *   KITE_TUNE=SxK[x2|x3]  pins the 1D sweep's ring depth S, CTAs per SM K and steps per pass
