@@ -98,3 +98,24 @@ def test_full_size_panels_match_oracle(ctx):
     er, ec = np.max(np.abs(mu[rows, :] - pr)), np.max(np.abs(mu[:, cols] - pc))
     print(f"full-size panels: max|mu| {scale:.4e}, row error {er / scale:.2e}, column error {ec / scale:.2e}")
     assert er <= 1e-5 * scale and ec <= 1e-5 * scale
+
+
+def test_family_streams_do_not_change_the_moments(ctx, monkeypatch):
+    """The A and B families on two streams side by side (default) or in sequence on one
+    (KITE_FAM_STREAMS=1): independent recursions into separate buffers, so the moments are
+    bit-identical; R = 5 runs three vector batches (the fork and join every batch), S = 2
+    two realisations, and a context rebound to another stream keeps its second stream."""
+    d = dict(lattice=0, Lx=40, Ly=24, t=-2.7, W=1.5, p_vac=0.01, seed=9)
+    mu2, _ = run2d(ctx, d, 24, 5, S=2)
+    monkeypatch.setenv("KITE_FAM_STREAMS", "1")
+    mu1, _ = run2d(ctx, d, 24, 5, S=2)
+    assert np.array_equal(mu1, mu2)
+    monkeypatch.delenv("KITE_FAM_STREAMS")
+    torch = pytest.importorskip("torch")
+    s = torch.cuda.Stream()
+    ctx.set_stream(s.cuda_stream)
+    try:
+        mu3, _ = run2d(ctx, d, 24, 5, S=2)
+    finally:
+        ctx.set_stream(None)
+    assert np.array_equal(mu3, mu2)
