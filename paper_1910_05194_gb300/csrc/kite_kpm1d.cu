@@ -213,7 +213,7 @@ int sweep_two(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, v
     launch_pdl(k_step2<Real, LAT, C, NST2>, G, kBlock2, SM2, st,
         w4(n - 1), w4(n), w4(n + 1), w4(n + 2), r0, vt, tt, p.Lx, p.Ly, units,
         partial + (size_t)(n + 1) * G * Q,
-        partial + (size_t)(n + 2) * G * Q, ctx->d_status, p.realv ? 1 : 0);
+        partial + (size_t)(n + 2) * G * Q, ctx->d_status, p.realv ? 1 : 0, nullptr, nullptr);
     bytes += launch_bytes(5);  // r_{n-1}, r_n, r_0 in; r_{n+1}, r_{n+2} out
   }
   if (n + 1 <= M - 1) {
@@ -237,6 +237,65 @@ int sweep_two(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, v
   *step_bytes += bytes;
   *last_cur = w4(M - 1);
   *last_prev = w4(M - 2);
+  return KITE_OK;
+}
+
+// Temporal blocking of the doubling sweep: after the first step (r_1, slots 0 and 1), each
+// pass takes (r_{n-1}, r_n) to (r_{n+1}, r_{n+2}) with the slots 2n .. 2n+3; an odd
+// remainder takes one doubling step.  Four vector streams per two steps instead of six.
+template <typename Real, int LAT, int C, int NST2>
+int sweep_two_dbl(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0, void* bA, void* bB,
+                  void* bC, void* bD, double* partial, int G, long long units, int nvec, int vec_base,
+                  const unsigned long long* n_eff, double* mu_vec, void** last_prev, void** last_cur,
+                  double* step_seconds, int64_t* step_launches, double* step_bytes) {
+  constexpr int NST1 = 4;
+  constexpr int VPC = Chunk<Real>::kVecs;
+  constexpr int Q = 2 * C * VPC;
+  cudaStream_t st = ctx->stream;
+  const int M = p.M;
+  const int steps = steps_for(p);  // iterates r_1 .. r_steps
+  const double chunk_bytes = 16.0 * StepShape<LAT, C>::SORB * C * (double)p.ncell;
+  auto launch_bytes = [&](int vecs) { return vecs * chunk_bytes + (double)p.N * sizeof(Real); };
+  constexpr int SMD = StepShape<LAT, C, NST1>::SMEM_NR0, SM2 = Step2Shape<LAT, C, NST2, true>::SMEM;
+  step_occupancy<Real, LAT, C, 3, NST1>();  // sets the kernels' shared-memory limits
+  step2_occupancy<Real, LAT, C, NST2, true>();
+  KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev2, st));
+  void* bufs[4] = {bC, bA, bB, bD};
+  auto w4 = [&](int n) -> void* { return n == 0 ? r0 : bufs[n & 3]; };
+  auto slot = [&](int k) { return partial + (size_t)k * G * Q; };
+  launch_pdl(k_step<Real, LAT, C, true, 3, NST1>, G, kBlock, SMD, st,
+      nullptr, r0, w4(1), nullptr, vt, tt, p.Lx, p.Ly, units, slot(1), slot(0), ctx->d_status, ctx->debug_stall,
+      FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr, p.open);
+  ctx->debug_stall = 0;
+  int n = 1;
+  int64_t launches = 1;
+  double bytes = launch_bytes(2);  // r_0 in, r_1 out
+  for (; n + 2 <= steps; n += 2, ++launches) {
+    launch_pdl(k_step2<Real, LAT, C, NST2, true>, G, kBlock2, SM2, st,
+        w4(n - 1), w4(n), w4(n + 1), w4(n + 2), nullptr, vt, tt, p.Lx, p.Ly, units, slot(2 * n),
+        slot(2 * n + 1), ctx->d_status, p.realv ? 1 : 0, slot(2 * n + 2), slot(2 * n + 3));
+    bytes += launch_bytes(4);  // r_{n-1}, r_n in; r_{n+1}, r_{n+2} out
+  }
+  if (n + 1 <= steps) {
+    launch_pdl(k_step<Real, LAT, C, false, 3, NST1>, G, kBlock, SMD, st,
+        w4(n - 1), w4(n), w4(n + 1), nullptr, vt, tt, p.Lx, p.Ly, units, slot(2 * n + 1), slot(2 * n),
+        ctx->d_status, 0, FamOut{}, p.realv ? 1 : 0, SeriesOut{}, nullptr, p.open);
+    ++launches;
+    bytes += launch_bytes(3);
+  }
+  KITE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev3, st));
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  k_reduce<<<(M * Q + 255) / 256, 256, 0, st>>>(partial, M, G, Q, nvec, vec_base, n_eff, mu_vec,
+                                                 p.realv ? 1 : 0);
+  k_undouble<<<(nvec * M + 255) / 256, 256, 0, st>>>(mu_vec, M, nvec, vec_base);
+  KITE_CUDA_TRY(ctx, cudaGetLastError());
+  float ms = 0.f;
+  KITE_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev3));
+  KITE_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev3));
+  *step_seconds += 1e-3 * ms;
+  *step_launches += launches;
+  *step_bytes += bytes;
+  *last_cur = *last_prev = nullptr;
   return KITE_OK;
 }
 
@@ -310,7 +369,7 @@ int sweep_three(kite_ctx* ctx, const Plan& p, const Real* vt, Real tt, void* r0,
     take_free(prev, cur, &o1, &o2);
     launch_pdl(k_step2<Real, LAT, C, NST2>, G, kBlock2, SM2, st,
         prev, cur, o1, o2, r0, vt, tt, p.Lx, p.Ly, units, slot(n + 1), slot(n + 2), ctx->d_status,
-        p.realv ? 1 : 0);
+        p.realv ? 1 : 0, nullptr, nullptr);
     bytes += launch_bytes(5);
     rotate(o1, o2);
     n += 2;
@@ -368,25 +427,27 @@ inline int pass_steps_pinned() {
   return (e && (e[0] == '1' || e[0] == '2' || e[0] == '3') && e[1] == 0) ? e[0] - '0' : 0;
 }
 
-template <typename Real, int LAT, int C, int NST>
+template <typename Real, int LAT, int C, int NST, bool DBL = false>
 int step2_grid(kite_ctx* ctx, long long units, int ctas_per_sm = 0) {
-  const int occ = std::max(1, step2_occupancy<Real, LAT, C, NST>());
+  const int occ = std::max(1, step2_occupancy<Real, LAT, C, NST, DBL>());
   const int k = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
   return (int)std::max(1LL, std::min((long long)ctx->num_sms * k, units));
 }
 
-// Seconds per recursion step of the two-step pass: three launches = six steps.
-template <typename Real, int LAT, int C, int NST>
+// Seconds per recursion step of the two-step pass (DBL: its doubling form): three launches
+// = six steps.
+template <typename Real, int LAT, int C, int NST, bool DBL = false>
 float time_candidate2(kite_ctx* ctx, int k, long long units, const Plan& p, const Real* vt, Real tt,
                       void* r0, void* bA, void* bB, void* bC, void* bD, double* partial) {
-  constexpr int SMEM = Step2Shape<LAT, C, NST>::SMEM;
+  constexpr int SMEM = Step2Shape<LAT, C, NST, DBL>::SMEM;
   constexpr int Q = 2 * C * Chunk<Real>::kVecs;
-  const int G = step2_grid<Real, LAT, C, NST>(ctx, units, k);
+  const int G = step2_grid<Real, LAT, C, NST, DBL>(ctx, units, k);
   cudaStream_t st = ctx->stream;
   auto launch = [&]() {
-    launch_pdl(k_step2<Real, LAT, C, NST>, G, kBlock2, SMEM, st,
+    launch_pdl(k_step2<Real, LAT, C, NST, DBL>, G, kBlock2, SMEM, st,
         bA, bB, bC, bD, r0, vt, tt, p.Lx, p.Ly, units, partial + (size_t)2 * G * Q,
-        partial + (size_t)3 * G * Q, ctx->d_status, p.realv ? 1 : 0);
+        partial + (size_t)3 * G * Q, ctx->d_status, p.realv ? 1 : 0,
+        DBL ? partial + (size_t)4 * G * Q : nullptr, DBL ? partial + (size_t)5 * G * Q : nullptr);
   };
   launch();  // warm-up
   cudaEventRecord(ctx->ev2, st);
@@ -451,13 +512,15 @@ float time_candidate(kite_ctx* ctx, int k, long long units, const Plan& p, const
   return ms / 3.0f;  // per recursion step
 }
 
-// The two-step pass is a candidate of the plain moment sweep (MODE 0) with enough moments
-// for at least one pass.
+// The two-step pass is a candidate of the plain moment sweep (MODE 0) and of the doubling
+// sweep (MODE 3) with enough moments for at least one pass.
 template <int MODE>
 bool two_step_allowed(const Plan& p) {
   // a field or an open boundary takes the one-step kernel (its variants stage the
   // neighbours the pass would have to rotate or zero in its halo)
-  return MODE == 0 && p.M >= 4 && !p.field && !p.open.x && !p.open.y && pass_steps_pinned() != 1;
+  // (doubling: at least one pass after the first step, ceil(M/2) >= 3)
+  return (MODE == 0 ? p.M >= 4 : (MODE == 3 && p.M >= 5)) && !p.field && !p.open.x && !p.open.y &&
+         pass_steps_pinned() != 1;
 }
 
 template <typename Real, int LAT, int C, int MODE>
@@ -469,10 +532,11 @@ Tune autotune(kite_ctx* ctx, long long units, const Plan& p, const Real* vt, Rea
   // (KITE_PASS_STEPS=3 or KITE_TUNE=...x3): on GB300 it measured slower than the two-step
   // pass wherever the two differ (2.5e11 against 3.2e11 updates/s on the 4096^2 workload:
   // at two CTAs per SM its latency is not hidden), so the autotuner does not time it
-  const bool three_ok = two_ok && p.M >= 5;
+  const bool three_ok = two_ok && MODE == 0 && p.M >= 5;
   const bool three_only = three_ok && pass_steps_pinned() == 3;
   Tune def{kStages, step_occupancy<Real, LAT, C, MODE, kStages>(), 0};
-  if (two_only) def = Tune{5, std::max(1, step2_occupancy<Real, LAT, C, 5>()), 1};
+  constexpr bool DB = MODE == 3;
+  if (two_only) def = Tune{5, std::max(1, step2_occupancy<Real, LAT, C, 5, DB>()), 1};
   if (three_only) def = Tune{8, std::max(1, step3_occupancy<Real, LAT, C, 8>()), 2};
   // KITE_TUNE=<stages>x<CTAs per SM>[x2|x3] pins one configuration (reproducible
   // profiles): stages 4 or 8 (5, 6 or 8 for the two-step pass, 7 or 8 for the three-step
@@ -485,9 +549,9 @@ Tune autotune(kite_ctx* ctx, long long units, const Plan& p, const Real* vt, Rea
         if (occ > 0 && k >= 1) return Tune{nst, std::min(k, occ), 2};
       }
       const bool t2 = two == 2 && two_ok;
-      const int occ = t2 ? (nst == 5   ? step2_occupancy<Real, LAT, C, 5>()
-                            : nst == 6 ? step2_occupancy<Real, LAT, C, 6>()
-                            : nst == 8 ? step2_occupancy<Real, LAT, C, 8>() : 0)
+      const int occ = t2 ? (nst == 5   ? step2_occupancy<Real, LAT, C, 5, DB>()
+                            : nst == 6 ? step2_occupancy<Real, LAT, C, 6, DB>()
+                            : nst == 8 ? step2_occupancy<Real, LAT, C, 8, DB>() : 0)
                          : (nst == 4   ? step_occupancy<Real, LAT, C, MODE, 4>()
                             : nst == 8 ? step_occupancy<Real, LAT, C, MODE, 8>() : 0);
       if (occ > 0 && k >= 1) return Tune{nst, std::min(k, occ), t2 ? 1 : 0};
@@ -520,18 +584,18 @@ Tune autotune(kite_ctx* ctx, long long units, const Plan& p, const Real* vt, Rea
     // it needs two extra iterate buffers)
     const float bar = two_only ? 1e30f : 0.97f * best_ms;
     best2 = bar;
-    const int o8 = step2_occupancy<Real, LAT, C, 8>(), o6 = step2_occupancy<Real, LAT, C, 6>(),
-              o5 = step2_occupancy<Real, LAT, C, 5>();
+    const int o8 = step2_occupancy<Real, LAT, C, 8, DB>(), o6 = step2_occupancy<Real, LAT, C, 6, DB>(),
+              o5 = step2_occupancy<Real, LAT, C, 5, DB>();
     for (int k = 1; k <= o8; ++k) {
-      const float ms = time_candidate2<Real, LAT, C, 8>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
+      const float ms = time_candidate2<Real, LAT, C, 8, DB>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
       if (ms < best2) best2 = ms, best = Tune{8, k, 1};
     }
     for (int k = 1; k <= o6; ++k) {
-      const float ms = time_candidate2<Real, LAT, C, 6>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
+      const float ms = time_candidate2<Real, LAT, C, 6, DB>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
       if (ms < best2 * 0.98f) best2 = ms, best = Tune{6, k, 1};
     }
     for (int k = 1; k <= o5; ++k) {
-      const float ms = time_candidate2<Real, LAT, C, 5>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
+      const float ms = time_candidate2<Real, LAT, C, 5, DB>(ctx, k, units, p, vt, tt, r0, bA, bB, bC, bD, partial);
       if (ms < best2 * 0.98f) best2 = ms, best = Tune{5, k, 1};
     }
   }
@@ -558,9 +622,9 @@ int max_grid_c(kite_ctx* ctx, int C, long long units) {
   auto occ = [&](auto cc) {
     constexpr int CC = decltype(cc)::value;
     int o = std::max(step_occupancy<Real, LAT, CC, MODE, 8>(), step_occupancy<Real, LAT, CC, MODE, 4>());
-    if (MODE == 0)
-      o = std::max({o, step2_occupancy<Real, LAT, CC, 8>(), step2_occupancy<Real, LAT, CC, 6>(),
-                    step2_occupancy<Real, LAT, CC, 5>()});
+    if (MODE == 0 || MODE == 3)
+      o = std::max({o, step2_occupancy<Real, LAT, CC, 8, MODE == 3>(), step2_occupancy<Real, LAT, CC, 6, MODE == 3>(),
+                    step2_occupancy<Real, LAT, CC, 5, MODE == 3>()});
     return o;
   };
   if (C == 1) return g(occ(std::integral_constant<int, 1>{}));
@@ -694,7 +758,7 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
   Carver cv(nullptr);
   // two more iterate buffers when the two-step pass may run (its outputs never alias its
   // inputs)
-  const bool two_possible = !p.doubling && p.M >= 4 && !p.field && pass_steps_pinned() != 1;
+  const bool two_possible = (p.doubling ? p.M >= 5 : p.M >= 4) && !p.field && pass_steps_pinned() != 1;
   // the cluster sweep's moment partials (16 CTAs per lane, the larger size)
   const size_t cluster_part =
       (p.field || cluster_pinned() == 1)
@@ -788,6 +852,20 @@ int run_typed(kite_ctx* ctx, const kite_system* sys, const kite_kpm* kpm, const 
                                                                  &step_bytes);                       \
       };                                                                                            \
       rc = t.nst == 7 ? run3(std::integral_constant<int, 7>{}) : run3(std::integral_constant<int, 8>{}); \
+    } else if (t.two && p.doubling) {                                                               \
+      const int G = t.nst == 5   ? step2_grid<Real, LAT, CC, 5, true>(ctx, u, t.k)                  \
+                    : t.nst == 6 ? step2_grid<Real, LAT, CC, 6, true>(ctx, u, t.k)                  \
+                                 : step2_grid<Real, LAT, CC, 8, true>(ctx, u, t.k);                 \
+      grid_used = G;                                                                                \
+      auto run2 = [&](auto nst) {                                                                   \
+        return sweep_two_dbl<Real, LAT, CC, decltype(nst)::value>(ctx, p, vt, tt, r0, bA, bB, bC, bD, \
+                                                                   partial, G, u, nvec, vec_base, ne, \
+                                                                   mu_vec, &lp, &lc, &step_s,        \
+                                                                   &step_n, &step_bytes);            \
+      };                                                                                            \
+      rc = t.nst == 5   ? run2(std::integral_constant<int, 5>{})                                    \
+           : t.nst == 6 ? run2(std::integral_constant<int, 6>{})                                    \
+                        : run2(std::integral_constant<int, 8>{});                                   \
     } else if (t.two) {                                                                             \
       const int G = t.nst == 5   ? step2_grid<Real, LAT, CC, 5>(ctx, u, t.k)                        \
                     : t.nst == 6 ? step2_grid<Real, LAT, CC, 6>(ctx, u, t.k)                        \

@@ -24,15 +24,18 @@
 namespace kite {
 namespace {
 
-template <int LAT, int C, int NST>
+// DBL: the moment-doubling pass (no r_0 staged; four moment slots per pass, their FP64
+// partials kept in shared memory: kBlock threads x 4 slots x 4 doubles at most).
+template <int LAT, int C, int NST, bool DBL = false>
 struct Step2Shape {
   using S1 = StepShape<LAT, C, NST>;
   static constexpr int SORB = S1::SORB, TPC = S1::TPC, TX = S1::TX, CELLB = S1::CELLB;
   static constexpr int RNB = (TX + 4) * CELLB;  // r_n row, two halo cells each side
-  static constexpr int R0B = TX * CELLB;        // r_0 row
+  static constexpr int R0B = DBL ? 0 : TX * CELLB;  // r_0 row
   static constexpr int STAGEB = RNB + R0B;      // (r_{n-1} is read once per site: registers)
   static constexpr int TILEB = (TX + 2) * CELLB;  // one r_{n+1} row of the tile ring
-  static constexpr int SMEM = kBarBytes + NST * STAGEB + 4 * TILEB;
+  static constexpr int DACCB = DBL ? kBlock * 4 * 4 * 8 : 0;
+  static constexpr int SMEM = kBarBytes + NST * STAGEB + 4 * TILEB + DACCB;
 };
 
 // Threads: kBlock compute threads (one 16-byte chunk of an owned cell each, as in the
@@ -41,16 +44,20 @@ struct Step2Shape {
 // compute warps carry equal work between the barriers.
 constexpr int kBlock2 = kBlock + 32;
 
-template <typename Real, int LAT, int C, int NST>
+// Plain moments: partial1 <- <r_0|r_{n+1}>, partial2 <- <r_0|r_{n+2}>.  DBL (moment doubling,
+// the slots of k_undouble): partial1 <- <r_n|r_n>, partial2 <- <r_n|r_{n+1}>, partial3 <-
+// <r_{n+1}|r_{n+1}>, partial4 <- <r_{n+1}|r_{n+2}> (slots 2n .. 2n+3); r0 is not read.
+template <typename Real, int LAT, int C, int NST, bool DBL = false>
 __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const void* __restrict__ r_prev,
                                            const void* __restrict__ r_cur, void* __restrict__ out1,
                                            void* __restrict__ out2, const void* __restrict__ r0,
                                            const Real* __restrict__ vt, Real tt, int Lx, int Ly, long long units,
                                            double* __restrict__ partial1, double* __restrict__ partial2,
-                                           int* __restrict__ err, int realv) {
+                                           int* __restrict__ err, int realv, double* __restrict__ partial3 = nullptr,
+                                           double* __restrict__ partial4 = nullptr) {
   using Ch = Chunk<Real>;
   using Acc = typename AccT<Real>::T;
-  using Sh = Step2Shape<LAT, C, NST>;
+  using Sh = Step2Shape<LAT, C, NST, DBL>;
   const Real tt2 = tt + tt;  // exact; the on-site terms vt hold 2 V~
   constexpr int VPC = Ch::kVecs, NR = Ch::kReals;
   constexpr int SORB = Sh::SORB, TPC = Sh::TPC, TX = Sh::TX, CELLB = Sh::CELLB;
@@ -84,6 +91,19 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
 #pragma unroll
   for (int k = 0; k < QT; ++k) dacc1[k] = dacc2[k] = 0.0, facc1[k] = facc2[k] = Acc(0);
   int rows1 = 0, rows2 = 0;
+  // doubling: the <r|r> halves of the two levels in FP32 (facc1/facc2 take <r|r_next>), the
+  // FP64 sums of all four slots in this thread's row of shared memory
+  Acc gacc1[QT], gacc2[QT];
+#pragma unroll
+  for (int k = 0; k < QT; ++k) gacc1[k] = gacc2[k] = Acc(0);
+  double* dsm = DBL ? reinterpret_cast<double*>(ring.stages + NST * Sh::STAGEB + 4 * Sh::TILEB) +
+                          (size_t)(compute ? tid : 0) * 4 * QT
+                    : nullptr;
+  if constexpr (DBL) {
+    if (compute)
+#pragma unroll
+      for (int k = 0; k < 4 * QT; ++k) dsm[k] = 0.0;
+  }
   long long gslot = ring.gslot;
   bool aborted = false;
 
@@ -122,7 +142,7 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
       int row = yb - 2 + jj;
       while (row < 0) row += Ly;
       while (row >= Ly) row -= Ly;
-      const bool need_r0 = jj >= 2 && jj <= nr + 1;  // owned rows
+      const bool need_r0 = !DBL && jj >= 2 && jj <= nr + 1;  // owned rows
       const uint32_t bytes = (uint32_t)(txv + 4) * CELLB + (need_r0 ? (uint32_t)txv * CELLB : 0u);
       mbar_arrive_expect_tx(&bars[st], bytes);
       const size_t roff = (size_t)row * Lx * CELLB;
@@ -221,6 +241,36 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
       }
     };
 
+    // doubling: fr <- <me|out> (complex chain as in the one-step kernel), fg <- <me|me>
+    // (real part); every kFlushRows rows both go into this thread's FP64 slots ka, kb
+    auto accumulate_dbl = [&](Acc(&fr)[QT], Acc(&fg)[QT], int& rows, int ka, int kb, const Ch& me,
+                              const Ch& out) {
+      if (realv) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+          const Acc a = me.v[k], b = out.v[k];
+          fr[k] += a * b;
+          fg[k] += a * a;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < VPC; ++q) {
+          cacc(fr[2 * q], fr[2 * q + 1], me.v[2 * q], me.v[2 * q + 1], out.v[2 * q], out.v[2 * q + 1]);
+          const Acc ar = me.v[2 * q], ai = me.v[2 * q + 1];
+          fg[2 * q] = rfma(ai, ai, rfma(ar, ar, fg[2 * q]));
+        }
+      }
+      if (++rows == kFlushRows) {
+        rows = 0;
+#pragma unroll
+        for (int k = 0; k < QT; ++k) {
+          dsm[ka * QT + k] += (double)fg[k];
+          dsm[kb * QT + k] += (double)fr[k];
+          fr[k] = fg[k] = Acc(0);
+        }
+      }
+    };
+
     const bool active = compute && xl < txv;
     // on-site terms prefetched one row ahead: the owned (or halo) cell of r_{n+1} row
     // y1 = yb-1+i; r_{n+2} row y2 = y1-1 reuses the previous row's value
@@ -290,8 +340,13 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         *reinterpret_cast<Ch*>(t3 + (xl + 1) * CELLB + choff) = o;
         if (i >= 1 && i <= nr) {
           o.st(po1, 0);
-          const Ch z0 = *reinterpret_cast<const Ch*>(mid + Sh::RNB + xl * CELLB + choff);
-          accumulate(facc1, dacc1, rows1, z0, o);
+          if constexpr (DBL) {
+            const Ch me = *reinterpret_cast<const Ch*>(mid + (xl + 2) * CELLB + choff);  // r_n
+            accumulate_dbl(facc1, gacc1, rows1, 0, 1, me, o);
+          } else {
+            const Ch z0 = *reinterpret_cast<const Ch*>(mid + Sh::RNB + xl * CELLB + choff);
+            accumulate(facc1, dacc1, rows1, z0, o);
+          }
         }
       }
       if (do1 && ok && halo) {  // halo cell left (tile cell 0) or right (tile cell txv+1)
@@ -303,8 +358,13 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
         const unsigned char* prev = stages + stm * Sh::STAGEB;
         const Ch o = site2(tile + o0, tile + o1, tile + o2, prev, vm2);
         o.st(po2, 0);
-        const Ch z0 = *reinterpret_cast<const Ch*>(prev + Sh::RNB + xl * CELLB + choff);
-        accumulate(facc2, dacc2, rows2, z0, o);
+        if constexpr (DBL) {
+          const Ch me = *reinterpret_cast<const Ch*>(tile + o1 + (xl + 1) * CELLB + choff);  // r_{n+1}
+          accumulate_dbl(facc2, gacc2, rows2, 2, 3, me, o);
+        } else {
+          const Ch z0 = *reinterpret_cast<const Ch*>(prev + Sh::RNB + xl * CELLB + choff);
+          accumulate(facc2, dacc2, rows2, z0, o);
+        }
       }
       vm2 = vm1;
       vm1 = v1;
@@ -358,21 +418,38 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
   // partial1 <- <r_0|r_{n+1}>, partial2 <- <r_0|r_{n+2}>: fixed-order sums over the compute
   // threads holding each chunk, as in the one-step kernel (the ring is drained; its
   // memory is reused)
-#pragma unroll
-  for (int k = 0; k < QT; ++k) dacc1[k] += (double)facc1[k], dacc2[k] += (double)facc2[k];
   double* red = reinterpret_cast<double*>(stages);
   constexpr int Q = C * QT;
+  if constexpr (DBL) {
+    // slot k's FP64 sum from shared memory plus the FP32 rows since the last flush
+    double* const outs[4] = {partial1, partial2, partial3, partial4};
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      double d[QT];
+#pragma unroll
+      for (int k = 0; k < QT; ++k) {
+        const Acc f = kk == 0 ? gacc1[k] : kk == 1 ? facc1[k] : kk == 2 ? gacc2[k] : facc2[k];
+        d[k] = compute ? dsm[kk * QT + k] + (double)f : 0.0;
+      }
+      if (kk) __syncthreads();
+      cta_lane_sums<QT, C>(d, compute, red, outs[kk] + (size_t)cta * Q);
+    }
+    return true;
+  }
+#pragma unroll
+  for (int k = 0; k < QT; ++k) dacc1[k] += (double)facc1[k], dacc2[k] += (double)facc2[k];
   cta_lane_sums<QT, C>(dacc1, compute, red, partial1 + (size_t)cta * Q);
   __syncthreads();
   cta_lane_sums<QT, C>(dacc2, compute, red, partial2 + (size_t)cta * Q);
   return true;
 }
 
-template <typename Real, int LAT, int C, int NST>
-__global__ void __launch_bounds__(kBlock2, 3 * Step2Shape<LAT, C, NST>::SMEM <= 227 * 1024 ? 3 : 2)
+template <typename Real, int LAT, int C, int NST, bool DBL = false>
+__global__ void __launch_bounds__(kBlock2, 3 * Step2Shape<LAT, C, NST, DBL>::SMEM <= 227 * 1024 ? 3 : 2)
     k_step2(const void* r_prev, const void* __restrict__ r_cur, void* out1, void* out2,
             const void* __restrict__ r0, const Real* __restrict__ vt, Real tt, int Lx, int Ly, long long units,
-            double* __restrict__ partial1, double* __restrict__ partial2, int* __restrict__ err, int realv) {
+            double* __restrict__ partial1, double* __restrict__ partial2, int* __restrict__ err, int realv,
+            double* __restrict__ partial3 = nullptr, double* __restrict__ partial4 = nullptr) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
@@ -384,18 +461,19 @@ __global__ void __launch_bounds__(kBlock2, 3 * Step2Shape<LAT, C, NST>::SMEM <= 
   Ring ring{bars, smem + kBarBytes, &s_abort, 0};
   griddep_wait();  // the previous launch's iterates and partials are complete
   griddep_launch_dependents();
-  step2_body<Real, LAT, C, NST>(ring, blockIdx.x, gridDim.x, r_prev, r_cur, out1, out2, r0, vt, tt, Lx, Ly,
-                                units, partial1, partial2, err, realv);
+  step2_body<Real, LAT, C, NST, DBL>(ring, blockIdx.x, gridDim.x, r_prev, r_cur, out1, out2, r0, vt, tt, Lx, Ly,
+                                     units, partial1, partial2, err, realv, partial3, partial4);
 }
 
-template <typename Real, int LAT, int C, int NST>
+template <typename Real, int LAT, int C, int NST, bool DBL = false>
 int step2_occupancy() {
   static int occ = -1;
   if (occ < 0) {
     int o = 0;
-    const int smem = Step2Shape<LAT, C, NST>::SMEM;
-    cudaFuncSetAttribute(k_step2<Real, LAT, C, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_step2<Real, LAT, C, NST>, kBlock2, smem) != cudaSuccess)
+    const int smem = Step2Shape<LAT, C, NST, DBL>::SMEM;
+    cudaFuncSetAttribute(k_step2<Real, LAT, C, NST, DBL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_step2<Real, LAT, C, NST, DBL>, kBlock2, smem) !=
+        cudaSuccess)
       o = 0;
     occ = o;
   }

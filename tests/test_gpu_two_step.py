@@ -46,7 +46,7 @@ def pass_steps(v):
             os.environ["KITE_PASS_STEPS"] = old
 
 
-def run(ctx, d, M, R, precision=kite.FP32, r0=None, want_last=False, real_vectors=False, S=1):
+def run(ctx, d, M, R, precision=kite.FP32, r0=None, want_last=False, real_vectors=False, S=1, doubling=False):
     s = kite.make_system(**d)
     n = oracle.norb(oracle.make_system(**d))
     r0a = None
@@ -54,7 +54,7 @@ def run(ctx, d, M, R, precision=kite.FP32, r0=None, want_last=False, real_vector
         r0a = np.ascontiguousarray(np.stack([r0.real, r0.imag], -1).astype(np.float64))
     dt = np.complex64 if precision == kite.FP32 else np.complex128
     last = np.zeros((S * R, 2, n), dt) if want_last else None
-    kpm = kite.make_kpm(M, R, S, precision, 0.0, 0.0, r0a, last, real_vectors=real_vectors)
+    kpm = kite.make_kpm(M, R, S, precision, 0.0, 0.0, r0a, last, real_vectors=real_vectors, doubling=doubling)
     mu = np.zeros(M, np.float64)
     muv = np.zeros((S * R, M, 2), np.float64)
     st = kite.moments_1d(ctx, s, kpm, mu, muv)
@@ -207,3 +207,43 @@ def test_two_step_full_size_sampled_sites_match_window_oracle(ctx):
     # the grids differ (occupancy of the two kernels): moments agree to FP32 regrouping
     assert np.max(np.abs(out["1"][1] - out["2"][1])) <= 1e-7
     assert abs(out["2"][1][0] - 1.0) <= 1e-6
+
+
+DOUBLING = [
+    # (case, precision, real vectors, S, bar): M odd and even, passes with and without an
+    # odd remainder step, padded batches, realisations
+    (CASES[0], "fp32", False, 1, 1e-5), (CASES[1], "fp32", False, 2, 1e-5), (CASES[3], "fp64", False, 1, 1e-12),
+    (CASES[4], "fp32", False, 1, 1e-5), (CASES[5], "fp64", False, 1, 1e-12), (CASES[8], "fp32", False, 1, 1e-5),
+    (CASES[0], "fp32", True, 1, 1e-5), (CASES[2], "fp64", True, 2, 1e-12),
+]
+
+
+@pytest.mark.parametrize("case,prec,realv,S,bar", DOUBLING)
+def test_two_step_doubling_against_oracle_and_one_step(ctx, case, prec, realv, S, bar):
+    """Moment doubling through the two-step pass (slots <r_n|r_n>, <r_n|r_{n+1}>,
+    <r_{n+1}|r_{n+1}>, <r_{n+1}|r_{n+2}> per pass, no r_0 read): against the oracle's plain
+    moments, and bit-identical to the one-step doubling sweep where both launch one CTA per
+    row unit."""
+    d, R, M = sysd(case, 81)
+    if M < 5:
+        pytest.skip("no pass")
+    precision = kite.FP64 if prec == "fp64" else kite.FP32
+    with pass_steps("2"):
+        mu2, muv2, _, st2 = run(ctx, d, M, R, precision=precision, real_vectors=realv, S=S, doubling=True)
+    with pass_steps("1"):
+        mu1, muv1, _, st1 = run(ctx, d, M, R, precision=precision, real_vectors=realv, S=S, doubling=True)
+    assert st2.steps_per_pass == 2 and st1.steps_per_pass == 1
+    steps = (M + 1) // 2
+    max_batch = (16 if realv else 8) if prec == "fp32" else (8 if realv else 4)
+    batches = S * -(-R // max_batch)
+    assert st2.step_launches == batches * (1 + (steps - 1) // 2 + (steps - 1) % 2)
+    s = oracle.make_system(**d)
+    ref = np.concatenate([oracle.moments_1d(s, M, R, realisation=k,
+                                            r0=oracle.random_real(s, R, k) if realv else None)
+                          for k in range(S)], 0)
+    assert np.max(np.abs(muv2 - ref)) <= bar
+    assert np.max(np.abs(mu2 - ref.real.mean(0))) <= bar
+    if st1.grid == st2.grid:
+        assert np.array_equal(muv1, muv2)
+    else:
+        assert np.max(np.abs(muv1 - muv2)) <= (1e-7 if prec == "fp32" else 1e-13)
