@@ -138,16 +138,16 @@ __global__ void __launch_bounds__(kBlock, 3)  // <= 85 registers: three CTAs fit
   }
 }
 
-// The batched sweep with temporal blocking (plain moments, no field), after a one-step
-// launch of k_batched has written every system's r_1 (and the moments 0, 1): passes of two
-// steps (r_{n-1}, r_n) -> (r_{n+1}, r_{n+2}) with the moments n+1, n+2 (the two-step body
-// of kite_step2.cuh) and a team barrier after each.  When r_1 .. r_last leaves an odd step,
-// the last pass also computes r_{last+1} (its moment lands in the spare slot M, unread), so
-// the kernel holds the two-step body alone.
+// The batched sweep with temporal blocking (no field), after a one-step launch of k_batched
+// has written every system's r_1 (and the moment slots 0, 1): passes of two steps (r_{n-1},
+// r_n) -> (r_{n+1}, r_{n+2}) with the moments n+1, n+2 -- or, with doubling, the slots
+// 2n .. 2n+3 -- (the two-step body of kite_step2.cuh) and a team barrier after each.  When
+// r_1 .. r_last leaves an odd step, the last pass also computes r_{last+1} (its moment slots
+// lie past M - 1, unread), so the kernel holds the two-step body alone.
 // Iterate k >= 1 lives in buffer k mod 4 so that a pass's outputs never alias its inputs.
-template <int LAT, int C, int NST>
+template <int LAT, int C, int NST, bool DBL = false>
 struct Batched2Shape {
-  static constexpr int SMEM = Step2Shape<LAT, C, NST>::SMEM;
+  static constexpr int SMEM = Step2Shape<LAT, C, NST, DBL>::SMEM;
 };
 
 // Two CTAs per SM: the per-system state that the persistent loop carries around the pass
@@ -157,7 +157,7 @@ struct Batched2Shape {
 #ifndef KITE_BATCHED2_MIN_CTAS
 #define KITE_BATCHED2_MIN_CTAS 2
 #endif
-template <int LAT, int C, int NST>
+template <int LAT, int C, int NST, bool DBL = false>
 __global__ void __launch_bounds__(kBlock2, KITE_BATCHED2_MIN_CTAS)
     k_batched2(const BSys* __restrict__ systems, const BTeam* __restrict__ teams,
                const int* __restrict__ order, const int* __restrict__ cta_team,
@@ -192,12 +192,18 @@ __global__ void __launch_bounds__(kBlock2, KITE_BATCHED2_MIN_CTAS)
     void* const bufs[4] = {S.bC, S.bA, S.bB, S.bD};
     auto w4 = [&](int n) -> void* { return n == 0 ? const_cast<void*>(S.r0) : bufs[n & 3]; };
     auto slot = [&](int k) { return S.partial + (size_t)k * T.ncta * Q; };
-    const int full = max(S.M - 1, 1);
+    const int full = DBL ? (S.M + 1) / 2 : max(S.M - 1, 1);
     const int last = mcap > 0 ? min(full, mcap) : full;  // iterates r_1 .. r_last
     for (int n = 1; n + 1 <= last; n += 2) {
-      if (!step2_body<float, LAT, C, NST>(ring, rank, T.ncta, w4(n - 1), w4(n), w4(n + 1), w4(n + 2), S.r0,
-                                          S.vt, S.tt, S.Lx, S.Ly, S.units, slot(n + 1), slot(n + 2), err, 0))
-        return;
+      // plain: moments n+1, n+2; doubling: slots 2n .. 2n+3 (<r_n|r_n>, <r_n|r_{n+1}>, ...)
+      const bool ok = DBL ? step2_body<float, LAT, C, NST, true>(ring, rank, T.ncta, w4(n - 1), w4(n), w4(n + 1),
+                                                                 w4(n + 2), nullptr, S.vt, S.tt, S.Lx, S.Ly,
+                                                                 S.units, slot(2 * n), slot(2 * n + 1), err, 0,
+                                                                 slot(2 * n + 2), slot(2 * n + 3))
+                          : step2_body<float, LAT, C, NST>(ring, rank, T.ncta, w4(n - 1), w4(n), w4(n + 1),
+                                                           w4(n + 2), S.r0, S.vt, S.tt, S.Lx, S.Ly, S.units,
+                                                           slot(n + 1), slot(n + 2), err, 0);
+      if (!ok) return;
       if (!sync_team()) return;
     }
   }
@@ -293,16 +299,17 @@ inline int batched_pass_steps_pinned() {
   return (e && (e[0] == '1' || e[0] == '2') && e[1] == 0) ? e[0] - '0' : 0;
 }
 
-template <int LAT, int C, int NST>
+template <int LAT, int C, int NST, bool DBL = false>
 int batched2_occupancy() {
   static int occ = -1;
   if (occ < 0) {
-    constexpr int SMEM = Batched2Shape<LAT, C, NST>::SMEM;
+    constexpr int SMEM = Batched2Shape<LAT, C, NST, DBL>::SMEM;
     int o = 0;
     if (SMEM > 227 * 1024 ||
-        cudaFuncSetAttribute(k_batched2<LAT, C, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) !=
+        cudaFuncSetAttribute(k_batched2<LAT, C, NST, DBL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batched2<LAT, C, NST>, kBlock2, SMEM) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batched2<LAT, C, NST, DBL>, kBlock2, SMEM) !=
+            cudaSuccess)
       o = 0;
     cudaGetLastError();
     occ = o;
@@ -357,12 +364,12 @@ cudaError_t launch_batched(kite_ctx* ctx, const BPlan& pl, const BSys* d_sys, co
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const int* cta_team = d_ints + pl.sc.order.size();
-  if constexpr (!DBL && !FIELD) {
+  if constexpr (!FIELD) {
     if (pl.two) {
       // every system's first step with the one-step kernel (capped at one step), then the
       // passes; the team barrier counters start again from zero
-      cfg.dynamicSmemBytes = StepShape<LAT, C, 4>::template smem_bytes<0>();
-      cudaError_t ce = cudaLaunchKernelEx(&cfg, k_batched<LAT, C, false, 4, false>, d_sys, d_teams, d_ints, cta_team,
+      cfg.dynamicSmemBytes = StepShape<LAT, C, 4>::template smem_bytes<DBL ? 3 : 0>();
+      cudaError_t ce = cudaLaunchKernelEx(&cfg, k_batched<LAT, C, DBL, 4, false>, d_sys, d_teams, d_ints, cta_team,
                                           counters, ctx->d_status, stall, 1);
       if (ce == cudaSuccess)
         ce = cudaMemsetAsync(counters, 0, sizeof(unsigned int) * pl.sc.teams.size(), ctx->stream);
@@ -370,8 +377,8 @@ cudaError_t launch_batched(kite_ctx* ctx, const BPlan& pl, const BSys* d_sys, co
       cfg.blockDim = dim3(kBlock2);
       auto go = [&](auto nst) {
         constexpr int NST = decltype(nst)::value;
-        cfg.dynamicSmemBytes = Batched2Shape<LAT, C, NST>::SMEM;
-        return cudaLaunchKernelEx(&cfg, k_batched2<LAT, C, NST>, d_sys, d_teams, d_ints, cta_team, counters,
+        cfg.dynamicSmemBytes = Batched2Shape<LAT, C, NST, DBL>::SMEM;
+        return cudaLaunchKernelEx(&cfg, k_batched2<LAT, C, NST, DBL>, d_sys, d_teams, d_ints, cta_team, counters,
                                   ctx->d_status, 0, mcap);
       };
       return pl.nst == 5   ? go(std::integral_constant<int, 5>{})
@@ -412,9 +419,9 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
   if (occ8 < 1 && occ4 < 1) return fail(ctx, KITE_ERR_CUDA, "occupancy query for the batched kernel failed");
   const bool tune = autotune_enabled_batched() && count > 1;
   const int pin = batched_pass_steps_pinned();
-  // the two-step kernel: plain moments without a field, every system with M >= 4
-  bool two_ok = !DBL && !FIELD && pin != 1;
-  for (int i = 0; i < count; ++i) two_ok = two_ok && kpm[i].M >= 4;
+  // the two-step kernel: no field, every system with M >= 4 (doubling: M >= 5)
+  bool two_ok = !FIELD && pin != 1;
+  for (int i = 0; i < count; ++i) two_ok = two_ok && kpm[i].M >= (DBL ? 5 : 4);
   if (pin != 2 || !two_ok) {
     for (int nst : {8, 4}) {
       const int occ = nst == 8 ? occ8 : occ4;
@@ -430,8 +437,8 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
   }
   if (two_ok && (tune || pin == 2)) {
     for (int nst : {8, 6, 5}) {
-      const int occ = nst == 8 ? batched2_occupancy<LAT, C, 8>()
-                               : (nst == 6 ? batched2_occupancy<LAT, C, 6>() : batched2_occupancy<LAT, C, 5>());
+      const int occ = nst == 8 ? batched2_occupancy<LAT, C, 8, DBL>()
+                               : (nst == 6 ? batched2_occupancy<LAT, C, 6, DBL>() : batched2_occupancy<LAT, C, 5, DBL>());
       // (the first-step launch runs the one-step kernel with four stages on the same grid)
       for (int k = std::min(2, occ); k <= std::min(occ, occ4); ++k) {
         BPlan pl;
@@ -465,7 +472,8 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
         if (record) off_ph[i] = (size_t)ph;
       }
       char* b = k.take<char>((has_two ? 5 : 3) * vb);
-      char* c = k.take<char>(sizeof(double) * (size_t)(std::max(kpm[i].M, 2) + 1) * max_ncta[i] * Q);
+      // (the two-step doubling pass may write slots up to M + 2)
+      char* c = k.take<char>(sizeof(double) * (size_t)(std::max(kpm[i].M, 2) + 3) * max_ncta[i] * Q);
       if (record) {
         off_vt[i] = (size_t)a;
         off_vec[i] = (size_t)b;
@@ -676,11 +684,11 @@ int run_batched(kite_ctx* ctx, int count, const kite_system* sys, const kite_kpm
       const double N = (double)sys[i].Lx * sys[i].Ly * SORB;
       upd += (double)ne_h[i] * kpm[i].M * R;
       if (pl.two) {
-        // first step: r_0 in, r_1 out; a pass: r_{n-1}, r_n, r_0 in, r_{n+1}, r_{n+2} out; the
-        // on-site term once per step or pass
-        // (an odd last step runs as a whole pass)
-        const int last = std::max(kpm[i].M - 1, 1), passes = last / 2;
-        bytes += (2.0 * 8.0 * R + 4.0) * N + passes * (5.0 * 8.0 * R + 4.0) * N;
+        // first step: r_0 in, r_1 out; a pass: r_{n-1}, r_n (and r_0 without doubling) in,
+        // r_{n+1}, r_{n+2} out; the on-site term once per step or pass (an odd last step
+        // runs as a whole pass)
+        const int last = DBL ? steps_of(kpm[i].M) : std::max(kpm[i].M - 1, 1), passes = last / 2;
+        bytes += (2.0 * 8.0 * R + 4.0) * N + passes * ((DBL ? 4.0 : 5.0) * 8.0 * R + 4.0) * N;
       } else {
         // per orbital and step: r_{n-1}, r_n (and r_0 without doubling) in, r_{n+1} out, on-site
         bytes += ((DBL ? 3.0 : 4.0) * 8.0 * R + 4.0) * N * (DBL ? steps_of(kpm[i].M) : std::max(kpm[i].M - 1, 0));

@@ -103,6 +103,22 @@ def test_honeycomb_batch_against_oracle(ctx, steps, doubling, R, monkeypatch):
         assert np.max(np.abs(mu - oracle_mu(sp, R, lattice=oracle.HONEYCOMB))) <= 1e-5, sp
 
 
+@pytest.mark.parametrize("steps", ["1", "2"])
+def test_doubling_batch_pinned_steps_per_pass(ctx, steps, monkeypatch):
+    """Moment doubling with one step per pass or two (the doubling form of the two-step
+    pass: slots 2n .. 2n+3 per pass, an odd last step run as a whole pass): every system
+    within 1e-5 of the oracle's plain moments."""
+    specs = [dict(L=400, Ly=300, W=1.0, M=96, seed=11), dict(L=17, Ly=5, W=0.0, M=33, seed=13),
+             dict(L=130, W=4.0, M=64, seed=14, p=0.02), dict(L=64, W=2.5, M=127, seed=15),
+             dict(L=257, Ly=40, W=3.0, M=48, seed=16), dict(L=9, W=1.0, M=5, seed=17),
+             dict(L=77, W=3.5, M=201, seed=19), dict(L=31, W=2.0, M=6, seed=20)]
+    monkeypatch.setenv("KITE_PASS_STEPS", steps)
+    mus, st = batch(ctx, specs, doubling=True)
+    assert st.steps_per_pass == int(steps)
+    for sp, mu in zip(specs, mus):
+        assert np.max(np.abs(mu - oracle_mu(sp))) <= 1e-5, sp
+
+
 def test_team_barrier_timeout_is_reported(ctx):
     specs = [dict(L=600, W=1.0, M=24, seed=21), dict(L=20, W=1.0, M=8, seed=22)]
     kite.debug_stall_once(ctx)
