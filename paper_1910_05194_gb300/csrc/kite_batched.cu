@@ -147,15 +147,16 @@ __global__ void __launch_bounds__(kBlock, 3)  // <= 85 registers: three CTAs fit
 // Iterate k >= 1 lives in buffer k mod 4 so that a pass's outputs never alias its inputs.
 template <int LAT, int C, int NST, bool DBL = false>
 struct Batched2Shape {
-  static constexpr int SMEM = Step2Shape<LAT, C, NST, DBL>::SMEM;
+  static constexpr int SMEM = Step2Shape<LAT, C, NST, DBL, true>::SMEM;
 };
 
-// Two CTAs per SM: the per-system state that the persistent loop carries around the pass
-// costs registers that the one-launch-per-pass kernel takes from its parameters; squeezed
-// to three CTAs per SM (72 registers) it spills, and measured 1.35e11 against 2.23e11
-// updates/s on the 256-system square-lattice batch.
+// Three CTAs per SM (72 registers): the per-system state that the persistent loop carries
+// around the pass costs registers that the one-launch-per-pass kernel takes from its
+// parameters, so the pass keeps its FP64 moment sums in shared memory (SMACC).  Measured
+// on the 256-system square-lattice batch: 2.46e11 updates/s (2.30e11 at two CTAs per SM;
+// 1.35e11 at three with the sums in registers, which spilled).
 #ifndef KITE_BATCHED2_MIN_CTAS
-#define KITE_BATCHED2_MIN_CTAS 2
+#define KITE_BATCHED2_MIN_CTAS 3
 #endif
 template <int LAT, int C, int NST, bool DBL = false>
 __global__ void __launch_bounds__(kBlock2, KITE_BATCHED2_MIN_CTAS)
@@ -200,9 +201,9 @@ __global__ void __launch_bounds__(kBlock2, KITE_BATCHED2_MIN_CTAS)
                                                                  w4(n + 2), nullptr, S.vt, S.tt, S.Lx, S.Ly,
                                                                  S.units, slot(2 * n), slot(2 * n + 1), err, 0,
                                                                  slot(2 * n + 2), slot(2 * n + 3))
-                          : step2_body<float, LAT, C, NST>(ring, rank, T.ncta, w4(n - 1), w4(n), w4(n + 1),
-                                                           w4(n + 2), S.r0, S.vt, S.tt, S.Lx, S.Ly, S.units,
-                                                           slot(n + 1), slot(n + 2), err, 0);
+                          : step2_body<float, LAT, C, NST, false, true>(
+                                ring, rank, T.ncta, w4(n - 1), w4(n), w4(n + 1), w4(n + 2), S.r0, S.vt, S.tt,
+                                S.Lx, S.Ly, S.units, slot(n + 1), slot(n + 2), err, 0);
       if (!ok) return;
       if (!sync_team()) return;
     }

@@ -25,8 +25,10 @@ namespace kite {
 namespace {
 
 // DBL: the moment-doubling pass (no r_0 staged; four moment slots per pass, their FP64
-// partials kept in shared memory: kBlock threads x 4 slots x 4 doubles at most).
-template <int LAT, int C, int NST, bool DBL = false>
+// partials kept in shared memory: kBlock threads x 4 slots x 4 doubles at most).  SMACC:
+// the plain pass with its two FP64 partials in shared memory as well (fewer registers, for
+// the persistent batched kernel).
+template <int LAT, int C, int NST, bool DBL = false, bool SMACC = false>
 struct Step2Shape {
   using S1 = StepShape<LAT, C, NST>;
   static constexpr int SORB = S1::SORB, TPC = S1::TPC, TX = S1::TX, CELLB = S1::CELLB;
@@ -34,7 +36,7 @@ struct Step2Shape {
   static constexpr int R0B = DBL ? 0 : TX * CELLB;  // r_0 row
   static constexpr int STAGEB = RNB + R0B;      // (r_{n-1} is read once per site: registers)
   static constexpr int TILEB = (TX + 2) * CELLB;  // one r_{n+1} row of the tile ring
-  static constexpr int DACCB = DBL ? kBlock * 4 * 4 * 8 : 0;
+  static constexpr int DACCB = (DBL ? 4 : (SMACC ? 2 : 0)) * kBlock * 4 * 8;
   static constexpr int SMEM = kBarBytes + NST * STAGEB + 4 * TILEB + DACCB;
 };
 
@@ -47,7 +49,7 @@ constexpr int kBlock2 = kBlock + 32;
 // Plain moments: partial1 <- <r_0|r_{n+1}>, partial2 <- <r_0|r_{n+2}>.  DBL (moment doubling,
 // the slots of k_undouble): partial1 <- <r_n|r_n>, partial2 <- <r_n|r_{n+1}>, partial3 <-
 // <r_{n+1}|r_{n+1}>, partial4 <- <r_{n+1}|r_{n+2}> (slots 2n .. 2n+3); r0 is not read.
-template <typename Real, int LAT, int C, int NST, bool DBL = false>
+template <typename Real, int LAT, int C, int NST, bool DBL = false, bool SMACC = false>
 __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const void* __restrict__ r_prev,
                                            const void* __restrict__ r_cur, void* __restrict__ out1,
                                            void* __restrict__ out2, const void* __restrict__ r0,
@@ -57,7 +59,8 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
                                            double* __restrict__ partial4 = nullptr) {
   using Ch = Chunk<Real>;
   using Acc = typename AccT<Real>::T;
-  using Sh = Step2Shape<LAT, C, NST, DBL>;
+  using Sh = Step2Shape<LAT, C, NST, DBL, SMACC>;
+  constexpr bool SMEMSUMS = DBL || SMACC;  // FP64 partials in shared memory
   const Real tt2 = tt + tt;  // exact; the on-site terms vt hold 2 V~
   constexpr int VPC = Ch::kVecs, NR = Ch::kReals;
   constexpr int SORB = Sh::SORB, TPC = Sh::TPC, TX = Sh::TX, CELLB = Sh::CELLB;
@@ -96,13 +99,14 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
   Acc gacc1[QT], gacc2[QT];
 #pragma unroll
   for (int k = 0; k < QT; ++k) gacc1[k] = gacc2[k] = Acc(0);
-  double* dsm = DBL ? reinterpret_cast<double*>(ring.stages + NST * Sh::STAGEB + 4 * Sh::TILEB) +
-                          (size_t)(compute ? tid : 0) * 4 * QT
-                    : nullptr;
-  if constexpr (DBL) {
+  constexpr int NSUM = DBL ? 4 : 2;  // FP64 sums per thread and QT lane
+  double* dsm = SMEMSUMS ? reinterpret_cast<double*>(ring.stages + NST * Sh::STAGEB + 4 * Sh::TILEB) +
+                               (size_t)(compute ? tid : 0) * NSUM * QT
+                         : nullptr;
+  if constexpr (SMEMSUMS) {
     if (compute)
 #pragma unroll
-      for (int k = 0; k < 4 * QT; ++k) dsm[k] = 0.0;
+      for (int k = 0; k < NSUM * QT; ++k) dsm[k] = 0.0;
   }
   long long gslot = ring.gslot;
   bool aborted = false;
@@ -241,6 +245,22 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
       }
     };
 
+    // the plain moment with its FP64 sum in this thread's shared-memory slot ks
+    auto accumulate_sm = [&](Acc(&facc)[QT], int& rows, int ks, const Ch& z0, const Ch& out) {
+      if (realv) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) facc[k] += (Acc)z0.v[k] * (Acc)out.v[k];
+      } else {
+#pragma unroll
+        for (int q = 0; q < VPC; ++q) cacc(facc[2 * q], facc[2 * q + 1], z0.v[2 * q], z0.v[2 * q + 1],
+                                            out.v[2 * q], out.v[2 * q + 1]);
+      }
+      if (++rows == kFlushRows) {
+        rows = 0;
+#pragma unroll
+        for (int k = 0; k < QT; ++k) dsm[ks * QT + k] += (double)facc[k], facc[k] = Acc(0);
+      }
+    };
     // doubling: fr <- <me|out> (complex chain as in the one-step kernel), fg <- <me|me>
     // (real part); every kFlushRows rows both go into this thread's FP64 slots ka, kb
     auto accumulate_dbl = [&](Acc(&fr)[QT], Acc(&fg)[QT], int& rows, int ka, int kb, const Ch& me,
@@ -345,7 +365,8 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
             accumulate_dbl(facc1, gacc1, rows1, 0, 1, me, o);
           } else {
             const Ch z0 = *reinterpret_cast<const Ch*>(mid + Sh::RNB + xl * CELLB + choff);
-            accumulate(facc1, dacc1, rows1, z0, o);
+            if constexpr (SMACC) accumulate_sm(facc1, rows1, 0, z0, o);
+            else accumulate(facc1, dacc1, rows1, z0, o);
           }
         }
       }
@@ -363,7 +384,8 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
           accumulate_dbl(facc2, gacc2, rows2, 2, 3, me, o);
         } else {
           const Ch z0 = *reinterpret_cast<const Ch*>(prev + Sh::RNB + xl * CELLB + choff);
-          accumulate(facc2, dacc2, rows2, z0, o);
+          if constexpr (SMACC) accumulate_sm(facc2, rows2, 1, z0, o);
+          else accumulate(facc2, dacc2, rows2, z0, o);
         }
       }
       vm2 = vm1;
@@ -435,6 +457,13 @@ __device__ __forceinline__ bool step2_body(Ring& ring, int cta, int ncta, const 
       cta_lane_sums<QT, C>(d, compute, red, outs[kk] + (size_t)cta * Q);
     }
     return true;
+  }
+  if constexpr (SMACC) {
+#pragma unroll
+    for (int k = 0; k < QT; ++k) {
+      dacc1[k] = compute ? dsm[k] : 0.0;
+      dacc2[k] = compute ? dsm[QT + k] : 0.0;
+    }
   }
 #pragma unroll
   for (int k = 0; k < QT; ++k) dacc1[k] += (double)facc1[k], dacc2[k] += (double)facc2[k];
