@@ -575,8 +575,11 @@ def main():
                     "step_launches_per_step": dn // args.steps,
                     "step_gbs": db / ds / 1e9, "step_frac": db / ds / 1e9 / peak,
                     "max_abs_diff_vs_plain": float((mu_d - mu).abs().max().item()),
+                    "autotuned": {"ring_stages": st_d.ring_stages, "ctas_per_sm": st_d.ctas_per_sm,
+                                  "steps_per_pass": st_d.steps_per_pass},
                     "note": "mu_2n = 2<r_n|r_n> - mu_0, mu_2n+1 = 2<r_n|r_n+1> - mu_1: ceil(M/2) "
-                            "steps, r_0 not re-read; same M moments, same unit"}
+                            "steps, r_0 not re-read (with two steps per pass: four vector streams per "
+                            "two steps); same M moments, same unit"}
 
     # ---- real +-1 vectors (16 per batch, half the bytes per vector), with doubling -------
     realvec = None
@@ -601,6 +604,8 @@ def main():
         realvec = {"value": v_r, "unit": UNIT, "R": R2,
                    "ms_per_step": ms_r, "step_gbs": rb / rs / 1e9, "step_frac": rb / rs / 1e9 / peak,
                    "max_abs_diff_vs_complex_plain": float((mu_r - mu).abs().max().item()),
+                   "autotuned": {"ring_stages": st_r.ring_stages, "ctas_per_sm": st_r.ctas_per_sm,
+                                 "steps_per_pass": st_r.steps_per_pass},
                    "note": "real +-1 vectors (Sec. 2c white noise) with moment doubling; a real vector "
                            "has twice the trace-estimate variance of a unit-phase one, so R=16 real "
                            "carries the statistical weight of R=8 complex at the same bytes"}
