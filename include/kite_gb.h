@@ -38,7 +38,7 @@ extern "C" {
 #define KITE_ERR_BOUNDS (-4)      /* |mu_n| > 1 + 1e-3 or non-finite: spectrum left
                                      [-1,1] (Eq. e6 requires ||H~|| <= 1)               */
 #define KITE_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up                 */
-#define KITE_ERR_UNSUPPORTED (-6) /* valid request this build does not implement        */
+#define KITE_ERR_UNSUPPORTED (-6) /* valid request the library does not implement      */
 
 /* ---- enums -------------------------------------------------------------------- */
 #define KITE_HONEYCOMB 0 /* Listing 1: a1=[a,0], a2=[a/2, a sqrt3/2], two orbitals A, B   */

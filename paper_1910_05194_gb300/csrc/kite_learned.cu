@@ -6,7 +6,7 @@
 // The paper has no learned component.  Its Sec. 2a notes that the resolution of the
 // Chebyshev reconstruction scales as the inverse number of moments; the model maps the
 // first KITE_MLP_IN moments to the density that many more moments give, and the plain
-// Jackson reconstruction (Eq. e8a) is both its fallback and the judge of its error.
+// Jackson reconstruction (Eq. e8a) is both its fallback and the reference for its error.
 #include <math.h>
 
 #include <string>
