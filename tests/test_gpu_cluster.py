@@ -197,3 +197,16 @@ def test_autotuned_choice_on_the_64x64_workload(ctx):
         print(f"64x64 FP64 M=256 R=4 doubling={dbl}: cluster CTAs {st.cluster_ctas}, "
               f"{st.seconds * 1e3:.3f} ms, {st.step_seconds * 1e3:.3f} ms in the steps")
         assert np.max(np.abs(muv.real - ref.real)) <= 1e-12
+
+
+@pytest.mark.parametrize("prec,M,bar,dbl", [(kite.FP64, 1500, 1e-12, False), (kite.FP64, 1501, 1e-12, True),
+                                           (kite.FP32, 2048, 1e-5, False)])
+def test_cluster_long_sweeps_against_oracle(ctx, prec, M, bar, dbl):
+    """Long sweeps on chip (many 16-moment transposes, a partial last one): FP64 within 1e-12
+    of the oracle, FP32 at the large-DOS workload's order within 1e-5."""
+    d = sysd(oracle.HONEYCOMB, 64, 48, W=2.0, p=0.005, seed=6)
+    mu, muv, _, st = run(ctx, d, M, 4, precision=prec, doubling=dbl)
+    assert st.cluster_ctas >= 8
+    ref = oracle.moments_1d(oracle.make_system(**d), M, 4)
+    assert np.max(np.abs(muv.real - ref.real)) <= bar
+    assert np.max(np.abs(mu - ref.real.mean(0))) <= bar
