@@ -13,7 +13,7 @@
 //     sum of two real dot products.  The imaginary part, <a_0|T_n b_0> - <b_0|T_n a_0>,
 //     vanishes for a symmetric T_n(H~) and is not formed.  Each real recursion (one part
 //     of one complex vector, or one real vector: a "lane") is independent of the others.
-//   * One cluster of CS CTAs (8 to 16, one CTA per SM) runs one lane.  The CTAs split the
+//   * One cluster of CS CTAs (4 to 16, one CTA per SM) runs one lane.  The CTAs split the
 //     lattice's rows; each keeps its rows of r_0, r_{n-1}, r_n and the on-site terms in
 //     shared memory for the whole sweep and writes r_{n+1} over r_{n-1} in place (site o's
 //     r_{n-1} is read by site o alone).

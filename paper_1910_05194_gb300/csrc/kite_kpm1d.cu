@@ -637,7 +637,7 @@ int max_grid_c(kite_ctx* ctx, int C, long long units) {
 // (KITE_CLUSTER_CTAS=2..16 then pins the cluster size); unset, it is a candidate of the
 // autotuner for lattices too small to give the streaming step kernels four work units per
 // SM, and runs when it is measured faster per recursion step.  It needs a real H~ (no
-// field) and at least 8 rows.
+// field) and at least 4 rows.
 inline int cluster_pinned() {  // 0 unset, 1 off, 2 on
   const char* e = getenv("KITE_CLUSTER");
   return (e && (e[0] == '0' || e[0] == '1') && e[1] == 0) ? e[0] - '0' + 1 : 0;
@@ -671,18 +671,23 @@ int cluster_choice(kite_ctx* ctx, const Plan& p, const ClusterSweep& c, long lon
   if (pin == 0 && (!autotune_enabled() || pass_steps_pinned() || getenv("KITE_TUNE") ||
                    units >= 4LL * ctx->num_sms))
     return 0;
-  // Cluster sizes from 16 down to 8 CTAs: more CTAs split the FP64 work of a step further,
-  // but fewer clusters are resident at once (on GB300 7 of 16 CTAs, 15 of 8), and a batch
-  // with more lanes than that runs in two waves.
+  // Cluster sizes from 16 CTAs down: more CTAs split the work of a step further, but fewer
+  // clusters are resident at once (on GB300 7 of 16 CTAs, 8 of 12, 15 of 8), and a batch
+  // with more lanes than that runs in several waves.  The candidates are the largest size
+  // for each number of waves (eight FP64 lanes: 16 and 12 CTAs; sixteen FP32 lanes: 16, 12
+  // and 6).
   const int fixed = cluster_ctas_pinned();
   const int lanes = c.realv ? c.nvec : 2 * c.nvec;
-  int cand[16], nc = 0, one_wave = 0;
-  for (int cs = 16; cs >= 2; --cs) {
-    if (fixed ? cs != fixed : (cs < 8 || cs % 2)) continue;
+  int cand[16], nc = 0, one_wave = 0, fewest = 1 << 30;
+  for (int cs = 16; cs >= (fixed ? 2 : 4); --cs) {
+    if (fixed && cs != fixed) continue;
     const int act = cluster_active(ctx, c, cs);
     if (act < 1) continue;
+    const int waves = (lanes + act - 1) / act;
+    if (waves >= fewest) continue;
+    fewest = waves;
     cand[nc++] = cs;
-    if (!one_wave && act >= lanes) one_wave = cs;
+    if (!one_wave && waves == 1) one_wave = cs;
   }
   if (nc == 0) return 0;
   if (pin == 2) return one_wave ? one_wave : cand[0];

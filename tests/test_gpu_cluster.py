@@ -145,7 +145,7 @@ def test_cluster_moments_match_oracle(ctx, case):
     d, M, R, S, prec, dbl, realv, bar = case
     o = oracle.make_system(**d)
     mu, muv, _, st = run(ctx, d, M, R, S=S, precision=prec, doubling=dbl, real_vectors=realv)
-    assert 8 <= st.cluster_ctas <= 16
+    assert 2 <= st.cluster_ctas <= 16
     per_batch = (16 if prec == kite.FP32 else 8) if realv else (8 if prec == kite.FP32 else 4)
     batches = S * -(-R // per_batch)
     assert st.step_launches == batches
@@ -172,10 +172,10 @@ def test_cluster_sweep_is_deterministic_and_matches_the_streaming_kernels(ctx):
     assert np.max(np.abs(a[0] - s[0])) <= 1e-14
 
 
-def test_cluster_sweep_needs_eight_rows_and_no_field(ctx):
-    d = sysd(oracle.SQUARE, 300, 5, W=3.0, p=0.05)
+def test_cluster_sweep_needs_four_rows_and_no_field(ctx):
+    d = sysd(oracle.SQUARE, 300, 3, W=3.0, p=0.05)
     mu, muv, _, st = run(ctx, d, 33, 2)
-    assert st.cluster_ctas == 0  # 5 rows: the streaming kernels
+    assert st.cluster_ctas == 0  # 3 rows: the streaming kernels
     ref = oracle.moments_1d(oracle.make_system(**d), 33, 2)
     assert np.max(np.abs(muv - ref)) <= 1e-5
     k = kite.make_system(kite.HONEYCOMB, 32, 32, -2.7, 1.0, 0.0, 0.0, 3)
@@ -206,7 +206,7 @@ def test_cluster_long_sweeps_against_oracle(ctx, prec, M, bar, dbl):
     of the oracle, FP32 at the large-DOS workload's order within 1e-5."""
     d = sysd(oracle.HONEYCOMB, 64, 48, W=2.0, p=0.005, seed=6)
     mu, muv, _, st = run(ctx, d, M, 4, precision=prec, doubling=dbl)
-    assert st.cluster_ctas >= 8
+    assert st.cluster_ctas >= 2
     ref = oracle.moments_1d(oracle.make_system(**d), M, 4)
     assert np.max(np.abs(muv.real - ref.real)) <= bar
     assert np.max(np.abs(mu - ref.real.mean(0))) <= bar
