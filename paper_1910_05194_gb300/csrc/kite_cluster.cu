@@ -35,7 +35,6 @@
 // number of them.
 #include <algorithm>
 #include <cstdint>
-#include <cstdio>
 #include <map>
 #include <mutex>
 #include <set>
@@ -459,9 +458,6 @@ int cluster_active(kite_ctx* ctx, const ClusterSweep& a, int cs) {
     std::lock_guard<std::mutex> lock(mu);
     cache[key] = active;
   }
-#ifdef KITE_CLUSTER_PROBE
-  fprintf(stderr, "cluster size %d: %d clusters resident, smem %zu\n", cs, active, cfg.dynamicSmemBytes);
-#endif
   return active;
 }
 
