@@ -1245,3 +1245,35 @@ def test_wave_packet_propagation_matches_dense_exponential():
     printed = np.exp(-1j * 0.5 * (hi + lo) * dt) * np.where(nn == 0, 1.0, 2.0) * (-1.0) ** nn * jv(nn, 0.5 * (hi - lo) * dt)
     bad = oracle.chebyshev_sum(s, printed, psi0)
     assert np.max(np.abs(bad[keep] - U @ psi0[keep])) > 1e-3
+
+
+@pytest.mark.parametrize("lattice", [oracle.HONEYCOMB, oracle.SQUARE])
+def test_complex_moments_split_into_real_and_imaginary_recursions(lattice):
+    """With no field H~ is real and symmetric, so for r_0 = a + i b the moment
+    <r_0|T_n(H~)|r_0> equals <a|T_n a> + <b|T_n b> and its imaginary part vanishes: the
+    reading behind the on-chip cluster sweep (one real recursion per part) and the FP64
+    sweeps (imaginary part not formed), checked on the plain FP64 definition."""
+    s = oracle.make_system(lattice=lattice, Lx=7, Ly=5, t=-2.7 if lattice == oracle.HONEYCOMB else -1.0,
+                           W=2.0, delta=0.3 if lattice == oracle.HONEYCOMB else 0.0, p_vac=0.1, seed=13)
+    n = oracle.norb(s)
+    _, vac = oracle.disorder(s)
+    rng = np.random.default_rng(4)
+    z = (rng.standard_normal((3, n)) + 1j * rng.standard_normal((3, n))) * (vac == 0)
+    M = 40
+    mu = oracle.moments_1d(s, M, 3, r0=z)
+    mu_a = oracle.moments_1d(s, M, 3, r0=z.real.astype(complex))
+    mu_b = oracle.moments_1d(s, M, 3, r0=z.imag.astype(complex))
+    scale = np.max(np.abs(mu))
+    assert np.max(np.abs(mu.imag)) <= 1e-13 * scale
+    assert np.max(np.abs(mu.real - (mu_a.real + mu_b.real))) <= 1e-13 * scale
+    # and in a field (complex Hermitian H~) the split fails while Im still vanishes
+    f = oracle.make_system(lattice=lattice, Lx=7, Ly=6, t=-2.7 if lattice == oracle.HONEYCOMB else -1.0,
+                           W=2.0, p_vac=0.0, seed=13, flux=2 / 6 if lattice == oracle.HONEYCOMB else 1 / 6)
+    nf = oracle.norb(f)
+    zf = rng.standard_normal((2, nf)) + 1j * rng.standard_normal((2, nf))
+    mf = oracle.moments_1d(f, M, 2, r0=zf)
+    mfa = oracle.moments_1d(f, M, 2, r0=zf.real.astype(complex))
+    mfb = oracle.moments_1d(f, M, 2, r0=zf.imag.astype(complex))
+    sf = np.max(np.abs(mf))
+    assert np.max(np.abs(mf.imag)) <= 1e-13 * sf
+    assert np.max(np.abs(mf.real - (mfa.real + mfb.real))) > 1e-6 * sf
