@@ -43,3 +43,24 @@ def test_flux_commensurability_and_open_boundaries(lib_loaded):
     bad.open_y = 3
     with pytest.raises(kite.KiteError):
         kite.bounds(bad)
+
+
+def test_committed_traffic_summary_matches_the_step_kernel_sources():
+    """The bench reports the dominant kernel's DRAM traffic from the committed ncu summary
+    only while the step kernels' sources are the ones measured; this keeps the summary
+    re-measured whenever they change (else the bench line would carry traffic = null)."""
+    import importlib.util
+    import json
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    with open(os.path.join(root, "profiles", "kpm_step2_traffic.json")) as f:
+        summary = json.load(f)
+    assert summary["kernel_source_hash"] == bench.kernel_source_hash()
+    # per launch: the measured bytes per update times the launch's updates; within 2 % of the
+    # algorithmic bytes (no wasted re-reads)
+    per_update = summary["dram_bytes_per_update"]
+    assert bench.profiled_traffic(1.0e6, 2) == pytest.approx(per_update * 1.0e6)
+    assert abs(per_update / summary["algorithmic_bytes_per_update"] - 1.0) <= 0.02
